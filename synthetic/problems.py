@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs for the augmented-Lagrangian Stokes workloads.
+
+This module produces DATA only: coefficient fields sampled at quadrature
+points, right-hand sides, Dirichlet values and sinker centres.  It holds none
+of the discretisation or solver arithmetic, so the FP64 oracle and the GPU
+library can both consume what it writes without sharing any method code.
+
+Sampling layout (the one the C ABI expects):
+  * unit box (0,1)^d, n[k] uniform cells per direction, cell index with the
+    x index fastest;
+  * 3 points per direction inside each cell at the Gauss-Legendre abscissae
+    mapped from [-1,1], point index with the x index fastest;
+  * nodal arrays live on the Q2 node lattice ((2n+1) nodes per direction,
+    x fastest), one array per velocity component.
+
+Workloads follow the multi-sinker benchmark of Sec. 6.2 (viscosity and
+buoyancy law, DR(mu) = mu_max/mu_min with mu_max = DR^(1/2),
+mu_min = DR^(-1/2)) and the manufactured solution used for the convergence
+check.  The readings of the garbled sinker formula are stated in the
+repository's design notes: mu = mu_min + (mu_max - mu_min)(1 - chi) with a
+squared distance in the Gaussian, sinkers are the high-viscosity,
+negatively buoyant inclusions.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Gauss-Legendre abscissae on [-1, 1] for the 3-point rule; these fix WHERE
+# the coefficient fields are sampled (the layout contract of the inputs).
+_SAMPLE_ABSCISSAE = (-math.sqrt(0.6), 0.0, math.sqrt(0.6))
+
+
+def _as_tuple(n, d):
+    if np.isscalar(n):
+        return (int(n),) * d
+    n = tuple(int(v) for v in n)
+    assert len(n) == d
+    return n
+
+
+def level_sizes(n, levels):
+    """Cells per direction on levels 0 (coarsest) .. levels-1 (finest)."""
+    out = []
+    for lvl in range(levels):
+        f = 2 ** (levels - 1 - lvl)
+        for v in n:
+            if v % f:
+                raise ValueError(f"n={n} not divisible by 2^{levels - 1}")
+        out.append(tuple(v // f for v in n))
+    return out
+
+
+def sample_points(d, n):
+    """Physical coordinates of the sampling points, shape (ncells, 3^d, d)."""
+    n = _as_tuple(n, d)
+    g = np.asarray(_SAMPLE_ABSCISSAE)
+    axes = []
+    for k in range(d):
+        h = 1.0 / n[k]
+        c = np.arange(n[k])
+        axes.append(((c[:, None] + 0.5 * (1.0 + g[None, :])) * h))  # (n_k, 3)
+    # cell multi-index (x fastest) and point multi-index (x fastest)
+    cells = np.stack(np.meshgrid(*[np.arange(v) for v in n], indexing="ij"), -1)
+    cells = cells.transpose(*reversed(range(d)), d).reshape(-1, d)  # x fastest
+    pts = np.stack(np.meshgrid(*[np.arange(3)] * d, indexing="ij"), -1)
+    pts = pts.transpose(*reversed(range(d)), d).reshape(-1, d)
+    x = np.empty((cells.shape[0], pts.shape[0], d))
+    for k in range(d):
+        x[:, :, k] = axes[k][cells[:, k][:, None], pts[:, k][None, :]]
+    return x
+
+
+def node_points(d, n):
+    """Coordinates of the Q2 node lattice, shape ((2n+1)^d, d), x fastest."""
+    n = _as_tuple(n, d)
+    ax = [np.arange(2 * v + 1) * (0.5 / v) for v in n]
+    grid = np.meshgrid(*ax, indexing="ij")
+    return np.stack([g.transpose(*reversed(range(d))).reshape(-1) for g in grid], -1)
+
+
+# ----------------------------------------------------------------------------
+# multi-sinker benchmark (Sec. 6.2)
+# ----------------------------------------------------------------------------
+def sinker_centres(seed, count, d):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, size=(count, d))
+
+
+def sinker_chi(x, centres, omega, delta):
+    """chi(x) = prod_i [1 - exp(-delta * max(0, |x - c_i| - omega/2)^2)]."""
+    chi = np.ones(x.shape[:-1])
+    for c in centres:
+        dist = np.sqrt(((x - c) ** 2).sum(-1))
+        s = np.maximum(0.0, dist - 0.5 * omega)
+        chi *= 1.0 - np.exp(-delta * s * s)
+    return chi
+
+
+def sinker_viscosity(x, centres, omega, delta, dr):
+    mu_max, mu_min = math.sqrt(dr), 1.0 / math.sqrt(dr)
+    chi = sinker_chi(x, centres, omega, delta)
+    return mu_min + (mu_max - mu_min) * (1.0 - chi)
+
+
+def sinker_force(x, centres, omega, delta, beta):
+    """f = (0, .., -beta (1 - chi)): buoyancy pulling the sinkers down."""
+    chi = sinker_chi(x, centres, omega, delta)
+    f = np.zeros(x.shape)
+    f[..., -1] = -beta * (1.0 - chi)
+    return f
+
+
+# ----------------------------------------------------------------------------
+# manufactured solution (2D): u = (sin pi x sin pi y, cos pi x cos pi y), p = 0
+# ----------------------------------------------------------------------------
+def manufactured_u(x):
+    px, py = math.pi * x[..., 0], math.pi * x[..., 1]
+    return np.stack([np.sin(px) * np.sin(py), np.cos(px) * np.cos(py)], -1)
+
+
+def manufactured_grad_u(x):
+    """Exact gradient, shape (..., 2, 2), [..., comp, direction]."""
+    px, py = math.pi * x[..., 0], math.pi * x[..., 1]
+    g = np.empty(x.shape[:-1] + (2, 2))
+    g[..., 0, 0] = math.pi * np.cos(px) * np.sin(py)
+    g[..., 0, 1] = math.pi * np.sin(px) * np.cos(py)
+    g[..., 1, 0] = -math.pi * np.sin(px) * np.cos(py)
+    g[..., 1, 1] = -math.pi * np.cos(px) * np.sin(py)
+    return g
+
+
+def manufactured_f(x):
+    """-div(2 eps(u)) + grad p with mu = 1, p = 0, div u = 0: f = 2 pi^2 u."""
+    return 2.0 * math.pi ** 2 * manufactured_u(x)
+
+
+# ----------------------------------------------------------------------------
+# problem bundles
+# ----------------------------------------------------------------------------
+@dataclass
+class Problem:
+    """Everything a solve needs, for every multigrid level."""
+    name: str
+    d: int
+    n: tuple
+    levels: int
+    gamma: float
+    mu: list                  # per level (ncells_l, 3^d) viscosity at sample points
+    f: np.ndarray             # finest level (ncells, 3^d, d) body force at sample points
+    u_bc: np.ndarray          # finest level (d, N) nodal Dirichlet values (boundary read only)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def level_n(self):
+        return level_sizes(self.n, self.levels)
+
+
+def manufactured_problem(n=16, levels=2, gamma=1e4):
+    d = 2
+    nn = _as_tuple(n, d)
+    mus = [np.ones((int(np.prod(m)), 9)) for m in level_sizes(nn, levels)]
+    xq = sample_points(d, nn)
+    xn = node_points(d, nn)
+    u_bc = manufactured_u(xn).T.copy()
+    return Problem("manufactured_2d", d, nn, levels, float(gamma), mus,
+                   manufactured_f(xq), u_bc, {"mu": 1.0})
+
+
+def sinker_problem(d, n, levels, count, omega, delta, dr, beta=10.0, gamma=1e4, seed=0):
+    nn = _as_tuple(n, d)
+    c = sinker_centres(seed, count, d)
+    mus = [sinker_viscosity(sample_points(d, m), c, omega, delta, dr)
+           for m in level_sizes(nn, levels)]
+    xq = sample_points(d, nn)
+    f = sinker_force(xq, c, omega, delta, beta)
+    u_bc = np.zeros((d, int(np.prod([2 * v + 1 for v in nn]))))
+    return Problem(f"sinker_{d}d", d, nn, levels, float(gamma), mus, f, u_bc,
+                   {"centres": c, "omega": omega, "delta": delta, "dr": dr,
+                    "beta": beta, "seed": seed})
+
+
+def sinker_2d(n=128, levels=5, gamma=1e4, dr=1e6, seed=0, count=8):
+    """2D multi-sinker, 8 sinkers, omega = 0.1, delta = 200, DR = 1e6."""
+    return sinker_problem(2, n, levels, count, 0.1, 200.0, dr, 10.0, gamma, seed)
+
+
+def sinker_3d(n=32, levels=4, gamma=1e4, dr=1e8, seed=0, count=16):
+    """3D multi-sinker, 16 sinkers, omega = 0.15, delta = 200, DR = 1e8."""
+    return sinker_problem(3, n, levels, count, 0.15, 200.0, dr, 10.0, gamma, seed)
+
+
+def random_vector(seed, size, lo=-1.0, hi=1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=size)
