@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark: AL-multigrid Stokes solves on one GB300 (mixed precision vs FP64).
+
+One step = setup for the step's coefficients (vertex-star patch assembly and
+FP64 factorisation on every level, coarse Cholesky, Schur blocks) followed by
+an FGMRES solve of the augmented Stokes system to a 1e-8 relative residual,
+preconditioned by the block-LDU preconditioner with a robust multigrid
+V-cycle for A_gamma.  Default workload: the 3D multi-sinker problem on 32^3
+hexes ([Q2]^3 x P1disc, 4 levels, 16 sinkers, DR = 1e8).
+
+Printed JSON (one line, rank 0):
+  value       solve DoF/s of the mixed path, inputs resident in HBM
+              (free velocity + pressure DoFs per step / step time, all ranks)
+  e2e         the same through the C ABI with host buffers (coefficients and
+              force copied in, solution copied out inside the timed region)
+  roofline    dominant kernel (finest-level vertex-star patch kernel): bytes
+              per launch / CUDA-event launch time, measured during the timed steps
+  cpu_baseline the FP64 oracle on a bounded sample of the same workload
+Multi-GPU (torchrun): every rank solves its own replica (no communication on
+the data path); the timed region is bracketed by barriers and the max over
+ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # 3D multi-sinker, 32^3 hexes, 4 levels (coarse 4^3), 16 sinkers, omega 0.15, delta 200, DR 1e8
+    "sinker3d_32": dict(d=3, n=32, levels=4, count=16, omega=0.15, delta=200.0, dr=1e8, beta=10.0,
+                        gamma=10.0, seed=0, sweeps=5),
+    # 2D multi-sinker, 128^2 quads, 5 levels (coarse 8^2), 8 sinkers, omega 0.1, delta 200, DR 1e6
+    "sinker2d_128": dict(d=2, n=128, levels=5, count=8, omega=0.1, delta=200.0, dr=1e6, beta=10.0,
+                         gamma=1e4, seed=0, sweeps=5),
+}
+# bounded samples of the same law for the oracle (CPU baseline / reference arm)
+SAMPLES = {
+    "sinker3d_32": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
+    "sinker2d_128": dict(cpu_baseline=dict(n=64, levels=4), reference=dict(n=32, levels=3)),
+}
+RTOL = 1e-8
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def make_problem(spec, n=None, levels=None):
+    from synthetic.problems import sinker_problem
+    return sinker_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["count"], spec["omega"],
+                          spec["delta"], spec["dr"], spec["beta"], spec["gamma"], spec["seed"])
+
+
+def problem_dofs(pb):
+    """Free velocity DoFs + pressure DoFs of the finest level."""
+    free_nodes = math.prod(2 * v - 1 for v in pb.n)
+    return pb.d * free_nodes + (pb.d + 1) * math.prod(pb.n)
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# --------------------------------------------------------------------------
+class Dist:
+    def __init__(self, gpus):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if self._cuda() else "gloo"
+            if backend == "nccl":
+                import torch
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    @staticmethod
+    def _cuda():
+        try:
+            import torch
+            return torch.cuda.is_available()
+        except Exception:
+            return False
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read only)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def stored_traffic(kernel, workload):
+    """Per-launch DRAM traffic from the committed ncu summary, if it was taken on the
+    current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        rec = d.get(kernel, {})
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha") or rec.get("workload") != workload:
+            return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample_step(spec, n, levels):
+    import warnings
+    warnings.simplefilter("ignore")
+    from oracle.mg import Hierarchy
+    from oracle.stokes import StokesSolver
+    pb = make_problem(spec, n, levels)
+    t0 = time.perf_counter()
+    H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"])
+    u, p, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=RTOL)
+    dt = time.perf_counter() - t0
+    return problem_dofs(pb), dt, its
+
+
+def cpu_worker(args):
+    """Runs in a fresh single-threaded interpreter; prints one JSON line."""
+    spec = WORKLOADS[args.workload]
+    smp = SAMPLES[args.workload][args.sample_kind]
+    out = []
+    for _ in range(args.reps):
+        dof, dt, its = oracle_sample_step(spec, smp["n"], smp["levels"])
+        out.append((dof, dt, its))
+    print(json.dumps({"runs": out}))
+
+
+def run_oracle_subprocess(workload, kind, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
+                        "--sample-kind", kind, "--reps", str(reps)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["runs"]
+
+
+def cpu_baseline(workload):
+    smp = SAMPLES[workload]["cpu_baseline"]
+    runs = run_oracle_subprocess(workload, "cpu_baseline", 1)
+    dof, dt, its = runs[0]
+    spec = WORKLOADS[workload]
+    return {"value": dof / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"same law, {spec['d']}D {smp['n']}^{spec['d']} cells, {smp['levels']} levels, "
+                      f"setup+solve to {RTOL:g} ({its} FGMRES its, {dt:.1f} s, {dof} DoFs), FP64 NumPy/SciPy, "
+                      f"1 thread"}
+
+
+def reference_arm(args, dist):
+    """The oracle as it stands, on the host cores: each step one bounded sample."""
+    if dist.rank != 0:
+        return
+    spec = WORKLOADS[args.workload]
+    smp = SAMPLES[args.workload]["reference"]
+    runs = run_oracle_subprocess(args.workload, "reference", args.warmup + args.steps)[args.warmup:]
+    t = sum(r[1] for r in runs)
+    dof = runs[0][0]
+    value = dof * len(runs) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(runs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": f"{spec['d']}D {smp['n']}^{spec['d']}, "
+                       f"{smp['levels']} levels, same law", "rtol": RTOL},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{spec['d']}D {smp['n']}^{spec['d']} cells, {smp['levels']} levels"},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iterations": runs[0][2]}
+    print(json.dumps(line))
+
+
+METRIC = "AL-MG V-cycles/s & solve DoF/s to 1e-8 rel. residual, mixed vs FP64, 1xGB300"
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def ours(args, dist):
+    import numpy as np
+    import torch
+
+    from paper_2107_00820_gb300 import Context, alstokes as A
+
+    torch.cuda.set_device(dist.local)
+    spec = WORKLOADS[args.workload]
+    pb = make_problem(spec)
+    dofs = problem_dofs(pb)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    mu_d = [dev(m) for m in pb.mu]
+    f_d, ubc_d = dev(pb.f), dev(pb.u_bc)
+    nu = pb.d * math.prod(2 * v + 1 for v in pb.n)
+    npres = (pb.d + 1) * math.prod(pb.n)
+    u_d = torch.zeros(nu, dtype=torch.float64, device="cuda")
+    p_d = torch.zeros(npres, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, stream=stream, mode=A.ALS_MODE_MIXED, rtol=RTOL,
+                  maxit=200, sweeps=spec["sweeps"])
+
+    def step():
+        ctx.update_coefficients(mu_d)
+        return ctx.solve(f_d, ubc_d, None, u_d, p_d)[2]
+
+    for _ in range(args.warmup):
+        info = step()
+    ctx.profile(True)
+    step()                                  # capture the profiled V-cycle graph outside the timed region
+    ctx.profile_read()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = A.als_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    its = []
+    for _ in range(args.steps):
+        info = step()
+        its.append(info.iterations)
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = A.als_kernel_launches() - launches0
+    clk = clocks.stop()
+    k4_ms, k4_n = ctx.profile_read()
+    ctx.profile(False)
+    t_step = dist.max(e0.elapsed_time(e1) / args.steps) / 1e3
+    value = dist.world * dofs / t_step
+
+    # V-cycles/s of the mixed (FP32) cycle, replayed back to back
+    b32 = torch.randn(nu, dtype=torch.float32, device="cuda")
+    x32 = torch.zeros_like(b32)
+    for _ in range(3):
+        ctx.vcycle(b32, x32, A.ALS_PREC_FP32)
+    torch.cuda.synchronize()
+    nv = 20
+    e0.record()
+    for _ in range(nv):
+        ctx.vcycle(b32, x32, A.ALS_PREC_FP32)
+    e1.record()
+    torch.cuda.synchronize()
+    vcyc_s = nv / (e0.elapsed_time(e1) / 1e3)
+    b64, x64 = b32.double(), torch.zeros(nu, dtype=torch.float64, device="cuda")
+    ctx.vcycle(b64, x64, A.ALS_PREC_FP64)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        ctx.vcycle(b64, x64, A.ALS_PREC_FP64)
+    e1.record()
+    torch.cuda.synchronize()
+    vcyc64_s = 3 / (e0.elapsed_time(e1) / 1e3)
+
+    # all-FP64 GPU path on the same problem
+    ctx64 = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, stream=stream, mode=A.ALS_MODE_FP64, rtol=RTOL,
+                    maxit=200, sweeps=spec["sweeps"])
+    u64 = torch.zeros_like(u_d)
+    p64 = torch.zeros_like(p_d)
+    ctx64.solve(f_d, ubc_d, None, u64, p64)
+    torch.cuda.synchronize()
+    e0.record()
+    ctx64.update_coefficients(mu_d)
+    info64 = ctx64.solve(f_d, ubc_d, None, u64, p64)[2]
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    err_u = float(torch.linalg.norm(u_d - u64) / torch.linalg.norm(u64))
+    err_p = float(torch.linalg.norm(p_d - p64) / torch.linalg.norm(p64))
+    ctx64.close()
+
+    # end to end through the C ABI with host buffers
+    mu_h = [np.ascontiguousarray(m) for m in pb.mu]
+    f_h = np.ascontiguousarray(pb.f)
+    ubc_h = np.ascontiguousarray(pb.u_bc)
+    u_h = np.zeros(nu)
+    p_h = np.zeros(npres)
+    h2d = sum(m.nbytes for m in mu_h) + f_h.nbytes + ubc_h.nbytes
+    d2h = u_h.nbytes + p_h.nbytes
+    ctx.update_coefficients(mu_h)
+    ctx.solve(f_h, ubc_h, None, u_h, p_h)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(args.steps):
+        ctx.update_coefficients(mu_h)
+        ctx.solve(f_h, ubc_h, None, u_h, p_h)
+    e1.record()
+    torch.cuda.synchronize()
+    t_e2e = dist.max(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / args.steps)
+    ctx.close()
+
+    # roofline of the dominant kernel: finest-level patch kernel
+    F = pb.n
+    nverts = math.prod(v + 1 for v in F)
+    npatch = pb.d * 3 ** pb.d
+    packed = npatch * (npatch + 1) // 2
+    bytes_per_launch = nverts * (packed * 4 + npatch * 4) + nu * 4
+    k4_launch_s = (k4_ms / max(k4_n, 1)) / 1e3
+    achieved = bytes_per_launch / k4_launch_s / 1e9 if k4_n else None
+    peak, peak_kind = measured_peak_hbm()
+    out = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "dim": pb.d, "cells": list(pb.n), "levels": pb.levels,
+                   "gamma": pb.gamma, "dr": spec["dr"], "sinkers": spec["count"], "dofs": dofs,
+                   "smoother": f"GMRES({spec['sweeps']}) x vertex-star PSC", "rtol": RTOL,
+                   "step": "setup (patch factorisation, coarse Cholesky, Schur) + mixed FGMRES solve",
+                   "l2": "inputs larger than L2 (fine-level FP32+FP64 patch inverses 1.4 GB)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "iterations": its[-1] if its else None,
+        "vcycles_per_s": vcyc_s,
+        "fp64": {"solve_dof_per_s": dofs / t64, "ms_per_step": t64 * 1e3, "iterations": info64.iterations,
+                 "vcycles_per_s": vcyc64_s},
+        "mixed_vs_fp64_speedup": t64 / t_step,
+        "mixed_vs_fp64_rel_err": {"u": err_u, "p": err_p},
+        "e2e": {"value": dist.world * dofs / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "kernel": "k_patch_apply<float,float,%d> (finest level)" % pb.d,
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,
+                     "traffic": stored_traffic("k_patch_apply_f32_fine", args.workload)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if dist.rank == 0:
+        if dist.world == 1 and not args.no_cpu_baseline:
+            try:
+                out["cpu_baseline"] = cpu_baseline(args.workload)
+            except Exception as e:  # noqa: BLE001
+                out["cpu_baseline"] = {"error": str(e)[:200]}
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sinker3d_32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--sample-kind", default="cpu_baseline")
+    ap.add_argument("--reps", type=int, default=1)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        # the oracle arm needs no process group: rank 0 runs it, the other ranks exit
+        reference_arm(args, _RankOnly())
+        return
+    dist = Dist(args.gpus)
+    try:
+        ours(args, dist)
+    finally:
+        dist.close()
+
+
+class _RankOnly:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * alstokes.h - C ABI of a GB300 (sm_103a) implementation of the gamma-robust
+ * augmented-Lagrangian multigrid solver for variable-viscosity Stokes flow of
+ * Shih, Stadler & Wechsung, "Robust multigrid techniques for augmented
+ * Lagrangian preconditioning of incompressible Stokes equations with extreme
+ * viscosity variations" (arXiv 2107.00820).
+ *
+ * Discretisation: [Q2]^d x P1^disc (d = 2, 3) on a uniform quad/hex mesh of the
+ * unit box (0,1)^d with n[k] cells per direction, homogeneous structure on
+ * every multigrid level (level 0 = coarsest, level L-1 = finest, n_l = n / 2^(L-1-l)).
+ *
+ * Data layout (all arrays dense, C order, no padding):
+ *   velocity vector : d blocks of N nodal values, N = prod(2 n_k + 1), node
+ *                     index x-fastest; Dirichlet (boundary) entries are kept
+ *                     and carry identity rows.
+ *   pressure vector : [cell][d+1] coefficients of {1, xi_0, .., xi_(d-1)} on the
+ *                     reference cell [-1,1]^d, cell index x-fastest.
+ *   point data      : [cell][3^d] at the 3-point Gauss-Legendre points of each
+ *                     cell (point index x-fastest), optionally [..][m] with
+ *                     m = 3 (2D vector), 6 / 21 (Mandel tensor, upper triangle
+ *                     row-major; components (e00,e11,sqrt2 e01) in 2D and
+ *                     (e00,e11,e22,sqrt2 e12,sqrt2 e02,sqrt2 e01) in 3D).
+ *
+ * Ownership: array arguments of als_create and als_solve may be host or
+ * device pointers (copied with cudaMemcpyDefault); vectors passed to
+ * als_apply_agamma, als_vcycle and the stage entry points are caller-owned
+ * DEVICE pointers of the stated precision, valid for the duration of the
+ * call.  The context owns every internal buffer and frees it in als_destroy.
+ * The context runs its kernels on an internal stream that is ordered after
+ * the work already queued on the stream given to als_create; every call
+ * returns after its own work has finished.  A context is not thread-safe.
+ *
+ * Errors: every call returns an als_status; no exception crosses the ABI.
+ * Device-side failures (a non-positive pivot, a Krylov breakdown) are
+ * recorded on the device and reported by the call that finishes the work;
+ * als_last_error() returns a message.  A failed als_create leaves *out NULL.
+ */
+#ifndef ALSTOKES_H
+#define ALSTOKES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct als_ctx als_ctx;
+
+typedef enum {
+  ALS_OK = 0,
+  ALS_EINVAL = 1,      /* invalid argument (sizes, levels, options, NULL) */
+  ALS_ENOMEM = 2,      /* device allocation failed */
+  ALS_ECUDA = 3,       /* a CUDA runtime call failed */
+  ALS_ENOTSPD = 4,     /* non-positive pivot in a patch or coarse Cholesky factorisation */
+  ALS_ENOTCONV = 5,    /* FGMRES did not reach rtol within maxit iterations */
+  ALS_EBREAKDOWN = 6,  /* Krylov breakdown or a non-finite residual */
+  ALS_ETIMEOUT = 7     /* reserved: a bounded device-side wait gave up */
+} als_status;
+
+enum { ALS_COEFF_SCALAR = 0, ALS_COEFF_TENSOR = 1 };
+enum { ALS_PREC_FP64 = 0, ALS_PREC_FP32 = 1 };
+enum { ALS_MODE_FP64 = 0, ALS_MODE_MIXED = 1 };
+enum { ALS_SMOOTH_GMRES = 0, ALS_SMOOTH_RICHARDSON = 1 };
+enum { ALS_TRANSFER_ROBUST = 0, ALS_TRANSFER_STANDARD = 1 };
+enum { ALS_SCHUR_P1 = 0, ALS_SCHUR_P2 = 1 };
+
+/* Unit box (0,1)^dim with n[k] cells per direction on the finest level;
+ * n[k] must be divisible by 2^(levels-1) and the coarsest level must have
+ * at least 2 cells per direction.  n[2] is ignored for dim = 2. */
+typedef struct {
+  int dim;
+  int n[3];
+  int levels;
+} als_mesh;
+
+/* Viscosity at the Gauss points of every level (rediscretisation on each
+ * level, Sec. 6.1).  SCALAR: qp[l] is [cell][3^d] mu.  TENSOR: qp[l] is
+ * [cell][3^d][6|21] Mandel C (Eq. (stokes-lin)) and mu_eff[l] is the
+ * [cell][3^d] scalar used by the Schur-complement approximation. */
+typedef struct {
+  int kind;
+  const double* const* qp;
+  const double* const* mu_eff;
+} als_coeff;
+
+typedef struct {
+  int smoother;   /* ALS_SMOOTH_GMRES (default): s GMRES steps right-preconditioned
+                     by the vertex-star PSC operator; or damped Richardson */
+  int sweeps;     /* smoothing steps per level, pre and post (default 5) */
+  double tau;     /* Richardson damping (default 2^-d) */
+  int transfer;   /* ALS_TRANSFER_ROBUST (default, Eq. (Ptilde)) or ALS_TRANSFER_STANDARD */
+  int schur;      /* ALS_SCHUR_P1 (default, Eq. (P1P2)) */
+  int mode;       /* ALS_MODE_FP64 or ALS_MODE_MIXED (FP32 V-cycle, FP64 outer loop) */
+  double rtol;    /* FGMRES relative residual reduction (default 1e-8) */
+  int maxit;      /* FGMRES iterations, no restart (default 300) */
+} als_options;
+
+typedef struct {
+  int iterations;     /* FGMRES iterations */
+  int vcycles;        /* V-cycles applied (2 per iteration) */
+  int converged;
+  double res0;        /* ||b||_2 of the augmented, lifted system */
+  double res_final;   /* FGMRES residual estimate at exit */
+  double solve_ms;    /* wall time of the solve on the context stream */
+} als_solve_info;
+
+/* Fills *opt with the defaults listed above. */
+void als_default_options(als_options* opt);
+
+/* Setup (Secs. 5-6): copies the coefficients, assembles and factors the
+ * vertex-star patch matrices of levels 1..L-1 in FP64 (stored as FP64 and
+ * FP32 inverses), factors the coarsest A_gamma (dense FP64 Cholesky) and
+ * forms the per-cell Schur-complement blocks of the finest level.
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
+                      void* stream, als_ctx** out);
+
+als_status als_destroy(als_ctx* ctx);
+
+/* y = A_gamma x on `level` (Eq. (augstokessys), W = M_p), matrix-free.
+ * x, y: device vectors of length d*N_level in precision `prec`
+ * (ALS_PREC_FP64: double, ALS_PREC_FP32: float).  Boundary rows: y_D = x_D. */
+als_status als_apply_agamma(als_ctx* ctx, int level, int prec, const void* x, void* y);
+
+/* x = one V-cycle for A_gamma x = b on the finest level from x = 0
+ * (pre-smoothing, robust restriction, recursion, coarse Cholesky solve,
+ * robust prolongation, post-smoothing).  b, x: device, precision `prec`;
+ * ALS_PREC_FP32 runs the whole cycle in FP32 except the FP64 coarse solve. */
+als_status als_vcycle(als_ctx* ctx, int prec, const void* b, void* x);
+
+/* Stage entry points (one step of the V-cycle each, device vectors):
+ *   als_star_smooth : z = sum_v I_v A_v^-1 I_v^T r on `level` >= 1 (Sec. 5.1)
+ *   als_prolong     : xf = P~ xc from level-1 to `level` (Eq. (Ptilde)),
+ *                     or P_H xc when the context uses ALS_TRANSFER_STANDARD
+ *   als_restrict    : rc = P~^T rf from `level` to level-1
+ *   als_coarse_solve: x = A_0^-1 b on the free dofs of level 0 */
+als_status als_star_smooth(als_ctx* ctx, int level, int prec, const void* r, void* z);
+als_status als_prolong(als_ctx* ctx, int level, int prec, const void* xc, void* xf);
+als_status als_restrict(als_ctx* ctx, int level, int prec, const void* rf, void* rc);
+als_status als_coarse_solve(als_ctx* ctx, int prec, const void* b, void* x);
+
+/* FP64 system operator of Eq. (augstokessys) on the finest level:
+ * [yu; yp] = [[A_gamma, B^T], [B, 0]] [u; p] (device vectors). */
+als_status als_apply_stokes(als_ctx* ctx, const double* u, const double* p, double* yu, double* yp);
+
+/* Copies the FP64 inverse of the patch matrix of vertex `vertex` on `level`
+ * as a full (d*3^d) x (d*3^d) row-major matrix to `out` (host or device).
+ * Patch dof order: component-major, node offsets (-1,0,1)^d x-fastest;
+ * rows of nodes outside the domain or on the boundary are identity rows. */
+als_status als_patch_inverse(als_ctx* ctx, int level, long long vertex, double* out);
+
+/* Solve the augmented Stokes system (Eqs. (stokessys), (augstokessys)) on the
+ * finest level with FGMRES preconditioned by the block-LDU preconditioner of
+ * Eq. (precond): V-cycle for A_gamma, P1 Schur approximation.
+ *   f_qp : [cell][3^d][d] body force at the Gauss points (required)
+ *   u_bc : [d][N] nodal Dirichlet values, only boundary entries are read (NULL = 0)
+ *   r2   : [cell][d+1] divergence right-hand side (NULL = 0)
+ *   u    : [d][N] output velocity including the boundary values
+ *   p    : [cell][d+1] output pressure, zero mean
+ * Returns ALS_ENOTCONV if rtol was not reached (u, p hold the last iterate). */
+als_status als_solve(als_ctx* ctx, const double* f_qp, const double* u_bc, const double* r2, double* u,
+                     double* p, als_solve_info* info);
+
+/* Re-runs the setup of als_create (patch factorisations, coarse Cholesky,
+ * Schur blocks) for new coefficients of the same kind and sizes, reusing every
+ * allocation and the captured V-cycle graphs: the per-linearisation setup of
+ * a nonlinear (Newton) iteration, Sec. 6.3.  Host or device pointers. */
+als_status als_update_coefficients(als_ctx* ctx, const als_coeff* coeff);
+
+/* Live timing of the finest-level vertex-star patch kernel inside V-cycles:
+ * als_profile(ctx, 1) makes every subsequent V-cycle record a CUDA event
+ * pair around each such launch on the stream it runs on (the V-cycle graph is
+ * recaptured with event-record nodes); als_profile_read() returns the summed
+ * kernel time in ms and the number of launches measured since the previous
+ * read, and restarts the accumulation.  als_profile(ctx, 0) turns it off. */
+als_status als_profile(als_ctx* ctx, int on);
+als_status als_profile_read(als_ctx* ctx, double* total_ms, long long* launches);
+
+/* Process-wide number of kernels this library has launched (a replay of a
+ * captured V-cycle counts its kernel nodes). */
+long long als_kernel_launches(void);
+
+/* Last error message of the context (never NULL; "" when none). */
+const char* als_last_error(const als_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALSTOKES_H */

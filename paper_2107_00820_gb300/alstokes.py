@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libalstokes.so (include/alstokes.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  Device vectors are passed as torch CUDA tensors (their data
+pointers); setup/solve arrays may be NumPy arrays or torch tensors.  There is
+no CPU fallback: importing works anywhere, but every call needs the built
+library and a CUDA device, and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+ALS_OK, ALS_EINVAL, ALS_ENOMEM, ALS_ECUDA, ALS_ENOTSPD, ALS_ENOTCONV, ALS_EBREAKDOWN, ALS_ETIMEOUT = range(8)
+STATUS_NAMES = ["ALS_OK", "ALS_EINVAL", "ALS_ENOMEM", "ALS_ECUDA", "ALS_ENOTSPD", "ALS_ENOTCONV",
+                "ALS_EBREAKDOWN", "ALS_ETIMEOUT"]
+ALS_COEFF_SCALAR, ALS_COEFF_TENSOR = 0, 1
+ALS_PREC_FP64, ALS_PREC_FP32 = 0, 1
+ALS_MODE_FP64, ALS_MODE_MIXED = 0, 1
+ALS_SMOOTH_GMRES, ALS_SMOOTH_RICHARDSON = 0, 1
+ALS_TRANSFER_ROBUST, ALS_TRANSFER_STANDARD = 0, 1
+ALS_SCHUR_P1, ALS_SCHUR_P2 = 0, 1
+
+
+class als_mesh(Structure):
+    _fields_ = [("dim", c_int), ("n", c_int * 3), ("levels", c_int)]
+
+
+class als_coeff(Structure):
+    _fields_ = [("kind", c_int), ("qp", POINTER(c_void_p)), ("mu_eff", POINTER(c_void_p))]
+
+
+class als_options(Structure):
+    _fields_ = [("smoother", c_int), ("sweeps", c_int), ("tau", c_double), ("transfer", c_int),
+                ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int)]
+
+
+class als_solve_info(Structure):
+    _fields_ = [("iterations", c_int), ("vcycles", c_int), ("converged", c_int), ("res0", c_double),
+                ("res_final", c_double), ("solve_ms", c_double)]
+
+
+# name -> (restype, argtypes); the exported C ABI
+SIGNATURES = {
+    "als_default_options": (None, [POINTER(als_options)]),
+    "als_create": (c_int, [POINTER(als_mesh), POINTER(als_coeff), c_double, POINTER(als_options), c_void_p,
+                           POINTER(c_void_p)]),
+    "als_destroy": (c_int, [c_void_p]),
+    "als_apply_agamma": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "als_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "als_star_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "als_prolong": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "als_restrict": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "als_coarse_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "als_apply_stokes": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "als_patch_inverse": (c_int, [c_void_p, c_int, c_longlong, c_void_p]),
+    "als_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(als_solve_info)]),
+    "als_last_error": (ctypes.c_char_p, [c_void_p]),
+    "als_update_coefficients": (c_int, [c_void_p, POINTER(als_coeff)]),
+    "als_profile": (c_int, [c_void_p, c_int]),
+    "als_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
+    "als_kernel_launches": (c_longlong, []),
+}
+
+_LIB = None
+
+
+class ALSError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libalstokes.so (building it first if asked).  Raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA extension {path} is not built; run paper_2107_00820_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or a NumPy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_dtype(a, prec):
+    if a is None:
+        return
+    name = str(a.dtype)
+    want = "float64" if prec == ALS_PREC_FP64 else "float32"
+    if not name.endswith(want):
+        raise TypeError(f"expected {want} data for prec={prec}, got {name}")
+
+
+def _cuda_tensor(a):
+    if not (hasattr(a, "is_cuda") and a.is_cuda):
+        raise TypeError("this entry point takes CUDA tensors (device pointers)")
+
+
+def default_options(**kw):
+    lib = load()
+    o = als_options()
+    lib.als_default_options(byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """An als_ctx: setup once (als_create), then apply / V-cycle / solve."""
+
+    def __init__(self, dim, n, levels, coeffs, gamma, mu_eff=None, stream=None, **options):
+        lib = load()
+        n = (n,) * dim if np.isscalar(n) else tuple(n)
+        self.dim, self.n, self.levels, self.gamma = dim, n, levels, float(gamma)
+        mesh = als_mesh(dim, (c_int * 3)(*(list(n) + [1] * (3 - len(n)))), levels)
+        kind = ALS_COEFF_TENSOR if mu_eff is not None else ALS_COEFF_SCALAR
+        self._keep = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c for c in coeffs]
+        qp = (c_void_p * levels)(*[_ptr(c) for c in self._keep])
+        mu = None
+        if mu_eff is not None:
+            self._keep_mu = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c
+                             for c in mu_eff]
+            mu = (c_void_p * levels)(*[_ptr(c) for c in self._keep_mu])
+        coeff = als_coeff(kind, qp, mu)
+        self._kind = kind
+        self.options = default_options(**options)
+        out = c_void_p()
+        st = lib.als_create(byref(mesh), byref(coeff), self.gamma, byref(self.options),
+                            c_void_p(stream) if stream else None, byref(out))
+        if st != ALS_OK:
+            raise ALSError(st, "als_create failed (see stderr)")
+        self._ctx = out
+        self._lib = lib
+
+    # sizes -----------------------------------------------------------------
+    def level_n(self, level):
+        f = 2 ** (self.levels - 1 - level)
+        return tuple(v // f for v in self.n)
+
+    def nu(self, level=None):
+        nl = self.level_n(self.levels - 1 if level is None else level)
+        return self.dim * int(np.prod([2 * v + 1 for v in nl]))
+
+    def npres(self):
+        return (self.dim + 1) * int(np.prod(self.n))
+
+    # calls -----------------------------------------------------------------
+    def _call(self, name, *args):
+        st = getattr(self._lib, name)(self._ctx, *args)
+        if st != ALS_OK:
+            raise ALSError(st, self._lib.als_last_error(self._ctx).decode())
+        return st
+
+    def apply_agamma(self, x, y, level=None, prec=ALS_PREC_FP64):
+        level = self.levels - 1 if level is None else level
+        _cuda_tensor(x); _cuda_tensor(y); _check_dtype(x, prec); _check_dtype(y, prec)
+        self._call("als_apply_agamma", level, prec, _ptr(x), _ptr(y))
+
+    def vcycle(self, b, x, prec=ALS_PREC_FP64):
+        _cuda_tensor(b); _cuda_tensor(x); _check_dtype(b, prec); _check_dtype(x, prec)
+        self._call("als_vcycle", prec, _ptr(b), _ptr(x))
+
+    def star_smooth(self, level, r, z, prec=ALS_PREC_FP64):
+        _cuda_tensor(r); _cuda_tensor(z); _check_dtype(r, prec)
+        self._call("als_star_smooth", level, prec, _ptr(r), _ptr(z))
+
+    def prolong(self, level, xc, xf, prec=ALS_PREC_FP64):
+        _cuda_tensor(xc); _cuda_tensor(xf); _check_dtype(xc, prec)
+        self._call("als_prolong", level, prec, _ptr(xc), _ptr(xf))
+
+    def restrict(self, level, rf, rc, prec=ALS_PREC_FP64):
+        _cuda_tensor(rf); _cuda_tensor(rc); _check_dtype(rf, prec)
+        self._call("als_restrict", level, prec, _ptr(rf), _ptr(rc))
+
+    def coarse_solve(self, b, x, prec=ALS_PREC_FP64):
+        _cuda_tensor(b); _cuda_tensor(x); _check_dtype(b, prec)
+        self._call("als_coarse_solve", prec, _ptr(b), _ptr(x))
+
+    def apply_stokes(self, u, p, yu, yp):
+        for a in (u, p, yu, yp):
+            _cuda_tensor(a); _check_dtype(a, ALS_PREC_FP64)
+        self._call("als_apply_stokes", _ptr(u), _ptr(p), _ptr(yu), _ptr(yp))
+
+    def patch_inverse(self, level, vertex):
+        np_ = self.dim * 3 ** self.dim
+        out = np.zeros((np_, np_))
+        self._call("als_patch_inverse", level, int(vertex), _ptr(out))
+        return out
+
+    def solve(self, f_qp, u_bc=None, r2=None, u=None, p=None, check=True):
+        """Returns (u, p, info); inputs/outputs may be host (NumPy) or device (torch)."""
+        if u is None:
+            u = np.zeros(self.nu())
+        if p is None:
+            p = np.zeros(self.npres())
+        info = als_solve_info()
+        st = self._lib.als_solve(self._ctx, _ptr(f_qp), _ptr(u_bc), _ptr(r2), _ptr(u), _ptr(p), byref(info))
+        if st != ALS_OK and (check or st != ALS_ENOTCONV):
+            raise ALSError(st, self._lib.als_last_error(self._ctx).decode())
+        return u, p, info
+
+    def update_coefficients(self, coeffs, mu_eff=None):
+        """Re-run the setup for new per-level coefficients (host or device arrays)."""
+        keep = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c for c in coeffs]
+        qp = (c_void_p * self.levels)(*[_ptr(c) for c in keep])
+        mu = None
+        if mu_eff is not None:
+            keep_mu = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c for c in mu_eff]
+            mu = (c_void_p * self.levels)(*[_ptr(c) for c in keep_mu])
+        coeff = als_coeff(self._kind, qp, mu)
+        self._call("als_update_coefficients", byref(coeff))
+
+    def profile(self, on=True):
+        self._call("als_profile", 1 if on else 0)
+
+    def profile_read(self):
+        ms, n = c_double(), c_longlong()
+        self._call("als_profile_read", byref(ms), byref(n))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None:
+            self._lib.als_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# module-level functions with the C names (thin pass-through)
+def als_create(dim, n, levels, coeffs, gamma, **kw):
+    return Context(dim, n, levels, coeffs, gamma, **kw)
+
+
+def als_destroy(ctx):
+    ctx.close()
+
+
+def als_apply_agamma(ctx, level, prec, x, y):
+    ctx.apply_agamma(x, y, level, prec)
+
+
+def als_vcycle(ctx, prec, b, x):
+    ctx.vcycle(b, x, prec)
+
+
+def als_solve(ctx, f_qp, u_bc, r2, u, p):
+    return ctx.solve(f_qp, u_bc, r2, u, p)
+
+
+def als_kernel_launches():
+    return int(load().als_kernel_launches())

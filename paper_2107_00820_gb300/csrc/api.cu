@@ -1,0 +1,872 @@
+// C ABI of the AL-multigrid Stokes library: context, multigrid hierarchy,
+// V-cycle (captured once per precision as a CUDA graph), block-LDU
+// preconditioner and FGMRES.  Every arithmetic step runs in the kernels of
+// operator.cu, patches.cu, transfer.cu, coarse.cu and krylov.cu; the host only
+// sequences launches and reads one residual scalar per FGMRES iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/alstokes.h"
+#include "cell.cuh"
+#include "krylov.h"
+#include "level.h"
+
+using namespace als;
+
+namespace {
+
+struct MGWork {
+  int prec = 0;
+  size_t es = 8;
+  std::vector<void*> b, x, t, t2, t3, scratch, V, Z;
+  std::vector<double*> small;  // per level: H, cs, sn, g, y, res, beta, nrm2
+  double* partial = nullptr;
+  cudaGraph_t graph_tmpl = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+};
+
+// Live timing of the finest-level patch kernel (K4) inside the V-cycle: the
+// captured graph holds event-record nodes around each such launch; before every
+// replay they are re-pointed at fresh events from a pool, so every launch of
+// the timed region is measured with CUDA events on the stream it runs on.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> slots;           // events recorded at capture time (2 per launch)
+  std::vector<cudaGraphNode_t> nodes32, nodes64;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  std::vector<std::pair<size_t, size_t>> pairs;
+  cudaEvent_t spare0 = nullptr, spare1 = nullptr;
+};
+
+// offsets into the per-level small workspace of the GMRES smoother
+struct SmallLayout {
+  int s, ldh;
+  size_t H, cs, sn, g, y, res, beta, nrm2, total;
+  explicit SmallLayout(int steps) : s(steps), ldh(steps + 1) {
+    H = 0;
+    cs = H + (size_t)ldh * s;
+    sn = cs + s;
+    g = sn + s;
+    y = g + s + 1;
+    res = y + s;
+    beta = res + 1;
+    nrm2 = beta + 1;
+    total = nrm2 + 1;
+  }
+};
+
+}  // namespace
+
+struct als_ctx {
+  cudaStream_t stream = nullptr;       // internal, non-blocking
+  cudaStream_t user_stream = nullptr;  // caller's stream: work is ordered after it
+  cudaEvent_t order_ev = nullptr;
+  int dim = 0, L = 0;
+  double gamma = 0.0;
+  als_options opt{};
+  std::vector<LevelDev> lev;
+  CoarseDev coarse{0, nullptr};
+  DevStatus* st = nullptr;
+  double* schur = nullptr;
+  MGWork w64, w32;
+  // outer solve buffers (FP64), allocated on first solve
+  int maxit_alloc = 0;
+  long long nu = 0, np = 0, n = 0;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *res = nullptr, *beta = nullptr, *h2 = nullptr, *nrm2 = nullptr, *partial = nullptr;
+  double *f_dev = nullptr, *ubc_dev = nullptr, *r2_dev = nullptr, *uD = nullptr, *tu = nullptr, *tu2 = nullptr;
+  double *tp = nullptr, *tp2 = nullptr, *xsol = nullptr;
+  double* host_res = nullptr;  // pinned
+  std::vector<void*> allocs;
+  std::string err;
+  bool use_graph = true;
+  Prof prof;
+  const double* const* src_qp = nullptr;   // only valid during a setup call
+};
+
+namespace {
+
+als_status fail(als_ctx* c, als_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+als_status cuda_check(als_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, ALS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return ALS_OK;
+}
+
+template <typename T>
+als_status dalloc(als_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&v, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, ALS_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  c->allocs.push_back(v);
+  *p = (T*)v;
+  return ALS_OK;
+}
+
+#define ALS_TRY(expr)                 \
+  do {                                \
+    als_status _s = (expr);           \
+    if (_s != ALS_OK) return _s;      \
+  } while (0)
+
+Geom make_geom(int dim, const int n[3]) {
+  Geom g{};
+  g.dim = dim;
+  for (int k = 0; k < 3; ++k) {
+    const bool act = k < dim;
+    g.n[k] = act ? n[k] : 1;
+    g.nn[k] = act ? 2 * n[k] + 1 : 1;
+    g.nv[k] = act ? n[k] + 1 : 1;
+    g.h[k] = act ? 1.0 / n[k] : 0.0;
+  }
+  g.N = (long long)g.nn[0] * g.nn[1] * g.nn[2];
+  g.ncells = (long long)g.n[0] * g.n[1] * g.n[2];
+  g.nverts = (long long)g.nv[0] * g.nv[1] * g.nv[2];
+  return g;
+}
+
+als_status check_status(als_ctx* c, const char* stage) {
+  DevStatus h{};
+  if (cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_check(c, stage);
+  if (h.code != 0) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: device reported status %d at index %lld", stage, h.code, h.where);
+    cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+    return fail(c, (als_status)h.code, buf);
+  }
+  return ALS_OK;
+}
+
+als_status alloc_work(als_ctx* c, MGWork& w, int prec) {
+  w.prec = prec;
+  w.es = prec == PREC_F64 ? 8 : 4;
+  const int s = std::max(1, c->opt.sweeps);
+  SmallLayout sl(s);
+  const int L = c->L;
+  w.b.assign(L, nullptr); w.x.assign(L, nullptr); w.t.assign(L, nullptr); w.t2.assign(L, nullptr);
+  w.t3.assign(L, nullptr); w.scratch.assign(L, nullptr); w.V.assign(L, nullptr); w.Z.assign(L, nullptr);
+  w.small.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const size_t len = (size_t)(c->lev[l].g.N * c->dim);
+    char* p = nullptr;
+    ALS_TRY(dalloc(c, &p, len * w.es * 5));
+    w.b[l] = p; w.x[l] = p + len * w.es; w.t[l] = p + 2 * len * w.es;
+    w.t2[l] = p + 3 * len * w.es; w.t3[l] = p + 4 * len * w.es;
+    if (l > 0) {
+      char* q = nullptr;
+      ALS_TRY(dalloc(c, &q, patch_scratch_bytes(c->lev[l], prec)));
+      w.scratch[l] = q;
+      ALS_TRY(dalloc(c, &q, len * w.es * (2 * s + 1)));
+      w.V[l] = q;
+      w.Z[l] = q + len * w.es * (s + 1);
+      ALS_TRY(dalloc(c, &w.small[l], sl.total));
+    }
+  }
+  ALS_TRY(dalloc(c, &w.partial, multidot_partial_doubles(std::max(s + 1, 8))));
+  return ALS_OK;
+}
+
+void free_graphs(als_ctx* c) {
+  for (MGWork* w : {&c->w64, &c->w32}) {
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->graph_tmpl) cudaGraphDestroy(w->graph_tmpl);
+    w->graph = nullptr;
+    w->graph_tmpl = nullptr;
+  }
+  c->prof.nodes32.clear();
+  c->prof.nodes64.clear();
+}
+
+static thread_local bool t_capturing = false;
+cudaEvent_t prof_take(als_ctx* c);
+
+// events for the k-th finest-level patch launch of the V-cycle being issued:
+// placeholders while a graph is captured, pool events otherwise
+void prof_events(als_ctx* c, int& counter, cudaEvent_t& e0, cudaEvent_t& e1) {
+  e0 = e1 = nullptr;
+  if (!c->prof.on) return;
+  if (!t_capturing) {
+    e0 = prof_take(c);
+    e1 = prof_take(c);
+    if (e0 && e1) c->prof.pairs.push_back({c->prof.next - 2, c->prof.next - 1});
+    else e0 = e1 = nullptr;
+    return;
+  }
+  const size_t need = 2 * (size_t)(counter + 1);
+  while (c->prof.slots.size() < need) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->prof.slots.push_back(e);
+  }
+  e0 = c->prof.slots[2 * counter];
+  e1 = c->prof.slots[2 * counter + 1];
+  ++counter;
+}
+
+// --------------------------------------------------------------------------
+// smoothing, transfers, V-cycle (all stream-ordered, no host synchronisation)
+// --------------------------------------------------------------------------
+inline char* vptr(void* base, size_t es, long long off) { return (char*)base + es * off; }
+
+static thread_local int t_prof_counter = 0;
+
+void smooth(als_ctx* c, MGWork& w, int l) {
+  const LevelDev& Lv = c->lev[l];
+  const int prec = w.prec;
+  const long long len = Lv.g.N * c->dim;
+  const cudaStream_t s = c->stream;
+  const int steps = std::max(1, c->opt.sweeps);
+  if (c->opt.smoother == ALS_SMOOTH_RICHARDSON) {
+    for (int it = 0; it < steps; ++it) {
+      op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
+      vec_axpby(prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                 // t = b - A x
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
+      patch_smooth(Lv, prec, w.t[l], w.t2[l], w.scratch[l], s, e0, e1);  // t2 = D^-1 t
+      vec_axpby(prec, len, c->opt.tau, w.t2[l], 1.0, w.x[l], s);         // x += tau t2
+    }
+    return;
+  }
+  // s steps of GMRES right-preconditioned by D^-1 (classical Gram-Schmidt)
+  SmallLayout sl(steps);
+  double* sm = w.small[l];
+  void* V0 = w.V[l];
+  op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, w.x[l], V0, nullptr, nullptr, s);
+  vec_axpby(prec, len, 1.0, w.b[l], -1.0, V0, s);                        // V0 = b - A x
+  vec_multidot(prec, len, 1, V0, len, V0, sm + sl.nrm2, w.partial, s);
+  dev_init_g(steps + 1, sm + sl.nrm2, sm + sl.g, sm + sl.beta, s);
+  vec_scale_dev(prec, len, nullptr, sm + sl.beta, V0, V0, s);
+  for (int j = 0; j < steps; ++j) {
+    void* Vj = vptr(w.V[l], w.es, (long long)j * len);
+    void* Vn = vptr(w.V[l], w.es, (long long)(j + 1) * len);
+    void* Zj = vptr(w.Z[l], w.es, (long long)j * len);
+    double* hcol = sm + sl.H + (size_t)j * sl.ldh;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
+    patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1);
+    op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, Zj, Vn, nullptr, nullptr, s);
+    vec_multidot(prec, len, j + 1, w.V[l], len, Vn, hcol, w.partial, s);
+    vec_multiaxpy(prec, len, j + 1, w.V[l], len, hcol, Vn, s, -1.0);
+    vec_multidot(prec, len, 1, Vn, len, Vn, sm + sl.nrm2, w.partial, s);
+    dev_hess_finish(j, hcol, nullptr, sm + sl.nrm2, s);
+    vec_scale_dev(prec, len, nullptr, hcol + j + 1, Vn, Vn, s);
+    dev_givens_step(j, sm + sl.H, sl.ldh, sm + sl.cs, sm + sl.sn, sm + sl.g, sm + sl.res, s);
+  }
+  dev_backsolve(steps, sm + sl.H, sl.ldh, sm + sl.g, sm + sl.y, s);
+  vec_multiaxpy(prec, len, steps, w.Z[l], len, sm + sl.y, w.x[l], s, 1.0);
+}
+
+// rc = P~^T rf : restrict the fine residual in w.t[l] into w.b[l-1]
+void restrict_level(als_ctx* c, MGWork& w, int l, const void* rf, void* rc) {
+  const LevelDev& F = c->lev[l];
+  const LevelDev& C = c->lev[l - 1];
+  const long long len = F.g.N * c->dim;
+  const cudaStream_t s = c->stream;
+  if (c->opt.transfer == ALS_TRANSFER_ROBUST) {
+    // t2 = sum_K E_K A_K^-1 E_K^T rf ; t3 = G t2 ; t2 = rf - t3
+    patch_interior_solve(F, w.prec, rf, w.t2[l], 0, s);
+    op_apply(F, w.prec, OP_AL, c->gamma, w.t2[l], w.t3[l], nullptr, nullptr, s);
+    vec_axpby(w.prec, len, 1.0, rf, 0.0, w.t2[l], s);
+    vec_axpby(w.prec, len, -1.0, w.t3[l], 1.0, w.t2[l], s);
+    restrict_std(C, F, w.prec, w.t2[l], rc, s);
+  } else {
+    restrict_std(C, F, w.prec, rf, rc, s);
+  }
+}
+
+// xf = P~ xc  (xf overwritten)
+void prolong_level(als_ctx* c, MGWork& w, int l, const void* xc, void* xf) {
+  const LevelDev& F = c->lev[l];
+  const LevelDev& C = c->lev[l - 1];
+  const cudaStream_t s = c->stream;
+  prolong_std(C, F, w.prec, xc, xf, s);
+  if (c->opt.transfer == ALS_TRANSFER_ROBUST) {
+    op_apply(F, w.prec, OP_AL, c->gamma, xf, w.t3[l], nullptr, nullptr, s);   // t3 = G P_H xc
+    patch_interior_solve(F, w.prec, w.t3[l], xf, 1, s);                       // xf -= sum_K E A^-1 E^T t3
+  }
+}
+
+void vcycle_level(als_ctx* c, MGWork& w, int l) {
+  const cudaStream_t s = c->stream;
+  if (l == 0) {
+    coarse_apply(c->lev[0], c->coarse, w.prec, w.b[0], w.x[0], s);
+    return;
+  }
+  const LevelDev& Lv = c->lev[l];
+  const long long len = Lv.g.N * c->dim;
+  vec_zero(w.prec, len, w.x[l], s);
+  smooth(c, w, l);
+  op_apply(Lv, w.prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
+  vec_axpby(w.prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                  // t = b - A x
+  restrict_level(c, w, l, w.t[l], w.b[l - 1]);
+  vcycle_level(c, w, l - 1);
+  prolong_level(c, w, l, w.x[l - 1], w.t[l]);
+  vec_axpby(w.prec, len, 1.0, w.t[l], 1.0, w.x[l], s);                   // x += P~ e_c
+  smooth(c, w, l);
+}
+
+cudaEvent_t prof_take(als_ctx* c) {
+  Prof& p = c->prof;
+  if (p.next < p.pool.size()) return p.pool[p.next++];
+  return nullptr;
+}
+
+// one V-cycle on the finest level: w.b[L-1] -> w.x[L-1]
+als_status run_vcycle(als_ctx* c, MGWork& w) {
+  Prof& pf = c->prof;
+  if (!c->use_graph) {
+    vcycle_level(c, w, c->L - 1);
+    return cuda_check(c, "vcycle");
+  }
+  std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
+  if (!w.graph) {
+    t_prof_counter = 0;
+    const long long c0 = launch_count();
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cuda_check(c, "begin capture");
+    t_capturing = true;
+    vcycle_level(c, w, c->L - 1);
+    t_capturing = false;
+    if (cudaStreamEndCapture(c->stream, &w.graph_tmpl) != cudaSuccess) return cuda_check(c, "end capture");
+    w.graph_kernels = launch_count() - c0;
+    count_launch(-w.graph_kernels);
+    nodes.clear();
+    if (pf.on) {
+      // map every event-record node to its slot (capture order is the slot order)
+      const int nslots = 2 * t_prof_counter;
+      nodes.assign(nslots, nullptr);
+      size_t nn = 0;
+      cudaGraphGetNodes(w.graph_tmpl, nullptr, &nn);
+      std::vector<cudaGraphNode_t> all(nn);
+      cudaGraphGetNodes(w.graph_tmpl, all.data(), &nn);
+      for (cudaGraphNode_t nd : all) {
+        cudaGraphNodeType ty;
+        cudaGraphNodeGetType(nd, &ty);
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        cudaGraphEventRecordNodeGetEvent(nd, &ev);
+        for (int i = 0; i < nslots; ++i)
+          if (pf.slots[i] == ev) nodes[i] = nd;
+      }
+    }
+    cudaError_t e = cudaGraphInstantiate(&w.graph, w.graph_tmpl, 0);
+    if (e != cudaSuccess) return cuda_check(c, "graph instantiate");
+  }
+  if (pf.on && !nodes.empty()) {
+    for (size_t i = 0; i + 1 < nodes.size(); i += 2) {
+      cudaEvent_t a = prof_take(c), b = prof_take(c);
+      if (!a || !b) { a = pf.spare0; b = pf.spare1; }
+      else pf.pairs.push_back({pf.next - 2, pf.next - 1});
+      if (nodes[i]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i], a);
+      if (nodes[i + 1]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i + 1], b);
+    }
+  }
+  if (cudaGraphLaunch(w.graph, c->stream) != cudaSuccess) return cuda_check(c, "graph launch");
+  count_launch(w.graph_kernels);
+  return ALS_OK;
+}
+
+MGWork& work_for(als_ctx* c, int prec) { return prec == PREC_F64 ? c->w64 : c->w32; }
+
+// --------------------------------------------------------------------------
+// outer solve
+// --------------------------------------------------------------------------
+als_status alloc_solve(als_ctx* c, int maxit) {
+  if (c->maxit_alloc >= maxit) return ALS_OK;
+  if (c->maxit_alloc > 0) return fail(c, ALS_EINVAL, "maxit larger than the first solve's is not supported");
+  const LevelDev& F = c->lev[c->L - 1];
+  c->nu = F.g.N * c->dim;
+  c->np = F.g.ncells * (c->dim + 1);
+  c->n = c->nu + c->np;
+  const int ldh = maxit + 1;
+  ALS_TRY(dalloc(c, &c->V, (size_t)(maxit + 1) * c->n));
+  ALS_TRY(dalloc(c, &c->Z, (size_t)maxit * c->n));
+  ALS_TRY(dalloc(c, &c->H, (size_t)ldh * maxit));
+  ALS_TRY(dalloc(c, &c->cs, maxit));
+  ALS_TRY(dalloc(c, &c->sn, maxit));
+  ALS_TRY(dalloc(c, &c->g, maxit + 1));
+  ALS_TRY(dalloc(c, &c->y, maxit));
+  ALS_TRY(dalloc(c, &c->res, 1));
+  ALS_TRY(dalloc(c, &c->beta, 1));
+  ALS_TRY(dalloc(c, &c->h2, maxit + 1));
+  ALS_TRY(dalloc(c, &c->nrm2, 1));
+  ALS_TRY(dalloc(c, &c->partial, multidot_partial_doubles(maxit + 1)));
+  ALS_TRY(dalloc(c, &c->f_dev, (size_t)F.g.ncells * (c->dim == 2 ? 9 : 27) * c->dim));
+  ALS_TRY(dalloc(c, &c->ubc_dev, c->nu));
+  ALS_TRY(dalloc(c, &c->r2_dev, c->np));
+  ALS_TRY(dalloc(c, &c->uD, c->nu));
+  ALS_TRY(dalloc(c, &c->tu, c->nu));
+  ALS_TRY(dalloc(c, &c->tu2, c->nu));
+  ALS_TRY(dalloc(c, &c->tp, c->np));
+  ALS_TRY(dalloc(c, &c->tp2, c->np));
+  ALS_TRY(dalloc(c, &c->xsol, c->n));
+  if (!c->host_res && cudaMallocHost(&c->host_res, 2 * sizeof(double)) != cudaSuccess)
+    return fail(c, ALS_ENOMEM, "pinned host allocation failed");
+  c->maxit_alloc = maxit;
+  return ALS_OK;
+}
+
+// z1 = A^-1 f through one V-cycle in the context's precision mode (FP64 in/out)
+als_status apply_Ahat(als_ctx* c, const double* f, double* z1) {
+  const int prec = c->opt.mode == ALS_MODE_MIXED ? PREC_F32 : PREC_F64;
+  MGWork& w = work_for(c, prec);
+  const int l = c->L - 1;
+  vec_cast(c->nu, f, PREC_F64, w.b[l], prec, c->stream);
+  ALS_TRY(run_vcycle(c, w));
+  vec_cast(c->nu, w.x[l], prec, z1, PREC_F64, c->stream);
+  return ALS_OK;
+}
+
+// Eq. (precond): z = P v, v = (f, g), z = (x1, z2)
+als_status precondition(als_ctx* c, const double* v, double* z) {
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  const double* f = v;
+  const double* gp = v + c->nu;
+  double* x1 = z;
+  double* z2 = z + c->nu;
+  ALS_TRY(apply_Ahat(c, f, c->tu));                                                  // z1 = A^-1 f
+  op_apply(F, PREC_F64, OP_B, c->gamma, c->tu, nullptr, nullptr, c->tp, s);          // tp = B z1
+  vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                               // tp = g - B z1
+  schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                       // z2 = -S^-1 tp
+  op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, z2, nullptr, s);           // tu2 = B^T z2
+  ALS_TRY(apply_Ahat(c, c->tu2, x1));                                                // x1 = A^-1 B^T z2
+  vec_axpby(PREC_F64, c->nu, 1.0, c->tu, -1.0, x1, s);                               // x1 = z1 - x1
+  project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+  return ALS_OK;
+}
+
+void matvec(als_ctx* c, const double* x, double* y) {
+  const LevelDev& F = c->lev[c->L - 1];
+  op_apply(F, PREC_F64, OP_VISC | OP_AL | OP_BT | OP_B, c->gamma, x, y, x + c->nu, y + c->nu, c->stream);
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void als_default_options(als_options* opt) {
+  if (!opt) return;
+  opt->smoother = ALS_SMOOTH_GMRES;
+  opt->sweeps = 5;
+  opt->tau = 0.0;
+  opt->transfer = ALS_TRANSFER_ROBUST;
+  opt->schur = ALS_SCHUR_P1;
+  opt->mode = ALS_MODE_FP64;
+  opt->rtol = 1e-8;
+  opt->maxit = 300;
+}
+
+const char* als_last_error(const als_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+als_status als_destroy(als_ctx* ctx) {
+  if (!ctx) return ALS_EINVAL;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_graphs(ctx);
+  coarse_free(&ctx->coarse);
+  for (cudaEvent_t e : ctx->prof.slots) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  if (ctx->prof.spare0) cudaEventDestroy(ctx->prof.spare0);
+  if (ctx->prof.spare1) cudaEventDestroy(ctx->prof.spare1);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->host_res) cudaFreeHost(ctx->host_res);
+  if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return ALS_OK;
+}
+
+// Setup (Secs. 5-6) with the coefficients of every level: copies them, builds
+// the vertex-star patch inverses, the coarse factorisation and the Schur blocks.
+static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
+  const int NB = c->dim == 2 ? 9 : 27;
+  for (int l = 0; l < c->L; ++l) {
+    LevelDev& Lv = c->lev[l];
+    const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
+    if (!coeff->qp[l]) return fail(c, ALS_EINVAL, "missing coefficients for a level");
+    if (cudaMemcpyAsync(Lv.coef64, coeff->qp[l], ncq * sizeof(double), cudaMemcpyDefault, c->stream) != cudaSuccess)
+      return cuda_check(c, "copy coefficients");
+    vec_cast((long long)ncq, Lv.coef64, PREC_F64, Lv.coef32, PREC_F32, c->stream);
+    if (Lv.tensor) {
+      if (!coeff->mu_eff[l]) return fail(c, ALS_EINVAL, "missing mu_eff for a level");
+      const size_t nq = (size_t)Lv.g.ncells * NB;
+      if (cudaMemcpyAsync(Lv.mu64, coeff->mu_eff[l], nq * sizeof(double), cudaMemcpyDefault, c->stream) != cudaSuccess)
+        return cuda_check(c, "copy mu_eff");
+    }
+    if (l > 0) {
+      patch_setup(Lv, c->gamma, 1, c->st, c->stream);
+      ALS_TRY(cuda_check(c, "patch setup"));
+    }
+  }
+  coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream);
+  ALS_TRY(cuda_check(c, "coarse setup"));
+  const LevelDev& F = c->lev[c->L - 1];
+  schur_setup(F.g, c->gamma, F.mu64, c->schur, c->st, c->stream);
+  ALS_TRY(cuda_check(c, "schur setup"));
+  return check_status(c, "setup");
+}
+
+static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff* coeff, double gamma,
+                               const als_options* opt) {
+  if (!mesh || !coeff || !coeff->qp) return fail(c, ALS_EINVAL, "null mesh or coefficients");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(c, ALS_EINVAL, "dim must be 2 or 3");
+  if (mesh->levels < 1 || mesh->levels > 12) return fail(c, ALS_EINVAL, "levels must be in [1, 12]");
+  if (!(gamma >= 0.0) || !std::isfinite(gamma)) return fail(c, ALS_EINVAL, "gamma must be finite and >= 0");
+  if (coeff->kind != ALS_COEFF_SCALAR && coeff->kind != ALS_COEFF_TENSOR)
+    return fail(c, ALS_EINVAL, "unknown coefficient kind");
+  if (coeff->kind == ALS_COEFF_TENSOR && !coeff->mu_eff)
+    return fail(c, ALS_EINVAL, "tensor coefficients need mu_eff");
+  c->dim = mesh->dim;
+  c->L = mesh->levels;
+  c->gamma = gamma;
+  if (opt) c->opt = *opt; else als_default_options(&c->opt);
+  if (c->opt.sweeps < 1 || c->opt.sweeps > 64) return fail(c, ALS_EINVAL, "sweeps must be in [1, 64]");
+  if (c->opt.tau <= 0.0) c->opt.tau = std::pow(2.0, -c->dim);
+  if (c->opt.maxit < 1 || c->opt.maxit > 2000) return fail(c, ALS_EINVAL, "maxit must be in [1, 2000]");
+  if (c->opt.schur != ALS_SCHUR_P1) return fail(c, ALS_EINVAL, "only the P1 Schur approximation (W = M_p) is built");
+  if (c->opt.smoother != ALS_SMOOTH_GMRES && c->opt.smoother != ALS_SMOOTH_RICHARDSON)
+    return fail(c, ALS_EINVAL, "unknown smoother");
+  if (c->opt.transfer != ALS_TRANSFER_ROBUST && c->opt.transfer != ALS_TRANSFER_STANDARD)
+    return fail(c, ALS_EINVAL, "unknown transfer");
+  if (c->opt.mode != ALS_MODE_FP64 && c->opt.mode != ALS_MODE_MIXED) return fail(c, ALS_EINVAL, "unknown mode");
+  const int f = 1 << (c->L - 1);
+  for (int k = 0; k < c->dim; ++k) {
+    if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
+      return fail(c, ALS_EINVAL, "n must be divisible by 2^(levels-1) with >= 2 coarse cells per direction");
+  }
+  if (coeff->kind == ALS_COEFF_TENSOR && c->L > 1)
+    return fail(c, ALS_EINVAL, "tensor coefficients with more than one level: patch setup not built");
+  const char* ng = getenv("ALS_NO_GRAPH");
+  c->use_graph = !(ng && ng[0] == '1');
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_check(c, "stream create");
+  if (cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_check(c, "event create");
+  ALS_TRY(dalloc(c, &c->st, 1));
+  cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+  const int NB = c->dim == 2 ? 9 : 27;
+  const int NC = c->dim == 2 ? 6 : 21;
+  c->lev.resize(c->L);
+  for (int l = 0; l < c->L; ++l) {
+    int nl[3] = {1, 1, 1};
+    for (int k = 0; k < c->dim; ++k) nl[k] = mesh->n[k] >> (c->L - 1 - l);
+    LevelDev& Lv = c->lev[l];
+    Lv = LevelDev{};
+    Lv.g = make_geom(c->dim, nl);
+    Lv.tensor = coeff->kind == ALS_COEFF_TENSOR;
+    Lv.ncoef = Lv.tensor ? NC : 1;
+    Lv.np = c->dim * NB;
+    Lv.pstride = packed_stride(Lv.np);
+    const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
+    ALS_TRY(dalloc(c, &Lv.coef64, ncq));
+    ALS_TRY(dalloc(c, &Lv.coef32, ncq));
+    if (Lv.tensor) ALS_TRY(dalloc(c, &Lv.mu64, (size_t)Lv.g.ncells * NB));
+    else Lv.mu64 = Lv.coef64;
+    if (l > 0) {
+      ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
+      ALS_TRY(dalloc(c, &Lv.inv32, (size_t)Lv.g.nverts * Lv.pstride));
+    }
+  }
+  if (coarse_alloc(c->lev[0], &c->coarse) != 0) {
+    cudaGetLastError();
+    return fail(c, ALS_ENOMEM, "coarse setup allocation failed");
+  }
+  const LevelDev& F = c->lev[c->L - 1];
+  ALS_TRY(dalloc(c, &c->schur, (size_t)F.g.ncells * (c->dim + 1) * (c->dim + 1)));
+  ALS_TRY(alloc_work(c, c->w64, PREC_F64));
+  ALS_TRY(alloc_work(c, c->w32, PREC_F32));
+  return run_setup(c, coeff);
+}
+
+als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
+                      void* stream, als_ctx** out) {
+  if (!out) return ALS_EINVAL;
+  *out = nullptr;
+  als_ctx* c = new als_ctx();
+  c->user_stream = (cudaStream_t)stream;
+  if (stream) cudaStreamSynchronize((cudaStream_t)stream);
+  als_status st = create_impl(c, mesh, coeff, gamma, opt);
+  if (st != ALS_OK) {
+    // keep the message for the caller through a static buffer: the context is gone
+    static thread_local std::string last;
+    last = c->err;
+    als_destroy(c);
+    fprintf(stderr, "als_create: %s\n", last.c_str());
+    return st;
+  }
+  *out = c;
+  return ALS_OK;
+}
+
+als_status als_update_coefficients(als_ctx* c, const als_coeff* coeff) {
+  if (!c || !coeff || !coeff->qp) return c ? fail(c, ALS_EINVAL, "null coefficients") : ALS_EINVAL;
+  if ((coeff->kind == ALS_COEFF_TENSOR) != (c->lev[0].tensor != 0))
+    return fail(c, ALS_EINVAL, "coefficient kind differs from the one the context was created with");
+  if (coeff->kind == ALS_COEFF_TENSOR && !coeff->mu_eff) return fail(c, ALS_EINVAL, "tensor coefficients need mu_eff");
+  cudaEventRecord(c->order_ev, c->user_stream);
+  cudaStreamWaitEvent(c->stream, c->order_ev, 0);
+  return run_setup(c, coeff);
+}
+
+als_status als_profile(als_ctx* c, int on) {
+  if (!c) return ALS_EINVAL;
+  Prof& p = c->prof;
+  if ((on != 0) == p.on) return ALS_OK;
+  cudaStreamSynchronize(c->stream);
+  free_graphs(c);  // the V-cycle graphs are recaptured with (or without) event nodes
+  p.on = on != 0;
+  if (p.on && p.pool.empty()) {
+    p.pool.resize(16384);
+    for (auto& e : p.pool)
+      if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(c, "profiling events");
+    cudaEventCreate(&p.spare0);
+    cudaEventCreate(&p.spare1);
+  }
+  p.next = 0;
+  p.pairs.clear();
+  return ALS_OK;
+}
+
+als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) {
+  if (!c || !total_ms || !launches) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "profile read");
+  double tot = 0.0;
+  for (auto& pr : c->prof.pairs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof.pool[pr.first], c->prof.pool[pr.second]) == cudaSuccess) tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (long long)c->prof.pairs.size();
+  c->prof.pairs.clear();
+  c->prof.next = 0;
+  return ALS_OK;
+}
+
+long long als_kernel_launches(void) { return launch_count(); }
+
+static als_status check_level(als_ctx* c, int level, int prec) {
+  if (!c) return ALS_EINVAL;
+  if (level < 0 || level >= c->L) return fail(c, ALS_EINVAL, "level out of range");
+  if (prec != PREC_F64 && prec != PREC_F32) return fail(c, ALS_EINVAL, "prec must be ALS_PREC_FP64 or ALS_PREC_FP32");
+  return ALS_OK;
+}
+
+// order the context's stream after the work already queued on the caller's stream
+static void begin(als_ctx* c) {
+  cudaEventRecord(c->order_ev, c->user_stream);
+  cudaStreamWaitEvent(c->stream, c->order_ev, 0);
+}
+
+static als_status finish(als_ctx* c, const char* what) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, what);
+  ALS_TRY(cuda_check(c, what));
+  return check_status(c, what);
+}
+
+als_status als_apply_agamma(als_ctx* c, int level, int prec, const void* x, void* y) {
+  ALS_TRY(check_level(c, level, prec));
+  if (!x || !y) return fail(c, ALS_EINVAL, "null vector");
+  begin(c);
+  op_apply(c->lev[level], prec, OP_VISC | OP_AL, c->gamma, x, y, nullptr, nullptr, c->stream);
+  return finish(c, "apply_agamma");
+}
+
+als_status als_vcycle(als_ctx* c, int prec, const void* b, void* x) {
+  ALS_TRY(check_level(c, c ? c->L - 1 : 0, prec));
+  if (!b || !x) return fail(c, ALS_EINVAL, "null vector");
+  MGWork& w = work_for(c, prec);
+  const int l = c->L - 1;
+  const size_t bytes = (size_t)(c->lev[l].g.N * c->dim) * w.es;
+  begin(c);
+  cudaMemcpyAsync(w.b[l], b, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  ALS_TRY(run_vcycle(c, w));
+  cudaMemcpyAsync(x, w.x[l], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  return finish(c, "vcycle");
+}
+
+als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void* z) {
+  ALS_TRY(check_level(c, level, prec));
+  if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no smoother");
+  MGWork& w = work_for(c, prec);
+  begin(c);
+  patch_smooth(c->lev[level], prec, r, z, w.scratch[level], c->stream);
+  return finish(c, "star_smooth");
+}
+
+als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf) {
+  ALS_TRY(check_level(c, level, prec));
+  if (level < 1) return fail(c, ALS_EINVAL, "prolongation needs level >= 1");
+  begin(c);
+  prolong_level(c, work_for(c, prec), level, xc, xf);
+  return finish(c, "prolong");
+}
+
+als_status als_restrict(als_ctx* c, int level, int prec, const void* rf, void* rc) {
+  ALS_TRY(check_level(c, level, prec));
+  if (level < 1) return fail(c, ALS_EINVAL, "restriction needs level >= 1");
+  begin(c);
+  restrict_level(c, work_for(c, prec), level, rf, rc);
+  return finish(c, "restrict");
+}
+
+als_status als_coarse_solve(als_ctx* c, int prec, const void* b, void* x) {
+  ALS_TRY(check_level(c, 0, prec));
+  begin(c);
+  coarse_apply(c->lev[0], c->coarse, prec, b, x, c->stream);
+  return finish(c, "coarse_solve");
+}
+
+als_status als_apply_stokes(als_ctx* c, const double* u, const double* p, double* yu, double* yp) {
+  if (!c || !u || !p || !yu || !yp) return c ? fail(c, ALS_EINVAL, "null vector") : ALS_EINVAL;
+  const LevelDev& F = c->lev[c->L - 1];
+  begin(c);
+  op_apply(F, PREC_F64, OP_VISC | OP_AL | OP_BT | OP_B, c->gamma, u, yu, p, yp, c->stream);
+  return finish(c, "apply_stokes");
+}
+
+als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* out) {
+  ALS_TRY(check_level(c, level, PREC_F64));
+  if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no patches");
+  const LevelDev& Lv = c->lev[level];
+  if (vertex < 0 || vertex >= Lv.g.nverts) return fail(c, ALS_EINVAL, "vertex out of range");
+  std::vector<double> packed(Lv.pstride), full((size_t)Lv.np * Lv.np);
+  if (cudaMemcpyAsync(packed.data(), Lv.inv64 + vertex * Lv.pstride, sizeof(double) * Lv.pstride,
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_check(c, "patch_inverse");
+  const int np = Lv.np;
+  for (int t = 0; t < np; ++t)
+    for (int i = 0; i + t < np; ++i) {
+      const double v = packed[diag_start(np, t) + i];
+      full[(size_t)i * np + i + t] = v;
+      full[(size_t)(i + t) * np + i] = v;
+    }
+  if (cudaMemcpy(out, full.data(), sizeof(double) * full.size(), cudaMemcpyDefault) != cudaSuccess)
+    return cuda_check(c, "patch_inverse copy");
+  return ALS_OK;
+}
+
+als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u, double* p,
+                     als_solve_info* info) {
+  if (!c) return ALS_EINVAL;
+  if (!f_qp || !u || !p) return fail(c, ALS_EINVAL, "f_qp, u and p are required");
+  const int maxit = c->opt.maxit;
+  ALS_TRY(alloc_solve(c, maxit));
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  const int NB = c->dim == 2 ? 9 : 27;
+  begin(c);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  // inputs (host or device)
+  cudaMemcpyAsync(c->f_dev, f_qp, sizeof(double) * F.g.ncells * NB * c->dim, cudaMemcpyDefault, s);
+  if (u_bc) cudaMemcpyAsync(c->ubc_dev, u_bc, sizeof(double) * c->nu, cudaMemcpyDefault, s);
+  else cudaMemsetAsync(c->ubc_dev, 0, sizeof(double) * c->nu, s);
+  if (r2) cudaMemcpyAsync(c->r2_dev, r2, sizeof(double) * c->np, cudaMemcpyDefault, s);
+  else cudaMemsetAsync(c->r2_dev, 0, sizeof(double) * c->np, s);
+  ALS_TRY(cuda_check(c, "solve inputs"));
+  // lifted, augmented right-hand side (Eq. (augstokessys))
+  double* rhs = c->V;
+  double* rhs_u = rhs;
+  double* rhs_p = rhs + c->nu;
+  bnd_mask(F.g, c->ubc_dev, c->uD, 1, s);                                              // u_D
+  op_load_vector(F, c->f_dev, c->tu, s);                                               // F
+  op_apply(F, PREC_F64, OP_VISC | OP_AL | OP_RAW, c->gamma, c->uD, c->tu2, nullptr, nullptr, s);  // A_gamma u_D
+  vec_axpby(PREC_F64, c->nu, -1.0, c->tu2, 1.0, c->tu, s);                            // F - A_gamma u_D
+  op_apply(F, PREC_F64, OP_B | OP_RAW, c->gamma, c->uD, nullptr, nullptr, c->tp, s);   // B u_D
+  vec_axpby(PREC_F64, c->np, 1.0, c->r2_dev, -1.0, c->tp, s);                          // r2 - B u_D
+  cudaMemcpyAsync(rhs_p, c->tp, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, s);
+  winv_scale(F.g, c->gamma, c->r2_dev, c->tp2, s);                                     // gamma W^-1 r2 (user part)
+  op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);         // B^T gamma W^-1 r2
+  vec_axpby(PREC_F64, c->nu, 1.0, c->tu2, 1.0, c->tu, s);
+  bnd_mask(F.g, c->tu, rhs_u, 0, s);                                                   // zero boundary rows
+  // FGMRES (Sec. 6.1), right preconditioned, CGS2, x0 = 0
+  const int ldh = maxit + 1;
+  vec_multidot(PREC_F64, c->n, 1, rhs, c->n, rhs, c->nrm2, c->partial, s);
+  dev_init_g(maxit + 1, c->nrm2, c->g, c->beta, s);
+  vec_scale_dev(PREC_F64, c->n, nullptr, c->beta, rhs, rhs, s);
+  cudaMemsetAsync(c->H, 0, sizeof(double) * ldh * maxit, s);
+  cudaMemcpyAsync(c->host_res + 1, c->beta, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "solve rhs");
+  ALS_TRY(check_status(c, "solve rhs"));
+  const double beta = c->host_res[1];
+  int its = 0;
+  double resid = beta;
+  bool converged = beta == 0.0;
+  for (int k = 0; k < maxit && !converged; ++k) {
+    double* vk = c->V + (size_t)k * c->n;
+    double* zk = c->Z + (size_t)k * c->n;
+    double* w = c->V + (size_t)(k + 1) * c->n;
+    double* hcol = c->H + (size_t)k * ldh;
+    ALS_TRY(precondition(c, vk, zk));
+    matvec(c, zk, w);
+    vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, hcol, c->partial, s);
+    vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, hcol, w, s, -1.0);
+    vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, c->h2, c->partial, s);
+    vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, c->h2, w, s, -1.0);
+    vec_multidot(PREC_F64, c->n, 1, w, c->n, w, c->nrm2, c->partial, s);
+    dev_hess_finish(k, hcol, c->h2, c->nrm2, s);
+    vec_scale_dev(PREC_F64, c->n, nullptr, hcol + k + 1, w, w, s);
+    dev_givens_step(k, c->H, ldh, c->cs, c->sn, c->g, c->res, s);
+    cudaMemcpyAsync(c->host_res, c->res, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "fgmres");
+    its = k + 1;
+    resid = c->host_res[0];
+    if (!std::isfinite(resid)) {
+      ALS_TRY(check_status(c, "fgmres"));
+      return fail(c, ALS_EBREAKDOWN, "non-finite FGMRES residual");
+    }
+    if (resid <= c->opt.rtol * beta) converged = true;
+  }
+  // x = Z y; u = x_u + u_D; p = x_p with zero mean
+  cudaMemsetAsync(c->xsol, 0, sizeof(double) * c->n, s);
+  if (its > 0) {
+    dev_backsolve(its, c->H, ldh, c->g, c->y, s);
+    vec_multiaxpy(PREC_F64, c->n, its, c->Z, c->n, c->y, c->xsol, s, 1.0);
+  }
+  vec_axpby(PREC_F64, c->nu, 1.0, c->uD, 1.0, c->xsol, s);
+  project_constant(F.g.ncells, c->dim + 1, c->xsol + c->nu, c->partial, s);
+  cudaMemcpyAsync(u, c->xsol, sizeof(double) * c->nu, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(p, c->xsol + c->nu, sizeof(double) * c->np, cudaMemcpyDefault, s);
+  cudaEventRecord(e1, s);
+  ALS_TRY(finish(c, "solve"));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = its;
+    info->vcycles = 2 * its;
+    info->converged = converged ? 1 : 0;
+    info->res0 = beta;
+    info->res_final = resid;
+    info->solve_ms = ms;
+  }
+  if (!converged) return fail(c, ALS_ENOTCONV, "FGMRES did not converge within maxit");
+  return ALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Shared device-side definitions for the AL-multigrid Stokes library.
+//
+// Discretisation: [Q2]^d x P1^disc on a uniform mesh of (0,1)^d (Sec. 5 of
+// Shih, Stadler & Wechsung, "Robust multigrid techniques for augmented
+// Lagrangian preconditioning of incompressible Stokes equations with extreme
+// viscosity variations").  Velocity vectors hold d blocks of nodal values on
+// the (2n+1)^d Q2 lattice (x fastest); pressures are [cell][d+1] coefficients
+// of {1, xi_0, .., xi_(d-1)} on the reference cell [-1,1]^d.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace als {
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int dim;
+  int n[3];      // cells per direction (n[2] = 1 in 2D)
+  int nn[3];     // Q2 nodes per direction, 2n+1 (nn[2] = 1 in 2D)
+  int nv[3];     // vertices per direction, n+1 (nv[2] = 1 in 2D)
+  long long N;   // nodes
+  long long ncells;
+  long long nverts;
+  double h[3];
+};
+
+// Reference-element tables on [-1,1], as compile-time formulas: the three
+// quadratic Lagrange polynomials l_0 = xi(xi-1)/2, l_1 = 1-xi^2,
+// l_2 = xi(xi+1)/2 on the nodes -1, 0, 1 and their derivatives, evaluated at
+// the 3-point Gauss-Legendre abscissae (-g, 0, g), g = sqrt(3/5), with weights
+// (5/9, 8/9, 5/9).  With g^2 = 3/5: l_0(-g) = l_2(g) = 3/10 + g/2,
+// l_2(-g) = l_0(g) = 3/10 - g/2, l_1(+-g) = 2/5.
+template <typename T>
+struct Ref {
+  static constexpr T g = T(0.774596669241483377035853079956);
+  __host__ __device__ __forceinline__ static constexpr T G(int q) {
+    return q == 0 ? -g : (q == 1 ? T(0) : g);
+  }
+  __host__ __device__ __forceinline__ static constexpr T W(int q) {
+    return q == 1 ? T(8.0 / 9.0) : T(5.0 / 9.0);
+  }
+  __host__ __device__ __forceinline__ static constexpr T B(int q, int a) {
+    return q == 1 ? (a == 1 ? T(1) : T(0))
+                  : (a == 1 ? T(0.4) : (((q == 0) == (a == 0)) ? T(0.3) + T(0.5) * g : T(0.3) - T(0.5) * g));
+  }
+  __host__ __device__ __forceinline__ static constexpr T D(int q, int a) {
+    return a == 0 ? G(q) - T(0.5) : (a == 1 ? T(-2) * G(q) : G(q) + T(0.5));
+  }
+};
+
+// ---------------------------------------------------------------- status
+// Device-side failures never trap: kernels record a code and an index here
+// and the host reads the record back at the end of setup/solve.
+struct DevStatus {
+  int code;        // 0 = ok, otherwise an als_status value
+  long long where; // e.g. the vertex whose patch matrix had a non-positive pivot
+};
+
+__device__ __forceinline__ void report(DevStatus* st, int code, long long where) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+__host__ __device__ __forceinline__ bool on_boundary(const Geom& g, int i, int j, int k) {
+  if (i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1) return true;
+  if (g.dim == 3 && (k == 0 || k == g.nn[2] - 1)) return true;
+  return false;
+}
+
+__host__ __device__ __forceinline__ long long node_id(const Geom& g, int i, int j, int k) {
+  return (long long)i + (long long)g.nn[0] * ((long long)j + (long long)g.nn[1] * k);
+}
+
+template <int DIM> struct Sz;
+template <> struct Sz<2> { static constexpr int NB = 9, NP = 18, NPR = 3, NM = 3, NC = 6, NCELL_STAR = 4; };
+template <> struct Sz<3> { static constexpr int NB = 27, NP = 81, NPR = 4, NM = 6, NC = 21, NCELL_STAR = 8; };
+
+// packed symmetric storage of an NP x NP patch inverse, by diagonals:
+// diagonal t (0..NP-1) holds the entries (i, i+t), i = 0..NP-1-t.
+__host__ __device__ constexpr int diag_start(int np, int t) { return t * np - (t * (t - 1)) / 2; }
+__host__ __device__ constexpr int packed_size(int np) { return np * (np + 1) / 2; }
+// per-patch stride, rounded to a multiple of 4 entries (16-byte aligned rows)
+__host__ __device__ constexpr int packed_stride(int np) { return (packed_size(np) + 3) & ~3; }
+
+}  // namespace als

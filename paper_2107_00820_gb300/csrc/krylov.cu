@@ -1,0 +1,397 @@
+// K8/K9/K11: vector kernels, Krylov bookkeeping on the device, Schur block apply.
+//
+// All reductions use a fixed grid and a fixed combination order, so results
+// are bitwise reproducible from run to run.  Small dense work (Givens
+// rotations of the Hessenberg matrices, triangular solves) runs in
+// single-thread kernels so that no step of a solve needs the host.
+#include <math.h>
+
+#include <atomic>
+
+#include "krylov.h"
+#include "level.h"
+
+namespace als {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launch(long long n) { g_launches += n; }
+
+static constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+static constexpr int RED_THREADS = 256;
+
+template <typename T>
+__global__ void k_axpby(long long n, double a, const T* __restrict__ x, double b, T* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)(a * (double)x[i] + (b == 0.0 ? 0.0 : b * (double)y[i]));
+}
+
+template <typename T>
+__global__ void k_axpy_dev(long long n, const double* __restrict__ a, double sign, const T* __restrict__ x,
+                           T* __restrict__ y) {
+  const T s = (T)(sign * a[0]);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += s * x[i];
+}
+
+template <typename S, typename D>
+__global__ void k_cast(long long n, const S* __restrict__ x, D* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (D)x[i];
+}
+
+template <typename T>
+__global__ void k_scale_dev(long long n, const double* __restrict__ num, const double* __restrict__ den,
+                            const T* __restrict__ x, T* __restrict__ y) {
+  const double dn = den ? den[0] : 1.0;
+  const double f = (num ? num[0] : 1.0);
+  const T s = (T)(dn != 0.0 ? f / dn : 0.0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = s * x[i];
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;  // valid in thread 0
+}
+
+// partial[b*k + j] = sum over block b's elements of V_j . w  (4 rows per sweep)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int k, const T* __restrict__ V, long long ld,
+                                                          const T* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double sh[RED_THREADS / 32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double wi = (double)w[i];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+        if (j0 + jj < k) acc[jj] += (double)V[(long long)(j0 + jj) * ld + i] * wi;
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (j0 + jj >= k) break;
+      const double s = block_sum(acc[jj], sh);
+      if (threadIdx.x == 0) partial[(long long)blockIdx.x * k + j0 + jj] = s;
+    }
+  }
+}
+
+__global__ void k_multidot_final(int k, int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[(long long)b * k + j];
+  out[j] = s;
+}
+
+template <typename T>
+__global__ void k_multiaxpy(long long n, int k, const T* __restrict__ V, long long ld, const double* __restrict__ h,
+                            double sign, T* __restrict__ w) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += (double)V[(long long)j * ld + i] * h[j];
+    w[i] = (T)((double)w[i] + sign * acc);
+  }
+}
+
+static unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 8) b = 152LL * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+void vec_axpby(int prec, long long n, double a, const void* x, double b, void* y, cudaStream_t s) {
+  if (prec == PREC_F64) k_axpby<double><<<grid_for(n), 256, 0, s>>>(n, a, (const double*)x, b, (double*)y);
+  else k_axpby<float><<<grid_for(n), 256, 0, s>>>(n, a, (const float*)x, b, (float*)y);
+  count_launch(1);
+}
+
+void vec_axpy_dev(int prec, long long n, const double* a, double sign, const void* x, void* y, cudaStream_t s) {
+  if (prec == PREC_F64) k_axpy_dev<double><<<grid_for(n), 256, 0, s>>>(n, a, sign, (const double*)x, (double*)y);
+  else k_axpy_dev<float><<<grid_for(n), 256, 0, s>>>(n, a, sign, (const float*)x, (float*)y);
+  count_launch(1);
+}
+
+void vec_cast(long long n, const void* src, int src_prec, void* dst, int dst_prec, cudaStream_t s) {
+  if (src_prec == PREC_F64 && dst_prec == PREC_F32) {
+    k_cast<double, float><<<grid_for(n), 256, 0, s>>>(n, (const double*)src, (float*)dst);
+    count_launch(1);
+  } else if (src_prec == PREC_F32 && dst_prec == PREC_F64) {
+    k_cast<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float*)src, (double*)dst);
+    count_launch(1);
+  } else
+    cudaMemcpyAsync(dst, src, n * (src_prec == PREC_F64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
+}
+
+void vec_zero(int prec, long long n, void* x, cudaStream_t s) {
+  cudaMemsetAsync(x, 0, n * (prec == PREC_F64 ? 8 : 4), s);
+}
+
+size_t multidot_partial_doubles(int k) { return (size_t)RED_BLOCKS * (size_t)k; }
+
+void vec_multidot(int prec, long long n, int k, const void* V, long long ld, const void* w, double* out,
+                  double* partial, cudaStream_t s) {
+  if (prec == PREC_F64)
+    k_multidot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial);
+  else
+    k_multidot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial);
+  k_multidot_final<<<(k + 127) / 128, 128, 0, s>>>(k, RED_BLOCKS, partial, out);
+  count_launch(2);
+}
+
+void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h, void* w,
+                   cudaStream_t s, double sign) {
+  if (prec == PREC_F64)
+    k_multiaxpy<double><<<grid_for(n), 256, 0, s>>>(n, k, (const double*)V, ld, h, sign, (double*)w);
+  else
+    k_multiaxpy<float><<<grid_for(n), 256, 0, s>>>(n, k, (const float*)V, ld, h, sign, (float*)w);
+  count_launch(1);
+}
+
+void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h, void* w,
+                   cudaStream_t s) {
+  vec_multiaxpy(prec, n, k, V, ld, h, w, s, -1.0);
+}
+
+void vec_scale_dev(int prec, long long n, const double* num, const double* den, const void* x, void* y,
+                   cudaStream_t s) {
+  if (prec == PREC_F64) k_scale_dev<double><<<grid_for(n), 256, 0, s>>>(n, num, den, (const double*)x, (double*)y);
+  else k_scale_dev<float><<<grid_for(n), 256, 0, s>>>(n, num, den, (const float*)x, (float*)y);
+  count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// small dense work on the device
+// ---------------------------------------------------------------------------
+__global__ void k_sqrt(const double* __restrict__ in, double* __restrict__ out) { out[0] = sqrt(fmax(in[0], 0.0)); }
+
+void dev_sqrt(const double* in, double* out, cudaStream_t s) { k_sqrt<<<1, 1, 0, s>>>(in, out);
+  count_launch(1); }
+
+// h[0..k] += h2[0..k]; H[k+1][k] (stored at hcol[k+1]) = sqrt(nrm2)
+__global__ void k_hess_finish(int k, double* __restrict__ hcol, const double* __restrict__ h2,
+                              const double* __restrict__ nrm2) {
+  for (int i = 0; i <= k; ++i) hcol[i] += h2 ? h2[i] : 0.0;
+  hcol[k + 1] = sqrt(fmax(nrm2[0], 0.0));
+}
+
+void dev_hess_finish(int k, double* hcol, const double* h2, const double* nrm2, cudaStream_t s) {
+  k_hess_finish<<<1, 1, 0, s>>>(k, hcol, h2, nrm2);
+  count_launch(1);
+}
+
+// Incremental Givens QR of the Hessenberg matrix of (F)GMRES.
+// H is column-major with leading dimension ldh; column k has entries 0..k+1.
+// State: cs, sn (rotations), g (rotated right-hand side, g[0] = beta initially).
+// Writes |g[k+1]| (the residual norm of the least-squares problem) to res.
+__global__ void k_givens_step(int k, double* __restrict__ H, int ldh, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res) {
+  double* h = H + (long long)k * ldh;
+  for (int i = 0; i < k; ++i) {
+    const double a = h[i], b = h[i + 1];
+    h[i] = cs[i] * a + sn[i] * b;
+    h[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = h[k], b = h[k + 1];
+  const double r = hypot(a, b);
+  double c = 1.0, sv = 0.0;
+  if (r > 0.0) { c = a / r; sv = b / r; }
+  cs[k] = c; sn[k] = sv;
+  h[k] = r; h[k + 1] = 0.0;
+  g[k + 1] = -sv * g[k];
+  g[k] = c * g[k];
+  res[0] = fabs(g[k + 1]);
+}
+
+void dev_givens_step(int k, double* H, int ldh, double* cs, double* sn, double* g, double* res, cudaStream_t s) {
+  k_givens_step<<<1, 1, 0, s>>>(k, H, ldh, cs, sn, g, res);
+  count_launch(1);
+}
+
+// y = R^-1 g for the rotated (upper-triangular) k x k Hessenberg; a zero
+// pivot (exact breakdown) drops that direction.
+__global__ void k_backsolve(int k, const double* __restrict__ H, int ldh, const double* __restrict__ g,
+                            double* __restrict__ y) {
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int j = i + 1; j < k; ++j) acc -= H[(long long)j * ldh + i] * y[j];
+    const double d = H[(long long)i * ldh + i];
+    y[i] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+void dev_backsolve(int k, const double* H, int ldh, const double* g, double* y, cudaStream_t s) {
+  k_backsolve<<<1, 1, 0, s>>>(k, H, ldh, g, y);
+  count_launch(1);
+}
+
+// g = (beta, 0, ...), where beta = sqrt(nrm2)
+__global__ void k_init_g(int m, const double* __restrict__ nrm2, double* __restrict__ g, double* __restrict__ beta) {
+  const double b = sqrt(fmax(nrm2[0], 0.0));
+  beta[0] = b;
+  g[0] = b;
+  for (int i = 1; i < m; ++i) g[i] = 0.0;
+}
+
+void dev_init_g(int m, const double* nrm2, double* g, double* beta, cudaStream_t s) {
+  k_init_g<<<1, 1, 0, s>>>(m, nrm2, g, beta);
+  count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// pressure space: Schur block apply and constant-mode projection
+// ---------------------------------------------------------------------------
+__global__ void k_schur(long long ncells, int npr, const double* __restrict__ S, const double* __restrict__ t,
+                        double* __restrict__ z) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int i = 0; i < npr; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < npr; ++j) acc += S[(c * npr + i) * npr + j] * t[c * npr + j];
+    z[c * npr + i] = -acc;
+  }
+}
+
+void schur_apply(long long ncells, int npr, const double* S, const double* t, double* z, cudaStream_t s) {
+  k_schur<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(ncells, npr, S, t, z);
+  count_launch(1);
+}
+
+__global__ void k_slot0_sum(long long ncells, int npr, const double* __restrict__ p, double* __restrict__ partial) {
+  __shared__ double sh[RED_THREADS / 32];
+  double acc = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long long)gridDim.x * blockDim.x)
+    acc += p[c * npr];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_slot0_sub(long long ncells, int npr, const double* __restrict__ partial, int nb, double* __restrict__ p) {
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[b];
+  const double mean = s / (double)ncells;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long long)gridDim.x * blockDim.x)
+    p[c * npr] -= mean;
+}
+
+// p <- p - (n.p / n.n) n with n = 1 on the constant-basis slot of every cell
+void project_constant(long long ncells, int npr, double* p, double* partial, cudaStream_t s) {
+  k_slot0_sum<<<RED_BLOCKS, RED_THREADS, 0, s>>>(ncells, npr, p, partial);
+  k_slot0_sub<<<grid_for(ncells), 256, 0, s>>>(ncells, npr, partial, RED_BLOCKS, p);
+  count_launch(2);
+}
+
+}  // namespace als
+
+namespace als {
+
+// ---------------------------------------------------------------------------
+// Schur-complement blocks of Eq. (P1P2), variant P1, one (d+1)x(d+1) FP64 block
+// per cell: S_K = M_K(1/mu)^-1 + gamma M_K^-1 with
+// [M_K(1/mu)]_ab = sum_q |J| w_q mu_q^-1 psi_a(x_q) psi_b(x_q) (Eq. (inv-visc-mass))
+// and M_K = |K| diag(1, 1/3, ..).  The small SPD block is inverted through
+// its Cholesky factor.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_schur_setup(Geom g, double gamma, const double* __restrict__ mu, double* __restrict__ S,
+                              DevStatus* st) {
+  constexpr int NPR = DIM + 1, NB = DIM == 2 ? 9 : 27;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncells) return;
+  double wdet = 1.0, vol = 1.0;
+  for (int k = 0; k < DIM; ++k) { wdet *= 0.5 * g.h[k]; vol *= g.h[k]; }
+  double M[NPR][NPR];
+  for (int a = 0; a < NPR; ++a)
+    for (int b = 0; b < NPR; ++b) M[a][b] = 0.0;
+  for (int q = 0; q < NB; ++q) {
+    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+    double psi[NPR];
+    psi[0] = 1.0; psi[1] = Ref<double>::G(qx); psi[2] = Ref<double>::G(qy);
+    if (DIM == 3) psi[3] = Ref<double>::G(qz);
+    const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) /
+                     mu[c * NB + q];
+    for (int a = 0; a < NPR; ++a)
+      for (int b = 0; b < NPR; ++b) M[a][b] += w * psi[a] * psi[b];
+  }
+  // Cholesky M = L L^T, then X = L^-1, inverse = X^T X
+  double Lm[NPR][NPR] = {};
+  for (int j = 0; j < NPR; ++j) {
+    double d = M[j][j];
+    for (int k = 0; k < j; ++k) d -= Lm[j][k] * Lm[j][k];
+    if (!(d > 0.0)) { report(st, 4, c); d = 1.0; }
+    Lm[j][j] = sqrt(d);
+    for (int i = j + 1; i < NPR; ++i) {
+      double v = M[i][j];
+      for (int k = 0; k < j; ++k) v -= Lm[i][k] * Lm[j][k];
+      Lm[i][j] = v / Lm[j][j];
+    }
+  }
+  double X[NPR][NPR] = {};
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) acc -= Lm[i][k] * X[k][j];
+      X[i][j] = acc / Lm[i][i];
+    }
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j < NPR; ++j) {
+      double acc = 0.0;
+      for (int k = (i > j ? i : j); k < NPR; ++k) acc += X[k][i] * X[k][j];
+      if (i == j) acc += gamma * (i == 0 ? 1.0 : 3.0) / vol;
+      S[(c * NPR + i) * NPR + j] = acc;
+    }
+}
+
+void schur_setup(const Geom& g, double gamma, const double* mu, double* S, DevStatus* st, cudaStream_t s) {
+  const unsigned b = (unsigned)((g.ncells + 127) / 128);
+  if (g.dim == 2) k_schur_setup<2><<<b, 128, 0, s>>>(g, gamma, mu, S, st);
+  else k_schur_setup<3><<<b, 128, 0, s>>>(g, gamma, mu, S, st);
+  count_launch(1);
+}
+
+// keep_boundary = 1: y = x on boundary nodes, 0 inside; keep_boundary = 0: the converse
+__global__ void k_bnd_mask(Geom g, const double* __restrict__ x, double* __restrict__ y, int keep_boundary) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N * g.dim) return;
+  const long long nd = t % g.N;
+  const int i = (int)(nd % g.nn[0]);
+  const long long r = nd / g.nn[0];
+  const int j = (int)(r % g.nn[1]);
+  const int k = (int)(r / g.nn[1]);
+  const bool b = on_boundary(g, i, j, k);
+  y[t] = (b == (keep_boundary != 0)) ? x[t] : 0.0;
+}
+
+void bnd_mask(const Geom& g, const double* x, double* y, int keep_boundary, cudaStream_t s) {
+  const long long tot = g.N * g.dim;
+  k_bnd_mask<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, x, y, keep_boundary);
+  count_launch(1);
+}
+
+// out = gamma W^-1 r2 with W = M_p = |K| diag(1, 1/3, ..) on every cell
+__global__ void k_winv(long long ncells, int npr, double scale0, double scale1, const double* __restrict__ r2,
+                       double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncells * npr) return;
+  out[t] = r2[t] * ((t % npr) == 0 ? scale0 : scale1);
+}
+
+void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cudaStream_t s) {
+  double vol = 1.0;
+  for (int k = 0; k < g.dim; ++k) vol *= g.h[k];
+  const long long tot = g.ncells * (g.dim + 1);
+  k_winv<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g.ncells, g.dim + 1, gamma / vol, 3.0 * gamma / vol, r2, out);
+  count_launch(1);
+}
+
+}  // namespace als

@@ -1,0 +1,36 @@
+// Device-side Krylov helpers shared by the V-cycle smoother and the outer FGMRES.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace als {
+
+void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h, void* w,
+                   cudaStream_t s, double sign);
+void dev_sqrt(const double* in, double* out, cudaStream_t s);
+void dev_hess_finish(int k, double* hcol, const double* h2, const double* nrm2, cudaStream_t s);
+void dev_givens_step(int k, double* H, int ldh, double* cs, double* sn, double* g, double* res, cudaStream_t s);
+void dev_backsolve(int k, const double* H, int ldh, const double* g, double* y, cudaStream_t s);
+void dev_init_g(int m, const double* nrm2, double* g, double* beta, cudaStream_t s);
+void schur_apply(long long ncells, int npr, const double* S, const double* t, double* z, cudaStream_t s);
+void project_constant(long long ncells, int npr, double* p, double* partial, cudaStream_t s);
+
+// coarse.cu
+struct CoarseDev {
+  int nfree = 0;
+  double* inv = nullptr;   // nfree x nfree, row-major, FP64 inverse of the coarse free-dof block
+  double* X = nullptr;     // setup scratch: unit columns, their images, the dense matrix
+  double* Y = nullptr;
+  double* A = nullptr;
+};
+int coarse_alloc(const struct LevelDev& L, CoarseDev* C);
+void coarse_setup(const struct LevelDev& L, double gamma, CoarseDev* C, struct DevStatus* st, cudaStream_t s);
+void coarse_apply(const struct LevelDev& L, const CoarseDev& C, int prec, const void* b, void* x, cudaStream_t s);
+void coarse_free(CoarseDev* C);
+
+}  // namespace als
+
+namespace als {
+void schur_setup(const struct Geom& g, double gamma, const double* mu, double* S, struct DevStatus* st, cudaStream_t s);
+void bnd_mask(const struct Geom& g, const double* x, double* y, int keep_boundary, cudaStream_t s);
+void winv_scale(const struct Geom& g, double gamma, const double* r2, double* out, cudaStream_t s);
+}  // namespace als

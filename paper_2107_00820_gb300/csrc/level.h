@@ -1,0 +1,74 @@
+// Host-side description of one multigrid level as seen by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace als {
+
+struct LevelDev {
+  Geom g;
+  int tensor;            // 0: scalar mu per point, 1: Mandel tensor per point
+  int ncoef;             // values per point (1 or NC)
+  double* coef64;        // [cell][3^d][ncoef]
+  float* coef32;
+  double* mu64;          // scalar viscosity per point (mu or mu_eff), FP64
+  // vertex-star patch inverses, packed symmetric by diagonals, one per vertex
+  double* inv64;
+  float* inv32;
+  int np;                // patch size d*3^d
+  int pstride;           // entries per patch (padded)
+};
+
+enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
+
+// Process-wide count of kernels this library has put on a stream (graph
+// replays add the number of kernel nodes of the graph).  Launchers call
+// count_launch(); while a V-cycle is being captured the count is attributed
+// to the graph instead.
+long long launch_count();
+void count_launch(long long n);
+
+// ---- operator.cu
+void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y,
+              const void* p_in, void* p_out, cudaStream_t s);
+void op_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
+void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y, int nvec,
+                    long long stride, cudaStream_t s);
+
+// ---- patches.cu
+void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s);
+// e0/e1 (optional) are recorded immediately before and after the patch kernel
+void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
+                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
+size_t patch_scratch_bytes(const LevelDev& L, int prec);
+// local solves on the coarse-cell interiors (stars of the fine vertices at the
+// coarse-cell centres):  mode 0: out = sum_K E_K A_K^-1 E_K^T in  (out zeroed first)
+//                        mode 1: out -= sum_K E_K A_K^-1 E_K^T in
+void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract,
+                          cudaStream_t s);
+
+// ---- transfer.cu
+void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf,
+                 cudaStream_t s);
+void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc,
+                  cudaStream_t s);
+
+// ---- krylov.cu (vector kernels)
+void vec_axpby(int prec, long long n, double a, const void* x, double b, void* y, cudaStream_t s);
+void vec_axpy_dev(int prec, long long n, const double* a, double sign, const void* x, void* y,
+                  cudaStream_t s);
+void vec_cast(long long n, const void* src, int src_prec, void* dst, int dst_prec, cudaStream_t s);
+void vec_zero(int prec, long long n, void* x, cudaStream_t s);
+// out[j] = <V_j, w> for j < k, V stored as k rows of length n with leading dim ld
+void vec_multidot(int prec, long long n, int k, const void* V, long long ld, const void* w,
+                  double* out, double* partial, cudaStream_t s);
+// w -= sum_j V_j h[j]
+void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h,
+                   void* w, cudaStream_t s);
+void vec_scale_dev(int prec, long long n, const double* num, const double* den, const void* x, void* y,
+                   cudaStream_t s);
+size_t multidot_partial_doubles(int k);
+
+}  // namespace als

@@ -1,0 +1,379 @@
+// K2/K3/K4: vertex-star patches of the PSC smoother (Sec. 5.1, Eq. (viim)).
+//
+// For every vertex v the local space V_v = {v in V_h : supp v in star(v)} is
+// spanned by the free dofs at the 3^d Q2 nodes within half a cell of v.  Its
+// matrix A_v is the restriction of the assembled A_(h,gamma) to V_v; here it is
+// accumulated directly from the contributions of the 2^d cells of the star,
+// factored by Cholesky in FP64 and inverted, and the inverse is stored packed
+// (symmetric, by diagonals) in FP64 and optionally FP32.  Missing nodes of
+// boundary stars become identity rows so that every patch has d*3^d entries.
+//
+// The smoother applies z = sum_v I_v A_v^-1 I_v^T r in two deterministic steps:
+// one warp per patch computes y_v = A_v^-1 r|_v into a per-patch buffer, then
+// one thread per node sums the <= 2^d patch values that contain it in a fixed
+// order (no floating-point atomics).
+#include <algorithm>
+
+#include "level.h"
+
+namespace als {
+
+// node offset index o in [0, 3^d): offsets (o%3 - 1, (o/3)%3 - 1, o/9 - 1) from 2v
+template <int DIM>
+__device__ __forceinline__ bool patch_node(const Geom& g, int vx, int vy, int vz, int o, long long& nd) {
+  const int i = 2 * vx + o % 3 - 1;
+  const int j = 2 * vy + (o / 3) % 3 - 1;
+  const int k = (DIM == 3) ? 2 * vz + o / 9 - 1 : 0;
+  if (i <= 0 || i >= g.nn[0] - 1 || j <= 0 || j >= g.nn[1] - 1) return false;
+  if (DIM == 3 && (k <= 0 || k >= g.nn[2] - 1)) return false;
+  nd = node_id(g, i, j, k);
+  return true;
+}
+
+template <int DIM>
+__device__ __forceinline__ void vertex_coords(const Geom& g, long long v, int& vx, int& vy, int& vz) {
+  vx = (int)(v % g.nv[0]);
+  const long long r = v / g.nv[0];
+  vy = (int)(r % g.nv[1]);
+  vz = (DIM == 3) ? (int)(r / g.nv[1]) : 0;
+}
+
+// ---------------------------------------------------------------------------
+// K2 + K3: assemble, factor and invert one patch per CTA (FP64)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ mu, double* __restrict__ inv64,
+                              float* __restrict__ inv32, int pstride, DevStatus* st) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
+  constexpr int NSUB = 1 << DIM;  // patch nodes inside one cell of the star
+  extern __shared__ double sm[];
+  double* A = sm;                    // NP x NP, lower triangle used
+  double* X = A + NP * NP;           // NP x NP, L^-1
+  double* gt = X + NP * NP;          // [q][a][k] physical gradient of phi_a at point q
+  double* bt = gt + NB * NB * DIM;   // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
+  double* wq = bt + NPR * DIM * NB;  // [q] |J| w_q mu_q of the current cell
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long v = blockIdx.x;
+  int vx, vy, vz;
+  vertex_coords<DIM>(g, v, vx, vy, vz);
+
+  double s[3] = {2.0 / g.h[0], 2.0 / g.h[1], DIM == 3 ? 2.0 / g.h[2] : 0.0};
+  double wdet = 1.0, vol = 1.0;
+  for (int k = 0; k < DIM; ++k) { wdet *= 0.5 * g.h[k]; vol *= g.h[k]; }
+
+  for (int e = tid; e < NP * NP; e += nt) A[e] = 0.0;
+  for (int e = tid; e < NB * NB; e += nt) {
+    const int q = e / NB, a = e % NB;
+    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    const double bx = Ref<double>::B(qx, ax), by = Ref<double>::B(qy, ay);
+    const double bz = DIM == 3 ? Ref<double>::B(qz, az) : 1.0;
+    gt[e * DIM + 0] = Ref<double>::D(qx, ax) * by * bz * s[0];
+    gt[e * DIM + 1] = bx * Ref<double>::D(qy, ay) * bz * s[1];
+    if (DIM == 3) gt[e * DIM + 2] = bx * by * Ref<double>::D(qz, az) * s[2];
+  }
+  __syncthreads();
+  for (int e = tid; e < NPR * DIM * NB; e += nt) {
+    const int p = e / (DIM * NB), al = (e / NB) % DIM, a = e % NB;
+    double acc = 0.0;
+    for (int q = 0; q < NB; ++q) {
+      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+      const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
+      const double psi = p == 0 ? 1.0 : Ref<double>::G(p == 1 ? qx : (p == 2 ? qy : qz));
+      acc += w * psi * gt[(q * NB + a) * DIM + al];
+    }
+    bt[e] = -acc;
+  }
+
+  // contributions of the 2^d cells of the star
+  for (int sc = 0; sc < NSUB; ++sc) {
+    const int sx = sc & 1, sy = (sc >> 1) & 1, sz = (sc >> 2) & 1;
+    const int cx = vx - 1 + sx, cy = vy - 1 + sy, cz = DIM == 3 ? vz - 1 + sz : 0;
+    const bool valid = cx >= 0 && cx < g.n[0] && cy >= 0 && cy < g.n[1] &&
+                       (DIM == 2 || (cz >= 0 && cz < g.n[2]));
+    __syncthreads();
+    if (!valid) continue;
+    const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
+    for (int q = tid; q < NB; q += nt) {
+      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+      wq[q] = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) *
+              mu[cell * NB + q];
+    }
+    __syncthreads();
+    for (int pr = tid; pr < NSUB * NSUB; pr += nt) {
+      const int i = pr / NSUB, j = pr % NSUB;
+      // patch offset o_k and cell-local index a_k of sub-node i (same for j):
+      //   s_k = 0 (cell below the vertex): o_k in {0,1}, a_k = o_k + 1
+      //   s_k = 1 (cell above):            o_k in {1,2}, a_k = o_k - 1
+      int oi[3], ai[3], oj[3], aj[3];
+      const int sv[3] = {sx, sy, sz};
+      for (int k = 0; k < 3; ++k) {
+        const int bi = (i >> k) & 1, bj = (j >> k) & 1;
+        oi[k] = sv[k] ? bi + 1 : bi; ai[k] = sv[k] ? oi[k] - 1 : oi[k] + 1;
+        oj[k] = sv[k] ? bj + 1 : bj; aj[k] = sv[k] ? oj[k] - 1 : oj[k] + 1;
+      }
+      const int P = oi[0] + 3 * oi[1] + (DIM == 3 ? 9 * oi[2] : 0);
+      const int Q = oj[0] + 3 * oj[1] + (DIM == 3 ? 9 * oj[2] : 0);
+      long long ndP, ndQ;
+      if (!patch_node<DIM>(g, vx, vy, vz, P, ndP) || !patch_node<DIM>(g, vx, vy, vz, Q, ndQ)) continue;
+      const int a = ai[0] + 3 * ai[1] + (DIM == 3 ? 9 * ai[2] : 0);
+      const int b = aj[0] + 3 * aj[1] + (DIM == 3 ? 9 * aj[2] : 0);
+      double G[DIM][DIM];
+      for (int k = 0; k < DIM; ++k)
+        for (int l = 0; l < DIM; ++l) G[k][l] = 0.0;
+      for (int q = 0; q < NB; ++q) {
+        const double w = wq[q];
+        for (int k = 0; k < DIM; ++k) {
+          const double ga = w * gt[(q * NB + a) * DIM + k];
+          for (int l = 0; l < DIM; ++l) G[k][l] += ga * gt[(q * NB + b) * DIM + l];
+        }
+      }
+      double tr = 0.0;
+      for (int k = 0; k < DIM; ++k) tr += G[k][k];
+      for (int al = 0; al < DIM; ++al)
+        for (int be = 0; be < DIM; ++be) {
+          double val = G[be][al] + (al == be ? tr : 0.0);
+          double alv = 0.0;
+          for (int p = 0; p < NPR; ++p)
+            alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
+          val += gamma / vol * alv;
+          A[(al * NB + P) * NP + be * NB + Q] += val;
+        }
+    }
+  }
+  __syncthreads();
+  // identity rows for nodes outside the domain or on the Dirichlet boundary
+  for (int i = tid; i < NP; i += nt) {
+    long long nd;
+    if (!patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) A[i * NP + i] = 1.0;
+  }
+  __syncthreads();
+
+  // Cholesky A = L L^T (lower triangle, in place)
+  for (int k = 0; k < NP; ++k) {
+    if (tid == 0) {
+      double d = A[k * NP + k];
+      if (!(d > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, v); d = 1.0; }
+      A[k * NP + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = A[k * NP + k];
+    for (int i = k + 1 + tid; i < NP; i += nt) A[i * NP + k] /= piv;
+    __syncthreads();
+    for (int i = k + 1 + tid; i < NP; i += nt) {
+      const double lik = A[i * NP + k];
+      for (int j = k + 1; j <= i; ++j) A[i * NP + j] -= lik * A[j * NP + k];
+    }
+    __syncthreads();
+  }
+  // X = L^-1 by rows
+  for (int i = 0; i < NP; ++i) {
+    const double lii = A[i * NP + i];
+    for (int j = tid; j <= i; j += nt) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) acc -= A[i * NP + k] * X[k * NP + j];
+      X[i * NP + j] = acc / lii;
+    }
+    __syncthreads();
+  }
+  // A^-1 = X^T X, written packed by diagonals: entry (i, i+t)
+  constexpr int NPK = NP * (NP + 1) / 2;
+  for (int e = tid; e < NPK; e += nt) {
+    int t = 0;
+    while (diag_start(NP, t + 1) <= e) ++t;
+    const int i = e - diag_start(NP, t), j = i + t;
+    double acc = 0.0;
+    for (int k = j; k < NP; ++k) acc += X[k * NP + i] * X[k * NP + j];
+    if (inv64) inv64[v * pstride + e] = acc;
+    if (inv32) inv32[v * pstride + e] = (float)acc;
+  }
+}
+
+static size_t setup_smem(int dim) {
+  const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1;
+  return sizeof(double) * (2 * NP * NP + NB * NB * dim + NPR * dim * NB + NB);
+}
+
+void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
+  const size_t smem = setup_smem(L.g.dim);
+  if (L.g.dim == 2) {
+    k_patch_setup<2><<<(unsigned)L.g.nverts, 64, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
+                                                             store32 ? L.inv32 : nullptr, L.pstride, st);
+  } else {
+    cudaFuncSetAttribute(k_patch_setup<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_patch_setup<3><<<(unsigned)L.g.nverts, 128, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
+                                                              store32 ? L.inv32 : nullptr, L.pstride, st);
+  }
+  count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// K4: y_v = A_v^-1 r|_v, one warp per patch; rows by lanes, diagonals in order
+// ---------------------------------------------------------------------------
+template <typename TF, typename TV, int DIM>
+__device__ __forceinline__ void patch_gemv(const TF* __restrict__ S, const TV* rs, int lane, TV (&acc)[(Sz<DIM>::NP + 31) / 32]) {
+  constexpr int NP = Sz<DIM>::NP, R = (NP + 31) / 32;
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = TV(0);
+#pragma unroll 3
+  for (int t = 0; t < NP; ++t) {
+    const TF* d = S + diag_start(NP, t);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < NP) {
+        if (i + t < NP) acc[k] += (TV)d[i] * rs[i + t];
+        if (t > 0 && i >= t) acc[k] += (TV)d[i - t] * rs[i - t];
+      }
+    }
+  }
+}
+
+template <typename TF, typename TV, int DIM>
+__global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restrict__ inv, int pstride,
+                                                     const TV* __restrict__ r, TV* __restrict__ out) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, R = (NP + 31) / 32;
+  __shared__ TV rsh[8][NP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + w; v < g.nverts; v += nwarps) {
+    int vx, vy, vz;
+    vertex_coords<DIM>(g, v, vx, vy, vz);
+    for (int i = lane; i < NP; i += 32) {
+      long long nd;
+      const bool ok = patch_node<DIM>(g, vx, vy, vz, i % NB, nd);
+      rsh[w][i] = ok ? r[(i / NB) * g.N + nd] : TV(0);
+    }
+    __syncwarp();
+    TV acc[R];
+    patch_gemv<TF, TV, DIM>(inv + v * pstride, rsh[w], lane, acc);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < NP) out[v * NP + i] = acc[k];
+    }
+    __syncwarp();
+  }
+}
+
+// z at node (c, i, j, k) = sum of the patch outputs of the vertices whose star contains it
+template <typename TV, int DIM>
+__global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N * DIM) return;
+  const int c = (int)(t / g.N);
+  const long long nd = t % g.N;
+  const int i = (int)(nd % g.nn[0]);
+  const long long rr = nd / g.nn[0];
+  const int j = (int)(rr % g.nn[1]);
+  const int k = (int)(rr / g.nn[1]);
+  if (on_boundary(g, i, j, k)) { z[t] = TV(0); return; }
+  // per axis: even node index -> its own vertex (offset 0); odd -> the two neighbours
+  int nva[3], vv[3][2], oo[3][2];
+  const int idx[3] = {i, j, k};
+  for (int a = 0; a < DIM; ++a) {
+    if ((idx[a] & 1) == 0) { nva[a] = 1; vv[a][0] = idx[a] >> 1; oo[a][0] = 1; }
+    else { nva[a] = 2; vv[a][0] = (idx[a] - 1) >> 1; oo[a][0] = 2; vv[a][1] = (idx[a] + 1) >> 1; oo[a][1] = 0; }
+  }
+  TV acc = TV(0);
+  const int nz = DIM == 3 ? nva[2] : 1;
+  for (int cz = 0; cz < nz; ++cz)
+    for (int cy = 0; cy < nva[1]; ++cy)
+      for (int cx = 0; cx < nva[0]; ++cx) {
+        const long long vid = (long long)vv[0][cx] +
+                              (long long)g.nv[0] * ((long long)vv[1][cy] + (DIM == 3 ? (long long)g.nv[1] * vv[2][cz] : 0));
+        const int o = oo[0][cx] + 3 * oo[1][cy] + (DIM == 3 ? 9 * oo[2][cz] : 0);
+        acc += out[vid * NP + c * NB + o];
+      }
+  z[t] = acc;
+}
+
+size_t patch_scratch_bytes(const LevelDev& L, int prec) {
+  return (size_t)L.g.nverts * L.np * (prec == PREC_F64 ? sizeof(double) : sizeof(float));
+}
+
+template <typename TF, typename TV, int DIM>
+static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z, void* scratch, cudaStream_t s,
+                        cudaEvent_t e0, cudaEvent_t e1) {
+  const long long warps = L.g.nverts;
+  const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
+  if (e0) cudaEventRecord(e0, s);
+  k_patch_apply<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
+  if (e1) cudaEventRecord(e1, s);
+  const long long tot = L.g.N * DIM;
+  k_patch_gather<TV, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z);
+  count_launch(2);
+}
+
+void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
+                  cudaEvent_t e0, cudaEvent_t e1) {
+  if (prec == PREC_F64) {
+    if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1);
+    else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1);
+  } else {
+    if (L.g.dim == 2) smooth_impl<float, float, 2>(L, L.inv32, r, z, scratch, s, e0, e1);
+    else smooth_impl<float, float, 3>(L, L.inv32, r, z, scratch, s, e0, e1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// local solves on coarse-cell interiors (robust transfer, Eq. (Ptilde)):
+// coarse cell K <-> fine vertex 2K+1, whose star is exactly int(K)
+// ---------------------------------------------------------------------------
+template <typename TF, typename TV, int DIM>
+__global__ void __launch_bounds__(256) k_interior_solve(Geom g, const TF* __restrict__ inv, int pstride,
+                                                        const TV* __restrict__ in, TV* __restrict__ out,
+                                                        int subtract) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, R = (NP + 31) / 32;
+  __shared__ TV rsh[8][NP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ncx = g.n[0] / 2, ncy = g.n[1] / 2, ncz = DIM == 3 ? g.n[2] / 2 : 1;
+  const long long ncoarse = (long long)ncx * ncy * ncz;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long K = (long long)blockIdx.x * (blockDim.x >> 5) + w; K < ncoarse; K += nwarps) {
+    const int kx = (int)(K % ncx), ky = (int)((K / ncx) % ncy), kz = DIM == 3 ? (int)(K / ((long long)ncx * ncy)) : 0;
+    const int vx = 2 * kx + 1, vy = 2 * ky + 1, vz = DIM == 3 ? 2 * kz + 1 : 0;
+    const long long v = (long long)vx + (long long)g.nv[0] * ((long long)vy + (long long)g.nv[1] * vz);
+    for (int i = lane; i < NP; i += 32) {
+      long long nd;
+      patch_node<DIM>(g, vx, vy, vz, i % NB, nd);  // always interior
+      rsh[w][i] = in[(i / NB) * g.N + nd];
+    }
+    __syncwarp();
+    TV acc[R];
+    patch_gemv<TF, TV, DIM>(inv + v * pstride, rsh[w], lane, acc);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < NP) {
+        long long nd;
+        patch_node<DIM>(g, vx, vy, vz, i % NB, nd);
+        TV* o = out + (i / NB) * g.N + nd;
+        *o = subtract ? *o - acc[k] : acc[k];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename TF, typename TV, int DIM>
+static void interior_impl(const LevelDev& L, const TF* inv, const void* in, void* out, int subtract, cudaStream_t s) {
+  long long nc = (long long)(L.g.n[0] / 2) * (L.g.n[1] / 2) * (DIM == 3 ? L.g.n[2] / 2 : 1);
+  if (!subtract) cudaMemsetAsync(out, 0, sizeof(TV) * L.g.N * DIM, s);
+  const unsigned blocks = (unsigned)std::min<long long>((nc + 7) / 8, 152LL * 16);
+  k_interior_solve<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)in, (TV*)out, subtract);
+  count_launch(1);
+}
+
+void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s) {
+  if (prec == PREC_F64) {
+    if (fine.g.dim == 2) interior_impl<double, double, 2>(fine, fine.inv64, in, out, subtract, s);
+    else interior_impl<double, double, 3>(fine, fine.inv64, in, out, subtract, s);
+  } else {
+    if (fine.g.dim == 2) interior_impl<float, float, 2>(fine, fine.inv32, in, out, subtract, s);
+    else interior_impl<float, float, 3>(fine, fine.inv32, in, out, subtract, s);
+  }
+}
+
+}  // namespace als

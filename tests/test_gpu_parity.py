@@ -1,0 +1,315 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative l2):
+  * FP64 operator applies, transfers, coarse solve: 1e-12 (spec bar);
+  * FP64 patch inverses / smoother / V-cycle: the oracle factors each patch with
+    LAPACK and the GPU with its own Cholesky, so the two inverses differ by
+    O(cond(A_v) eps); the tests use well-conditioned cases at 1e-12 and a
+    cond-scaled bound for the extreme-contrast cases;
+  * FP32 paths: 2e-5 (single-precision rounding of O(100)-term sums).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import context, dev, host, oracle, random_free, rel, sinker, torch  # noqa: F401
+from oracle.fem import Level
+from oracle.mg import star_dofs, all_vertices
+from oracle.stokes import StokesSolver
+
+pytestmark = pytest.mark.gpu
+
+from paper_2107_00820_gb300 import alstokes as A  # noqa: E402
+
+
+# --------------------------------------------------------------------------
+# a1: A_gamma apply
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n,levels", [(2, 8, 2), (2, (12, 6), 2), (3, 4, 2), (3, 6, 1)])
+@pytest.mark.parametrize("gamma", [0.0, 1e4])
+def test_apply_agamma_fp64(d, n, levels, gamma):
+    pb = sinker(d, n, levels, gamma, dr=1e6, seed=1)
+    ctx = context(pb)
+    H = oracle(pb, smoother="richardson", steps=1)
+    for lvl in range(levels):
+        lv = H.levels[lvl]
+        x = np.random.default_rng(lvl).standard_normal(lv.mesh.nu)   # boundary entries nonzero too
+        y = torch.zeros(lv.mesh.nu, dtype=torch.float64, device="cuda")
+        ctx.apply_agamma(dev(x), y, lvl)
+        assert rel(host(y), lv.A @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("d,n", [(2, 16), (3, 6)])
+def test_apply_agamma_fp32(d, n):
+    pb = sinker(d, n, 1, 1e3, dr=1e4, seed=2)
+    ctx = context(pb)
+    lv = Level(d, pb.n, pb.mu[0], pb.gamma)
+    x = np.random.default_rng(3).standard_normal(lv.mesh.nu)
+    y = torch.zeros(lv.mesh.nu, dtype=torch.float32, device="cuda")
+    ctx.apply_agamma(dev(x, torch.float32), y, 0, A.ALS_PREC_FP32)
+    assert rel(host(y), lv.A @ x.astype(np.float32).astype(np.float64)) <= 2e-5
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_apply_agamma_tensor_fp64(d):
+    """a2: anisotropic 4th-order tensor C at every point (Eq. (stokes-lin))."""
+    n = 4 if d == 3 else 8
+    rng = np.random.default_rng(7)
+    nm = 3 if d == 2 else 6
+    ncells, nq = n ** d, 3 ** d
+    M = rng.standard_normal((ncells, nq, nm, nm))
+    C = np.einsum("cqij,cqkj->cqik", M, M) + 0.5 * np.eye(nm)
+    iu = np.triu_indices(nm)
+    Cp = np.ascontiguousarray(C[:, :, iu[0], iu[1]])
+    mu_eff = np.ascontiguousarray(C[:, :, 0, 0] / 2)
+    from paper_2107_00820_gb300 import Context
+    ctx = Context(d, n, 1, [Cp], 10.0, mu_eff=[mu_eff])
+    lv = Level(d, n, Cp, 10.0, kind="tensor", mu_eff=mu_eff)
+    x = rng.standard_normal(lv.mesh.nu)
+    y = torch.zeros_like(dev(x))
+    ctx.apply_agamma(dev(x), y, 0)
+    assert rel(host(y), lv.A @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 4)])
+def test_apply_stokes_fp64(d, n):
+    pb = sinker(d, n, 2, 1e2, dr=1e4, seed=4)
+    ctx = context(pb)
+    s = StokesSolver(oracle(pb, smoother="richardson", steps=1))
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(s.nu)
+    p = rng.standard_normal(s.np_)
+    yu = torch.zeros(s.nu, dtype=torch.float64, device="cuda")
+    yp = torch.zeros(s.np_, dtype=torch.float64, device="cuda")
+    ctx.apply_stokes(dev(u), dev(p), yu, yp)
+    ref = s.matvec(np.concatenate([u, p]))
+    assert rel(host(yu), ref[: s.nu]) <= 1e-12
+    assert rel(host(yp), ref[s.nu:]) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# a3/a4: patch setup and the star smoother
+# --------------------------------------------------------------------------
+def _patch_cond(H, lvl, v):
+    lv = H.levels[lvl]
+    idx = star_dofs(lv.mesh, v)
+    Av = lv.A[idx][:, idx].toarray()
+    return np.linalg.cond(Av), idx, Av
+
+
+@pytest.mark.parametrize("d,n,gamma,dr", [(2, 8, 1.0, 1e2), (2, 8, 1e4, 1e6), (3, 4, 1e2, 1e4)])
+def test_patch_inverses_sampled(d, n, gamma, dr):
+    pb = sinker(d, n, 2, gamma, dr, seed=6)
+    ctx = context(pb)
+    H = oracle(pb, smoother="richardson", steps=1)
+    m = H.levels[1].mesh
+    verts = all_vertices(m)
+    rng = np.random.default_rng(0)
+    picks = list(rng.choice(len(verts), size=min(12, len(verts)), replace=False)) + [0, len(verts) - 1]
+    NB = 3 ** d
+    for vid in picks:
+        v = verts[vid]
+        cond, idx, Av = _patch_cond(H, 1, v)
+        full = ctx.patch_inverse(1, int(vid))
+        # rows of the GPU patch that correspond to free nodes, in oracle order
+        keep = []
+        for a in range(d):
+            for o in range(NB):
+                g = 2 * v + (np.array([o % 3, (o // 3) % 3, o // 9][:d]) - 1)
+                if np.all(g > 0) and np.all(g < np.array(m.nn) - 1):
+                    keep.append(a * NB + o)
+        keep = np.array(keep)
+        assert len(keep) == len(idx)
+        got = full[np.ix_(keep, keep)]
+        ref = np.linalg.inv(Av)
+        tol = max(1e-12, 20 * cond * 2.2e-16)
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (vid, cond)
+        # identity rows for absent nodes
+        other = np.setdiff1d(np.arange(d * NB), keep)
+        if len(other):
+            assert np.allclose(full[np.ix_(other, other)], np.eye(len(other)))
+
+
+@pytest.mark.parametrize("d,n", [(2, 16), (3, 4)])
+@pytest.mark.parametrize("prec", [A.ALS_PREC_FP64, A.ALS_PREC_FP32])
+def test_star_smoother(d, n, prec):
+    pb = sinker(d, n, 2, 1e2, dr=1e3, seed=8)
+    ctx = context(pb)
+    H = oracle(pb, smoother="richardson", steps=1)
+    lv = H.levels[1]
+    r = random_free(lv, 9)
+    dt = torch.float64 if prec == A.ALS_PREC_FP64 else torch.float32
+    z = torch.zeros(lv.mesh.nu, dtype=dt, device="cuda")
+    ctx.star_smooth(1, dev(r, dt), z, prec)
+    ref = H.patches[1].apply(r)
+    assert rel(host(z), ref) <= (1e-11 if prec == A.ALS_PREC_FP64 else 1e-4)
+
+
+# --------------------------------------------------------------------------
+# a5/a6: robust prolongation and restriction, standard transfers
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 4)])
+@pytest.mark.parametrize("transfer", [A.ALS_TRANSFER_ROBUST, A.ALS_TRANSFER_STANDARD])
+def test_transfers_fp64(d, n, transfer):
+    pb = sinker(d, n, 2, 1e2, dr=1e3, seed=10)
+    ctx = context(pb, transfer=transfer)
+    H = oracle(pb, smoother="richardson", steps=1, transfer="robust" if transfer == 0 else "standard")
+    c, f = H.levels[0], H.levels[1]
+    xc = random_free(c, 11)
+    xf = torch.zeros(f.mesh.nu, dtype=torch.float64, device="cuda")
+    ctx.prolong(1, dev(xc), xf)
+    assert rel(host(xf), H.P[1] @ xc) <= 1e-11
+    rf = random_free(f, 12)
+    rc = torch.zeros(c.mesh.nu, dtype=torch.float64, device="cuda")
+    ctx.restrict(1, dev(rf), rc)
+    assert rel(host(rc), H.P[1].T @ rf) <= 1e-11
+
+
+# --------------------------------------------------------------------------
+# a7: coarse solve
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n", [(2, 4), (2, 8), (3, 2), (3, 4)])
+def test_coarse_solve(d, n):
+    pb = sinker(d, n, 1, 1e2, dr=1e4, seed=13)
+    ctx = context(pb)
+    H = oracle(pb, smoother="richardson", steps=1)
+    b = random_free(H.levels[0], 14)
+    x = torch.zeros_like(dev(b))
+    ctx.coarse_solve(dev(b), x)
+    ref = H.coarse_solve(b)
+    cond = np.linalg.cond(H.levels[0].A.toarray())
+    assert rel(host(x), ref) <= max(1e-12, 10 * cond * 2.2e-16)
+
+
+# --------------------------------------------------------------------------
+# a8: V-cycle
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("smoother", [A.ALS_SMOOTH_RICHARDSON, A.ALS_SMOOTH_GMRES])
+@pytest.mark.parametrize("d,n,levels", [(2, 16, 3), (3, 8, 3)])
+def test_vcycle_fp64(smoother, d, n, levels):
+    pb = sinker(d, n, levels, 1.0, dr=1e2, seed=15)
+    ctx = context(pb, smoother=smoother, sweeps=2)
+    H = oracle(pb, smoother="gmres" if smoother == A.ALS_SMOOTH_GMRES else "richardson", steps=2)
+    b = random_free(H.levels[-1], 16)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.vcycle(b)) <= 1e-12
+
+
+def _max_patch_cond(H, lvl, count=40):
+    m = H.levels[lvl].mesh
+    verts = all_vertices(m)
+    picks = np.random.default_rng(0).choice(len(verts), size=min(count, len(verts)), replace=False)
+    return max(_patch_cond(H, lvl, verts[i])[0] for i in picks)
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, 32, 4), (3, 8, 3)])
+def test_vcycle_extreme_contrast(d, n, levels):
+    """gamma = 1e4, DR = 1e8: the patch matrices are ill-conditioned, so the FP64
+    cycle matches the oracle to a cond-scaled bound, and both cycles must reduce
+    the residual equally well; the FP32 cycle must still be a useful smoother."""
+    pb = sinker(d, n, levels, 1e4, dr=1e8, seed=17)
+    ctx = context(pb, sweeps=3)
+    H = oracle(pb, steps=3)
+    A_f = H.levels[-1].A
+    b = random_free(H.levels[-1], 18)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    ref = H.vcycle(b)
+    cond = _max_patch_cond(H, levels - 1)
+    assert rel(host(x), ref) <= max(1e-10, 100 * cond * 2.2e-16), cond
+    r_ref = np.linalg.norm(b - A_f @ ref) / np.linalg.norm(b)
+    r_gpu = np.linalg.norm(b - A_f @ host(x)) / np.linalg.norm(b)
+    assert abs(r_gpu - r_ref) <= 0.01 * r_ref
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, 32, 4), (3, 8, 3)])
+def test_vcycle_fp32_within_its_precision_range(d, n, levels):
+    """The FP32 cycle evaluates gamma div u and the patch inverses in single
+    precision; with W = M_p its relative error grows like eps32 * gamma / mu_min.
+    At gamma / mu_min = 1e5 (gamma 10, DR 1e8) it must smooth as well as FP64."""
+    pb = sinker(d, n, levels, 10.0, dr=1e8, seed=17)
+    ctx = context(pb, sweeps=3)
+    H = oracle(pb, steps=3)
+    A_f = H.levels[-1].A
+    b = random_free(H.levels[-1], 18)
+    ref = H.vcycle(b)
+    r_ref = np.linalg.norm(b - A_f @ ref) / np.linalg.norm(b)
+    x32 = torch.zeros(b.shape[0], dtype=torch.float32, device="cuda")
+    ctx.vcycle(dev(b, torch.float32), x32, A.ALS_PREC_FP32)
+    r32 = np.linalg.norm(b - A_f @ host(x32)) / np.linalg.norm(b)
+    assert r32 <= 1.5 * r_ref + 1e-4, (r32, r_ref)
+
+
+# --------------------------------------------------------------------------
+# a9/a10: full solve
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n,levels,gamma,dr", [(2, 16, 3, 1e2, 1e4), (3, 8, 2, 1e3, 1e4)])
+def test_solve_fp64_matches_oracle(d, n, levels, gamma, dr):
+    pb = sinker(d, n, levels, gamma, dr, seed=19)
+    ctx = context(pb, rtol=1e-8)
+    s = StokesSolver(oracle(pb))
+    uo, po, its, hist = s.solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged == 1
+    assert abs(info.iterations - its) <= 0, (info.iterations, its)
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
+
+
+def test_solve_manufactured_config():
+    """Smallest configuration: 2D 16x16, mu = 1, gamma = 1e4, 2 levels, 2 sweeps, rtol 1e-10."""
+    from synthetic.problems import manufactured_problem
+    pb = manufactured_problem(16, 2, 1e4)
+    ctx = context(pb, sweeps=2, rtol=1e-10)
+    s = StokesSolver(oracle(pb, steps=2))
+    uo, po, its, _ = s.solve(pb.f, pb.u_bc, rtol=1e-10)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its
+    assert rel(u, uo) <= 1e-9
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, 32, 4), (3, 8, 2)])
+def test_solve_mixed_precision(d, n, levels):
+    pb = sinker(d, n, levels, 1e3, dr=1e6, seed=21)
+    ref = context(pb, rtol=1e-8)
+    mixed = context(pb, rtol=1e-8, mode=A.ALS_MODE_MIXED)
+    s = StokesSolver(oracle(pb))
+    uo, po, its, _ = s.solve(pb.f, pb.u_bc, rtol=1e-10)
+    u, p, info = mixed.solve(pb.f, pb.u_bc)
+    _, _, info64 = ref.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations <= info64.iterations + 2
+    assert rel(u, uo) <= 1e-7 * 10 and rel(p, po) <= 1e-6 * 10
+
+
+def test_solve_device_buffers():
+    pb = sinker(2, 16, 3, 1e2, dr=1e4, seed=23)
+    ctx = context(pb)
+    u_h, p_h, _ = ctx.solve(pb.f, pb.u_bc)
+    u = torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda")
+    p = torch.zeros(ctx.npres(), dtype=torch.float64, device="cuda")
+    ctx.solve(dev(pb.f), dev(pb.u_bc), None, u, p)
+    # deterministic accumulation order: host and device buffers give identical bits
+    assert np.array_equal(host(u), u_h) and np.array_equal(host(p), p_h)
+    u2, p2, _ = ctx.solve(pb.f, pb.u_bc)
+    assert np.array_equal(u2, u_h) and np.array_equal(p2, p_h)
+
+
+# --------------------------------------------------------------------------
+# errors
+# --------------------------------------------------------------------------
+def test_invalid_arguments_and_non_spd():
+    from paper_2107_00820_gb300 import ALSError, Context
+    pb = sinker(2, 8, 2, 1.0, dr=1e2)
+    with pytest.raises(ALSError) as e:
+        Context(2, 6, 3, pb.mu, 1.0)            # 6 not divisible by 4
+    assert e.value.status == A.ALS_EINVAL
+    with pytest.raises(ALSError) as e:
+        Context(1, 8, 2, pb.mu, 1.0)
+    assert e.value.status == A.ALS_EINVAL
+    bad = [-m for m in pb.mu]                    # negative viscosity: patch matrices not SPD
+    with pytest.raises(ALSError) as e:
+        Context(2, 8, 2, bad, 0.0)
+    assert e.value.status == A.ALS_ENOTSPD
+    ctx = context(pb)
+    with pytest.raises(ALSError):
+        ctx.apply_agamma(torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda"),
+                         torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda"), level=7)
