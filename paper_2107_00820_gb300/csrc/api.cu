@@ -652,12 +652,18 @@ als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) {
   if (!c || !total_ms || !launches) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "profile read");
   double tot = 0.0;
+  long long n = 0;
   for (auto& pr : c->prof.pairs) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->prof.pool[pr.first], c->prof.pool[pr.second]) == cudaSuccess) tot += ms;
+    if (cudaEventElapsedTime(&ms, c->prof.pool[pr.first], c->prof.pool[pr.second]) == cudaSuccess) {
+      tot += ms;
+      ++n;
+    } else {
+      cudaGetLastError();  // an unrecorded pair is skipped, not left as a sticky error
+    }
   }
   *total_ms = tot;
-  *launches = (long long)c->prof.pairs.size();
+  *launches = n;
   c->prof.pairs.clear();
   c->prof.next = 0;
   return ALS_OK;

@@ -85,12 +85,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int k, co
   }
 }
 
-__global__ void k_multidot_final(int k, int nb, const double* __restrict__ partial, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= k) return;
+// out[j] = sum_b partial[b*k + j]: one block per j, a fixed reduction tree
+__global__ void __launch_bounds__(RED_THREADS) k_multidot_final(int k, int nb, const double* __restrict__ partial,
+                                                                double* __restrict__ out) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int j = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(long long)b * k + j];
-  out[j] = s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(long long)b * k + j];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[j] = s;
 }
 
 template <typename T>
@@ -145,7 +148,7 @@ void vec_multidot(int prec, long long n, int k, const void* V, long long ld, con
     k_multidot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial);
   else
     k_multidot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial);
-  k_multidot_final<<<(k + 127) / 128, 128, 0, s>>>(k, RED_BLOCKS, partial, out);
+  k_multidot_final<<<k, RED_THREADS, 0, s>>>(k, RED_BLOCKS, partial, out);
   count_launch(2);
 }
 

@@ -86,79 +86,304 @@ __device__ __forceinline__ bool colour_cell(const Colour& col, long long t, int&
   return true;
 }
 
-template <typename T, int DIM, bool RAW>
-__device__ __forceinline__ void load_cell(const Geom& g, const T* __restrict__ x, int cx, int cy, int cz,
-                                          T (&u)[DIM][Sz<DIM>::NB]) {
-#pragma unroll
-  for (int a = 0; a < Sz<DIM>::NB; ++a) {
-    const int i = 2 * cx + a % 3, j = 2 * cy + (a / 3) % 3, k = (DIM == 3) ? 2 * cz + a / 9 : 0;
-    const bool bnd = !RAW && on_boundary(g, i, j, k);
-    const long long nd = node_id(g, i, j, k);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) u[c][a] = bnd ? T(0) : x[c * g.N + nd];
-  }
-}
-
-template <typename T, int DIM, bool RAW>
-__device__ __forceinline__ void scatter_cell(const Geom& g, T* __restrict__ y, int cx, int cy, int cz,
-                                             const T (&yl)[DIM][Sz<DIM>::NB]) {
-#pragma unroll
-  for (int a = 0; a < Sz<DIM>::NB; ++a) {
-    const int i = 2 * cx + a % 3, j = 2 * cy + (a / 3) % 3, k = (DIM == 3) ? 2 * cz + a / 9 : 0;
-    if (!RAW && on_boundary(g, i, j, k)) continue;
-    const long long nd = node_id(g, i, j, k);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) y[c * g.N + nd] += yl[c][a];
-  }
-}
-
+// One warp evaluates one cell (3D: 27 lanes = 27 nodes = 27 Gauss points) or
+// three cells (2D: 9 lanes each).  The three 1D contractions of the sum
+// factorisation run lane-parallel through shared memory, the divergence
+// moments are a warp (3D) or lane-group (2D) reduction, and the isotropic AL /
+// pressure part of the stress is formed at every point before the transposed
+// contractions take the fluxes back to the nodes.
 template <typename T, int DIM, bool TENSOR, int MODE>
-__global__ void __launch_bounds__(128) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
+__global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
                                                T* __restrict__ y, const T* __restrict__ coef,
                                                const T* __restrict__ p_in, T* __restrict__ p_out,
                                                long long vstride) {
   constexpr int NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
-  constexpr bool RAW = (MODE & OP_RAW) != 0;
-  x += blockIdx.y * vstride;
-  y += blockIdx.y * vstride;
+  constexpr int CPW = DIM == 2 ? 3 : 1;        // cells per warp
   constexpr int NCQ = TENSOR ? Sz<DIM>::NC : 1;
+  constexpr bool RAW = (MODE & OP_RAW) != 0;
+  constexpr bool VISC = (MODE & OP_VISC) != 0;
   constexpr bool NEED_U = (MODE & (OP_VISC | OP_AL | OP_B)) != 0;
   constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
-  int cx, cy, cz;
-  if (!colour_cell(col, (long long)blockIdx.x * blockDim.x + threadIdx.x, cx, cy, cz)) return;
+  __shared__ T sh[8][2][9][27];
+  x += blockIdx.y * vstride;
+  y += blockIdx.y * vstride;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int grp = lane / NB < CPW ? lane / NB : 0;
+  const bool lane_ok = lane < CPW * NB;
+  const int l = lane_ok ? lane - grp * NB : 0;
+  const int base = grp * NB;
+  T (*SA)[27] = sh[w][0];
+  T (*SB)[27] = sh[w][1];
+  const long long t = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * CPW + grp;
+  int cx = 0, cy = 0, cz = 0;
+  const bool act = lane_ok && colour_cell(col, t, cx, cy, cz);
   const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
-  T u[DIM][NB];
-  if constexpr (NEED_U) load_cell<T, DIM, RAW>(g, x, cx, cy, cz, u);
-  else {
+  const int i0 = l % 3, i1 = (l / 3) % 3, i2 = DIM == 3 ? l / 9 : 0;
+  const int ni = 2 * cx + i0, nj = 2 * cy + i1, nk = DIM == 3 ? 2 * cz + i2 : 0;
+  const long long nd = node_id(g, ni, nj, nk);
+  const bool bnd = on_boundary(g, ni, nj, nk);
+
+  T grad[DIM][DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) grad[c][k] = T(0);
+
+  if constexpr (NEED_U) {
+    // stage 1: nodal values (Dirichlet columns masked unless RAW)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const T v = (act && (RAW || !bnd)) ? x[c * g.N + nd] : T(0);
+      if (lane_ok) SA[c][base + l] = v;
+    }
+    __syncwarp();
+    if constexpr (DIM == 3) {
+      // stage 2 (x): lane = (qx, ay, az): B_x u, D_x u
+      if (lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T t0 = T(0), t1 = T(0);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const T v = SA[c][a + 3 * i1 + 9 * i2];
+            t0 += Ref<T>::B(i0, a) * v;
+            t1 += Ref<T>::D(i0, a) * v;
+          }
+          SB[c][l] = t0;
+          SB[3 + c][l] = t1;
+        }
+      }
+      __syncwarp();
+      // stage 3 (y): lane = (qx, qy, az): B_x B_y u, B_x D_y u, D_x B_y u
+      if (lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const T v0 = SB[c][i0 + 3 * b + 9 * i2], v1 = SB[3 + c][i0 + 3 * b + 9 * i2];
+            a0 += Ref<T>::B(i1, b) * v0;
+            a1 += Ref<T>::D(i1, b) * v0;
+            a2 += Ref<T>::B(i1, b) * v1;
+          }
+          SA[c][l] = a0;
+          SA[3 + c][l] = a1;
+          SA[6 + c][l] = a2;
+        }
+      }
+      __syncwarp();
+      // stage 4 (z): lane = (qx, qy, qz): the gradient at this point
+      if (lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int idx = i0 + 3 * i1 + 9 * k;
+            gx += Ref<T>::B(i2, k) * SA[6 + c][idx];
+            gy += Ref<T>::B(i2, k) * SA[3 + c][idx];
+            gz += Ref<T>::D(i2, k) * SA[c][idx];
+          }
+          grad[c][0] = gx * cc.s[0];
+          grad[c][1] = gy * cc.s[1];
+          grad[c][2] = gz * cc.s[2];
+        }
+      }
+    } else {
+      // stage 2 (x): lane = (qx, ay): B_x u, D_x u
+      if (lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          T t0 = T(0), t1 = T(0);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const T v = SA[c][base + a + 3 * i1];
+            t0 += Ref<T>::B(i0, a) * v;
+            t1 += Ref<T>::D(i0, a) * v;
+          }
+          SB[c][base + l] = t0;
+          SB[2 + c][base + l] = t1;
+        }
+      }
+      __syncwarp();
+      // stage 3 (y): lane = (qx, qy)
+      if (lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          T gx = T(0), gy = T(0);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            gx += Ref<T>::B(i1, b) * SB[2 + c][base + i0 + 3 * b];
+            gy += Ref<T>::D(i1, b) * SB[c][base + i0 + 3 * b];
+          }
+          grad[c][0] = gx * cc.s[0];
+          grad[c][1] = gy * cc.s[1];
+        }
+      }
+    }
+  }
+
+  // point weight, pressure basis at this point
+  const T wq = cc.wdet * Ref<T>::W(i0) * Ref<T>::W(i1) * (DIM == 3 ? Ref<T>::W(i2) : T(1));
+  T psi[NPR];
+  psi[0] = T(1);
+  psi[1] = Ref<T>::G(i0);
+  psi[2] = Ref<T>::G(i1);
+  if constexpr (DIM == 3) psi[3] = Ref<T>::G(i2);
+
+  // divergence moments m_p = (psi_p, div u)_K
+  T m[NPR];
+#pragma unroll
+  for (int p = 0; p < NPR; ++p) m[p] = T(0);
+  if constexpr ((MODE & (OP_AL | OP_B)) != 0) {
+    T dv = T(0);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dv += grad[c][c];
+    dv = lane_ok ? wq * dv : T(0);
+    if constexpr (DIM == 3) {
+#pragma unroll
+      for (int p = 0; p < NPR; ++p) {
+        T v = dv * psi[p];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        m[p] = v;
+      }
+    } else {
+      __syncwarp();
+      if (lane_ok) {
+#pragma unroll
+        for (int p = 0; p < NPR; ++p) SB[p][base + l] = dv * psi[p];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int p = 0; p < NPR; ++p) {
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v += SB[p][base + q];
+        m[p] = v;
+      }
+    }
+    if constexpr ((MODE & OP_B) != 0) {
+      if (act && l < NPR) p_out[cell * NPR + l] = -m[l];
+    }
+  }
+  if constexpr (NEED_FLUX) {
+  // isotropic part of the stress: gamma Pi div u - p_h
+  T pi[NPR];
+#pragma unroll
+  for (int p = 0; p < NPR; ++p) {
+    pi[p] = T(0);
+    if constexpr ((MODE & OP_AL) != 0) pi[p] += cc.gamma * m[p] * (p == 0 ? cc.inv_m0 : cc.inv_m1);
+    if constexpr ((MODE & OP_BT) != 0) pi[p] -= act ? p_in[cell * NPR + p] : T(0);
+  }
+  T iso = T(0);
+#pragma unroll
+  for (int p = 0; p < NPR; ++p) iso += pi[p] * psi[p];
+  T sg[DIM][DIM];
+  if constexpr (VISC) {
+    if (act) stress<T, DIM, TENSOR>(coef + (cell * NB + l) * NCQ, grad, iso, sg);
+    else {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) sg[c][k] = T(0);
+    }
+  } else {
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
 #pragma unroll
-      for (int a = 0; a < NB; ++a) u[c][a] = T(0);
+      for (int k = 0; k < DIM; ++k) sg[c][k] = (c == k) ? iso : T(0);
   }
-  T pi[NPR];
+  __syncwarp();
+  // fluxes F[c][k] = |J| w_q sigma_ck (2/h_k)
+  if (lane_ok) {
 #pragma unroll
-  for (int p = 0; p < NPR; ++p) pi[p] = T(0);
-  if constexpr ((MODE & (OP_AL | OP_B)) != 0) {
-    T m[NPR];
-    div_moments<T, DIM>(u, cc.s, cc.wdet, m);
-    if constexpr ((MODE & OP_B) != 0) {
+    for (int c = 0; c < DIM; ++c)
 #pragma unroll
-      for (int p = 0; p < NPR; ++p) p_out[cell * NPR + p] = -m[p];
+      for (int k = 0; k < DIM; ++k) SA[DIM * c + k][base + l] = wq * sg[c][k] * cc.s[k];
+  }
+  __syncwarp();
+  T yl[DIM];
+  if constexpr (DIM == 3) {
+    // stage 5 (z^T): lane = (qx, qy, az)
+    if (lane_ok) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T ge = T(0), gb = T(0), ga = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int idx = i0 + 3 * i1 + 9 * q;
+          ge += Ref<T>::B(q, i2) * SA[3 * c + 0][idx];
+          gb += Ref<T>::B(q, i2) * SA[3 * c + 1][idx];
+          ga += Ref<T>::D(q, i2) * SA[3 * c + 2][idx];
+        }
+        SB[c][l] = ge;
+        SB[3 + c][l] = gb;
+        SB[6 + c][l] = ga;
+      }
     }
-    if constexpr ((MODE & OP_AL) != 0) {
+    __syncwarp();
+    // stage 6 (y^T): lane = (qx, ay, az)
+    if (lane_ok) {
 #pragma unroll
-      for (int p = 0; p < NPR; ++p) pi[p] += cc.gamma * m[p] * (p == 0 ? cc.inv_m0 : cc.inv_m1);
+      for (int c = 0; c < 3; ++c) {
+        T p0 = T(0), p1 = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int idx = i0 + 3 * q + 9 * i2;
+          p0 += Ref<T>::B(q, i1) * SB[6 + c][idx] + Ref<T>::D(q, i1) * SB[3 + c][idx];
+          p1 += Ref<T>::B(q, i1) * SB[c][idx];
+        }
+        SA[c][l] = p0;
+        SA[3 + c][l] = p1;
+      }
+    }
+    __syncwarp();
+    // stage 7 (x^T): lane = (ax, ay, az)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int idx = q + 3 * i1 + 9 * i2;
+        v += Ref<T>::B(q, i0) * SA[c][idx] + Ref<T>::D(q, i0) * SA[3 + c][idx];
+      }
+      yl[c] = v;
+    }
+  } else {
+    // stage 5 (y^T): lane = (qx, ay)
+    if (lane_ok) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T p0 = T(0), p1 = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int idx = base + i0 + 3 * q;
+          p0 += Ref<T>::D(q, i1) * SA[2 * c + 1][idx];
+          p1 += Ref<T>::B(q, i1) * SA[2 * c + 0][idx];
+        }
+        SB[c][base + l] = p0;
+        SB[2 + c][base + l] = p1;
+      }
+    }
+    __syncwarp();
+    // stage 6 (x^T): lane = (ax, ay)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int idx = base + q + 3 * i1;
+        v += Ref<T>::B(q, i0) * SB[c][idx] + Ref<T>::D(q, i0) * SB[2 + c][idx];
+      }
+      yl[c] = v;
     }
   }
-  if constexpr ((MODE & OP_BT) != 0) {
+  if (act && (RAW || !bnd)) {
 #pragma unroll
-    for (int p = 0; p < NPR; ++p) pi[p] -= p_in[cell * NPR + p];
+    for (int c = 0; c < DIM; ++c) y[c * g.N + nd] += yl[c];
   }
-  if constexpr (NEED_FLUX) {
-    T yl[DIM][NB];
-    cell_flux_apply<T, DIM, TENSOR, (MODE & OP_VISC) != 0>(u, coef + cell * NB * NCQ, cc.s, cc.wdet, pi, yl);
-    scatter_cell<T, DIM, RAW>(g, y, cx, cy, cz, yl);
-  }
+  }  // NEED_FLUX
 }
 
 // y_D = x_D (identity rows) when keep_bnd, else 0; interior rows zeroed.
@@ -197,8 +422,9 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
     const int ncol = NEED_FLUX ? (1 << DIM) : 1;   // B u alone is cell-local: one launch
     for (int colour = 0; colour < ncol; ++colour) {
       const Colour col = NEED_FLUX ? make_colour(g, colour) : all_cells(g);
-      dim3 grid((unsigned)((col.count + 127) / 128), nv);
-      k_apply<T, DIM, TENSOR, MODE><<<grid, 128, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
+      constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);   // cells per 256-thread block
+      dim3 grid((unsigned)((col.count + CPB - 1) / CPB), nv);
+      k_apply<T, DIM, TENSOR, MODE><<<grid, 256, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
                                                          (const T*)p_in, (T*)p_out, vstride);
     }
     count_launch((NEED_FLUX ? 1 : 0) + ncol);

@@ -298,9 +298,10 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
                         cudaEvent_t e0, cudaEvent_t e1) {
   const long long warps = L.g.nverts;
   const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
-  if (e0) cudaEventRecord(e0, s);
+  // External records become event-record nodes when the stream is being captured
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   k_patch_apply<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
-  if (e1) cudaEventRecord(e1, s);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   const long long tot = L.g.N * DIM;
   k_patch_gather<TV, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z);
   count_launch(2);
