@@ -178,6 +178,35 @@ als_status als_profile_read(als_ctx* ctx, double* total_ms, long long* launches)
  * captured V-cycle counts its kernel nodes). */
 long long als_kernel_launches(void);
 
+/* Allocation-free star smoother.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they
+ * smooth -- code running inside a stream capture in global mode (where
+ * cudaMalloc is not allowed), real-time loops that reserve all device memory
+ * up front, or plugins whose host framework owns the allocator.  It computes
+ * the same z = sum_v I_v A_v^-1 I_v^T r as als_star_smooth, but without a
+ * context: the caller passes the mesh, the packed patch inverses, r and z
+ * (all device memory it already owns), and the per-patch scratch the
+ * smoother needs between its two kernels is a fixed device array of
+ * ALS_STATIC_SCRATCH_BYTES inside this library.
+ *   dim, n : mesh of the level (n[k] cells per direction, n[2] ignored in 2D)
+ *   prec   : ALS_PREC_FP64 (double inv/r/z) or ALS_PREC_FP32 (float)
+ *   inv    : device, one block per vertex (vertex index x-fastest), each block
+ *            the upper triangle of the (d*3^d)^2 inverse stored by diagonals,
+ *            entries (i, i+t) for t = 0.., i = 0..np-1-t, padded to a multiple
+ *            of 4 entries; patch dof order as in als_patch_inverse
+ *   r, z   : device velocity vectors of the level (boundary entries of z = 0)
+ *   stream : cudaStream_t the two kernels are queued on; the call returns
+ *            without waiting for them
+ * Returns ALS_EINVAL if (n+1)^d * d*3^d * sizeof(element) exceeds
+ * ALS_STATIC_SCRATCH_BYTES (32 MiB: e.g. up to 32^3 hexes in FP64, 45^3 in
+ * FP32).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Nothing is allocated and nothing needs to start at zero, but every call
+ * shares the one array: calls that overlap on the GPU race. */
+#define ALS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+als_status als_star_smooth_static(int dim, const int* n, int prec, const void* inv, const void* r, void* z,
+                                  void* stream);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char* als_last_error(const als_ctx* ctx);
 

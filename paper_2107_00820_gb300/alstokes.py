@@ -65,6 +65,7 @@ SIGNATURES = {
     "als_profile": (c_int, [c_void_p, c_int]),
     "als_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
     "als_kernel_launches": (c_longlong, []),
+    "als_star_smooth_static": (c_int, [c_int, POINTER(c_int), c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _LIB = None
@@ -293,3 +294,12 @@ def als_solve(ctx, f_qp, u_bc, r2, u, p):
 
 def als_kernel_launches():
     return int(load().als_kernel_launches())
+
+
+def als_star_smooth_static(dim, n, prec, inv, r, z, stream=None):
+    """Allocation-free smoother (scratch in a fixed device array); queued on `stream`."""
+    n = (list(n) + [1, 1, 1])[:3]
+    st = load().als_star_smooth_static(dim, (c_int * 3)(*n), prec, _ptr(inv), _ptr(r), _ptr(z),
+                                       c_void_p(stream) if stream else None)
+    if st != ALS_OK:
+        raise ALSError(st, "als_star_smooth_static failed")
