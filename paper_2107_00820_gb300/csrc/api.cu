@@ -181,6 +181,7 @@ als_status alloc_work(als_ctx* c, MGWork& w, int prec) {
     }
   }
   ALS_TRY(dalloc(c, &w.partial, multidot_partial_doubles(std::max(s + 1, 8))));
+  cudaMemsetAsync(w.partial, 0, sizeof(double) * multidot_partial_doubles(std::max(s + 1, 8)), c->stream);
   return ALS_OK;
 }
 
@@ -264,11 +265,9 @@ void smooth(als_ctx* c, MGWork& w, int l) {
     patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1);
     op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, Zj, Vn, nullptr, nullptr, s);
     vec_multidot(prec, len, j + 1, w.V[l], len, Vn, hcol, w.partial, s);
-    vec_multiaxpy(prec, len, j + 1, w.V[l], len, hcol, Vn, s, -1.0);
-    vec_multidot(prec, len, 1, Vn, len, Vn, sm + sl.nrm2, w.partial, s);
-    dev_hess_finish(j, hcol, nullptr, sm + sl.nrm2, s);
-    vec_scale_dev(prec, len, nullptr, hcol + j + 1, Vn, Vn, s);
-    dev_givens_step(j, sm + sl.H, sl.ldh, sm + sl.cs, sm + sl.sn, sm + sl.g, sm + sl.res, s);
+    vec_multiaxpy_norm(prec, len, j + 1, w.V[l], len, hcol, -1.0, Vn, w.partial, sm + sl.nrm2, s);
+    vec_scale_dev(prec, len, nullptr, sm + sl.nrm2, Vn, Vn, s, 1);
+    dev_hess_givens(j, sm + sl.H, sl.ldh, nullptr, sm + sl.nrm2, sm + sl.cs, sm + sl.sn, sm + sl.g, sm + sl.res, s);
   }
   dev_backsolve(steps, sm + sl.H, sl.ldh, sm + sl.g, sm + sl.y, s);
   vec_multiaxpy(prec, len, steps, w.Z[l], len, sm + sl.y, w.x[l], s, 1.0);
@@ -409,6 +408,7 @@ als_status alloc_solve(als_ctx* c, int maxit) {
   ALS_TRY(dalloc(c, &c->h2, maxit + 1));
   ALS_TRY(dalloc(c, &c->nrm2, 1));
   ALS_TRY(dalloc(c, &c->partial, multidot_partial_doubles(maxit + 1)));
+  cudaMemsetAsync(c->partial, 0, sizeof(double) * multidot_partial_doubles(maxit + 1), c->stream);
   ALS_TRY(dalloc(c, &c->f_dev, (size_t)F.g.ncells * (c->dim == 2 ? 9 : 27) * c->dim));
   ALS_TRY(dalloc(c, &c->ubc_dev, c->nu));
   ALS_TRY(dalloc(c, &c->r2_dev, c->np));
@@ -578,11 +578,17 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     Lv.ncoef = Lv.tensor ? NC : 1;
     Lv.np = c->dim * NB;
     Lv.pstride = packed_stride(Lv.np);
+    Lv.status = c->st;
     const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
     ALS_TRY(dalloc(c, &Lv.coef64, ncq));
     ALS_TRY(dalloc(c, &Lv.coef32, ncq));
     if (Lv.tensor) ALS_TRY(dalloc(c, &Lv.mu64, (size_t)Lv.g.ncells * NB));
     else Lv.mu64 = Lv.coef64;
+    {
+      double* e = nullptr;
+      ALS_TRY(dalloc(c, &e, (size_t)Lv.g.ncells * NB * c->dim));
+      Lv.ebuf = e;
+    }
     if (l > 0) {
       ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
       ALS_TRY(dalloc(c, &Lv.inv32, (size_t)Lv.g.nverts * Lv.pstride));
@@ -832,11 +838,9 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
     vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, hcol, c->partial, s);
     vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, hcol, w, s, -1.0);
     vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, c->h2, c->partial, s);
-    vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, c->h2, w, s, -1.0);
-    vec_multidot(PREC_F64, c->n, 1, w, c->n, w, c->nrm2, c->partial, s);
-    dev_hess_finish(k, hcol, c->h2, c->nrm2, s);
-    vec_scale_dev(PREC_F64, c->n, nullptr, hcol + k + 1, w, w, s);
-    dev_givens_step(k, c->H, ldh, c->cs, c->sn, c->g, c->res, s);
+    vec_multiaxpy_norm(PREC_F64, c->n, k + 1, c->V, c->n, c->h2, -1.0, w, c->partial, c->nrm2, s);
+    vec_scale_dev(PREC_F64, c->n, nullptr, c->nrm2, w, w, s, 1);
+    dev_hess_givens(k, c->H, ldh, c->h2, c->nrm2, c->cs, c->sn, c->g, c->res, s);
     cudaMemcpyAsync(c->host_res, c->res, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "fgmres");
     its = k + 1;

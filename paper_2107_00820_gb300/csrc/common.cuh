@@ -81,4 +81,30 @@ __host__ __device__ constexpr int packed_size(int np) { return np * (np + 1) / 2
 // per-patch stride, rounded to a multiple of 4 entries (16-byte aligned rows)
 __host__ __device__ constexpr int packed_stride(int np) { return (packed_size(np) + 3) & ~3; }
 
+// "Block-packed" storage of the same symmetric NP x NP matrix (NP = 9 NBR), used
+// for the FP32 inverses: 9x9 blocks (I, J), I <= J, numbered off-diagonal blocks
+// first (row-major over I < J), then the NBR diagonal blocks.  Element e of a
+// block is r*9 + c (off-diagonal) or the row-major index of (r, c), r <= c, in
+// the 45-entry upper triangle (diagonal).  Elements e < 45 of all NBP blocks are
+// stored first, interleaved by block (e * NBP + b), then elements 45..80 of the
+// off-diagonal blocks (45 NBP + (e - 45) NOFF + b): thread b of a patch reads
+// consecutive words.  The total is still NP (NP + 1) / 2 entries.
+struct BlockLayout {
+  int nbr, nbp, noff;
+  __host__ __device__ constexpr explicit BlockLayout(int np)
+      : nbr(np / 9), nbp((np / 9) * (np / 9 + 1) / 2), noff((np / 9) * (np / 9 - 1) / 2) {}
+  __host__ __device__ constexpr int offdiag(int I, int J) const {  // I < J
+    return I * (nbr - 1) - (I * (I - 1)) / 2 + (J - I - 1);
+  }
+  __host__ __device__ constexpr int slot(int e, int b) const {
+    return e < 45 ? e * nbp + b : 45 * nbp + (e - 45) * noff + b;
+  }
+  // position of entry (i, j), i <= j
+  __host__ __device__ constexpr int index(int i, int j) const {
+    const int I = i / 9, r = i % 9, J = j / 9, c = j % 9;
+    if (I == J) return slot(r * 9 - (r * (r - 1)) / 2 + (c - r), noff + I);
+    return slot(r * 9 + c, offdiag(I, J));
+  }
+};
+
 }  // namespace als

@@ -42,8 +42,8 @@ __global__ void k_cast(long long n, const S* __restrict__ x, D* __restrict__ y) 
 
 template <typename T>
 __global__ void k_scale_dev(long long n, const double* __restrict__ num, const double* __restrict__ den,
-                            const T* __restrict__ x, T* __restrict__ y) {
-  const double dn = den ? den[0] : 1.0;
+                            const T* __restrict__ x, T* __restrict__ y, int sqrt_den) {
+  const double dn = den ? (sqrt_den ? sqrt(fmax(den[0], 0.0)) : den[0]) : 1.0;
   const double f = (num ? num[0] : 1.0);
   const T s = (T)(dn != 0.0 ? f / dn : 0.0);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -62,10 +62,37 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// partial[b*k + j] = sum over block b's elements of V_j . w  (4 rows per sweep)
+// Reductions in one launch: every block writes its partial sums, takes a ticket
+// from a counter, and the block holding the last ticket adds all partials in a
+// fixed order (so the result does not depend on which block finishes last) and
+// resets the counter for the next launch.  Workspace layout: slot 0 holds the
+// counter, the partials start at slot 1.
+__device__ __forceinline__ bool last_block(double* ws) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned int*>(ws), 1u) == gridDim.x - 1;
+  __syncthreads();
+  return is_last;
+}
+
+__device__ __forceinline__ void finish_sums(double* ws, int k, int nb, double* out, double* sh) {
+  __threadfence();
+  const double* partial = ws + 1;
+  for (int j = 0; j < k; ++j) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[(long long)b * k + j];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) out[j] = v;
+  }
+  if (threadIdx.x == 0) *reinterpret_cast<unsigned int*>(ws) = 0u;
+}
+
+// out[j] = V_j . w for j < k  (rows read 4 at a time)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int k, const T* __restrict__ V, long long ld,
-                                                          const T* __restrict__ w, double* __restrict__ partial) {
+                                                          const T* __restrict__ w, double* __restrict__ partial,
+                                                          double* __restrict__ out) {
   __shared__ double sh[RED_THREADS / 32];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (int j0 = 0; j0 < k; j0 += 4) {
@@ -80,20 +107,31 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int k, co
     for (int jj = 0; jj < 4; ++jj) {
       if (j0 + jj >= k) break;
       const double s = block_sum(acc[jj], sh);
-      if (threadIdx.x == 0) partial[(long long)blockIdx.x * k + j0 + jj] = s;
+      if (threadIdx.x == 0) partial[1 + (long long)blockIdx.x * k + j0 + jj] = s;
     }
   }
+  if (last_block(partial)) finish_sums(partial, k, gridDim.x, out, sh);
 }
 
-// out[j] = sum_b partial[b*k + j]: one block per j, a fixed reduction tree
-__global__ void __launch_bounds__(RED_THREADS) k_multidot_final(int k, int nb, const double* __restrict__ partial,
-                                                                double* __restrict__ out) {
+// w <- w + sign * sum_j V_j h_j, and nrm2 = w . w of the updated w
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_multiaxpy_norm(long long n, int k, const T* __restrict__ V,
+                                                                long long ld, const double* __restrict__ h,
+                                                                double sign, T* __restrict__ w,
+                                                                double* __restrict__ partial,
+                                                                double* __restrict__ nrm2) {
   __shared__ double sh[RED_THREADS / 32];
-  const int j = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(long long)b * k + j];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) out[j] = s;
+  double acc2 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += (double)V[(long long)j * ld + i] * h[j];
+    const T wn = (T)((double)w[i] + sign * acc);
+    w[i] = wn;
+    acc2 += (double)wn * (double)wn;
+  }
+  const double s2 = block_sum(acc2, sh);
+  if (threadIdx.x == 0) partial[1 + blockIdx.x] = s2;
+  if (last_block(partial)) finish_sums(partial, 1, gridDim.x, nrm2, sh);
 }
 
 template <typename T>
@@ -140,16 +178,27 @@ void vec_zero(int prec, long long n, void* x, cudaStream_t s) {
   cudaMemsetAsync(x, 0, n * (prec == PREC_F64 ? 8 : 4), s);
 }
 
-size_t multidot_partial_doubles(int k) { return (size_t)RED_BLOCKS * (size_t)k; }
+// ticket counter slot + partial sums of RED_BLOCKS blocks for k columns
+size_t multidot_partial_doubles(int k) { return (size_t)RED_BLOCKS * (size_t)k + 1; }
 
 void vec_multidot(int prec, long long n, int k, const void* V, long long ld, const void* w, double* out,
                   double* partial, cudaStream_t s) {
   if (prec == PREC_F64)
-    k_multidot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial);
+    k_multidot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial, out);
   else
-    k_multidot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial);
-  k_multidot_final<<<k, RED_THREADS, 0, s>>>(k, RED_BLOCKS, partial, out);
-  count_launch(2);
+    k_multidot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial, out);
+  count_launch(1);
+}
+
+void vec_multiaxpy_norm(int prec, long long n, int k, const void* V, long long ld, const double* h, double sign,
+                        void* w, double* partial, double* nrm2, cudaStream_t s) {
+  if (prec == PREC_F64)
+    k_multiaxpy_norm<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, h, sign, (double*)w,
+                                                                  partial, nrm2);
+  else
+    k_multiaxpy_norm<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, h, sign, (float*)w,
+                                                                 partial, nrm2);
+  count_launch(1);
 }
 
 void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h, void* w,
@@ -167,9 +216,10 @@ void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, co
 }
 
 void vec_scale_dev(int prec, long long n, const double* num, const double* den, const void* x, void* y,
-                   cudaStream_t s) {
-  if (prec == PREC_F64) k_scale_dev<double><<<grid_for(n), 256, 0, s>>>(n, num, den, (const double*)x, (double*)y);
-  else k_scale_dev<float><<<grid_for(n), 256, 0, s>>>(n, num, den, (const float*)x, (float*)y);
+                   cudaStream_t s, int sqrt_den) {
+  if (prec == PREC_F64)
+    k_scale_dev<double><<<grid_for(n), 256, 0, s>>>(n, num, den, (const double*)x, (double*)y, sqrt_den);
+  else k_scale_dev<float><<<grid_for(n), 256, 0, s>>>(n, num, den, (const float*)x, (float*)y, sqrt_den);
   count_launch(1);
 }
 
@@ -214,6 +264,37 @@ __global__ void k_givens_step(int k, double* __restrict__ H, int ldh, double* __
   g[k + 1] = -sv * g[k];
   g[k] = c * g[k];
   res[0] = fabs(g[k + 1]);
+}
+
+// column k of the Hessenberg matrix: h[0..k] += h2 (second Gram-Schmidt pass, optional),
+// h[k+1] = sqrt(nrm2); then the Givens step as in k_givens_step
+__global__ void k_hess_givens(int k, double* __restrict__ H, int ldh, const double* __restrict__ h2,
+                              const double* __restrict__ nrm2, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, double* __restrict__ res) {
+  double* h = H + (long long)k * ldh;
+  if (h2)
+    for (int i = 0; i <= k; ++i) h[i] += h2[i];
+  h[k + 1] = sqrt(fmax(nrm2[0], 0.0));
+  for (int i = 0; i < k; ++i) {
+    const double a = h[i], b = h[i + 1];
+    h[i] = cs[i] * a + sn[i] * b;
+    h[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = h[k], b = h[k + 1];
+  const double r = hypot(a, b);
+  double c = 1.0, sv = 0.0;
+  if (r > 0.0) { c = a / r; sv = b / r; }
+  cs[k] = c; sn[k] = sv;
+  h[k] = r; h[k + 1] = 0.0;
+  g[k + 1] = -sv * g[k];
+  g[k] = c * g[k];
+  res[0] = fabs(g[k + 1]);
+}
+
+void dev_hess_givens(int k, double* H, int ldh, const double* h2, const double* nrm2, double* cs, double* sn,
+                     double* g, double* res, cudaStream_t s) {
+  k_hess_givens<<<1, 1, 0, s>>>(k, H, ldh, h2, nrm2, cs, sn, g, res);
+  count_launch(1);
 }
 
 void dev_givens_step(int k, double* H, int ldh, double* cs, double* sn, double* g, double* res, cudaStream_t s) {
@@ -276,12 +357,12 @@ __global__ void k_slot0_sum(long long ncells, int npr, const double* __restrict_
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long long)gridDim.x * blockDim.x)
     acc += p[c * npr];
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (threadIdx.x == 0) partial[1 + blockIdx.x] = s;
 }
 
 __global__ void k_slot0_sub(long long ncells, int npr, const double* __restrict__ partial, int nb, double* __restrict__ p) {
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[b];
+  for (int b = 0; b < nb; ++b) s += partial[1 + b];
   const double mean = s / (double)ncells;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long long)gridDim.x * blockDim.x)
     p[c * npr] -= mean;

@@ -9,6 +9,8 @@ void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, co
 void dev_sqrt(const double* in, double* out, cudaStream_t s);
 void dev_hess_finish(int k, double* hcol, const double* h2, const double* nrm2, cudaStream_t s);
 void dev_givens_step(int k, double* H, int ldh, double* cs, double* sn, double* g, double* res, cudaStream_t s);
+void dev_hess_givens(int k, double* H, int ldh, const double* h2, const double* nrm2, double* cs, double* sn,
+                     double* g, double* res, cudaStream_t s);
 void dev_backsolve(int k, const double* H, int ldh, const double* g, double* y, cudaStream_t s);
 void dev_init_g(int m, const double* nrm2, double* g, double* beta, cudaStream_t s);
 void schur_apply(long long ncells, int npr, const double* S, const double* t, double* z, cudaStream_t s);

@@ -19,6 +19,8 @@ struct LevelDev {
   float* inv32;
   int np;                // patch size d*3^d
   int pstride;           // entries per patch (padded)
+  DevStatus* status;     // where kernels of this level record device-side failures
+  void* ebuf;            // per-cell output buffer of the operator apply, [cell][d][3^d] (FP64-sized)
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
@@ -67,8 +69,12 @@ void vec_multidot(int prec, long long n, int k, const void* V, long long ld, con
 // w -= sum_j V_j h[j]
 void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h,
                    void* w, cudaStream_t s);
+// y = x * num / den (num, den device scalars, NULL = 1; den <- sqrt(den) if sqrt_den)
 void vec_scale_dev(int prec, long long n, const double* num, const double* den, const void* x, void* y,
-                   cudaStream_t s);
+                   cudaStream_t s, int sqrt_den = 0);
+// w <- w + sign * sum_j V_j h_j and nrm2 = |w|^2, one launch
+void vec_multiaxpy_norm(int prec, long long n, int k, const void* V, long long ld, const double* h, double sign,
+                        void* w, double* partial, double* nrm2, cudaStream_t s);
 size_t multidot_partial_doubles(int k);
 
 }  // namespace als

@@ -1,10 +1,12 @@
 // K1: matrix-free application of the augmented Stokes operators on one level.
 //
-// One thread per cell evaluates the cell's contribution with the sum-factorised
-// kernels of cell.cuh and adds it to the nodal output.  Cells are processed in
-// 2^d colours (parity of the cell index per axis): cells of one colour share no
-// node, so each launch adds with plain loads and stores, and the fixed colour
-// order makes every result bitwise reproducible.  Dirichlet rows carry
+// One warp per cell (three in 2D) evaluates the cell's contribution with sum
+// factorisation.  The nodal sum is formed without atomics, in a fixed order so
+// every result is bitwise reproducible: normally all cells write their local
+// outputs to a per-cell buffer and one gather kernel sums the <= 2^d values of
+// each node (two launches per apply); batched applies (many vectors at once)
+// instead run the cells in 2^d colours (parity of the cell index per axis) whose
+// cells share no node and add into y directly.  Dirichlet rows carry
 // the identity (y_D = x_D) and Dirichlet columns are masked (x_D treated as 0),
 // which is the constrained operator of Eq. (augstokessys) in the form Firedrake
 // and PETSc use.  B u (Eq. (stokessys)) is cell-local and written directly.
@@ -92,11 +94,11 @@ __device__ __forceinline__ bool colour_cell(const Colour& col, long long t, int&
 // moments are a warp (3D) or lane-group (2D) reduction, and the isotropic AL /
 // pressure part of the stress is formed at every point before the transposed
 // contractions take the fluxes back to the nodes.
-template <typename T, int DIM, bool TENSOR, int MODE>
+template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
 __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
                                                T* __restrict__ y, const T* __restrict__ coef,
                                                const T* __restrict__ p_in, T* __restrict__ p_out,
-                                               long long vstride) {
+                                               long long vstride, T* __restrict__ ebuf) {
   constexpr int NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
   constexpr int CPW = DIM == 2 ? 3 : 1;        // cells per warp
   constexpr int NCQ = TENSOR ? Sz<DIM>::NC : 1;
@@ -379,9 +381,17 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
       yl[c] = v;
     }
   }
-  if (act && (RAW || !bnd)) {
+  if constexpr (STAGED) {
+    // per-cell outputs [cell][c][3^d], summed per node by k_gather_cells in a fixed order
+    if (act) {
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) y[c * g.N + nd] += yl[c];
+      for (int c = 0; c < DIM; ++c) ebuf[(cell * DIM + c) * NB + l] = yl[c];
+    }
+  } else {
+    if (act && (RAW || !bnd)) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) y[c * g.N + nd] += yl[c];
+    }
   }
   }  // NEED_FLUX
 }
@@ -403,11 +413,68 @@ __global__ void k_init_out(Geom g, const T* __restrict__ x, T* __restrict__ y, i
   y[t] = (bnd && keep_bnd) ? x[t] : T(0);
 }
 
+// y(c, node) = sum of the per-cell outputs of the <= 2^d cells containing the
+// node, in a fixed order; Dirichlet rows: y_D = x_D (keep_bnd) or 0, unless raw.
+template <typename T, int DIM>
+__global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
+                               int keep_bnd, int raw) {
+  constexpr int NB = Sz<DIM>::NB;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N * DIM) return;
+  const int c = (int)(t / g.N);
+  const long long nd = t % g.N;
+  const int idx[3] = {(int)(nd % g.nn[0]), (int)((nd / g.nn[0]) % g.nn[1]),
+                      DIM == 3 ? (int)(nd / ((long long)g.nn[0] * g.nn[1])) : 0};
+  if (!raw && on_boundary(g, idx[0], idx[1], idx[2])) {
+    y[t] = keep_bnd ? x[t] : T(0);
+    return;
+  }
+  // per axis: odd node -> its own cell (local 1); even node -> cell below (local 2) and above (local 0)
+  int ncand[3] = {1, 1, 1}, cell[3][2] = {{0, 0}, {0, 0}, {0, 0}}, loc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int a = 0; a < DIM; ++a) {
+    const int i = idx[a];
+    if (i & 1) { cell[a][0] = i >> 1; loc[a][0] = 1; }
+    else {
+      int k = 0;
+      if (i > 0) { cell[a][k] = (i >> 1) - 1; loc[a][k] = 2; ++k; }
+      if (i < 2 * g.n[a]) { cell[a][k] = i >> 1; loc[a][k] = 0; ++k; }
+      ncand[a] = k;
+    }
+  }
+  T acc = T(0);
+  for (int cz = 0; cz < ncand[2]; ++cz)
+    for (int cy = 0; cy < ncand[1]; ++cy)
+      for (int cx = 0; cx < ncand[0]; ++cx) {
+        const long long ce = (long long)cell[0][cx] +
+                             (long long)g.n[0] * ((long long)cell[1][cy] + (DIM == 3 ? (long long)g.n[1] * cell[2][cz] : 0));
+        const int l = loc[0][cx] + 3 * loc[1][cy] + (DIM == 3 ? 9 * loc[2][cz] : 0);
+        acc += ebuf[(ce * DIM + c) * NB + l];
+      }
+  y[t] = acc;
+}
+
 template <typename T, int DIM, bool TENSOR, int MODE>
 static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y, const void* p_in,
                          void* p_out, int nvec, long long vstride, cudaStream_t s) {
   const Geom& g = L.g;
   constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
+  constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);   // cells per 256-thread block
+  const T* coef = nullptr;
+  if constexpr (std::is_same<T, double>::value) coef = L.coef64; else coef = L.coef32;
+  const int keep_bnd = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
+  if (nvec == 1 && L.ebuf) {
+    // one launch over all cells into the per-cell buffer, one gather launch per node
+    const Colour col = all_cells(g);
+    k_apply<T, DIM, TENSOR, MODE, true><<<(unsigned)((col.count + CPB - 1) / CPB), 256, 0, s>>>(
+        g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in, (T*)p_out, 0, (T*)L.ebuf);
+    if (NEED_FLUX) {
+      const long long tot = g.N * g.dim;
+      k_gather_cells<T, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
+                                                                          (T*)y, keep_bnd, (MODE & OP_RAW) ? 1 : 0);
+    }
+    count_launch(NEED_FLUX ? 2 : 1);
+    return;
+  }
   for (int v0 = 0; v0 < nvec; v0 += 65535) {
     const int nv = nvec - v0 < 65535 ? nvec - v0 : 65535;
     const T* xv = (const T*)x + v0 * vstride;
@@ -415,17 +482,14 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
     if (NEED_FLUX) {
       const long long tot = g.N * g.dim;
       dim3 grid((unsigned)((tot + 255) / 256), nv);
-      k_init_out<T><<<grid, 256, 0, s>>>(g, xv, yv, ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0, vstride);
+      k_init_out<T><<<grid, 256, 0, s>>>(g, xv, yv, keep_bnd, vstride);
     }
-    const T* coef = nullptr;
-    if constexpr (std::is_same<T, double>::value) coef = L.coef64; else coef = L.coef32;
     const int ncol = NEED_FLUX ? (1 << DIM) : 1;   // B u alone is cell-local: one launch
     for (int colour = 0; colour < ncol; ++colour) {
       const Colour col = NEED_FLUX ? make_colour(g, colour) : all_cells(g);
-      constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);   // cells per 256-thread block
       dim3 grid((unsigned)((col.count + CPB - 1) / CPB), nv);
-      k_apply<T, DIM, TENSOR, MODE><<<grid, 256, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
-                                                         (const T*)p_in, (T*)p_out, vstride);
+      k_apply<T, DIM, TENSOR, MODE, false><<<grid, 256, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
+                                                                (const T*)p_in, (T*)p_out, vstride, nullptr);
     }
     count_launch((NEED_FLUX ? 1 : 0) + ncol);
   }

@@ -3,15 +3,17 @@
 // For every vertex v the local space V_v = {v in V_h : supp v in star(v)} is
 // spanned by the free dofs at the 3^d Q2 nodes within half a cell of v.  Its
 // matrix A_v is the restriction of the assembled A_(h,gamma) to V_v; here it is
-// accumulated directly from the contributions of the 2^d cells of the star,
-// factored by Cholesky in FP64 and inverted, and the inverse is stored packed
-// (symmetric, by diagonals) in FP64 and optionally FP32.  Missing nodes of
+// accumulated directly from the contributions of the 2^d cells of the star and
+// inverted in FP64 by Gauss-Jordan elimination (no pivoting: A_v is SPD), and
+// the inverse is stored packed (symmetric) in FP64 and FP32.  Missing nodes of
 // boundary stars become identity rows so that every patch has d*3^d entries.
 //
 // The smoother applies z = sum_v I_v A_v^-1 I_v^T r in two deterministic steps:
 // one warp per patch computes y_v = A_v^-1 r|_v into a per-patch buffer, then
 // one thread per node sums the <= 2^d patch values that contain it in a fixed
 // order (no floating-point atomics).
+#include <stdint.h>
+
 #include <algorithm>
 
 #include "level.h"
@@ -47,9 +49,9 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ m
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
   constexpr int NSUB = 1 << DIM;  // patch nodes inside one cell of the star
   extern __shared__ double sm[];
-  double* A = sm;                    // NP x NP, lower triangle used
-  double* X = A + NP * NP;           // NP x NP, L^-1
-  double* gt = X + NP * NP;          // [q][a][k] physical gradient of phi_a at point q
+  double* A = sm;                    // NP x NP patch matrix, inverted in place
+  double* X = A + NP * NP;           // 2 NP: pivot column and scaled pivot row
+  double* gt = X + 2 * NP;           // [q][a][k] physical gradient of phi_a at point q
   double* bt = gt + NB * NB * DIM;   // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
   double* wq = bt + NPR * DIM * NB;  // [q] |J| w_q mu_q of the current cell
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -149,59 +151,350 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ m
   }
   __syncthreads();
 
-  // Cholesky A = L L^T (lower triangle, in place)
+  // In-place Gauss-Jordan inversion without pivoting.  A_v is SPD, so every pivot
+  // is a Schur complement of a leading block and is positive (as in Cholesky);
+  // a non-positive pivot is reported as ALS_ENOTSPD.  Per pivot k: the scaled
+  // row k and the column k are taken aside (pk, rk), then every entry is
+  // updated, A[i][j] -= A[i][k] A[k][j] / A[k][k].
+  double* pk = X;
+  double* rk = X + NP;
   for (int k = 0; k < NP; ++k) {
-    if (tid == 0) {
-      double d = A[k * NP + k];
-      if (!(d > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, v); d = 1.0; }
-      A[k * NP + k] = sqrt(d);
+    double d = A[k * NP + k];
+    if (!(d > 0.0)) {
+      if (tid == 0) report(st, 4 /* ALS_ENOTSPD */, v);
+      d = 1.0;
+    }
+    const double p = 1.0 / d;
+    for (int i = tid; i < NP; i += nt) {
+      pk[i] = (i == k) ? 0.0 : A[i * NP + k];
+      rk[i] = (i == k) ? p : A[k * NP + i] * p;
     }
     __syncthreads();
-    const double piv = A[k * NP + k];
-    for (int i = k + 1 + tid; i < NP; i += nt) A[i * NP + k] /= piv;
-    __syncthreads();
-    for (int i = k + 1 + tid; i < NP; i += nt) {
-      const double lik = A[i * NP + k];
-      for (int j = k + 1; j <= i; ++j) A[i * NP + j] -= lik * A[j * NP + k];
-    }
-    __syncthreads();
-  }
-  // X = L^-1 by rows
-  for (int i = 0; i < NP; ++i) {
-    const double lii = A[i * NP + i];
-    for (int j = tid; j <= i; j += nt) {
-      double acc = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) acc -= A[i * NP + k] * X[k * NP + j];
-      X[i * NP + j] = acc / lii;
+    for (int e = tid; e < NP * NP; e += nt) {
+      const int i = e / NP, j = e % NP;
+      if (i == k) A[e] = rk[j];
+      else A[e] = ((j == k) ? 0.0 : A[e]) - pk[i] * rk[j];
     }
     __syncthreads();
   }
-  // A^-1 = X^T X, written packed by diagonals: entry (i, i+t)
+  // A^-1 (symmetrised), packed by diagonals in FP64 and block-packed in FP32
   constexpr int NPK = NP * (NP + 1) / 2;
   for (int e = tid; e < NPK; e += nt) {
     int t = 0;
     while (diag_start(NP, t + 1) <= e) ++t;
     const int i = e - diag_start(NP, t), j = i + t;
-    double acc = 0.0;
-    for (int k = j; k < NP; ++k) acc += X[k * NP + i] * X[k * NP + j];
-    if (inv64) inv64[v * pstride + e] = acc;
-    if (inv32) inv32[v * pstride + e] = (float)acc;
+    const double val = 0.5 * (A[i * NP + j] + A[j * NP + i]);
+    if (inv64) inv64[v * pstride + e] = val;
+    if (inv32) inv32[v * pstride + BlockLayout(NP).index(i, j)] = (float)val;
   }
+}
+
+// ---------------------------------------------------------------------------
+// K4 (FP32): TMA-pipelined block-packed patch products
+//
+// Persistent CTAs of 128 threads.  Each iteration handles PPI patches whose
+// block-packed inverses (see BlockLayout) are streamed into a ring of NSTAGE
+// shared-memory stages by 1D bulk copies (cp.async.bulk, completion counted on
+// an mbarrier), issued by thread 0 NSTAGE iterations ahead.  Thread b of a
+// patch owns one 9x9 block S_IJ and forms both S_IJ r_J and S_IJ^T r_I from
+// registers, so each stored entry is read from shared memory exactly once; a
+// fixed-order reduction of the block partials gives y_v = A_v^-1 r|_v.
+// Every mbarrier wait is bounded: on expiry the kernel records ALS_ETIMEOUT,
+// waits (bounded) for the copies it issued and returns.
+// ---------------------------------------------------------------------------
+namespace tma {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: ~2^22 polls with back-off (well over a second), false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(256);
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+}  // namespace tma
+
+enum PatchOut { OUT_SCRATCH = 0, OUT_WRITE = 1, OUT_SUBTRACT = 2 };
+
+template <int DIM>
+struct TmaCfg {
+  static constexpr int NP = Sz<DIM>::NP;
+  static constexpr int NB = Sz<DIM>::NB;
+  static constexpr int THREADS = 64;
+  static constexpr int TPP = DIM == 3 ? 64 : 4;        // threads per patch (>= blocks per patch)
+  static constexpr int PPI = THREADS / TPP;            // patches per iteration
+  static constexpr int NSTAGE = 3;
+  static constexpr int STRIDE = packed_stride(NP);     // floats per patch
+  static constexpr BlockLayout BL = BlockLayout(NP);
+  static constexpr int NBP = (NP / 9) * (NP / 9 + 1) / 2;
+  static constexpr int RPT = (PPI * NP + THREADS - 1) / THREADS;   // r values gathered per thread
+  static constexpr size_t stage_floats = (size_t)PPI * STRIDE;
+  // dynamic shared memory: [mbarriers | stages | r | partials]; the barriers need
+  // 8-byte and the bulk-copy destinations 16-byte alignment
+  static constexpr size_t bar_bytes = 128;
+  static constexpr size_t smem_bytes =
+      bar_bytes + NSTAGE * stage_floats * 4 + (size_t)PPI * NP * 4 + (size_t)PPI * 18 * NBP * 4;
+  static_assert(NSTAGE * 8 <= bar_bytes, "mbarrier area too small");
+  static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
+};
+
+// vertex id of slot p of the work list (all vertices, or the centres 2K+1 of
+// coarse cells) and its lattice coordinates; -1 past the end
+template <int DIM>
+__device__ __forceinline__ int work_vertex(const Geom& g, int interior, int p, int count, int& vx, int& vy,
+                                           int& vz) {
+  if (p >= count) return -1;
+  if (!interior) {
+    const int nvx = g.nv[0], nvy = g.nv[1];
+    vx = p % nvx;
+    const int q = p / nvx;
+    vy = q % nvy;
+    vz = DIM == 3 ? q / nvy : 0;
+    return p;
+  }
+  const int ncx = g.n[0] >> 1, ncy = g.n[1] >> 1;
+  const int kx = p % ncx, q = p / ncx, ky = q % ncy, kz = DIM == 3 ? q / ncy : 0;
+  vx = 2 * kx + 1;
+  vy = 2 * ky + 1;
+  vz = DIM == 3 ? 2 * kz + 1 : 0;
+  return vx + g.nv[0] * (vy + g.nv[1] * vz);
+}
+
+// r at patch entry i of the vertex (absent nodes give 0)
+template <int DIM>
+__device__ __forceinline__ float patch_r(const Geom& g, const float* __restrict__ r, int vid, int vx, int vy, int vz,
+                                         int i) {
+  constexpr int NB = Sz<DIM>::NB;
+  if (vid < 0) return 0.f;
+  long long nd;
+  return patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
+                                                  const float* __restrict__ r, float* __restrict__ out, int mode,
+                                                  DevStatus* st) {
+  using C = TmaCfg<DIM>;
+  constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBP = C::NBP;
+  constexpr int RPT = C::RPT, THREADS = C::THREADS;
+  constexpr BlockLayout BL = C::BL;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
+  float* stages = reinterpret_cast<float*>(smraw + C::bar_bytes);
+  float* rs = stages + NSTAGE * C::stage_floats;          // [PPI][NP]
+  float* part = rs + PPI * NP;                            // [PPI][18][NBP]
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int ngroups = (count + PPI - 1) / PPI;
+
+  auto issue = [&](int grp, int stage) {   // thread 0: one bulk copy per patch of the group
+    uint32_t bytes = 0;
+    int vids[PPI];
+    for (int ps = 0; ps < PPI; ++ps) {
+      int vx, vy, vz;
+      vids[ps] = work_vertex<DIM>(g, interior, grp * PPI + ps, count, vx, vy, vz);
+      if (vids[ps] >= 0) bytes += C::STRIDE * 4;
+    }
+    tma::mbar_expect_tx(&bars[stage], bytes);
+    for (int ps = 0; ps < PPI; ++ps)
+      if (vids[ps] >= 0)
+        tma::bulk_load(stages + stage * C::stage_floats + (size_t)ps * C::STRIDE,
+                       inv + (long long)vids[ps] * C::STRIDE, C::STRIDE * 4, &bars[stage]);
+  };
+  // r values of group grp handled by this thread: elements tid + k THREADS
+  auto gather = [&](int grp, float (&v)[RPT]) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int e = tid + k * THREADS;
+      v[k] = 0.f;
+      if (e < PPI * NP && grp < ngroups) {
+        int vx, vy, vz;
+        const int vid = work_vertex<DIM>(g, interior, grp * PPI + e / NP, count, vx, vy, vz);
+        v[k] = patch_r<DIM>(g, r, vid, vx, vy, vz, e % NP);
+      }
+    }
+  };
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < NSTAGE; ++i) tma::mbar_init(&bars[i], 1);
+    tma::fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < NSTAGE; ++i) {
+      const int grp = blockIdx.x + i * gridDim.x;
+      if (grp < ngroups) issue(grp, i);
+    }
+  float rpre[RPT];
+  gather(blockIdx.x, rpre);
+
+  const int ps = tid / TPP, b = tid % TPP;
+  int it = 0;
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int stage = it % NSTAGE;
+    const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int e = tid + k * THREADS;
+      if (e < PPI * NP) rs[e] = rpre[k];
+    }
+    gather(grp + gridDim.x, rpre);          // next group's r: in flight while this one is computed
+    if (!tma::mbar_wait(&bars[stage], parity)) {
+      if (tid == 0) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    // block products
+    const float* S = stages + stage * C::stage_floats + (size_t)ps * C::STRIDE;
+    if (b < NBP) {
+      const bool diag = b >= BL.noff;
+      int I = 0, J = 0;
+      if (diag) {
+        I = J = b - BL.noff;
+      } else {
+        int rem = b;
+        while (rem >= BL.nbr - 1 - I) { rem -= BL.nbr - 1 - I; ++I; }
+        J = I + 1 + rem;
+      }
+      float rI[9], rJ[9], yI[9], yJ[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        rI[k] = rs[ps * NP + 9 * I + k];
+        rJ[k] = rs[ps * NP + 9 * J + k];
+        yI[k] = 0.f;
+        yJ[k] = 0.f;
+      }
+      if (diag) {
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+          for (int cc = rr; cc < 9; ++cc) {
+            const int e = rr * 9 - (rr * (rr - 1)) / 2 + (cc - rr);
+            const float sv = S[BL.slot(e, b)];
+            yI[rr] += sv * rI[cc];
+            if (cc != rr) yI[cc] += sv * rI[rr];
+          }
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < 9; ++cc) {
+            const float sv = S[BL.slot(rr * 9 + cc, b)];
+            yI[rr] += sv * rJ[cc];
+            yJ[cc] += sv * rI[rr];
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        part[(ps * 18 + k) * NBP + b] = yI[k];
+        part[(ps * 18 + 9 + k) * NBP + b] = yJ[k];
+      }
+    }
+    __syncthreads();
+    // the stage is consumed: refill it NSTAGE groups ahead while the partials are reduced
+    if (tid == 0) {
+      const int nxt = grp + NSTAGE * gridDim.x;
+      if (nxt < ngroups) {
+        tma::fence_async();
+        issue(nxt, stage);
+      }
+    }
+    // y_i = sum over the blocks of row-block I, fixed order J = 0..NBR-1
+    for (int e = tid; e < PPI * NP; e += THREADS) {
+      const int p = e / NP, i = e % NP;
+      int vx, vy, vz;
+      const int v = work_vertex<DIM>(g, interior, grp * PPI + p, count, vx, vy, vz);
+      if (v < 0) continue;
+      const int I = i / 9, rr = i % 9;
+      float acc = 0.f;
+      for (int J = 0; J < BL.nbr; ++J) {
+        if (J == I) acc += part[(p * 18 + rr) * NBP + BL.noff + I];
+        else if (J > I) acc += part[(p * 18 + rr) * NBP + BL.offdiag(I, J)];
+        else acc += part[(p * 18 + 9 + rr) * NBP + BL.offdiag(J, I)];
+      }
+      if (mode == OUT_SCRATCH) {
+        out[(long long)v * NP + i] = acc;
+      } else {
+        long long nd;
+        if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
+          float* o = out + (i / NB) * g.N + nd;
+          *o = mode == OUT_SUBTRACT ? *o - acc : acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) {
+    // drain: wait (bounded) for every copy this CTA issued and did not consume
+    int k = it;
+    for (int grp = blockIdx.x + it * gridDim.x; grp < ngroups && k < it + NSTAGE; grp += gridDim.x, ++k)
+      tma::mbar_wait(&bars[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1));
+  }
+}
+
+template <int DIM>
+static void launch_patch_tma(const LevelDev& L, int interior, long long count, const float* r, float* out, int mode,
+                             DevStatus* st, cudaStream_t s) {
+  using C = TmaCfg<DIM>;
+  const long long groups = (count + C::PPI - 1) / C::PPI;
+  const long long per_sm = (227 * 1024) / (long long)(C::smem_bytes + 1024);   // resident CTAs per SM
+  const long long cap = 152 * (per_sm < 1 ? 1 : per_sm);
+  const long long grid = groups < cap ? groups : cap;
+  if (grid <= 0) return;
+  k_patch_tma<DIM><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count, r, out,
+                                                                     mode, st);
+  count_launch(1);
 }
 
 static size_t setup_smem(int dim) {
   const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1;
-  return sizeof(double) * (2 * NP * NP + NB * NB * dim + NPR * dim * NB + NB);
+  return sizeof(double) * (NP * NP + 2 * NP + NB * NB * dim + NPR * dim * NB + NB);
+}
+
+template <int DIM>
+static void set_tma_smem() {
+  cudaFuncSetAttribute(k_patch_tma<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaCfg<DIM>::smem_bytes);
 }
 
 void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
+  // shared-memory limit of the FP32 patch kernel, set here, before any graph capture
+  if (L.g.dim == 2) set_tma_smem<2>(); else set_tma_smem<3>();
   const size_t smem = setup_smem(L.g.dim);
   if (L.g.dim == 2) {
-    k_patch_setup<2><<<(unsigned)L.g.nverts, 64, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
+    k_patch_setup<2><<<(unsigned)L.g.nverts, 128, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
                                                              store32 ? L.inv32 : nullptr, L.pstride, st);
   } else {
     cudaFuncSetAttribute(k_patch_setup<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_patch_setup<3><<<(unsigned)L.g.nverts, 128, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
+    k_patch_setup<3><<<(unsigned)L.g.nverts, 256, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
                                                               store32 ? L.inv32 : nullptr, L.pstride, st);
   }
   count_launch(1);
@@ -307,14 +600,25 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
   count_launch(2);
 }
 
+template <int DIM>
+static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
+                       cudaEvent_t e1) {
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  const long long tot = L.g.N * DIM;
+  k_patch_gather<float, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z);
+  count_launch(1);
+}
+
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
                   cudaEvent_t e0, cudaEvent_t e1) {
   if (prec == PREC_F64) {
     if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1);
     else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1);
   } else {
-    if (L.g.dim == 2) smooth_impl<float, float, 2>(L, L.inv32, r, z, scratch, s, e0, e1);
-    else smooth_impl<float, float, 3>(L, L.inv32, r, z, scratch, s, e0, e1);
+    if (L.g.dim == 2) smooth_tma<2>(L, r, z, scratch, s, e0, e1);
+    else smooth_tma<3>(L, r, z, scratch, s, e0, e1);
   }
 }
 
@@ -372,8 +676,12 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
     if (fine.g.dim == 2) interior_impl<double, double, 2>(fine, fine.inv64, in, out, subtract, s);
     else interior_impl<double, double, 3>(fine, fine.inv64, in, out, subtract, s);
   } else {
-    if (fine.g.dim == 2) interior_impl<float, float, 2>(fine, fine.inv32, in, out, subtract, s);
-    else interior_impl<float, float, 3>(fine, fine.inv32, in, out, subtract, s);
+    const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2) * (fine.g.dim == 3 ? fine.g.n[2] / 2 : 1);
+    if (!subtract) cudaMemsetAsync(out, 0, sizeof(float) * fine.g.N * fine.g.dim, s);
+    if (fine.g.dim == 2)
+      launch_patch_tma<2>(fine, 1, nc, (const float*)in, (float*)out, subtract ? OUT_SUBTRACT : OUT_WRITE, fine.status, s);
+    else
+      launch_patch_tma<3>(fine, 1, nc, (const float*)in, (float*)out, subtract ? OUT_SUBTRACT : OUT_WRITE, fine.status, s);
   }
 }
 
