@@ -172,20 +172,23 @@ def measured_peak_hbm():
 
 
 def stored_traffic(kernel, workload):
-    """Per-launch DRAM traffic from the committed ncu summary, if it was taken on the
-    current source of the kernel; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """Per-launch DRAM traffic from the committed ncu summary (profiles/traffic.txt),
+    if it was taken on the current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    try:
-        d = json.load(open(path))
-        rec = d.get(kernel, {})
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha") or rec.get("workload") != workload:
+    for line in open(path):
+        parts = line.split()
+        if len(parts) != 5 or line.startswith("#") or parts[0] != kernel or parts[1] != workload:
+            continue
+        try:
+            src = open(os.path.join(ROOT, parts[2]), "rb").read()
+        except OSError:
             return None
-        return float(rec["bytes_per_launch"])
-    except Exception:
-        return None
+        if hashlib.sha256(src).hexdigest()[:16] != parts[3]:
+            return None
+        return float(parts[4])
+    return None
 
 
 # --------------------------------------------------------------------------
@@ -405,7 +408,7 @@ def ours(args, dist):
         "mixed_vs_fp64_rel_err": {"u": err_u, "p": err_p},
         "e2e": {"value": dist.world * dofs / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "kernel": "k_patch_apply<float,float,%d> (finest level)" % pb.d,
+        "roofline": {"bound": "hbm", "kernel": "k_patch_tma<%d> (FP32 star smoother, finest level)" % pb.d,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,

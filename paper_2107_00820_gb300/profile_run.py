@@ -1,0 +1,60 @@
+"""Profiling driver: setup plus a few V-cycles of a benchmark workload inside a
+cudaProfilerStart/Stop region, for `ncu --profile-from-start off`.
+
+    python -m paper_2107_00820_gb300.profile_run --workload sinker3d_32 --vcycles 1 --prec fp32
+
+Only the region (the V-cycles, optionally one setup) is profiled; problem
+generation and the context's own setup run before it.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    import bench
+    from paper_2107_00820_gb300 import Context, alstokes as A
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="sinker3d_32", choices=sorted(bench.WORKLOADS))
+    ap.add_argument("--vcycles", type=int, default=1)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "both"])
+    ap.add_argument("--setup", action="store_true", help="profile one coefficient setup instead")
+    args = ap.parse_args()
+    spec = bench.WORKLOADS[args.workload]
+    pb = bench.make_problem(spec)
+    mu = [torch.as_tensor(m, device="cuda") for m in pb.mu]
+    ctx = Context(pb.d, pb.n, pb.levels, mu, pb.gamma, mode=A.ALS_MODE_MIXED, sweeps=spec["sweeps"])
+    nu = ctx.nu()
+    vecs = {}
+    if args.prec in ("fp32", "both"):
+        vecs[A.ALS_PREC_FP32] = torch.randn(nu, dtype=torch.float32, device="cuda")
+    if args.prec in ("fp64", "both"):
+        vecs[A.ALS_PREC_FP64] = torch.randn(nu, dtype=torch.float64, device="cuda")
+    outs = {p: torch.zeros_like(b) for p, b in vecs.items()}
+    for p, b in vecs.items():           # capture the V-cycle graphs before the region
+        ctx.vcycle(b, outs[p], p)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    if args.setup:
+        ctx.update_coefficients(mu)
+    else:
+        for _ in range(args.vcycles):
+            for p, b in vecs.items():
+                ctx.vcycle(b, outs[p], p)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    ctx.close()
+    print("profile region done")
+
+
+if __name__ == "__main__":
+    main()
