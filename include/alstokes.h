@@ -87,7 +87,9 @@ typedef struct {
   int sweeps;     /* smoothing steps per level, pre and post (default 5) */
   double tau;     /* Richardson damping (default 2^-d) */
   int transfer;   /* ALS_TRANSFER_ROBUST (default, Eq. (Ptilde)) or ALS_TRANSFER_STANDARD */
-  int schur;      /* ALS_SCHUR_P1 (default, Eq. (P1P2)) */
+  int schur;      /* ALS_SCHUR_P1 (default): S^-1 ~ M_p(1/mu)^-1 + gamma M_p^-1 with the
+                     augmentation weight W = M_p; ALS_SCHUR_P2: S^-1 ~ (1+gamma) M_p(1/mu)^-1
+                     with W = M_p(1/mu) in A_gamma too (Eq. (P1P2)) */
   int mode;       /* ALS_MODE_FP64 or ALS_MODE_MIXED (FP32 V-cycle, FP64 outer loop) */
   double rtol;    /* FGMRES relative residual reduction (default 1e-8) */
   int maxit;      /* FGMRES iterations, no restart (default 300) */
@@ -115,7 +117,8 @@ als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma
 
 als_status als_destroy(als_ctx* ctx);
 
-/* y = A_gamma x on `level` (Eq. (augstokessys), W = M_p), matrix-free.
+/* y = A_gamma x on `level` (Eq. (augstokessys); W = M_p, or M_p(1/mu) with
+ * ALS_SCHUR_P2), matrix-free.
  * x, y: device vectors of length d*N_level in precision `prec`
  * (ALS_PREC_FP64: double, ALS_PREC_FP32: float).  Boundary rows: y_D = x_D. */
 als_status als_apply_agamma(als_ctx* ctx, int level, int prec, const void* x, void* y);

@@ -514,6 +514,10 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
       if (cudaMemcpyAsync(Lv.mu64, coeff->mu_eff[l], nq * sizeof(double), cudaMemcpyDefault, c->stream) != cudaSuccess)
         return cuda_check(c, "copy mu_eff");
     }
+    if (Lv.winv64) {
+      schur_setup(Lv.g, c->gamma, Lv.mu64, nullptr, c->st, c->stream, 1, Lv.winv64, Lv.winv32);
+      ALS_TRY(cuda_check(c, "mass blocks"));
+    }
     if (l > 0) {
       patch_setup(Lv, c->gamma, 1, c->st, c->stream);
       ALS_TRY(cuda_check(c, "patch setup"));
@@ -522,7 +526,7 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream);
   ALS_TRY(cuda_check(c, "coarse setup"));
   const LevelDev& F = c->lev[c->L - 1];
-  schur_setup(F.g, c->gamma, F.mu64, c->schur, c->st, c->stream);
+  schur_setup(F.g, c->gamma, F.mu64, c->schur, c->st, c->stream, c->opt.schur == ALS_SCHUR_P2 ? 1 : 0);
   ALS_TRY(cuda_check(c, "schur setup"));
   return check_status(c, "setup");
 }
@@ -544,7 +548,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.sweeps < 1 || c->opt.sweeps > 64) return fail(c, ALS_EINVAL, "sweeps must be in [1, 64]");
   if (c->opt.tau <= 0.0) c->opt.tau = std::pow(2.0, -c->dim);
   if (c->opt.maxit < 1 || c->opt.maxit > 2000) return fail(c, ALS_EINVAL, "maxit must be in [1, 2000]");
-  if (c->opt.schur != ALS_SCHUR_P1) return fail(c, ALS_EINVAL, "only the P1 Schur approximation (W = M_p) is built");
+  if (c->opt.schur != ALS_SCHUR_P1 && c->opt.schur != ALS_SCHUR_P2) return fail(c, ALS_EINVAL, "unknown Schur variant");
   if (c->opt.smoother != ALS_SMOOTH_GMRES && c->opt.smoother != ALS_SMOOTH_RICHARDSON)
     return fail(c, ALS_EINVAL, "unknown smoother");
   if (c->opt.transfer != ALS_TRANSFER_ROBUST && c->opt.transfer != ALS_TRANSFER_STANDARD)
@@ -555,8 +559,6 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
       return fail(c, ALS_EINVAL, "n must be divisible by 2^(levels-1) with >= 2 coarse cells per direction");
   }
-  if (coeff->kind == ALS_COEFF_TENSOR && c->L > 1)
-    return fail(c, ALS_EINVAL, "tensor coefficients with more than one level: patch setup not built");
   const char* ng = getenv("ALS_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -588,6 +590,11 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
       double* e = nullptr;
       ALS_TRY(dalloc(c, &e, (size_t)Lv.g.ncells * NB * c->dim));
       Lv.ebuf = e;
+    }
+    if (c->opt.schur == ALS_SCHUR_P2) {   // P2 pairs the augmentation weight W = M_p(1/mu)
+      const size_t nb2 = (size_t)Lv.g.ncells * (c->dim + 1) * (c->dim + 1);
+      ALS_TRY(dalloc(c, &Lv.winv64, nb2));
+      ALS_TRY(dalloc(c, &Lv.winv32, nb2));
     }
     if (l > 0) {
       ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
@@ -811,7 +818,7 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
   op_apply(F, PREC_F64, OP_B | OP_RAW, c->gamma, c->uD, nullptr, nullptr, c->tp, s);   // B u_D
   vec_axpby(PREC_F64, c->np, 1.0, c->r2_dev, -1.0, c->tp, s);                          // r2 - B u_D
   cudaMemcpyAsync(rhs_p, c->tp, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, s);
-  winv_scale(F.g, c->gamma, c->r2_dev, c->tp2, s);                                     // gamma W^-1 r2 (user part)
+  winv_scale(F.g, c->gamma, c->r2_dev, c->tp2, s, F.winv64);                           // gamma W^-1 r2 (user part)
   op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);         // B^T gamma W^-1 r2
   vec_axpby(PREC_F64, c->nu, 1.0, c->tu2, 1.0, c->tu, s);
   bnd_mask(F.g, c->tu, rhs_u, 0, s);                                                   // zero boundary rows

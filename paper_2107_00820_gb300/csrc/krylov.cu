@@ -388,7 +388,7 @@ namespace als {
 // ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void k_schur_setup(Geom g, double gamma, const double* __restrict__ mu, double* __restrict__ S,
-                              DevStatus* st) {
+                              DevStatus* st, int variant, double* __restrict__ winv64, float* __restrict__ winv32) {
   constexpr int NPR = DIM + 1, NB = DIM == 2 ? 9 : 27;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncells) return;
@@ -429,17 +429,25 @@ __global__ void k_schur_setup(Geom g, double gamma, const double* __restrict__ m
     }
   for (int i = 0; i < NPR; ++i)
     for (int j = 0; j < NPR; ++j) {
-      double acc = 0.0;
+      double acc = 0.0;                     // [M_K(1/mu)^-1]_ij
       for (int k = (i > j ? i : j); k < NPR; ++k) acc += X[k][i] * X[k][j];
-      if (i == j) acc += gamma * (i == 0 ? 1.0 : 3.0) / vol;
+      if (winv64) winv64[(c * NPR + i) * NPR + j] = acc;
+      if (winv32) winv32[(c * NPR + i) * NPR + j] = (float)acc;
+      if (!S) continue;
+      if (variant == 0) {                   // P1: M_p(1/mu)^-1 + gamma M_p^-1
+        if (i == j) acc += gamma * (i == 0 ? 1.0 : 3.0) / vol;
+      } else {                              // P2: (1 + gamma) M_p(1/mu)^-1
+        acc *= 1.0 + gamma;
+      }
       S[(c * NPR + i) * NPR + j] = acc;
     }
 }
 
-void schur_setup(const Geom& g, double gamma, const double* mu, double* S, DevStatus* st, cudaStream_t s) {
+void schur_setup(const Geom& g, double gamma, const double* mu, double* S, DevStatus* st, cudaStream_t s,
+                 int variant, double* winv64, float* winv32) {
   const unsigned b = (unsigned)((g.ncells + 127) / 128);
-  if (g.dim == 2) k_schur_setup<2><<<b, 128, 0, s>>>(g, gamma, mu, S, st);
-  else k_schur_setup<3><<<b, 128, 0, s>>>(g, gamma, mu, S, st);
+  if (g.dim == 2) k_schur_setup<2><<<b, 128, 0, s>>>(g, gamma, mu, S, st, variant, winv64, winv32);
+  else k_schur_setup<3><<<b, 128, 0, s>>>(g, gamma, mu, S, st, variant, winv64, winv32);
   count_launch(1);
 }
 
@@ -470,7 +478,23 @@ __global__ void k_winv(long long ncells, int npr, double scale0, double scale1, 
   out[t] = r2[t] * ((t % npr) == 0 ? scale0 : scale1);
 }
 
-void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cudaStream_t s) {
+__global__ void k_winv_block(long long ncells, int npr, double gamma, const double* __restrict__ winv,
+                             const double* __restrict__ r2, double* __restrict__ out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int i = 0; i < npr; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < npr; ++j) acc += winv[(c * npr + i) * npr + j] * r2[c * npr + j];
+    out[c * npr + i] = gamma * acc;
+  }
+}
+
+void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cudaStream_t s, const double* winv) {
+  if (winv) {
+    k_winv_block<<<(unsigned)((g.ncells + 255) / 256), 256, 0, s>>>(g.ncells, g.dim + 1, gamma, winv, r2, out);
+    count_launch(1);
+    return;
+  }
   double vol = 1.0;
   for (int k = 0; k < g.dim; ++k) vol *= g.h[k];
   const long long tot = g.ncells * (g.dim + 1);

@@ -32,7 +32,11 @@ void coarse_free(CoarseDev* C);
 }  // namespace als
 
 namespace als {
-void schur_setup(const struct Geom& g, double gamma, const double* mu, double* S, struct DevStatus* st, cudaStream_t s);
+// per-cell mass blocks: W^-1 = M_K(1/mu)^-1 into winv64/winv32 (if non-NULL) and the
+// Schur blocks S (if non-NULL) of variant 0 (P1) or 1 (P2), Eq. (P1P2)
+void schur_setup(const struct Geom& g, double gamma, const double* mu, double* S, struct DevStatus* st, cudaStream_t s,
+                 int variant = 0, double* winv64 = nullptr, float* winv32 = nullptr);
 void bnd_mask(const struct Geom& g, const double* x, double* y, int keep_boundary, cudaStream_t s);
-void winv_scale(const struct Geom& g, double gamma, const double* r2, double* out, cudaStream_t s);
+void winv_scale(const struct Geom& g, double gamma, const double* r2, double* out, cudaStream_t s,
+                const double* winv = nullptr);
 }  // namespace als

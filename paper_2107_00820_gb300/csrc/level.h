@@ -21,6 +21,9 @@ struct LevelDev {
   int pstride;           // entries per patch (padded)
   DevStatus* status;     // where kernels of this level record device-side failures
   void* ebuf;            // per-cell output buffer of the operator apply, [cell][d][3^d] (FP64-sized)
+  // W^-1 of the augmentation when W = M_p(1/mu): per-cell (d+1)^2 blocks; NULL when W = M_p
+  double* winv64;
+  float* winv32;
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };

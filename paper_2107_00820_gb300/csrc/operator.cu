@@ -98,7 +98,8 @@ template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
 __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
                                                T* __restrict__ y, const T* __restrict__ coef,
                                                const T* __restrict__ p_in, T* __restrict__ p_out,
-                                               long long vstride, T* __restrict__ ebuf) {
+                                               long long vstride, T* __restrict__ ebuf,
+                                               const T* __restrict__ winv) {
   constexpr int NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
   constexpr int CPW = DIM == 2 ? 3 : 1;        // cells per warp
   constexpr int NCQ = TENSOR ? Sz<DIM>::NC : 1;
@@ -275,7 +276,18 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
 #pragma unroll
   for (int p = 0; p < NPR; ++p) {
     pi[p] = T(0);
-    if constexpr ((MODE & OP_AL) != 0) pi[p] += cc.gamma * m[p] * (p == 0 ? cc.inv_m0 : cc.inv_m1);
+    if constexpr ((MODE & OP_AL) != 0) {
+      if (winv) {   // W = M_p(1/mu): per-cell (d+1)^2 block of W^-1
+        T acc = T(0);
+        if (act) {
+#pragma unroll
+          for (int q = 0; q < NPR; ++q) acc += winv[(cell * NPR + p) * NPR + q] * m[q];
+        }
+        pi[p] += cc.gamma * acc;
+      } else {      // W = M_p = |K| diag(1, 1/3, ..)
+        pi[p] += cc.gamma * m[p] * (p == 0 ? cc.inv_m0 : cc.inv_m1);
+      }
+    }
     if constexpr ((MODE & OP_BT) != 0) pi[p] -= act ? p_in[cell * NPR + p] : T(0);
   }
   T iso = T(0);
@@ -460,13 +472,15 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
   constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
   constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);   // cells per 256-thread block
   const T* coef = nullptr;
-  if constexpr (std::is_same<T, double>::value) coef = L.coef64; else coef = L.coef32;
+  const T* winv = nullptr;
+  if constexpr (std::is_same<T, double>::value) { coef = L.coef64; winv = L.winv64; }
+  else { coef = L.coef32; winv = L.winv32; }
   const int keep_bnd = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
   if (nvec == 1 && L.ebuf) {
     // one launch over all cells into the per-cell buffer, one gather launch per node
     const Colour col = all_cells(g);
     k_apply<T, DIM, TENSOR, MODE, true><<<(unsigned)((col.count + CPB - 1) / CPB), 256, 0, s>>>(
-        g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in, (T*)p_out, 0, (T*)L.ebuf);
+        g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in, (T*)p_out, 0, (T*)L.ebuf, winv);
     if (NEED_FLUX) {
       const long long tot = g.N * g.dim;
       k_gather_cells<T, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
@@ -489,7 +503,7 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
       const Colour col = NEED_FLUX ? make_colour(g, colour) : all_cells(g);
       dim3 grid((unsigned)((col.count + CPB - 1) / CPB), nv);
       k_apply<T, DIM, TENSOR, MODE, false><<<grid, 256, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
-                                                                (const T*)p_in, (T*)p_out, vstride, nullptr);
+                                                                (const T*)p_in, (T*)p_out, vstride, nullptr, winv);
     }
     count_launch((NEED_FLUX ? 1 : 0) + ncol);
   }

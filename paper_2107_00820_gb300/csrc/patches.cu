@@ -43,17 +43,39 @@ __device__ __forceinline__ void vertex_coords(const Geom& g, long long v, int& v
 // ---------------------------------------------------------------------------
 // K2 + K3: assemble, factor and invert one patch per CTA (FP64)
 // ---------------------------------------------------------------------------
+// Mandel vector of eps(phi e_al) for grad phi = gr: components (00, 11[, 22], [12, 02,] 01),
+// sqrt2 on the shear components
 template <int DIM>
-__global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ mu, double* __restrict__ inv64,
-                              float* __restrict__ inv32, int pstride, DevStatus* st) {
+__device__ __forceinline__ void mandel_of(int al, const double* gr, double* e) {
+  constexpr double ir2 = 0.70710678118654752440;
+  if (DIM == 2) {
+    e[0] = al == 0 ? gr[0] : 0.0;
+    e[1] = al == 1 ? gr[1] : 0.0;
+    e[2] = ((al == 0 ? gr[1] : 0.0) + (al == 1 ? gr[0] : 0.0)) * ir2;
+  } else {
+    e[0] = al == 0 ? gr[0] : 0.0;
+    e[1] = al == 1 ? gr[1] : 0.0;
+    e[2] = al == 2 ? gr[2] : 0.0;
+    e[3] = ((al == 1 ? gr[2] : 0.0) + (al == 2 ? gr[1] : 0.0)) * ir2;
+    e[4] = ((al == 0 ? gr[2] : 0.0) + (al == 2 ? gr[0] : 0.0)) * ir2;
+    e[5] = ((al == 0 ? gr[1] : 0.0) + (al == 1 ? gr[0] : 0.0)) * ir2;
+  }
+}
+
+// coef: scalar mu [cell][3^d] or Mandel tensor C [cell][3^d][NC] (upper triangle, row-major)
+template <int DIM, bool TENSOR>
+__global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ coef, double* __restrict__ inv64,
+                              float* __restrict__ inv32, int pstride, DevStatus* st,
+                              const double* __restrict__ winv) {
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
+  constexpr int NM = Sz<DIM>::NM, NC = Sz<DIM>::NC;
   constexpr int NSUB = 1 << DIM;  // patch nodes inside one cell of the star
   extern __shared__ double sm[];
   double* A = sm;                    // NP x NP patch matrix, inverted in place
   double* X = A + NP * NP;           // 2 NP: pivot column and scaled pivot row
   double* gt = X + 2 * NP;           // [q][a][k] physical gradient of phi_a at point q
   double* bt = gt + NB * NB * DIM;   // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
-  double* wq = bt + NPR * DIM * NB;  // [q] |J| w_q mu_q of the current cell
+  double* wq = bt + NPR * DIM * NB;  // [q] |J| w_q mu_q, or [q][NC] |J| w_q C_q, of the current cell
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long v = blockIdx.x;
   int vx, vy, vz;
@@ -96,10 +118,11 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ m
     __syncthreads();
     if (!valid) continue;
     const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
-    for (int q = tid; q < NB; q += nt) {
+    for (int e = tid; e < NB * (TENSOR ? NC : 1); e += nt) {
+      const int q = TENSOR ? e / NC : e;
       const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-      wq[q] = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) *
-              mu[cell * NB + q];
+      wq[e] = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) *
+              coef[cell * NB * (TENSOR ? NC : 1) + e];
     }
     __syncthreads();
     for (int pr = tid; pr < NSUB * NSUB; pr += nt) {
@@ -120,25 +143,65 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ m
       if (!patch_node<DIM>(g, vx, vy, vz, P, ndP) || !patch_node<DIM>(g, vx, vy, vz, Q, ndQ)) continue;
       const int a = ai[0] + 3 * ai[1] + (DIM == 3 ? 9 * ai[2] : 0);
       const int b = aj[0] + 3 * aj[1] + (DIM == 3 ? 9 * aj[2] : 0);
-      double G[DIM][DIM];
+      // viscous block V[al][be] = sum_q |J| w_q (C eps(phi_b e_be)) : eps(phi_a e_al);
+      // scalar mu: 2 mu eps : eps = mu (delta_ab grad phi_a . grad phi_b + d_be phi_a d_al phi_b)
+      double V[DIM][DIM];
       for (int k = 0; k < DIM; ++k)
-        for (int l = 0; l < DIM; ++l) G[k][l] = 0.0;
-      for (int q = 0; q < NB; ++q) {
-        const double w = wq[q];
-        for (int k = 0; k < DIM; ++k) {
-          const double ga = w * gt[(q * NB + a) * DIM + k];
-          for (int l = 0; l < DIM; ++l) G[k][l] += ga * gt[(q * NB + b) * DIM + l];
+        for (int l = 0; l < DIM; ++l) V[k][l] = 0.0;
+      if constexpr (!TENSOR) {
+        double G[DIM][DIM];
+        for (int k = 0; k < DIM; ++k)
+          for (int l = 0; l < DIM; ++l) G[k][l] = 0.0;
+        for (int q = 0; q < NB; ++q) {
+          const double w = wq[q];
+          for (int k = 0; k < DIM; ++k) {
+            const double ga = w * gt[(q * NB + a) * DIM + k];
+            for (int l = 0; l < DIM; ++l) G[k][l] += ga * gt[(q * NB + b) * DIM + l];
+          }
+        }
+        double tr = 0.0;
+        for (int k = 0; k < DIM; ++k) tr += G[k][k];
+        for (int al = 0; al < DIM; ++al)
+          for (int be = 0; be < DIM; ++be) V[al][be] = G[be][al] + (al == be ? tr : 0.0);
+      } else {
+        for (int q = 0; q < NB; ++q) {
+          const double* Cq = wq + q * NC;
+          double eA[DIM][NM], t[DIM][NM];
+          for (int al = 0; al < DIM; ++al) mandel_of<DIM>(al, gt + (q * NB + a) * DIM, eA[al]);
+          for (int be = 0; be < DIM; ++be) {
+            double eB[NM];
+            mandel_of<DIM>(be, gt + (q * NB + b) * DIM, eB);
+            for (int m = 0; m < NM; ++m) t[be][m] = 0.0;
+            int idx = 0;
+            for (int m = 0; m < NM; ++m)
+              for (int n = m; n < NM; ++n) {
+                const double c = Cq[idx++];
+                t[be][m] += c * eB[n];
+                if (n != m) t[be][n] += c * eB[m];
+              }
+          }
+          for (int al = 0; al < DIM; ++al)
+            for (int be = 0; be < DIM; ++be) {
+              double acc = 0.0;
+              for (int m = 0; m < NM; ++m) acc += eA[al][m] * t[be][m];
+              V[al][be] += acc;
+            }
         }
       }
-      double tr = 0.0;
-      for (int k = 0; k < DIM; ++k) tr += G[k][k];
       for (int al = 0; al < DIM; ++al)
         for (int be = 0; be < DIM; ++be) {
-          double val = G[be][al] + (al == be ? tr : 0.0);
+          double val = V[al][be];
           double alv = 0.0;
-          for (int p = 0; p < NPR; ++p)
-            alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
-          val += gamma / vol * alv;
+          if (winv) {   // gamma B_K^T W_K^-1 B_K with W = M_p(1/mu)
+            for (int p = 0; p < NPR; ++p)
+              for (int q2 = 0; q2 < NPR; ++q2)
+                alv += bt[(p * DIM + al) * NB + a] * winv[(cell * NPR + p) * NPR + q2] * bt[(q2 * DIM + be) * NB + b];
+            val += gamma * alv;
+          } else {      // W = M_p = |K| diag(1, 1/3, ..)
+            for (int p = 0; p < NPR; ++p)
+              alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
+            val += gamma / vol * alv;
+          }
           A[(al * NB + P) * NP + be * NB + Q] += val;
         }
     }
@@ -475,9 +538,9 @@ static void launch_patch_tma(const LevelDev& L, int interior, long long count, c
   count_launch(1);
 }
 
-static size_t setup_smem(int dim) {
-  const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1;
-  return sizeof(double) * (NP * NP + 2 * NP + NB * NB * dim + NPR * dim * NB + NB);
+static size_t setup_smem(int dim, bool tensor) {
+  const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1, NC = dim == 2 ? 6 : 21;
+  return sizeof(double) * (NP * NP + 2 * NP + NB * NB * dim + NPR * dim * NB + NB * (tensor ? NC : 1));
 }
 
 template <int DIM>
@@ -485,19 +548,25 @@ static void set_tma_smem() {
   cudaFuncSetAttribute(k_patch_tma<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaCfg<DIM>::smem_bytes);
 }
 
+template <int DIM, bool TENSOR>
+static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
+  const size_t smem = setup_smem(DIM, TENSOR);
+  cudaFuncSetAttribute(k_patch_setup<DIM, TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_patch_setup<DIM, TENSOR><<<(unsigned)L.g.nverts, DIM == 3 ? 256 : 128, smem, s>>>(
+      L.g, gamma, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st, L.winv64);
+  count_launch(1);
+}
+
 void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
   // shared-memory limit of the FP32 patch kernel, set here, before any graph capture
   if (L.g.dim == 2) set_tma_smem<2>(); else set_tma_smem<3>();
-  const size_t smem = setup_smem(L.g.dim);
   if (L.g.dim == 2) {
-    k_patch_setup<2><<<(unsigned)L.g.nverts, 128, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
-                                                             store32 ? L.inv32 : nullptr, L.pstride, st);
+    if (L.tensor) patch_setup_impl<2, true>(L, gamma, store32, st, s);
+    else patch_setup_impl<2, false>(L, gamma, store32, st, s);
   } else {
-    cudaFuncSetAttribute(k_patch_setup<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_patch_setup<3><<<(unsigned)L.g.nverts, 256, smem, s>>>(L.g, gamma, L.mu64, L.inv64,
-                                                              store32 ? L.inv32 : nullptr, L.pstride, st);
+    if (L.tensor) patch_setup_impl<3, true>(L, gamma, store32, st, s);
+    else patch_setup_impl<3, false>(L, gamma, store32, st, s);
   }
-  count_launch(1);
 }
 
 // ---------------------------------------------------------------------------

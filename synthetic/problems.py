@@ -194,3 +194,96 @@ def sinker_3d(n=32, levels=4, gamma=1e4, dr=1e8, seed=0, count=16):
 
 def random_vector(seed, size, lo=-1.0, hi=1.0):
     return np.random.default_rng(seed).uniform(lo, hi, size=size)
+
+
+# ----------------------------------------------------------------------------
+# anisotropic viscoplastic linearisation (tensor viscosity, Eq. (stokes-lin))
+# ----------------------------------------------------------------------------
+def _mandel(eps, d):
+    """Mandel vector of symmetric tensors eps (..., d, d)."""
+    r2 = math.sqrt(2.0)
+    if d == 2:
+        return np.stack([eps[..., 0, 0], eps[..., 1, 1], r2 * eps[..., 0, 1]], -1)
+    return np.stack([eps[..., 0, 0], eps[..., 1, 1], eps[..., 2, 2],
+                     r2 * eps[..., 1, 2], r2 * eps[..., 0, 2], r2 * eps[..., 0, 1]], -1)
+
+
+def fourier_modes(seed, d, count=12, kmax=4):
+    """Seeded wave vectors (|k|_inf <= kmax, nonzero), amplitudes and phases."""
+    rng = np.random.default_rng(seed)
+    ks = []
+    while len(ks) < count:
+        k = rng.integers(-kmax, kmax + 1, size=d)
+        if np.any(k != 0):
+            ks.append(k)
+    ncomp = 1 if d == 2 else 3
+    return np.array(ks, float), rng.standard_normal((count, ncomp)), rng.uniform(0, 2 * math.pi, count)
+
+
+def solenoidal_strain_rate(x, modes):
+    """sym grad v of a divergence-free field: v = (d psi/dy, -d psi/dx) in 2D,
+    v = curl Psi in 3D, with psi / Psi = sum_m A_m cos(2 pi k_m . x + phi_m)."""
+    ks, amps, phases = modes
+    d = x.shape[-1]
+    grad = np.zeros(x.shape[:-1] + (d, d))
+    for k, a, ph in zip(ks, amps, phases):
+        c = np.cos(2 * math.pi * (x @ k) + ph)[..., None, None]
+        if d == 2:
+            # psi Hessian = -(2 pi)^2 a cos k k^T; grad v rows: (psi_yx, psi_yy), (-psi_xx, -psi_xy)
+            h = -(2 * math.pi) ** 2 * a[0] * np.outer(k, k)
+            g = np.array([[h[1, 0], h[1, 1]], [-h[0, 0], -h[0, 1]]])
+        else:
+            # d_j v_i = -(2 pi)^2 cos(theta) (k x A)_i k_j
+            g = -(2 * math.pi) ** 2 * np.outer(np.cross(k, a), k)
+        grad = grad + c * g
+    return 0.5 * (grad + np.swapaxes(grad, -1, -2))
+
+
+def viscoplastic_coefficients(x, modes, scale, tau_y=1.0, alpha_max=0.99, mu_floor=1e-4,
+                              layers=((1.0 / 3.0, 1e6), (2.0 / 3.0, 1e1), (math.inf, 1e-4))):
+    """C = 2 mu_eff [I - alpha (e e^T)/(e.e)] (Mandel, upper triangle row-major) and mu_eff.
+
+    mu_eff = max(mu_floor, min(mu0(x), tau_y / (2 eps_II))), eps_II = (eps:eps / 2)^(1/2),
+    alpha = alpha_max (1 - mu_eff / mu0): anisotropic where the material yields.
+    mu0 is layered along the last coordinate.
+    """
+    d = x.shape[-1]
+    eps = scale * solenoidal_strain_rate(x, modes)
+    e = _mandel(eps, d)
+    ee = (e * e).sum(-1)
+    eii = np.sqrt(0.5 * ee)
+    z = x[..., -1]
+    mu0 = np.full(z.shape, layers[-1][1])
+    for top, val in reversed(layers):
+        mu0 = np.where(z < top, val, mu0)
+    with np.errstate(divide="ignore"):
+        mu_eff = np.maximum(mu_floor, np.minimum(mu0, tau_y / (2.0 * eii)))
+    alpha = alpha_max * (1.0 - mu_eff / mu0)
+    m = e.shape[-1]
+    unit = e / np.sqrt(np.maximum(ee, 1e-300))[..., None]
+    C = 2.0 * mu_eff[..., None, None] * (np.eye(m) - alpha[..., None, None] * unit[..., :, None] * unit[..., None, :])
+    iu = np.triu_indices(m)
+    return np.ascontiguousarray(C[..., iu[0], iu[1]]), np.ascontiguousarray(mu_eff)
+
+
+def viscoplastic_problem(d=3, n=48, levels=4, gamma=1e3, seed=0, rms_strain_rate=1e-4, beta=10.0):
+    """Tensor-viscosity workload: per-point 4th-order C on every level, mu_eff for the
+    Schur block, and a body force f = (0, .., -beta sin(2 pi x)) that is not a gradient."""
+    nn = _as_tuple(n, d)
+    modes = fourier_modes(seed, d)
+    xf = sample_points(d, nn)
+    eps = solenoidal_strain_rate(xf, modes)
+    eii = np.sqrt(0.5 * (_mandel(eps, d) ** 2).sum(-1))
+    scale = rms_strain_rate / math.sqrt((eii ** 2).mean())
+    Cs, mus = [], []
+    for m in level_sizes(nn, levels):
+        C, mu = viscoplastic_coefficients(sample_points(d, m), modes, scale)
+        Cs.append(C)
+        mus.append(mu)
+    f = np.zeros(xf.shape)
+    f[..., -1] = -beta * np.sin(2.0 * math.pi * xf[..., 0])      # not a gradient: drives flow
+    u_bc = np.zeros((d, int(np.prod([2 * v + 1 for v in nn]))))
+    pb = Problem(f"viscoplastic_{d}d", d, nn, levels, float(gamma), Cs, f, u_bc,
+                 {"seed": seed, "scale": scale, "contrast": float(np.max(mus[-1]) / np.min(mus[-1]))})
+    pb.meta["mu_eff"] = mus
+    return pb

@@ -313,3 +313,103 @@ def test_invalid_arguments_and_non_spd():
     with pytest.raises(ALSError):
         ctx.apply_agamma(torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda"),
                          torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda"), level=7)
+
+
+# --------------------------------------------------------------------------
+# a2 through the whole hierarchy: anisotropic tensor viscosity (Eq. (stokes-lin))
+# --------------------------------------------------------------------------
+def _tensor_problem(d, n, levels, gamma, seed=1):
+    from synthetic.problems import viscoplastic_problem
+    return viscoplastic_problem(d, n, levels, gamma=gamma, seed=seed)
+
+
+def _tensor_ctx(pb, **opt):
+    from paper_2107_00820_gb300 import Context
+    return Context(pb.d, pb.n, pb.levels, pb.mu, pb.gamma, mu_eff=pb.meta["mu_eff"], **opt)
+
+
+def _tensor_oracle(pb, **kw):
+    from oracle.mg import Hierarchy
+    return Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, kind="tensor", mu_eff=pb.meta["mu_eff"], **kw)
+
+
+@pytest.mark.parametrize("d,n", [(2, 12), (3, 4)])
+def test_tensor_patch_inverses_sampled(d, n):
+    pb = _tensor_problem(d, n, 2, 1e2)
+    ctx = _tensor_ctx(pb)
+    H = _tensor_oracle(pb, smoother="richardson", steps=1)
+    m = H.levels[1].mesh
+    verts = all_vertices(m)
+    NB = 3 ** d
+    for vid in list(np.random.default_rng(2).choice(len(verts), size=10, replace=False)) + [0]:
+        v = verts[vid]
+        cond, idx, Av = _patch_cond(H, 1, v)
+        full = ctx.patch_inverse(1, int(vid))
+        keep = [a * NB + o for a in range(d) for o in range(NB)
+                if np.all((g := 2 * v + (np.array([o % 3, (o // 3) % 3, o // 9][:d]) - 1)) > 0)
+                and np.all(g < np.array(m.nn) - 1)]
+        got = full[np.ix_(keep, keep)]
+        ref = np.linalg.inv(Av)
+        assert np.linalg.norm(got - ref) <= max(1e-12, 20 * cond * 2.2e-16) * np.linalg.norm(ref), (vid, cond)
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, 24, 3), (3, 8, 2)])
+def test_tensor_vcycle_fp64(d, n, levels):
+    pb = _tensor_problem(d, n, levels, 1e2)
+    ctx = _tensor_ctx(pb, sweeps=2)
+    H = _tensor_oracle(pb, steps=2)
+    b = random_free(H.levels[-1], 3)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    ref = H.vcycle(b)
+    cond = _max_patch_cond(H, levels - 1, count=20)
+    assert rel(host(x), ref) <= max(1e-11, 100 * cond * 2.2e-16), cond
+
+
+@pytest.mark.parametrize("d,n,levels,gamma", [(2, 24, 3, 1e3), (3, 6, 2, 1e2)])
+def test_tensor_solve_fp64_and_mixed(d, n, levels, gamma):
+    pb = _tensor_problem(d, n, levels, gamma)
+    from oracle.stokes import StokesSolver
+    uo, po, its, _ = StokesSolver(_tensor_oracle(pb)).solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = _tensor_ctx(pb, rtol=1e-8).solve(pb.f, pb.u_bc)
+    assert info.converged and abs(info.iterations - its) <= 1, (info.iterations, its)
+    assert rel(u, uo) <= 1e-7 and rel(p, po) <= 1e-5
+    pb10 = _tensor_problem(d, n, levels, 10.0)
+    _, _, i64 = _tensor_ctx(pb10, rtol=1e-8).solve(pb10.f, pb10.u_bc)
+    um, pm, im = _tensor_ctx(pb10, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb10.f, pb10.u_bc)
+    assert im.converged and im.iterations <= i64.iterations + 2
+
+
+# --------------------------------------------------------------------------
+# P2 (Eq. (P1P2)): W = M_p(1/mu) in the augmentation and S^-1 ~ (1 + gamma) M_p(1/mu)^-1
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 4)])
+def test_apply_agamma_w_mu_fp64(d, n):
+    pb = sinker(d, n, 2, 1e3, dr=1e6, seed=5)
+    ctx = context(pb, schur=A.ALS_SCHUR_P2)
+    H = oracle(pb, smoother="richardson", steps=1, W="Mp_mu")
+    for lvl in range(2):
+        lv = H.levels[lvl]
+        x = np.random.default_rng(lvl + 7).standard_normal(lv.mesh.nu)
+        y = torch.zeros(lv.mesh.nu, dtype=torch.float64, device="cuda")
+        ctx.apply_agamma(dev(x), y, lvl)
+        assert rel(host(y), lv.A @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, 16, 3), (3, 8, 2)])
+def test_solve_p2_fp64_matches_oracle(d, n, levels):
+    pb = sinker(d, n, levels, 1e2, dr=1e4, seed=9)
+    s = StokesSolver(oracle(pb, W="Mp_mu"), schur="P2")
+    uo, po, its, _ = s.solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8).solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its, (info.iterations, its)
+    assert rel(u, uo) <= 1e-8 and rel(p, po) <= 1e-7
+
+
+def test_mixed_p2_at_extreme_contrast_and_gamma():
+    """With W = M_p(1/mu) the AL term scales with mu, so the FP32 V-cycle keeps
+    working where the P1 pairing (W = M_p) loses it (gamma / mu_min = 1e7)."""
+    pb = sinker(3, 8, 2, 1e3, dr=1e8, seed=11)
+    _, _, i64 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8).solve(pb.f, pb.u_bc)
+    u32, p32, i32 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
+    assert i64.converged and i32.converged and i32.iterations <= i64.iterations + 2, (i32.iterations, i64.iterations)
