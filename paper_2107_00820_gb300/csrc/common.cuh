@@ -84,20 +84,24 @@ __host__ __device__ constexpr int packed_stride(int np) { return (packed_size(np
 // "Block-packed" storage of the same symmetric NP x NP matrix (NP = 9 NBR), used
 // for the FP32 inverses: 9x9 blocks (I, J), I <= J, numbered off-diagonal blocks
 // first (row-major over I < J), then the NBR diagonal blocks.  Element e of a
-// block is r*9 + c (off-diagonal) or the row-major index of (r, c), r <= c, in
-// the 45-entry upper triangle (diagonal).  Elements e < 45 of all NBP blocks are
-// stored first, interleaved by block (e * NBP + b), then elements 45..80 of the
-// off-diagonal blocks (45 NBP + (e - 45) NOFF + b): thread b of a patch reads
-// consecutive words.  The total is still NP (NP + 1) / 2 entries.
+// block is r*9 + c (off-diagonal, 81 entries) or the row-major index of (r, c),
+// r <= c, in the 45-entry upper triangle (diagonal).  Storage is interleaved by
+// block in 16-byte quads so that thread b of a patch reads consecutive 16-byte
+// words: elements 0..43 of all NBP blocks as 11 quads (quad q of block b at
+// 4 (q NBP + b)), then element 44 of all blocks (padded to a multiple of 4
+// floats), then elements 45..80 of the off-diagonal blocks as 9 quads.  The
+// total is NP (NP + 1) / 2 entries plus that padding (= packed_stride(NP)).
 struct BlockLayout {
-  int nbr, nbp, noff;
+  int nbr, nbp, noff, q2;
   __host__ __device__ constexpr explicit BlockLayout(int np)
-      : nbr(np / 9), nbp((np / 9) * (np / 9 + 1) / 2), noff((np / 9) * (np / 9 - 1) / 2) {}
+      : nbr(np / 9), nbp((np / 9) * (np / 9 + 1) / 2), noff((np / 9) * (np / 9 - 1) / 2),
+        q2(44 * ((np / 9) * (np / 9 + 1) / 2) + ((((np / 9) * (np / 9 + 1) / 2) + 3) & ~3)) {}
   __host__ __device__ constexpr int offdiag(int I, int J) const {  // I < J
     return I * (nbr - 1) - (I * (I - 1)) / 2 + (J - I - 1);
   }
   __host__ __device__ constexpr int slot(int e, int b) const {
-    return e < 45 ? e * nbp + b : 45 * nbp + (e - 45) * noff + b;
+    return e < 44 ? 4 * ((e >> 2) * nbp + b) + (e & 3)
+                  : (e == 44 ? 44 * nbp + b : q2 + 4 * (((e - 45) >> 2) * noff + b) + ((e - 45) & 3));
   }
   // position of entry (i, j), i <= j
   __host__ __device__ constexpr int index(int i, int j) const {

@@ -13,6 +13,7 @@
 // one thread per node sums the <= 2^d patch values that contain it in a fixed
 // order (no floating-point atomics).
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -242,6 +243,10 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
   }
   // A^-1 (symmetrised), packed by diagonals in FP64 and block-packed in FP32
   constexpr int NPK = NP * (NP + 1) / 2;
+  if (inv32) {
+    constexpr BlockLayout BLp = BlockLayout(NP);
+    for (int e = 44 * BLp.nbp + BLp.nbp + tid; e < BLp.q2; e += nt) inv32[v * pstride + e] = 0.f;
+  }
   for (int e = tid; e < NPK; e += nt) {
     int t = 0;
     while (diag_start(NP, t + 1) <= e) ++t;
@@ -307,24 +312,96 @@ __device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.
 
 enum PatchOut { OUT_SCRATCH = 0, OUT_WRITE = 1, OUT_SUBTRACT = 2 };
 
-template <int DIM>
+// S_IJ r_J -> yI and S_IJ^T r_I -> yJ for block b of one block-packed patch at S
+// (global or shared memory).  Diagonal blocks use the symmetric upper triangle.
+template <bool GLOBAL>
+__device__ __forceinline__ float4 ld4(const float* p) {
+  if constexpr (GLOBAL) return __ldg(reinterpret_cast<const float4*>(p));
+  else return *reinterpret_cast<const float4*>(p);
+}
+template <bool GLOBAL>
+__device__ __forceinline__ float ld1(const float* p) {
+  if constexpr (GLOBAL) return __ldg(p);
+  else return *p;
+}
+
+template <bool GLOBAL>
+__device__ __forceinline__ void block_product(const BlockLayout& BL, const float* __restrict__ S, int b, bool diag,
+                                              const float (&rI)[9], const float (&rJ)[9], float (&yI)[9],
+                                              float (&yJ)[9]) {
+  float e[84];
+#pragma unroll
+  for (int q = 0; q < 11; ++q) {
+    const float4 v = ld4<GLOBAL>(S + 4 * (q * BL.nbp + b));
+    e[4 * q] = v.x; e[4 * q + 1] = v.y; e[4 * q + 2] = v.z; e[4 * q + 3] = v.w;
+  }
+  e[44] = ld1<GLOBAL>(S + 44 * BL.nbp + b);
+  if (!diag) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const float4 v = ld4<GLOBAL>(S + BL.q2 + 4 * (q * BL.noff + b));
+      e[45 + 4 * q] = v.x; e[46 + 4 * q] = v.y; e[47 + 4 * q] = v.z; e[48 + 4 * q] = v.w;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { yI[k] = 0.f; yJ[k] = 0.f; }
+  if (diag) {
+#pragma unroll
+    for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+      for (int cc = rr; cc < 9; ++cc) {
+        const float sv = e[rr * 9 - (rr * (rr - 1)) / 2 + (cc - rr)];
+        yI[rr] += sv * rI[cc];
+        if (cc != rr) yI[cc] += sv * rI[rr];
+      }
+  } else {
+    float yI2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) yI2[k] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 9; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) {
+        const float sv = e[rr * 9 + cc];
+        if (cc & 1) yI2[rr] += sv * rJ[cc];   // two independent partial sums per row
+        else yI[rr] += sv * rJ[cc];
+        yJ[cc] += sv * rI[rr];
+      }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) yI[k] += yI2[k];
+  }
+}
+
+__device__ __forceinline__ void block_of(const BlockLayout& BL, int b, int& I, int& J, bool& diag) {
+  diag = b >= BL.noff;
+  I = 0;
+  J = 0;
+  if (diag) {
+    I = J = b - BL.noff;
+  } else {
+    int rem = b;
+    while (rem >= BL.nbr - 1 - I) { rem -= BL.nbr - 1 - I; ++I; }
+    J = I + 1 + rem;
+  }
+}
+
+template <int DIM, int NST>
 struct TmaCfg {
   static constexpr int NP = Sz<DIM>::NP;
   static constexpr int NB = Sz<DIM>::NB;
   static constexpr int THREADS = 64;
   static constexpr int TPP = DIM == 3 ? 64 : 4;        // threads per patch (>= blocks per patch)
   static constexpr int PPI = THREADS / TPP;            // patches per iteration
-  static constexpr int NSTAGE = 3;
+  static constexpr int NSTAGE = NST;
   static constexpr int STRIDE = packed_stride(NP);     // floats per patch
-  static constexpr BlockLayout BL = BlockLayout(NP);
-  static constexpr int NBP = (NP / 9) * (NP / 9 + 1) / 2;
+  static constexpr int NBR = NP / 9;
   static constexpr int RPT = (PPI * NP + THREADS - 1) / THREADS;   // r values gathered per thread
   static constexpr size_t stage_floats = (size_t)PPI * STRIDE;
-  // dynamic shared memory: [mbarriers | stages | r | partials]; the barriers need
-  // 8-byte and the bulk-copy destinations 16-byte alignment
+  // dynamic shared memory: [mbarriers | stages | r (x2) | partials (x2)]; the barriers
+  // need 8-byte and the bulk-copy destinations 16-byte alignment
   static constexpr size_t bar_bytes = 128;
   static constexpr size_t smem_bytes =
-      bar_bytes + NSTAGE * stage_floats * 4 + (size_t)PPI * NP * 4 + (size_t)PPI * 18 * NBP * 4;
+      bar_bytes + NSTAGE * stage_floats * 4 + 2 * (size_t)PPI * NP * 4 + 2 * (size_t)PPI * NP * NBR * 4;
   static_assert(NSTAGE * 8 <= bar_bytes, "mbarrier area too small");
   static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
 };
@@ -361,24 +438,26 @@ __device__ __forceinline__ float patch_r(const Geom& g, const float* __restrict_
   return patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
 }
 
-template <int DIM>
+template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
                                                   DevStatus* st) {
-  using C = TmaCfg<DIM>;
-  constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBP = C::NBP;
+  using C = TmaCfg<DIM, NST>;
+  constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
-  constexpr BlockLayout BL = C::BL;
+  constexpr BlockLayout BL = BlockLayout(NP);
+  constexpr int ISSUER = THREADS - 1;                     // idle in the block phase (b >= NBP)
+  static_assert(ISSUER % TPP >= BlockLayout(NP).nbp, "the issuing thread must not own a block");
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
   float* stages = reinterpret_cast<float*>(smraw + C::bar_bytes);
-  float* rs = stages + NSTAGE * C::stage_floats;          // [PPI][NP]
-  float* part = rs + PPI * NP;                            // [PPI][18][NBP]
+  float* rsb = stages + NSTAGE * C::stage_floats;         // [2][PPI][NP]
+  float* partb = rsb + 2 * PPI * NP;                      // [2][PPI][NP][NBR]
   __shared__ int s_fail;
   const int tid = threadIdx.x;
   const int ngroups = (count + PPI - 1) / PPI;
 
-  auto issue = [&](int grp, int stage) {   // thread 0: one bulk copy per patch of the group
+  auto issue = [&](int grp, int stage) {   // one bulk copy per patch of the group
     uint32_t bytes = 0;
     int vids[PPI];
     for (int ps = 0; ps < PPI; ++ps) {
@@ -392,7 +471,6 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
         tma::bulk_load(stages + stage * C::stage_floats + (size_t)ps * C::STRIDE,
                        inv + (long long)vids[ps] * C::STRIDE, C::STRIDE * 4, &bars[stage]);
   };
-  // r values of group grp handled by this thread: elements tid + k THREADS
   auto gather = [&](int grp, float (&v)[RPT]) {
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -406,13 +484,13 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     }
   };
 
-  if (tid == 0) {
+  if (tid == ISSUER) {
     s_fail = 0;
     for (int i = 0; i < NSTAGE; ++i) tma::mbar_init(&bars[i], 1);
     tma::fence_init();
   }
   __syncthreads();
-  if (tid == 0)
+  if (tid == ISSUER)
     for (int i = 0; i < NSTAGE; ++i) {
       const int grp = blockIdx.x + i * gridDim.x;
       if (grp < ngroups) issue(grp, i);
@@ -421,10 +499,15 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   gather(blockIdx.x, rpre);
 
   const int ps = tid / TPP, b = tid % TPP;
+  int I = 0, J = 0;
+  bool diag = false;
+  if (b < BL.nbp) block_of(BL, b, I, J, diag);
   int it = 0;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
-    const int stage = it % NSTAGE;
+    const int stage = it % NSTAGE, buf = it & 1;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
+    float* rs = rsb + buf * PPI * NP;
+    float* part = partb + buf * PPI * NP * NBR;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int e = tid + k * THREADS;
@@ -432,78 +515,44 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     }
     gather(grp + gridDim.x, rpre);          // next group's r: in flight while this one is computed
     if (!tma::mbar_wait(&bars[stage], parity)) {
-      if (tid == 0) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
+      if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
     }
-    __syncthreads();
+    __syncthreads();                        // (A) r and the stage are visible
     if (s_fail) break;
-    // block products
-    const float* S = stages + stage * C::stage_floats + (size_t)ps * C::STRIDE;
-    if (b < NBP) {
-      const bool diag = b >= BL.noff;
-      int I = 0, J = 0;
-      if (diag) {
-        I = J = b - BL.noff;
-      } else {
-        int rem = b;
-        while (rem >= BL.nbr - 1 - I) { rem -= BL.nbr - 1 - I; ++I; }
-        J = I + 1 + rem;
-      }
+    if (b < BL.nbp) {
+      const float* S = stages + stage * C::stage_floats + (size_t)ps * C::STRIDE;
       float rI[9], rJ[9], yI[9], yJ[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         rI[k] = rs[ps * NP + 9 * I + k];
         rJ[k] = rs[ps * NP + 9 * J + k];
-        yI[k] = 0.f;
-        yJ[k] = 0.f;
       }
-      if (diag) {
+      block_product<false>(BL, S, b, diag, rI, rJ, yI, yJ);
+      float* pp = part + ps * NP * NBR;
 #pragma unroll
-        for (int rr = 0; rr < 9; ++rr)
+      for (int k = 0; k < 9; ++k) pp[(9 * I + k) * NBR + J] = yI[k];
+      if (!diag) {
 #pragma unroll
-          for (int cc = rr; cc < 9; ++cc) {
-            const int e = rr * 9 - (rr * (rr - 1)) / 2 + (cc - rr);
-            const float sv = S[BL.slot(e, b)];
-            yI[rr] += sv * rI[cc];
-            if (cc != rr) yI[cc] += sv * rI[rr];
-          }
-      } else {
-#pragma unroll
-        for (int rr = 0; rr < 9; ++rr)
-#pragma unroll
-          for (int cc = 0; cc < 9; ++cc) {
-            const float sv = S[BL.slot(rr * 9 + cc, b)];
-            yI[rr] += sv * rJ[cc];
-            yJ[cc] += sv * rI[rr];
-          }
-      }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        part[(ps * 18 + k) * NBP + b] = yI[k];
-        part[(ps * 18 + 9 + k) * NBP + b] = yJ[k];
+        for (int k = 0; k < 9; ++k) pp[(9 * J + k) * NBR + I] = yJ[k];
       }
     }
-    __syncthreads();
-    // the stage is consumed: refill it NSTAGE groups ahead while the partials are reduced
-    if (tid == 0) {
+    __syncthreads();                        // (B) the stage is consumed, the partials are complete
+    if (tid == ISSUER) {                    // refill the stage NSTAGE groups ahead
       const int nxt = grp + NSTAGE * gridDim.x;
       if (nxt < ngroups) {
         tma::fence_async();
         issue(nxt, stage);
       }
     }
-    // y_i = sum over the blocks of row-block I, fixed order J = 0..NBR-1
+    // y_i = sum_J partial(i, J), fixed order
     for (int e = tid; e < PPI * NP; e += THREADS) {
       const int p = e / NP, i = e % NP;
       int vx, vy, vz;
       const int v = work_vertex<DIM>(g, interior, grp * PPI + p, count, vx, vy, vz);
       if (v < 0) continue;
-      const int I = i / 9, rr = i % 9;
       float acc = 0.f;
-      for (int J = 0; J < BL.nbr; ++J) {
-        if (J == I) acc += part[(p * 18 + rr) * NBP + BL.noff + I];
-        else if (J > I) acc += part[(p * 18 + rr) * NBP + BL.offdiag(I, J)];
-        else acc += part[(p * 18 + 9 + rr) * NBP + BL.offdiag(J, I)];
-      }
+#pragma unroll
+      for (int jb = 0; jb < NBR; ++jb) acc += part[(p * NP + i) * NBR + jb];
       if (mode == OUT_SCRATCH) {
         out[(long long)v * NP + i] = acc;
       } else {
@@ -514,9 +563,10 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
         }
       }
     }
-    __syncthreads();
+    // no third barrier: r and the partials are double-buffered, and iteration it+2
+    // rewrites these buffers only after every thread has passed barrier (A) of it+1
   }
-  if (s_fail && tid == 0) {
+  if (s_fail && tid == ISSUER) {
     // drain: wait (bounded) for every copy this CTA issued and did not consume
     int k = it;
     for (int grp = blockIdx.x + it * gridDim.x; grp < ngroups && k < it + NSTAGE; grp += gridDim.x, ++k)
@@ -524,17 +574,125 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// K4 (FP32), direct variant: each thread streams its 9x9 block of the
+// block-packed inverse straight from global memory with coalesced 16-byte
+// loads (thread b of a patch reads consecutive words), gathers its r_I, r_J
+// itself, and the block partials are reduced through double-buffered shared
+// memory: one barrier per iteration, 2 (3D) or 32 (2D) patches per 128-thread CTA.
+// ---------------------------------------------------------------------------
+template <int DIM>
+struct DirCfg {
+  static constexpr int NP = Sz<DIM>::NP;
+  static constexpr int THREADS = 128;
+  static constexpr int TPP = DIM == 3 ? 64 : 4;
+  static constexpr int PPC = THREADS / TPP;
+  static constexpr int NBR = NP / 9;
+  static constexpr int STRIDE = packed_stride(NP);
+};
+
+// r at entry 9*IB + k (k < 9) of the patch of vertex (vx, vy, vz)
+template <int DIM>
+__device__ __forceinline__ void gather9(const Geom& g, const float* __restrict__ r, int vx, int vy, int vz, int IB,
+                                        float (&out)[9]) {
+  constexpr int NB = Sz<DIM>::NB;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int i = 9 * IB + k;
+    long long nd;
+    out[k] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __restrict__ inv, int interior, int count,
+                                                      const float* __restrict__ r, float* __restrict__ out,
+                                                      int mode) {
+  using C = DirCfg<DIM>;
+  constexpr int NP = C::NP, NB = Sz<DIM>::NB, PPC = C::PPC, TPP = C::TPP, NBR = C::NBR;
+  constexpr BlockLayout BL = BlockLayout(NP);
+  __shared__ float part[2][PPC][NP][NBR];
+  const int tid = threadIdx.x, ps = tid / TPP, b = tid % TPP;
+  const int ngroups = (count + PPC - 1) / PPC;
+  int buf = 0;
+  int I = 0, J = 0;
+  bool diag = false;
+  if (b < BL.nbp) block_of(BL, b, I, J, diag);
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
+    if (b < BL.nbp) {
+      int vx, vy, vz;
+      const int v = work_vertex<DIM>(g, interior, grp * PPC + ps, count, vx, vy, vz);
+      if (v >= 0) {
+        float rI[9], rJ[9], yI[9], yJ[9];
+        gather9<DIM>(g, r, vx, vy, vz, I, rI);
+        gather9<DIM>(g, r, vx, vy, vz, J, rJ);
+        block_product<true>(BL, inv + (long long)v * C::STRIDE, b, diag, rI, rJ, yI, yJ);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) part[buf][ps][9 * I + k][J] = yI[k];
+        if (!diag) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) part[buf][ps][9 * J + k][I] = yJ[k];
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < PPC * NP; e += C::THREADS) {
+      const int p = e / NP, i = e % NP;
+      int vx, vy, vz;
+      const int v = work_vertex<DIM>(g, interior, grp * PPC + p, count, vx, vy, vz);
+      if (v < 0) continue;
+      float acc = 0.f;
+#pragma unroll
+      for (int jb = 0; jb < NBR; ++jb) acc += part[buf][p][i][jb];
+      if (mode == OUT_SCRATCH) {
+        out[(long long)v * NP + i] = acc;
+      } else {
+        long long nd;
+        if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
+          float* o = out + (i / NB) * g.N + nd;
+          *o = mode == OUT_SUBTRACT ? *o - acc : acc;
+        }
+      }
+    }
+  }
+}
+
+template <int DIM>
+static void launch_patch_direct(const LevelDev& L, int interior, long long count, const float* r, float* out, int mode,
+                                cudaStream_t s) {
+  using C = DirCfg<DIM>;
+  const long long groups = (count + C::PPC - 1) / C::PPC;
+  const long long cap = 152LL * 8;
+  const long long grid = groups < cap ? groups : cap;
+  if (grid <= 0) return;
+  k_patch_direct<DIM><<<(unsigned)grid, C::THREADS, 0, s>>>(L.g, L.inv32, interior, (int)count, r, out, mode);
+  count_launch(1);
+}
+
+// FP32 patch products: the TMA-staged kernel, or the direct-load one when the
+// environment sets ALS_PATCH_KERNEL=direct
+static bool use_direct_patch_kernel() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("ALS_PATCH_KERNEL");
+    v = (e && e[0] == 'd') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+constexpr int kTmaStages = 2;
+
 template <int DIM>
 static void launch_patch_tma(const LevelDev& L, int interior, long long count, const float* r, float* out, int mode,
                              DevStatus* st, cudaStream_t s) {
-  using C = TmaCfg<DIM>;
+  using C = TmaCfg<DIM, kTmaStages>;
   const long long groups = (count + C::PPI - 1) / C::PPI;
   const long long per_sm = (227 * 1024) / (long long)(C::smem_bytes + 1024);   // resident CTAs per SM
   const long long cap = 152 * (per_sm < 1 ? 1 : per_sm);
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  k_patch_tma<DIM><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count, r, out,
-                                                                     mode, st);
+  k_patch_tma<DIM, kTmaStages><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count,
+                                                                                 r, out, mode, st);
   count_launch(1);
 }
 
@@ -545,7 +703,8 @@ static size_t setup_smem(int dim, bool tensor) {
 
 template <int DIM>
 static void set_tma_smem() {
-  cudaFuncSetAttribute(k_patch_tma<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaCfg<DIM>::smem_bytes);
+  cudaFuncSetAttribute(k_patch_tma<DIM, kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaCfg<DIM, kTmaStages>::smem_bytes);
 }
 
 template <int DIM, bool TENSOR>
@@ -673,7 +832,10 @@ template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
                        cudaEvent_t e1) {
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+  if (use_direct_patch_kernel())
+    launch_patch_direct<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, s);
+  else
+    launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   const long long tot = L.g.N * DIM;
   k_patch_gather<float, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z);
@@ -747,10 +909,14 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
   } else {
     const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2) * (fine.g.dim == 3 ? fine.g.n[2] / 2 : 1);
     if (!subtract) cudaMemsetAsync(out, 0, sizeof(float) * fine.g.N * fine.g.dim, s);
-    if (fine.g.dim == 2)
-      launch_patch_tma<2>(fine, 1, nc, (const float*)in, (float*)out, subtract ? OUT_SUBTRACT : OUT_WRITE, fine.status, s);
-    else
-      launch_patch_tma<3>(fine, 1, nc, (const float*)in, (float*)out, subtract ? OUT_SUBTRACT : OUT_WRITE, fine.status, s);
+    const int md = subtract ? OUT_SUBTRACT : OUT_WRITE;
+    if (use_direct_patch_kernel()) {
+      if (fine.g.dim == 2) launch_patch_direct<2>(fine, 1, nc, (const float*)in, (float*)out, md, s);
+      else launch_patch_direct<3>(fine, 1, nc, (const float*)in, (float*)out, md, s);
+    } else {
+      if (fine.g.dim == 2) launch_patch_tma<2>(fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
+      else launch_patch_tma<3>(fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
+    }
   }
 }
 
