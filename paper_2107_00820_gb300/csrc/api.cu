@@ -50,7 +50,7 @@ struct Prof {
 // offsets into the per-level small workspace of the GMRES smoother
 struct SmallLayout {
   int s, ldh;
-  size_t H, cs, sn, g, y, res, beta, nrm2, total;
+  size_t H, cs, sn, g, y, res, beta, nrm2, hn, total;
   explicit SmallLayout(int steps) : s(steps), ldh(steps + 1) {
     H = 0;
     cs = H + (size_t)ldh * s;
@@ -60,7 +60,11 @@ struct SmallLayout {
     res = y + s;
     beta = res + 1;
     nrm2 = beta + 1;
-    total = nrm2 + 1;
+    hn = nrm2 + 1;
+    total = hn + s + 1;
+  }
+  GmresDev dev(double* base) const {
+    return GmresDev{base + H, ldh, base + cs, base + sn, base + g, base + res, base + hn, base + beta, s + 1};
   }
 };
 
@@ -180,8 +184,10 @@ als_status alloc_work(als_ctx* c, MGWork& w, int prec) {
       ALS_TRY(dalloc(c, &w.small[l], sl.total));
     }
   }
-  ALS_TRY(dalloc(c, &w.partial, multidot_partial_doubles(std::max(s + 1, 8))));
-  cudaMemsetAsync(w.partial, 0, sizeof(double) * multidot_partial_doubles(std::max(s + 1, 8)), c->stream);
+  const size_t npart = std::max(multidot_partial_doubles(std::max(s + 1, 8)),
+                                 gmres_partial_doubles(c->lev[c->L - 1].g.N * c->dim));
+  ALS_TRY(dalloc(c, &w.partial, npart));
+  cudaMemsetAsync(w.partial, 0, sizeof(double) * npart, c->stream);
   return ALS_OK;
 }
 
@@ -229,7 +235,45 @@ inline char* vptr(void* base, size_t es, long long off) { return (char*)base + e
 
 static thread_local int t_prof_counter = 0;
 
-void smooth(als_ctx* c, MGWork& w, int l) {
+// GMRES(s) smoothing with the fused kernels: the basis is stored unnormalised
+// (column i = hn[i] v_i), the dots ride on the operator's gather, the
+// Gram-Schmidt update carries the Givens step, and the final update also forms
+// the residual b - A x from the Arnoldi relation when `t` is given.
+bool fused_gmres(const als_ctx* c) {
+  return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB;
+}
+
+void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
+  const LevelDev& Lv = c->lev[l];
+  const int prec = w.prec;
+  const long long len = Lv.g.N * c->dim;
+  const cudaStream_t s = c->stream;
+  const int steps = std::max(1, c->opt.sweeps);
+  SmallLayout sl(steps);
+  double* sm = w.small[l];
+  const GmresDev st = sl.dev(sm);
+  void* V0 = w.V[l];
+  if (x_is_zero) {
+    gm_start(prec, len, w.b[l], V0, w.partial, st, s);                   // V0 = b
+  } else {
+    ApplyEpi e{w.b[l], -1.0, 0, nullptr, 0, nullptr, 1, st, w.partial};
+    op_apply_epi(Lv, prec, c->gamma, w.x[l], V0, e, s);                  // V0 = b - A x
+  }
+  for (int j = 0; j < steps; ++j) {
+    void* Vj = vptr(w.V[l], w.es, (long long)j * len);
+    void* Vn = vptr(w.V[l], w.es, (long long)(j + 1) * len);
+    void* Zj = vptr(w.Z[l], w.es, (long long)j * len);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
+    patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, st.hn + j);  // Z_j = D^-1 v_j
+    ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, st.H + (size_t)j * sl.ldh, 0, st, w.partial};
+    op_apply_epi(Lv, prec, c->gamma, Zj, Vn, e, s);                      // A Z_j, H[0..j][j]
+    gm_orth(prec, len, j, w.V[l], len, w.partial, st, s);                 // V_{j+1}, Givens step j
+  }
+  gm_update(prec, len, steps, w.Z[l], w.V[l], len, st, w.x[l], x_is_zero ? 1 : 0, t, s);
+}
+
+void smooth(als_ctx* c, MGWork& w, int l, bool x_is_zero = false) {
   const LevelDev& Lv = c->lev[l];
   const int prec = w.prec;
   const long long len = Lv.g.N * c->dim;
@@ -250,8 +294,12 @@ void smooth(als_ctx* c, MGWork& w, int l) {
   SmallLayout sl(steps);
   double* sm = w.small[l];
   void* V0 = w.V[l];
-  op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, w.x[l], V0, nullptr, nullptr, s);
-  vec_axpby(prec, len, 1.0, w.b[l], -1.0, V0, s);                        // V0 = b - A x
+  if (x_is_zero) {
+    vec_axpby(prec, len, 1.0, w.b[l], 0.0, V0, s);                       // V0 = b (x = 0)
+  } else {
+    op_apply(Lv, prec, OP_VISC | OP_AL, c->gamma, w.x[l], V0, nullptr, nullptr, s);
+    vec_axpby(prec, len, 1.0, w.b[l], -1.0, V0, s);                      // V0 = b - A x
+  }
   vec_multidot(prec, len, 1, V0, len, V0, sm + sl.nrm2, w.partial, s);
   dev_init_g(steps + 1, sm + sl.nrm2, sm + sl.g, sm + sl.beta, s);
   vec_scale_dev(prec, len, nullptr, sm + sl.beta, V0, V0, s);
@@ -277,29 +325,26 @@ void smooth(als_ctx* c, MGWork& w, int l) {
 void restrict_level(als_ctx* c, MGWork& w, int l, const void* rf, void* rc) {
   const LevelDev& F = c->lev[l];
   const LevelDev& C = c->lev[l - 1];
-  const long long len = F.g.N * c->dim;
   const cudaStream_t s = c->stream;
   if (c->opt.transfer == ALS_TRANSFER_ROBUST) {
-    // t2 = sum_K E_K A_K^-1 E_K^T rf ; t3 = G t2 ; t2 = rf - t3
+    // t2 = sum_K E_K A_K^-1 E_K^T rf ; t3 = G t2 ; rc = P_H^T (rf - t3)
     patch_interior_solve(F, w.prec, rf, w.t2[l], 0, s);
     op_apply(F, w.prec, OP_AL, c->gamma, w.t2[l], w.t3[l], nullptr, nullptr, s);
-    vec_axpby(w.prec, len, 1.0, rf, 0.0, w.t2[l], s);
-    vec_axpby(w.prec, len, -1.0, w.t3[l], 1.0, w.t2[l], s);
-    restrict_std(C, F, w.prec, w.t2[l], rc, s);
+    restrict_std(C, F, w.prec, rf, rc, s, w.t3[l]);                        // P_H^T (rf - t3)
   } else {
     restrict_std(C, F, w.prec, rf, rc, s);
   }
 }
 
-// xf = P~ xc  (xf overwritten)
-void prolong_level(als_ctx* c, MGWork& w, int l, const void* xc, void* xf) {
+// x += P~ xc with t as scratch for P_H xc; x == NULL: t = P~ xc
+void prolong_level(als_ctx* c, MGWork& w, int l, const void* xc, void* t, void* x) {
   const LevelDev& F = c->lev[l];
   const LevelDev& C = c->lev[l - 1];
   const cudaStream_t s = c->stream;
-  prolong_std(C, F, w.prec, xc, xf, s);
+  prolong_std(C, F, w.prec, xc, t, s, x);                                     // t = P_H xc, x += t
   if (c->opt.transfer == ALS_TRANSFER_ROBUST) {
-    op_apply(F, w.prec, OP_AL, c->gamma, xf, w.t3[l], nullptr, nullptr, s);   // t3 = G P_H xc
-    patch_interior_solve(F, w.prec, w.t3[l], xf, 1, s);                       // xf -= sum_K E A^-1 E^T t3
+    op_apply(F, w.prec, OP_AL, c->gamma, t, w.t3[l], nullptr, nullptr, s);    // t3 = G P_H xc
+    patch_interior_solve(F, w.prec, w.t3[l], x ? x : t, 1, s);                // -= sum_K E A^-1 E^T t3
   }
 }
 
@@ -311,15 +356,19 @@ void vcycle_level(als_ctx* c, MGWork& w, int l) {
   }
   const LevelDev& Lv = c->lev[l];
   const long long len = Lv.g.N * c->dim;
-  vec_zero(w.prec, len, w.x[l], s);
-  smooth(c, w, l);
-  op_apply(Lv, w.prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
-  vec_axpby(w.prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                  // t = b - A x
+  if (fused_gmres(c)) {
+    smooth_fused(c, w, l, true, w.t[l]);                                 // x, and t = b - A x
+  } else {
+    vec_zero(w.prec, len, w.x[l], s);
+    smooth(c, w, l, c->opt.smoother == ALS_SMOOTH_GMRES);
+    op_apply(Lv, w.prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
+    vec_axpby(w.prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                // t = b - A x
+  }
   restrict_level(c, w, l, w.t[l], w.b[l - 1]);
   vcycle_level(c, w, l - 1);
-  prolong_level(c, w, l, w.x[l - 1], w.t[l]);
-  vec_axpby(w.prec, len, 1.0, w.t[l], 1.0, w.x[l], s);                   // x += P~ e_c
-  smooth(c, w, l);
+  prolong_level(c, w, l, w.x[l - 1], w.t[l], w.x[l]);                  // x += P~ e_c
+  if (fused_gmres(c)) smooth_fused(c, w, l, false, nullptr);
+  else smooth(c, w, l);
 }
 
 cudaEvent_t prof_take(als_ctx* c) {
@@ -559,6 +608,14 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
       return fail(c, ALS_EINVAL, "n must be divisible by 2^(levels-1) with >= 2 coarse cells per direction");
   }
+  {
+    long long nu = c->dim;   // vector kernels index velocity entries with 32 bits
+    for (int k = 0; k < c->dim; ++k) nu *= 2LL * mesh->n[k] + 1;
+    if (nu >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d (2n+1)^d must stay below 2^31");
+    long long ne = c->dim * (c->dim == 2 ? 9 : 27);   // per-cell output buffer, 32-bit offsets
+    for (int k = 0; k < c->dim; ++k) ne *= mesh->n[k];
+    if (ne >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d 3^d n^d must stay below 2^31");
+  }
   const char* ng = getenv("ALS_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -737,7 +794,7 @@ als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "prolongation needs level >= 1");
   begin(c);
-  prolong_level(c, work_for(c, prec), level, xc, xf);
+  prolong_level(c, work_for(c, prec), level, xc, xf, nullptr);
   return finish(c, "prolong");
 }
 

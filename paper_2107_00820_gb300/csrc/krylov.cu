@@ -10,6 +10,7 @@
 
 #include "krylov.h"
 #include "level.h"
+#include "reduce.cuh"
 
 namespace als {
 
@@ -17,8 +18,7 @@ static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
 void count_launch(long long n) { g_launches += n; }
 
-static constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
-static constexpr int RED_THREADS = 256;
+static constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs (two-pass sums of the pressure space)
 
 template <typename T>
 __global__ void k_axpby(long long n, double a, const T* __restrict__ x, double b, T* __restrict__ y) {
@@ -62,55 +62,26 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// Reductions in one launch: every block writes its partial sums, takes a ticket
-// from a counter, and the block holding the last ticket adds all partials in a
-// fixed order (so the result does not depend on which block finishes last) and
-// resets the counter for the next launch.  Workspace layout: slot 0 holds the
-// counter, the partials start at slot 1.
-__device__ __forceinline__ bool last_block(double* ws) {
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned int*>(ws), 1u) == gridDim.x - 1;
-  __syncthreads();
-  return is_last;
-}
-
-__device__ __forceinline__ void finish_sums(double* ws, int k, int nb, double* out, double* sh) {
-  __threadfence();
-  const double* partial = ws + 1;
-  for (int j = 0; j < k; ++j) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[(long long)b * k + j];
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) out[j] = v;
-  }
-  if (threadIdx.x == 0) *reinterpret_cast<unsigned int*>(ws) = 0u;
-}
-
-// out[j] = V_j . w for j < k  (rows read 4 at a time)
+// out[j] = V_j . w for j < k
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_multidot(long long n, int k, const T* __restrict__ V, long long ld,
                                                           const T* __restrict__ w, double* __restrict__ partial,
                                                           double* __restrict__ out) {
-  __shared__ double sh[RED_THREADS / 32];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int j0 = 0; j0 < k; j0 += 4) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j0 = 0; j0 < k; j0 += KMAXB) {
+    const int kk = (k - j0) < KMAXB ? (k - j0) : KMAXB;
+    double acc[KMAXB];
+#pragma unroll
+    for (int jj = 0; jj < KMAXB; ++jj) acc[jj] = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       const double wi = (double)w[i];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
-        if (j0 + jj < k) acc[jj] += (double)V[(long long)(j0 + jj) * ld + i] * wi;
+      for (int jj = 0; jj < KMAXB; ++jj)
+        if (jj < kk) acc[jj] += (double)V[(long long)(j0 + jj) * ld + i] * wi;
     }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      if (j0 + jj >= k) break;
-      const double s = block_sum(acc[jj], sh);
-      if (threadIdx.x == 0) partial[1 + (long long)blockIdx.x * k + j0 + jj] = s;
-    }
+    block_partials(acc, kk, partial + 1 + (long long)blockIdx.x * k + j0);
   }
-  if (last_block(partial)) finish_sums(partial, k, gridDim.x, out, sh);
+  if (last_block(partial)) finish_sums(partial, k, out);
 }
 
 // w <- w + sign * sum_j V_j h_j, and nrm2 = w . w of the updated w
@@ -120,7 +91,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_multiaxpy_norm(long long n, int
                                                                 double sign, T* __restrict__ w,
                                                                 double* __restrict__ partial,
                                                                 double* __restrict__ nrm2) {
-  __shared__ double sh[RED_THREADS / 32];
   double acc2 = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -129,9 +99,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_multiaxpy_norm(long long n, int
     w[i] = wn;
     acc2 += (double)wn * (double)wn;
   }
-  const double s2 = block_sum(acc2, sh);
-  if (threadIdx.x == 0) partial[1 + blockIdx.x] = s2;
-  if (last_block(partial)) finish_sums(partial, 1, gridDim.x, nrm2, sh);
+  double a8[KMAXB] = {acc2};
+  block_partials(a8, 1, partial + 1 + blockIdx.x);
+  if (last_block(partial)) finish_sums(partial, 1, nrm2);
 }
 
 template <typename T>
@@ -178,26 +148,28 @@ void vec_zero(int prec, long long n, void* x, cudaStream_t s) {
   cudaMemsetAsync(x, 0, n * (prec == PREC_F64 ? 8 : 4), s);
 }
 
-// ticket counter slot + partial sums of RED_BLOCKS blocks for k columns
-size_t multidot_partial_doubles(int k) { return (size_t)RED_BLOCKS * (size_t)k + 1; }
+// ticket counter slot + partial sums of up to RED_MAX_BLOCKS blocks for k columns
+size_t multidot_partial_doubles(int k) { return (size_t)RED_MAX_BLOCKS * (size_t)k + 1; }
+
+static unsigned red_grid(long long n) { return red_blocks(n); }
 
 void vec_multidot(int prec, long long n, int k, const void* V, long long ld, const void* w, double* out,
                   double* partial, cudaStream_t s) {
   if (prec == PREC_F64)
-    k_multidot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial, out);
+    k_multidot<double><<<red_grid(n), RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, (const double*)w, partial, out);
   else
-    k_multidot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial, out);
+    k_multidot<float><<<red_grid(n), RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, (const float*)w, partial, out);
   count_launch(1);
 }
 
 void vec_multiaxpy_norm(int prec, long long n, int k, const void* V, long long ld, const double* h, double sign,
                         void* w, double* partial, double* nrm2, cudaStream_t s) {
   if (prec == PREC_F64)
-    k_multiaxpy_norm<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, h, sign, (double*)w,
-                                                                  partial, nrm2);
+    k_multiaxpy_norm<double><<<red_grid(n), RED_THREADS, 0, s>>>(n, k, (const double*)V, ld, h, sign, (double*)w,
+                                                                   partial, nrm2);
   else
-    k_multiaxpy_norm<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, h, sign, (float*)w,
-                                                                 partial, nrm2);
+    k_multiaxpy_norm<float><<<red_grid(n), RED_THREADS, 0, s>>>(n, k, (const float*)V, ld, h, sign, (float*)w,
+                                                                  partial, nrm2);
   count_launch(1);
 }
 
@@ -221,6 +193,182 @@ void vec_scale_dev(int prec, long long n, const double* num, const double* den, 
     k_scale_dev<double><<<grid_for(n), 256, 0, s>>>(n, num, den, (const double*)x, (double*)y, sqrt_den);
   else k_scale_dev<float><<<grid_for(n), 256, 0, s>>>(n, num, den, (const float*)x, (float*)y, sqrt_den);
   count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(s) smoother steps with an unnormalised stored basis (see GmresDev)
+// ---------------------------------------------------------------------------
+// Each thread handles PER entries spaced RED_THREADS apart, with all loads of
+// its entries issued before any arithmetic; the grid then has about n / (256 PER)
+// blocks, which keeps the ticket counter of the single-launch reduction cold
+// (same-address atomics serialise: several thousand blocks cost microseconds).
+// Column loops are unrolled to KMAXB with predicates.  In FP32 the arithmetic
+// and the in-block sums run in float.
+constexpr int GM_PER = 4;
+
+// V0 = b, |b|^2 -> gmres_start
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* __restrict__ b, T* __restrict__ V0,
+                                                          double* __restrict__ partial, GmresDev st) {
+  __shared__ double nrm2_s[1];
+  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  T v[GM_PER];
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+    v[q] = i < n ? b[i] : T(0);
+  }
+  T acc[KMAXB] = {T(0)};
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+    if (i < n) V0[i] = v[q];
+    acc[0] += v[q] * v[q];
+  }
+  block_partials(acc, 1, partial + 1 + blockIdx.x);
+  if (last_block(partial)) {
+    finish_sums(partial, 1, nrm2_s);
+    if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
+  }
+}
+
+// Gram-Schmidt update of the new column w = V_{j+1} against columns 0..j with the
+// coefficients H[0..j][j] / hn[i], then |w|^2 -> gmres_step(j)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, const T* __restrict__ V, long long ld,
+                                                         double* __restrict__ partial, GmresDev st) {
+  __shared__ T coef[KMAXB];
+  __shared__ double nrm2_s[1];
+  const double* hcol = st.H + (long long)j * st.ldh;
+  if ((int)threadIdx.x <= j)
+    coef[threadIdx.x] = (T)(st.hn[threadIdx.x] != 0.0 ? hcol[threadIdx.x] / st.hn[threadIdx.x] : 0.0);
+  __syncthreads();
+  T* w = const_cast<T*>(V) + (long long)(j + 1) * ld;
+  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  T a[GM_PER];
+  T vc[GM_PER][KMAXB];
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+    const bool in = i < n;
+    a[q] = in ? w[i] : T(0);
+#pragma unroll
+    for (int c = 0; c < KMAXB; ++c) vc[q][c] = (in && c <= j) ? V[(long long)c * ld + i] : T(0);
+  }
+  T acc[KMAXB] = {T(0)};
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+#pragma unroll
+    for (int c = 0; c < KMAXB; ++c)
+      if (c <= j) a[q] -= vc[q][c] * coef[c];
+    if (i < n) w[i] = a[q];
+    acc[0] += a[q] * a[q];
+  }
+  block_partials(acc, 1, partial + 1 + blockIdx.x);
+  if (last_block(partial)) {
+    finish_sums(partial, 1, nrm2_s);
+    if (threadIdx.x == 0) gmres_step(st, j, nrm2_s[0]);
+  }
+}
+
+// x = (x_zero ? 0 : x) + sum_j Z_j y_j with y = R^-1 g (back substitution, redone
+// by every block), and, if t != NULL, the GMRES residual
+//   t = r0 - A Z y = sum_i u_i v_i,  u = Q^T (g[k] e_k)
+// from the Arnoldi relation (Q = product of the Givens rotations), no operator apply.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, const T* __restrict__ Z,
+                                                           const T* __restrict__ V, long long ld, GmresDev st,
+                                                           T* __restrict__ x, int x_zero, T* __restrict__ t) {
+  __shared__ T y[KMAXB], u[KMAXB + 1];
+  if (threadIdx.x == 0) {
+    double Hs[KMAXB][KMAXB], gs[KMAXB + 1], cs[KMAXB], sn[KMAXB], hn[KMAXB + 1];
+    for (int c = 0; c < k; ++c) {
+      for (int r = 0; r <= c; ++r) Hs[r][c] = st.H[(long long)c * st.ldh + r];
+      cs[c] = st.cs[c]; sn[c] = st.sn[c];
+    }
+    for (int c = 0; c <= k; ++c) { gs[c] = st.g[c]; hn[c] = st.hn[c]; }
+    double ys[KMAXB];
+    for (int i = k - 1; i >= 0; --i) {
+      double a = gs[i];
+      for (int c = i + 1; c < k; ++c) a -= Hs[i][c] * ys[c];
+      ys[i] = Hs[i][i] != 0.0 ? a / Hs[i][i] : 0.0;
+      y[i] = (T)ys[i];
+    }
+    if (t) {
+      double us[KMAXB + 1];
+      for (int i = 0; i < k; ++i) us[i] = 0.0;
+      us[k] = gs[k];
+      for (int i = k - 1; i >= 0; --i) {
+        const double a = us[i], b = us[i + 1];
+        us[i] = cs[i] * a - sn[i] * b;
+        us[i + 1] = sn[i] * a + cs[i] * b;
+      }
+      for (int i = 0; i <= k; ++i) u[i] = (T)(hn[i] != 0.0 ? us[i] / hn[i] : 0.0);
+    }
+  }
+  __syncthreads();
+  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+    if (i >= n) break;
+    T zc[KMAXB];
+#pragma unroll
+    for (int c = 0; c < KMAXB; ++c) zc[c] = c < k ? Z[(long long)c * ld + i] : T(0);
+    T a = x_zero ? T(0) : x[i];
+#pragma unroll
+    for (int c = 0; c < KMAXB; ++c)
+      if (c < k) a += zc[c] * y[c];
+    x[i] = a;
+    if (t) {
+      T vc[KMAXB + 1];
+#pragma unroll
+      for (int c = 0; c <= KMAXB; ++c) vc[c] = c <= k ? V[(long long)c * ld + i] : T(0);
+      T r = T(0);
+#pragma unroll
+      for (int c = 0; c <= KMAXB; ++c)
+        if (c <= k) r += vc[c] * u[c];
+      t[i] = r;
+    }
+  }
+}
+
+static unsigned full_grid(long long n) {
+  return (unsigned)((n + RED_THREADS * GM_PER - 1) / (RED_THREADS * GM_PER));
+}
+
+void gm_start(int prec, long long n, const void* b, void* V0, double* partial, const GmresDev& st, cudaStream_t s) {
+  if (prec == PREC_F64)
+    k_gm_start<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, (const double*)b, (double*)V0, partial, st);
+  else
+    k_gm_start<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, (const float*)b, (float*)V0, partial, st);
+  count_launch(1);
+}
+
+void gm_orth(int prec, long long n, int j, const void* V, long long ld, double* partial, const GmresDev& st,
+             cudaStream_t s) {
+  if (prec == PREC_F64)
+    k_gm_orth<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, j, (const double*)V, ld, partial, st);
+  else
+    k_gm_orth<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, j, (const float*)V, ld, partial, st);
+  count_launch(1);
+}
+
+void gm_update(int prec, long long n, int k, const void* Z, const void* V, long long ld, const GmresDev& st,
+               void* x, int x_zero, void* t, cudaStream_t s) {
+  if (prec == PREC_F64)
+    k_gm_update<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, k, (const double*)Z, (const double*)V, ld,
+                                                               st, (double*)x, x_zero, (double*)t);
+  else
+    k_gm_update<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, k, (const float*)Z, (const float*)V, ld,
+                                                              st, (float*)x, x_zero, (float*)t);
+  count_launch(1);
+}
+
+// workspace of the smoother's fused reductions: one partial row of KMAXB per block
+size_t gmres_partial_doubles(long long n) {
+  return (size_t)((n + RED_THREADS - 1) / RED_THREADS) * KMAXB + 1;   // covers every grid used
 }
 
 // ---------------------------------------------------------------------------

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "reduce.cuh"
 
 namespace als {
 
@@ -38,6 +39,23 @@ void count_launch(long long n);
 // ---- operator.cu
 void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y,
               const void* p_in, void* p_out, cudaStream_t s);
+// A_gamma apply (viscous + AL) fused with the reduction that consumes y:
+//   y = b + sigma A x (b NULL: y = sigma A x);
+//   start = 0: out[j] = (V_j . y) / st.hn[j] for j < k (k <= KMAXB; Arnoldi dots)
+//   start = 1: |y|^2 starts the GMRES cycle st
+struct ApplyEpi {
+  const void* b;
+  double sigma;
+  int k;
+  const void* V;
+  long long ld;
+  double* out;
+  int start;
+  GmresDev st;
+  double* partial;
+};
+void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                  cudaStream_t s);
 void op_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
 void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y, int nvec,
                     long long stride, cudaStream_t s);
@@ -45,8 +63,9 @@ void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y,
 // ---- patches.cu
 void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s);
 // e0/e1 (optional) are recorded immediately before and after the patch kernel
+// den (optional device scalar): z = D^-1 r / den (0 where den == 0)
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
-                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
+                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, const double* den = nullptr);
 size_t patch_scratch_bytes(const LevelDev& L, int prec);
 // local solves on the coarse-cell interiors (stars of the fine vertices at the
 // coarse-cell centres):  mode 0: out = sum_K E_K A_K^-1 E_K^T in  (out zeroed first)
@@ -55,10 +74,12 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
                           cudaStream_t s);
 
 // ---- transfer.cu
+// xf = P_H xc; if xadd, also xadd += P_H xc
 void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf,
-                 cudaStream_t s);
+                 cudaStream_t s, void* xadd = nullptr);
+// rc = P_H^T rf, or P_H^T (rf - sub) when sub is given
 void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc,
-                  cudaStream_t s);
+                  cudaStream_t s, const void* sub = nullptr);
 
 // ---- krylov.cu (vector kernels)
 void vec_axpby(int prec, long long n, double a, const void* x, double b, void* y, cudaStream_t s);
@@ -78,6 +99,15 @@ void vec_scale_dev(int prec, long long n, const double* num, const double* den, 
 // w <- w + sign * sum_j V_j h_j and nrm2 = |w|^2, one launch
 void vec_multiaxpy_norm(int prec, long long n, int k, const void* V, long long ld, const double* h, double sign,
                         void* w, double* partial, double* nrm2, cudaStream_t s);
+// GMRES(s) smoother with an unnormalised stored basis (GmresDev): V0 = b and start;
+// orthogonalise column j+1 and take the Givens step j; x (+)= Z y and, if t, the
+// GMRES residual t = r0 - A Z y from the Arnoldi relation.  s <= KMAXB.
+size_t gmres_partial_doubles(long long n);   // workspace of op_apply_epi and gm_* for n entries
+void gm_start(int prec, long long n, const void* b, void* V0, double* partial, const GmresDev& st, cudaStream_t s);
+void gm_orth(int prec, long long n, int j, const void* V, long long ld, double* partial, const GmresDev& st,
+             cudaStream_t s);
+void gm_update(int prec, long long n, int k, const void* Z, const void* V, long long ld, const GmresDev& st,
+               void* x, int x_zero, void* t, cudaStream_t s);
 size_t multidot_partial_doubles(int k);
 
 }  // namespace als

@@ -12,6 +12,7 @@
 // and PETSc use.  B u (Eq. (stokessys)) is cell-local and written directly.
 #include "cell.cuh"
 #include "level.h"
+#include "reduce.cuh"
 
 #include <type_traits>
 
@@ -76,12 +77,14 @@ static Colour make_colour(const Geom& g, int colour) {
   return c;
 }
 
+// 32-bit arithmetic: cell counts stay below 2^31 (checked when a context is created)
 __device__ __forceinline__ bool colour_cell(const Colour& col, long long t, int& cx, int& cy, int& cz) {
   if (t >= col.count) return false;
-  const int i = (int)(t % col.m[0]);
-  const long long r = t / col.m[0];
-  const int j = (int)(r % col.m[1]);
-  const int k = (int)(r / col.m[1]);
+  const unsigned tu = (unsigned)t, m0 = (unsigned)col.m[0], m1 = (unsigned)col.m[1];
+  const unsigned r = tu / m0;
+  const int i = (int)(tu - r * m0);
+  const unsigned k = r / m1;
+  const int j = (int)(r - k * m1);
   cx = col.step * i + col.b[0];
   cy = col.step * j + col.b[1];
   cz = col.step * k + col.b[2];
@@ -120,10 +123,10 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
   const long long t = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * CPW + grp;
   int cx = 0, cy = 0, cz = 0;
   const bool act = lane_ok && colour_cell(col, t, cx, cy, cz);
-  const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
+  const long long cell = (long long)(unsigned)(cx + g.n[0] * (cy + g.n[1] * cz));
   const int i0 = l % 3, i1 = (l / 3) % 3, i2 = DIM == 3 ? l / 9 : 0;
   const int ni = 2 * cx + i0, nj = 2 * cy + i1, nk = DIM == 3 ? 2 * cz + i2 : 0;
-  const long long nd = node_id(g, ni, nj, nk);
+  const long long nd = (long long)(unsigned)(ni + g.nn[0] * (nj + g.nn[1] * nk));
   const bool bnd = on_boundary(g, ni, nj, nk);
 
   T grad[DIM][DIM];
@@ -425,44 +428,111 @@ __global__ void k_init_out(Geom g, const T* __restrict__ x, T* __restrict__ y, i
   y[t] = (bnd && keep_bnd) ? x[t] : T(0);
 }
 
-// y(c, node) = sum of the per-cell outputs of the <= 2^d cells containing the
-// node, in a fixed order; Dirichlet rows: y_D = x_D (keep_bnd) or 0, unless raw.
+// (A x)(c, node) = sum of the per-cell outputs of the <= 2^d cells containing the
+// node, in a fixed order; Dirichlet rows: x_D (keep_bnd) or 0, unless raw.
+// Two fixed taps per axis (predicated), so all loads of a node issue together.
+template <typename T, int DIM>
+__device__ __forceinline__ T gather_node(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
+                                         unsigned t, int keep_bnd, int raw) {
+  constexpr int NB = Sz<DIM>::NB;
+  const unsigned N = (unsigned)g.N, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const unsigned c = t / N, nd = t - c * N;
+  const unsigned r = nd / nx;
+  const int idx[3] = {(int)(nd - r * nx), DIM == 3 ? (int)(r % ny) : (int)r, DIM == 3 ? (int)(r / ny) : 0};
+  if (!raw && on_boundary(g, idx[0], idx[1], idx[2])) return keep_bnd ? x[t] : T(0);
+  // per axis: odd node -> its own cell (local 1); even node -> cell below (local 2) and
+  // above (local 0).  Tap 0 is the lower cell; tap 1 is one cell further along the axis.
+  int c0[3], l0[3], l1[3];
+  bool ok0[3], ok1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int i = a < DIM ? idx[a] : 1;
+    const int na = a < DIM ? g.n[a] : 1;
+    if (i & 1) { c0[a] = i >> 1; l0[a] = 1; ok0[a] = true; l1[a] = 0; ok1[a] = false; }
+    else { c0[a] = (i >> 1) - 1; l0[a] = 2; ok0[a] = i > 0; l1[a] = 0; ok1[a] = i < 2 * na; }
+  }
+  // cell index of tap (0,0,0) may be -1 along an axis whose lower tap is absent; the
+  // offsets below only combine it with taps that exist, so every address read is valid
+  const int sx = DIM * NB, sy = g.n[0] * DIM * NB, sz = g.n[0] * g.n[1] * DIM * NB;
+  const int base = (c0[0] + g.n[0] * (c0[1] + (DIM == 3 ? g.n[1] * c0[2] : 0))) * DIM * NB + (int)c * NB;
+  T v[DIM == 3 ? 8 : 4];
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int q = cx + 2 * cy + 4 * cz;
+        const bool use = (cx ? ok1[0] : ok0[0]) && (cy ? ok1[1] : ok0[1]) && (DIM == 2 || (cz ? ok1[2] : ok0[2]));
+        const int l = (cx ? l1[0] : l0[0]) + 3 * (cy ? l1[1] : l0[1]) + (DIM == 3 ? 9 * (cz ? l1[2] : l0[2]) : 0);
+        const int off = base + cx * sx + cy * sy + (DIM == 3 ? cz * sz : 0) + l;
+        v[q] = use ? ebuf[off] : T(0);
+      }
+  T acc = T(0);
+#pragma unroll
+  for (int q = 0; q < (DIM == 3 ? 8 : 4); ++q) acc += v[q];
+  return acc;
+}
+
 template <typename T, int DIM>
 __global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
                                int keep_bnd, int raw) {
-  constexpr int NB = Sz<DIM>::NB;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.N * DIM) return;
-  const int c = (int)(t / g.N);
-  const long long nd = t % g.N;
-  const int idx[3] = {(int)(nd % g.nn[0]), (int)((nd / g.nn[0]) % g.nn[1]),
-                      DIM == 3 ? (int)(nd / ((long long)g.nn[0] * g.nn[1])) : 0};
-  if (!raw && on_boundary(g, idx[0], idx[1], idx[2])) {
-    y[t] = keep_bnd ? x[t] : T(0);
-    return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(g.N * DIM)) return;
+  y[t] = gather_node<T, DIM>(g, ebuf, x, t, keep_bnd, raw);
+}
+
+// Gather fused with the reduction that consumes the result:
+//   y = b + sigma A x (b NULL: y = sigma A x);  out[j] = (V_j . y) / hn[j], j < k;
+//   start: |y|^2 starts a GMRES cycle.  Fixed grid and order: reproducible.
+// Each thread gathers GATHER_PER entries (spaced RED_THREADS apart) with all
+// their loads issued first; the sums run in T inside a block, in double across blocks.
+constexpr int GATHER_PER = 4;
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __restrict__ ebuf,
+                                                            const T* __restrict__ x, T* __restrict__ y,
+                                                            const T* __restrict__ b, double sigma, int k,
+                                                            const T* __restrict__ V, long long ld,
+                                                            double* __restrict__ out, int start, GmresDev st,
+                                                            double* __restrict__ partial) {
+  __shared__ double nrm2_s[1];
+  const unsigned n = (unsigned)(g.N * DIM);
+  const unsigned base = blockIdx.x * (RED_THREADS * GATHER_PER) + threadIdx.x;
+  const int kk = start ? 1 : k;
+  T yv[GATHER_PER];
+#pragma unroll
+  for (int q = 0; q < GATHER_PER; ++q) {
+    const unsigned t = base + q * RED_THREADS;
+    yv[q] = t < n ? gather_node<T, DIM>(g, ebuf, x, t, 1, 0) : T(0);
   }
-  // per axis: odd node -> its own cell (local 1); even node -> cell below (local 2) and above (local 0)
-  int ncand[3] = {1, 1, 1}, cell[3][2] = {{0, 0}, {0, 0}, {0, 0}}, loc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  for (int a = 0; a < DIM; ++a) {
-    const int i = idx[a];
-    if (i & 1) { cell[a][0] = i >> 1; loc[a][0] = 1; }
-    else {
-      int k = 0;
-      if (i > 0) { cell[a][k] = (i >> 1) - 1; loc[a][k] = 2; ++k; }
-      if (i < 2 * g.n[a]) { cell[a][k] = i >> 1; loc[a][k] = 0; ++k; }
-      ncand[a] = k;
+  T acc[KMAXB];
+#pragma unroll
+  for (int j = 0; j < KMAXB; ++j) acc[j] = T(0);
+#pragma unroll
+  for (int q = 0; q < GATHER_PER; ++q) {
+    const unsigned t = base + q * RED_THREADS;
+    if (t < n) {
+      const T v = (b ? b[t] : T(0)) + (T)sigma * yv[q];
+      y[t] = v;
+      if (start) {
+        acc[0] += v * v;
+      } else {
+#pragma unroll
+        for (int j = 0; j < KMAXB; ++j)
+          if (j < k) acc[j] += V[(long long)j * ld + t] * v;
+      }
     }
   }
-  T acc = T(0);
-  for (int cz = 0; cz < ncand[2]; ++cz)
-    for (int cy = 0; cy < ncand[1]; ++cy)
-      for (int cx = 0; cx < ncand[0]; ++cx) {
-        const long long ce = (long long)cell[0][cx] +
-                             (long long)g.n[0] * ((long long)cell[1][cy] + (DIM == 3 ? (long long)g.n[1] * cell[2][cz] : 0));
-        const int l = loc[0][cx] + 3 * loc[1][cy] + (DIM == 3 ? 9 * loc[2][cz] : 0);
-        acc += ebuf[(ce * DIM + c) * NB + l];
-      }
-  y[t] = acc;
+  block_partials(acc, kk, partial + 1 + (long long)blockIdx.x * kk);
+  if (last_block(partial)) {
+    if (start) {
+      finish_sums(partial, 1, nrm2_s);
+      if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
+    } else {
+      finish_sums(partial, k, out, st.hn);
+    }
+  }
 }
 
 template <typename T, int DIM, bool TENSOR, int MODE>
@@ -560,6 +630,46 @@ static void op_dispatch(const LevelDev& L, int prec, int mode, double gamma, con
 void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y,
               const void* p_in, void* p_out, cudaStream_t s) {
   op_dispatch(L, prec, mode, gamma, x, y, p_in, p_out, 1, 0, s);
+}
+
+template <typename T, int DIM, bool TENSOR>
+static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, void* y, const ApplyEpi& e,
+                             cudaStream_t s) {
+  const Geom& g = L.g;
+  constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);
+  const T* coef = nullptr;
+  const T* winv = nullptr;
+  if constexpr (std::is_same<T, double>::value) { coef = L.coef64; winv = L.winv64; }
+  else { coef = L.coef32; winv = L.winv32; }
+  const Colour col = all_cells(g);
+  k_apply<T, DIM, TENSOR, OP_VISC | OP_AL, true><<<(unsigned)((col.count + CPB - 1) / CPB), 256, 0, s>>>(
+      g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr, nullptr, 0, (T*)L.ebuf, winv);
+  const long long per_block = (long long)RED_THREADS * GATHER_PER;
+  k_gather_epi<T, DIM><<<(unsigned)((g.N * DIM + per_block - 1) / per_block), RED_THREADS, 0, s>>>(
+      g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
+      e.st, e.partial);
+  count_launch(2);
+}
+
+void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                  cudaStream_t s) {
+  if (prec == PREC_F64) {
+    if (L.g.dim == 2) {
+      if (L.tensor) launch_apply_epi<double, 2, true>(L, gamma, x, y, e, s);
+      else launch_apply_epi<double, 2, false>(L, gamma, x, y, e, s);
+    } else {
+      if (L.tensor) launch_apply_epi<double, 3, true>(L, gamma, x, y, e, s);
+      else launch_apply_epi<double, 3, false>(L, gamma, x, y, e, s);
+    }
+  } else {
+    if (L.g.dim == 2) {
+      if (L.tensor) launch_apply_epi<float, 2, true>(L, gamma, x, y, e, s);
+      else launch_apply_epi<float, 2, false>(L, gamma, x, y, e, s);
+    } else {
+      if (L.tensor) launch_apply_epi<float, 3, true>(L, gamma, x, y, e, s);
+      else launch_apply_epi<float, 3, false>(L, gamma, x, y, e, s);
+    }
+  }
 }
 
 // Several independent FP64 applies of A_gamma (used to form the coarse matrix

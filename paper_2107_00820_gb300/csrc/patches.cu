@@ -777,36 +777,53 @@ __global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restric
   }
 }
 
-// z at node (c, i, j, k) = sum of the patch outputs of the vertices whose star contains it
+// z at node (c, i, j, k) = sum of the patch outputs of the vertices whose star
+// contains it (fixed order; two predicated taps per axis, all loads issued at once),
+// divided by den[0] when den is given
 template <typename TV, int DIM>
-__global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z) {
+__global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
+                               const double* __restrict__ den) {
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.N * DIM) return;
-  const int c = (int)(t / g.N);
-  const long long nd = t % g.N;
-  const int i = (int)(nd % g.nn[0]);
-  const long long rr = nd / g.nn[0];
-  const int j = (int)(rr % g.nn[1]);
-  const int k = (int)(rr / g.nn[1]);
-  if (on_boundary(g, i, j, k)) { z[t] = TV(0); return; }
-  // per axis: even node index -> its own vertex (offset 0); odd -> the two neighbours
-  int nva[3], vv[3][2], oo[3][2];
-  const int idx[3] = {i, j, k};
-  for (int a = 0; a < DIM; ++a) {
-    if ((idx[a] & 1) == 0) { nva[a] = 1; vv[a][0] = idx[a] >> 1; oo[a][0] = 1; }
-    else { nva[a] = 2; vv[a][0] = (idx[a] - 1) >> 1; oo[a][0] = 2; vv[a][1] = (idx[a] + 1) >> 1; oo[a][1] = 0; }
+  __shared__ TV inv_den;
+  if (den) {                        // one division per block, not per entry
+    if (threadIdx.x == 0) inv_den = den[0] != 0.0 ? (TV)(1.0 / den[0]) : TV(0);
+    __syncthreads();
   }
-  TV acc = TV(0);
-  const int nz = DIM == 3 ? nva[2] : 1;
-  for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < nva[1]; ++cy)
-      for (int cx = 0; cx < nva[0]; ++cx) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(g.N * DIM)) return;
+  const unsigned N = (unsigned)g.N, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const int c = (int)(t / N);
+  const unsigned nd = t - (unsigned)c * N;
+  const unsigned rr = nd / nx;
+  const int idx[3] = {(int)(nd - rr * nx), DIM == 3 ? (int)(rr % ny) : (int)rr, DIM == 3 ? (int)(rr / ny) : 0};
+  if (on_boundary(g, idx[0], idx[1], idx[2])) { z[t] = TV(0); return; }
+  // per axis: even node index -> its own vertex (offset 1); odd -> the two neighbours (offsets 2, 0)
+  int vv[3][2], oo[3][2];
+  bool ok[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int i = a < DIM ? idx[a] : 0;
+    if ((i & 1) == 0) { vv[a][0] = i >> 1; oo[a][0] = 1; ok[a][0] = true; vv[a][1] = 0; oo[a][1] = 0; ok[a][1] = false; }
+    else { vv[a][0] = (i - 1) >> 1; oo[a][0] = 2; ok[a][0] = true; vv[a][1] = (i + 1) >> 1; oo[a][1] = 0; ok[a][1] = true; }
+  }
+  TV v[DIM == 3 ? 8 : 4];
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int q = cx + 2 * cy + 4 * cz;
+        const bool use = ok[0][cx] && ok[1][cy] && (DIM == 2 || ok[2][cz]);
         const long long vid = (long long)vv[0][cx] +
                               (long long)g.nv[0] * ((long long)vv[1][cy] + (DIM == 3 ? (long long)g.nv[1] * vv[2][cz] : 0));
         const int o = oo[0][cx] + 3 * oo[1][cy] + (DIM == 3 ? 9 * oo[2][cz] : 0);
-        acc += out[vid * NP + c * NB + o];
+        v[q] = use ? out[vid * NP + c * NB + o] : TV(0);
       }
+  TV acc = TV(0);
+#pragma unroll
+  for (int q = 0; q < (DIM == 3 ? 8 : 4); ++q) acc += v[q];
+  if (den) acc *= inv_den;
   z[t] = acc;
 }
 
@@ -816,7 +833,7 @@ size_t patch_scratch_bytes(const LevelDev& L, int prec) {
 
 template <typename TF, typename TV, int DIM>
 static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z, void* scratch, cudaStream_t s,
-                        cudaEvent_t e0, cudaEvent_t e1) {
+                        cudaEvent_t e0, cudaEvent_t e1, const double* den) {
   const long long warps = L.g.nverts;
   const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
   // External records become event-record nodes when the stream is being captured
@@ -824,13 +841,13 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
   k_patch_apply<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   const long long tot = L.g.N * DIM;
-  k_patch_gather<TV, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z);
+  k_patch_gather<TV, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z, den);
   count_launch(2);
 }
 
 template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
-                       cudaEvent_t e1) {
+                       cudaEvent_t e1, const double* den) {
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   if (use_direct_patch_kernel())
     launch_patch_direct<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, s);
@@ -838,18 +855,19 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
     launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   const long long tot = L.g.N * DIM;
-  k_patch_gather<float, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z);
+  k_patch_gather<float, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z,
+                                                                           den);
   count_launch(1);
 }
 
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
-                  cudaEvent_t e0, cudaEvent_t e1) {
+                  cudaEvent_t e0, cudaEvent_t e1, const double* den) {
   if (prec == PREC_F64) {
-    if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1);
-    else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1);
+    if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1, den);
+    else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1, den);
   } else {
-    if (L.g.dim == 2) smooth_tma<2>(L, r, z, scratch, s, e0, e1);
-    else smooth_tma<3>(L, r, z, scratch, s, e0, e1);
+    if (L.g.dim == 2) smooth_tma<2>(L, r, z, scratch, s, e0, e1, den);
+    else smooth_tma<3>(L, r, z, scratch, s, e0, e1, den);
   }
 }
 

@@ -1,0 +1,148 @@
+// Single-launch, bitwise-reproducible reductions and the one-thread GMRES
+// bookkeeping that runs in the epilogue of the last block of a reduction.
+//
+// Every block writes the partial sums of its columns to a workspace row, takes
+// a ticket from a counter, and the block holding the last ticket adds the
+// partials of all blocks in a fixed order (so the result does not depend on
+// which block finished last) and resets the counter.  Workspace layout: slot 0
+// is the counter, the partials [block][column] start at slot 1.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace als {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1216;   // 8 x 152 SMs: one full wave at 256 threads per block
+constexpr int KMAXB = 8;               // columns reduced together in registers
+
+// blocks for a reduction over n entries: about `per_thread` entries per thread
+inline unsigned red_blocks(long long n, int per_thread = 4) {
+  long long b = (n + (long long)RED_THREADS * per_thread - 1) / ((long long)RED_THREADS * per_thread);
+  if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// block partials of kk <= KMAXB columns: warp shuffles, one shared pass, written to row[0..kk).
+// A is the accumulation type inside the block (float in the FP32 kernels: FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU); the block
+// partials are stored and combined across blocks in double.
+template <typename A>
+__device__ __forceinline__ void block_partials(const A (&acc)[KMAXB], int kk, double* row) {
+  __shared__ A sh[RED_THREADS / 32][KMAXB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KMAXB; ++j) {
+    if (j >= kk) break;
+    A v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w][j] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < kk) {
+    A v = A(0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += sh[i][threadIdx.x];
+    row[threadIdx.x] = (double)v;
+    __threadfence();   // the writers publish their partial before the block takes its ticket
+  }
+  __syncthreads();
+}
+
+// called right after block_partials (whose writers fenced their partials)
+__device__ __forceinline__ bool last_block(double* ws) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned int*>(ws), 1u) == gridDim.x - 1;
+  __syncthreads();
+  return is_last;
+}
+
+// Run by every thread of the last block: out[j] = (sum over blocks of column j) / div[j]
+// (div NULL: no division; div[j] == 0 gives 0).  The partials are read through L2
+// (other blocks wrote them), each thread over a fixed strided subset, then one
+// fixed block reduction per group of KMAXB columns.
+__device__ __forceinline__ void finish_sums(double* ws, int k, double* out, const double* div = nullptr) {
+  if (threadIdx.x == 0) __threadfence();
+  __syncthreads();
+  const double* partial = ws + 1;
+  const int nb = gridDim.x;
+  for (int j0 = 0; j0 < k; j0 += KMAXB) {
+    const int kk = (k - j0) < KMAXB ? (k - j0) : KMAXB;
+    double acc[KMAXB];
+#pragma unroll
+    for (int j = 0; j < KMAXB; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < KMAXB; ++j)
+        if (j < kk) acc[j] += __ldcg(partial + (long long)b * k + j0 + j);
+    }
+    __shared__ double tot[KMAXB];
+    block_partials(acc, kk, tot);
+    if ((int)threadIdx.x < kk) {
+      const int j = j0 + threadIdx.x;
+      double v = tot[threadIdx.x];
+      if (div) v = div[j] != 0.0 ? v / div[j] : 0.0;
+      out[j] = v;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *reinterpret_cast<unsigned int*>(ws) = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(s) state on the device (column-major Hessenberg H, leading dim ldh).
+// The Krylov basis is stored unnormalised: column i holds hn[i] * v_i, where
+// v_i is the orthonormal Arnoldi vector, and every consumer divides by hn[i].
+// ---------------------------------------------------------------------------
+struct GmresDev {
+  double* H;
+  int ldh;
+  double* cs;
+  double* sn;
+  double* g;      // rotated right-hand side, length s + 1
+  double* res;    // |g[k+1]| after step k
+  double* hn;     // stored-column norms, length s + 1
+  double* beta;   // |r0|
+  int m;          // s + 1
+};
+
+// start: beta = |r0|, g = (beta, 0, ...), hn[0] = beta   (one thread)
+__device__ __forceinline__ void gmres_start(const GmresDev& st, double nrm2) {
+  const double b = sqrt(fmax(nrm2, 0.0));
+  st.beta[0] = b;
+  st.hn[0] = b;
+  st.g[0] = b;
+  for (int i = 1; i < st.m; ++i) st.g[i] = 0.0;
+}
+
+// step k (k < KMAXB): H[k+1][k] = |w|, hn[k+1] = |w|, then the rotations of
+// column k; all operands are loaded first so the chain runs in registers (one thread)
+__device__ __forceinline__ void gmres_step(const GmresDev& st, int k, double nrm2) {
+  double* hg = st.H + (long long)k * st.ldh;
+  double h[KMAXB + 1], cs[KMAXB], sn[KMAXB];
+  for (int i = 0; i <= k; ++i) h[i] = hg[i];
+  for (int i = 0; i < k; ++i) { cs[i] = st.cs[i]; sn[i] = st.sn[i]; }
+  const double gk = st.g[k];
+  const double hk1 = sqrt(fmax(nrm2, 0.0));
+  h[k + 1] = hk1;
+  for (int i = 0; i < k; ++i) {
+    const double a = h[i], b = h[i + 1];
+    h[i] = cs[i] * a + sn[i] * b;
+    h[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = h[k], b = h[k + 1];
+  const double r = hypot(a, b);
+  double c = 1.0, sv = 0.0;
+  if (r > 0.0) { c = a / r; sv = b / r; }
+  h[k] = r;
+  for (int i = 0; i <= k; ++i) hg[i] = h[i];
+  hg[k + 1] = 0.0;
+  st.hn[k + 1] = hk1;
+  st.cs[k] = c; st.sn[k] = sv;
+  st.g[k + 1] = -sv * gk;
+  st.g[k] = c * gk;
+  st.res[0] = fabs(sv * gk);
+}
+
+}  // namespace als

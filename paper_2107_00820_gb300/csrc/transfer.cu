@@ -10,100 +10,148 @@
 
 namespace als {
 
-template <int DIM>
-__device__ __forceinline__ void node_ijk(const Geom& g, long long nd, int& i, int& j, int& k) {
-  i = (int)(nd % g.nn[0]);
-  const long long r = nd / g.nn[0];
-  j = (int)(r % g.nn[1]);
-  k = (DIM == 3) ? (int)(r / g.nn[1]) : 0;
+// Fixed tap sets per axis (predicated, fully unrolled, so every load of an
+// output issues at once).  A tap is used only if it lies inside the axis and off
+// its Dirichlet ends: the boundary of the box is exactly the set of nodes with
+// some coordinate at an end, so the per-axis test removes boundary rows/columns.
+
+// fine node f (1D) -> three coarse taps (nc coarse nodes on the axis)
+template <typename W>
+__device__ __forceinline__ void prolong_taps(int f, int nc, int* m, W* w, bool* ok) {
+  if ((f & 1) == 0) {
+    m[0] = f >> 1; w[0] = W(1); m[1] = m[0]; w[1] = W(0); m[2] = m[0]; w[2] = W(0);
+  } else {
+    const int c = f >> 2;           // coarse cell
+    const bool first = (f & 3) == 1;
+    m[0] = 2 * c; m[1] = 2 * c + 1; m[2] = 2 * c + 2;
+    w[0] = first ? W(0.375) : W(-0.125); w[1] = W(0.75); w[2] = first ? W(-0.125) : W(0.375);
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) ok[q] = w[q] != W(0) && m[q] >= 1 && m[q] <= nc - 2;
 }
 
-// fine node f (1D): coarse nodes and weights of the interpolation
-__device__ __forceinline__ int prolong_weights_1d(int f, int* m, double* w) {
-  if ((f & 1) == 0) { m[0] = f >> 1; w[0] = 1.0; return 1; }
-  const int c = f >> 2;           // coarse cell
-  const bool first = (f & 3) == 1;
-  m[0] = 2 * c; m[1] = 2 * c + 1; m[2] = 2 * c + 2;
-  w[0] = first ? 0.375 : -0.125; w[1] = 0.75; w[2] = first ? -0.125 : 0.375;
-  return 3;
+// coarse node m (1D) -> five fine taps of the transpose (nf fine nodes on the axis)
+template <typename W>
+__device__ __forceinline__ void restrict_taps(int m, int nf, int* f, W* w, bool* ok) {
+  f[0] = 2 * m; w[0] = W(1);
+  f[1] = 2 * m - 1; f[2] = 2 * m + 1;
+  f[3] = 2 * m - 3; f[4] = 2 * m + 3;
+  if (m & 1) { w[1] = w[2] = W(0.75); w[3] = w[4] = W(0); }
+  else { w[1] = w[2] = W(0.375); w[3] = w[4] = W(-0.125); }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) ok[q] = w[q] != W(0) && f[q] >= 1 && f[q] <= nf - 2;
 }
 
-// coarse node m (1D): fine nodes and weights of the transpose (nf = fine nodes per axis)
-__device__ __forceinline__ int restrict_weights_1d(int m, int nf, int* f, double* w) {
-  int cnt = 0;
-  auto add = [&](int ff, double ww) { if (ff >= 0 && ff < nf) { f[cnt] = ff; w[cnt] = ww; ++cnt; } };
-  add(2 * m, 1.0);
-  if (m & 1) { add(2 * m - 1, 0.75); add(2 * m + 1, 0.75); }
-  else { add(2 * m - 1, 0.375); add(2 * m + 1, 0.375); add(2 * m - 3, -0.125); add(2 * m + 3, -0.125); }
-  return cnt;
+__device__ __forceinline__ void decode(const Geom& g, unsigned t, int dim, int& c, int& i, int& j, int& k) {
+  const unsigned N = (unsigned)g.N, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  c = (int)(t / N);
+  const unsigned nd = t - (unsigned)c * N;
+  const unsigned r = nd / nx;
+  i = (int)(nd - r * nx);
+  j = dim == 3 ? (int)(r % ny) : (int)r;
+  k = dim == 3 ? (int)(r / ny) : 0;
 }
 
+// The 1D weights are dyadic (1, 3/4, 3/8, -1/8), so they and their products are
+// exact in either precision; the sums run in the vector's precision T.
 template <typename T, int DIM>
-__global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= gf.N * DIM) return;
-  const int c = (int)(t / gf.N);
-  int i, j, k;
-  node_ijk<DIM>(gf, t % gf.N, i, j, k);
-  if (on_boundary(gf, i, j, k)) { xf[t] = T(0); return; }
-  int mx[3], my[3], mz[3] = {0, 0, 0};
-  double wx[3], wy[3], wz[3] = {1.0, 0.0, 0.0};
-  const int nx = prolong_weights_1d(i, mx, wx), ny = prolong_weights_1d(j, my, wy);
-  const int nz = DIM == 3 ? prolong_weights_1d(k, mz, wz) : 1;
-  double acc = 0.0;
-  for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < ny; ++cy)
-      for (int cx = 0; cx < nx; ++cx) {
-        if (on_boundary(gc, mx[cx], my[cy], mz[cz])) continue;
-        acc += wx[cx] * wy[cy] * wz[cz] * (double)xc[c * gc.N + node_id(gc, mx[cx], my[cy], mz[cz])];
+__global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(gf.N * DIM)) return;
+  int c, i, j, k;
+  decode(gf, t, DIM, c, i, j, k);
+  if (on_boundary(gf, i, j, k)) { xf[t] = T(0); return; }   // xadd unchanged there
+  int mx[3], my[3], mz[3];
+  T wx[3], wy[3], wz[3];
+  bool ox[3], oy[3], oz[3];
+  prolong_taps(i, gc.nn[0], mx, wx, ox);
+  prolong_taps(j, gc.nn[1], my, wy, oy);
+  if (DIM == 3) prolong_taps(k, gc.nn[2], mz, wz, oz);
+  else { mz[0] = mz[1] = mz[2] = 0; wz[0] = T(1); wz[1] = wz[2] = T(0); oz[0] = true; oz[1] = oz[2] = false; }
+  const T* xcc = xc + (long long)c * gc.N;
+  T acc = T(0);
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 3 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      const long long row = (long long)gc.nn[0] * ((long long)my[cy] + (long long)gc.nn[1] * mz[cz]);
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) {
+        const bool use = ox[cx] && oy[cy] && oz[cz];
+        const T v = use ? xcc[row + mx[cx]] : T(0);
+        acc += wx[cx] * wy[cy] * wz[cz] * v;
       }
-  xf[t] = (T)acc;
+    }
+  xf[t] = acc;
+  if (xadd) xadd[t] += acc;
 }
 
 template <typename T, int DIM>
-__global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, T* __restrict__ rc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= gc.N * DIM) return;
-  const int c = (int)(t / gc.N);
-  int i, j, k;
-  node_ijk<DIM>(gc, t % gc.N, i, j, k);
+__global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub, T* __restrict__ rc) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(gc.N * DIM)) return;
+  int c, i, j, k;
+  decode(gc, t, DIM, c, i, j, k);
   if (on_boundary(gc, i, j, k)) { rc[t] = T(0); return; }
-  int fx[5], fy[5], fz[5] = {0, 0, 0, 0, 0};
-  double wx[5], wy[5], wz[5] = {1.0, 0, 0, 0, 0};
-  const int nx = restrict_weights_1d(i, gf.nn[0], fx, wx), ny = restrict_weights_1d(j, gf.nn[1], fy, wy);
-  const int nz = DIM == 3 ? restrict_weights_1d(k, gf.nn[2], fz, wz) : 1;
-  double acc = 0.0;
-  for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < ny; ++cy)
-      for (int cx = 0; cx < nx; ++cx) {
-        if (on_boundary(gf, fx[cx], fy[cy], fz[cz])) continue;
-        acc += wx[cx] * wy[cy] * wz[cz] * (double)rf[c * gf.N + node_id(gf, fx[cx], fy[cy], fz[cz])];
+  int fx[5], fy[5], fz[5];
+  T wx[5], wy[5], wz[5];
+  bool ox[5], oy[5], oz[5];
+  restrict_taps(i, gf.nn[0], fx, wx, ox);
+  restrict_taps(j, gf.nn[1], fy, wy, oy);
+  if (DIM == 3) restrict_taps(k, gf.nn[2], fz, wz, oz);
+  else {
+    for (int q = 0; q < 5; ++q) { fz[q] = 0; wz[q] = T(0); oz[q] = false; }
+    wz[0] = T(1); oz[0] = true;
+  }
+  const T* rfc = rf + (long long)c * gf.N;
+  const T* sbc = sub ? sub + (long long)c * gf.N : nullptr;
+  T acc = T(0);
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 5 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 5; ++cy) {
+      const long long row = (long long)gf.nn[0] * ((long long)fy[cy] + (long long)gf.nn[1] * fz[cz]);
+      T part = T(0);
+#pragma unroll
+      for (int cx = 0; cx < 5; ++cx) {
+        const bool use = ox[cx] && oy[cy] && oz[cz];
+        T v = T(0);
+        if (use) v = sbc ? rfc[row + fx[cx]] - sbc[row + fx[cx]] : rfc[row + fx[cx]];
+        part += wx[cx] * v;
       }
-  rc[t] = (T)acc;
+      acc += wy[cy] * wz[cz] * part;
+    }
+  rc[t] = acc;
 }
 
-void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s) {
+void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
+                 void* xadd) {
   const long long tot = fine.g.N * fine.g.dim;
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {
-    if (fine.g.dim == 2) k_prolong<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf);
-    else k_prolong<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf);
+    if (fine.g.dim == 2)
+      k_prolong<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
+    else k_prolong<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
   } else {
-    if (fine.g.dim == 2) k_prolong<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf);
-    else k_prolong<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf);
+    if (fine.g.dim == 2)
+      k_prolong<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+    else k_prolong<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
   }
   count_launch(1);
 }
 
-void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s) {
+void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
+                  const void* sub) {
   const long long tot = coarse.g.N * coarse.g.dim;
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {
-    if (fine.g.dim == 2) k_restrict<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (double*)rc);
-    else k_restrict<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (double*)rc);
+    if (fine.g.dim == 2)
+      k_restrict<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
+    else k_restrict<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
   } else {
-    if (fine.g.dim == 2) k_restrict<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (float*)rc);
-    else k_restrict<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (float*)rc);
+    if (fine.g.dim == 2)
+      k_restrict<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
+    else k_restrict<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
   }
   count_launch(1);
 }

@@ -195,6 +195,21 @@ def test_vcycle_fp64(smoother, d, n, levels):
     assert rel(host(x), H.vcycle(b)) <= 1e-12
 
 
+@pytest.mark.parametrize("sweeps,transfer", [(1, A.ALS_TRANSFER_ROBUST), (8, A.ALS_TRANSFER_STANDARD),
+                                             (10, A.ALS_TRANSFER_ROBUST)])
+def test_vcycle_fp64_gmres_steps(sweeps, transfer):
+    """GMRES smoothing with 1 and 8 steps (fused kernels, unnormalised basis, residual
+    from the Arnoldi relation) and 10 steps (the explicit path), both transfers."""
+    pb = sinker(2, 16, 3, 1.0, dr=1e2, seed=16)
+    ctx = context(pb, smoother=A.ALS_SMOOTH_GMRES, sweeps=sweeps, transfer=transfer)
+    H = oracle(pb, smoother="gmres", steps=sweeps,
+               transfer="robust" if transfer == A.ALS_TRANSFER_ROBUST else "standard")
+    b = random_free(H.levels[-1], 17)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.vcycle(b)) <= 1e-12
+
+
 def _max_patch_cond(H, lvl, count=40):
     m = H.levels[lvl].mesh
     verts = all_vertices(m)
