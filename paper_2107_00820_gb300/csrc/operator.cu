@@ -535,6 +535,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
   }
 }
 
+#include "apply_lines.cuh"
+
+// one launch of the cell kernel: the line form in 3D, the point form in 2D
+template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
+static void launch_cells(dim3 grid, cudaStream_t s, const Geom& g, const Colour& col, const CellConst<T>& cc,
+                         const T* x, T* y, const T* coef, const T* p_in, T* p_out, long long vstride, T* ebuf,
+                         const T* winv) {
+  if constexpr (DIM == 3)
+    k_apply_lines<T, TENSOR, MODE, STAGED><<<grid, 256, 0, s>>>(g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf,
+                                                                winv);
+  else
+    k_apply<T, DIM, TENSOR, MODE, STAGED><<<grid, 256, 0, s>>>(g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf,
+                                                               winv);
+}
+
 template <typename T, int DIM, bool TENSOR, int MODE>
 static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y, const void* p_in,
                          void* p_out, int nvec, long long vstride, cudaStream_t s) {
@@ -549,8 +564,9 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
   if (nvec == 1 && L.ebuf) {
     // one launch over all cells into the per-cell buffer, one gather launch per node
     const Colour col = all_cells(g);
-    k_apply<T, DIM, TENSOR, MODE, true><<<(unsigned)((col.count + CPB - 1) / CPB), 256, 0, s>>>(
-        g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in, (T*)p_out, 0, (T*)L.ebuf, winv);
+    launch_cells<T, DIM, TENSOR, MODE, true>(dim3((unsigned)((col.count + CPB - 1) / CPB)), s, g, col,
+                                             cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in,
+                                             (T*)p_out, 0, (T*)L.ebuf, winv);
     if (NEED_FLUX) {
       const long long tot = g.N * g.dim;
       k_gather_cells<T, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
@@ -572,8 +588,8 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
     for (int colour = 0; colour < ncol; ++colour) {
       const Colour col = NEED_FLUX ? make_colour(g, colour) : all_cells(g);
       dim3 grid((unsigned)((col.count + CPB - 1) / CPB), nv);
-      k_apply<T, DIM, TENSOR, MODE, false><<<grid, 256, 0, s>>>(g, col, cell_const<T>(g, gamma), xv, yv, coef,
-                                                                (const T*)p_in, (T*)p_out, vstride, nullptr, winv);
+      launch_cells<T, DIM, TENSOR, MODE, false>(grid, s, g, col, cell_const<T>(g, gamma), xv, yv, coef,
+                                                (const T*)p_in, (T*)p_out, vstride, nullptr, winv);
     }
     count_launch((NEED_FLUX ? 1 : 0) + ncol);
   }
@@ -642,8 +658,9 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
   if constexpr (std::is_same<T, double>::value) { coef = L.coef64; winv = L.winv64; }
   else { coef = L.coef32; winv = L.winv32; }
   const Colour col = all_cells(g);
-  k_apply<T, DIM, TENSOR, OP_VISC | OP_AL, true><<<(unsigned)((col.count + CPB - 1) / CPB), 256, 0, s>>>(
-      g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr, nullptr, 0, (T*)L.ebuf, winv);
+  launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true>(dim3((unsigned)((col.count + CPB - 1) / CPB)), s, g, col,
+                                                       cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr,
+                                                       nullptr, 0, (T*)L.ebuf, winv);
   const long long per_block = (long long)RED_THREADS * GATHER_PER;
   k_gather_epi<T, DIM><<<(unsigned)((g.N * DIM + per_block - 1) / per_block), RED_THREADS, 0, s>>>(
       g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
