@@ -292,13 +292,12 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
       T yd[3], yb[3];
       line_bwd<T, true>(v0, yd);
       line_bwd<T, false>(v1, yb);
-      if (act) {
-        if constexpr (STAGED) {
-          // per-cell outputs [cell][c][3^3], summed per node by the gather in a fixed order
-          T* e = ebuf + (cell * 3 + c) * NB + 3 * b1 + 9 * b2;
+      if constexpr (STAGED) {
+        // the cell's 27 x-line outputs to shared memory (row = lane); written out below
 #pragma unroll
-          for (int a = 0; a < 3; ++a) e[a] = yd[a] + yb[a];
-        } else {
+        for (int a = 0; a < 3; ++a) SA[lane * 3 + a] = yd[a] + yb[a];
+      } else if (act) {
+        {
           const int nj = 2 * cy + b1, nk = 2 * cz + b2;
           const long long row = (long long)c * g.N + (long long)(unsigned)(g.nn[0] * (nj + g.nn[1] * nk));
 #pragma unroll
@@ -306,6 +305,27 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
             const int ni = 2 * cx + a;
             if (RAW || !on_boundary(g, ni, nj, nk)) y[row + ni] += yd[a] + yb[a];
           }
+        }
+      }
+    }
+    if constexpr (STAGED) {
+      // Block write-out in the row layout (stage_row), summed per node by the gather in
+      // a fixed order: thread (row rr, cell wc) stores that cell's three values of the
+      // row, so the eight cells of a block (consecutive in x when n0 is a multiple of 8)
+      // fill one contiguous run of 24 values per row.
+      __shared__ int cc_xyz[8][4];
+      if (lane == 0) { cc_xyz[w][0] = cx; cc_xyz[w][1] = cy; cc_xyz[w][2] = cz; cc_xyz[w][3] = act ? 1 : 0; }
+      __syncthreads();
+      if (threadIdx.x < 27 * 8) {
+        const int rr = threadIdx.x >> 3, wc = threadIdx.x & 7;
+        if (cc_xyz[wc][3]) {
+          const int cr = rr / 9, lz = (rr / 3) % 3, ly = rr % 3;
+          T* e = ebuf + (long long)stage_row(g, cr, ly, lz, cc_xyz[wc][1], cc_xyz[wc][2]) * (3 * g.n[0]) +
+                 3 * cc_xyz[wc][0];
+          const T* src = &shA[wc][rr * 3];
+          e[0] = src[0];
+          e[1] = src[1];
+          e[2] = src[2];
         }
       }
     }

@@ -70,6 +70,18 @@ __host__ __device__ __forceinline__ long long node_id(const Geom& g, int i, int 
   return (long long)i + (long long)g.nn[0] * ((long long)j + (long long)g.nn[1] * k);
 }
 
+// Row layout of per-cell staged outputs (operator apply, star patches): the
+// value a cell (cx, cy, cz) contributes to its local node (lx, ly, lz) of
+// component c sits in row ((c L + lz) 3 + ly) n1 n2 + cz n1 + cy at column
+// 3 cx + lx, rows of 3 n0 values (L = 3 in 3D, 1 in 2D).  Along a row of
+// global nodes x = 0..2 n0 the contributions are then contiguous: node 2i reads
+// columns 3i-1 and 3i, node 2i+1 column 3i+1, so a gather over x is a
+// streaming read.
+__host__ __device__ __forceinline__ int stage_row(const Geom& g, int c, int ly, int lz, int cy, int cz) {
+  const int L = g.dim == 3 ? 3 : 1;
+  return ((c * L + lz) * 3 + ly) * (g.n[1] * g.n[2]) + cz * g.n[1] + cy;
+}
+
 template <int DIM> struct Sz;
 template <> struct Sz<2> { static constexpr int NB = 9, NP = 18, NPR = 3, NM = 3, NC = 6, NCELL_STAR = 4; };
 template <> struct Sz<3> { static constexpr int NB = 27, NP = 81, NPR = 4, NM = 6, NC = 21, NCELL_STAR = 8; };

@@ -397,10 +397,11 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
     }
   }
   if constexpr (STAGED) {
-    // per-cell outputs [cell][c][3^d], summed per node by k_gather_cells in a fixed order
+    // staged outputs in the row layout (stage_row), summed per node by the gather in a fixed order
     if (act) {
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) ebuf[(cell * DIM + c) * NB + l] = yl[c];
+      for (int c = 0; c < DIM; ++c)
+        ebuf[(long long)stage_row(g, c, i1, i2, cy, cz) * (3 * g.n[0]) + 3 * cx + i0] = yl[c];
     }
   } else {
     if (act && (RAW || !bnd)) {
@@ -428,67 +429,110 @@ __global__ void k_init_out(Geom g, const T* __restrict__ x, T* __restrict__ y, i
   y[t] = (bnd && keep_bnd) ? x[t] : T(0);
 }
 
-// (A x)(c, node) = sum of the per-cell outputs of the <= 2^d cells containing the
-// node, in a fixed order; Dirichlet rows: x_D (keep_bnd) or 0, unless raw.
-// Two fixed taps per axis (predicated), so all loads of a node issue together.
+// (A x) along a row of global nodes: one thread sums GX = 4 consecutive nodes
+// x = 4j .. 4j+3 of row (c, y, z) from the staged outputs (row layout, see
+// stage_row).  Per (y, z) tap pair the four nodes read the six contiguous
+// columns 6j-1 .. 6j+4; a column exists iff it lies in [0, 3 n0).  The taps are
+// added in a fixed order (z tap, y tap, then the x pair), so results are
+// reproducible.  Dirichlet rows: x_D (keep_bnd) or 0, unless raw.
+constexpr int GX = 4;
+
+struct RowChunk {
+  int c, y, z, j;
+  long long t0;   // vector index of node x = 4j
+};
+
+__device__ __forceinline__ bool row_chunk(const Geom& g, int dim, unsigned t, RowChunk& rc) {
+  const unsigned cpr = (unsigned)((g.nn[0] + GX - 1) / GX);
+  const unsigned rows = (unsigned)(dim * g.nn[1] * g.nn[2]);
+  const unsigned row = t / cpr;
+  if (row >= rows) return false;
+  rc.j = (int)(t - row * cpr);
+  const unsigned ny = (unsigned)g.nn[1], nz = (unsigned)g.nn[2];
+  const unsigned rz = row / ny;
+  rc.y = (int)(row - rz * ny);
+  rc.c = (int)(rz / nz);
+  rc.z = (int)(rz - (unsigned)rc.c * nz);
+  rc.t0 = (long long)rc.c * g.N + ((long long)rc.z * g.nn[1] + rc.y) * g.nn[0] + GX * rc.j;
+  return true;
+}
+
 template <typename T, int DIM>
-__device__ __forceinline__ T gather_node(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
-                                         unsigned t, int keep_bnd, int raw) {
-  constexpr int NB = Sz<DIM>::NB;
-  const unsigned N = (unsigned)g.N, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
-  const unsigned c = t / N, nd = t - c * N;
-  const unsigned r = nd / nx;
-  const int idx[3] = {(int)(nd - r * nx), DIM == 3 ? (int)(r % ny) : (int)r, DIM == 3 ? (int)(r / ny) : 0};
-  if (!raw && on_boundary(g, idx[0], idx[1], idx[2])) return keep_bnd ? x[t] : T(0);
-  // per axis: odd node -> its own cell (local 1); even node -> cell below (local 2) and
-  // above (local 0).  Tap 0 is the lower cell; tap 1 is one cell further along the axis.
-  int c0[3], l0[3], l1[3];
-  bool ok0[3], ok1[3];
+__device__ __forceinline__ void gather_chunk(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
+                                             const RowChunk& rc, int keep_bnd, int raw, T (&out)[GX]) {
+  const int nn0 = g.nn[0];
+  const bool row_bnd = rc.y == 0 || rc.y == g.nn[1] - 1 || (DIM == 3 && (rc.z == 0 || rc.z == g.nn[2] - 1));
+  if (!raw && row_bnd) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int i = a < DIM ? idx[a] : 1;
-    const int na = a < DIM ? g.n[a] : 1;
-    if (i & 1) { c0[a] = i >> 1; l0[a] = 1; ok0[a] = true; l1[a] = 0; ok1[a] = false; }
-    else { c0[a] = (i >> 1) - 1; l0[a] = 2; ok0[a] = i > 0; l1[a] = 0; ok1[a] = i < 2 * na; }
+    for (int q = 0; q < GX; ++q) {
+      const int xi = GX * rc.j + q;
+      out[q] = (keep_bnd && xi < nn0) ? x[rc.t0 + q] : T(0);
+    }
+    return;
   }
-  // cell index of tap (0,0,0) may be -1 along an axis whose lower tap is absent; the
-  // offsets below only combine it with taps that exist, so every address read is valid
-  const int sx = DIM * NB, sy = g.n[0] * DIM * NB, sz = g.n[0] * g.n[1] * DIM * NB;
-  const int base = (c0[0] + g.n[0] * (c0[1] + (DIM == 3 ? g.n[1] * c0[2] : 0))) * DIM * NB + (int)c * NB;
-  T v[DIM == 3 ? 8 : 4];
+  // y and z taps: (cell, local index, exists)
+  int cyv[2], lyv[2], czv[2], lzv[2];
+  bool oky[2], okz[2];
+  {
+    const int yy = rc.y;
+    if (yy & 1) { cyv[0] = yy >> 1; lyv[0] = 1; oky[0] = true; cyv[1] = 0; lyv[1] = 0; oky[1] = false; }
+    else { cyv[0] = (yy >> 1) - 1; lyv[0] = 2; oky[0] = yy > 0; cyv[1] = yy >> 1; lyv[1] = 0; oky[1] = yy < 2 * g.n[1]; }
+    const int zz = DIM == 3 ? rc.z : 1;
+    const int n2 = DIM == 3 ? g.n[2] : 1;
+    if (zz & 1) { czv[0] = zz >> 1; lzv[0] = 1; okz[0] = true; czv[1] = 0; lzv[1] = 0; okz[1] = false; }
+    else { czv[0] = (zz >> 1) - 1; lzv[0] = 2; okz[0] = zz > 0; czv[1] = zz >> 1; lzv[1] = 0; okz[1] = zz < 2 * n2; }
+    if (DIM == 2) { czv[0] = 0; lzv[0] = 0; }
+  }
+  const int ncol = 3 * g.n[0];
+  const int p0 = 6 * rc.j - 1;
+  T acc[GX];
 #pragma unroll
-  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+  for (int q = 0; q < GX; ++q) acc[q] = T(0);
 #pragma unroll
-    for (int cy = 0; cy < 2; ++cy)
+  for (int tz = 0; tz < (DIM == 3 ? 2 : 1); ++tz)
 #pragma unroll
-      for (int cx = 0; cx < 2; ++cx) {
-        const int q = cx + 2 * cy + 4 * cz;
-        const bool use = (cx ? ok1[0] : ok0[0]) && (cy ? ok1[1] : ok0[1]) && (DIM == 2 || (cz ? ok1[2] : ok0[2]));
-        const int l = (cx ? l1[0] : l0[0]) + 3 * (cy ? l1[1] : l0[1]) + (DIM == 3 ? 9 * (cz ? l1[2] : l0[2]) : 0);
-        const int off = base + cx * sx + cy * sy + (DIM == 3 ? cz * sz : 0) + l;
-        v[q] = use ? ebuf[off] : T(0);
+    for (int ty = 0; ty < 2; ++ty) {
+      if (!(oky[ty] && (DIM == 2 || okz[tz]))) continue;
+      const T* rowp = ebuf + (long long)stage_row(g, rc.c, lyv[ty], lzv[tz], cyv[ty], czv[tz]) * ncol;
+      T v[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int p = p0 + k;
+        v[k] = (p >= 0 && p < ncol) ? rowp[p] : T(0);
       }
-  T acc = T(0);
+      acc[0] += v[0] + v[1];
+      acc[1] += v[2];
+      acc[2] += v[3] + v[4];
+      acc[3] += v[5];
+    }
 #pragma unroll
-  for (int q = 0; q < (DIM == 3 ? 8 : 4); ++q) acc += v[q];
-  return acc;
+  for (int q = 0; q < GX; ++q) {
+    const int xi = GX * rc.j + q;
+    if (!raw && (xi == 0 || xi == nn0 - 1)) acc[q] = (keep_bnd && xi < nn0) ? x[rc.t0 + q] : T(0);
+    out[q] = acc[q];
+  }
 }
 
 template <typename T, int DIM>
 __global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
                                int keep_bnd, int raw) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)(g.N * DIM)) return;
-  y[t] = gather_node<T, DIM>(g, ebuf, x, t, keep_bnd, raw);
+  RowChunk rc;
+  if (!row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) return;
+  T out[GX];
+  gather_chunk<T, DIM>(g, ebuf, x, rc, keep_bnd, raw, out);
+#pragma unroll
+  for (int q = 0; q < GX; ++q)
+    if (GX * rc.j + q < g.nn[0]) y[rc.t0 + q] = out[q];
+}
+
+static unsigned gather_threads(const Geom& g) {
+  return (unsigned)(g.dim * g.nn[1] * g.nn[2] * ((g.nn[0] + GX - 1) / GX));
 }
 
 // Gather fused with the reduction that consumes the result:
 //   y = b + sigma A x (b NULL: y = sigma A x);  out[j] = (V_j . y) / hn[j], j < k;
 //   start: |y|^2 starts a GMRES cycle.  Fixed grid and order: reproducible.
-// Each thread gathers GATHER_PER entries (spaced RED_THREADS apart) with all
-// their loads issued first; the sums run in T inside a block, in double across blocks.
-constexpr int GATHER_PER = 4;
-
+// The sums run in T inside a block, in double across blocks.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __restrict__ ebuf,
                                                             const T* __restrict__ x, T* __restrict__ y,
@@ -497,30 +541,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
                                                             double* __restrict__ out, int start, GmresDev st,
                                                             double* __restrict__ partial) {
   __shared__ double nrm2_s[1];
-  const unsigned n = (unsigned)(g.N * DIM);
-  const unsigned base = blockIdx.x * (RED_THREADS * GATHER_PER) + threadIdx.x;
   const int kk = start ? 1 : k;
-  T yv[GATHER_PER];
-#pragma unroll
-  for (int q = 0; q < GATHER_PER; ++q) {
-    const unsigned t = base + q * RED_THREADS;
-    yv[q] = t < n ? gather_node<T, DIM>(g, ebuf, x, t, 1, 0) : T(0);
-  }
   T acc[KMAXB];
 #pragma unroll
   for (int j = 0; j < KMAXB; ++j) acc[j] = T(0);
+  RowChunk rc;
+  if (row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) {
+    T ax[GX];
+    gather_chunk<T, DIM>(g, ebuf, x, rc, 1, 0, ax);
 #pragma unroll
-  for (int q = 0; q < GATHER_PER; ++q) {
-    const unsigned t = base + q * RED_THREADS;
-    if (t < n) {
-      const T v = (b ? b[t] : T(0)) + (T)sigma * yv[q];
+    for (int q = 0; q < GX; ++q) {
+      if (GX * rc.j + q >= g.nn[0]) break;
+      const long long t = rc.t0 + q;
+      const T v = (b ? b[t] : T(0)) + (T)sigma * ax[q];
       y[t] = v;
       if (start) {
         acc[0] += v * v;
       } else {
 #pragma unroll
-        for (int j = 0; j < KMAXB; ++j)
-          if (j < k) acc[j] += V[(long long)j * ld + t] * v;
+        for (int jj = 0; jj < KMAXB; ++jj)
+          if (jj < k) acc[jj] += V[(long long)jj * ld + t] * v;
       }
     }
   }
@@ -568,8 +608,7 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
                                              cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in,
                                              (T*)p_out, 0, (T*)L.ebuf, winv);
     if (NEED_FLUX) {
-      const long long tot = g.N * g.dim;
-      k_gather_cells<T, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
+      k_gather_cells<T, DIM><<<(gather_threads(g) + 255) / 256, 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
                                                                           (T*)y, keep_bnd, (MODE & OP_RAW) ? 1 : 0);
     }
     count_launch(NEED_FLUX ? 2 : 1);
@@ -661,8 +700,7 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
   launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true>(dim3((unsigned)((col.count + CPB - 1) / CPB)), s, g, col,
                                                        cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr,
                                                        nullptr, 0, (T*)L.ebuf, winv);
-  const long long per_block = (long long)RED_THREADS * GATHER_PER;
-  k_gather_epi<T, DIM><<<(unsigned)((g.N * DIM + per_block - 1) / per_block), RED_THREADS, 0, s>>>(
+  k_gather_epi<T, DIM><<<(gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(
       g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
       e.st, e.partial);
   count_launch(2);
