@@ -82,6 +82,44 @@ __host__ __device__ __forceinline__ int stage_row(const Geom& g, int c, int ly, 
   return ((c * L + lz) * 3 + ly) * (g.n[1] * g.n[2]) + cz * g.n[1] + cy;
 }
 
+// Row gathers: one thread handles GX consecutive nodes x = GX j .. GX j + GX-1 of
+// the node row (component c, y, z).
+constexpr int GX = 4;
+
+struct RowChunk {
+  int c, y, z, j;
+  long long t0;   // vector index of node x = 4j
+};
+
+__device__ __forceinline__ bool row_chunk(const Geom& g, int dim, unsigned t, RowChunk& rc) {
+  const unsigned cpr = (unsigned)((g.nn[0] + GX - 1) / GX);
+  const unsigned rows = (unsigned)(dim * g.nn[1] * g.nn[2]);
+  const unsigned row = t / cpr;
+  if (row >= rows) return false;
+  rc.j = (int)(t - row * cpr);
+  const unsigned ny = (unsigned)g.nn[1], nz = (unsigned)g.nn[2];
+  const unsigned rz = row / ny;
+  rc.y = (int)(row - rz * ny);
+  rc.c = (int)(rz / nz);
+  rc.z = (int)(rz - (unsigned)rc.c * nz);
+  rc.t0 = (long long)rc.c * g.N + ((long long)rc.z * g.nn[1] + rc.y) * g.nn[0] + GX * rc.j;
+  return true;
+}
+
+// Row layout of vertex-star patch outputs: entry (c, ox, oy, oz) of the patch of
+// vertex (vx, vy, vz) (node 2v - 1 + o per axis) sits in row
+// ((c L + oz) 3 + oy) nv1 nv2 + vz nv1 + vy at column 3 vx + ox, rows of 3 nv0
+// values.  Node 2v reads column 3v+1; node 2v+1 reads columns 3v+2 and 3v+3.
+template <int DIM>
+__host__ __device__ __forceinline__ long long patch_out_index(const Geom& g, int vx, int vy, int vz, int i) {
+  constexpr int NB = DIM == 3 ? 27 : 9;
+  const int c = i / NB, o = i - c * NB;
+  const int ox = o % 3, oy = (o / 3) % 3, oz = DIM == 3 ? o / 9 : 0;
+  const int L = DIM == 3 ? 3 : 1;
+  const int row = ((c * L + oz) * 3 + oy) * (g.nv[1] * g.nv[2]) + vz * g.nv[1] + vy;
+  return (long long)row * (3 * g.nv[0]) + 3 * vx + ox;
+}
+
 template <int DIM> struct Sz;
 template <> struct Sz<2> { static constexpr int NB = 9, NP = 18, NPR = 3, NM = 3, NC = 6, NCELL_STAR = 4; };
 template <> struct Sz<3> { static constexpr int NB = 27, NP = 81, NPR = 4, NM = 6, NC = 21, NCELL_STAR = 8; };

@@ -435,28 +435,6 @@ __global__ void k_init_out(Geom g, const T* __restrict__ x, T* __restrict__ y, i
 // columns 6j-1 .. 6j+4; a column exists iff it lies in [0, 3 n0).  The taps are
 // added in a fixed order (z tap, y tap, then the x pair), so results are
 // reproducible.  Dirichlet rows: x_D (keep_bnd) or 0, unless raw.
-constexpr int GX = 4;
-
-struct RowChunk {
-  int c, y, z, j;
-  long long t0;   // vector index of node x = 4j
-};
-
-__device__ __forceinline__ bool row_chunk(const Geom& g, int dim, unsigned t, RowChunk& rc) {
-  const unsigned cpr = (unsigned)((g.nn[0] + GX - 1) / GX);
-  const unsigned rows = (unsigned)(dim * g.nn[1] * g.nn[2]);
-  const unsigned row = t / cpr;
-  if (row >= rows) return false;
-  rc.j = (int)(t - row * cpr);
-  const unsigned ny = (unsigned)g.nn[1], nz = (unsigned)g.nn[2];
-  const unsigned rz = row / ny;
-  rc.y = (int)(row - rz * ny);
-  rc.c = (int)(rz / nz);
-  rc.z = (int)(rz - (unsigned)rc.c * nz);
-  rc.t0 = (long long)rc.c * g.N + ((long long)rc.z * g.nn[1] + rc.y) * g.nn[0] + GX * rc.j;
-  return true;
-}
-
 template <typename T, int DIM>
 __device__ __forceinline__ void gather_chunk(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
                                              const RowChunk& rc, int keep_bnd, int raw, T (&out)[GX]) {

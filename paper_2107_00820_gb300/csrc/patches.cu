@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
 #pragma unroll
       for (int jb = 0; jb < NBR; ++jb) acc += part[(p * NP + i) * NBR + jb];
       if (mode == OUT_SCRATCH) {
-        out[(long long)v * NP + i] = acc;
+        out[patch_out_index<DIM>(g, vx, vy, vz, i)] = acc;
       } else {
         long long nd;
         if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __res
 #pragma unroll
       for (int jb = 0; jb < NBR; ++jb) acc += part[buf][p][i][jb];
       if (mode == OUT_SCRATCH) {
-        out[(long long)v * NP + i] = acc;
+        out[patch_out_index<DIM>(g, vx, vy, vz, i)] = acc;
       } else {
         long long nd;
         if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
@@ -771,60 +771,79 @@ __global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restric
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int i = lane + 32 * k;
-      if (i < NP) out[v * NP + i] = acc[k];
+      if (i < NP) out[patch_out_index<DIM>(g, vx, vy, vz, i)] = acc[k];
     }
     __syncwarp();
   }
 }
 
-// z at node (c, i, j, k) = sum of the patch outputs of the vertices whose star
-// contains it (fixed order; two predicated taps per axis, all loads issued at once),
-// divided by den[0] when den is given
+// z on GX consecutive nodes of a node row = sum of the outputs of the patches whose
+// stars contain each node (row layout, patch_out_index): per (y, z) tap pair the
+// chunk x = 4j .. 4j+3 reads the six contiguous columns 6j+1 .. 6j+6 (node 4j:
+// first; 4j+1: second and third; 4j+2: fourth; 4j+3: fifth and sixth).  Fixed
+// order; Dirichlet nodes get 0; divided by den[0] when den is given.
 template <typename TV, int DIM>
 __global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
                                const double* __restrict__ den) {
-  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB;
   __shared__ TV inv_den;
   if (den) {                        // one division per block, not per entry
     if (threadIdx.x == 0) inv_den = den[0] != 0.0 ? (TV)(1.0 / den[0]) : TV(0);
     __syncthreads();
   }
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)(g.N * DIM)) return;
-  const unsigned N = (unsigned)g.N, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
-  const int c = (int)(t / N);
-  const unsigned nd = t - (unsigned)c * N;
-  const unsigned rr = nd / nx;
-  const int idx[3] = {(int)(nd - rr * nx), DIM == 3 ? (int)(rr % ny) : (int)rr, DIM == 3 ? (int)(rr / ny) : 0};
-  if (on_boundary(g, idx[0], idx[1], idx[2])) { z[t] = TV(0); return; }
-  // per axis: even node index -> its own vertex (offset 1); odd -> the two neighbours (offsets 2, 0)
-  int vv[3][2], oo[3][2];
-  bool ok[3][2];
+  RowChunk rc;
+  if (!row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) return;
+  const int nn0 = g.nn[0];
+  TV acc[GX];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int i = a < DIM ? idx[a] : 0;
-    if ((i & 1) == 0) { vv[a][0] = i >> 1; oo[a][0] = 1; ok[a][0] = true; vv[a][1] = 0; oo[a][1] = 0; ok[a][1] = false; }
-    else { vv[a][0] = (i - 1) >> 1; oo[a][0] = 2; ok[a][0] = true; vv[a][1] = (i + 1) >> 1; oo[a][1] = 0; ok[a][1] = true; }
-  }
-  TV v[DIM == 3 ? 8 : 4];
+  for (int q = 0; q < GX; ++q) acc[q] = TV(0);
+  const bool row_bnd = rc.y == 0 || rc.y == g.nn[1] - 1 || (DIM == 3 && (rc.z == 0 || rc.z == g.nn[2] - 1));
+  if (!row_bnd) {
+    // per axis: even node 2v -> vertex v (offset 1); odd node 2v+1 -> vertices v (offset 2), v+1 (offset 0)
+    int vyv[2], oyv[2], vzv[2], ozv[2];
+    bool oky[2], okz[2];
+    if (rc.y & 1) { vyv[0] = rc.y >> 1; oyv[0] = 2; vyv[1] = vyv[0] + 1; oyv[1] = 0; oky[0] = oky[1] = true; }
+    else { vyv[0] = rc.y >> 1; oyv[0] = 1; oky[0] = true; vyv[1] = 0; oyv[1] = 0; oky[1] = false; }
+    if (DIM == 3) {
+      if (rc.z & 1) { vzv[0] = rc.z >> 1; ozv[0] = 2; vzv[1] = vzv[0] + 1; ozv[1] = 0; okz[0] = okz[1] = true; }
+      else { vzv[0] = rc.z >> 1; ozv[0] = 1; okz[0] = true; vzv[1] = 0; ozv[1] = 0; okz[1] = false; }
+    } else {
+      vzv[0] = 0; ozv[0] = 0; okz[0] = true; vzv[1] = 0; ozv[1] = 0; okz[1] = false;
+    }
+    const int ncol = 3 * g.nv[0];
+    const int L = DIM == 3 ? 3 : 1;
+    const int p0 = 6 * rc.j + 1;
 #pragma unroll
-  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+    for (int tz = 0; tz < (DIM == 3 ? 2 : 1); ++tz)
 #pragma unroll
-    for (int cy = 0; cy < 2; ++cy)
+      for (int ty = 0; ty < 2; ++ty) {
+        if (!(oky[ty] && okz[tz])) continue;
+        const int row = ((rc.c * L + ozv[tz]) * 3 + oyv[ty]) * (g.nv[1] * g.nv[2]) + vzv[tz] * g.nv[1] + vyv[ty];
+        const TV* rowp = out + (long long)row * ncol;
+        TV v[6];
 #pragma unroll
-      for (int cx = 0; cx < 2; ++cx) {
-        const int q = cx + 2 * cy + 4 * cz;
-        const bool use = ok[0][cx] && ok[1][cy] && (DIM == 2 || ok[2][cz]);
-        const long long vid = (long long)vv[0][cx] +
-                              (long long)g.nv[0] * ((long long)vv[1][cy] + (DIM == 3 ? (long long)g.nv[1] * vv[2][cz] : 0));
-        const int o = oo[0][cx] + 3 * oo[1][cy] + (DIM == 3 ? 9 * oo[2][cz] : 0);
-        v[q] = use ? out[vid * NP + c * NB + o] : TV(0);
+        for (int k = 0; k < 6; ++k) {
+          const int p = p0 + k;
+          v[k] = p < ncol ? rowp[p] : TV(0);
+        }
+        acc[0] += v[0];
+        acc[1] += v[1] + v[2];
+        acc[2] += v[3];
+        acc[3] += v[4] + v[5];
       }
-  TV acc = TV(0);
+  }
 #pragma unroll
-  for (int q = 0; q < (DIM == 3 ? 8 : 4); ++q) acc += v[q];
-  if (den) acc *= inv_den;
-  z[t] = acc;
+  for (int q = 0; q < GX; ++q) {
+    const int xi = GX * rc.j + q;
+    if (xi >= nn0) break;
+    TV vq = (row_bnd || xi == 0 || xi == nn0 - 1) ? TV(0) : acc[q];
+    if (den) vq *= inv_den;
+    z[rc.t0 + q] = vq;
+  }
+}
+
+static unsigned row_gather_blocks(const Geom& g, int dim) {
+  const long long th = (long long)dim * g.nn[1] * g.nn[2] * ((g.nn[0] + GX - 1) / GX);
+  return (unsigned)((th + 255) / 256);
 }
 
 size_t patch_scratch_bytes(const LevelDev& L, int prec) {
@@ -840,8 +859,7 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   k_patch_apply<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  const long long tot = L.g.N * DIM;
-  k_patch_gather<TV, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z, den);
+  k_patch_gather<TV, DIM><<<row_gather_blocks(L.g, DIM), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z, den);
   count_launch(2);
 }
 
@@ -854,9 +872,8 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
   else
     launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  const long long tot = L.g.N * DIM;
-  k_patch_gather<float, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z,
-                                                                           den);
+  k_patch_gather<float, DIM><<<row_gather_blocks(L.g, DIM), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z,
+                                                                         den);
   count_launch(1);
 }
 
