@@ -268,6 +268,11 @@ METRIC = "AL-MG V-cycles/s & solve DoF/s to 1e-8 rel. residual, mixed vs FP64, 1
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+# flops per cell of the sum-factorised A_gamma apply (scalar mu): forward
+# gradients, point-wise stress and AL projection, transposed contractions
+APPLY_FLOPS_PER_CELL = {2: 1100, 3: 8000}
+
+
 def ours(args, dist):
     import numpy as np
     import torch
@@ -315,7 +320,26 @@ def ours(args, dist):
     launches = A.als_kernel_launches() - launches0
     clk = clocks.stop()
     k4_ms, k4_n = ctx.profile_read()
+    k1_ms, k1_n = ctx.profile_read_kernel(1)
     ctx.profile(False)
+
+    # phases of one step: setup alone, solve alone (CUDA events on the stream); the
+    # first solve after profiling recaptures the V-cycle graphs and is not timed
+    ctx.solve(f_d, ubc_d, None, u_d, p_d)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(3):
+        ctx.update_coefficients(mu_d)
+    p1.record()
+    torch.cuda.synchronize()
+    t_setup = p0.elapsed_time(p1) / 3 / 1e3
+    p0.record()
+    info_s = ctx.solve(f_d, ubc_d, None, u_d, p_d)[2]
+    p1.record()
+    torch.cuda.synchronize()
+    t_solve = p0.elapsed_time(p1) / 1e3
+    fp32_peak, fp64_peak = A.als_measure_fma_peaks(stream)
     t_step = dist.max(e0.elapsed_time(e1) / args.steps) / 1e3
     value = dist.world * dofs / t_step
 
@@ -355,6 +379,11 @@ def ours(args, dist):
     e1.record()
     torch.cuda.synchronize()
     t64 = e0.elapsed_time(e1) / 1e3
+    e0.record()
+    ctx64.solve(f_d, ubc_d, None, u64, p64)
+    e1.record()
+    torch.cuda.synchronize()
+    t64_solve = e0.elapsed_time(e1) / 1e3
     err_u = float(torch.linalg.norm(u_d - u64) / torch.linalg.norm(u64))
     err_p = float(torch.linalg.norm(p_d - p64) / torch.linalg.norm(p64))
     ctx64.close()
@@ -390,6 +419,22 @@ def ours(args, dist):
     k4_launch_s = (k4_ms / max(k4_n, 1)) / 1e3
     achieved = bytes_per_launch / k4_launch_s / 1e9 if k4_n else None
     peak, peak_kind = measured_peak_hbm()
+    # operator apply (K1 cell kernel) on the finest level, timed live inside the smoother
+    ncells = math.prod(F)
+    nq = 3 ** pb.d
+    k1_bytes = nu * 4 * 2 + ncells * nq * 4            # read x, write y, read mu (FP32)
+    k1_flops = ncells * APPLY_FLOPS_PER_CELL[pb.d]
+    k1_s = (k1_ms / max(k1_n, 1)) / 1e3
+    roofline_apply = None
+    if k1_n:
+        roofline_apply = {
+            "bound": "alu", "kernel": "k_apply_lines (FP32 A_gamma cell kernel, finest level)",
+            "achieved": k1_flops / k1_s / 1e12, "peak": fp32_peak, "peak_kind": "measured FP32 FMA",
+            "unit": "TFLOP/s", "frac": (k1_flops / k1_s / 1e12) / fp32_peak if fp32_peak else None,
+            "hbm": {"achieved": k1_bytes / k1_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": (k1_bytes / k1_s / 1e9) / peak},
+            "us_per_launch": k1_s * 1e6, "launches_timed": k1_n,
+            "bytes_per_launch": k1_bytes, "flops_per_launch": k1_flops}
     out = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -413,6 +458,12 @@ def ours(args, dist):
                      "frac": (achieved / peak) if achieved else None,
                      "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,
                      "traffic": stored_traffic("k_patch_apply_f32_fine", args.workload)},
+        "roofline_apply": roofline_apply,
+        "phases": {"setup_ms": t_setup * 1e3, "solve_ms": t_solve * 1e3,
+                   "solve_dof_per_s": dofs / t_solve, "solve_iterations": info_s.iterations,
+                   "fp64_solve_ms": t64_solve * 1e3, "fp64_solve_dof_per_s": dofs / t64_solve},
+        "measured_peaks": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
+                           "how": "als_measure_fma_peaks: FMA chains on every SM, CUDA events"},
         "gpu_launches": launches,
         "clocks": clk,
     }

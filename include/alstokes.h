@@ -178,6 +178,11 @@ als_status als_update_coefficients(als_ctx* ctx, const als_coeff* coeff);
  * read, and restarts the accumulation.  als_profile(ctx, 0) turns it off. */
 als_status als_profile(als_ctx* ctx, int on);
 als_status als_profile_read(als_ctx* ctx, double* total_ms, long long* launches);
+/* As als_profile_read for one kernel class: kind 0 = the finest-level star-patch
+ * kernel (same as als_profile_read), kind 1 = the finest-level operator-apply cell
+ * kernel of the GMRES smoother steps (its node gather excluded).  Each kind
+ * accumulates separately and is reset by its own read.  ALS_EINVAL for another kind. */
+als_status als_profile_read_kernel(als_ctx* ctx, int kind, double* total_ms, long long* launches);
 
 /* Process-wide number of kernels this library has launched (a replay of a
  * captured V-cycle counts its kernel nodes). */
@@ -211,6 +216,13 @@ long long als_kernel_launches(void);
 #define ALS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 als_status als_star_smooth_static(int dim, const int* n, int prec, const void* inv, const void* r, void* z,
                                   void* stream);
+
+/* Measured FP32 and FP64 fused multiply-add throughput of the current GPU's
+ * CUDA cores, in TFLOP/s (2 flops per FMA), for the ALU rooflines.  Runs two
+ * short kernels (about 0.1 s) on `stream` (a cudaStream_t) and waits for them;
+ * allocates and frees 2 KiB of device memory.  Returns ALS_EINVAL for NULL
+ * outputs, ALS_ENOMEM or ALS_ECUDA on a runtime failure. */
+als_status als_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
 /* Last error message of the context (never NULL; "" when none). */
 const char* als_last_error(const als_ctx* ctx);

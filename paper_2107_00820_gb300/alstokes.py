@@ -64,8 +64,10 @@ SIGNATURES = {
     "als_update_coefficients": (c_int, [c_void_p, POINTER(als_coeff)]),
     "als_profile": (c_int, [c_void_p, c_int]),
     "als_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
+    "als_profile_read_kernel": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
     "als_kernel_launches": (c_longlong, []),
     "als_star_smooth_static": (c_int, [c_int, POINTER(c_int), c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "als_measure_fma_peaks": (c_int, [POINTER(c_double), POINTER(c_double), c_void_p]),
 }
 
 _LIB = None
@@ -253,6 +255,12 @@ class Context:
         self._call("als_profile_read", byref(ms), byref(n))
         return ms.value, n.value
 
+    def profile_read_kernel(self, kind):
+        """(total ms, launches) of kernel class `kind` (0 patch kernel, 1 operator apply)."""
+        ms, n = c_double(), c_longlong()
+        self._call("als_profile_read_kernel", c_int(kind), byref(ms), byref(n))
+        return ms.value, n.value
+
     def close(self):
         if getattr(self, "_ctx", None) is not None:
             self._lib.als_destroy(self._ctx)
@@ -303,3 +311,12 @@ def als_star_smooth_static(dim, n, prec, inv, r, z, stream=None):
                                        c_void_p(stream) if stream else None)
     if st != ALS_OK:
         raise ALSError(st, "als_star_smooth_static failed")
+
+
+def als_measure_fma_peaks(stream=None):
+    """Measured (FP32, FP64) FMA throughput of the current GPU in TFLOP/s."""
+    f32, f64 = c_double(), c_double()
+    st = load().als_measure_fma_peaks(byref(f32), byref(f64), c_void_p(stream) if stream else None)
+    if st != ALS_OK:
+        raise ALSError(st, "als_measure_fma_peaks failed")
+    return f32.value, f64.value

@@ -33,17 +33,26 @@ struct MGWork {
   long long graph_kernels = 0;
 };
 
-// Live timing of the finest-level patch kernel (K4) inside the V-cycle: the
-// captured graph holds event-record nodes around each such launch; before every
-// replay they are re-pointed at fresh events from a pool, so every launch of
+// Live timing of finest-level kernels inside the V-cycle: kind 0 = the star-patch
+// kernel (K4), kind 1 = the operator-apply cell kernel (K1, without its gather).
+// The captured graph holds event-record nodes around each such launch; before
+// every replay they are re-pointed at fresh events from a pool, so every launch of
 // the timed region is measured with CUDA events on the stream it runs on.
+struct ProfPair {
+  size_t a, b;
+  int kind;
+};
 struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> slots;           // events recorded at capture time (2 per launch)
+  std::vector<int> slot_kind;               // kind of each captured pair, capture order
   std::vector<cudaGraphNode_t> nodes32, nodes64;
+  std::vector<int> kinds32, kinds64;
   std::vector<cudaEvent_t> pool;
   size_t next = 0;
-  std::vector<std::pair<size_t, size_t>> pairs;
+  std::vector<ProfPair> pairs;
+  double acc_ms[2] = {0.0, 0.0};
+  long long acc_n[2] = {0, 0};
   cudaEvent_t spare0 = nullptr, spare1 = nullptr;
 };
 
@@ -207,13 +216,13 @@ cudaEvent_t prof_take(als_ctx* c);
 
 // events for the k-th finest-level patch launch of the V-cycle being issued:
 // placeholders while a graph is captured, pool events otherwise
-void prof_events(als_ctx* c, int& counter, cudaEvent_t& e0, cudaEvent_t& e1) {
+void prof_events(als_ctx* c, int& counter, cudaEvent_t& e0, cudaEvent_t& e1, int kind = 0) {
   e0 = e1 = nullptr;
   if (!c->prof.on) return;
   if (!t_capturing) {
     e0 = prof_take(c);
     e1 = prof_take(c);
-    if (e0 && e1) c->prof.pairs.push_back({c->prof.next - 2, c->prof.next - 1});
+    if (e0 && e1) c->prof.pairs.push_back({c->prof.next - 2, c->prof.next - 1, kind});
     else e0 = e1 = nullptr;
     return;
   }
@@ -225,6 +234,8 @@ void prof_events(als_ctx* c, int& counter, cudaEvent_t& e0, cudaEvent_t& e1) {
   }
   e0 = c->prof.slots[2 * counter];
   e1 = c->prof.slots[2 * counter + 1];
+  if (c->prof.slot_kind.size() < (size_t)counter + 1) c->prof.slot_kind.resize(counter + 1);
+  c->prof.slot_kind[counter] = kind;
   ++counter;
 }
 
@@ -267,7 +278,9 @@ void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
     if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
     patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, st.hn + j);  // Z_j = D^-1 v_j
     ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, st.H + (size_t)j * sl.ldh, 0, st, w.partial};
-    op_apply_epi(Lv, prec, c->gamma, Zj, Vn, e, s);                      // A Z_j, H[0..j][j]
+    cudaEvent_t a0 = nullptr, a1 = nullptr;
+    if (l == c->L - 1) prof_events(c, t_prof_counter, a0, a1, 1);
+    op_apply_epi(Lv, prec, c->gamma, Zj, Vn, e, s, a0, a1);            // A Z_j, H[0..j][j]
     gm_orth(prec, len, j, w.V[l], len, w.partial, st, s);                 // V_{j+1}, Givens step j
   }
   gm_update(prec, len, steps, w.Z[l], w.V[l], len, st, w.x[l], x_is_zero ? 1 : 0, t, s);
@@ -385,6 +398,7 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
     return cuda_check(c, "vcycle");
   }
   std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
+  std::vector<int>& kinds = w.prec == PREC_F64 ? pf.kinds64 : pf.kinds32;
   if (!w.graph) {
     t_prof_counter = 0;
     const long long c0 = launch_count();
@@ -401,6 +415,7 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
       // map every event-record node to its slot (capture order is the slot order)
       const int nslots = 2 * t_prof_counter;
       nodes.assign(nslots, nullptr);
+      kinds.assign(pf.slot_kind.begin(), pf.slot_kind.begin() + t_prof_counter);
       size_t nn = 0;
       cudaGraphGetNodes(w.graph_tmpl, nullptr, &nn);
       std::vector<cudaGraphNode_t> all(nn);
@@ -422,7 +437,7 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
     for (size_t i = 0; i + 1 < nodes.size(); i += 2) {
       cudaEvent_t a = prof_take(c), b = prof_take(c);
       if (!a || !b) { a = pf.spare0; b = pf.spare1; }
-      else pf.pairs.push_back({pf.next - 2, pf.next - 1});
+      else pf.pairs.push_back({pf.next - 2, pf.next - 1, kinds[i / 2]});
       if (nodes[i]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i], a);
       if (nodes[i + 1]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i + 1], b);
     }
@@ -715,28 +730,41 @@ als_status als_profile(als_ctx* c, int on) {
   }
   p.next = 0;
   p.pairs.clear();
+  p.acc_ms[0] = p.acc_ms[1] = 0.0;
+  p.acc_n[0] = p.acc_n[1] = 0;
   return ALS_OK;
 }
 
-als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) {
-  if (!c || !total_ms || !launches) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
+// moves the recorded pairs into the per-kind accumulators
+static als_status prof_drain(als_ctx* c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "profile read");
-  double tot = 0.0;
-  long long n = 0;
   for (auto& pr : c->prof.pairs) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->prof.pool[pr.first], c->prof.pool[pr.second]) == cudaSuccess) {
-      tot += ms;
-      ++n;
+    if (cudaEventElapsedTime(&ms, c->prof.pool[pr.a], c->prof.pool[pr.b]) == cudaSuccess) {
+      c->prof.acc_ms[pr.kind] += ms;
+      c->prof.acc_n[pr.kind] += 1;
     } else {
       cudaGetLastError();  // an unrecorded pair is skipped, not left as a sticky error
     }
   }
-  *total_ms = tot;
-  *launches = n;
   c->prof.pairs.clear();
   c->prof.next = 0;
   return ALS_OK;
+}
+
+als_status als_profile_read_kernel(als_ctx* c, int kind, double* total_ms, long long* launches) {
+  if (!c || !total_ms || !launches) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
+  if (kind < 0 || kind > 1) return fail(c, ALS_EINVAL, "kind must be 0 (patch kernel) or 1 (operator apply)");
+  ALS_TRY(prof_drain(c));
+  *total_ms = c->prof.acc_ms[kind];
+  *launches = c->prof.acc_n[kind];
+  c->prof.acc_ms[kind] = 0.0;
+  c->prof.acc_n[kind] = 0;
+  return ALS_OK;
+}
+
+als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) {
+  return als_profile_read_kernel(c, 0, total_ms, launches);
 }
 
 long long als_kernel_launches(void) { return launch_count(); }

@@ -54,8 +54,9 @@ struct ApplyEpi {
   GmresDev st;
   double* partial;
 };
+// e0/e1 (optional) are recorded immediately before and after the cell kernel
 void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
-                  cudaStream_t s);
+                  cudaStream_t s, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 void op_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
 void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y, int nvec,
                     long long stride, cudaStream_t s);

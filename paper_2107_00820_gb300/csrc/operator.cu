@@ -667,7 +667,7 @@ void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x
 
 template <typename T, int DIM, bool TENSOR>
 static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, void* y, const ApplyEpi& e,
-                             cudaStream_t s) {
+                             cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   const Geom& g = L.g;
   constexpr int CPB = 8 * (DIM == 2 ? 3 : 1);
   const T* coef = nullptr;
@@ -675,9 +675,12 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
   if constexpr (std::is_same<T, double>::value) { coef = L.coef64; winv = L.winv64; }
   else { coef = L.coef32; winv = L.winv32; }
   const Colour col = all_cells(g);
+  // External records become event-record nodes when the stream is being captured
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true>(dim3((unsigned)((col.count + CPB - 1) / CPB)), s, g, col,
                                                        cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr,
                                                        nullptr, 0, (T*)L.ebuf, winv);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   k_gather_epi<T, DIM><<<(gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(
       g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
       e.st, e.partial);
@@ -685,22 +688,22 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
 }
 
 void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
-                  cudaStream_t s) {
+                  cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   if (prec == PREC_F64) {
     if (L.g.dim == 2) {
-      if (L.tensor) launch_apply_epi<double, 2, true>(L, gamma, x, y, e, s);
-      else launch_apply_epi<double, 2, false>(L, gamma, x, y, e, s);
+      if (L.tensor) launch_apply_epi<double, 2, true>(L, gamma, x, y, e, s, e0, e1);
+      else launch_apply_epi<double, 2, false>(L, gamma, x, y, e, s, e0, e1);
     } else {
-      if (L.tensor) launch_apply_epi<double, 3, true>(L, gamma, x, y, e, s);
-      else launch_apply_epi<double, 3, false>(L, gamma, x, y, e, s);
+      if (L.tensor) launch_apply_epi<double, 3, true>(L, gamma, x, y, e, s, e0, e1);
+      else launch_apply_epi<double, 3, false>(L, gamma, x, y, e, s, e0, e1);
     }
   } else {
     if (L.g.dim == 2) {
-      if (L.tensor) launch_apply_epi<float, 2, true>(L, gamma, x, y, e, s);
-      else launch_apply_epi<float, 2, false>(L, gamma, x, y, e, s);
+      if (L.tensor) launch_apply_epi<float, 2, true>(L, gamma, x, y, e, s, e0, e1);
+      else launch_apply_epi<float, 2, false>(L, gamma, x, y, e, s, e0, e1);
     } else {
-      if (L.tensor) launch_apply_epi<float, 3, true>(L, gamma, x, y, e, s);
-      else launch_apply_epi<float, 3, false>(L, gamma, x, y, e, s);
+      if (L.tensor) launch_apply_epi<float, 3, true>(L, gamma, x, y, e, s, e0, e1);
+      else launch_apply_epi<float, 3, false>(L, gamma, x, y, e, s, e0, e1);
     }
   }
 }
