@@ -61,6 +61,8 @@ enum { ALS_MODE_FP64 = 0, ALS_MODE_MIXED = 1 };
 enum { ALS_SMOOTH_GMRES = 0, ALS_SMOOTH_RICHARDSON = 1 };
 enum { ALS_TRANSFER_ROBUST = 0, ALS_TRANSFER_STANDARD = 1 };
 enum { ALS_SCHUR_P1 = 0, ALS_SCHUR_P2 = 1 };
+enum { ALS_CYCLE_V = 0, ALS_CYCLE_F = 1 };
+enum { ALS_FACT_FULL = 0, ALS_FACT_UPPER = 1, ALS_FACT_LOWER = 2, ALS_FACT_DIAG = 3 };
 
 /* Unit box (0,1)^dim with n[k] cells per direction on the finest level;
  * n[k] must be divisible by 2^(levels-1) and the coarsest level must have
@@ -93,11 +95,18 @@ typedef struct {
   int mode;       /* ALS_MODE_FP64 or ALS_MODE_MIXED (FP32 V-cycle, FP64 outer loop) */
   double rtol;    /* FGMRES relative residual reduction (default 1e-8) */
   int maxit;      /* FGMRES iterations, no restart (default 300) */
+  int cycle;      /* ALS_CYCLE_V (default) or ALS_CYCLE_F: the coarse correction on each
+                     level is an F-cycle from zero followed by a V-cycle from its result
+                     (the textbook F-cycle; the paper runs an F-cycle, Sec. 7) */
+  int fact;       /* block factorisation of Eq. (precond): ALS_FACT_FULL (default, L D U,
+                     two cycles per iteration); ALS_FACT_UPPER [[A, B^T], [0, -S]]^-1,
+                     ALS_FACT_LOWER [[A, 0], [B, -S]]^-1, ALS_FACT_DIAG diag(A^-1, -S^-1):
+                     one cycle per iteration */
 } als_options;
 
 typedef struct {
   int iterations;     /* FGMRES iterations */
-  int vcycles;        /* V-cycles applied (2 per iteration) */
+  int vcycles;        /* multigrid cycles applied (2 per iteration with ALS_FACT_FULL, else 1) */
   int converged;
   double res0;        /* ||b||_2 of the augmented, lifted system */
   double res_final;   /* FGMRES residual estimate at exit */

@@ -211,11 +211,12 @@ class Hierarchy:
     """Levels 0 (coarsest) .. L-1 (finest) with smoother and transfer data.
 
     smoother: "gmres" (default), "richardson" or "jacobi" (point Jacobi,
-    the standard-multigrid negative control); transfer: "robust" or "standard".
+    the standard-multigrid negative control); transfer: "robust" or "standard";
+    cycle: "V" (default) or "F" (what the paper ran, Sec. 7).
     """
 
     def __init__(self, d, n, coeffs, gamma, kind="scalar", mu_eff=None,
-                 smoother="gmres", steps=5, tau=None, transfer="robust", W="Mp"):
+                 smoother="gmres", steps=5, tau=None, transfer="robust", W="Mp", cycle="V"):
         L = len(coeffs)
         self.d, self.L = d, L
         self.levels = []
@@ -225,6 +226,9 @@ class Hierarchy:
             me = None if mu_eff is None else mu_eff[lvl]
             self.levels.append(Level(d, nl, coeffs[lvl], gamma, kind, me, W))
         self.smoother, self.steps, self.transfer = smoother, steps, transfer
+        if cycle not in ("V", "F"):
+            raise ValueError(cycle)
+        self.cycle_type = cycle
         self.tau = tau if tau is not None else (2.0 ** -d if smoother == "richardson" else 1.0)
         self.patches = [None] + [star_patches(lv) if smoother != "jacobi" else None
                                  for lv in self.levels[1:]]
@@ -262,16 +266,42 @@ class Hierarchy:
             return smooth_gmres(A, self.Dinv(lvl), x, b, self.steps)
         return smooth_richardson(A, self.Dinv(lvl), x, b, self.steps, self.tau)
 
-    def vcycle(self, b, lvl=None):
-        """One V-cycle for A_(lvl) x = b from x = 0 (Sec. 5, Fig. algo-outline)."""
+    def vcycle(self, b, lvl=None, x0=None):
+        """One V-cycle for A_(lvl) x = b from x = x0 (default 0) (Sec. 5, Fig. algo-outline)."""
         lvl = self.L - 1 if lvl is None else lvl
         if lvl == 0:
             return self.coarse_solve(b)
         A = self.levels[lvl].A
-        x = np.zeros_like(b)
+        x = np.zeros_like(b) if x0 is None else x0.copy()
         x = self.smooth(lvl, x, b)
         r = b - A @ x
         bc = self.P[lvl].T @ r
         ec = self.vcycle(bc, lvl - 1)
         x = x + self.P[lvl] @ ec
         return self.smooth(lvl, x, b)
+
+    def fcycle(self, b, lvl=None):
+        """One F-cycle for A_(lvl) x = b from x = 0.
+
+        The paper runs an F-cycle (Sec. 7) without defining it; this is the
+        textbook recursion: as the V-cycle, but the coarse correction is an
+        F-cycle on level lvl-1 from zero followed by a V-cycle on level lvl-1
+        started from that result.  On the coarsest level both are the exact
+        solve, so one solve is done.
+        """
+        lvl = self.L - 1 if lvl is None else lvl
+        if lvl == 0:
+            return self.coarse_solve(b)
+        A = self.levels[lvl].A
+        x = self.smooth(lvl, np.zeros_like(b), b)
+        r = b - A @ x
+        bc = self.P[lvl].T @ r
+        ec = self.fcycle(bc, lvl - 1)
+        if lvl - 1 > 0:
+            ec = self.vcycle(bc, lvl - 1, x0=ec)
+        x = x + self.P[lvl] @ ec
+        return self.smooth(lvl, x, b)
+
+    def cycle(self, b):
+        """The configured multigrid cycle (V or F) on the finest level from 0."""
+        return self.fcycle(b) if self.cycle_type == "F" else self.vcycle(b)

@@ -5,7 +5,10 @@ TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  Follows:
     [r1 + gamma B^T W^-1 r2; r2] with W = M_p;
   * Eq. (precond): P = [[I, -A^-1 B^T], [0, I]] diag(A^-1, -S^-1) [[I, 0], [-B A^-1, I]],
     applied literally right to left, so the (1,1) approximation (a multigrid
-    V-cycle) is applied twice per preconditioner application;
+    cycle) is applied twice per preconditioner application ("full");
+    the factorisation types that keep only some factors, with the same
+    blocks: "upper" = [[A, B^T], [0, -S]]^-1, "lower" = [[A, 0], [B, -S]]^-1,
+    "diag" = diag(A^-1, -S^-1), one (1,1) application each;
   * Eq. (P1P2): P1: S_gamma^-1 = M_p(1/mu)^-1 + gamma M_p^-1;
     P2: S_gamma^-1 = (1 + gamma) M_p(1/mu)^-1, both block diagonal (one
     (d+1)x(d+1) block per cell, Sec. 6.1);
@@ -54,7 +57,10 @@ def pressure_nullvector(level):
 class StokesSolver:
     """Block-preconditioned FGMRES on the augmented system (Secs. 3, 6.1)."""
 
-    def __init__(self, hierarchy: Hierarchy, schur="P1", exact_A=False):
+    def __init__(self, hierarchy: Hierarchy, schur="P1", exact_A=False, fact="full"):
+        if fact not in ("full", "upper", "lower", "diag"):
+            raise ValueError(fact)
+        self.fact = fact
         self.H = hierarchy
         self.fine = lv = hierarchy.levels[-1]
         self.nu, self.np_ = lv.mesh.nu, lv.mesh.npres
@@ -74,7 +80,7 @@ class StokesSolver:
     def Ahat_inv(self, f):
         if self.exact_A:
             return self._lu.solve(f)
-        return self.H.vcycle(f)
+        return self.H.cycle(f)
 
     def project(self, p):
         n = self.nvec
@@ -83,9 +89,19 @@ class StokesSolver:
     def precondition(self, x):
         lv = self.fine
         f, g = x[: self.nu], x[self.nu:]
-        z1 = self.Ahat_inv(f)
-        z2 = -(self.Sinv @ (g - lv.B @ z1))
-        x1 = z1 - self.Ahat_inv(lv.Bt @ z2)
+        if self.fact == "full":
+            z1 = self.Ahat_inv(f)
+            z2 = -(self.Sinv @ (g - lv.B @ z1))
+            x1 = z1 - self.Ahat_inv(lv.Bt @ z2)
+        elif self.fact == "upper":
+            z2 = -(self.Sinv @ g)
+            x1 = self.Ahat_inv(f - lv.Bt @ z2)
+        elif self.fact == "lower":
+            x1 = self.Ahat_inv(f)
+            z2 = -(self.Sinv @ (g - lv.B @ x1))
+        else:
+            x1 = self.Ahat_inv(f)
+            z2 = -(self.Sinv @ g)
         return np.concatenate([x1, self.project(z2)])
 
     def fgmres(self, rhs, rtol=1e-8, maxit=300):

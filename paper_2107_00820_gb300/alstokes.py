@@ -25,6 +25,8 @@ ALS_MODE_FP64, ALS_MODE_MIXED = 0, 1
 ALS_SMOOTH_GMRES, ALS_SMOOTH_RICHARDSON = 0, 1
 ALS_TRANSFER_ROBUST, ALS_TRANSFER_STANDARD = 0, 1
 ALS_SCHUR_P1, ALS_SCHUR_P2 = 0, 1
+ALS_CYCLE_V, ALS_CYCLE_F = 0, 1
+ALS_FACT_FULL, ALS_FACT_UPPER, ALS_FACT_LOWER, ALS_FACT_DIAG = 0, 1, 2, 3
 
 
 class als_mesh(Structure):
@@ -37,7 +39,8 @@ class als_coeff(Structure):
 
 class als_options(Structure):
     _fields_ = [("smoother", c_int), ("sweeps", c_int), ("tau", c_double), ("transfer", c_int),
-                ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int)]
+                ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int),
+                ("cycle", c_int), ("fact", c_int)]
 
 
 class als_solve_info(Structure):

@@ -361,7 +361,11 @@ void prolong_level(als_ctx* c, MGWork& w, int l, const void* xc, void* t, void* 
   }
 }
 
-void vcycle_level(als_ctx* c, MGWork& w, int l) {
+// One multigrid cycle on level l for A_l x_l = b_l.  zero_guess: x_l starts at 0
+// (else from its current value).  fcycle: the coarse correction is an F-cycle on
+// level l-1 from zero followed by a V-cycle on level l-1 from that result (one
+// exact solve when l-1 is the coarsest level); otherwise a V-cycle from zero.
+void cycle_level(als_ctx* c, MGWork& w, int l, bool fcycle, bool zero_guess) {
   const cudaStream_t s = c->stream;
   if (l == 0) {
     coarse_apply(c->lev[0], c->coarse, w.prec, w.b[0], w.x[0], s);
@@ -370,15 +374,16 @@ void vcycle_level(als_ctx* c, MGWork& w, int l) {
   const LevelDev& Lv = c->lev[l];
   const long long len = Lv.g.N * c->dim;
   if (fused_gmres(c)) {
-    smooth_fused(c, w, l, true, w.t[l]);                                 // x, and t = b - A x
+    smooth_fused(c, w, l, zero_guess, w.t[l]);                           // x, and t = b - A x
   } else {
-    vec_zero(w.prec, len, w.x[l], s);
-    smooth(c, w, l, c->opt.smoother == ALS_SMOOTH_GMRES);
+    if (zero_guess) vec_zero(w.prec, len, w.x[l], s);
+    smooth(c, w, l, zero_guess && c->opt.smoother == ALS_SMOOTH_GMRES);
     op_apply(Lv, w.prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
     vec_axpby(w.prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                // t = b - A x
   }
   restrict_level(c, w, l, w.t[l], w.b[l - 1]);
-  vcycle_level(c, w, l - 1);
+  cycle_level(c, w, l - 1, fcycle, true);
+  if (fcycle && l - 1 > 0) cycle_level(c, w, l - 1, false, false);
   prolong_level(c, w, l, w.x[l - 1], w.t[l], w.x[l]);                  // x += P~ e_c
   if (fused_gmres(c)) smooth_fused(c, w, l, false, nullptr);
   else smooth(c, w, l);
@@ -394,7 +399,7 @@ cudaEvent_t prof_take(als_ctx* c) {
 als_status run_vcycle(als_ctx* c, MGWork& w) {
   Prof& pf = c->prof;
   if (!c->use_graph) {
-    vcycle_level(c, w, c->L - 1);
+    cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
     return cuda_check(c, "vcycle");
   }
   std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
@@ -405,7 +410,7 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cuda_check(c, "begin capture");
     t_capturing = true;
-    vcycle_level(c, w, c->L - 1);
+    cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
     t_capturing = false;
     if (cudaStreamEndCapture(c->stream, &w.graph_tmpl) != cudaSuccess) return cuda_check(c, "end capture");
     w.graph_kernels = launch_count() - c0;
@@ -507,6 +512,26 @@ als_status precondition(als_ctx* c, const double* v, double* z) {
   const double* gp = v + c->nu;
   double* x1 = z;
   double* z2 = z + c->nu;
+  if (c->opt.fact != ALS_FACT_FULL) {
+    // the factorisation types with one (1,1) application (oracle: StokesSolver.precondition)
+    if (c->opt.fact == ALS_FACT_UPPER) {                        // [[A, B^T], [0, -S]]^-1
+      schur_apply(F.g.ncells, c->dim + 1, c->schur, gp, z2, s);                      // z2 = -S^-1 g
+      op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, z2, nullptr, s);         // tu2 = B^T z2
+      vec_axpby(PREC_F64, c->nu, 1.0, f, -1.0, c->tu2, s);                             // tu2 = f - tu2
+      ALS_TRY(apply_Ahat(c, c->tu2, x1));                                              // x1 = A^-1 tu2
+    } else {
+      ALS_TRY(apply_Ahat(c, f, x1));                                                   // x1 = A^-1 f
+      if (c->opt.fact == ALS_FACT_LOWER) {                      // [[A, 0], [B, -S]]^-1
+        op_apply(F, PREC_F64, OP_B, c->gamma, x1, nullptr, nullptr, c->tp, s);        // tp = B x1
+        vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                           // tp = g - B x1
+        schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                   // z2 = -S^-1 tp
+      } else {                                                  // diag(A^-1, -S^-1)
+        schur_apply(F.g.ncells, c->dim + 1, c->schur, gp, z2, s);                      // z2 = -S^-1 g
+      }
+    }
+    project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+    return ALS_OK;
+  }
   ALS_TRY(apply_Ahat(c, f, c->tu));                                                  // z1 = A^-1 f
   op_apply(F, PREC_F64, OP_B, c->gamma, c->tu, nullptr, nullptr, c->tp, s);          // tp = B z1
   vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                               // tp = g - B z1
@@ -540,6 +565,8 @@ void als_default_options(als_options* opt) {
   opt->mode = ALS_MODE_FP64;
   opt->rtol = 1e-8;
   opt->maxit = 300;
+  opt->cycle = ALS_CYCLE_V;
+  opt->fact = ALS_FACT_FULL;
 }
 
 const char* als_last_error(const als_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -613,6 +640,9 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.tau <= 0.0) c->opt.tau = std::pow(2.0, -c->dim);
   if (c->opt.maxit < 1 || c->opt.maxit > 2000) return fail(c, ALS_EINVAL, "maxit must be in [1, 2000]");
   if (c->opt.schur != ALS_SCHUR_P1 && c->opt.schur != ALS_SCHUR_P2) return fail(c, ALS_EINVAL, "unknown Schur variant");
+  if (c->opt.cycle != ALS_CYCLE_V && c->opt.cycle != ALS_CYCLE_F) return fail(c, ALS_EINVAL, "unknown cycle");
+  if (c->opt.fact < ALS_FACT_FULL || c->opt.fact > ALS_FACT_DIAG)
+    return fail(c, ALS_EINVAL, "unknown factorisation type");
   if (c->opt.smoother != ALS_SMOOTH_GMRES && c->opt.smoother != ALS_SMOOTH_RICHARDSON)
     return fail(c, ALS_EINVAL, "unknown smoother");
   if (c->opt.transfer != ALS_TRANSFER_ROBUST && c->opt.transfer != ALS_TRANSFER_STANDARD)
@@ -961,7 +991,7 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
   cudaEventDestroy(e1);
   if (info) {
     info->iterations = its;
-    info->vcycles = 2 * its;
+    info->vcycles = (c->opt.fact == ALS_FACT_FULL ? 2 : 1) * its;
     info->converged = converged ? 1 : 0;
     info->res0 = beta;
     info->res_final = resid;

@@ -210,6 +210,20 @@ def test_vcycle_fp64_gmres_steps(sweeps, transfer):
     assert rel(host(x), H.vcycle(b)) <= 1e-12
 
 
+@pytest.mark.parametrize("smoother", [A.ALS_SMOOTH_RICHARDSON, A.ALS_SMOOTH_GMRES])
+@pytest.mark.parametrize("d,n,levels", [(2, 16, 4), (3, 8, 3)])
+def test_fcycle_fp64(smoother, d, n, levels):
+    """F-cycle (F-cycle then V-cycle from its result on each coarser level)."""
+    pb = sinker(d, n, levels, 1.0, dr=1e2, seed=25)
+    ctx = context(pb, smoother=smoother, sweeps=2, cycle=A.ALS_CYCLE_F)
+    H = oracle(pb, smoother="gmres" if smoother == A.ALS_SMOOTH_GMRES else "richardson", steps=2, cycle="F")
+    b = random_free(H.levels[-1], 26)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.cycle(b)) <= 1e-12
+    assert rel(host(x), H.vcycle(b)) > 1e-6          # really a different cycle
+
+
 def _max_patch_cond(H, lvl, count=40):
     m = H.levels[lvl].mesh
     verts = all_vertices(m)
@@ -267,6 +281,20 @@ def test_solve_fp64_matches_oracle(d, n, levels, gamma, dr):
     u, p, info = ctx.solve(pb.f, pb.u_bc)
     assert info.converged == 1
     assert abs(info.iterations - its) <= 0, (info.iterations, its)
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
+
+
+@pytest.mark.parametrize("fact,name", [(A.ALS_FACT_UPPER, "upper"), (A.ALS_FACT_LOWER, "lower"),
+                                       (A.ALS_FACT_DIAG, "diag")])
+def test_solve_factorisation_types(fact, name):
+    """Block-triangular and block-diagonal forms of Eq. (precond), FP64, F-cycle."""
+    pb = sinker(2, 16, 3, 1e2, dr=1e4, seed=27)
+    ctx = context(pb, rtol=1e-8, fact=fact, cycle=A.ALS_CYCLE_F)
+    s = StokesSolver(oracle(pb, cycle="F"), fact=name)
+    uo, po, its, _ = s.solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged == 1 and info.iterations == its, (info.iterations, its)
+    assert info.vcycles == its
     assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
 
 

@@ -443,6 +443,56 @@ def test_vcycle_equals_explicit_operator_product():
         assert np.allclose(H.vcycle(b), M @ b, rtol=1e-9, atol=1e-9 * np.abs(M @ b).max())
 
 
+def _fcycle_matrix(H, lvl):
+    """Dense operator of the Richardson F-cycle from the textbook error propagation:
+    I - F_l A_l = S^s (I - P C P^T A_l) S^s, where the coarse correction C satisfies
+    I - C A_c = (I - V_(l-1) A_c)(I - F_(l-1) A_c)  (F-cycle, then a V-cycle from its
+    result), and C = A_c^-1 when level l-1 is the coarsest."""
+    A = H.levels[lvl].A.toarray()
+    f = H.levels[lvl].free
+    n = A.shape[0]
+    Ainv = np.zeros_like(A)
+    Ainv[np.ix_(f, f)] = np.linalg.inv(A[np.ix_(f, f)])
+    if lvl == 0:
+        return Ainv
+    Ac = H.levels[lvl - 1].A.toarray()
+    fc = H.levels[lvl - 1].free
+    Acinv = np.zeros_like(Ac)
+    Acinv[np.ix_(fc, fc)] = np.linalg.inv(Ac[np.ix_(fc, fc)])
+    if lvl - 1 == 0:
+        C = Acinv
+    else:
+        Ic = np.eye(Ac.shape[0])
+        Ec = (Ic - _vcycle_matrix(H, lvl - 1) @ Ac) @ (Ic - _fcycle_matrix(H, lvl - 1) @ Ac)
+        C = (Ic - Ec) @ Acinv
+    Dinv = np.stack([H.patches[lvl].apply(e) for e in np.eye(n)], 1)
+    Ss = np.linalg.matrix_power(np.eye(n) - H.tau * Dinv @ A, H.steps)
+    Pm = H.P[lvl].toarray()
+    E = Ss @ (np.eye(n) - Pm @ C @ Pm.T @ A) @ Ss
+    return (np.eye(n) - E) @ Ainv
+
+
+def test_fcycle_equals_textbook_error_propagation():
+    """The recursive F-cycle against its error-propagation formula (3 levels, so the
+    coarse correction on level 1 is an F-cycle followed by a V-cycle from its result);
+    it also contracts at least as well as the V-cycle."""
+    mus = P.sinker_problem(2, 8, 3, 3, 0.3, 50.0, 1e4, seed=1).mu
+    H = Hierarchy(2, 8, mus, 1e2, smoother="richardson", steps=2, cycle="F")
+    MF = _fcycle_matrix(H, 2)
+    MV = _vcycle_matrix(H, 2)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        b = rng.standard_normal(H.levels[2].mesh.nu); b[H.levels[2].bdof] = 0
+        ref = MF @ b
+        assert np.allclose(H.cycle(b), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+        assert not np.allclose(H.vcycle(b), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+    f = H.levels[2].free
+    A = H.levels[2].A.toarray()
+    I = np.eye(A.shape[0])
+    rho = lambda M: np.abs(np.linalg.eigvals((I - M @ A)[np.ix_(f, f)])).max()  # noqa: E731
+    assert rho(MF) <= rho(MV) + 1e-12
+
+
 def _two_level_rho(gamma, smoother, transfer):
     mus = [np.ones((16, 9)), np.ones((64, 9))]
     H = Hierarchy(2, 8, mus, gamma, smoother=smoother, steps=2, transfer=transfer,
@@ -468,6 +518,44 @@ def test_vcycle_contraction_gamma_robust_and_standard_mg_fails():
 # --------------------------------------------------------------------------
 # outer solver
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("fact,its", [("full", 1), ("upper", 2), ("lower", 2), ("diag", 3)])
+def test_factorisation_types_with_exact_blocks(fact, its):
+    """With the exact A_gamma^-1 and the exact Schur complement, the full factorisation
+    is the inverse (1 FGMRES iteration), the block-triangular ones leave a
+    preconditioned operator with the single eigenvalue 1 and minimal polynomial of
+    degree 2 (2 iterations), and the block-diagonal one three distinct eigenvalues
+    (3 iterations) -- Murphy, Golub & Wathen (2000), Ipsen (2001).  A sign or a
+    dropped factor in any variant changes these counts."""
+    from oracle.stokes import StokesSolver
+    mus = [np.ones((4, 9)), np.ones((16, 9))]
+    H = Hierarchy(2, 4, mus, 10.0, smoother="richardson", steps=1)
+    sol = StokesSolver(H, "P1", exact_A=True, fact=fact)
+    lv = sol.fine
+    A = lv.A.toarray()
+    S = lv.B.toarray() @ np.linalg.solve(A, lv.Bt.toarray())
+    sol.Sinv = np.linalg.pinv(S, rcond=1e-10)
+    rng = np.random.default_rng(11)
+    rhs = rng.standard_normal(sol.nu + sol.np_)
+    rhs[np.flatnonzero(lv.bdof)] = 0.0
+    rhs[sol.nu:] = sol.project(rhs[sol.nu:])
+    x, k, hist = sol.fgmres(rhs, rtol=1e-10, maxit=10)
+    assert k == its, (fact, k, hist)
+    assert np.linalg.norm(sol.matvec(x) - rhs) <= 1e-8 * np.linalg.norm(rhs)
+    # the minimal polynomial of T = K P on compatible vectors fixes the signs too:
+    # full: T = I; triangular: (T - I)^2 = 0 (a flipped S gives (T - I)(T + I) = 0);
+    # diagonal with -S^-1: (T - I)(T^2 - T + I) = 0 (eigenvalues 1, (1 +- i sqrt 3)/2)
+    T = lambda v: sol.matvec(sol.precondition(v))  # noqa: E731
+    v = rhs / np.linalg.norm(rhs)
+    if fact == "full":
+        r = T(v) - v
+    elif fact in ("upper", "lower"):
+        w = T(v) - v
+        r = T(w) - w
+    else:
+        w = T(v) - v
+        r = T(T(w)) - T(w) + w
+    assert np.linalg.norm(r) <= 1e-8, (fact, np.linalg.norm(r))
+
 @pytest.mark.parametrize("schur,W", [("P1", "Mp"), ("P2", "Mp_mu")])
 def test_fgmres_matches_direct_solve(schur, W):
     pb = P.sinker_2d(n=16, levels=3, gamma=1e2, dr=1e4, seed=2)
