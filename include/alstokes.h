@@ -233,6 +233,46 @@ als_status als_star_smooth_static(int dim, const int* n, int prec, const void* i
  * outputs, ALS_ENOMEM or ALS_ECUDA on a runtime failure. */
 als_status als_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
+/* ---- Batches of independent instances (serving-style sweeps) ----------------
+ * A batch holds `count` independent problems, each with its own mesh, level
+ * count, coefficients, gamma and options (2D and 3D may be mixed); instance i
+ * is a full context (als_batch_context gives it for the per-instance calls).
+ * als_batch_solve runs all solves together: each round queues one FGMRES
+ * iteration of every unfinished instance, each on its own stream, then waits
+ * once, so the instances' kernels run concurrently; results are bitwise those
+ * of als_solve on the same instance.  als_batch_vcycle applies one multigrid
+ * cycle to every instance with a single graph launch whose independent branches
+ * are the instances' captured cycles.
+ * Arrays are indexed by instance: meshes/coeffs/gammas[count]; opts[count] or
+ * NULL (defaults); f_qp, u_bc, r2, u, p, b, x: arrays of count pointers with
+ * the meaning and layout of the single-instance calls (u_bc, r2 may be NULL
+ * arrays or hold NULL entries); infos[count] or NULL.
+ * Errors: als_batch_create returns the first failing instance's status (and
+ * creates nothing); als_batch_solve finishes every instance and returns the
+ * first non-OK status (the message names the instance); als_batch_vcycle needs
+ * graph capture on and profiling off in every instance (ALS_EINVAL otherwise). */
+typedef struct als_batch als_batch;
+als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* coeffs, const double* gammas,
+                            const als_options* opts, void* stream, als_batch** out);
+als_status als_batch_destroy(als_batch* batch);
+als_status als_batch_context(als_batch* batch, int i, als_ctx** ctx);
+als_status als_batch_solve(als_batch* batch, const double* const* f_qp, const double* const* u_bc,
+                           const double* const* r2, double* const* u, double* const* p, als_solve_info* infos);
+als_status als_batch_vcycle(als_batch* batch, int prec, const void* const* b, void* const* x);
+const char* als_batch_last_error(const als_batch* batch);
+
+/* Autotuner record of a smoothed level (1 <= level < levels).  Before the FP32
+ * cycle is first captured, each level times its FP32 star-patch kernel variants
+ * (0: TMA ring with 2 stages, 1: TMA ring with 3 stages, 2: direct 16-byte loads;
+ * one warm-up and three timed launches each) and keeps the fastest.  *variant gets
+ * the choice (-1 before tuning); ms[3] (optional) the measured time per launch of
+ * each variant.  ALS_PATCH_KERNEL = tma2 | tma3 | direct in the environment forces
+ * a variant. */
+als_status als_autotune_info(als_ctx* ctx, int level, int* variant, float* ms);
+/* Sets the FP32 patch-kernel variant of a level (0, 1, 2 as above; -1 = tune again
+ * before the next capture); the captured cycles are dropped and recaptured. */
+als_status als_set_patch_kernel(als_ctx* ctx, int level, int variant);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char* als_last_error(const als_ctx* ctx);
 

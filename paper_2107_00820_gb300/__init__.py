@@ -5,4 +5,4 @@ this package holds its sources (csrc/), its in-tree build (build.py) and a thin
 ctypes binding (alstokes.py).
 """
 from . import alstokes  # noqa: F401
-from .alstokes import ALSError, Context, load  # noqa: F401
+from .alstokes import ALSError, Batch, Context, load  # noqa: F401

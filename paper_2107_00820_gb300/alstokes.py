@@ -71,6 +71,16 @@ SIGNATURES = {
     "als_kernel_launches": (c_longlong, []),
     "als_star_smooth_static": (c_int, [c_int, POINTER(c_int), c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "als_measure_fma_peaks": (c_int, [POINTER(c_double), POINTER(c_double), c_void_p]),
+    "als_batch_create": (c_int, [c_int, POINTER(als_mesh), POINTER(als_coeff), POINTER(c_double),
+                                 POINTER(als_options), c_void_p, POINTER(c_void_p)]),
+    "als_batch_destroy": (c_int, [c_void_p]),
+    "als_batch_context": (c_int, [c_void_p, c_int, POINTER(c_void_p)]),
+    "als_batch_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                POINTER(c_void_p), POINTER(c_void_p), POINTER(als_solve_info)]),
+    "als_batch_vcycle": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_void_p)]),
+    "als_batch_last_error": (ctypes.c_char_p, [c_void_p]),
+    "als_autotune_info": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(ctypes.c_float)]),
+    "als_set_patch_kernel": (c_int, [c_void_p, c_int, c_int]),
 }
 
 _LIB = None
@@ -258,6 +268,16 @@ class Context:
         self._call("als_profile_read", byref(ms), byref(n))
         return ms.value, n.value
 
+    def autotune_info(self, level):
+        """(chosen FP32 patch-kernel variant, [ms per launch of variants 0, 1, 2]) of a level."""
+        v = c_int()
+        ms = (ctypes.c_float * 3)()
+        self._call("als_autotune_info", c_int(level), byref(v), ms)
+        return v.value, list(ms)
+
+    def set_patch_kernel(self, level, variant):
+        self._call("als_set_patch_kernel", c_int(level), c_int(variant))
+
     def profile_read_kernel(self, kind):
         """(total ms, launches) of kernel class `kind` (0 patch kernel, 1 operator apply)."""
         ms, n = c_double(), c_longlong()
@@ -283,6 +303,84 @@ class Context:
 
 
 # module-level functions with the C names (thin pass-through)
+class Batch:
+    """An als_batch: independent instances solved together.
+
+    instances: list of dicts with keys dim, n, levels, coeffs (per-level arrays),
+    gamma and optionally mu_eff and options (keyword options of default_options).
+    """
+
+    def __init__(self, instances, stream=None):
+        lib = load()
+        k = len(instances)
+        meshes = (als_mesh * k)()
+        coeffs = (als_coeff * k)()
+        gammas = (c_double * k)()
+        opts = (als_options * k)()
+        self._keep = []
+        self.shapes = []
+        for i, ins in enumerate(instances):
+            dim, levels = ins["dim"], ins["levels"]
+            n = (ins["n"],) * dim if np.isscalar(ins["n"]) else tuple(ins["n"])
+            meshes[i] = als_mesh(dim, (c_int * 3)(*(list(n) + [1] * (3 - len(n)))), levels)
+            keep = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c
+                    for c in ins["coeffs"]]
+            qp = (c_void_p * levels)(*[_ptr(c) for c in keep])
+            mu = None
+            if ins.get("mu_eff") is not None:
+                keep_mu = [np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c
+                           for c in ins["mu_eff"]]
+                mu = (c_void_p * levels)(*[_ptr(c) for c in keep_mu])
+                keep += keep_mu
+            coeffs[i] = als_coeff(ALS_COEFF_TENSOR if mu is not None else ALS_COEFF_SCALAR, qp, mu)
+            self._keep += [keep, qp, mu]
+            gammas[i] = float(ins["gamma"])
+            opts[i] = default_options(**ins.get("options", {}))
+            nu = dim * int(np.prod([2 * v + 1 for v in n]))
+            self.shapes.append((nu, (dim + 1) * int(np.prod(n))))
+        out = c_void_p()
+        st = lib.als_batch_create(k, meshes, coeffs, gammas, opts, c_void_p(stream) if stream else None, byref(out))
+        if st != ALS_OK:
+            raise ALSError(st, "als_batch_create failed")
+        self._b = out
+        self._lib = lib
+        self.count = k
+
+    def _check(self, st):
+        if st != ALS_OK:
+            raise ALSError(st, self._lib.als_batch_last_error(self._b).decode())
+
+    def solve(self, f_qp, u_bc=None, r2=None, u=None, p=None, check=True):
+        """Solves every instance; returns (u list, p list, info list)."""
+        k = self.count
+        u = u if u is not None else [np.zeros(s[0]) for s in self.shapes]
+        p = p if p is not None else [np.zeros(s[1]) for s in self.shapes]
+        arr = lambda xs: (c_void_p * k)(*[_ptr(x) for x in xs]) if xs is not None else None  # noqa: E731
+        infos = (als_solve_info * k)()
+        st = self._lib.als_batch_solve(self._b, arr(f_qp), arr(u_bc), arr(r2), arr(u), arr(p), infos)
+        if st != ALS_OK and (check or st != ALS_ENOTCONV):
+            self._check(st)
+        return u, p, list(infos)
+
+    def vcycle(self, b, x, prec=ALS_PREC_FP64):
+        for t in list(b) + list(x):
+            _cuda_tensor(t); _check_dtype(t, prec)
+        k = self.count
+        self._check(self._lib.als_batch_vcycle(self._b, prec, (c_void_p * k)(*[_ptr(t) for t in b]),
+                                               (c_void_p * k)(*[_ptr(t) for t in x])))
+
+    def close(self):
+        if getattr(self, "_b", None) is not None:
+            self._lib.als_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
 def als_create(dim, n, levels, coeffs, gamma, **kw):
     return Context(dim, n, levels, coeffs, gamma, **kw)
 

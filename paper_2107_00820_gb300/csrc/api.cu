@@ -104,6 +104,16 @@ struct als_ctx {
   bool use_graph = true;
   Prof prof;
   const double* const* src_qp = nullptr;   // only valid during a setup call
+  // state of the solve in progress (als_solve runs it to the end; a batch interleaves several)
+  struct SolveRun {
+    int k = 0, its = 0;
+    double beta = 0.0, resid = 0.0;
+    bool converged = false, done = false;
+    als_status status = ALS_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double* u = nullptr;
+    double* p = nullptr;
+  } run;
 };
 
 namespace {
@@ -395,13 +405,22 @@ cudaEvent_t prof_take(als_ctx* c) {
   return nullptr;
 }
 
-// one V-cycle on the finest level: w.b[L-1] -> w.x[L-1]
-als_status run_vcycle(als_ctx* c, MGWork& w) {
-  Prof& pf = c->prof;
-  if (!c->use_graph) {
-    cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
-    return cuda_check(c, "vcycle");
+// FP32: pick the patch-kernel variant of every smoothed level (once, before capture)
+void tune_patches(als_ctx* c, MGWork& w) {
+  if (w.prec != PREC_F32) return;
+  for (int l = 1; l < c->L; ++l) {
+    LevelDev& Lv = c->lev[l];
+    if (Lv.patch_kernel >= 0) continue;
+    const long long len = Lv.g.N * c->dim;
+    vec_zero(PREC_F32, len, w.V[l], c->stream);
+    patch_autotune(Lv, w.V[l], w.scratch[l], c->stream, Lv.tune_ms);
   }
+}
+
+// capture the cycle of this precision as a graph (once); nothing is launched
+als_status ensure_graph(als_ctx* c, MGWork& w) {
+  Prof& pf = c->prof;
+  if (!w.graph) tune_patches(c, w);
   std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
   std::vector<int>& kinds = w.prec == PREC_F64 ? pf.kinds64 : pf.kinds32;
   if (!w.graph) {
@@ -438,6 +457,20 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
     cudaError_t e = cudaGraphInstantiate(&w.graph, w.graph_tmpl, 0);
     if (e != cudaSuccess) return cuda_check(c, "graph instantiate");
   }
+  return ALS_OK;
+}
+
+// one cycle on the finest level: w.b[L-1] -> w.x[L-1]
+als_status run_vcycle(als_ctx* c, MGWork& w) {
+  Prof& pf = c->prof;
+  if (!c->use_graph) {
+    tune_patches(c, w);
+    cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
+    return cuda_check(c, "vcycle");
+  }
+  ALS_TRY(ensure_graph(c, w));
+  std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
+  std::vector<int>& kinds = w.prec == PREC_F64 ? pf.kinds64 : pf.kinds32;
   if (pf.on && !nodes.empty()) {
     for (size_t i = 0; i + 1 < nodes.size(); i += 2) {
       cudaEvent_t a = prof_take(c), b = prof_take(c);
@@ -678,6 +711,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     LevelDev& Lv = c->lev[l];
     Lv = LevelDev{};
     Lv.g = make_geom(c->dim, nl);
+    Lv.patch_kernel = -1;
     Lv.tensor = coeff->kind == ALS_COEFF_TENSOR;
     Lv.ncoef = Lv.tensor ? NC : 1;
     Lv.np = c->dim * NB;
@@ -901,20 +935,28 @@ als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* ou
   return ALS_OK;
 }
 
-als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u, double* p,
-                     als_solve_info* info) {
-  if (!c) return ALS_EINVAL;
+// ---- the outer solve in stages, so that a batch can interleave the FGMRES
+// iterations of several contexts (each on its own stream) with one host wait
+// per round: start (inputs, lifted rhs, |b| on its way to the host), then rounds
+// of launch-iteration / iteration-done, then finish.
+
+// queue the inputs, the lifted augmented right-hand side and |b| (no wait)
+static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u,
+                              double* p) {
   if (!f_qp || !u || !p) return fail(c, ALS_EINVAL, "f_qp, u and p are required");
+  als_ctx::SolveRun& R = c->run;
+  R = als_ctx::SolveRun{};
+  R.u = u;
+  R.p = p;
   const int maxit = c->opt.maxit;
   ALS_TRY(alloc_solve(c, maxit));
   const LevelDev& F = c->lev[c->L - 1];
   const cudaStream_t s = c->stream;
   const int NB = c->dim == 2 ? 9 : 27;
   begin(c);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
+  cudaEventCreate(&R.e0);
+  cudaEventCreate(&R.e1);
+  cudaEventRecord(R.e0, s);
   // inputs (host or device)
   cudaMemcpyAsync(c->f_dev, f_qp, sizeof(double) * F.g.ncells * NB * c->dim, cudaMemcpyDefault, s);
   if (u_bc) cudaMemcpyAsync(c->ubc_dev, u_bc, sizeof(double) * c->nu, cudaMemcpyDefault, s);
@@ -944,60 +986,298 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
   vec_scale_dev(PREC_F64, c->n, nullptr, c->beta, rhs, rhs, s);
   cudaMemsetAsync(c->H, 0, sizeof(double) * ldh * maxit, s);
   cudaMemcpyAsync(c->host_res + 1, c->beta, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "solve rhs");
+  return cuda_check(c, "solve rhs");
+}
+
+// after the stream has drained: read |b|
+static als_status solve_rhs_done(als_ctx* c) {
+  als_ctx::SolveRun& R = c->run;
   ALS_TRY(check_status(c, "solve rhs"));
-  const double beta = c->host_res[1];
-  int its = 0;
-  double resid = beta;
-  bool converged = beta == 0.0;
-  for (int k = 0; k < maxit && !converged; ++k) {
-    double* vk = c->V + (size_t)k * c->n;
-    double* zk = c->Z + (size_t)k * c->n;
-    double* w = c->V + (size_t)(k + 1) * c->n;
-    double* hcol = c->H + (size_t)k * ldh;
-    ALS_TRY(precondition(c, vk, zk));
-    matvec(c, zk, w);
-    vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, hcol, c->partial, s);
-    vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, hcol, w, s, -1.0);
-    vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, c->h2, c->partial, s);
-    vec_multiaxpy_norm(PREC_F64, c->n, k + 1, c->V, c->n, c->h2, -1.0, w, c->partial, c->nrm2, s);
-    vec_scale_dev(PREC_F64, c->n, nullptr, c->nrm2, w, w, s, 1);
-    dev_hess_givens(k, c->H, ldh, c->h2, c->nrm2, c->cs, c->sn, c->g, c->res, s);
-    cudaMemcpyAsync(c->host_res, c->res, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "fgmres");
-    its = k + 1;
-    resid = c->host_res[0];
-    if (!std::isfinite(resid)) {
-      ALS_TRY(check_status(c, "fgmres"));
-      return fail(c, ALS_EBREAKDOWN, "non-finite FGMRES residual");
-    }
-    if (resid <= c->opt.rtol * beta) converged = true;
+  R.beta = c->host_res[1];
+  R.resid = R.beta;
+  R.converged = R.beta == 0.0;
+  R.done = R.converged || c->opt.maxit <= 0;
+  return ALS_OK;
+}
+
+// queue FGMRES iteration k (no wait); the residual estimate is on its way to the host
+static als_status solve_iter_launch(als_ctx* c) {
+  als_ctx::SolveRun& R = c->run;
+  const cudaStream_t s = c->stream;
+  const int k = R.k, ldh = c->opt.maxit + 1;
+  double* vk = c->V + (size_t)k * c->n;
+  double* zk = c->Z + (size_t)k * c->n;
+  double* w = c->V + (size_t)(k + 1) * c->n;
+  double* hcol = c->H + (size_t)k * ldh;
+  ALS_TRY(precondition(c, vk, zk));
+  matvec(c, zk, w);
+  vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, hcol, c->partial, s);
+  vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, hcol, w, s, -1.0);
+  vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, c->h2, c->partial, s);
+  vec_multiaxpy_norm(PREC_F64, c->n, k + 1, c->V, c->n, c->h2, -1.0, w, c->partial, c->nrm2, s);
+  vec_scale_dev(PREC_F64, c->n, nullptr, c->nrm2, w, w, s, 1);
+  dev_hess_givens(k, c->H, ldh, c->h2, c->nrm2, c->cs, c->sn, c->g, c->res, s);
+  cudaMemcpyAsync(c->host_res, c->res, sizeof(double), cudaMemcpyDeviceToHost, s);
+  return ALS_OK;
+}
+
+// after the stream has drained: read the residual estimate of the iteration
+static als_status solve_iter_done(als_ctx* c) {
+  als_ctx::SolveRun& R = c->run;
+  R.its = ++R.k;
+  R.resid = c->host_res[0];
+  if (!std::isfinite(R.resid)) {
+    R.done = true;
+    ALS_TRY(check_status(c, "fgmres"));
+    return fail(c, ALS_EBREAKDOWN, "non-finite FGMRES residual");
   }
-  // x = Z y; u = x_u + u_D; p = x_p with zero mean
+  if (R.resid <= c->opt.rtol * R.beta) R.converged = true;
+  R.done = R.converged || R.k >= c->opt.maxit;
+  return ALS_OK;
+}
+
+// x = Z y; u = x_u + u_D; p = x_p with zero mean; wait; report
+static als_status solve_finish(als_ctx* c, als_solve_info* info) {
+  als_ctx::SolveRun& R = c->run;
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  const int ldh = c->opt.maxit + 1;
   cudaMemsetAsync(c->xsol, 0, sizeof(double) * c->n, s);
-  if (its > 0) {
-    dev_backsolve(its, c->H, ldh, c->g, c->y, s);
-    vec_multiaxpy(PREC_F64, c->n, its, c->Z, c->n, c->y, c->xsol, s, 1.0);
+  if (R.its > 0) {
+    dev_backsolve(R.its, c->H, ldh, c->g, c->y, s);
+    vec_multiaxpy(PREC_F64, c->n, R.its, c->Z, c->n, c->y, c->xsol, s, 1.0);
   }
   vec_axpby(PREC_F64, c->nu, 1.0, c->uD, 1.0, c->xsol, s);
   project_constant(F.g.ncells, c->dim + 1, c->xsol + c->nu, c->partial, s);
-  cudaMemcpyAsync(u, c->xsol, sizeof(double) * c->nu, cudaMemcpyDefault, s);
-  cudaMemcpyAsync(p, c->xsol + c->nu, sizeof(double) * c->np, cudaMemcpyDefault, s);
-  cudaEventRecord(e1, s);
-  ALS_TRY(finish(c, "solve"));
+  cudaMemcpyAsync(R.u, c->xsol, sizeof(double) * c->nu, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(R.p, c->xsol + c->nu, sizeof(double) * c->np, cudaMemcpyDefault, s);
+  cudaEventRecord(R.e1, s);
+  const als_status st = finish(c, "solve");
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, R.e0, R.e1);
+  cudaEventDestroy(R.e0);
+  cudaEventDestroy(R.e1);
+  R.e0 = R.e1 = nullptr;
   if (info) {
-    info->iterations = its;
-    info->vcycles = (c->opt.fact == ALS_FACT_FULL ? 2 : 1) * its;
-    info->converged = converged ? 1 : 0;
-    info->res0 = beta;
-    info->res_final = resid;
+    info->iterations = R.its;
+    info->vcycles = (c->opt.fact == ALS_FACT_FULL ? 2 : 1) * R.its;
+    info->converged = R.converged ? 1 : 0;
+    info->res0 = R.beta;
+    info->res_final = R.resid;
     info->solve_ms = ms;
   }
-  if (!converged) return fail(c, ALS_ENOTCONV, "FGMRES did not converge within maxit");
+  ALS_TRY(st);
+  if (!R.converged) return fail(c, ALS_ENOTCONV, "FGMRES did not converge within maxit");
+  return ALS_OK;
+}
+
+als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u, double* p,
+                     als_solve_info* info) {
+  if (!c) return ALS_EINVAL;
+  ALS_TRY(solve_start(c, f_qp, u_bc, r2, u, p));
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "solve rhs");
+  ALS_TRY(solve_rhs_done(c));
+  while (!c->run.done) {
+    ALS_TRY(solve_iter_launch(c));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "fgmres");
+    ALS_TRY(solve_iter_done(c));
+  }
+  return solve_finish(c, info);
+}
+
+
+// ============================================================================
+// Batches of independent instances (uneven sizes, dimensions and parameters).
+// Each instance is a full context with its own stream.  A batched solve
+// interleaves the instances' FGMRES iterations: every round queues one
+// iteration of every unfinished instance on its own stream and then waits once
+// for all of them, so the kernels of different instances run concurrently.  A
+// batched cycle launches one graph whose branches are the instances' captured
+// cycle graphs (no edges between them), so all cycles run as one launch.
+// ============================================================================
+}  // extern "C"
+
+struct als_batch {
+  std::vector<als_ctx*> ctx;
+  cudaStream_t user_stream = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::string err;
+};
+
+static als_status batch_fail(als_batch* b, als_status code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+extern "C" {
+
+als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* coeffs, const double* gammas,
+                            const als_options* opts, void* stream, als_batch** out) {
+  if (!out) return ALS_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !meshes || !coeffs || !gammas) return ALS_EINVAL;
+  als_batch* b = new als_batch;
+  b->user_stream = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    als_ctx* c = nullptr;
+    const als_status st = als_create(&meshes[i], &coeffs[i], gammas[i], opts ? &opts[i] : nullptr, stream, &c);
+    if (st != ALS_OK) {
+      for (als_ctx* d : b->ctx) als_destroy(d);
+      delete b;
+      return st;
+    }
+    b->ctx.push_back(c);
+  }
+  *out = b;
+  return ALS_OK;
+}
+
+als_status als_batch_destroy(als_batch* b) {
+  if (!b) return ALS_EINVAL;
+  for (int k = 0; k < 2; ++k) {
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+  }
+  for (als_ctx* c : b->ctx) als_destroy(c);
+  delete b;
+  return ALS_OK;
+}
+
+als_status als_batch_context(als_batch* b, int i, als_ctx** ctx) {
+  if (!b || !ctx) return ALS_EINVAL;
+  if (i < 0 || i >= (int)b->ctx.size()) return batch_fail(b, ALS_EINVAL, "instance index out of range");
+  *ctx = b->ctx[i];
+  return ALS_OK;
+}
+
+als_status als_batch_solve(als_batch* b, const double* const* f_qp, const double* const* u_bc,
+                           const double* const* r2, double* const* u, double* const* p, als_solve_info* infos) {
+  if (!b || !f_qp || !u || !p) return ALS_EINVAL;
+  const int n = (int)b->ctx.size();
+  std::vector<als_status> st(n, ALS_OK);
+  std::vector<bool> live(n, false);
+  for (int i = 0; i < n; ++i) {
+    st[i] = solve_start(b->ctx[i], f_qp[i], u_bc ? u_bc[i] : nullptr, r2 ? r2[i] : nullptr, u[i], p[i]);
+    live[i] = st[i] == ALS_OK;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!live[i]) continue;
+    if (cudaStreamSynchronize(b->ctx[i]->stream) != cudaSuccess) st[i] = cuda_check(b->ctx[i], "solve rhs");
+    else st[i] = solve_rhs_done(b->ctx[i]);
+    live[i] = st[i] == ALS_OK;
+  }
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (!live[i] || b->ctx[i]->run.done) continue;
+      st[i] = solve_iter_launch(b->ctx[i]);
+      if (st[i] != ALS_OK) live[i] = false;
+      else any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < n; ++i) {
+      if (!live[i] || b->ctx[i]->run.done) continue;
+      if (cudaStreamSynchronize(b->ctx[i]->stream) != cudaSuccess) st[i] = cuda_check(b->ctx[i], "fgmres");
+      else st[i] = solve_iter_done(b->ctx[i]);
+      if (st[i] != ALS_OK) live[i] = false;
+    }
+  }
+  als_status first = ALS_OK;
+  for (int i = 0; i < n; ++i) {
+    if (live[i]) st[i] = solve_finish(b->ctx[i], infos ? &infos[i] : nullptr);
+    else if (infos) infos[i] = als_solve_info{b->ctx[i]->run.its, 0, 0, b->ctx[i]->run.beta, b->ctx[i]->run.resid, 0.0};
+    if (st[i] != ALS_OK && first == ALS_OK) {
+      first = st[i];
+      b->err = "instance " + std::to_string(i) + ": " + b->ctx[i]->err;
+    }
+  }
+  return first;
+}
+
+als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void* const* xv) {
+  if (!b || !bv || !xv) return ALS_EINVAL;
+  if (prec != PREC_F64 && prec != PREC_F32) return batch_fail(b, ALS_EINVAL, "prec must be FP64 or FP32");
+  const int n = (int)b->ctx.size();
+  const int k = prec == PREC_F64 ? 0 : 1;
+  if (!b->exec[k]) {
+    // one graph: the instances' captured cycle graphs as independent child graphs
+    auto drop = [&](als_status st, const std::string& msg) {
+      if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+      b->graph[k] = nullptr;
+      cudaGetLastError();
+      return batch_fail(b, st, msg);
+    };
+    if (cudaGraphCreate(&b->graph[k], 0) != cudaSuccess) return drop(ALS_ECUDA, "graph create");
+    for (int i = 0; i < n; ++i) {
+      als_ctx* c = b->ctx[i];
+      if (c->prof.on || !c->use_graph)
+        return drop(ALS_EINVAL, "batched cycles need graph capture and profiling off");
+      MGWork& w = work_for(c, prec);
+      const als_status st = ensure_graph(c, w);
+      if (st != ALS_OK) return drop(st, c->err);
+      cudaGraphNode_t node;
+      if (cudaGraphAddChildGraphNode(&node, b->graph[k], nullptr, 0, w.graph_tmpl) != cudaSuccess)
+        return drop(ALS_ECUDA, "child graph node");
+    }
+    if (cudaGraphInstantiate(&b->exec[k], b->graph[k], 0) != cudaSuccess) {
+      b->exec[k] = nullptr;
+      return drop(ALS_ECUDA, "batch graph instantiate");
+    }
+  }
+  // the instances' streams must be idle: their buffers are the graph's
+  for (int i = 0; i < n; ++i) cudaStreamSynchronize(b->ctx[i]->stream);
+  const cudaStream_t s = b->ctx[0]->stream;
+  cudaEvent_t ev = b->ctx[0]->order_ev;
+  cudaEventRecord(ev, b->user_stream);
+  cudaStreamWaitEvent(s, ev, 0);
+  for (int i = 0; i < n; ++i) {
+    als_ctx* c = b->ctx[i];
+    MGWork& w = work_for(c, prec);
+    const int l = c->L - 1;
+    if (!bv[i] || !xv[i]) return batch_fail(b, ALS_EINVAL, "null vector");
+    cudaMemcpyAsync(w.b[l], bv[i], (size_t)(c->lev[l].g.N * c->dim) * w.es, cudaMemcpyDeviceToDevice, s);
+  }
+  if (cudaGraphLaunch(b->exec[k], s) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "batch graph launch");
+  long long kernels = 0;
+  for (int i = 0; i < n; ++i) {
+    als_ctx* c = b->ctx[i];
+    MGWork& w = work_for(c, prec);
+    const int l = c->L - 1;
+    kernels += w.graph_kernels;
+    cudaMemcpyAsync(xv[i], w.x[l], (size_t)(c->lev[l].g.N * c->dim) * w.es, cudaMemcpyDeviceToDevice, s);
+  }
+  count_launch(kernels);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return batch_fail(b, ALS_ECUDA, std::string("batch cycle: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < n; ++i) {
+    const als_status st = check_status(b->ctx[i], "batch cycle");
+    if (st != ALS_OK) return batch_fail(b, st, b->ctx[i]->err);
+  }
+  return ALS_OK;
+}
+
+const char* als_batch_last_error(const als_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+als_status als_set_patch_kernel(als_ctx* c, int level, int variant) {
+  if (!c) return ALS_EINVAL;
+  if (level < 1 || level >= c->L) return fail(c, ALS_EINVAL, "level must be in [1, levels)");
+  if (variant < -1 || variant > 2) return fail(c, ALS_EINVAL, "variant must be -1, 0, 1 or 2");
+  cudaStreamSynchronize(c->stream);
+  free_graphs(c);   // the captured cycles embed the variant
+  c->lev[level].patch_kernel = variant;
+  return ALS_OK;
+}
+
+als_status als_autotune_info(als_ctx* c, int level, int* variant, float* ms) {
+  if (!c || !variant) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
+  if (level < 1 || level >= c->L) return fail(c, ALS_EINVAL, "level must be in [1, levels)");
+  const LevelDev& Lv = c->lev[level];
+  *variant = Lv.patch_kernel;
+  if (ms)
+    for (int k = 0; k < 3; ++k) ms[k] = Lv.patch_kernel >= 0 ? Lv.tune_ms[k] : 0.f;
   return ALS_OK;
 }
 

@@ -25,6 +25,8 @@ struct LevelDev {
   // W^-1 of the augmentation when W = M_p(1/mu): per-cell (d+1)^2 blocks; NULL when W = M_p
   double* winv64;
   float* winv32;
+  int patch_kernel;      // FP32 patch-kernel variant picked by patch_autotune (-1: not yet tuned)
+  float tune_ms[3];      // measured time per launch of each variant (ms)
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
@@ -68,6 +70,8 @@ void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cu
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
                   cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, const double* den = nullptr);
 size_t patch_scratch_bytes(const LevelDev& L, int prec);
+// times the FP32 patch-kernel variants on this level and keeps the fastest (ms_out[3], optional)
+int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out = nullptr);
 // local solves on the coarse-cell interiors (stars of the fine vertices at the
 // coarse-cell centres):  mode 0: out = sum_K E_K A_K^-1 E_K^T in  (out zeroed first)
 //                        mode 1: out -= sum_K E_K A_K^-1 E_K^T in

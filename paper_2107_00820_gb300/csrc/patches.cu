@@ -669,42 +669,65 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
   count_launch(1);
 }
 
-// FP32 patch products: the TMA-staged kernel, or the direct-load one when the
-// environment sets ALS_PATCH_KERNEL=direct
-static bool use_direct_patch_kernel() {
-  static int v = -1;
-  if (v < 0) {
+// FP32 patch-product kernel variants: 0 = TMA ring with 2 stages, 1 = TMA ring
+// with 3 stages, 2 = direct 16-byte loads.  A level uses L.patch_kernel (picked by
+// patch_autotune); the environment variable ALS_PATCH_KERNEL = tma2 | tma3 | direct
+// forces one for every level.
+static int forced_patch_kernel() {
+  static int v = -2;
+  if (v == -2) {
     const char* e = getenv("ALS_PATCH_KERNEL");
-    v = (e && e[0] == 'd') ? 1 : 0;
+    v = -1;
+    if (e && e[0] == 'd') v = 2;
+    else if (e && e[0] == 't' && e[3] == '3') v = 1;
+    else if (e && e[0] == 't') v = 0;
   }
-  return v == 1;
+  return v;
 }
 
-constexpr int kTmaStages = 2;
+static int patch_variant(const LevelDev& L) {
+  const int f = forced_patch_kernel();
+  if (f >= 0) return f;
+  return L.patch_kernel >= 0 ? L.patch_kernel : 0;
+}
 
-template <int DIM>
-static void launch_patch_tma(const LevelDev& L, int interior, long long count, const float* r, float* out, int mode,
-                             DevStatus* st, cudaStream_t s) {
-  using C = TmaCfg<DIM, kTmaStages>;
+template <int DIM, int NST>
+static void launch_patch_tma_n(const LevelDev& L, int interior, long long count, const float* r, float* out,
+                               int mode, DevStatus* st, cudaStream_t s) {
+  using C = TmaCfg<DIM, NST>;
   const long long groups = (count + C::PPI - 1) / C::PPI;
   const long long per_sm = (227 * 1024) / (long long)(C::smem_bytes + 1024);   // resident CTAs per SM
   const long long cap = 152 * (per_sm < 1 ? 1 : per_sm);
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  k_patch_tma<DIM, kTmaStages><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count,
-                                                                                 r, out, mode, st);
+  k_patch_tma<DIM, NST><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count, r, out,
+                                                                          mode, st);
   count_launch(1);
+}
+
+template <int DIM>
+static void launch_patch_variant(int v, const LevelDev& L, int interior, long long count, const float* r, float* out,
+                                 int mode, DevStatus* st, cudaStream_t s) {
+  if (v == 2) launch_patch_direct<DIM>(L, interior, count, r, out, mode, s);
+  else if (v == 1) launch_patch_tma_n<DIM, 3>(L, interior, count, r, out, mode, st, s);
+  else launch_patch_tma_n<DIM, 2>(L, interior, count, r, out, mode, st, s);
+}
+
+template <int DIM, int NST>
+static void set_tma_smem_n() {
+  cudaFuncSetAttribute(k_patch_tma<DIM, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaCfg<DIM, NST>::smem_bytes);
+}
+
+template <int DIM>
+static void set_tma_smem() {
+  set_tma_smem_n<DIM, 2>();
+  set_tma_smem_n<DIM, 3>();
 }
 
 static size_t setup_smem(int dim, bool tensor) {
   const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1, NC = dim == 2 ? 6 : 21;
   return sizeof(double) * (NP * NP + 2 * NP + NB * NB * dim + NPR * dim * NB + NB * (tensor ? NC : 1));
-}
-
-template <int DIM>
-static void set_tma_smem() {
-  cudaFuncSetAttribute(k_patch_tma<DIM, kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaCfg<DIM, kTmaStages>::smem_bytes);
 }
 
 template <int DIM, bool TENSOR>
@@ -867,10 +890,8 @@ template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
                        cudaEvent_t e1, const double* den) {
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  if (use_direct_patch_kernel())
-    launch_patch_direct<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, s);
-  else
-    launch_patch_tma<DIM>(L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+  launch_patch_variant<DIM>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+                            L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   k_patch_gather<float, DIM><<<row_gather_blocks(L.g, DIM), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z,
                                                                          den);
@@ -945,14 +966,42 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
     const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2) * (fine.g.dim == 3 ? fine.g.n[2] / 2 : 1);
     if (!subtract) cudaMemsetAsync(out, 0, sizeof(float) * fine.g.N * fine.g.dim, s);
     const int md = subtract ? OUT_SUBTRACT : OUT_WRITE;
-    if (use_direct_patch_kernel()) {
-      if (fine.g.dim == 2) launch_patch_direct<2>(fine, 1, nc, (const float*)in, (float*)out, md, s);
-      else launch_patch_direct<3>(fine, 1, nc, (const float*)in, (float*)out, md, s);
-    } else {
-      if (fine.g.dim == 2) launch_patch_tma<2>(fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
-      else launch_patch_tma<3>(fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
-    }
+    const int v = patch_variant(fine);
+    if (fine.g.dim == 2) launch_patch_variant<2>(v, fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
+    else launch_patch_variant<3>(v, fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
   }
+}
+
+// Autotuner: times each FP32 patch-kernel variant on this level (one warm-up and
+// three timed launches each, CUDA events on the stream, r and scratch supplied
+// by the caller) and stores the fastest in L.patch_kernel.  Runs outside any
+// stream capture; waits for its own work.  Returns the chosen variant.
+int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out) {
+  if (forced_patch_kernel() >= 0) { L.patch_kernel = forced_patch_kernel(); return L.patch_kernel; }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < 3; ++v) {
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s);
+      if (L.g.dim == 2) launch_patch_variant<2>(v, L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+                                                L.status, s);
+      else launch_patch_variant<3>(v, L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[v] = ms / 3.f;
+    if (ms < best_ms) { best_ms = ms; best = v; }
+  }
+  count_launch(-12);   // tuning launches are not work of the caller's step
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.patch_kernel = best;
+  return best;
 }
 
 }  // namespace als

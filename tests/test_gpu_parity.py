@@ -269,6 +269,31 @@ def test_vcycle_fp32_within_its_precision_range(d, n, levels):
     assert r32 <= 1.5 * r_ref + 1e-4, (r32, r_ref)
 
 
+@pytest.mark.parametrize("d,n,levels", [(2, 32, 3), (3, 8, 3)])
+def test_patch_kernel_variants_and_autotuner(d, n, levels):
+    """Every FP32 patch-kernel variant (TMA ring with 2 or 3 stages, direct loads)
+    gives the FP32 cycle to single-precision accuracy of the FP64 oracle cycle; the
+    autotuner picks one of them and records the times it measured."""
+    pb = sinker(d, n, levels, 10.0, dr=1e2, seed=41)
+    H = oracle(pb, steps=2)
+    b = random_free(H.levels[-1], 42)
+    ref = H.vcycle(b)
+    ctx = context(pb, sweeps=2)
+    x32 = torch.zeros(b.shape[0], dtype=torch.float32, device="cuda")
+    ctx.vcycle(dev(b, torch.float32), x32, A.ALS_PREC_FP32)
+    for lvl in range(1, levels):
+        v, ms = ctx.autotune_info(lvl)
+        assert v in (0, 1, 2) and all(t > 0 for t in ms) and ms[v] == min(ms), (lvl, v, ms)
+    assert rel(host(x32), ref) <= 1e-4
+    for variant in (0, 1, 2):
+        for lvl in range(1, levels):
+            ctx.set_patch_kernel(lvl, variant)
+        x = torch.zeros_like(x32)
+        ctx.vcycle(dev(b, torch.float32), x, A.ALS_PREC_FP32)
+        assert rel(host(x), ref) <= 1e-4, variant
+        assert ctx.autotune_info(1)[0] == variant
+
+
 # --------------------------------------------------------------------------
 # a9/a10: full solve
 # --------------------------------------------------------------------------
