@@ -476,13 +476,113 @@ def ours(args, dist):
         print(json.dumps(out))
 
 
+def ours_batch(args, dist):
+    """Serving-style sweep: 64 independent multi-sinker instances (32 2D, 32 3D, uneven
+    sizes, contrasts 1e4..1e8, gamma 1e2 / 1e4), mixed precision with the P2 Schur
+    pairing.  Batched solves (interleaved FGMRES rounds, one wait per round) and
+    batched cycles (one graph launch) against one-at-a-time calls on the same contexts."""
+    import numpy as np
+    import torch
+
+    from paper_2107_00820_gb300 import Batch, alstokes as A
+    from synthetic.problems import batch_instances
+
+    torch.cuda.set_device(dist.local)
+    pbs = batch_instances(32, 32, seed=64 * dist.rank)
+    dofs = [problem_dofs(pb) for pb in pbs]
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    stream = torch.cuda.current_stream().cuda_stream
+    opts = {"mode": A.ALS_MODE_MIXED, "schur": A.ALS_SCHUR_P2, "rtol": RTOL, "maxit": 300, "sweeps": 5}
+    inst = [{"dim": pb.d, "n": pb.n, "levels": pb.levels, "coeffs": [dev(m) for m in pb.mu], "gamma": pb.gamma,
+             "options": opts} for pb in pbs]
+    t0 = time.perf_counter()
+    batch = Batch(inst, stream)
+    t_create = time.perf_counter() - t0
+    f = [dev(pb.f) for pb in pbs]
+    ubc = [dev(pb.u_bc) for pb in pbs]
+    u = [torch.zeros(s[0], dtype=torch.float64, device="cuda") for s in batch.shapes]
+    p = [torch.zeros(s[1], dtype=torch.float64, device="cuda") for s in batch.shapes]
+    ctxs = [batch.instance(i) for i in range(len(pbs))]
+    for _ in range(max(1, args.warmup - 2)):                   # captures every cycle graph
+        _, _, infos = batch.solve(f, ubc, None, u, p)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - w0) / reps
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = A.als_kernel_launches()
+    t_batch = dist.max(timed(lambda: batch.solve(f, ubc, None, u, p), args.steps))
+    launches = (A.als_kernel_launches() - launches0) // max(args.steps, 1)
+    clk = clocks.stop()
+    infos = batch.solve(f, ubc, None, u, p)[2]
+    u_b = [x.clone() for x in u]
+
+    def one_at_a_time():
+        for i, c in enumerate(ctxs):
+            c.solve(f[i], ubc[i], None, u[i], p[i])
+    t_seq = dist.max(timed(one_at_a_time, 1))
+    same = all(torch.equal(a, b) for a, b in zip(u_b, u))
+
+    # cycles: one batched graph launch against the instances' own graph launches
+    b32 = [torch.randn(s[0], dtype=torch.float32, device="cuda") for s in batch.shapes]
+    x32 = [torch.zeros_like(t) for t in b32]
+    batch.vcycle(b32, x32, A.ALS_PREC_FP32)
+    t_bcyc = timed(lambda: batch.vcycle(b32, x32, A.ALS_PREC_FP32), 5)
+
+    def seq_cycles():
+        for i, c in enumerate(ctxs):
+            c.vcycle(b32[i], x32[i], A.ALS_PREC_FP32)
+    t_scyc = timed(seq_cycles, 3)
+    its = [int(x.iterations) for x in infos]
+    tuned = {}
+    for i, pb in enumerate(pbs):
+        for lvl in range(1, pb.levels):
+            v = ctxs[i].autotune_info(lvl)[0]
+            tuned[v] = tuned.get(v, 0) + 1
+    total = sum(dofs)
+    out = {
+        "metric": "aggregate solve DoF/s, 64 independent instances (batched), mixed, 1e-8",
+        "value": dist.world * total / t_batch, "unit": "DoF/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch64", "instances": len(pbs), "dim_mix": "32 2D (16^2..256^2) + 32 3D (8^3..32^3)",
+                   "dr": "10^U[4,8]", "gamma": "{1e2, 1e4}", "schur": "P2 (W = M_p(1/mu))", "rtol": RTOL,
+                   "total_dofs": total, "step": "batched FGMRES solves of all instances (setup excluded)",
+                   "l2": "inputs larger than L2 (all instances' patch inverses ~10^10 B)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "one_at_a_time": {"ms": t_seq * 1e3, "dof_per_s": total / t_seq, "bitwise_equal_to_batched": same},
+        "batched_vs_one_at_a_time": t_seq / t_batch,
+        "cycles": {"batched_ms": t_bcyc * 1e3, "one_at_a_time_ms": t_scyc * 1e3, "speedup": t_scyc / t_bcyc,
+                   "prec": "fp32"},
+        "iterations": {"min": min(its), "max": max(its), "mean": statistics.mean(its),
+                       "all_converged": all(int(x.converged) == 1 for x in infos)},
+        "autotuner_choices": {("tma2", "tma3", "direct")[k]: v for k, v in sorted(tuned.items())},
+        "create_s": t_create,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    batch.close()
+    if dist.rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sinker3d_32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sinker3d_32", choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--sample-kind", default="cpu_baseline")
@@ -499,7 +599,10 @@ def main():
         return
     dist = Dist(args.gpus)
     try:
-        ours(args, dist)
+        if args.workload == "batch64":
+            ours_batch(args, dist)
+        else:
+            ours(args, dist)
     finally:
         dist.close()
 

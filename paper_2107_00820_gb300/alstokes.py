@@ -319,6 +319,7 @@ class Batch:
         opts = (als_options * k)()
         self._keep = []
         self.shapes = []
+        self._meta = []
         for i, ins in enumerate(instances):
             dim, levels = ins["dim"], ins["levels"]
             n = (ins["n"],) * dim if np.isscalar(ins["n"]) else tuple(ins["n"])
@@ -338,6 +339,7 @@ class Batch:
             opts[i] = default_options(**ins.get("options", {}))
             nu = dim * int(np.prod([2 * v + 1 for v in n]))
             self.shapes.append((nu, (dim + 1) * int(np.prod(n))))
+            self._meta.append((dim, n, levels))
         out = c_void_p()
         st = lib.als_batch_create(k, meshes, coeffs, gammas, opts, c_void_p(stream) if stream else None, byref(out))
         if st != ALS_OK:
@@ -369,6 +371,16 @@ class Batch:
         self._check(self._lib.als_batch_vcycle(self._b, prec, (c_void_p * k)(*[_ptr(t) for t in b]),
                                                (c_void_p * k)(*[_ptr(t) for t in x])))
 
+    def instance(self, i):
+        """Instance i as a Context (owned by the batch: closing it does nothing)."""
+        ptr = c_void_p()
+        self._check(self._lib.als_batch_context(self._b, c_int(i), byref(ptr)))
+        ctx = Context.__new__(_BorrowedContext)
+        ctx._ctx, ctx._lib = ptr, self._lib
+        dim, n, levels = self._meta[i]
+        ctx.dim, ctx.n, ctx.levels = dim, n, levels
+        return ctx
+
     def close(self):
         if getattr(self, "_b", None) is not None:
             self._lib.als_batch_destroy(self._b)
@@ -379,6 +391,13 @@ class Batch:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+class _BorrowedContext(Context):
+    """A context owned by a batch."""
+
+    def close(self):
+        self._ctx = None
 
 
 def als_create(dim, n, levels, coeffs, gamma, **kw):

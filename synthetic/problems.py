@@ -182,6 +182,41 @@ def sinker_problem(d, n, levels, count, omega, delta, dr, beta=10.0, gamma=1e4, 
                     "beta": beta, "seed": seed})
 
 
+# ---------------------------------------------------------------------------
+# serving-style batch of independent multi-sinker instances
+# ---------------------------------------------------------------------------
+BATCH_SIZES_2D = (16, 32, 48, 64, 96, 128, 192, 256)
+BATCH_SIZES_3D = (8, 12, 16, 24, 32)
+
+
+def batch_levels(n, d):
+    """Largest level count L with n / 2^(L-1) an integer >= 3 (3D) or >= 4 (2D)."""
+    floor = 3 if d == 3 else 4
+    L = 1
+    while n % (2 ** L) == 0 and n // (2 ** L) >= floor:
+        L += 1
+    return L
+
+
+def batch_instances(count_2d=32, count_3d=32, seed=0):
+    """Independent multi-sinker instances of uneven size: per instance i (seed + i)
+    the mesh size from BATCH_SIZES_2D / _3D, the contrast 10^U[4,8], gamma from
+    {1e2, 1e4} and the sinker centres, all drawn from the instance's own seed;
+    8 sinkers (2D, omega 0.1) or 16 (3D, omega 0.15), delta 200, beta 10."""
+    out = []
+    for i in range(count_2d + count_3d):
+        d = 2 if i < count_2d else 3
+        rng = np.random.default_rng(seed + i)
+        n = int(rng.choice(BATCH_SIZES_2D if d == 2 else BATCH_SIZES_3D))
+        dr = float(10.0 ** rng.uniform(4.0, 8.0))
+        gamma = float(rng.choice([1e2, 1e4]))
+        count, omega = (8, 0.1) if d == 2 else (16, 0.15)
+        pb = sinker_problem(d, n, batch_levels(n, d), count, omega, 200.0, dr, 10.0, gamma,
+                            seed=1000 + seed + i)
+        out.append(pb)
+    return out
+
+
 def sinker_2d(n=128, levels=5, gamma=1e4, dr=1e6, seed=0, count=8):
     """2D multi-sinker, 8 sinkers, omega = 0.1, delta = 200, DR = 1e6."""
     return sinker_problem(2, n, levels, count, 0.1, 200.0, dr, 10.0, gamma, seed)
