@@ -43,11 +43,15 @@ WORKLOADS = {
     # 2D multi-sinker, 128^2 quads, 5 levels (coarse 8^2), 8 sinkers, omega 0.1, delta 200, DR 1e6
     "sinker2d_128": dict(d=2, n=128, levels=5, count=8, omega=0.1, delta=200.0, dr=1e6, beta=10.0,
                          gamma=1e4, seed=0, sweeps=5),
+    # 3D anisotropic viscoplastic linearisation, 48^3 hexes, 4 levels (coarse 6^3): per-point
+    # 4th-order tensor C (21 Mandel entries), mu_eff contrast ~1e10, gamma 1e3, P2 Schur pairing
+    "viscoplastic3d_48": dict(kind="tensor", d=3, n=48, levels=4, gamma=1e3, seed=0, sweeps=5, schur="P2"),
 }
 # bounded samples of the same law for the oracle (CPU baseline / reference arm)
 SAMPLES = {
     "sinker3d_32": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
     "sinker2d_128": dict(cpu_baseline=dict(n=64, levels=4), reference=dict(n=32, levels=3)),
+    "viscoplastic3d_48": dict(cpu_baseline=dict(n=8, levels=2), reference=dict(n=8, levels=2)),
 }
 RTOL = 1e-8
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -56,7 +60,9 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 def make_problem(spec, n=None, levels=None):
-    from synthetic.problems import sinker_problem
+    from synthetic.problems import sinker_problem, viscoplastic_problem
+    if spec.get("kind") == "tensor":
+        return viscoplastic_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["gamma"], spec["seed"])
     return sinker_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["count"], spec["omega"],
                           spec["delta"], spec["dr"], spec["beta"], spec["gamma"], spec["seed"])
 
@@ -201,8 +207,10 @@ def oracle_sample_step(spec, n, levels):
     from oracle.stokes import StokesSolver
     pb = make_problem(spec, n, levels)
     t0 = time.perf_counter()
-    H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"])
-    u, p, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=RTOL)
+    p2 = spec.get("schur") == "P2"
+    H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"], kind=spec.get("kind", "scalar"),
+                  mu_eff=pb.meta.get("mu_eff"), W="Mp_mu" if p2 else "Mp")
+    u, p, its, _ = StokesSolver(H, schur="P2" if p2 else "P1").solve(pb.f, pb.u_bc, rtol=RTOL)
     dt = time.perf_counter() - t0
     return problem_dofs(pb), dt, its
 
@@ -285,17 +293,20 @@ def ours(args, dist):
     dofs = problem_dofs(pb)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
     mu_d = [dev(m) for m in pb.mu]
+    tensor = spec.get("kind") == "tensor"
+    mue_d = [dev(m) for m in pb.meta["mu_eff"]] if tensor else None
+    schur = A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1
     f_d, ubc_d = dev(pb.f), dev(pb.u_bc)
     nu = pb.d * math.prod(2 * v + 1 for v in pb.n)
     npres = (pb.d + 1) * math.prod(pb.n)
     u_d = torch.zeros(nu, dtype=torch.float64, device="cuda")
     p_d = torch.zeros(npres, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    ctx = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, stream=stream, mode=A.ALS_MODE_MIXED, rtol=RTOL,
-                  maxit=200, sweeps=spec["sweeps"])
+    ctx = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_MIXED,
+                  rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur)
 
     def step():
-        ctx.update_coefficients(mu_d)
+        ctx.update_coefficients(mu_d, mue_d)
         return ctx.solve(f_d, ubc_d, None, u_d, p_d)[2]
 
     for _ in range(args.warmup):
@@ -330,7 +341,7 @@ def ours(args, dist):
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     for _ in range(3):
-        ctx.update_coefficients(mu_d)
+        ctx.update_coefficients(mu_d, mue_d)
     p1.record()
     torch.cuda.synchronize()
     t_setup = p0.elapsed_time(p1) / 3 / 1e3
@@ -367,14 +378,14 @@ def ours(args, dist):
     vcyc64_s = 3 / (e0.elapsed_time(e1) / 1e3)
 
     # all-FP64 GPU path on the same problem
-    ctx64 = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, stream=stream, mode=A.ALS_MODE_FP64, rtol=RTOL,
-                    maxit=200, sweeps=spec["sweeps"])
+    ctx64 = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_FP64,
+                    rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur)
     u64 = torch.zeros_like(u_d)
     p64 = torch.zeros_like(p_d)
     ctx64.solve(f_d, ubc_d, None, u64, p64)
     torch.cuda.synchronize()
     e0.record()
-    ctx64.update_coefficients(mu_d)
+    ctx64.update_coefficients(mu_d, mue_d)
     info64 = ctx64.solve(f_d, ubc_d, None, u64, p64)[2]
     e1.record()
     torch.cuda.synchronize()
@@ -390,20 +401,21 @@ def ours(args, dist):
 
     # end to end through the C ABI with host buffers
     mu_h = [np.ascontiguousarray(m) for m in pb.mu]
+    mue_h = [np.ascontiguousarray(m) for m in pb.meta["mu_eff"]] if tensor else None
     f_h = np.ascontiguousarray(pb.f)
     ubc_h = np.ascontiguousarray(pb.u_bc)
     u_h = np.zeros(nu)
     p_h = np.zeros(npres)
-    h2d = sum(m.nbytes for m in mu_h) + f_h.nbytes + ubc_h.nbytes
+    h2d = sum(m.nbytes for m in mu_h) + (sum(m.nbytes for m in mue_h) if tensor else 0) + f_h.nbytes + ubc_h.nbytes
     d2h = u_h.nbytes + p_h.nbytes
-    ctx.update_coefficients(mu_h)
+    ctx.update_coefficients(mu_h, mue_h)
     ctx.solve(f_h, ubc_h, None, u_h, p_h)
     dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e0.record()
     for _ in range(args.steps):
-        ctx.update_coefficients(mu_h)
+        ctx.update_coefficients(mu_h, mue_h)
         ctx.solve(f_h, ubc_h, None, u_h, p_h)
     e1.record()
     torch.cuda.synchronize()
@@ -422,8 +434,9 @@ def ours(args, dist):
     # operator apply (K1 cell kernel) on the finest level, timed live inside the smoother
     ncells = math.prod(F)
     nq = 3 ** pb.d
-    k1_bytes = nu * 4 * 2 + ncells * nq * 4            # read x, write y, read mu (FP32)
-    k1_flops = ncells * APPLY_FLOPS_PER_CELL[pb.d]
+    ncq = (6 if pb.d == 2 else 21) if tensor else 1
+    k1_bytes = nu * 4 * 2 + ncells * nq * ncq * 4      # read x, write y, read mu or C (FP32)
+    k1_flops = ncells * (APPLY_FLOPS_PER_CELL[pb.d] + (nq * 2 * 2 * ncq if tensor else 0))
     k1_s = (k1_ms / max(k1_n, 1)) / 1e3
     roofline_apply = None
     if k1_n:
@@ -440,10 +453,13 @@ def ours(args, dist):
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "dim": pb.d, "cells": list(pb.n), "levels": pb.levels,
-                   "gamma": pb.gamma, "dr": spec["dr"], "sinkers": spec["count"], "dofs": dofs,
+                   "gamma": pb.gamma, "dr": spec.get("dr", pb.meta.get("contrast")),
+                   "sinkers": spec.get("count"), "coefficients": "tensor C (21 per point)" if tensor else "scalar mu",
+                   "schur": spec.get("schur", "P1"), "dofs": dofs,
                    "smoother": f"GMRES({spec['sweeps']}) x vertex-star PSC", "rtol": RTOL,
                    "step": "setup (patch factorisation, coarse Cholesky, Schur) + mixed FGMRES solve",
-                   "l2": "inputs larger than L2 (fine-level FP32+FP64 patch inverses 1.4 GB)",
+                   "l2": "inputs larger than L2 (fine-level FP32+FP64 patch inverses %.1f GB)"
+                         % (math.prod(v + 1 for v in pb.n) * 12 * (pb.d * 3 ** pb.d) * (pb.d * 3 ** pb.d + 1) / 2 / 1e9),
                    "parallelism": f"replicas x{dist.world}"},
         "iterations": its[-1] if its else None,
         "vcycles_per_s": vcyc_s,

@@ -32,7 +32,10 @@ def main():
     spec = bench.WORKLOADS[args.workload]
     pb = bench.make_problem(spec)
     mu = [torch.as_tensor(m, device="cuda") for m in pb.mu]
-    ctx = Context(pb.d, pb.n, pb.levels, mu, pb.gamma, mode=A.ALS_MODE_MIXED, sweeps=spec["sweeps"])
+    tensor = spec.get("kind") == "tensor"
+    mue = [torch.as_tensor(m, device="cuda") for m in pb.meta["mu_eff"]] if tensor else None
+    ctx = Context(pb.d, pb.n, pb.levels, mu, pb.gamma, mu_eff=mue, mode=A.ALS_MODE_MIXED, sweeps=spec["sweeps"],
+                  schur=A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1)
     nu = ctx.nu()
     vecs = {}
     if args.prec in ("fp32", "both"):
@@ -45,7 +48,7 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
     if args.setup:
-        ctx.update_coefficients(mu)
+        ctx.update_coefficients(mu, mue)
     else:
         for _ in range(args.vcycles):
             for p, b in vecs.items():
