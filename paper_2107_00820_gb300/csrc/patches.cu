@@ -63,199 +63,7 @@ __device__ __forceinline__ void mandel_of(int al, const double* gr, double* e) {
   }
 }
 
-// coef: scalar mu [cell][3^d] or Mandel tensor C [cell][3^d][NC] (upper triangle, row-major)
-template <int DIM, bool TENSOR>
-__global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ coef, double* __restrict__ inv64,
-                              float* __restrict__ inv32, int pstride, DevStatus* st,
-                              const double* __restrict__ winv) {
-  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
-  constexpr int NM = Sz<DIM>::NM, NC = Sz<DIM>::NC;
-  constexpr int NSUB = 1 << DIM;  // patch nodes inside one cell of the star
-  extern __shared__ double sm[];
-  double* A = sm;                    // NP x NP patch matrix, inverted in place
-  double* X = A + NP * NP;           // 2 NP: pivot column and scaled pivot row
-  double* gt = X + 2 * NP;           // [q][a][k] physical gradient of phi_a at point q
-  double* bt = gt + NB * NB * DIM;   // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
-  double* wq = bt + NPR * DIM * NB;  // [q] |J| w_q mu_q, or [q][NC] |J| w_q C_q, of the current cell
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const long long v = blockIdx.x;
-  int vx, vy, vz;
-  vertex_coords<DIM>(g, v, vx, vy, vz);
-
-  double s[3] = {2.0 / g.h[0], 2.0 / g.h[1], DIM == 3 ? 2.0 / g.h[2] : 0.0};
-  double wdet = 1.0, vol = 1.0;
-  for (int k = 0; k < DIM; ++k) { wdet *= 0.5 * g.h[k]; vol *= g.h[k]; }
-
-  for (int e = tid; e < NP * NP; e += nt) A[e] = 0.0;
-  for (int e = tid; e < NB * NB; e += nt) {
-    const int q = e / NB, a = e % NB;
-    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    const double bx = Ref<double>::B(qx, ax), by = Ref<double>::B(qy, ay);
-    const double bz = DIM == 3 ? Ref<double>::B(qz, az) : 1.0;
-    gt[e * DIM + 0] = Ref<double>::D(qx, ax) * by * bz * s[0];
-    gt[e * DIM + 1] = bx * Ref<double>::D(qy, ay) * bz * s[1];
-    if (DIM == 3) gt[e * DIM + 2] = bx * by * Ref<double>::D(qz, az) * s[2];
-  }
-  __syncthreads();
-  for (int e = tid; e < NPR * DIM * NB; e += nt) {
-    const int p = e / (DIM * NB), al = (e / NB) % DIM, a = e % NB;
-    double acc = 0.0;
-    for (int q = 0; q < NB; ++q) {
-      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-      const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
-      const double psi = p == 0 ? 1.0 : Ref<double>::G(p == 1 ? qx : (p == 2 ? qy : qz));
-      acc += w * psi * gt[(q * NB + a) * DIM + al];
-    }
-    bt[e] = -acc;
-  }
-
-  // contributions of the 2^d cells of the star
-  for (int sc = 0; sc < NSUB; ++sc) {
-    const int sx = sc & 1, sy = (sc >> 1) & 1, sz = (sc >> 2) & 1;
-    const int cx = vx - 1 + sx, cy = vy - 1 + sy, cz = DIM == 3 ? vz - 1 + sz : 0;
-    const bool valid = cx >= 0 && cx < g.n[0] && cy >= 0 && cy < g.n[1] &&
-                       (DIM == 2 || (cz >= 0 && cz < g.n[2]));
-    __syncthreads();
-    if (!valid) continue;
-    const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
-    for (int e = tid; e < NB * (TENSOR ? NC : 1); e += nt) {
-      const int q = TENSOR ? e / NC : e;
-      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-      wq[e] = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) *
-              coef[cell * NB * (TENSOR ? NC : 1) + e];
-    }
-    __syncthreads();
-    for (int pr = tid; pr < NSUB * NSUB; pr += nt) {
-      const int i = pr / NSUB, j = pr % NSUB;
-      // patch offset o_k and cell-local index a_k of sub-node i (same for j):
-      //   s_k = 0 (cell below the vertex): o_k in {0,1}, a_k = o_k + 1
-      //   s_k = 1 (cell above):            o_k in {1,2}, a_k = o_k - 1
-      int oi[3], ai[3], oj[3], aj[3];
-      const int sv[3] = {sx, sy, sz};
-      for (int k = 0; k < 3; ++k) {
-        const int bi = (i >> k) & 1, bj = (j >> k) & 1;
-        oi[k] = sv[k] ? bi + 1 : bi; ai[k] = sv[k] ? oi[k] - 1 : oi[k] + 1;
-        oj[k] = sv[k] ? bj + 1 : bj; aj[k] = sv[k] ? oj[k] - 1 : oj[k] + 1;
-      }
-      const int P = oi[0] + 3 * oi[1] + (DIM == 3 ? 9 * oi[2] : 0);
-      const int Q = oj[0] + 3 * oj[1] + (DIM == 3 ? 9 * oj[2] : 0);
-      long long ndP, ndQ;
-      if (!patch_node<DIM>(g, vx, vy, vz, P, ndP) || !patch_node<DIM>(g, vx, vy, vz, Q, ndQ)) continue;
-      const int a = ai[0] + 3 * ai[1] + (DIM == 3 ? 9 * ai[2] : 0);
-      const int b = aj[0] + 3 * aj[1] + (DIM == 3 ? 9 * aj[2] : 0);
-      // viscous block V[al][be] = sum_q |J| w_q (C eps(phi_b e_be)) : eps(phi_a e_al);
-      // scalar mu: 2 mu eps : eps = mu (delta_ab grad phi_a . grad phi_b + d_be phi_a d_al phi_b)
-      double V[DIM][DIM];
-      for (int k = 0; k < DIM; ++k)
-        for (int l = 0; l < DIM; ++l) V[k][l] = 0.0;
-      if constexpr (!TENSOR) {
-        double G[DIM][DIM];
-        for (int k = 0; k < DIM; ++k)
-          for (int l = 0; l < DIM; ++l) G[k][l] = 0.0;
-        for (int q = 0; q < NB; ++q) {
-          const double w = wq[q];
-          for (int k = 0; k < DIM; ++k) {
-            const double ga = w * gt[(q * NB + a) * DIM + k];
-            for (int l = 0; l < DIM; ++l) G[k][l] += ga * gt[(q * NB + b) * DIM + l];
-          }
-        }
-        double tr = 0.0;
-        for (int k = 0; k < DIM; ++k) tr += G[k][k];
-        for (int al = 0; al < DIM; ++al)
-          for (int be = 0; be < DIM; ++be) V[al][be] = G[be][al] + (al == be ? tr : 0.0);
-      } else {
-        for (int q = 0; q < NB; ++q) {
-          const double* Cq = wq + q * NC;
-          double eA[DIM][NM], t[DIM][NM];
-          for (int al = 0; al < DIM; ++al) mandel_of<DIM>(al, gt + (q * NB + a) * DIM, eA[al]);
-          for (int be = 0; be < DIM; ++be) {
-            double eB[NM];
-            mandel_of<DIM>(be, gt + (q * NB + b) * DIM, eB);
-            for (int m = 0; m < NM; ++m) t[be][m] = 0.0;
-            int idx = 0;
-            for (int m = 0; m < NM; ++m)
-              for (int n = m; n < NM; ++n) {
-                const double c = Cq[idx++];
-                t[be][m] += c * eB[n];
-                if (n != m) t[be][n] += c * eB[m];
-              }
-          }
-          for (int al = 0; al < DIM; ++al)
-            for (int be = 0; be < DIM; ++be) {
-              double acc = 0.0;
-              for (int m = 0; m < NM; ++m) acc += eA[al][m] * t[be][m];
-              V[al][be] += acc;
-            }
-        }
-      }
-      for (int al = 0; al < DIM; ++al)
-        for (int be = 0; be < DIM; ++be) {
-          double val = V[al][be];
-          double alv = 0.0;
-          if (winv) {   // gamma B_K^T W_K^-1 B_K with W = M_p(1/mu)
-            for (int p = 0; p < NPR; ++p)
-              for (int q2 = 0; q2 < NPR; ++q2)
-                alv += bt[(p * DIM + al) * NB + a] * winv[(cell * NPR + p) * NPR + q2] * bt[(q2 * DIM + be) * NB + b];
-            val += gamma * alv;
-          } else {      // W = M_p = |K| diag(1, 1/3, ..)
-            for (int p = 0; p < NPR; ++p)
-              alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
-            val += gamma / vol * alv;
-          }
-          A[(al * NB + P) * NP + be * NB + Q] += val;
-        }
-    }
-  }
-  __syncthreads();
-  // identity rows for nodes outside the domain or on the Dirichlet boundary
-  for (int i = tid; i < NP; i += nt) {
-    long long nd;
-    if (!patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) A[i * NP + i] = 1.0;
-  }
-  __syncthreads();
-
-  // In-place Gauss-Jordan inversion without pivoting.  A_v is SPD, so every pivot
-  // is a Schur complement of a leading block and is positive (as in Cholesky);
-  // a non-positive pivot is reported as ALS_ENOTSPD.  Per pivot k: the scaled
-  // row k and the column k are taken aside (pk, rk), then every entry is
-  // updated, A[i][j] -= A[i][k] A[k][j] / A[k][k].
-  double* pk = X;
-  double* rk = X + NP;
-  for (int k = 0; k < NP; ++k) {
-    double d = A[k * NP + k];
-    if (!(d > 0.0)) {
-      if (tid == 0) report(st, 4 /* ALS_ENOTSPD */, v);
-      d = 1.0;
-    }
-    const double p = 1.0 / d;
-    for (int i = tid; i < NP; i += nt) {
-      pk[i] = (i == k) ? 0.0 : A[i * NP + k];
-      rk[i] = (i == k) ? p : A[k * NP + i] * p;
-    }
-    __syncthreads();
-    for (int e = tid; e < NP * NP; e += nt) {
-      const int i = e / NP, j = e % NP;
-      if (i == k) A[e] = rk[j];
-      else A[e] = ((j == k) ? 0.0 : A[e]) - pk[i] * rk[j];
-    }
-    __syncthreads();
-  }
-  // A^-1 (symmetrised), packed by diagonals in FP64 and block-packed in FP32
-  constexpr int NPK = NP * (NP + 1) / 2;
-  if (inv32) {
-    constexpr BlockLayout BLp = BlockLayout(NP);
-    for (int e = 44 * BLp.nbp + BLp.nbp + tid; e < BLp.q2; e += nt) inv32[v * pstride + e] = 0.f;
-  }
-  for (int e = tid; e < NPK; e += nt) {
-    int t = 0;
-    while (diag_start(NP, t + 1) <= e) ++t;
-    const int i = e - diag_start(NP, t), j = i + t;
-    const double val = 0.5 * (A[i * NP + j] + A[j * NP + i]);
-    if (inv64) inv64[v * pstride + e] = val;
-    if (inv32) inv32[v * pstride + BlockLayout(NP).index(i, j)] = (float)val;
-  }
-}
+#include "patch_setup.cuh"
 
 // ---------------------------------------------------------------------------
 // K4 (FP32): TMA-pipelined block-packed patch products
@@ -725,16 +533,12 @@ static void set_tma_smem() {
   set_tma_smem_n<DIM, 3>();
 }
 
-static size_t setup_smem(int dim, bool tensor) {
-  const int NP = dim == 2 ? 18 : 81, NB = dim == 2 ? 9 : 27, NPR = dim + 1, NC = dim == 2 ? 6 : 21;
-  return sizeof(double) * (NP * NP + 2 * NP + NB * NB * dim + NPR * dim * NB + NB * (tensor ? NC : 1));
-}
-
 template <int DIM, bool TENSOR>
 static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
-  const size_t smem = setup_smem(DIM, TENSOR);
+  using C = SetupCfg<DIM, TENSOR>;
+  const size_t smem = C::smem;
   cudaFuncSetAttribute(k_patch_setup<DIM, TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_patch_setup<DIM, TENSOR><<<(unsigned)L.g.nverts, DIM == 3 ? 256 : 128, smem, s>>>(
+  k_patch_setup<DIM, TENSOR><<<(unsigned)L.g.nverts, C::THREADS, smem, s>>>(
       L.g, gamma, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st, L.winv64);
   count_launch(1);
 }
