@@ -27,11 +27,13 @@ struct SetupCfg {
   static constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
   static constexpr int NM = Sz<DIM>::NM, NC = Sz<DIM>::NC, NSUB = 1 << DIM;
   static constexpr int NPK = NP * (NP + 1) / 2;
-  // shared doubles: M | pk | gt | bt | wq | T
-  static constexpr int n_M = NPK, n_pk = NP, n_gt = NB * NB * DIM, n_bt = NPR * DIM * NB;
-  static constexpr int n_wq = NB * (TENSOR ? NC : 1);
+  // shared doubles: M | pk | qk | gt | bt | wq | wpsi | T, then the row index of every packed entry
+  static constexpr int n_M = NPK, n_pk = NP, n_qk = NP, n_gt = NB * NB * DIM, n_bt = NPR * DIM * NB;
+  static constexpr int n_wq = NB * (TENSOR ? NC : 1), n_wpsi = NPR * NB;
   static constexpr int n_T = TENSOR ? NB * NSUB * DIM * NM : 0;
-  static constexpr size_t smem = sizeof(double) * (n_M + n_pk + n_gt + n_bt + n_wq + n_T);
+  static constexpr int n_dbl = n_M + n_pk + n_qk + n_gt + n_bt + n_wq + n_wpsi + n_T;
+  static constexpr size_t smem = sizeof(double) * n_dbl + NPK;   // + uint8 row index per entry
+  static_assert(NP <= 255, "row index stored in 8 bits");
   static constexpr int THREADS = DIM == 3 ? 256 : 128;
 };
 
@@ -52,10 +54,38 @@ __device__ __forceinline__ void sub_node(int i, int sx, int sy, int sz, int& P, 
   a = al[0] + 3 * al[1] + (DIM == 3 ? 9 * al[2] : 0);
 }
 
+// Nonzero Mandel entries of eps(phi e_al) for the gradient gr of phi: slot al with
+// d_al phi, and the shear slots of the pairs (al, o) with sqrt(1/2) d_o phi (the same
+// entries as mandel_of without its zeros; 3 in 3D, 2 in 2D).  3D shear slots:
+// 3 = (1,2), 4 = (0,2), 5 = (0,1); 2D: 2 = (0,1).
+template <int DIM>
+__device__ __forceinline__ void strain_nonzeros(int al, const double* gr, int (&n)[3], double (&e)[3]) {
+  constexpr double ir2 = 0.70710678118654752440;
+  n[0] = al;
+  e[0] = gr[al];
+  if (DIM == 2) {
+    n[1] = 2; e[1] = gr[1 - al] * ir2;
+    n[2] = 0; e[2] = 0.0;
+  } else {
+    const int o1 = al == 0 ? 1 : 0, o2 = al == 2 ? 1 : 2;      // the two other axes
+    n[1] = (al + o1 == 1) ? 5 : ((al + o1 == 2) ? 4 : 3);
+    n[2] = (al + o2 == 1) ? 5 : ((al + o2 == 2) ? 4 : 3);
+    e[1] = gr[o1] * ir2;
+    e[2] = gr[o2] * ir2;
+  }
+}
+
 // coef: scalar mu [cell][3^d] or Mandel tensor C [cell][3^d][NC] (upper triangle, row-major)
+// Level constants computed once on the host: 2/h per axis, |J| = prod h/2, |K|, gamma/|K|
+struct SetupGeo {
+  double s[3];
+  double wdet, vol, gvol;
+};
+
 template <int DIM, bool TENSOR>
-__global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ coef, double* __restrict__ inv64,
-                              float* __restrict__ inv32, int pstride, DevStatus* st,
+__global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : 3)
+k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef,
+                              double* __restrict__ inv64, float* __restrict__ inv32, int pstride, DevStatus* st,
                               const double* __restrict__ winv) {
   using C = SetupCfg<DIM, TENSOR>;
   constexpr int NP = C::NP, NB = C::NB, NPR = C::NPR, NM = C::NM, NC = C::NC, NSUB = C::NSUB;
@@ -63,21 +93,30 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
   __shared__ double s_dinv;
   double* M = sm;                    // packed upper triangle of the patch matrix, swept in place
   double* pk = M + C::n_M;           // pivot column of the current sweep
-  double* gt = pk + C::n_pk;         // [q][a][k] physical gradient of phi_a at point q
+  double* qk = pk + C::n_pk;         // pivot column / pivot
+  double* gt = qk + C::n_qk;         // [q][a][k] physical gradient of phi_a at point q
   double* bt = gt + C::n_gt;         // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
   double* wq = bt + C::n_bt;         // [q] |J| w_q mu_q, or [q][NC] |J| w_q C_q, of the current cell
-  double* T = wq + C::n_wq;          // tensor: [q][j][be][m] = (C_q eps(phi_b(j) e_be))_m
+  double* wpsi = wq + C::n_wq;       // [p][q] |J| w_q psi_p(q)
+  double* T = wpsi + C::n_wpsi;      // tensor: [q][j][be][m] = (C_q eps(phi_b(j) e_be))_m
+  unsigned char* rowof = reinterpret_cast<unsigned char*>(sm + C::n_dbl);   // row of every packed entry
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   const long long v = blockIdx.x;
   int vx, vy, vz;
   vertex_coords<DIM>(g, v, vx, vy, vz);
 
-  double s[3] = {2.0 / g.h[0], 2.0 / g.h[1], DIM == 3 ? 2.0 / g.h[2] : 0.0};
-  double wdet = 1.0, vol = 1.0;
-  for (int k = 0; k < DIM; ++k) { wdet *= 0.5 * g.h[k]; vol *= g.h[k]; }
+  const double* s = sg.s;
+  const double wdet = sg.wdet;
 
   for (int e = tid; e < C::NPK; e += nt) M[e] = 0.0;
+  for (int i = tid; i < NP; i += nt)
+    for (int j = i; j < NP; ++j) rowof[tri_row(NP, i) + (j - i)] = (unsigned char)i;
+  for (int e = tid; e < NPR * NB; e += nt) {
+    const int p = e / NB, q = e % NB;
+    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+    const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
+    wpsi[e] = p == 0 ? w : w * Ref<double>::G(p == 1 ? qx : (p == 2 ? qy : qz));
+  }
   for (int e = tid; e < NB * NB; e += nt) {
     const int q = e / NB, a = e % NB;
     const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
@@ -92,12 +131,7 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
   for (int e = tid; e < NPR * DIM * NB; e += nt) {
     const int p = e / (DIM * NB), al = (e / NB) % DIM, a = e % NB;
     double acc = 0.0;
-    for (int q = 0; q < NB; ++q) {
-      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-      const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
-      const double psi = p == 0 ? 1.0 : Ref<double>::G(p == 1 ? qx : (p == 2 ? qy : qz));
-      acc += w * psi * gt[(q * NB + a) * DIM + al];
-    }
+    for (int q = 0; q < NB; ++q) acc += wpsi[p * NB + q] * gt[(q * NB + a) * DIM + al];
     bt[e] = -acc;
   }
 
@@ -110,12 +144,7 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
     __syncthreads();
     if (!valid) continue;
     const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
-    for (int e = tid; e < C::n_wq; e += nt) {
-      const int q = TENSOR ? e / NC : e;
-      const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-      wq[e] = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0) *
-              coef[cell * C::n_wq + e];
-    }
+    for (int e = tid; e < C::n_wq; e += nt) wq[e] = wpsi[TENSOR ? e / NC : e] * coef[cell * C::n_wq + e];
     __syncthreads();
     if constexpr (TENSOR) {
       // T[q][j][be] = C_q eps(phi_b e_be), b the cell-local node of sub-node j
@@ -123,24 +152,31 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
         const int q = e / (NSUB * DIM), j = (e / DIM) % NSUB, be = e % DIM;
         int Q, b;
         sub_node<DIM>(j, sx, sy, sz, Q, b);
-        double eB[NM];
-        mandel_of<DIM>(be, gt + (q * NB + b) * DIM, eB);
+        // eps(phi_b e_be) in Mandel form has d nonzeros: slot be and the shear slots
+        int n_[3];
+        double e_[3];
+        strain_nonzeros<DIM>(be, gt + (q * NB + b) * DIM, n_, e_);
         const double* Cq = wq + q * NC;
         double* t = T + e * NM;
         for (int m = 0; m < NM; ++m) {
           double acc = 0.0;
-          for (int n = 0; n < NM; ++n) {
-            const int lo = m < n ? m : n, hi = m < n ? n : m;
-            acc += Cq[lo * NM - (lo * (lo - 1)) / 2 + (hi - lo)] * eB[n];
+#pragma unroll
+          for (int r = 0; r < DIM; ++r) {
+            const int n = n_[r], lo = m < n ? m : n, hi = m < n ? n : m;
+            acc += Cq[lo * NM - (lo * (lo - 1)) / 2 + (hi - lo)] * e_[r];
           }
           t[m] = acc;
         }
       }
       __syncthreads();
     }
-    // one thread per sub-node pair i <= j: the d x d block of the pair, entries stored at
-    // (min(row, col), max(row, col)); the pair (j, i) is the transpose and is skipped
-    for (int pr = tid; pr < NSUB * NSUB; pr += nt) {
+    // Sub-node pairs i <= j (the pair (j, i) is the transpose): one thread per pair
+    // (scalar mu: the d x d block from the 3x3 gradient products) or per (pair, row
+    // component al) (tensor: d rows of products with T).  Entries go to
+    // (min(row, col), max(row, col)); in a diagonal block (i == j) only row <= col.
+    constexpr int NAL = TENSOR ? DIM : 1;
+    for (int it = tid; it < NSUB * NSUB * NAL; it += nt) {
+      const int pr = it / NAL, al0 = it % NAL;
       const int i = pr / NSUB, j = pr % NSUB;
       if (i > j) continue;
       int P, a, Q, b;
@@ -179,24 +215,24 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
 #pragma unroll
           for (int be = 0; be < DIM; ++be) V[al][be] = G[be][al] + (al == be ? tr : 0.0);
       } else {
+        // (C eps(phi_b e_be)) : eps(phi_a e_al) with the d nonzeros of eps(phi_a e_al)
         for (int q = 0; q < NB; ++q) {
-          double eA[DIM][NM];
-#pragma unroll
-          for (int al = 0; al < DIM; ++al) mandel_of<DIM>(al, gt + (q * NB + a) * DIM, eA[al]);
+          int n_[3];
+          double e_[3];
+          strain_nonzeros<DIM>(al0, gt + (q * NB + a) * DIM, n_, e_);
           const double* t = T + (q * NSUB + j) * DIM * NM;
 #pragma unroll
-          for (int al = 0; al < DIM; ++al)
+          for (int be = 0; be < DIM; ++be) {
+            double acc = 0.0;
 #pragma unroll
-            for (int be = 0; be < DIM; ++be) {
-              double acc = 0.0;
-#pragma unroll
-              for (int m = 0; m < NM; ++m) acc += eA[al][m] * t[be * NM + m];
-              V[al][be] += acc;
-            }
+            for (int r = 0; r < DIM; ++r) acc += e_[r] * t[be * NM + n_[r]];
+            V[al0][be] += acc;
+          }
         }
       }
 #pragma unroll
-      for (int al = 0; al < DIM; ++al)
+      for (int al = 0; al < DIM; ++al) {
+        if (TENSOR && al != al0) continue;
 #pragma unroll
         for (int be = 0; be < DIM; ++be) {
           const int row = al * NB + P, col = be * NB + Q;
@@ -210,11 +246,12 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
           } else {      // W = M_p = |K| diag(1, 1/3, ..)
             for (int p = 0; p < NPR; ++p)
               alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
-            val += gamma / vol * alv;
+            val += sg.gvol * alv;
           }
           const int lo = row < col ? row : col, hi = row < col ? col : row;
           M[tri_row(NP, lo) + (hi - lo)] += val;
         }
+      }
     }
   }
   __syncthreads();
@@ -225,11 +262,14 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
   }
   __syncthreads();
 
-  // symmetric sweep of every pivot in order: M -> -A_v^-1
+  // symmetric sweep of every pivot in order: M -> -A_v^-1.  Three phases per pivot:
+  // the pivot column and 1/pivot (one division, thread 0); the scaled column; the
+  // rank-1 update over the packed entries (each thread a strided subset, full warps)
+  // with the pivot row/column written in the same phase (disjoint entries).
   for (int k = 0; k < NP; ++k) {
     for (int i = tid; i < NP; i += nt)
       pk[i] = (i == k) ? 0.0 : M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)];
-    if (tid == 0) {   // one FP64 division per pivot, not one per thread
+    if (tid == 0) {
       double d = M[tri_row(NP, k)];
       if (!(d > 0.0)) {
         report(st, 4 /* ALS_ENOTSPD */, v);
@@ -239,16 +279,16 @@ __global__ void k_patch_setup(Geom g, double gamma, const double* __restrict__ c
     }
     __syncthreads();
     const double dinv = s_dinv;
-    for (int i = warp; i < NP; i += nwarps) {
-      if (i == k) continue;
-      const double pi = pk[i] * dinv;
-      double* row = M + tri_row(NP, i) - i;
-      for (int j = i + lane; j < NP; j += 32)
-        if (j != k) row[j] -= pi * pk[j];
+    for (int i = tid; i < NP; i += nt) qk[i] = pk[i] * dinv;
+    __syncthreads();
+    for (int e = tid; e < C::NPK; e += nt) {
+      const int i = rowof[e];
+      const int j = e - tri_row(NP, i) + i;
+      if (i != k && j != k) M[e] -= qk[i] * pk[j];
     }
     for (int i = tid; i < NP; i += nt) {
       if (i == k) M[tri_row(NP, k)] = -dinv;
-      else M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)] = pk[i] * dinv;
+      else M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)] = qk[i];
     }
     __syncthreads();
   }

@@ -538,8 +538,16 @@ static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevSt
   using C = SetupCfg<DIM, TENSOR>;
   const size_t smem = C::smem;
   cudaFuncSetAttribute(k_patch_setup<DIM, TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  SetupGeo sg{};
+  sg.wdet = 1.0;
+  sg.vol = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    sg.s[k] = k < DIM ? 2.0 / L.g.h[k] : 0.0;
+    if (k < DIM) { sg.wdet *= 0.5 * L.g.h[k]; sg.vol *= L.g.h[k]; }
+  }
+  sg.gvol = gamma / sg.vol;
   k_patch_setup<DIM, TENSOR><<<(unsigned)L.g.nverts, C::THREADS, smem, s>>>(
-      L.g, gamma, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st, L.winv64);
+      L.g, gamma, sg, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st, L.winv64);
   count_launch(1);
 }
 
