@@ -87,7 +87,7 @@ struct als_ctx {
   double gamma = 0.0;
   als_options opt{};
   std::vector<LevelDev> lev;
-  CoarseDev coarse{0, nullptr};
+  CoarseDev coarse{};
   DevStatus* st = nullptr;
   double* schur = nullptr;
   MGWork w64, w32;

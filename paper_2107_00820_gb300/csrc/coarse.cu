@@ -1,11 +1,14 @@
 // K7: coarse-grid solve (Sec. 6.1 uses a sparse direct solver on the coarsest
-// level; here the coarsest A_gamma is small and dense-factored on the GPU).
+// level; here the coarsest A_gamma is small and dense-inverted on the GPU).
 //
 // Setup: the free-dof block of the coarsest A_gamma is formed column by column
-// by applying the matrix-free operator to unit vectors, factored by a
-// right-looking FP64 Cholesky (one column per step), and its inverse
-// L^-T L^-1 is formed by one triangular solve pair per column.  Each V-cycle
-// then applies the stored FP64 inverse as a dense matrix-vector product.
+// by applying the matrix-free operator to unit vectors and inverted in FP64 by a
+// blocked symmetric sweep (the operator of the patch setup, applied to 64-wide
+// pivot blocks): per block K, S = A_KK^-1 by a one-CTA sweep of the diagonal
+// block, U = A_{:K} S, A_RR -= A_{RK} U_R^T on the upper triangle of tiles, and
+// the pivot row/column set to U (A_KK to -S).  After every block the matrix holds
+// -A^-1.  A is SPD, so every pivot is a Schur complement and positive.  Each
+// V-cycle then applies the stored inverse as a dense matrix-vector product.
 #include "krylov.h"
 #include "level.h"
 
@@ -35,56 +38,148 @@ __global__ void k_unit_columns(Geom g, int nfree, long long len, double* __restr
   X[t] = (dof == free_dof(g, col)) ? 1.0 : 0.0;
 }
 
-__global__ void k_extract(Geom g, int nfree, long long len, const double* __restrict__ Y, double* __restrict__ A) {
+constexpr int CT = 64;   // tile width of the blocked sweep
+
+// column `col` of A is A e_col; stored row-major in the padded matrix (npad columns)
+__global__ void k_extract(Geom g, int nfree, int npad, long long len, const double* __restrict__ Y,
+                          double* __restrict__ A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nfree * nfree) return;
   const int col = (int)(t / nfree), row = (int)(t % nfree);
-  // column `col` of A is A e_col; stored row-major A[row][col]
-  A[(long long)row * nfree + col] = Y[(long long)col * len + free_dof(g, row)];
+  A[(long long)row * npad + col] = Y[(long long)col * len + free_dof(g, row)];
 }
 
-__global__ void k_chol_col(int n, int k, double* __restrict__ A, DevStatus* st) {
-  __shared__ double piv;
-  if (threadIdx.x == 0) {
-    double d = A[(long long)k * n + k];
-    if (!(d > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, -1 - (long long)k); d = 1.0; }
-    piv = sqrt(d);
-    A[(long long)k * n + k] = piv;
+// identity on the padding rows/columns (their blocks stay decoupled)
+__global__ void k_pad_diag(int nfree, int npad, double* __restrict__ A) {
+  const int i = nfree + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) A[(long long)i * npad + i] = 1.0;
+}
+
+// P[r][c] = A(r, p*CT + c) from the upper triangle of tiles
+__global__ void k_panel_gather(int npad, int p, const double* __restrict__ A, double* __restrict__ P) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * CT) return;
+  const int r = (int)(t / CT), c = (int)(t % CT), k = p * CT + c;
+  const bool upper = r <= k;
+  P[t] = upper ? A[(long long)r * npad + k] : A[(long long)k * npad + r];
+}
+
+// S = D^-1 for the diagonal block D = P[p*CT .. p*CT+CT) by the symmetric sweep
+// in shared memory (one CTA); a non-positive pivot is reported as ALS_ENOTSPD
+__global__ void __launch_bounds__(256) k_diag_sweep(int p, const double* __restrict__ P, double* __restrict__ S,
+                                                    DevStatus* st) {
+  __shared__ double D[CT][CT + 1];
+  __shared__ double col[CT], q[CT];
+  __shared__ double dinv;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < CT * CT; e += blockDim.x) D[e / CT][e % CT] = P[(long long)(p * CT + e / CT) * CT + e % CT];
+  __syncthreads();
+  for (int kk = 0; kk < CT; ++kk) {
+    if (tid < CT) col[tid] = tid == kk ? 0.0 : D[tid][kk];
+    if (tid == 0) {
+      double d = D[kk][kk];
+      if (!(d > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, -1 - (long long)(p * CT + kk)); d = 1.0; }
+      dinv = 1.0 / d;
+    }
+    __syncthreads();
+    if (tid < CT) q[tid] = col[tid] * dinv;
+    __syncthreads();
+    for (int e = tid; e < CT * CT; e += blockDim.x) {
+      const int i = e / CT, j = e % CT;
+      if (i != kk && j != kk) D[i][j] -= q[i] * col[j];
+      else if (i == kk && j == kk) D[i][j] = -dinv;
+      else D[i][j] = q[i == kk ? j : i];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < CT * CT; e += blockDim.x) S[e] = -D[e / CT][e % CT];
+}
+
+// 64x64 output tile out = X_tile * Y (Y 64x64 row-major) or X_tile * Y_tile^T, 4x4 per thread
+__device__ __forceinline__ void tile_mma(const double (*Xs)[CT + 1], const double (*Ys)[CT + 1], bool yt,
+                                         double (&acc)[4][4], int r0, int c0) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k = 0; k < CT; ++k) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Xs[r0 + 16 * i][k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = yt ? Ys[c0 + 16 * j][k] : Ys[k][c0 + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+}
+
+// U[rows of tile blockIdx.x] = P[those rows] S
+__global__ void __launch_bounds__(256) k_panel_mul(const double* __restrict__ P, const double* __restrict__ S,
+                                                   double* __restrict__ U) {
+  extern __shared__ double smc[];
+  double (*Ps)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc);
+  double (*Ss)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc + CT * (CT + 1));
+  const int tid = threadIdx.x;
+  const long long r0 = (long long)blockIdx.x * CT;
+  for (int e = tid; e < CT * CT; e += blockDim.x) {
+    Ps[e / CT][e % CT] = P[(r0 + e / CT) * CT + e % CT];
+    Ss[e / CT][e % CT] = S[e];
   }
   __syncthreads();
-  for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + k] /= piv;
+  double acc[4][4];
+  const int tr = tid / 16, tc = tid % 16;
+  tile_mma(Ps, Ss, false, acc, tr, tc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) U[(r0 + tr + 16 * i) * CT + tc + 16 * j] = acc[i][j];
 }
 
-__global__ void k_chol_update(int n, int k, double* __restrict__ A) {
-  const int i = k + 1 + blockIdx.x;
-  if (i >= n) return;
-  const double lik = A[(long long)i * n + k];
-  for (int j = k + 1 + threadIdx.x; j <= i; j += blockDim.x) A[(long long)i * n + j] -= lik * A[(long long)j * n + k];
+// A[I][J] -= P[I] U[J]^T for the upper tiles I <= J outside the pivot row/column p
+__global__ void __launch_bounds__(256) k_sym_update(int npad, int nt, int p, const double* __restrict__ P,
+                                                    const double* __restrict__ U, double* __restrict__ A) {
+  int b = blockIdx.x, I = 0;
+  while (b >= nt - I) { b -= nt - I; ++I; }
+  const int J = I + b;
+  if (I == p || J == p) return;
+  extern __shared__ double smc[];
+  double (*Ps)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc);
+  double (*Us)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc + CT * (CT + 1));
+  const int tid = threadIdx.x;
+  for (int e = tid; e < CT * CT; e += blockDim.x) {
+    Ps[e / CT][e % CT] = P[((long long)I * CT + e / CT) * CT + e % CT];
+    Us[e / CT][e % CT] = U[((long long)J * CT + e / CT) * CT + e % CT];
+  }
+  __syncthreads();
+  double acc[4][4];
+  const int tr = tid / 16, tc = tid % 16;
+  tile_mma(Ps, Us, true, acc, tr, tc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      A[((long long)I * CT + tr + 16 * i) * npad + (long long)J * CT + tc + 16 * j] -= acc[i][j];
 }
 
-// column j of (L L^T)^-1: forward then backward substitution, one warp per column
-__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __restrict__ X) {
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= n) return;
-  // X stored row-major; column j written as X[i*n + j]
-  for (int i = 0; i < j; ++i)
-    if (lane == 0) X[(long long)i * n + j] = 0.0;
-  __syncwarp();
-  for (int i = j; i < n; ++i) {
-    double acc = 0.0;
-    for (int k = j + lane; k < i; k += 32) acc += L[(long long)i * n + k] * X[(long long)k * n + j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) X[(long long)i * n + j] = ((i == j ? 1.0 : 0.0) - acc) / L[(long long)i * n + i];
-    __syncwarp();
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    double acc = 0.0;
-    for (int k = i + 1 + lane; k < n; k += 32) acc += L[(long long)k * n + i] * X[(long long)k * n + j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) X[(long long)i * n + j] = (X[(long long)i * n + j] - acc) / L[(long long)i * n + i];
-    __syncwarp();
-  }
+// pivot row/column p of the upper triangle: A(r, K) = U(r) for r outside K, A_KK = -S
+__global__ void k_panel_write(int npad, int p, const double* __restrict__ U, const double* __restrict__ S,
+                              double* __restrict__ A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * CT) return;
+  const int r = (int)(t / CT), c = (int)(t % CT), k = p * CT + c, I = r / CT;
+  if (I < p) A[(long long)r * npad + k] = U[t];
+  else if (I > p) A[(long long)k * npad + r] = U[t];
+  else A[(long long)r * npad + k] = -S[(r - p * CT) * CT + c];
+}
+
+// inv = -(swept matrix) on the free block, both triangles
+__global__ void k_finalize(int nfree, int npad, const double* __restrict__ A, double* __restrict__ inv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nfree * nfree) return;
+  const int r = (int)(t / nfree), c = (int)(t % nfree);
+  inv[t] = -(r <= c ? A[(long long)r * npad + c] : A[(long long)c * npad + r]);
 }
 
 int coarse_alloc(const LevelDev& L, CoarseDev* C) {
@@ -94,8 +189,13 @@ int coarse_alloc(const LevelDev& L, CoarseDev* C) {
   C->nfree = nfree;
   if (cudaMalloc(&C->X, sizeof(double) * nfree * len) != cudaSuccess) return 2;
   if (cudaMalloc(&C->Y, sizeof(double) * nfree * len) != cudaSuccess) return 2;
-  if (cudaMalloc(&C->A, sizeof(double) * nfree * nfree) != cudaSuccess) return 2;
+  const int npad = (nfree + CT - 1) / CT * CT;
+  C->npad = npad;
+  if (cudaMalloc(&C->A, sizeof(double) * npad * npad) != cudaSuccess) return 2;
   if (cudaMalloc(&C->inv, sizeof(double) * nfree * nfree) != cudaSuccess) return 2;
+  if (cudaMalloc(&C->P, sizeof(double) * npad * CT) != cudaSuccess) return 2;
+  if (cudaMalloc(&C->U, sizeof(double) * npad * CT) != cudaSuccess) return 2;
+  if (cudaMalloc(&C->S, sizeof(double) * CT * CT) != cudaSuccess) return 2;
   return 0;
 }
 
@@ -109,13 +209,23 @@ void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, 
   k_unit_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nfree, len, X);
   op_apply_multi(L, gamma, X, Y, nfree, len, s);
   const long long tot2 = (long long)nfree * nfree;
-  k_extract<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(g, nfree, len, Y, A);
-  for (int k = 0; k < nfree; ++k) {
-    k_chol_col<<<1, 256, 0, s>>>(nfree, k, A, st);
-    if (k + 1 < nfree) k_chol_update<<<nfree - k - 1, 128, 0, s>>>(nfree, k, A);
+  const int npad = C->npad, nt = npad / CT;
+  cudaMemsetAsync(A, 0, sizeof(double) * npad * npad, s);
+  if (npad > nfree) k_pad_diag<<<(npad - nfree + 127) / 128, 128, 0, s>>>(nfree, npad, A);
+  k_extract<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(g, nfree, npad, len, Y, A);
+  const size_t smem2 = sizeof(double) * 2 * CT * (CT + 1);
+  cudaFuncSetAttribute(k_panel_mul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  cudaFuncSetAttribute(k_sym_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  const unsigned pblocks = (unsigned)(((long long)npad * CT + 255) / 256);
+  for (int p = 0; p < nt; ++p) {
+    k_panel_gather<<<pblocks, 256, 0, s>>>(npad, p, A, C->P);
+    k_diag_sweep<<<1, 256, 0, s>>>(p, C->P, C->S, st);
+    k_panel_mul<<<nt, 256, smem2, s>>>(C->P, C->S, C->U);
+    k_sym_update<<<nt * (nt + 1) / 2, 256, smem2, s>>>(npad, nt, p, C->P, C->U, A);
+    k_panel_write<<<pblocks, 256, 0, s>>>(npad, p, C->U, C->S, A);
   }
-  k_chol_inverse<<<(nfree + 3) / 4, 128, 0, s>>>(nfree, A, C->inv);
-  count_launch(3 + 2 * nfree);
+  k_finalize<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(nfree, npad, A, C->inv);
+  count_launch(3 + (npad > nfree ? 1 : 0) + 5LL * nt);
 }
 
 template <typename TV>
@@ -140,7 +250,7 @@ void coarse_apply(const LevelDev& L, const CoarseDev& C, int prec, const void* b
 }
 
 void coarse_free(CoarseDev* C) {
-  for (double** p : {&C->inv, &C->X, &C->Y, &C->A}) {
+  for (double** p : {&C->inv, &C->X, &C->Y, &C->A, &C->P, &C->U, &C->S}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }

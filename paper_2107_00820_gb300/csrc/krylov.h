@@ -19,10 +19,14 @@ void project_constant(long long ncells, int npr, double* p, double* partial, cud
 // coarse.cu
 struct CoarseDev {
   int nfree = 0;
+  int npad = 0;            // nfree rounded up to the 64-wide tiles of the blocked sweep
   double* inv = nullptr;   // nfree x nfree, row-major, FP64 inverse of the coarse free-dof block
   double* X = nullptr;     // setup scratch: unit columns, their images, the dense matrix
   double* Y = nullptr;
-  double* A = nullptr;
+  double* A = nullptr;     // npad x npad, swept in place (upper triangle)
+  double* P = nullptr;     // npad x 64: the current pivot-column panel
+  double* U = nullptr;     // npad x 64: the panel times the inverse of its diagonal block
+  double* S = nullptr;     // 64 x 64: that inverse
 };
 int coarse_alloc(const struct LevelDev& L, CoarseDev* C);
 void coarse_setup(const struct LevelDev& L, double gamma, CoarseDev* C, struct DevStatus* st, cudaStream_t s);
