@@ -1,0 +1,81 @@
+"""Edge and degenerate cases of the GPU path against the oracle: a single level
+(the cycle is the coarse solve), a zero right-hand side, meshes with different
+cell counts per axis, gamma = 0 (no augmentation), and the size limits."""
+import numpy as np
+import pytest
+
+from gpu_helpers import context, dev, host, oracle, random_free, rel, sinker
+
+torch = pytest.importorskip("torch")
+from paper_2107_00820_gb300 import alstokes as A  # noqa: E402
+from oracle.stokes import StokesSolver  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _coarse_cond(H):
+    lv0 = H.levels[0]
+    f = np.flatnonzero(lv0.free)
+    return np.linalg.cond(lv0.A.toarray()[np.ix_(f, f)])
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 4)])
+def test_single_level(d, n):
+    """levels = 1: no smoothing; the cycle is the dense coarse solve, and FGMRES with
+    it matches the oracle's iteration count."""
+    pb = sinker(d, n, 1, 1e2, dr=1e4, seed=51)
+    ctx = context(pb, rtol=1e-8)
+    H = oracle(pb)
+    b = random_free(H.levels[-1], 52)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.vcycle(b)) <= max(1e-12, 100 * _coarse_cond(H) * 2.2e-16)
+    uo, po, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
+
+
+def test_zero_right_hand_side():
+    """f = 0 and zero boundary data: no iteration, u = 0 and p = 0 exactly."""
+    pb = sinker(2, 16, 3, 1e2, dr=1e4, seed=53)
+    ctx = context(pb)
+    u, p, info = ctx.solve(np.zeros_like(pb.f), np.zeros_like(pb.u_bc))
+    assert info.converged == 1 and info.iterations == 0
+    assert not np.any(u) and not np.any(p)
+
+
+@pytest.mark.parametrize("d,n,levels", [(2, (16, 8), 3), (3, (8, 4, 4), 2)])
+def test_anisotropic_mesh(d, n, levels):
+    """Different cell counts per axis: cycle parity and an identical solve."""
+    pb = sinker(d, n, levels, 1e2, dr=1e4, seed=54)
+    ctx = context(pb, sweeps=2, rtol=1e-8)
+    H = oracle(pb, steps=2)
+    b = random_free(H.levels[-1], 55)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.vcycle(b)) <= 1e-11
+    uo, po, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
+
+
+def test_gamma_zero():
+    """gamma = 0: the plain Stokes system with the same block preconditioner."""
+    pb = sinker(2, 16, 3, 0.0, dr=1e2, seed=56)
+    ctx = context(pb, rtol=1e-8, maxit=300)
+    uo, po, its, _ = StokesSolver(oracle(pb)).solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8
+
+
+def test_size_limits_rejected():
+    """Meshes whose velocity vector or per-cell staging buffer would need more than
+    32-bit indices are refused with ALS_EINVAL before anything is allocated."""
+    from paper_2107_00820_gb300 import ALSError, Context
+    dummy = [np.zeros(1), np.zeros(1)]
+    with pytest.raises(ALSError) as e:
+        Context(3, 1024, 2, dummy, 1.0)          # 3 * 2049^3 velocity values > 2^31
+    assert e.value.status == A.ALS_EINVAL
