@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int k = 0; k < 3; ++k) grad[a][k] = T(0);
+  pdl_wait();
 
   if constexpr (NEED_U) {
     // stage X: lane (c, ay = b1, az = b2) loads the x-line of component c
@@ -330,4 +331,5 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
       }
     }
   }  // NEED_FLUX
+  pdl_trigger();
 }

@@ -11,6 +11,7 @@
 // V-cycle then applies the stored inverse as a dense matrix-vector product.
 #include "krylov.h"
 #include "level.h"
+#include "pdl.cuh"
 
 namespace als {
 
@@ -231,6 +232,7 @@ void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, 
 template <typename TV>
 __global__ void k_coarse_apply(Geom g, int nfree, const double* __restrict__ inv, const TV* __restrict__ b,
                                TV* __restrict__ x) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= nfree) return;
@@ -244,8 +246,8 @@ void coarse_apply(const LevelDev& L, const CoarseDev& C, int prec, const void* b
   const long long len = L.g.N * L.g.dim;
   cudaMemsetAsync(x, 0, len * (prec == PREC_F64 ? 8 : 4), s);
   const unsigned blocks = (unsigned)((C.nfree + 7) / 8);
-  if (prec == PREC_F64) k_coarse_apply<double><<<blocks, 256, 0, s>>>(L.g, C.nfree, C.inv, (const double*)b, (double*)x);
-  else k_coarse_apply<float><<<blocks, 256, 0, s>>>(L.g, C.nfree, C.inv, (const float*)b, (float*)x);
+  if (prec == PREC_F64) launch_pdl(k_coarse_apply<double>, blocks, 256, 0, s, L.g, C.nfree, C.inv, (const double*)b, (double*)x);
+  else launch_pdl(k_coarse_apply<float>, blocks, 256, 0, s, L.g, C.nfree, C.inv, (const float*)b, (float*)x);
   count_launch(1);
 }
 

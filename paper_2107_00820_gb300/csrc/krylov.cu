@@ -11,6 +11,7 @@
 #include "krylov.h"
 #include "level.h"
 #include "reduce.cuh"
+#include "pdl.cuh"
 
 namespace als {
 
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* _
                                                           double* __restrict__ partial, GmresDev st) {
   __shared__ double nrm2_s[1];
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  pdl_wait();
   T v[GM_PER];
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* _
     if (i < n) V0[i] = v[q];
     acc[0] += v[q] * v[q];
   }
+  pdl_trigger();
   block_partials(acc, 1, partial + 1 + blockIdx.x);
   if (last_block(partial)) {
     finish_sums(partial, 1, nrm2_s);
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
                                                          double* __restrict__ partial, GmresDev st) {
   __shared__ T coef[KMAXB];
   __shared__ double nrm2_s[1];
+  pdl_wait();
   const double* hcol = st.H + (long long)j * st.ldh;
   if ((int)threadIdx.x <= j)
     coef[threadIdx.x] = (T)(st.hn[threadIdx.x] != 0.0 ? hcol[threadIdx.x] / st.hn[threadIdx.x] : 0.0);
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
     if (i < n) w[i] = a[q];
     acc[0] += a[q] * a[q];
   }
+  pdl_trigger();
   block_partials(acc, 1, partial + 1 + blockIdx.x);
   if (last_block(partial)) {
     finish_sums(partial, 1, nrm2_s);
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, co
                                                            const T* __restrict__ V, long long ld, GmresDev st,
                                                            T* __restrict__ x, int x_zero, T* __restrict__ t) {
   __shared__ T y[KMAXB], u[KMAXB + 1];
+  pdl_wait();
   if (threadIdx.x == 0) {
     double Hs[KMAXB][KMAXB], gs[KMAXB + 1], cs[KMAXB], sn[KMAXB], hn[KMAXB + 1];
     for (int c = 0; c < k; ++c) {
@@ -340,28 +346,28 @@ static unsigned full_grid(long long n) {
 
 void gm_start(int prec, long long n, const void* b, void* V0, double* partial, const GmresDev& st, cudaStream_t s) {
   if (prec == PREC_F64)
-    k_gm_start<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, (const double*)b, (double*)V0, partial, st);
+    launch_pdl(k_gm_start<double>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, (const double*)b, (double*)V0, partial, st);
   else
-    k_gm_start<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, (const float*)b, (float*)V0, partial, st);
+    launch_pdl(k_gm_start<float>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, (const float*)b, (float*)V0, partial, st);
   count_launch(1);
 }
 
 void gm_orth(int prec, long long n, int j, const void* V, long long ld, double* partial, const GmresDev& st,
              cudaStream_t s) {
   if (prec == PREC_F64)
-    k_gm_orth<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, j, (const double*)V, ld, partial, st);
+    launch_pdl(k_gm_orth<double>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, j, (const double*)V, ld, partial, st);
   else
-    k_gm_orth<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, j, (const float*)V, ld, partial, st);
+    launch_pdl(k_gm_orth<float>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, j, (const float*)V, ld, partial, st);
   count_launch(1);
 }
 
 void gm_update(int prec, long long n, int k, const void* Z, const void* V, long long ld, const GmresDev& st,
                void* x, int x_zero, void* t, cudaStream_t s) {
   if (prec == PREC_F64)
-    k_gm_update<double><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, k, (const double*)Z, (const double*)V, ld,
+    launch_pdl(k_gm_update<double>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, k, (const double*)Z, (const double*)V, ld,
                                                                st, (double*)x, x_zero, (double*)t);
   else
-    k_gm_update<float><<<full_grid(n), RED_THREADS, 0, s>>>((unsigned)n, k, (const float*)Z, (const float*)V, ld,
+    launch_pdl(k_gm_update<float>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, k, (const float*)Z, (const float*)V, ld,
                                                               st, (float*)x, x_zero, (float*)t);
   count_launch(1);
 }

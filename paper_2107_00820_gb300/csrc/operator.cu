@@ -13,6 +13,7 @@
 #include "cell.cuh"
 #include "level.h"
 #include "reduce.cuh"
+#include "pdl.cuh"
 
 #include <type_traits>
 
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
     for (int k = 0; k < DIM; ++k) grad[c][k] = T(0);
+  pdl_wait();
 
   if constexpr (NEED_U) {
     // stage 1: nodal values (Dirichlet columns masked unless RAW)
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
     }
   }
   }  // NEED_FLUX
+  pdl_trigger();
 }
 
 // y_D = x_D (identity rows) when keep_bnd, else 0; interior rows zeroed.
@@ -494,6 +497,7 @@ __device__ __forceinline__ void gather_chunk(const Geom& g, const T* __restrict_
 template <typename T, int DIM>
 __global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
                                int keep_bnd, int raw) {
+  pdl_wait();
   RowChunk rc;
   if (!row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) return;
   T out[GX];
@@ -523,6 +527,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
   T acc[KMAXB];
 #pragma unroll
   for (int j = 0; j < KMAXB; ++j) acc[j] = T(0);
+  pdl_wait();
   RowChunk rc;
   if (row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) {
     T ax[GX];
@@ -542,6 +547,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
       }
     }
   }
+  pdl_trigger();
   block_partials(acc, kk, partial + 1 + (long long)blockIdx.x * kk);
   if (last_block(partial)) {
     if (start) {
@@ -561,11 +567,11 @@ static void launch_cells(dim3 grid, cudaStream_t s, const Geom& g, const Colour&
                          const T* x, T* y, const T* coef, const T* p_in, T* p_out, long long vstride, T* ebuf,
                          const T* winv) {
   if constexpr (DIM == 3)
-    k_apply_lines<T, TENSOR, MODE, STAGED><<<grid, 256, 0, s>>>(g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf,
-                                                                winv);
+    launch_pdl(k_apply_lines<T, TENSOR, MODE, STAGED>, grid, 256, 0, s, g, col, cc, x, y, coef, p_in, p_out, vstride,
+               ebuf, winv);
   else
-    k_apply<T, DIM, TENSOR, MODE, STAGED><<<grid, 256, 0, s>>>(g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf,
-                                                               winv);
+    launch_pdl(k_apply<T, DIM, TENSOR, MODE, STAGED>, grid, 256, 0, s, g, col, cc, x, y, coef, p_in, p_out, vstride,
+               ebuf, winv);
 }
 
 template <typename T, int DIM, bool TENSOR, int MODE>
@@ -586,8 +592,8 @@ static void launch_apply(const LevelDev& L, double gamma, const void* x, void* y
                                              cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, (const T*)p_in,
                                              (T*)p_out, 0, (T*)L.ebuf, winv);
     if (NEED_FLUX) {
-      k_gather_cells<T, DIM><<<(gather_threads(g) + 255) / 256, 256, 0, s>>>(g, (const T*)L.ebuf, (const T*)x,
-                                                                          (T*)y, keep_bnd, (MODE & OP_RAW) ? 1 : 0);
+      launch_pdl(k_gather_cells<T, DIM>, (gather_threads(g) + 255) / 256, 256, 0, s, g, (const T*)L.ebuf,
+                 (const T*)x, (T*)y, keep_bnd, (MODE & OP_RAW) ? 1 : 0);
     }
     count_launch(NEED_FLUX ? 2 : 1);
     return;
@@ -681,9 +687,9 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
                                                        cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr,
                                                        nullptr, 0, (T*)L.ebuf, winv);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  k_gather_epi<T, DIM><<<(gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(
-      g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
-      e.st, e.partial);
+  launch_pdl(k_gather_epi<T, DIM>, (gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s, g,
+             (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
+             e.st, e.partial);
   count_launch(2);
 }
 

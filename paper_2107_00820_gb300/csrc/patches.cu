@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "level.h"
+#include "pdl.cuh"
 
 namespace als {
 
@@ -303,6 +304,9 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       const int grp = blockIdx.x + i * gridDim.x;
       if (grp < ngroups) issue(grp, i);
     }
+  // the first inverse blocks (written only by the setup) are in flight; r comes from
+  // the preceding kernel of the cycle
+  pdl_wait();
   float rpre[RPT];
   gather(blockIdx.x, rpre);
 
@@ -374,6 +378,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // no third barrier: r and the partials are double-buffered, and iteration it+2
     // rewrites these buffers only after every thread has passed barrier (A) of it+1
   }
+  pdl_trigger();
   if (s_fail && tid == ISSUER) {
     // drain: wait (bounded) for every copy this CTA issued and did not consume
     int k = it;
@@ -426,6 +431,7 @@ __global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __res
   int I = 0, J = 0;
   bool diag = false;
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
+  pdl_wait();
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
     if (b < BL.nbp) {
       int vx, vy, vz;
@@ -473,7 +479,7 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
   const long long cap = 152LL * 8;
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  k_patch_direct<DIM><<<(unsigned)grid, C::THREADS, 0, s>>>(L.g, L.inv32, interior, (int)count, r, out, mode);
+  launch_pdl(k_patch_direct<DIM>, (unsigned)grid, C::THREADS, 0, s, L.g, L.inv32, interior, (int)count, r, out, mode);
   count_launch(1);
 }
 
@@ -508,8 +514,8 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
   const long long cap = 152 * (per_sm < 1 ? 1 : per_sm);
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  k_patch_tma<DIM, NST><<<(unsigned)grid, C::THREADS, C::smem_bytes, s>>>(L.g, L.inv32, interior, (int)count, r, out,
-                                                                          mode, st);
+  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
+             (int)count, r, out, mode, st);
   count_launch(1);
 }
 
@@ -592,6 +598,7 @@ __global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restric
   __shared__ TV rsh[8][NP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  pdl_wait();
   for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + w; v < g.nverts; v += nwarps) {
     int vx, vy, vz;
     vertex_coords<DIM>(g, v, vx, vy, vz);
@@ -621,6 +628,7 @@ template <typename TV, int DIM>
 __global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
                                const double* __restrict__ den) {
   __shared__ TV inv_den;
+  pdl_wait();
   if (den) {                        // one division per block, not per entry
     if (threadIdx.x == 0) inv_den = den[0] != 0.0 ? (TV)(1.0 / den[0]) : TV(0);
     __syncthreads();
@@ -692,9 +700,9 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
   const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
   // External records become event-record nodes when the stream is being captured
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  k_patch_apply<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
+  launch_pdl(k_patch_apply<TF, TV, DIM>, blocks, 256, 0, s, L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  k_patch_gather<TV, DIM><<<row_gather_blocks(L.g, DIM), 256, 0, s>>>(L.g, (const TV*)scratch, (TV*)z, den);
+  launch_pdl(k_patch_gather<TV, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const TV*)scratch, (TV*)z, den);
   count_launch(2);
 }
 
@@ -705,8 +713,8 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
   launch_patch_variant<DIM>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
                             L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  k_patch_gather<float, DIM><<<row_gather_blocks(L.g, DIM), 256, 0, s>>>(L.g, (const float*)scratch, (float*)z,
-                                                                         den);
+  launch_pdl(k_patch_gather<float, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const float*)scratch,
+             (float*)z, den);
   count_launch(1);
 }
 
@@ -735,6 +743,7 @@ __global__ void __launch_bounds__(256) k_interior_solve(Geom g, const TF* __rest
   const int ncx = g.n[0] / 2, ncy = g.n[1] / 2, ncz = DIM == 3 ? g.n[2] / 2 : 1;
   const long long ncoarse = (long long)ncx * ncy * ncz;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  pdl_wait();
   for (long long K = (long long)blockIdx.x * (blockDim.x >> 5) + w; K < ncoarse; K += nwarps) {
     const int kx = (int)(K % ncx), ky = (int)((K / ncx) % ncy), kz = DIM == 3 ? (int)(K / ((long long)ncx * ncy)) : 0;
     const int vx = 2 * kx + 1, vy = 2 * ky + 1, vz = DIM == 3 ? 2 * kz + 1 : 0;
@@ -766,7 +775,7 @@ static void interior_impl(const LevelDev& L, const TF* inv, const void* in, void
   long long nc = (long long)(L.g.n[0] / 2) * (L.g.n[1] / 2) * (DIM == 3 ? L.g.n[2] / 2 : 1);
   if (!subtract) cudaMemsetAsync(out, 0, sizeof(TV) * L.g.N * DIM, s);
   const unsigned blocks = (unsigned)std::min<long long>((nc + 7) / 8, 152LL * 16);
-  k_interior_solve<TF, TV, DIM><<<blocks, 256, 0, s>>>(L.g, inv, L.pstride, (const TV*)in, (TV*)out, subtract);
+  launch_pdl(k_interior_solve<TF, TV, DIM>, blocks, 256, 0, s, L.g, inv, L.pstride, (const TV*)in, (TV*)out, subtract);
   count_launch(1);
 }
 

@@ -7,6 +7,7 @@
 // boundary) and columns (coarse boundary) are zero.  Both directions are
 // gathers (one thread per output value), so they need no atomics.
 #include "level.h"
+#include "pdl.cuh"
 
 namespace als {
 
@@ -56,6 +57,7 @@ __device__ __forceinline__ void decode(const Geom& g, unsigned t, int dim, int& 
 // exact in either precision; the sums run in the vector's precision T.
 template <typename T, int DIM>
 __global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+  pdl_wait();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)(gf.N * DIM)) return;
   int c, i, j, k;
@@ -88,6 +90,7 @@ __global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restr
 
 template <typename T, int DIM>
 __global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub, T* __restrict__ rc) {
+  pdl_wait();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)(gc.N * DIM)) return;
   int c, i, j, k;
@@ -130,12 +133,12 @@ void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const v
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {
     if (fine.g.dim == 2)
-      k_prolong<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
-    else k_prolong<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
+      launch_pdl(k_prolong<double, 2>, b, 256, 0, s, coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
+    else launch_pdl(k_prolong<double, 3>, b, 256, 0, s, coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
   } else {
     if (fine.g.dim == 2)
-      k_prolong<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
-    else k_prolong<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+      launch_pdl(k_prolong<float, 2>, b, 256, 0, s, coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+    else launch_pdl(k_prolong<float, 3>, b, 256, 0, s, coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
   }
   count_launch(1);
 }
@@ -146,12 +149,12 @@ void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const 
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {
     if (fine.g.dim == 2)
-      k_restrict<double, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
-    else k_restrict<double, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
+      launch_pdl(k_restrict<double, 2>, b, 256, 0, s, coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
+    else launch_pdl(k_restrict<double, 3>, b, 256, 0, s, coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
   } else {
     if (fine.g.dim == 2)
-      k_restrict<float, 2><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
-    else k_restrict<float, 3><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
+      launch_pdl(k_restrict<float, 2>, b, 256, 0, s, coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
+    else launch_pdl(k_restrict<float, 3>, b, 256, 0, s, coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
   }
   count_launch(1);
 }
