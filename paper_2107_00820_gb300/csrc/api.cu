@@ -98,6 +98,7 @@ struct als_ctx {
   double *res = nullptr, *beta = nullptr, *h2 = nullptr, *nrm2 = nullptr, *partial = nullptr;
   double *f_dev = nullptr, *ubc_dev = nullptr, *r2_dev = nullptr, *uD = nullptr, *tu = nullptr, *tu2 = nullptr;
   double *tp = nullptr, *tp2 = nullptr, *xsol = nullptr;
+  float* tp32 = nullptr;       // pressure-space vector of the FP32 B and B^T applies (mixed mode)
   double* host_res = nullptr;  // pinned
   std::vector<void*> allocs;
   std::string err;
@@ -519,6 +520,7 @@ als_status alloc_solve(als_ctx* c, int maxit) {
   ALS_TRY(dalloc(c, &c->tu2, c->nu));
   ALS_TRY(dalloc(c, &c->tp, c->np));
   ALS_TRY(dalloc(c, &c->tp2, c->np));
+  ALS_TRY(dalloc(c, &c->tp32, c->np));
   ALS_TRY(dalloc(c, &c->xsol, c->n));
   if (!c->host_res && cudaMallocHost(&c->host_res, 2 * sizeof(double)) != cudaSuccess)
     return fail(c, ALS_ENOMEM, "pinned host allocation failed");
@@ -562,6 +564,27 @@ als_status precondition(als_ctx* c, const double* v, double* z) {
         schur_apply(F.g.ncells, c->dim + 1, c->schur, gp, z2, s);                      // z2 = -S^-1 g
       }
     }
+    project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+    return ALS_OK;
+  }
+  if (c->opt.mode == ALS_MODE_MIXED) {
+    // The off-diagonal blocks run in the precision of the cycle: B reads the FP32
+    // cycle output directly and B^T writes the right-hand side of the second cycle,
+    // while g - B z1, the Schur blocks and the final combination stay in FP64.
+    MGWork& w = work_for(c, PREC_F32);
+    const int l = c->L - 1;
+    vec_cast(c->nu, f, PREC_F64, w.b[l], PREC_F32, s);
+    ALS_TRY(run_vcycle(c, w));                                                       // z1 = A^-1 f (FP32)
+    vec_cast(c->nu, w.x[l], PREC_F32, c->tu, PREC_F64, s);
+    op_apply(F, PREC_F32, OP_B, c->gamma, w.x[l], nullptr, nullptr, c->tp32, s);     // B z1 (FP32)
+    vec_cast(c->np, c->tp32, PREC_F32, c->tp, PREC_F64, s);
+    vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                             // tp = g - B z1
+    schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                     // z2 = -S^-1 tp
+    vec_cast(c->np, z2, PREC_F64, c->tp32, PREC_F32, s);
+    op_apply(F, PREC_F32, OP_BT, c->gamma, nullptr, w.b[l], c->tp32, nullptr, s);    // B^T z2 (FP32)
+    ALS_TRY(run_vcycle(c, w));                                                       // A^-1 B^T z2 (FP32)
+    vec_cast(c->nu, w.x[l], PREC_F32, x1, PREC_F64, s);
+    vec_axpby(PREC_F64, c->nu, 1.0, c->tu, -1.0, x1, s);                             // x1 = z1 - x1
     project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
     return ALS_OK;
   }

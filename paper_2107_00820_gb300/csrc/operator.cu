@@ -625,14 +625,14 @@ static void dispatch_mode(const LevelDev& L, int mode, double gamma, const void*
     case OP_VISC | OP_AL:
       launch_apply<T, DIM, TENSOR, OP_VISC | OP_AL>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
     case OP_AL: launch_apply<T, DIM, TENSOR, OP_AL>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
+    case OP_B: launch_apply<T, DIM, TENSOR, OP_B>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
+    case OP_BT: launch_apply<T, DIM, TENSOR, OP_BT>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
     default:
       if constexpr (std::is_same<T, double>::value) {
         switch (mode) {
           case OP_VISC | OP_AL | OP_BT | OP_B:
             launch_apply<T, DIM, TENSOR, OP_VISC | OP_AL | OP_BT | OP_B>(L, gamma, x, y, p_in, p_out, nvec, vstride, s);
             break;
-          case OP_B: launch_apply<T, DIM, TENSOR, OP_B>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
-          case OP_BT: launch_apply<T, DIM, TENSOR, OP_BT>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
           case OP_VISC | OP_AL | OP_RAW:
             launch_apply<T, DIM, TENSOR, OP_VISC | OP_AL | OP_RAW>(L, gamma, x, y, p_in, p_out, nvec, vstride, s);
             break;
