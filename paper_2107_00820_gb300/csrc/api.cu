@@ -59,7 +59,7 @@ struct Prof {
 // offsets into the per-level small workspace of the GMRES smoother
 struct SmallLayout {
   int s, ldh;
-  size_t H, cs, sn, g, y, res, beta, nrm2, hn, total;
+  size_t H, cs, sn, g, y, res, beta, nrm2, hn, yu, total;
   explicit SmallLayout(int steps) : s(steps), ldh(steps + 1) {
     H = 0;
     cs = H + (size_t)ldh * s;
@@ -70,10 +70,12 @@ struct SmallLayout {
     beta = res + 1;
     nrm2 = beta + 1;
     hn = nrm2 + 1;
-    total = hn + s + 1;
+    yu = hn + s + 1;
+    total = yu + 2 * s + 1;
   }
   GmresDev dev(double* base) const {
-    return GmresDev{base + H, ldh, base + cs, base + sn, base + g, base + res, base + hn, base + beta, s + 1};
+    return GmresDev{base + H, ldh, base + cs, base + sn, base + g, base + res, base + hn, base + beta, s + 1,
+                    base + yu};
   }
 };
 

@@ -273,46 +273,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
   block_partials(acc, 1, partial + 1 + blockIdx.x);
   if (last_block(partial)) {
     finish_sums(partial, 1, nrm2_s);
-    if (threadIdx.x == 0) gmres_step(st, j, nrm2_s[0]);
+    if (threadIdx.x == 0) {
+      gmres_step(st, j, nrm2_s[0]);
+      if (j == st.m - 2) gmres_coeffs(st, j + 1);   // last step: the update's coefficients, once
+    }
   }
 }
 
-// x = (x_zero ? 0 : x) + sum_j Z_j y_j with y = R^-1 g (back substitution, redone
-// by every block), and, if t != NULL, the GMRES residual
-//   t = r0 - A Z y = sum_i u_i v_i,  u = Q^T (g[k] e_k)
-// from the Arnoldi relation (Q = product of the Givens rotations), no operator apply.
+// x = (x_zero ? 0 : x) + sum_j Z_j y_j with y = R^-1 g, and, if t != NULL, the
+// GMRES residual  t = r0 - A Z y = sum_i u_i v_i,  u = Q^T (g[k] e_k)  from the
+// Arnoldi relation (Q = product of the Givens rotations), no operator apply.  y and
+// u were formed once by the last block of the last k_gm_orth (gmres_coeffs).
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, const T* __restrict__ Z,
                                                            const T* __restrict__ V, long long ld, GmresDev st,
                                                            T* __restrict__ x, int x_zero, T* __restrict__ t) {
   __shared__ T y[KMAXB], u[KMAXB + 1];
   pdl_wait();
-  if (threadIdx.x == 0) {
-    double Hs[KMAXB][KMAXB], gs[KMAXB + 1], cs[KMAXB], sn[KMAXB], hn[KMAXB + 1];
-    for (int c = 0; c < k; ++c) {
-      for (int r = 0; r <= c; ++r) Hs[r][c] = st.H[(long long)c * st.ldh + r];
-      cs[c] = st.cs[c]; sn[c] = st.sn[c];
-    }
-    for (int c = 0; c <= k; ++c) { gs[c] = st.g[c]; hn[c] = st.hn[c]; }
-    double ys[KMAXB];
-    for (int i = k - 1; i >= 0; --i) {
-      double a = gs[i];
-      for (int c = i + 1; c < k; ++c) a -= Hs[i][c] * ys[c];
-      ys[i] = Hs[i][i] != 0.0 ? a / Hs[i][i] : 0.0;
-      y[i] = (T)ys[i];
-    }
-    if (t) {
-      double us[KMAXB + 1];
-      for (int i = 0; i < k; ++i) us[i] = 0.0;
-      us[k] = gs[k];
-      for (int i = k - 1; i >= 0; --i) {
-        const double a = us[i], b = us[i + 1];
-        us[i] = cs[i] * a - sn[i] * b;
-        us[i + 1] = sn[i] * a + cs[i] * b;
-      }
-      for (int i = 0; i <= k; ++i) u[i] = (T)(hn[i] != 0.0 ? us[i] / hn[i] : 0.0);
-    }
-  }
+  // coefficients from the last k_gm_orth of the cycle (gmres_coeffs), cast to T
+  if ((int)threadIdx.x < k) y[threadIdx.x] = (T)st.yu[threadIdx.x];
+  else if ((int)threadIdx.x <= 2 * k && t) u[threadIdx.x - k] = (T)st.yu[threadIdx.x];
   __syncthreads();
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
 #pragma unroll

@@ -105,6 +105,7 @@ struct GmresDev {
   double* hn;     // stored-column norms, length s + 1
   double* beta;   // |r0|
   int m;          // s + 1
+  double* yu;     // after the last step: y = R^-1 g (s entries), then u = Q^T (g[s] e_s) / hn (s + 1)
 };
 
 // start: beta = |r0|, g = (beta, 0, ...), hn[0] = beta   (one thread)
@@ -143,6 +144,35 @@ __device__ __forceinline__ void gmres_step(const GmresDev& st, int k, double nrm
   st.g[k + 1] = -sv * gk;
   st.g[k] = c * gk;
   st.res[0] = fabs(sv * gk);
+}
+
+// after step k - 1 (one thread): y = R^-1 g by back substitution on the rotated
+// Hessenberg matrix, and u = Q^T (g[k] e_k) / hn (Q = product of the Givens
+// rotations), so that x + Z y is the GMRES iterate and its residual is
+// sum_i u_i (stored column i) by the Arnoldi relation.  Stored in st.yu.
+__device__ __forceinline__ void gmres_coeffs(const GmresDev& st, int k) {
+  double Hs[KMAXB][KMAXB], gs[KMAXB + 1], cs[KMAXB], sn[KMAXB], hn[KMAXB + 1];
+  for (int c = 0; c < k; ++c) {
+    for (int r = 0; r <= c; ++r) Hs[r][c] = st.H[(long long)c * st.ldh + r];
+    cs[c] = st.cs[c]; sn[c] = st.sn[c];
+  }
+  for (int c = 0; c <= k; ++c) { gs[c] = st.g[c]; hn[c] = st.hn[c]; }
+  double ys[KMAXB];
+  for (int i = k - 1; i >= 0; --i) {
+    double a = gs[i];
+    for (int c = i + 1; c < k; ++c) a -= Hs[i][c] * ys[c];
+    ys[i] = Hs[i][i] != 0.0 ? a / Hs[i][i] : 0.0;
+    st.yu[i] = ys[i];
+  }
+  double us[KMAXB + 1];
+  for (int i = 0; i < k; ++i) us[i] = 0.0;
+  us[k] = gs[k];
+  for (int i = k - 1; i >= 0; --i) {
+    const double a = us[i], b = us[i + 1];
+    us[i] = cs[i] * a - sn[i] * b;
+    us[i + 1] = sn[i] * a + cs[i] * b;
+  }
+  for (int i = 0; i <= k; ++i) st.yu[k + i] = hn[i] != 0.0 ? us[i] / hn[i] : 0.0;
 }
 
 }  // namespace als
