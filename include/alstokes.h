@@ -121,8 +121,9 @@ void als_default_options(als_options* opt);
  * FP32 inverses), factors the coarsest A_gamma (dense FP64 Cholesky) and
  * forms the per-cell Schur-complement blocks of the finest level.
  * stream: a cudaStream_t (NULL = legacy default stream).
- * Size limits (ALS_EINVAL): d (2n+1)^d velocity values and d 3^d n^d per-cell
- * outputs must each stay below 2^31 (the kernels index them with 32 bits). */
+ * Size limits (ALS_EINVAL): d (2n+1)^d velocity values, d 3^d n^d per-cell
+ * outputs and d 3^d (n+1)^d vertex-star patch outputs (products over the axes)
+ * must each stay below 2^31 (the kernels index them with 32 bits). */
 als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
                       void* stream, als_ctx** out);
 

@@ -718,6 +718,9 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     long long ne = c->dim * (c->dim == 2 ? 9 : 27);   // per-cell output buffer, 32-bit offsets
     for (int k = 0; k < c->dim; ++k) ne *= mesh->n[k];
     if (ne >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d 3^d n^d must stay below 2^31");
+    long long np = c->dim * (c->dim == 2 ? 9 : 27);   // vertex-star patch outputs, 32-bit offsets
+    for (int k = 0; k < c->dim; ++k) np *= mesh->n[k] + 1LL;
+    if (np >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d 3^d (n+1)^d must stay below 2^31");
   }
   const char* ng = getenv("ALS_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');

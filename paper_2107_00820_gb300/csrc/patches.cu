@@ -247,6 +247,63 @@ __device__ __forceinline__ float patch_r(const Geom& g, const float* __restrict_
   return patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
 }
 
+// One patch per iteration (3D): the index arithmetic of a thread's entries is split
+// into a per-entry part, fixed for the whole launch, and a per-patch part, formed
+// once per patch.  Entry i = c NB + o of the patch of vertex v sits at vector index
+// c N + node(2v - 1 + o) and at scratch index patch_out_index(v, i).
+struct EntryConst {
+  int ox, oy, oz;     // node offsets 0..2 per axis
+  int goff;           // c N + (oz - 1) nn0 nn1 + (oy - 1) nn0 + (ox - 1)
+  int ooff;           // ((c L + oz) 3 + oy) nv1 nv2 (3 nv0) + ox
+  bool ok;            // the thread owns this entry
+};
+struct PatchPos {
+  int vid, vx, vy, vz;
+  bool inner;         // no node of the patch on or beyond the boundary
+  int gbase;          // node index of 2v
+  int obase;          // (vz nv1 + vy) (3 nv0) + 3 vx
+};
+// (32-bit offsets: vector and scratch lengths stay below 2^31, checked when a context is created)
+template <int DIM>
+__device__ __forceinline__ EntryConst entry_const(const Geom& g, int e, int total) {
+  constexpr int NB = Sz<DIM>::NB;
+  EntryConst c{};
+  c.ok = e < total;
+  const int i = c.ok ? e % Sz<DIM>::NP : 0;
+  const int comp = i / NB, o = i - comp * NB;
+  c.ox = o % 3;
+  c.oy = (o / 3) % 3;
+  c.oz = DIM == 3 ? o / 9 : 1;
+  const int nn01 = g.nn[0] * g.nn[1];
+  c.goff = comp * (int)g.N + (c.oz - 1) * nn01 + (c.oy - 1) * g.nn[0] + (c.ox - 1);
+  const int L = DIM == 3 ? 3 : 1;
+  const int oz = DIM == 3 ? c.oz : 0;
+  c.ooff = ((comp * L + oz) * 3 + c.oy) * (g.nv[1] * g.nv[2]) * (3 * g.nv[0]) + c.ox;
+  return c;
+}
+template <int DIM>
+__device__ __forceinline__ PatchPos patch_pos(const Geom& g, int interior, int p, int count) {
+  PatchPos q{};
+  q.vid = work_vertex<DIM>(g, interior, p, count, q.vx, q.vy, q.vz);
+  q.inner = q.vx >= 1 && q.vx <= g.nv[0] - 2 && q.vy >= 1 && q.vy <= g.nv[1] - 2 &&
+            (DIM == 2 || (q.vz >= 1 && q.vz <= g.nv[2] - 2));
+  q.gbase = 2 * q.vx + 2 * q.vy * g.nn[0] + (DIM == 3 ? 2 * q.vz * g.nn[0] * g.nn[1] : 0);
+  q.obase = (q.vz * g.nv[1] + q.vy) * (3 * g.nv[0]) + 3 * q.vx;
+  return q;
+}
+// the node of entry c of the patch at q exists (inside the free nodes)
+template <int DIM>
+__device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const EntryConst& c) {
+  if (q.inner) return true;
+  const int i = 2 * q.vx + c.ox - 1, j = 2 * q.vy + c.oy - 1;
+  if (i <= 0 || i >= g.nn[0] - 1 || j <= 0 || j >= g.nn[1] - 1) return false;
+  if (DIM == 3) {
+    const int k = 2 * q.vz + c.oz - 1;
+    if (k <= 0 || k >= g.nn[2] - 1) return false;
+  }
+  return true;
+}
+
 template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
@@ -292,6 +349,17 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       }
     }
   };
+  // PPI == 1: the thread's entries all belong to the iteration's one patch
+  EntryConst ec[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) ec[k] = entry_const<DIM>(g, tid + k * THREADS, PPI * NP);
+  auto gather1 = [&](const PatchPos& q, float (&v)[RPT]) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      v[k] = 0.f;
+      if (ec[k].ok && q.vid >= 0 && entry_in<DIM>(g, q, ec[k])) v[k] = __ldg(r + (q.gbase + ec[k].goff));
+    }
+  };
 
   if (tid == ISSUER) {
     s_fail = 0;
@@ -308,7 +376,13 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   // the preceding kernel of the cycle
   pdl_wait();
   float rpre[RPT];
-  gather(blockIdx.x, rpre);
+  PatchPos qcur{}, qnext{};
+  if constexpr (PPI == 1) {
+    qnext = patch_pos<DIM>(g, interior, blockIdx.x, count);
+    gather1(qnext, rpre);
+  } else {
+    gather(blockIdx.x, rpre);
+  }
 
   const int ps = tid / TPP, b = tid % TPP;
   int I = 0, J = 0;
@@ -325,7 +399,14 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       const int e = tid + k * THREADS;
       if (e < PPI * NP) rs[e] = rpre[k];
     }
-    gather(grp + gridDim.x, rpre);          // next group's r: in flight while this one is computed
+    // next group's r: in flight while this one is computed
+    if constexpr (PPI == 1) {
+      qcur = qnext;
+      qnext = patch_pos<DIM>(g, interior, grp + gridDim.x, count);
+      gather1(qnext, rpre);
+    } else {
+      gather(grp + gridDim.x, rpre);
+    }
     if (!tma::mbar_wait(&bars[stage], parity)) {
       if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
     }
@@ -357,21 +438,38 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       }
     }
     // y_i = sum_J partial(i, J), fixed order
-    for (int e = tid; e < PPI * NP; e += THREADS) {
-      const int p = e / NP, i = e % NP;
-      int vx, vy, vz;
-      const int v = work_vertex<DIM>(g, interior, grp * PPI + p, count, vx, vy, vz);
-      if (v < 0) continue;
-      float acc = 0.f;
+    if constexpr (PPI == 1) {
 #pragma unroll
-      for (int jb = 0; jb < NBR; ++jb) acc += part[(p * NP + i) * NBR + jb];
-      if (mode == OUT_SCRATCH) {
-        out[patch_out_index<DIM>(g, vx, vy, vz, i)] = acc;
-      } else {
-        long long nd;
-        if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
-          float* o = out + (i / NB) * g.N + nd;
+      for (int k = 0; k < RPT; ++k) {
+        if (!ec[k].ok || qcur.vid < 0) continue;
+        const int i = tid + k * THREADS;
+        float acc = 0.f;
+#pragma unroll
+        for (int jb = 0; jb < NBR; ++jb) acc += part[i * NBR + jb];
+        if (mode == OUT_SCRATCH) {
+          out[qcur.obase + ec[k].ooff] = acc;
+        } else if (entry_in<DIM>(g, qcur, ec[k])) {
+          float* o = out + (qcur.gbase + ec[k].goff);
           *o = mode == OUT_SUBTRACT ? *o - acc : acc;
+        }
+      }
+    } else {
+      for (int e = tid; e < PPI * NP; e += THREADS) {
+        const int p = e / NP, i = e % NP;
+        int vx, vy, vz;
+        const int v = work_vertex<DIM>(g, interior, grp * PPI + p, count, vx, vy, vz);
+        if (v < 0) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int jb = 0; jb < NBR; ++jb) acc += part[(p * NP + i) * NBR + jb];
+        if (mode == OUT_SCRATCH) {
+          out[patch_out_index<DIM>(g, vx, vy, vz, i)] = acc;
+        } else {
+          long long nd;
+          if (patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) {
+            float* o = out + (i / NB) * g.N + nd;
+            *o = mode == OUT_SUBTRACT ? *o - acc : acc;
+          }
         }
       }
     }
