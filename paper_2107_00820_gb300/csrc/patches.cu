@@ -206,11 +206,11 @@ struct TmaCfg {
   static constexpr int NBR = NP / 9;
   static constexpr int RPT = (PPI * NP + THREADS - 1) / THREADS;   // r values gathered per thread
   static constexpr size_t stage_floats = (size_t)PPI * STRIDE;
-  // dynamic shared memory: [mbarriers | stages | r (x2) | partials (x2)]; the barriers
-  // need 8-byte and the bulk-copy destinations 16-byte alignment
+  // dynamic shared memory: [mbarriers | stages | r | partials]; the barriers need
+  // 8-byte and the bulk-copy destinations 16-byte alignment
   static constexpr size_t bar_bytes = 128;
   static constexpr size_t smem_bytes =
-      bar_bytes + NSTAGE * stage_floats * 4 + 2 * (size_t)PPI * NP * 4 + 2 * (size_t)PPI * NP * NBR * 4;
+      bar_bytes + NSTAGE * stage_floats * 4 + (size_t)PPI * NP * 4 + (size_t)PPI * NP * NBR * 4;
   static_assert(NSTAGE * 8 <= bar_bytes, "mbarrier area too small");
   static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
 };
@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
   float* stages = reinterpret_cast<float*>(smraw + C::bar_bytes);
-  float* rsb = stages + NSTAGE * C::stage_floats;         // [2][PPI][NP]
-  float* partb = rsb + 2 * PPI * NP;                      // [2][PPI][NP][NBR]
+  float* rs = stages + NSTAGE * C::stage_floats;          // [PPI][NP]
+  float* part = rs + PPI * NP;                            // [PPI][NP][NBR]
   __shared__ int s_fail;
   const int tid = threadIdx.x;
   const int ngroups = (count + PPI - 1) / PPI;
@@ -390,10 +390,8 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
   int it = 0;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
-    const int stage = it % NSTAGE, buf = it & 1;
+    const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
-    float* rs = rsb + buf * PPI * NP;
-    float* part = partb + buf * PPI * NP * NBR;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int e = tid + k * THREADS;
@@ -473,8 +471,9 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
         }
       }
     }
-    // no third barrier: r and the partials are double-buffered, and iteration it+2
-    // rewrites these buffers only after every thread has passed barrier (A) of it+1
+    // no third barrier: r is read only between (A) and (B) of an iteration and
+    // rewritten after (B); the partials are read after (B) and rewritten only after
+    // barrier (A) of the next iteration, which every thread reaches after its reads
   }
   pdl_trigger();
   if (s_fail && tid == ISSUER) {
