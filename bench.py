@@ -345,11 +345,14 @@ def ours(args, dist):
     p1.record()
     torch.cuda.synchronize()
     t_setup = p0.elapsed_time(p1) / 3 / 1e3
-    p0.record()
-    info_s = ctx.solve(f_d, ubc_d, None, u_d, p_d)[2]
-    p1.record()
-    torch.cuda.synchronize()
-    t_solve = p0.elapsed_time(p1) / 1e3
+    solves = []
+    for _ in range(3):
+        p0.record()
+        info_s = ctx.solve(f_d, ubc_d, None, u_d, p_d)[2]
+        p1.record()
+        torch.cuda.synchronize()
+        solves.append(p0.elapsed_time(p1) / 1e3)
+    t_solve = sorted(solves)[1]   # median of three
     fp32_peak, fp64_peak = A.als_measure_fma_peaks(stream)
     t_step = dist.max(e0.elapsed_time(e1) / args.steps) / 1e3
     value = dist.world * dofs / t_step

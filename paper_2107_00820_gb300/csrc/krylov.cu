@@ -242,23 +242,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
                                                          double* __restrict__ partial, GmresDev st) {
   __shared__ T coef[KMAXB];
   __shared__ double nrm2_s[1];
-  pdl_wait();
-  const double* hcol = st.H + (long long)j * st.ldh;
-  if ((int)threadIdx.x <= j)
-    coef[threadIdx.x] = (T)(st.hn[threadIdx.x] != 0.0 ? hcol[threadIdx.x] / st.hn[threadIdx.x] : 0.0);
-  __syncthreads();
   T* w = const_cast<T*>(V) + (long long)(j + 1) * ld;
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
   T a[GM_PER];
   T vc[GM_PER][KMAXB];
+  // columns 0..j come from earlier kernels of the chain (complete before this launch
+  // began): read through L2 before the wait; column j+1 and H come from the predecessor
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {
     const unsigned i = base + q * RED_THREADS;
-    const bool in = i < n;
-    a[q] = in ? w[i] : T(0);
 #pragma unroll
-    for (int c = 0; c < KMAXB; ++c) vc[q][c] = (in && c <= j) ? V[(long long)c * ld + i] : T(0);
+    for (int c = 0; c < KMAXB; ++c) vc[q][c] = (i < n && c <= j) ? __ldcg(V + (long long)c * ld + i) : T(0);
   }
+  pdl_wait();
+  const double* hcol = st.H + (long long)j * st.ldh;
+  if ((int)threadIdx.x <= j)
+    coef[threadIdx.x] = (T)(st.hn[threadIdx.x] != 0.0 ? hcol[threadIdx.x] / st.hn[threadIdx.x] : 0.0);
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+    a[q] = i < n ? w[i] : T(0);
+  }
+  __syncthreads();
   T acc[KMAXB] = {T(0)};
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {
@@ -289,25 +294,38 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, co
                                                            const T* __restrict__ V, long long ld, GmresDev st,
                                                            T* __restrict__ x, int x_zero, T* __restrict__ t) {
   __shared__ T y[KMAXB], u[KMAXB + 1];
+  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  // Z, x and V_0..V_{k-1} come from earlier kernels of the chain (complete before this
+  // launch began): read through L2 before the wait; V_k and the coefficients come
+  // from the predecessor (the last Gram-Schmidt step)
+  T zc[GM_PER][KMAXB], xa[GM_PER];
+#pragma unroll
+  for (int q = 0; q < GM_PER; ++q) {
+    const unsigned i = base + q * RED_THREADS;
+#pragma unroll
+    for (int c = 0; c < KMAXB; ++c) zc[q][c] = (i < n && c < k) ? __ldcg(Z + (long long)c * ld + i) : T(0);
+    xa[q] = (i < n && !x_zero) ? __ldcg(x + i) : T(0);
+  }
   pdl_wait();
   // coefficients from the last k_gm_orth of the cycle (gmres_coeffs), cast to T
   if ((int)threadIdx.x < k) y[threadIdx.x] = (T)st.yu[threadIdx.x];
   else if ((int)threadIdx.x <= 2 * k && t) u[threadIdx.x - k] = (T)st.yu[threadIdx.x];
   __syncthreads();
-  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {
     const unsigned i = base + q * RED_THREADS;
     if (i >= n) break;
-    T zc[KMAXB];
-#pragma unroll
-    for (int c = 0; c < KMAXB; ++c) zc[c] = c < k ? Z[(long long)c * ld + i] : T(0);
-    T a = x_zero ? T(0) : x[i];
+    T a = xa[q];
 #pragma unroll
     for (int c = 0; c < KMAXB; ++c)
-      if (c < k) a += zc[c] * y[c];
+      if (c < k) a += zc[q][c] * y[c];
     x[i] = a;
-    if (t) {
+  }
+  if (t) {
+#pragma unroll
+    for (int q = 0; q < GM_PER; ++q) {
+      const unsigned i = base + q * RED_THREADS;
+      if (i >= n) break;
       T vc[KMAXB + 1];
 #pragma unroll
       for (int c = 0; c <= KMAXB; ++c) vc[c] = c <= k ? V[(long long)c * ld + i] : T(0);

@@ -527,9 +527,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
   T acc[KMAXB];
 #pragma unroll
   for (int j = 0; j < KMAXB; ++j) acc[j] = T(0);
-  pdl_wait();
   RowChunk rc;
-  if (row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) {
+  const bool have = row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc);
+  // The basis columns come from earlier kernels of the chain, which completed before
+  // this launch began (every kernel waits on its predecessor before it lets its
+  // successor start): they are read through L2 while the preceding kernel finishes.
+  T vp[GX][KMAXB];
+#pragma unroll
+  for (int q = 0; q < GX; ++q)
+#pragma unroll
+    for (int jj = 0; jj < KMAXB; ++jj)
+      vp[q][jj] = (!start && have && jj < k && GX * rc.j + q < g.nn[0]) ? __ldcg(V + (long long)jj * ld + rc.t0 + q)
+                                                                         : T(0);
+  pdl_wait();
+  if (have) {
     T ax[GX];
     gather_chunk<T, DIM>(g, ebuf, x, rc, 1, 0, ax);
 #pragma unroll
@@ -543,7 +554,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
       } else {
 #pragma unroll
         for (int jj = 0; jj < KMAXB; ++jj)
-          if (jj < k) acc[jj] += V[(long long)jj * ld + t] * v;
+          if (jj < k) acc[jj] += vp[q][jj] * v;
       }
     }
   }
