@@ -56,27 +56,11 @@ struct Prof {
   cudaEvent_t spare0 = nullptr, spare1 = nullptr;
 };
 
-// offsets into the per-level small workspace of the GMRES smoother
-struct SmallLayout {
-  int s, ldh;
-  size_t H, cs, sn, g, y, res, beta, nrm2, hn, yu, total;
-  explicit SmallLayout(int steps) : s(steps), ldh(steps + 1) {
-    H = 0;
-    cs = H + (size_t)ldh * s;
-    sn = cs + s;
-    g = sn + s;
-    y = g + s + 1;
-    res = y + s;
-    beta = res + 1;
-    nrm2 = beta + 1;
-    hn = nrm2 + 1;
-    yu = hn + s + 1;
-    total = yu + 2 * s + 1;
-  }
-  GmresDev dev(double* base) const {
-    return GmresDev{base + H, ldh, base + cs, base + sn, base + g, base + res, base + hn, base + beta, s + 1,
-                    base + yu};
-  }
+// per-level GMRES state array (GmresLayout offsets): elements of the cycle's precision in the
+// fused smoother, doubles in the per-operation one
+struct SmallLayout : GmresLayout {
+  explicit SmallLayout(int steps) : GmresLayout(steps) {}
+  GmresDev dev(double* base) const { return GmresDev{base, s}; }
 };
 
 }  // namespace
@@ -289,8 +273,8 @@ void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
     void* Zj = vptr(w.Z[l], w.es, (long long)j * len);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
-    patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, st.hn + j);  // Z_j = D^-1 v_j
-    ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, st.H + (size_t)j * sl.ldh, 0, st, w.partial};
+    patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, vptr(sm, w.es, sl.hn + j));  // Z_j = D^-1 v_j
+    ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, vptr(sm, w.es, sl.H + (long long)j * sl.ldh), 0, st, w.partial};
     cudaEvent_t a0 = nullptr, a1 = nullptr;
     if (l == c->L - 1) prof_events(c, t_prof_counter, a0, a1, 1);
     op_apply_epi(Lv, prec, c->gamma, Zj, Vn, e, s, a0, a1);            // A Z_j, H[0..j][j]

@@ -204,14 +204,17 @@ void vec_scale_dev(int prec, long long n, const double* num, const double* den, 
 // blocks, which keeps the ticket counter of the single-launch reduction cold
 // (same-address atomics serialise: several thousand blocks cost microseconds).
 // Column loops are unrolled to KMAXB with predicates.  In FP32 the arithmetic
-// and the in-block sums run in float.
+// and all sums run in float, and so does the small GMRES bookkeeping (the state
+// array holds elements of the smoother's precision).
 constexpr int GM_PER = 4;
 
 // V0 = b, |b|^2 -> gmres_start
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* __restrict__ b, T* __restrict__ V0,
-                                                          double* __restrict__ partial, GmresDev st) {
-  __shared__ double nrm2_s[1];
+                                                          double* __restrict__ partial, GmresDev sd) {
+  __shared__ T nrm2_s[1];
+  const GmresView<T> st = gmres_view<T>(sd);
+  T* rows = reinterpret_cast<T*>(partial + 1);
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
   pdl_wait();
   T v[GM_PER];
@@ -228,9 +231,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* _
     acc[0] += v[q] * v[q];
   }
   pdl_trigger();
-  block_partials(acc, 1, partial + 1 + blockIdx.x);
+  block_partials<T, T>(acc, 1, rows + blockIdx.x);
   if (last_block(partial)) {
-    finish_sums(partial, 1, nrm2_s);
+    finish_sums<T>(partial, 1, nrm2_s);
     if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
   }
 }
@@ -239,9 +242,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* _
 // coefficients H[0..j][j] / hn[i], then |w|^2 -> gmres_step(j)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, const T* __restrict__ V, long long ld,
-                                                         double* __restrict__ partial, GmresDev st) {
+                                                         double* __restrict__ partial, GmresDev sd) {
   __shared__ T coef[KMAXB];
-  __shared__ double nrm2_s[1];
+  __shared__ T nrm2_s[1];
+  const GmresView<T> st = gmres_view<T>(sd);
+  T* rows = reinterpret_cast<T*>(partial + 1);
   T* w = const_cast<T*>(V) + (long long)(j + 1) * ld;
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
   T a[GM_PER];
@@ -255,9 +260,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
     for (int c = 0; c < KMAXB; ++c) vc[q][c] = (i < n && c <= j) ? __ldcg(V + (long long)c * ld + i) : T(0);
   }
   pdl_wait();
-  const double* hcol = st.H + (long long)j * st.ldh;
+  const T* hcol = st.H + (long long)j * st.ldh;
   if ((int)threadIdx.x <= j)
-    coef[threadIdx.x] = (T)(st.hn[threadIdx.x] != 0.0 ? hcol[threadIdx.x] / st.hn[threadIdx.x] : 0.0);
+    coef[threadIdx.x] = st.hn[threadIdx.x] != T(0) ? hcol[threadIdx.x] / st.hn[threadIdx.x] : T(0);
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {
     const unsigned i = base + q * RED_THREADS;
@@ -275,9 +280,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
     acc[0] += a[q] * a[q];
   }
   pdl_trigger();
-  block_partials(acc, 1, partial + 1 + blockIdx.x);
+  block_partials<T, T>(acc, 1, rows + blockIdx.x);
   if (last_block(partial)) {
-    finish_sums(partial, 1, nrm2_s);
+    finish_sums<T>(partial, 1, nrm2_s);
     if (threadIdx.x == 0) {
       gmres_step(st, j, nrm2_s[0]);
       if (j == st.m - 2) gmres_coeffs(st, j + 1);   // last step: the update's coefficients, once
@@ -291,9 +296,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
 // u were formed once by the last block of the last k_gm_orth (gmres_coeffs).
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, const T* __restrict__ Z,
-                                                           const T* __restrict__ V, long long ld, GmresDev st,
+                                                           const T* __restrict__ V, long long ld, GmresDev sd,
                                                            T* __restrict__ x, int x_zero, T* __restrict__ t) {
   __shared__ T y[KMAXB], u[KMAXB + 1];
+  const GmresView<T> st = gmres_view<T>(sd);
   const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
   // Z, x and V_0..V_{k-1} come from earlier kernels of the chain (complete before this
   // launch began): read through L2 before the wait; V_k and the coefficients come
@@ -308,8 +314,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, co
   }
   pdl_wait();
   // coefficients from the last k_gm_orth of the cycle (gmres_coeffs), cast to T
-  if ((int)threadIdx.x < k) y[threadIdx.x] = (T)st.yu[threadIdx.x];
-  else if ((int)threadIdx.x <= 2 * k && t) u[threadIdx.x - k] = (T)st.yu[threadIdx.x];
+  if ((int)threadIdx.x < k) y[threadIdx.x] = st.yu[threadIdx.x];
+  else if ((int)threadIdx.x <= 2 * k && t) u[threadIdx.x - k] = st.yu[threadIdx.x];
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < GM_PER; ++q) {

@@ -43,15 +43,16 @@ void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x
               const void* p_in, void* p_out, cudaStream_t s);
 // A_gamma apply (viscous + AL) fused with the reduction that consumes y:
 //   y = b + sigma A x (b NULL: y = sigma A x);
-//   start = 0: out[j] = (V_j . y) / st.hn[j] for j < k (k <= KMAXB; Arnoldi dots)
+//   start = 0: out[j] = (V_j . y) / hn[j] for j < k (k <= KMAXB; Arnoldi dots)
 //   start = 1: |y|^2 starts the GMRES cycle st
+// out and the GMRES state hold elements of the apply's precision.
 struct ApplyEpi {
   const void* b;
   double sigma;
   int k;
   const void* V;
   long long ld;
-  double* out;
+  void* out;
   int start;
   GmresDev st;
   double* partial;
@@ -66,9 +67,9 @@ void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y,
 // ---- patches.cu
 void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s);
 // e0/e1 (optional) are recorded immediately before and after the patch kernel
-// den (optional device scalar): z = D^-1 r / den (0 where den == 0)
+// den (optional device scalar of precision prec): z = D^-1 r / den (0 where den == 0)
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
-                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, const double* den = nullptr);
+                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, const void* den = nullptr);
 size_t patch_scratch_bytes(const LevelDev& L, int prec);
 // times the FP32 patch-kernel variants on this level and keeps the fastest (ms_out[3], optional)
 int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out = nullptr);

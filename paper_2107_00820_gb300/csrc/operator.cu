@@ -520,9 +520,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
                                                             const T* __restrict__ x, T* __restrict__ y,
                                                             const T* __restrict__ b, double sigma, int k,
                                                             const T* __restrict__ V, long long ld,
-                                                            double* __restrict__ out, int start, GmresDev st,
+                                                            T* __restrict__ out, int start, GmresDev sd,
                                                             double* __restrict__ partial) {
-  __shared__ double nrm2_s[1];
+  __shared__ T nrm2_s[1];
+  const GmresView<T> st = gmres_view<T>(sd);
+  T* rows = reinterpret_cast<T*>(partial + 1);
   const int kk = start ? 1 : k;
   T acc[KMAXB];
 #pragma unroll
@@ -559,13 +561,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
     }
   }
   pdl_trigger();
-  block_partials(acc, kk, partial + 1 + (long long)blockIdx.x * kk);
+  block_partials<T, T>(acc, kk, rows + (long long)blockIdx.x * kk);
   if (last_block(partial)) {
     if (start) {
-      finish_sums(partial, 1, nrm2_s);
+      finish_sums<T>(partial, 1, nrm2_s);
       if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
     } else {
-      finish_sums(partial, k, out, st.hn);
+      finish_sums<T>(partial, k, out, st.hn);
     }
   }
 }
@@ -699,8 +701,8 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
                                                        nullptr, 0, (T*)L.ebuf, winv);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   launch_pdl(k_gather_epi<T, DIM>, (gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s, g,
-             (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, e.out, e.start,
-             e.st, e.partial);
+             (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out,
+             e.start, e.st, e.partial);
   count_launch(2);
 }
 

@@ -723,11 +723,11 @@ __global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restric
 // order; Dirichlet nodes get 0; divided by den[0] when den is given.
 template <typename TV, int DIM>
 __global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
-                               const double* __restrict__ den) {
+                               const TV* __restrict__ den) {
   __shared__ TV inv_den;
   pdl_wait();
   if (den) {                        // one division per block, not per entry
-    if (threadIdx.x == 0) inv_den = den[0] != 0.0 ? (TV)(1.0 / den[0]) : TV(0);
+    if (threadIdx.x == 0) inv_den = den[0] != TV(0) ? TV(1) / den[0] : TV(0);
     __syncthreads();
   }
   RowChunk rc;
@@ -792,31 +792,32 @@ size_t patch_scratch_bytes(const LevelDev& L, int prec) {
 
 template <typename TF, typename TV, int DIM>
 static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z, void* scratch, cudaStream_t s,
-                        cudaEvent_t e0, cudaEvent_t e1, const double* den) {
+                        cudaEvent_t e0, cudaEvent_t e1, const void* den) {
   const long long warps = L.g.nverts;
   const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
   // External records become event-record nodes when the stream is being captured
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   launch_pdl(k_patch_apply<TF, TV, DIM>, blocks, 256, 0, s, L.g, inv, L.pstride, (const TV*)r, (TV*)scratch);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  launch_pdl(k_patch_gather<TV, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const TV*)scratch, (TV*)z, den);
+  launch_pdl(k_patch_gather<TV, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const TV*)scratch, (TV*)z,
+             (const TV*)den);
   count_launch(2);
 }
 
 template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
-                       cudaEvent_t e1, const double* den) {
+                       cudaEvent_t e1, const void* den) {
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   launch_patch_variant<DIM>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
                             L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   launch_pdl(k_patch_gather<float, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const float*)scratch,
-             (float*)z, den);
+             (float*)z, (const float*)den);
   count_launch(1);
 }
 
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
-                  cudaEvent_t e0, cudaEvent_t e1, const double* den) {
+                  cudaEvent_t e0, cudaEvent_t e1, const void* den) {
   if (prec == PREC_F64) {
     if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1, den);
     else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1, den);
