@@ -229,25 +229,73 @@ void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, 
   count_launch(3 + (npad > nfree ? 1 : 0) + 5LL * nt);
 }
 
-template <typename TV>
-__global__ void k_coarse_apply(Geom g, int nfree, const double* __restrict__ inv, const TV* __restrict__ b,
-                               TV* __restrict__ x) {
+// 32-bit form of free_dof for the apply (vector lengths stay below 2^31)
+__device__ __forceinline__ int free_dof32(const Geom& g, int f) {
+  const int ni = g.nn[0] - 2, nj = g.nn[1] - 2, nk = g.dim == 3 ? g.nn[2] - 2 : 1;
+  const int nint = ni * nj * nk;
+  const int c = f / nint;
+  const int m = f - c * nint;
+  const int q = m / ni;
+  const int i = m - q * ni + 1;
+  const int j = g.dim == 3 ? q % nj + 1 : q + 1;
+  const int k = g.dim == 3 ? q / nj + 1 : 0;
+  return c * (int)g.N + i + g.nn[0] * (j + g.nn[1] * k);
+}
+
+// x_free = inv b_free, one warp per row.  STAGE: b at the free dofs is first
+// gathered into shared memory (as double) by every block; otherwise (coarse
+// problems too large for shared memory) each term reads b through the index map.
+// Four independent FP64 partial sums per lane (dependent FP64 adds are slow on
+// this GPU), combined in a fixed order.
+template <typename TV, bool STAGE>
+__global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const double* __restrict__ inv,
+                                                      const TV* __restrict__ b, TV* __restrict__ x) {
+  extern __shared__ double bs[];
   pdl_wait();
+  if (STAGE) {
+    for (int c = threadIdx.x; c < nfree; c += blockDim.x) bs[c] = (double)b[free_dof32(g, c)];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= nfree) return;
-  double acc = 0.0;
-  for (int c = lane; c < nfree; c += 32) acc += inv[(long long)r * nfree + c] * (double)b[free_dof(g, c)];
+  const double* row = inv + (long long)r * nfree;
+  auto bv = [&](int c) { return STAGE ? bs[c] : (double)b[free_dof32(g, c)]; };
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = lane;
+  for (; c + 96 < nfree; c += 128) {
+    a0 += row[c] * bv(c);
+    a1 += row[c + 32] * bv(c + 32);
+    a2 += row[c + 64] * bv(c + 64);
+    a3 += row[c + 96] * bv(c + 96);
+  }
+  for (; c < nfree; c += 32) a0 += row[c] * bv(c);
+  double acc = (a0 + a1) + (a2 + a3);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) x[free_dof(g, r)] = (TV)acc;
+  if (lane == 0) x[free_dof32(g, r)] = (TV)acc;
+}
+
+template <typename TV>
+static void launch_coarse_apply(const LevelDev& L, const CoarseDev& C, const TV* b, TV* x, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((C.nfree + 7) / 8);
+  const size_t smem = (size_t)C.nfree * sizeof(double);
+  if (smem <= 200 * 1024) {
+    static size_t set = 0;   // largest opt-in applied so far
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(k_coarse_apply<TV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    launch_pdl(k_coarse_apply<TV, true>, blocks, 256, smem, s, L.g, C.nfree, (const double*)C.inv, b, x);
+  } else {
+    launch_pdl(k_coarse_apply<TV, false>, blocks, 256, 0, s, L.g, C.nfree, (const double*)C.inv, b, x);
+  }
 }
 
 void coarse_apply(const LevelDev& L, const CoarseDev& C, int prec, const void* b, void* x, cudaStream_t s) {
   const long long len = L.g.N * L.g.dim;
   cudaMemsetAsync(x, 0, len * (prec == PREC_F64 ? 8 : 4), s);
-  const unsigned blocks = (unsigned)((C.nfree + 7) / 8);
-  if (prec == PREC_F64) launch_pdl(k_coarse_apply<double>, blocks, 256, 0, s, L.g, C.nfree, C.inv, (const double*)b, (double*)x);
-  else launch_pdl(k_coarse_apply<float>, blocks, 256, 0, s, L.g, C.nfree, C.inv, (const float*)b, (float*)x);
+  if (prec == PREC_F64) launch_coarse_apply<double>(L, C, (const double*)b, (double*)x, s);
+  else launch_coarse_apply<float>(L, C, (const float*)b, (float*)x, s);
   count_launch(1);
 }
 
