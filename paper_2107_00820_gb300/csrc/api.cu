@@ -652,7 +652,7 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
       ALS_TRY(cuda_check(c, "mass blocks"));
     }
     if (l > 0) {
-      patch_setup(Lv, c->gamma, 1, c->st, c->stream);
+      patch_setup(Lv, c->gamma, 1, c->opt.mode == ALS_MODE_MIXED ? 1 : 0, c->st, c->stream);
       ALS_TRY(cuda_check(c, "patch setup"));
     }
   }
@@ -730,6 +730,11 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     Lv.pstride = packed_stride(Lv.np);
     Lv.status = c->st;
     const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
+    {
+      char* tab = nullptr;
+      ALS_TRY(dalloc(c, &tab, setup_tab_bytes(c->dim)));
+      Lv.setup_tab = tab;
+    }
     ALS_TRY(dalloc(c, &Lv.coef64, ncq));
     ALS_TRY(dalloc(c, &Lv.coef32, ncq));
     if (Lv.tensor) ALS_TRY(dalloc(c, &Lv.mu64, (size_t)Lv.g.ncells * NB));

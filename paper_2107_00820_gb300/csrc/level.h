@@ -27,6 +27,7 @@ struct LevelDev {
   float* winv32;
   int patch_kernel;      // FP32 patch-kernel variant picked by patch_autotune (-1: not yet tuned)
   float tune_ms[3];      // measured time per launch of each variant (ms)
+  void* setup_tab;       // reference tables of the patch setup (setup_tab_bytes)
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
@@ -65,7 +66,11 @@ void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y,
                     long long stride, cudaStream_t s);
 
 // ---- patches.cu
-void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s);
+// df64: assemble and invert in double-float arithmetic (FP32 pairs, about 48 bits),
+// enough for the FP32 inverse of the mixed cycle; otherwise in FP64.  L.setup_tab
+// holds setup_tab_bytes(dim) bytes of scratch for the level's reference tables.
+void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s);
+size_t setup_tab_bytes(int dim);
 // e0/e1 (optional) are recorded immediately before and after the patch kernel
 // den (optional device scalar of precision prec): z = D^-1 r / den (0 where den == 0)
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,

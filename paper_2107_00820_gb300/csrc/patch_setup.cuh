@@ -1,9 +1,11 @@
 // K3: vertex-star patch setup (included by patches.cu inside namespace als,
-// after patch_node / vertex_coords / mandel_of).
+// after patch_node / vertex_coords / mandel_of and df64.cuh).
 //
 // One CTA per vertex v assembles A_v, the restriction of A_(h,gamma) to the
 // d*3^d dofs of the vertex star (Sec. 5.1, Eq. viim), from the 2^d cells of the
-// star, and inverts it in FP64.  A_v is symmetric, so only its upper triangle is
+// star, and inverts it in the arithmetic R: FP64, or double-float (DF64, about 48
+// significant bits in FP32 pairs, see df64.cuh) when only the FP32 cycle needs the
+// inverse to FP32 accuracy.  A_v is symmetric, so only its upper triangle is
 // kept (packed by rows in shared memory) and it is inverted by the symmetric
 // sweep operator: sweeping pivot k maps M to
 //   M_ij - M_ik M_kj / M_kk  (i, j != k),   M_ik / M_kk,   -1 / M_kk  (the pivot),
@@ -19,6 +21,19 @@
 // so the kernel minimises FP64 operations rather than idle threads: one division
 // per pivot per block, no redundant sums.
 #pragma once
+
+// the two arithmetic types of the setup: conversions to and from FP64 inputs/outputs
+template <typename R> struct RealOps;
+template <> struct RealOps<double> {
+  static __device__ __forceinline__ double from(double d) { return d; }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+  static __device__ __forceinline__ float to_float(double v) { return (float)v; }
+};
+template <> struct RealOps<DF64> {
+  static __device__ __forceinline__ DF64 from(double d) { return df_from(d); }
+  static __device__ __forceinline__ double to_double(DF64 v) { return df_to_double(v); }
+  static __device__ __forceinline__ float to_float(DF64 v) { return v.hi; }
+};
 
 __host__ __device__ constexpr int tri_row(int np, int i) { return i * np - (i * (i - 1)) / 2; }
 
@@ -55,17 +70,16 @@ __device__ __forceinline__ void sub_node(int i, int sx, int sy, int sz, int& P, 
 }
 
 // Nonzero Mandel entries of eps(phi e_al) for the gradient gr of phi: slot al with
-// d_al phi, and the shear slots of the pairs (al, o) with sqrt(1/2) d_o phi (the same
-// entries as mandel_of without its zeros; 3 in 3D, 2 in 2D).  3D shear slots:
+// d_al phi, and the shear slots of the pairs (al, o) with ir2 = sqrt(1/2) times d_o phi
+// (the same entries as mandel_of without its zeros; 3 in 3D, 2 in 2D).  3D shear slots:
 // 3 = (1,2), 4 = (0,2), 5 = (0,1); 2D: 2 = (0,1).
-template <int DIM>
-__device__ __forceinline__ void strain_nonzeros(int al, const double* gr, int (&n)[3], double (&e)[3]) {
-  constexpr double ir2 = 0.70710678118654752440;
+template <int DIM, typename R>
+__device__ __forceinline__ void strain_nonzeros(int al, const R* gr, R ir2, int (&n)[3], R (&e)[3]) {
   n[0] = al;
   e[0] = gr[al];
   if (DIM == 2) {
     n[1] = 2; e[1] = gr[1 - al] * ir2;
-    n[2] = 0; e[2] = 0.0;
+    n[2] = 0; e[2] = gr[al] * R{};   // unused slot
   } else {
     const int o1 = al == 0 ? 1 : 0, o2 = al == 2 ? 1 : 2;      // the two other axes
     n[1] = (al + o1 == 1) ? 5 : ((al + o1 == 2) ? 4 : 3);
@@ -82,39 +96,26 @@ struct SetupGeo {
   double wdet, vol, gvol;
 };
 
-template <int DIM, bool TENSOR>
-__global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : 3)
-k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef,
-                              double* __restrict__ inv64, float* __restrict__ inv32, int pstride, DevStatus* st,
-                              const double* __restrict__ winv) {
-  using C = SetupCfg<DIM, TENSOR>;
-  constexpr int NP = C::NP, NB = C::NB, NPR = C::NPR, NM = C::NM, NC = C::NC, NSUB = C::NSUB;
-  extern __shared__ double sm[];
-  __shared__ double s_dinv;
-  double* M = sm;                    // packed upper triangle of the patch matrix, swept in place
-  double* pk = M + C::n_M;           // pivot column of the current sweep
-  double* qk = pk + C::n_pk;         // pivot column / pivot
-  double* gt = qk + C::n_qk;         // [q][a][k] physical gradient of phi_a at point q
-  double* bt = gt + C::n_gt;         // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
-  double* wq = bt + C::n_bt;         // [q] |J| w_q mu_q, or [q][NC] |J| w_q C_q, of the current cell
-  double* wpsi = wq + C::n_wq;       // [p][q] |J| w_q psi_p(q)
-  double* T = wpsi + C::n_wpsi;      // tensor: [q][j][be][m] = (C_q eps(phi_b(j) e_be))_m
-  unsigned char* rowof = reinterpret_cast<unsigned char*>(sm + C::n_dbl);   // row of every packed entry
+// The level's reference tables, in FP64 and stored in R (one CTA, once per setup):
+// wpsi [p][q] = |J| w_q psi_p(q); gt [q][a][k] = d phi_a / d x_k at point q;
+// bt [p][alpha][a] = -(psi_p, d phi_a / d x_alpha)_K.  Layout: gt | wpsi | bt.
+template <int DIM>
+struct SetupTab {
+  static constexpr int NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
+  static constexpr int n_gt = NB * NB * DIM, n_wpsi = NPR * NB, n_bt = NPR * DIM * NB;
+  static constexpr int total = n_gt + n_wpsi + n_bt;
+};
+
+template <int DIM, typename R>
+__global__ void k_setup_tables(SetupGeo sg, R* __restrict__ tab) {
+  using TB = SetupTab<DIM>;
+  constexpr int NB = TB::NB, NPR = TB::NPR;
+  __shared__ double gt[TB::n_gt], wpsi[TB::n_wpsi];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const long long v = blockIdx.x;
-  int vx, vy, vz;
-  vertex_coords<DIM>(g, v, vx, vy, vz);
-
-  const double* s = sg.s;
-  const double wdet = sg.wdet;
-
-  for (int e = tid; e < C::NPK; e += nt) M[e] = 0.0;
-  for (int i = tid; i < NP; i += nt)
-    for (int j = i; j < NP; ++j) rowof[tri_row(NP, i) + (j - i)] = (unsigned char)i;
   for (int e = tid; e < NPR * NB; e += nt) {
     const int p = e / NB, q = e % NB;
     const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-    const double w = wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
+    const double w = sg.wdet * Ref<double>::W(qx) * Ref<double>::W(qy) * (DIM == 3 ? Ref<double>::W(qz) : 1.0);
     wpsi[e] = p == 0 ? w : w * Ref<double>::G(p == 1 ? qx : (p == 2 ? qy : qz));
   }
   for (int e = tid; e < NB * NB; e += nt) {
@@ -123,17 +124,56 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
     const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
     const double bx = Ref<double>::B(qx, ax), by = Ref<double>::B(qy, ay);
     const double bz = DIM == 3 ? Ref<double>::B(qz, az) : 1.0;
-    gt[e * DIM + 0] = Ref<double>::D(qx, ax) * by * bz * s[0];
-    gt[e * DIM + 1] = bx * Ref<double>::D(qy, ay) * bz * s[1];
-    if (DIM == 3) gt[e * DIM + 2] = bx * by * Ref<double>::D(qz, az) * s[2];
+    gt[e * DIM + 0] = Ref<double>::D(qx, ax) * by * bz * sg.s[0];
+    gt[e * DIM + 1] = bx * Ref<double>::D(qy, ay) * bz * sg.s[1];
+    if (DIM == 3) gt[e * DIM + 2] = bx * by * Ref<double>::D(qz, az) * sg.s[2];
   }
   __syncthreads();
+  for (int e = tid; e < TB::n_gt; e += nt) tab[e] = RealOps<R>::from(gt[e]);
+  for (int e = tid; e < TB::n_wpsi; e += nt) tab[TB::n_gt + e] = RealOps<R>::from(wpsi[e]);
   for (int e = tid; e < NPR * DIM * NB; e += nt) {
     const int p = e / (DIM * NB), al = (e / NB) % DIM, a = e % NB;
     double acc = 0.0;
     for (int q = 0; q < NB; ++q) acc += wpsi[p * NB + q] * gt[(q * NB + a) * DIM + al];
-    bt[e] = -acc;
+    tab[TB::n_gt + TB::n_wpsi + e] = RealOps<R>::from(-acc);
   }
+}
+
+template <int DIM, bool TENSOR, typename R>
+__global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : 3)
+k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, const double* __restrict__ coef,
+              double* __restrict__ inv64, float* __restrict__ inv32, int pstride, DevStatus* st,
+              const double* __restrict__ winv) {
+  using C = SetupCfg<DIM, TENSOR>;
+  using O = RealOps<R>;
+  using TB = SetupTab<DIM>;
+  constexpr int NP = C::NP, NB = C::NB, NPR = C::NPR, NM = C::NM, NC = C::NC, NSUB = C::NSUB;
+  extern __shared__ double sm_raw[];
+  __shared__ R s_dinv;
+  __shared__ R s_winv[NPR * NPR];
+  R* sm = reinterpret_cast<R*>(sm_raw);
+  R* M = sm;                         // packed upper triangle of the patch matrix, swept in place
+  R* pk = M + C::n_M;                // pivot column of the current sweep
+  R* qk = pk + C::n_pk;              // pivot column / pivot
+  R* gt = qk + C::n_qk;              // [q][a][k] physical gradient of phi_a at point q
+  R* bt = gt + C::n_gt;              // [p][alpha][a]: B_K entries, -(psi_p, d phi_a / d x_alpha)_K
+  R* wq = bt + C::n_bt;              // [q] |J| w_q mu_q, or [q][NC] |J| w_q C_q, of the current cell
+  R* wpsi = wq + C::n_wq;            // [p][q] |J| w_q psi_p(q)
+  R* T = wpsi + C::n_wpsi;           // tensor: [q][j][be][m] = (C_q eps(phi_b(j) e_be))_m
+  unsigned char* rowof = reinterpret_cast<unsigned char*>(sm_raw + C::n_dbl);   // row of every packed entry
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long v = blockIdx.x;
+  int vx, vy, vz;
+  vertex_coords<DIM>(g, v, vx, vy, vz);
+  const R zero = O::from(0.0), one = O::from(1.0), three = O::from(3.0);
+  const R gamma = O::from(gamma_d), gvol = O::from(sg.gvol), ir2 = O::from(0.70710678118654752440);
+
+  for (int e = tid; e < C::NPK; e += nt) M[e] = zero;
+  for (int i = tid; i < NP; i += nt)
+    for (int j = i; j < NP; ++j) rowof[tri_row(NP, i) + (j - i)] = (unsigned char)i;
+  for (int e = tid; e < TB::n_gt; e += nt) gt[e] = tab[e];
+  for (int e = tid; e < TB::n_wpsi; e += nt) wpsi[e] = tab[TB::n_gt + e];
+  for (int e = tid; e < TB::n_bt; e += nt) bt[e] = tab[TB::n_gt + TB::n_wpsi + e];
 
   // contributions of the 2^d cells of the star
   for (int sc = 0; sc < NSUB; ++sc) {
@@ -144,7 +184,9 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
     __syncthreads();
     if (!valid) continue;
     const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
-    for (int e = tid; e < C::n_wq; e += nt) wq[e] = wpsi[TENSOR ? e / NC : e] * coef[cell * C::n_wq + e];
+    for (int e = tid; e < C::n_wq; e += nt) wq[e] = wpsi[TENSOR ? e / NC : e] * O::from(coef[cell * C::n_wq + e]);
+    if (winv)
+      for (int e = tid; e < NPR * NPR; e += nt) s_winv[e] = O::from(winv[cell * NPR * NPR + e]);
     __syncthreads();
     if constexpr (TENSOR) {
       // T[q][j][be] = C_q eps(phi_b e_be), b the cell-local node of sub-node j
@@ -154,12 +196,12 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
         sub_node<DIM>(j, sx, sy, sz, Q, b);
         // eps(phi_b e_be) in Mandel form has d nonzeros: slot be and the shear slots
         int n_[3];
-        double e_[3];
-        strain_nonzeros<DIM>(be, gt + (q * NB + b) * DIM, n_, e_);
-        const double* Cq = wq + q * NC;
-        double* t = T + e * NM;
+        R e_[3];
+        strain_nonzeros<DIM>(be, gt + (q * NB + b) * DIM, ir2, n_, e_);
+        const R* Cq = wq + q * NC;
+        R* t = T + e * NM;
         for (int m = 0; m < NM; ++m) {
-          double acc = 0.0;
+          R acc = zero;
 #pragma unroll
           for (int r = 0; r < DIM; ++r) {
             const int n = n_[r], lo = m < n ? m : n, hi = m < n ? n : m;
@@ -184,46 +226,46 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
       sub_node<DIM>(j, sx, sy, sz, Q, b);
       long long ndP, ndQ;
       if (!patch_node<DIM>(g, vx, vy, vz, P, ndP) || !patch_node<DIM>(g, vx, vy, vz, Q, ndQ)) continue;
-      double V[DIM][DIM];
+      R V[DIM][DIM];
 #pragma unroll
       for (int k = 0; k < DIM; ++k)
 #pragma unroll
-        for (int l = 0; l < DIM; ++l) V[k][l] = 0.0;
+        for (int l = 0; l < DIM; ++l) V[k][l] = zero;
       if constexpr (!TENSOR) {
         // 2 mu eps(phi_b e_be) : eps(phi_a e_al) = mu (d_be phi_a d_al phi_b + delta_(al,be) grad phi_a . grad phi_b)
-        double G[DIM][DIM];
+        R G[DIM][DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
 #pragma unroll
-          for (int l = 0; l < DIM; ++l) G[k][l] = 0.0;
+          for (int l = 0; l < DIM; ++l) G[k][l] = zero;
         for (int q = 0; q < NB; ++q) {
-          const double w = wq[q];
-          const double* ga = gt + (q * NB + a) * DIM;
-          const double* gb = gt + (q * NB + b) * DIM;
+          const R w = wq[q];
+          const R* ga = gt + (q * NB + a) * DIM;
+          const R* gb = gt + (q * NB + b) * DIM;
 #pragma unroll
           for (int k = 0; k < DIM; ++k) {
-            const double wa = w * ga[k];
+            const R wa = w * ga[k];
 #pragma unroll
             for (int l = 0; l < DIM; ++l) G[k][l] += wa * gb[l];
           }
         }
-        double tr = 0.0;
+        R tr = zero;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) tr += G[k][k];
 #pragma unroll
         for (int al = 0; al < DIM; ++al)
 #pragma unroll
-          for (int be = 0; be < DIM; ++be) V[al][be] = G[be][al] + (al == be ? tr : 0.0);
+          for (int be = 0; be < DIM; ++be) V[al][be] = al == be ? G[be][al] + tr : G[be][al];
       } else {
         // (C eps(phi_b e_be)) : eps(phi_a e_al) with the d nonzeros of eps(phi_a e_al)
         for (int q = 0; q < NB; ++q) {
           int n_[3];
-          double e_[3];
-          strain_nonzeros<DIM>(al0, gt + (q * NB + a) * DIM, n_, e_);
-          const double* t = T + (q * NSUB + j) * DIM * NM;
+          R e_[3];
+          strain_nonzeros<DIM>(al0, gt + (q * NB + a) * DIM, ir2, n_, e_);
+          const R* t = T + (q * NSUB + j) * DIM * NM;
 #pragma unroll
           for (int be = 0; be < DIM; ++be) {
-            double acc = 0.0;
+            R acc = zero;
 #pragma unroll
             for (int r = 0; r < DIM; ++r) acc += e_[r] * t[be * NM + n_[r]];
             V[al0][be] += acc;
@@ -237,16 +279,16 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
         for (int be = 0; be < DIM; ++be) {
           const int row = al * NB + P, col = be * NB + Q;
           if (i == j && row > col) continue;   // the diagonal block: upper triangle only
-          double alv = 0.0, val = V[al][be];
+          R alv = zero, val = V[al][be];
           if (winv) {   // gamma B_K^T W_K^-1 B_K with W = M_p(1/mu)
             for (int p = 0; p < NPR; ++p)
               for (int p2 = 0; p2 < NPR; ++p2)
-                alv += bt[(p * DIM + al) * NB + a] * winv[(cell * NPR + p) * NPR + p2] * bt[(p2 * DIM + be) * NB + b];
+                alv += bt[(p * DIM + al) * NB + a] * s_winv[p * NPR + p2] * bt[(p2 * DIM + be) * NB + b];
             val += gamma * alv;
           } else {      // W = M_p = |K| diag(1, 1/3, ..)
             for (int p = 0; p < NPR; ++p)
-              alv += (p == 0 ? 1.0 : 3.0) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
-            val += sg.gvol * alv;
+              alv += (p == 0 ? one : three) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
+            val += gvol * alv;
           }
           const int lo = row < col ? row : col, hi = row < col ? col : row;
           M[tri_row(NP, lo) + (hi - lo)] += val;
@@ -258,7 +300,7 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
   // identity rows for nodes outside the domain or on the Dirichlet boundary
   for (int i = tid; i < NP; i += nt) {
     long long nd;
-    if (!patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) M[tri_row(NP, i)] = 1.0;
+    if (!patch_node<DIM>(g, vx, vy, vz, i % NB, nd)) M[tri_row(NP, i)] = one;
   }
   __syncthreads();
 
@@ -268,17 +310,17 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
   // with the pivot row/column written in the same phase (disjoint entries).
   for (int k = 0; k < NP; ++k) {
     for (int i = tid; i < NP; i += nt)
-      pk[i] = (i == k) ? 0.0 : M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)];
+      pk[i] = (i == k) ? zero : M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)];
     if (tid == 0) {
-      double d = M[tri_row(NP, k)];
-      if (!(d > 0.0)) {
+      R d = M[tri_row(NP, k)];
+      if (!(d > 0.f)) {
         report(st, 4 /* ALS_ENOTSPD */, v);
-        d = 1.0;
+        d = one;
       }
-      s_dinv = 1.0 / d;
+      s_dinv = one / d;
     }
     __syncthreads();
-    const double dinv = s_dinv;
+    const R dinv = s_dinv;
     for (int i = tid; i < NP; i += nt) qk[i] = pk[i] * dinv;
     __syncthreads();
     for (int e = tid; e < C::NPK; e += nt) {
@@ -301,8 +343,8 @@ k_patch_setup(Geom g, double gamma, SetupGeo sg, const double* __restrict__ coef
     int t = 0;
     while (diag_start(NP, t + 1) <= e) ++t;
     const int i = e - diag_start(NP, t), j = i + t;
-    const double val = -M[tri_row(NP, i) + t];
-    if (inv64) inv64[v * pstride + e] = val;
-    if (inv32) inv32[v * pstride + BlockLayout(NP).index(i, j)] = (float)val;
+    const R val = -M[tri_row(NP, i) + t];
+    if (inv64) inv64[v * pstride + e] = O::to_double(val);
+    if (inv32) inv32[v * pstride + BlockLayout(NP).index(i, j)] = O::to_float(val);
   }
 }

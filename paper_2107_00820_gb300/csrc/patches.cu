@@ -17,6 +17,7 @@
 
 #include <algorithm>
 
+#include "df64.cuh"
 #include "level.h"
 #include "pdl.cuh"
 
@@ -636,11 +637,11 @@ static void set_tma_smem() {
   set_tma_smem_n<DIM, 3>();
 }
 
-template <int DIM, bool TENSOR>
+template <int DIM, bool TENSOR, typename R>
 static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
   using C = SetupCfg<DIM, TENSOR>;
   const size_t smem = C::smem;
-  cudaFuncSetAttribute(k_patch_setup<DIM, TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_patch_setup<DIM, TENSOR, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   SetupGeo sg{};
   sg.wdet = 1.0;
   sg.vol = 1.0;
@@ -649,21 +650,35 @@ static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevSt
     if (k < DIM) { sg.wdet *= 0.5 * L.g.h[k]; sg.vol *= L.g.h[k]; }
   }
   sg.gvol = gamma / sg.vol;
-  k_patch_setup<DIM, TENSOR><<<(unsigned)L.g.nverts, C::THREADS, smem, s>>>(
-      L.g, gamma, sg, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st, L.winv64);
-  count_launch(1);
+  R* tab = static_cast<R*>(L.setup_tab);
+  k_setup_tables<DIM, R><<<1, 256, 0, s>>>(sg, tab);
+  k_patch_setup<DIM, TENSOR, R><<<(unsigned)L.g.nverts, C::THREADS, smem, s>>>(
+      L.g, gamma, sg, tab, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st,
+      L.winv64);
+  count_launch(2);
 }
 
-void patch_setup(const LevelDev& L, double gamma, int store32, DevStatus* st, cudaStream_t s) {
+template <int DIM, bool TENSOR>
+static void patch_setup_arith(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st,
+                              cudaStream_t s) {
+  if (df64) patch_setup_impl<DIM, TENSOR, DF64>(L, gamma, store32, st, s);
+  else patch_setup_impl<DIM, TENSOR, double>(L, gamma, store32, st, s);
+}
+
+void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s) {
   // shared-memory limit of the FP32 patch kernel, set here, before any graph capture
   if (L.g.dim == 2) set_tma_smem<2>(); else set_tma_smem<3>();
   if (L.g.dim == 2) {
-    if (L.tensor) patch_setup_impl<2, true>(L, gamma, store32, st, s);
-    else patch_setup_impl<2, false>(L, gamma, store32, st, s);
+    if (L.tensor) patch_setup_arith<2, true>(L, gamma, store32, df64, st, s);
+    else patch_setup_arith<2, false>(L, gamma, store32, df64, st, s);
   } else {
-    if (L.tensor) patch_setup_impl<3, true>(L, gamma, store32, st, s);
-    else patch_setup_impl<3, false>(L, gamma, store32, st, s);
+    if (L.tensor) patch_setup_arith<3, true>(L, gamma, store32, df64, st, s);
+    else patch_setup_arith<3, false>(L, gamma, store32, df64, st, s);
   }
+}
+
+size_t setup_tab_bytes(int dim) {
+  return (size_t)(dim == 2 ? SetupTab<2>::total : SetupTab<3>::total) * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
