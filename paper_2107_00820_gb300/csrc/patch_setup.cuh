@@ -26,11 +26,13 @@
 template <typename R> struct RealOps;
 template <> struct RealOps<double> {
   static __device__ __forceinline__ double from(double d) { return d; }
+  static __device__ __forceinline__ double sub_prod(double m, double q, double p) { return m - q * p; }
   static __device__ __forceinline__ double to_double(double v) { return v; }
   static __device__ __forceinline__ float to_float(double v) { return (float)v; }
 };
 template <> struct RealOps<DF64> {
   static __device__ __forceinline__ DF64 from(double d) { return df_from(d); }
+  static __device__ __forceinline__ DF64 sub_prod(DF64 m, DF64 q, DF64 p) { return df_sub_prod(m, q, p); }
   static __device__ __forceinline__ double to_double(DF64 v) { return df_to_double(v); }
   static __device__ __forceinline__ float to_float(DF64 v) { return v.hi; }
 };
@@ -149,7 +151,6 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
   using TB = SetupTab<DIM>;
   constexpr int NP = C::NP, NB = C::NB, NPR = C::NPR, NM = C::NM, NC = C::NC, NSUB = C::NSUB;
   extern __shared__ double sm_raw[];
-  __shared__ R s_dinv;
   __shared__ R s_winv[NPR * NPR];
   R* sm = reinterpret_cast<R*>(sm_raw);
   R* M = sm;                         // packed upper triangle of the patch matrix, swept in place
@@ -304,31 +305,45 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
   }
   __syncthreads();
 
-  // symmetric sweep of every pivot in order: M -> -A_v^-1.  Three phases per pivot:
-  // the pivot column and 1/pivot (one division, thread 0); the scaled column; the
-  // rank-1 update over the packed entries (each thread a strided subset, full warps)
-  // with the pivot row/column written in the same phase (disjoint entries).
+  // symmetric sweep of every pivot in order: M -> -A_v^-1.  Two phases per pivot:
+  // threads i < NP read the pivot column, form 1/pivot themselves (no wait on one
+  // thread) and the scaled column; then every thread updates its contiguous segment
+  // of the packed entries (row and column tracked incrementally), and threads i < NP
+  // write the pivot row/column (entries the update skips).
+  constexpr int SEG = (C::NPK + C::THREADS - 1) / C::THREADS;
+  const int e0 = tid * SEG < C::NPK ? tid * SEG : C::NPK;
+  const int e1 = e0 + SEG < C::NPK ? e0 + SEG : C::NPK;
+  const int i0 = e0 < C::NPK ? (int)rowof[e0] : NP;
+  const int j0 = e0 < C::NPK ? e0 - tri_row(NP, i0) + i0 : NP;
   for (int k = 0; k < NP; ++k) {
-    for (int i = tid; i < NP; i += nt)
-      pk[i] = (i == k) ? zero : M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)];
-    if (tid == 0) {
+    R dinv = zero;
+    if (tid < NP) {
       R d = M[tri_row(NP, k)];
       if (!(d > 0.f)) {
-        report(st, 4 /* ALS_ENOTSPD */, v);
+        if (tid == 0) report(st, 4 /* ALS_ENOTSPD */, v);
         d = one;
       }
-      s_dinv = one / d;
+      dinv = one / d;
+      const int i = tid;
+      const R p = (i == k) ? zero : M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)];
+      pk[i] = p;
+      qk[i] = p * dinv;
     }
     __syncthreads();
-    const R dinv = s_dinv;
-    for (int i = tid; i < NP; i += nt) qk[i] = pk[i] * dinv;
-    __syncthreads();
-    for (int e = tid; e < C::NPK; e += nt) {
-      const int i = rowof[e];
-      const int j = e - tri_row(NP, i) + i;
-      if (i != k && j != k) M[e] -= qk[i] * pk[j];
+    {
+      int i = i0, j = j0;
+      R qi = i < NP ? qk[i] : zero;
+      for (int e = e0; e < e1; ++e) {
+        if (i != k && j != k) M[e] = O::sub_prod(M[e], qi, pk[j]);
+        if (++j == NP) {
+          ++i;
+          j = i;
+          if (i < NP) qi = qk[i];
+        }
+      }
     }
-    for (int i = tid; i < NP; i += nt) {
+    if (tid < NP) {
+      const int i = tid;
       if (i == k) M[tri_row(NP, k)] = -dinv;
       else M[i < k ? tri_row(NP, i) + (k - i) : tri_row(NP, k) + (i - k)] = qk[i];
     }
