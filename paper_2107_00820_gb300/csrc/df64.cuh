@@ -70,6 +70,21 @@ __device__ __forceinline__ DF64& operator+=(DF64& a, DF64 b) { return a = a + b;
 __device__ __forceinline__ DF64& operator-=(DF64& a, DF64 b) { return a = a - b; }
 __device__ __forceinline__ bool operator>(DF64 a, float b) { return a.hi > b || (a.hi == b && a.lo > 0.f); }
 
+// a + q p with one renormalisation (the accumulation form of df_sub_prod)
+__device__ __forceinline__ DF64 df_add_prod(DF64 a, DF64 q, DF64 p) {
+  const float ph = __fmul_rn(q.hi, p.hi);
+  float pl = __fmaf_rn(q.hi, p.hi, -ph);
+  pl = __fmaf_rn(q.hi, p.lo, pl);
+  pl = __fmaf_rn(q.lo, p.hi, pl);
+  const DF64 s = df_two_sum(a.hi, ph);
+  return df_quick_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, pl), a.lo));
+}
+// a + b with one renormalisation (error a few units of 2^-48 relative to |a| + |b|)
+__device__ __forceinline__ DF64 df_add_fast(DF64 a, DF64 b) {
+  const DF64 s = df_two_sum(a.hi, b.hi);
+  return df_quick_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, b.lo), a.lo));
+}
+
 // m - q p with one renormalisation: the exact product of the high parts plus the
 // cross terms, one TwoSum of the high parts, the low parts added once.  The error
 // is a few units of 2^-48 relative to |m| + |q p| (not to the result), which is the

@@ -27,12 +27,16 @@ template <typename R> struct RealOps;
 template <> struct RealOps<double> {
   static __device__ __forceinline__ double from(double d) { return d; }
   static __device__ __forceinline__ double sub_prod(double m, double q, double p) { return m - q * p; }
+  static __device__ __forceinline__ double add_prod(double a, double q, double p) { return a + q * p; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
   static __device__ __forceinline__ double to_double(double v) { return v; }
   static __device__ __forceinline__ float to_float(double v) { return (float)v; }
 };
 template <> struct RealOps<DF64> {
   static __device__ __forceinline__ DF64 from(double d) { return df_from(d); }
   static __device__ __forceinline__ DF64 sub_prod(DF64 m, DF64 q, DF64 p) { return df_sub_prod(m, q, p); }
+  static __device__ __forceinline__ DF64 add_prod(DF64 a, DF64 q, DF64 p) { return df_add_prod(a, q, p); }
+  static __device__ __forceinline__ DF64 add(DF64 a, DF64 b) { return df_add_fast(a, b); }
   static __device__ __forceinline__ double to_double(DF64 v) { return df_to_double(v); }
   static __device__ __forceinline__ float to_float(DF64 v) { return v.hi; }
 };
@@ -206,7 +210,7 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
 #pragma unroll
           for (int r = 0; r < DIM; ++r) {
             const int n = n_[r], lo = m < n ? m : n, hi = m < n ? n : m;
-            acc += Cq[lo * NM - (lo * (lo - 1)) / 2 + (hi - lo)] * e_[r];
+            acc = O::add_prod(acc, Cq[lo * NM - (lo * (lo - 1)) / 2 + (hi - lo)], e_[r]);
           }
           t[m] = acc;
         }
@@ -247,16 +251,16 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
           for (int k = 0; k < DIM; ++k) {
             const R wa = w * ga[k];
 #pragma unroll
-            for (int l = 0; l < DIM; ++l) G[k][l] += wa * gb[l];
+            for (int l = 0; l < DIM; ++l) G[k][l] = O::add_prod(G[k][l], wa, gb[l]);
           }
         }
         R tr = zero;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) tr += G[k][k];
+        for (int k = 0; k < DIM; ++k) tr = O::add(tr, G[k][k]);
 #pragma unroll
         for (int al = 0; al < DIM; ++al)
 #pragma unroll
-          for (int be = 0; be < DIM; ++be) V[al][be] = al == be ? G[be][al] + tr : G[be][al];
+          for (int be = 0; be < DIM; ++be) V[al][be] = al == be ? O::add(G[be][al], tr) : G[be][al];
       } else {
         // (C eps(phi_b e_be)) : eps(phi_a e_al) with the d nonzeros of eps(phi_a e_al)
         for (int q = 0; q < NB; ++q) {
@@ -268,8 +272,8 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
           for (int be = 0; be < DIM; ++be) {
             R acc = zero;
 #pragma unroll
-            for (int r = 0; r < DIM; ++r) acc += e_[r] * t[be * NM + n_[r]];
-            V[al0][be] += acc;
+            for (int r = 0; r < DIM; ++r) acc = O::add_prod(acc, e_[r], t[be * NM + n_[r]]);
+            V[al0][be] = O::add(V[al0][be], acc);
           }
         }
       }
@@ -284,15 +288,15 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
           if (winv) {   // gamma B_K^T W_K^-1 B_K with W = M_p(1/mu)
             for (int p = 0; p < NPR; ++p)
               for (int p2 = 0; p2 < NPR; ++p2)
-                alv += bt[(p * DIM + al) * NB + a] * s_winv[p * NPR + p2] * bt[(p2 * DIM + be) * NB + b];
-            val += gamma * alv;
+                alv = O::add_prod(alv, bt[(p * DIM + al) * NB + a] * s_winv[p * NPR + p2], bt[(p2 * DIM + be) * NB + b]);
+            val = O::add_prod(val, gamma, alv);
           } else {      // W = M_p = |K| diag(1, 1/3, ..)
             for (int p = 0; p < NPR; ++p)
-              alv += (p == 0 ? one : three) * bt[(p * DIM + al) * NB + a] * bt[(p * DIM + be) * NB + b];
-            val += gvol * alv;
+              alv = O::add_prod(alv, (p == 0 ? one : three) * bt[(p * DIM + al) * NB + a], bt[(p * DIM + be) * NB + b]);
+            val = O::add_prod(val, gvol, alv);
           }
           const int lo = row < col ? row : col, hi = row < col ? col : row;
-          M[tri_row(NP, lo) + (hi - lo)] += val;
+          M[tri_row(NP, lo) + (hi - lo)] = O::add(M[tri_row(NP, lo) + (hi - lo)], val);
         }
       }
     }
