@@ -656,7 +656,7 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
       ALS_TRY(cuda_check(c, "patch setup"));
     }
   }
-  coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream);
+  coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream, c->opt.mode == ALS_MODE_MIXED ? 1 : 0);
   ALS_TRY(cuda_check(c, "coarse setup"));
   const LevelDev& F = c->lev[c->L - 1];
   schur_setup(F.g, c->gamma, F.mu64, c->schur, c->st, c->stream, c->opt.schur == ALS_SCHUR_P2 ? 1 : 0);

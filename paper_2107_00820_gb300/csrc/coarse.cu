@@ -9,6 +9,7 @@
 // the pivot row/column set to U (A_KK to -S).  After every block the matrix holds
 // -A^-1.  A is SPD, so every pivot is a Schur complement and positive.  Each
 // V-cycle then applies the stored inverse as a dense matrix-vector product.
+#include "df64.cuh"
 #include "krylov.h"
 #include "level.h"
 #include "pdl.cuh"
@@ -41,23 +42,30 @@ __global__ void k_unit_columns(Geom g, int nfree, long long len, double* __restr
 
 constexpr int CT = 64;   // tile width of the blocked sweep
 
+// The blocked sweep runs in R = FP64, or DF64 (FP32 pairs, about 48 bits, see
+// df64.cuh) when only the FP32 cycle needs the inverse; the buffers A, P, U, S hold
+// elements of R (8 bytes either way) and the inverse is written in FP64.
+
 // column `col` of A is A e_col; stored row-major in the padded matrix (npad columns)
+template <typename R>
 __global__ void k_extract(Geom g, int nfree, int npad, long long len, const double* __restrict__ Y,
-                          double* __restrict__ A) {
+                          R* __restrict__ A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nfree * nfree) return;
   const int col = (int)(t / nfree), row = (int)(t % nfree);
-  A[(long long)row * npad + col] = Y[(long long)col * len + free_dof(g, row)];
+  A[(long long)row * npad + col] = RealOps<R>::from(Y[(long long)col * len + free_dof(g, row)]);
 }
 
 // identity on the padding rows/columns (their blocks stay decoupled)
-__global__ void k_pad_diag(int nfree, int npad, double* __restrict__ A) {
+template <typename R>
+__global__ void k_pad_diag(int nfree, int npad, R* __restrict__ A) {
   const int i = nfree + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < npad) A[(long long)i * npad + i] = 1.0;
+  if (i < npad) A[(long long)i * npad + i] = RealOps<R>::from(1.0);
 }
 
 // P[r][c] = A(r, p*CT + c) from the upper triangle of tiles
-__global__ void k_panel_gather(int npad, int p, const double* __restrict__ A, double* __restrict__ P) {
+template <typename R>
+__global__ void k_panel_gather(int npad, int p, const R* __restrict__ A, R* __restrict__ P) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)npad * CT) return;
   const int r = (int)(t / CT), c = (int)(t % CT), k = p * CT + c;
@@ -66,28 +74,34 @@ __global__ void k_panel_gather(int npad, int p, const double* __restrict__ A, do
 }
 
 // S = D^-1 for the diagonal block D = P[p*CT .. p*CT+CT) by the symmetric sweep
-// in shared memory (one CTA); a non-positive pivot is reported as ALS_ENOTSPD
-__global__ void __launch_bounds__(256) k_diag_sweep(int p, const double* __restrict__ P, double* __restrict__ S,
+// in shared memory (one CTA); a non-positive pivot is reported as ALS_ENOTSPD.
+// Every thread of the pivot column forms 1/pivot itself (no wait on one thread).
+template <typename R>
+__global__ void __launch_bounds__(256) k_diag_sweep(int p, const R* __restrict__ P, R* __restrict__ S,
                                                     DevStatus* st) {
-  __shared__ double D[CT][CT + 1];
-  __shared__ double col[CT], q[CT];
-  __shared__ double dinv;
+  using O = RealOps<R>;
+  __shared__ R D[CT][CT + 1];
+  __shared__ R col[CT], q[CT];
   const int tid = threadIdx.x;
+  const R zero = O::from(0.0), one = O::from(1.0);
   for (int e = tid; e < CT * CT; e += blockDim.x) D[e / CT][e % CT] = P[(long long)(p * CT + e / CT) * CT + e % CT];
   __syncthreads();
   for (int kk = 0; kk < CT; ++kk) {
-    if (tid < CT) col[tid] = tid == kk ? 0.0 : D[tid][kk];
-    if (tid == 0) {
-      double d = D[kk][kk];
-      if (!(d > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, -1 - (long long)(p * CT + kk)); d = 1.0; }
-      dinv = 1.0 / d;
+    R d = D[kk][kk];
+    if (!(d > 0.f)) {
+      if (tid == 0) report(st, 4 /* ALS_ENOTSPD */, -1 - (long long)(p * CT + kk));
+      d = one;
     }
-    __syncthreads();
-    if (tid < CT) q[tid] = col[tid] * dinv;
+    const R dinv = one / d;
+    if (tid < CT) {
+      const R c = tid == kk ? zero : D[tid][kk];
+      col[tid] = c;
+      q[tid] = c * dinv;
+    }
     __syncthreads();
     for (int e = tid; e < CT * CT; e += blockDim.x) {
       const int i = e / CT, j = e % CT;
-      if (i != kk && j != kk) D[i][j] -= q[i] * col[j];
+      if (i != kk && j != kk) D[i][j] = O::sub_prod(D[i][j], q[i], col[j]);
       else if (i == kk && j == kk) D[i][j] = -dinv;
       else D[i][j] = q[i == kk ? j : i];
     }
@@ -97,14 +111,16 @@ __global__ void __launch_bounds__(256) k_diag_sweep(int p, const double* __restr
 }
 
 // 64x64 output tile out = X_tile * Y (Y 64x64 row-major) or X_tile * Y_tile^T, 4x4 per thread
-__device__ __forceinline__ void tile_mma(const double (*Xs)[CT + 1], const double (*Ys)[CT + 1], bool yt,
-                                         double (&acc)[4][4], int r0, int c0) {
+template <typename R>
+__device__ __forceinline__ void tile_mma(const R (*Xs)[CT + 1], const R (*Ys)[CT + 1], bool yt, R (&acc)[4][4],
+                                         int r0, int c0) {
+  using O = RealOps<R>;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = O::from(0.0);
   for (int k = 0; k < CT; ++k) {
-    double a[4], b[4];
+    R a[4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) a[i] = Xs[r0 + 16 * i][k];
 #pragma unroll
@@ -112,16 +128,17 @@ __device__ __forceinline__ void tile_mma(const double (*Xs)[CT + 1], const doubl
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      for (int j = 0; j < 4; ++j) acc[i][j] = O::add_prod(acc[i][j], a[i], b[j]);
   }
 }
 
 // U[rows of tile blockIdx.x] = P[those rows] S
-__global__ void __launch_bounds__(256) k_panel_mul(const double* __restrict__ P, const double* __restrict__ S,
-                                                   double* __restrict__ U) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_panel_mul(const R* __restrict__ P, const R* __restrict__ S,
+                                                   R* __restrict__ U) {
   extern __shared__ double smc[];
-  double (*Ps)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc);
-  double (*Ss)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc + CT * (CT + 1));
+  R (*Ps)[CT + 1] = reinterpret_cast<R (*)[CT + 1]>(smc);
+  R (*Ss)[CT + 1] = reinterpret_cast<R (*)[CT + 1]>(smc + CT * (CT + 1));
   const int tid = threadIdx.x;
   const long long r0 = (long long)blockIdx.x * CT;
   for (int e = tid; e < CT * CT; e += blockDim.x) {
@@ -129,9 +146,9 @@ __global__ void __launch_bounds__(256) k_panel_mul(const double* __restrict__ P,
     Ss[e / CT][e % CT] = S[e];
   }
   __syncthreads();
-  double acc[4][4];
+  R acc[4][4];
   const int tr = tid / 16, tc = tid % 16;
-  tile_mma(Ps, Ss, false, acc, tr, tc);
+  tile_mma<R>(Ps, Ss, false, acc, tr, tc);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -139,34 +156,38 @@ __global__ void __launch_bounds__(256) k_panel_mul(const double* __restrict__ P,
 }
 
 // A[I][J] -= P[I] U[J]^T for the upper tiles I <= J outside the pivot row/column p
-__global__ void __launch_bounds__(256) k_sym_update(int npad, int nt, int p, const double* __restrict__ P,
-                                                    const double* __restrict__ U, double* __restrict__ A) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_sym_update(int npad, int nt, int p, const R* __restrict__ P,
+                                                    const R* __restrict__ U, R* __restrict__ A) {
   int b = blockIdx.x, I = 0;
   while (b >= nt - I) { b -= nt - I; ++I; }
   const int J = I + b;
   if (I == p || J == p) return;
   extern __shared__ double smc[];
-  double (*Ps)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc);
-  double (*Us)[CT + 1] = reinterpret_cast<double (*)[CT + 1]>(smc + CT * (CT + 1));
+  R (*Ps)[CT + 1] = reinterpret_cast<R (*)[CT + 1]>(smc);
+  R (*Us)[CT + 1] = reinterpret_cast<R (*)[CT + 1]>(smc + CT * (CT + 1));
   const int tid = threadIdx.x;
   for (int e = tid; e < CT * CT; e += blockDim.x) {
     Ps[e / CT][e % CT] = P[((long long)I * CT + e / CT) * CT + e % CT];
     Us[e / CT][e % CT] = U[((long long)J * CT + e / CT) * CT + e % CT];
   }
   __syncthreads();
-  double acc[4][4];
+  R acc[4][4];
   const int tr = tid / 16, tc = tid % 16;
-  tile_mma(Ps, Us, true, acc, tr, tc);
+  tile_mma<R>(Ps, Us, true, acc, tr, tc);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      A[((long long)I * CT + tr + 16 * i) * npad + (long long)J * CT + tc + 16 * j] -= acc[i][j];
+    for (int j = 0; j < 4; ++j) {
+      R& a = A[((long long)I * CT + tr + 16 * i) * npad + (long long)J * CT + tc + 16 * j];
+      a = RealOps<R>::add(a, -acc[i][j]);
+    }
 }
 
 // pivot row/column p of the upper triangle: A(r, K) = U(r) for r outside K, A_KK = -S
-__global__ void k_panel_write(int npad, int p, const double* __restrict__ U, const double* __restrict__ S,
-                              double* __restrict__ A) {
+template <typename R>
+__global__ void k_panel_write(int npad, int p, const R* __restrict__ U, const R* __restrict__ S,
+                              R* __restrict__ A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)npad * CT) return;
   const int r = (int)(t / CT), c = (int)(t % CT), k = p * CT + c, I = r / CT;
@@ -175,12 +196,13 @@ __global__ void k_panel_write(int npad, int p, const double* __restrict__ U, con
   else A[(long long)r * npad + k] = -S[(r - p * CT) * CT + c];
 }
 
-// inv = -(swept matrix) on the free block, both triangles
-__global__ void k_finalize(int nfree, int npad, const double* __restrict__ A, double* __restrict__ inv) {
+// inv = -(swept matrix) on the free block, both triangles, in FP64
+template <typename R>
+__global__ void k_finalize(int nfree, int npad, const R* __restrict__ A, double* __restrict__ inv) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nfree * nfree) return;
   const int r = (int)(t / nfree), c = (int)(t % nfree);
-  inv[t] = -(r <= c ? A[(long long)r * npad + c] : A[(long long)c * npad + r]);
+  inv[t] = -RealOps<R>::to_double(r <= c ? A[(long long)r * npad + c] : A[(long long)c * npad + r]);
 }
 
 int coarse_alloc(const LevelDev& L, CoarseDev* C) {
@@ -200,33 +222,47 @@ int coarse_alloc(const LevelDev& L, CoarseDev* C) {
   return 0;
 }
 
-// Forms and factors the coarsest A_gamma with the current coefficients (stream-ordered).
-void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, cudaStream_t s) {
+template <typename R>
+static void coarse_sweep(const LevelDev& L, CoarseDev* C, DevStatus* st, cudaStream_t s) {
   const Geom& g = L.g;
   const int nfree = C->nfree;
   const long long len = g.N * g.dim;
-  double *X = C->X, *Y = C->Y, *A = C->A;
-  const long long tot = (long long)nfree * len;
-  k_unit_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nfree, len, X);
-  op_apply_multi(L, gamma, X, Y, nfree, len, s);
+  R* A = reinterpret_cast<R*>(C->A);
+  R* P = reinterpret_cast<R*>(C->P);
+  R* U = reinterpret_cast<R*>(C->U);
+  R* S = reinterpret_cast<R*>(C->S);
   const long long tot2 = (long long)nfree * nfree;
   const int npad = C->npad, nt = npad / CT;
-  cudaMemsetAsync(A, 0, sizeof(double) * npad * npad, s);
-  if (npad > nfree) k_pad_diag<<<(npad - nfree + 127) / 128, 128, 0, s>>>(nfree, npad, A);
-  k_extract<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(g, nfree, npad, len, Y, A);
-  const size_t smem2 = sizeof(double) * 2 * CT * (CT + 1);
-  cudaFuncSetAttribute(k_panel_mul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-  cudaFuncSetAttribute(k_sym_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  cudaMemsetAsync(A, 0, sizeof(R) * npad * npad, s);   // all-zero bits are 0 in both types
+  if (npad > nfree) k_pad_diag<R><<<(npad - nfree + 127) / 128, 128, 0, s>>>(nfree, npad, A);
+  k_extract<R><<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(g, nfree, npad, len, C->Y, A);
+  const size_t smem2 = sizeof(R) * 2 * CT * (CT + 1);
+  cudaFuncSetAttribute(k_panel_mul<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  cudaFuncSetAttribute(k_sym_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   const unsigned pblocks = (unsigned)(((long long)npad * CT + 255) / 256);
   for (int p = 0; p < nt; ++p) {
-    k_panel_gather<<<pblocks, 256, 0, s>>>(npad, p, A, C->P);
-    k_diag_sweep<<<1, 256, 0, s>>>(p, C->P, C->S, st);
-    k_panel_mul<<<nt, 256, smem2, s>>>(C->P, C->S, C->U);
-    k_sym_update<<<nt * (nt + 1) / 2, 256, smem2, s>>>(npad, nt, p, C->P, C->U, A);
-    k_panel_write<<<pblocks, 256, 0, s>>>(npad, p, C->U, C->S, A);
+    k_panel_gather<R><<<pblocks, 256, 0, s>>>(npad, p, A, P);
+    k_diag_sweep<R><<<1, 256, 0, s>>>(p, P, S, st);
+    k_panel_mul<R><<<nt, 256, smem2, s>>>(P, S, U);
+    k_sym_update<R><<<nt * (nt + 1) / 2, 256, smem2, s>>>(npad, nt, p, P, U, A);
+    k_panel_write<R><<<pblocks, 256, 0, s>>>(npad, p, U, S, A);
   }
-  k_finalize<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(nfree, npad, A, C->inv);
-  count_launch(3 + (npad > nfree ? 1 : 0) + 5LL * nt);
+  k_finalize<R><<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(nfree, npad, A, C->inv);
+  count_launch(2 + (npad > nfree ? 1 : 0) + 5LL * nt);
+}
+
+// Forms and factors the coarsest A_gamma with the current coefficients (stream-ordered).
+// df64: the sweep in double-float arithmetic (the inverse then carries about 48 bits).
+void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, cudaStream_t s, int df64) {
+  const Geom& g = L.g;
+  const int nfree = C->nfree;
+  const long long len = g.N * g.dim;
+  const long long tot = (long long)nfree * len;
+  k_unit_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nfree, len, C->X);
+  op_apply_multi(L, gamma, C->X, C->Y, nfree, len, s);
+  count_launch(1);
+  if (df64) coarse_sweep<DF64>(L, C, st, s);
+  else coarse_sweep<double>(L, C, st, s);
 }
 
 // 32-bit form of free_dof for the apply (vector lengths stay below 2^31)

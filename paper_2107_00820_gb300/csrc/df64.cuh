@@ -98,4 +98,25 @@ __device__ __forceinline__ DF64 df_sub_prod(DF64 m, DF64 q, DF64 p) {
   return df_quick_two_sum(s.hi, __fadd_rn(__fsub_rn(s.lo, pl), m.lo));
 }
 
+// The two arithmetic types of the setup kernels, FP64 and DF64, behind one interface:
+// conversions from FP64 inputs and to FP64/FP32 outputs, and the fused forms
+// a + q p, m - q p and a + b (FP64: contracted to FMAs; DF64: one renormalisation).
+template <typename R> struct RealOps;
+template <> struct RealOps<double> {
+  static __device__ __forceinline__ double from(double d) { return d; }
+  static __device__ __forceinline__ double sub_prod(double m, double q, double p) { return m - q * p; }
+  static __device__ __forceinline__ double add_prod(double a, double q, double p) { return a + q * p; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+  static __device__ __forceinline__ float to_float(double v) { return (float)v; }
+};
+template <> struct RealOps<DF64> {
+  static __device__ __forceinline__ DF64 from(double d) { return df_from(d); }
+  static __device__ __forceinline__ DF64 sub_prod(DF64 m, DF64 q, DF64 p) { return df_sub_prod(m, q, p); }
+  static __device__ __forceinline__ DF64 add_prod(DF64 a, DF64 q, DF64 p) { return df_add_prod(a, q, p); }
+  static __device__ __forceinline__ DF64 add(DF64 a, DF64 b) { return df_add_fast(a, b); }
+  static __device__ __forceinline__ double to_double(DF64 v) { return df_to_double(v); }
+  static __device__ __forceinline__ float to_float(DF64 v) { return v.hi; }
+};
+
 }  // namespace als

@@ -29,7 +29,9 @@ struct CoarseDev {
   double* S = nullptr;     // 64 x 64: that inverse
 };
 int coarse_alloc(const struct LevelDev& L, CoarseDev* C);
-void coarse_setup(const struct LevelDev& L, double gamma, CoarseDev* C, struct DevStatus* st, cudaStream_t s);
+// df64: the sweep in double-float arithmetic (mixed mode), else FP64
+void coarse_setup(const struct LevelDev& L, double gamma, CoarseDev* C, struct DevStatus* st, cudaStream_t s,
+                  int df64);
 void coarse_apply(const struct LevelDev& L, const CoarseDev& C, int prec, const void* b, void* x, cudaStream_t s);
 void coarse_free(CoarseDev* C);
 

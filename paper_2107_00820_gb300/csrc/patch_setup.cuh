@@ -22,25 +22,6 @@
 // per pivot per block, no redundant sums.
 #pragma once
 
-// the two arithmetic types of the setup: conversions to and from FP64 inputs/outputs
-template <typename R> struct RealOps;
-template <> struct RealOps<double> {
-  static __device__ __forceinline__ double from(double d) { return d; }
-  static __device__ __forceinline__ double sub_prod(double m, double q, double p) { return m - q * p; }
-  static __device__ __forceinline__ double add_prod(double a, double q, double p) { return a + q * p; }
-  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-  static __device__ __forceinline__ double to_double(double v) { return v; }
-  static __device__ __forceinline__ float to_float(double v) { return (float)v; }
-};
-template <> struct RealOps<DF64> {
-  static __device__ __forceinline__ DF64 from(double d) { return df_from(d); }
-  static __device__ __forceinline__ DF64 sub_prod(DF64 m, DF64 q, DF64 p) { return df_sub_prod(m, q, p); }
-  static __device__ __forceinline__ DF64 add_prod(DF64 a, DF64 q, DF64 p) { return df_add_prod(a, q, p); }
-  static __device__ __forceinline__ DF64 add(DF64 a, DF64 b) { return df_add_fast(a, b); }
-  static __device__ __forceinline__ double to_double(DF64 v) { return df_to_double(v); }
-  static __device__ __forceinline__ float to_float(DF64 v) { return v.hi; }
-};
-
 __host__ __device__ constexpr int tri_row(int np, int i) { return i * np - (i * (i - 1)) / 2; }
 
 template <int DIM, bool TENSOR>
