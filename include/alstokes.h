@@ -181,11 +181,15 @@ als_status als_solve(als_ctx* ctx, const double* f_qp, const double* u_bc, const
 als_status als_update_coefficients(als_ctx* ctx, const als_coeff* coeff);
 
 /* Live timing of the finest-level vertex-star patch kernel inside V-cycles:
- * als_profile(ctx, 1) makes every subsequent V-cycle record a CUDA event
- * pair around each such launch on the stream it runs on (the V-cycle graph is
- * recaptured with event-record nodes); als_profile_read() returns the summed
- * kernel time in ms and the number of launches measured since the previous
- * read, and restarts the accumulation.  als_profile(ctx, 0) turns it off. */
+ * als_profile(ctx, 1) makes subsequent V-cycles record a CUDA event pair around
+ * each such launch on the stream it runs on.  With graph replay (the default) the
+ * cycle is captured a second time with event-record nodes and that graph is
+ * replayed for one cycle in every 8 (the first after als_profile and every 8th
+ * after it); the other cycles replay the plain graph, so timing barely slows the
+ * run it measures.  Without graphs (ALS_NO_GRAPH=1) every cycle is timed.
+ * als_profile_read() returns the summed kernel time in ms and the number of
+ * launches measured since the previous read, and restarts the accumulation.
+ * als_profile(ctx, 0) turns it off. */
 als_status als_profile(als_ctx* ctx, int on);
 als_status als_profile_read(als_ctx* ctx, double* total_ms, long long* launches);
 /* As als_profile_read for one kernel class: kind 0 = the finest-level star-patch

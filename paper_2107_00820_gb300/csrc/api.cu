@@ -31,6 +31,11 @@ struct MGWork {
   cudaGraph_t graph_tmpl = nullptr;
   cudaGraphExec_t graph = nullptr;
   long long graph_kernels = 0;
+  // while kernels are timed: the same cycle with event-record nodes, replayed for one
+  // cycle in every kProfEvery (the others replay the plain graph)
+  cudaGraph_t graph_prof_tmpl = nullptr;
+  cudaGraphExec_t graph_prof = nullptr;
+  long long replays = 0;
 };
 
 // Live timing of finest-level kernels inside the V-cycle: kind 0 = the star-patch
@@ -201,21 +206,27 @@ void free_graphs(als_ctx* c) {
   for (MGWork* w : {&c->w64, &c->w32}) {
     if (w->graph) cudaGraphExecDestroy(w->graph);
     if (w->graph_tmpl) cudaGraphDestroy(w->graph_tmpl);
+    if (w->graph_prof) cudaGraphExecDestroy(w->graph_prof);
+    if (w->graph_prof_tmpl) cudaGraphDestroy(w->graph_prof_tmpl);
     w->graph = nullptr;
     w->graph_tmpl = nullptr;
+    w->graph_prof = nullptr;
+    w->graph_prof_tmpl = nullptr;
+    w->replays = 0;
   }
   c->prof.nodes32.clear();
   c->prof.nodes64.clear();
 }
 
 static thread_local bool t_capturing = false;
+static thread_local bool t_capture_events = false;   // the graph being captured gets event-record nodes
 cudaEvent_t prof_take(als_ctx* c);
 
 // events for the k-th finest-level patch launch of the V-cycle being issued:
 // placeholders while a graph is captured, pool events otherwise
 void prof_events(als_ctx* c, int& counter, cudaEvent_t& e0, cudaEvent_t& e1, int kind = 0) {
   e0 = e1 = nullptr;
-  if (!c->prof.on) return;
+  if (!c->prof.on || (t_capturing && !t_capture_events)) return;
   if (!t_capturing) {
     e0 = prof_take(c);
     e1 = prof_take(c);
@@ -404,6 +415,30 @@ void tune_patches(als_ctx* c, MGWork& w) {
   }
 }
 
+// Timing of the finest-level kernels samples one cycle in every kProfEvery: the
+// event-record nodes split the programmatic-launch chain and every replay of the
+// timed graph re-points them, so timing every cycle would slow the cycles it times.
+constexpr long long kProfEvery = 8;
+
+// capture one cycle of this precision (with_events: with the event-record nodes of
+// the timed kernels) and instantiate it
+static als_status capture_cycle(als_ctx* c, MGWork& w, bool with_events, cudaGraph_t* tmpl, cudaGraphExec_t* exec) {
+  t_prof_counter = 0;
+  const long long c0 = launch_count();
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return cuda_check(c, "begin capture");
+  t_capturing = true;
+  t_capture_events = with_events;
+  cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
+  t_capturing = false;
+  t_capture_events = false;
+  if (cudaStreamEndCapture(c->stream, tmpl) != cudaSuccess) return cuda_check(c, "end capture");
+  w.graph_kernels = launch_count() - c0;
+  count_launch(-w.graph_kernels);
+  if (cudaGraphInstantiate(exec, *tmpl, 0) != cudaSuccess) return cuda_check(c, "graph instantiate");
+  return ALS_OK;
+}
+
 // capture the cycle of this precision as a graph (once); nothing is launched
 als_status ensure_graph(als_ctx* c, MGWork& w) {
   Prof& pf = c->prof;
@@ -411,38 +446,29 @@ als_status ensure_graph(als_ctx* c, MGWork& w) {
   std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
   std::vector<int>& kinds = w.prec == PREC_F64 ? pf.kinds64 : pf.kinds32;
   if (!w.graph) {
-    t_prof_counter = 0;
-    const long long c0 = launch_count();
-    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return cuda_check(c, "begin capture");
-    t_capturing = true;
-    cycle_level(c, w, c->L - 1, c->opt.cycle == ALS_CYCLE_F, true);
-    t_capturing = false;
-    if (cudaStreamEndCapture(c->stream, &w.graph_tmpl) != cudaSuccess) return cuda_check(c, "end capture");
-    w.graph_kernels = launch_count() - c0;
-    count_launch(-w.graph_kernels);
+    ALS_TRY(capture_cycle(c, w, false, &w.graph_tmpl, &w.graph));
     nodes.clear();
-    if (pf.on) {
-      // map every event-record node to its slot (capture order is the slot order)
-      const int nslots = 2 * t_prof_counter;
-      nodes.assign(nslots, nullptr);
-      kinds.assign(pf.slot_kind.begin(), pf.slot_kind.begin() + t_prof_counter);
-      size_t nn = 0;
-      cudaGraphGetNodes(w.graph_tmpl, nullptr, &nn);
-      std::vector<cudaGraphNode_t> all(nn);
-      cudaGraphGetNodes(w.graph_tmpl, all.data(), &nn);
-      for (cudaGraphNode_t nd : all) {
-        cudaGraphNodeType ty;
-        cudaGraphNodeGetType(nd, &ty);
-        if (ty != cudaGraphNodeTypeEventRecord) continue;
-        cudaEvent_t ev;
-        cudaGraphEventRecordNodeGetEvent(nd, &ev);
-        for (int i = 0; i < nslots; ++i)
-          if (pf.slots[i] == ev) nodes[i] = nd;
-      }
+    w.replays = 0;
+  }
+  if (pf.on && !w.graph_prof) {
+    ALS_TRY(capture_cycle(c, w, true, &w.graph_prof_tmpl, &w.graph_prof));
+    // map every event-record node to its slot (capture order is the slot order)
+    const int nslots = 2 * t_prof_counter;
+    nodes.assign(nslots, nullptr);
+    kinds.assign(pf.slot_kind.begin(), pf.slot_kind.begin() + t_prof_counter);
+    size_t nn = 0;
+    cudaGraphGetNodes(w.graph_prof_tmpl, nullptr, &nn);
+    std::vector<cudaGraphNode_t> all(nn);
+    cudaGraphGetNodes(w.graph_prof_tmpl, all.data(), &nn);
+    for (cudaGraphNode_t nd : all) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev;
+      cudaGraphEventRecordNodeGetEvent(nd, &ev);
+      for (int i = 0; i < nslots; ++i)
+        if (pf.slots[i] == ev) nodes[i] = nd;
     }
-    cudaError_t e = cudaGraphInstantiate(&w.graph, w.graph_tmpl, 0);
-    if (e != cudaSuccess) return cuda_check(c, "graph instantiate");
   }
   return ALS_OK;
 }
@@ -458,16 +484,19 @@ als_status run_vcycle(als_ctx* c, MGWork& w) {
   ALS_TRY(ensure_graph(c, w));
   std::vector<cudaGraphNode_t>& nodes = w.prec == PREC_F64 ? pf.nodes64 : pf.nodes32;
   std::vector<int>& kinds = w.prec == PREC_F64 ? pf.kinds64 : pf.kinds32;
-  if (pf.on && !nodes.empty()) {
+  cudaGraphExec_t exec = w.graph;
+  if (pf.on && w.graph_prof && !nodes.empty() && w.replays % kProfEvery == 0) {
+    exec = w.graph_prof;
     for (size_t i = 0; i + 1 < nodes.size(); i += 2) {
       cudaEvent_t a = prof_take(c), b = prof_take(c);
       if (!a || !b) { a = pf.spare0; b = pf.spare1; }
       else pf.pairs.push_back({pf.next - 2, pf.next - 1, kinds[i / 2]});
-      if (nodes[i]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i], a);
-      if (nodes[i + 1]) cudaGraphExecEventRecordNodeSetEvent(w.graph, nodes[i + 1], b);
+      if (nodes[i]) cudaGraphExecEventRecordNodeSetEvent(exec, nodes[i], a);
+      if (nodes[i + 1]) cudaGraphExecEventRecordNodeSetEvent(exec, nodes[i + 1], b);
     }
   }
-  if (cudaGraphLaunch(w.graph, c->stream) != cudaSuccess) return cuda_check(c, "graph launch");
+  ++w.replays;
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) return cuda_check(c, "graph launch");
   count_launch(w.graph_kernels);
   return ALS_OK;
 }

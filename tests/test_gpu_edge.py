@@ -79,3 +79,27 @@ def test_size_limits_rejected():
     with pytest.raises(ALSError) as e:
         Context(3, 1024, 2, dummy, 1.0)          # 3 * 2049^3 velocity values > 2^31
     assert e.value.status == A.ALS_EINVAL
+
+
+def test_profile_samples_one_cycle_in_eight():
+    """Kernel timing (als_profile) replays the event-timed graph for one cycle in every 8:
+    16 cycles with s = 2 smoothing steps time 2 cycles x 2 s finest-level patch launches,
+    and the cycle results do not depend on which graph ran."""
+    pb = sinker(3, 8, 2, 1e2, dr=1e4, seed=56)
+    ctx = context(pb, sweeps=2, mode=A.ALS_MODE_MIXED)
+    H = oracle(pb, steps=2)
+    b = dev(random_free(H.levels[-1], 57), torch.float32)
+    x0 = torch.zeros_like(b)
+    ctx.vcycle(b, x0, A.ALS_PREC_FP32)
+    ctx.profile(True)
+    outs = []
+    for _ in range(16):
+        x = torch.zeros_like(b)
+        ctx.vcycle(b, x, A.ALS_PREC_FP32)
+        outs.append(x)
+    torch.cuda.synchronize()
+    ms, n = ctx.profile_read()
+    ctx.profile(False)
+    assert n == 2 * 2 * 2 and ms > 0.0
+    for x in outs:
+        assert torch.equal(x, x0)
