@@ -608,8 +608,18 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
                                int mode, DevStatus* st, cudaStream_t s) {
   using C = TmaCfg<DIM, NST>;
   const long long groups = (count + C::PPI - 1) / C::PPI;
-  const long long per_sm = (227 * 1024) / (long long)(C::smem_bytes + 1024);   // resident CTAs per SM
-  const long long cap = 152 * (per_sm < 1 ? 1 : per_sm);
+  // the grid is persistent (grid-stride over the patches): every CTA must be resident,
+  // so size it by the occupancy the registers and shared memory actually allow
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_tma<DIM, NST>, C::THREADS,
+                                                      C::smem_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    if (per_sm < 1) per_sm = 1;
+  }
+  const long long cap = 152LL * per_sm;
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
   launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
