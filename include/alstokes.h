@@ -158,6 +158,8 @@ als_status als_apply_stokes(als_ctx* ctx, const double* u, const double* p, doub
 
 /* Copies the FP64 inverse of the patch matrix of vertex `vertex` on `level`
  * as a full (d*3^d) x (d*3^d) row-major matrix to `out` (host or device).
+ * In ALS_MODE_MIXED the patches are assembled and inverted in double-float
+ * arithmetic (about 48 significant bits), else in FP64.
  * Patch dof order: component-major, node offsets (-1,0,1)^d x-fastest;
  * rows of nodes outside the domain or on the boundary are identity rows. */
 als_status als_patch_inverse(als_ctx* ctx, int level, long long vertex, double* out);
