@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
   const long long t = (long long)blockIdx.x * (blockDim.x >> 5) + w;
   int cx = 0, cy = 0, cz = 0;
   const bool act = colour_cell(col, t, cx, cy, cz);
+  // no node of the cell on the boundary: the per-node Dirichlet tests are skipped (warp-uniform)
+  const bool inner = cx > 0 && cx < g.n[0] - 1 && cy > 0 && cy < g.n[1] - 1 && cz > 0 && cz < g.n[2] - 1;
   const long long cell = (long long)(unsigned)(cx + g.n[0] * (cy + g.n[1] * cz));
   // point stage: lane = Gauss point (i0, i1, i2)
   const int p = lane_ok ? lane : 0;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const int ni = 2 * cx + a;
-          if (RAW || !on_boundary(g, ni, nj, nk)) u[a] = x[row + ni];
+          if (RAW || inner || !on_boundary(g, ni, nj, nk)) u[a] = x[row + ni];
         }
       }
       T bu[3], du[3];
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const int ni = 2 * cx + a;
-            if (RAW || !on_boundary(g, ni, nj, nk)) y[row + ni] += yd[a] + yb[a];
+            if (RAW || inner || !on_boundary(g, ni, nj, nk)) y[row + ni] += yd[a] + yb[a];
           }
         }
       }
