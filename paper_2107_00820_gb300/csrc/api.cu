@@ -262,6 +262,17 @@ bool fused_gmres(const als_ctx* c) {
   return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB;
 }
 
+// FP32 3D cycles form Z_j inside the operator's cell kernel from the patch outputs
+// (one launch less per Arnoldi step); ALS_FUSE_GATHER=0 keeps the separate gather
+bool fuse_patch_gather(const als_ctx* c, int prec) {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("ALS_FUSE_GATHER");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1 && prec == PREC_F32 && c->dim == 3;
+}
+
 void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
   const LevelDev& Lv = c->lev[l];
   const int prec = w.prec;
@@ -284,8 +295,15 @@ void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
     void* Zj = vptr(w.Z[l], w.es, (long long)j * len);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (l == c->L - 1) prof_events(c, t_prof_counter, e0, e1);
-    patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, vptr(sm, w.es, sl.hn + j));  // Z_j = D^-1 v_j
     ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, vptr(sm, w.es, sl.H + (long long)j * sl.ldh), 0, st, w.partial};
+    if (fuse_patch_gather(c, prec)) {
+      // patch products only; the cell kernel sums them per node into Z_j (= D^-1 v_j / h_j)
+      patch_products(Lv, Vj, w.scratch[l], s, e0, e1);
+      e.pout = w.scratch[l];
+      e.pden = vptr(sm, w.es, sl.hn + j);
+    } else {
+      patch_smooth(Lv, prec, Vj, Zj, w.scratch[l], s, e0, e1, vptr(sm, w.es, sl.hn + j));  // Z_j = D^-1 v_j
+    }
     cudaEvent_t a0 = nullptr, a1 = nullptr;
     if (l == c->L - 1) prof_events(c, t_prof_counter, a0, a1, 1);
     op_apply_epi(Lv, prec, c->gamma, Zj, Vn, e, s, a0, a1);            // A Z_j, H[0..j][j]

@@ -58,12 +58,58 @@ __device__ __forceinline__ int ofs_xy(int m, int c, int x, int y, int z) { retur
 __device__ __forceinline__ int ofs_yz(int m, int c, int x, int y, int z) { return m * 81 + c * 9 + 3 * x + y + 27 * z; }
 __device__ __forceinline__ int ofs_pt(int m, int c, int x, int y, int z) { return m * 81 + c * 27 + 3 * x + 9 * y + z; }
 
-template <typename T, bool TENSOR, int MODE, bool STAGED>
+// Input of the apply taken straight from the star-patch outputs (ZP): x = z = (sum of the
+// <= 2^d patch outputs containing each node) / den, summed in the fixed order of the patch
+// gather (z tap, y tap, then the x pair), 0 at Dirichlet nodes; z is also stored, each node
+// by the one cell that owns it (the cell with the node's lower corner, the last cell for the
+// upper boundary nodes), so the separate gather launch is not needed.
+template <typename T>
+struct PatchIn {
+  const T* out;   // patch outputs in the row layout (patch_out_index)
+  const T* den;   // the GMRES column norm h_j (device scalar)
+  T* z;           // z written here
+};
+
+// z at the three nodes 2cx + a of the x-line (component c, y node nj, z node nk); 0 on Dirichlet rows
+template <typename T>
+__device__ __forceinline__ void patch_line(const Geom& g, const PatchIn<T>& pin, T inv_den, int c, int cx, int nj,
+                                           int nk, T (&u)[3]) {
+  u[0] = u[1] = u[2] = T(0);
+  if (nj == 0 || nj == g.nn[1] - 1 || nk == 0 || nk == g.nn[2] - 1) return;
+  // taps per axis: odd node 2v+1 -> vertices v (offset 2), v+1 (offset 0); even node 2v -> v (offset 1)
+  int vy[2], oy[2], vz[2], oz[2];
+  bool oky[2], okz[2];
+  if (nj & 1) { vy[0] = nj >> 1; oy[0] = 2; vy[1] = vy[0] + 1; oy[1] = 0; oky[0] = oky[1] = true; }
+  else { vy[0] = nj >> 1; oy[0] = 1; oky[0] = true; vy[1] = 0; oy[1] = 0; oky[1] = false; }
+  if (nk & 1) { vz[0] = nk >> 1; oz[0] = 2; vz[1] = vz[0] + 1; oz[1] = 0; okz[0] = okz[1] = true; }
+  else { vz[0] = nk >> 1; oz[0] = 1; okz[0] = true; vz[1] = 0; oz[1] = 0; okz[1] = false; }
+  const int ncol = 3 * g.nv[0];
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+    for (int ty = 0; ty < 2; ++ty) {
+      if (!(oky[ty] && okz[tz])) continue;
+      const int row = ((c * 3 + oz[tz]) * 3 + oy[ty]) * (g.nv[1] * g.nv[2]) + vz[tz] * g.nv[1] + vy[ty];
+      const T* rp = pin.out + (long long)row * ncol + 3 * cx;
+      const T v1 = rp[1], v2 = rp[2], v3 = rp[3], v4 = rp[4];   // nodes 2cx | 2cx+1 (two) | 2cx+2
+      acc[0] += v1;
+      acc[1] += v2 + v3;
+      acc[2] += v4;
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ni = 2 * cx + a;
+    u[a] = (ni == 0 || ni == g.nn[0] - 1) ? T(0) : acc[a] * inv_den;
+  }
+}
+
+template <typename T, bool TENSOR, int MODE, bool STAGED, bool ZP = false>
 __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
                                                      T* __restrict__ y, const T* __restrict__ coef,
                                                      const T* __restrict__ p_in, T* __restrict__ p_out,
                                                      long long vstride, T* __restrict__ ebuf,
-                                                     const T* __restrict__ winv) {
+                                                     const T* __restrict__ winv, PatchIn<T> pin) {
   constexpr int NB = 27, NPR = 4;
   constexpr int NCQ = TENSOR ? Sz<3>::NC : 1;
   constexpr bool RAW = (MODE & OP_RAW) != 0;
@@ -106,10 +152,21 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
       if (act && lane_ok) {
         const int nj = 2 * cy + b1, nk = 2 * cz + b2;
         const long long row = (long long)c * g.N + (long long)(unsigned)(g.nn[0] * (nj + g.nn[1] * nk));
+        if constexpr (ZP) {
+          const T dn = pin.den[0];
+          patch_line<T>(g, pin, dn != T(0) ? T(1) / dn : T(0), c, cx, nj, nk, u);
+          // the owned nodes of the line: lower corner, or the last cell for the upper boundary
+          if ((b1 < 2 || cy == g.n[1] - 1) && (b2 < 2 || cz == g.n[2] - 1)) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int ni = 2 * cx + a;
-          if (RAW || inner || !on_boundary(g, ni, nj, nk)) u[a] = x[row + ni];
+            for (int a = 0; a < 3; ++a)
+              if (a < 2 || cx == g.n[0] - 1) pin.z[row + 2 * cx + a] = u[a];
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int ni = 2 * cx + a;
+            if (RAW || inner || !on_boundary(g, ni, nj, nk)) u[a] = x[row + ni];
+          }
         }
       }
       T bu[3], du[3];

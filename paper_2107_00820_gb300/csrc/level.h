@@ -57,6 +57,11 @@ struct ApplyEpi {
   int start;
   GmresDev st;
   double* partial;
+  // FP32, 3D: when pout is set, the apply's input x is not read but formed from the
+  // star-patch outputs pout (row layout) divided by the device scalar pden, and stored
+  // into x (the patch gather fused into the cell kernel)
+  const void* pout = nullptr;
+  const void* pden = nullptr;
 };
 // e0/e1 (optional) are recorded immediately before and after the cell kernel
 void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
@@ -76,6 +81,10 @@ size_t setup_tab_bytes(int dim);
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
                   cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, const void* den = nullptr);
 size_t patch_scratch_bytes(const LevelDev& L, int prec);
+// FP32: the star-patch products y_v = A_v^-1 r|_v into the scratch rows only (their
+// node sums are formed by the consumer, see ApplyEpi::pout)
+void patch_products(const LevelDev& L, const void* r, void* scratch, cudaStream_t s, cudaEvent_t e0 = nullptr,
+                    cudaEvent_t e1 = nullptr);
 // times the FP32 patch-kernel variants on this level and keeps the fastest (ms_out[3], optional)
 int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out = nullptr);
 // local solves on the coarse-cell interiors (stars of the fine vertices at the

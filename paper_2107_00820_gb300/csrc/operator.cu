@@ -575,13 +575,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
 #include "apply_lines.cuh"
 
 // one launch of the cell kernel: the line form in 3D, the point form in 2D
-template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
+// (ZP, 3D staged only: the input comes from the star-patch outputs, see PatchIn)
+template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED, bool ZP = false>
 static void launch_cells(dim3 grid, cudaStream_t s, const Geom& g, const Colour& col, const CellConst<T>& cc,
                          const T* x, T* y, const T* coef, const T* p_in, T* p_out, long long vstride, T* ebuf,
-                         const T* winv) {
+                         const T* winv, PatchIn<T> pin = PatchIn<T>{}) {
   if constexpr (DIM == 3)
-    launch_pdl(k_apply_lines<T, TENSOR, MODE, STAGED>, grid, 256, 0, s, g, col, cc, x, y, coef, p_in, p_out, vstride,
-               ebuf, winv);
+    launch_pdl(k_apply_lines<T, TENSOR, MODE, STAGED, ZP>, grid, 256, 0, s, g, col, cc, x, y, coef, p_in, p_out,
+               vstride, ebuf, winv, pin);
   else
     launch_pdl(k_apply<T, DIM, TENSOR, MODE, STAGED>, grid, 256, 0, s, g, col, cc, x, y, coef, p_in, p_out, vstride,
                ebuf, winv);
@@ -696,9 +697,19 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
   const Colour col = all_cells(g);
   // External records become event-record nodes when the stream is being captured
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true>(dim3((unsigned)((col.count + CPB - 1) / CPB)), s, g, col,
-                                                       cell_const<T>(g, gamma), (const T*)x, (T*)y, coef, nullptr,
-                                                       nullptr, 0, (T*)L.ebuf, winv);
+  const dim3 grid((unsigned)((col.count + CPB - 1) / CPB));
+  bool fused = false;
+  if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+    if (e.pout) {   // x = z formed from the patch outputs; z stored on the way
+      launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true, true>(
+          grid, s, g, col, cell_const<T>(g, gamma), nullptr, (T*)y, coef, nullptr, nullptr, 0, (T*)L.ebuf, winv,
+          PatchIn<T>{(const T*)e.pout, (const T*)e.pden, (T*)x});
+      fused = true;
+    }
+  }
+  if (!fused)
+    launch_cells<T, DIM, TENSOR, OP_VISC | OP_AL, true>(grid, s, g, col, cell_const<T>(g, gamma), (const T*)x, (T*)y,
+                                                         coef, nullptr, nullptr, 0, (T*)L.ebuf, winv);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   launch_pdl(k_gather_epi<T, DIM>, (gather_threads(g) + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s, g,
              (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out,

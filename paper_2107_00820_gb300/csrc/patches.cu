@@ -841,6 +841,18 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
   count_launch(1);
 }
 
+void patch_products(const LevelDev& L, const void* r, void* scratch, cudaStream_t s, cudaEvent_t e0,
+                    cudaEvent_t e1) {
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  if (L.g.dim == 2)
+    launch_patch_variant<2>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+                            L.status, s);
+  else
+    launch_patch_variant<3>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+                            L.status, s);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+}
+
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
                   cudaEvent_t e0, cudaEvent_t e1, const void* den) {
   if (prec == PREC_F64) {

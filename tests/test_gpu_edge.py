@@ -103,3 +103,37 @@ def test_profile_samples_one_cycle_in_eight():
     assert n == 2 * 2 * 2 and ms > 0.0
     for x in outs:
         assert torch.equal(x, x0)
+
+
+_FUSE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + '/tests')
+from gpu_helpers import context, dev, oracle, random_free, sinker
+from paper_2107_00820_gb300 import alstokes as A
+pb = sinker(3, 8, 3, 1e2, dr=1e6, seed=58)
+ctx = context(pb, mode=A.ALS_MODE_MIXED)
+b = dev(random_free(oracle(pb).levels[-1], 59), torch.float32)
+x = torch.zeros_like(b)
+for _ in range(2):
+    ctx.vcycle(b, x, A.ALS_PREC_FP32)
+np.save(sys.argv[2], x.cpu().numpy())
+"""
+
+
+def test_fused_patch_gather_bitwise(tmp_path):
+    """The FP32 3D cycle forms Z_j inside the cell kernel from the patch outputs; with
+    ALS_FUSE_GATHER=0 a separate gather kernel does it.  Same sums in the same order:
+    the two cycles must agree bit for bit."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for flag in ("1", "0"):
+        path = str(tmp_path / f"x{flag}.npy")
+        env = dict(os.environ, ALS_FUSE_GATHER=flag)
+        subprocess.run([sys.executable, "-c", _FUSE_SCRIPT, root, path], env=env, check=True, timeout=600)
+        outs.append(np.load(path))
+    assert np.all(np.isfinite(outs[0]))
+    assert np.array_equal(outs[0], outs[1])
