@@ -438,13 +438,21 @@ def ours(args, dist):
     ncells = math.prod(F)
     nq = 3 ** pb.d
     ncq = (6 if pb.d == 2 else 21) if tensor else 1
-    k1_bytes = nu * 4 * 2 + ncells * nq * ncq * 4      # read x, write y, read mu or C (FP32)
+    fused = pb.d == 3 and os.environ.get("ALS_FUSE_GATHER", "1") != "0"
+    if fused:
+        # the 3D smoother's cell kernel also forms Z_j from the star-patch outputs: read the
+        # patch outputs, write Z_j and the staged cell outputs, read mu or C (FP32)
+        k1_bytes = nverts * npatch * 4 + nu * 4 + ncells * nq * pb.d * 4 + ncells * nq * ncq * 4
+    else:
+        k1_bytes = nu * 4 * 2 + ncells * nq * ncq * 4      # read x, write y, read mu or C (FP32)
     k1_flops = ncells * (APPLY_FLOPS_PER_CELL[pb.d] + (nq * 2 * 2 * ncq if tensor else 0))
     k1_s = (k1_ms / max(k1_n, 1)) / 1e3
     roofline_apply = None
     if k1_n:
         roofline_apply = {
-            "bound": "alu", "kernel": "k_apply_lines (FP32 A_gamma cell kernel, finest level)",
+            "bound": "alu",
+            "kernel": "k_apply_lines (FP32 A_gamma cell kernel%s, finest level)"
+                      % (" with the fused patch gather" if fused else ""),
             "achieved": k1_flops / k1_s / 1e12, "peak": fp32_peak, "peak_kind": "measured FP32 FMA",
             "unit": "TFLOP/s", "frac": (k1_flops / k1_s / 1e12) / fp32_peak if fp32_peak else None,
             "hbm": {"achieved": k1_bytes / k1_s / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

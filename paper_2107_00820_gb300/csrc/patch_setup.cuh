@@ -202,11 +202,14 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
     // (scalar mu: the d x d block from the 3x3 gradient products) or per (pair, row
     // component al) (tensor: d rows of products with T).  Entries go to
     // (min(row, col), max(row, col)); in a diagonal block (i == j) only row <= col.
+    // (only the NSUB (NSUB + 1) / 2 pairs i <= j are enumerated, so no thread idles on i > j)
     constexpr int NAL = TENSOR ? DIM : 1;
-    for (int it = tid; it < NSUB * NSUB * NAL; it += nt) {
+    constexpr int NPAIR = NSUB * (NSUB + 1) / 2;
+    for (int it = tid; it < NPAIR * NAL; it += nt) {
       const int pr = it / NAL, al0 = it % NAL;
-      const int i = pr / NSUB, j = pr % NSUB;
-      if (i > j) continue;
+      int i = 0, j = pr;
+      while (j >= NSUB - i) { j -= NSUB - i; ++i; }
+      j += i;
       int P, a, Q, b;
       sub_node<DIM>(i, sx, sy, sz, P, a);
       sub_node<DIM>(j, sx, sy, sz, Q, b);
