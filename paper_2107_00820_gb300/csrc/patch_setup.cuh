@@ -127,7 +127,7 @@ __global__ void k_setup_tables(SetupGeo sg, R* __restrict__ tab) {
 }
 
 template <int DIM, bool TENSOR, typename R>
-__global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : 3)
+__global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : (std::is_same<R, DF64>::value ? 4 : 3))
 k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, const double* __restrict__ coef,
               double* __restrict__ inv64, float* __restrict__ inv32, int pstride, DevStatus* st,
               const double* __restrict__ winv) {
