@@ -34,6 +34,13 @@
  * Device-side failures (a non-positive pivot, a Krylov breakdown) are
  * recorded on the device and reported by the call that finishes the work;
  * als_last_error() returns a message.  A failed als_create leaves *out NULL.
+ *
+ * Launch switches read once per process from the environment (results do not
+ * depend on them unless stated): ALS_NO_GRAPH=1 issues every cycle kernel by
+ * kernel instead of replaying a captured CUDA graph; ALS_PDL=0 launches without
+ * programmatic dependent launch; ALS_PATCH_KERNEL=tma2|tma3|direct forces one FP32
+ * star-patch kernel variant on every level; ALS_FUSE_GATHER=0 keeps the separate
+ * patch-gather kernel in the FP32 3D smoother (bitwise the same results).
  */
 #ifndef ALSTOKES_H
 #define ALSTOKES_H
