@@ -2,8 +2,8 @@
 // level; here the coarsest A_gamma is small and dense-inverted on the GPU).
 //
 // Setup: the free-dof block of the coarsest A_gamma is formed column by column
-// by applying the matrix-free operator to unit vectors and inverted in FP64 by a
-// blocked symmetric sweep (the operator of the patch setup, applied to 64-wide
+// by applying the matrix-free operator to unit vectors and inverted (in FP64, or in
+// double-float arithmetic for the mixed cycle) by a blocked symmetric sweep (the operator of the patch setup, applied to 64-wide
 // pivot blocks): per block K, S = A_KK^-1 by a one-CTA sweep of the diagonal
 // block, U = A_{:K} S, A_RR -= A_{RK} U_R^T on the upper triangle of tiles, and
 // the pivot row/column set to U (A_KK to -S).  After every block the matrix holds

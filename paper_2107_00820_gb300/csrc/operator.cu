@@ -514,7 +514,7 @@ static unsigned gather_threads(const Geom& g) {
 // Gather fused with the reduction that consumes the result:
 //   y = b + sigma A x (b NULL: y = sigma A x);  out[j] = (V_j . y) / hn[j], j < k;
 //   start: |y|^2 starts a GMRES cycle.  Fixed grid and order: reproducible.
-// The sums run in T inside a block, in double across blocks.
+// All sums run in T (in FP32 the GMRES state is float too, see GmresView).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __restrict__ ebuf,
                                                             const T* __restrict__ x, T* __restrict__ y,

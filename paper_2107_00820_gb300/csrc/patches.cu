@@ -4,14 +4,17 @@
 // spanned by the free dofs at the 3^d Q2 nodes within half a cell of v.  Its
 // matrix A_v is the restriction of the assembled A_(h,gamma) to V_v; here it is
 // accumulated directly from the contributions of the 2^d cells of the star and
-// inverted in FP64 by Gauss-Jordan elimination (no pivoting: A_v is SPD), and
-// the inverse is stored packed (symmetric) in FP64 and FP32.  Missing nodes of
-// boundary stars become identity rows so that every patch has d*3^d entries.
+// inverted by the symmetric sweep operator without pivoting (A_v is SPD; see
+// patch_setup.cuh), in FP64 or, for the mixed cycle, in double-float arithmetic;
+// the inverse is stored packed (symmetric) in FP64 and block-packed in FP32.
+// Missing nodes of boundary stars become identity rows so that every patch has
+// d*3^d entries.
 //
 // The smoother applies z = sum_v I_v A_v^-1 I_v^T r in two deterministic steps:
-// one warp per patch computes y_v = A_v^-1 r|_v into a per-patch buffer, then
-// one thread per node sums the <= 2^d patch values that contain it in a fixed
-// order (no floating-point atomics).
+// the patch kernel computes y_v = A_v^-1 r|_v into a per-patch buffer (row layout),
+// then the <= 2^d patch values that contain a node are summed in a fixed order (no
+// floating-point atomics) by the patch gather or, in the FP32 3D smoother, by the
+// operator's cell kernel that consumes z.
 #include <stdint.h>
 #include <stdlib.h>
 
