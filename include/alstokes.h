@@ -56,7 +56,7 @@ typedef enum {
   ALS_EINVAL = 1,      /* invalid argument (sizes, levels, options, NULL) */
   ALS_ENOMEM = 2,      /* device allocation failed */
   ALS_ECUDA = 3,       /* a CUDA runtime call failed */
-  ALS_ENOTSPD = 4,     /* non-positive pivot in a patch or coarse Cholesky factorisation */
+  ALS_ENOTSPD = 4,     /* non-positive pivot in the symmetric sweep of a patch or the coarse operator */
   ALS_ENOTCONV = 5,    /* FGMRES did not reach rtol within maxit iterations */
   ALS_EBREAKDOWN = 6,  /* Krylov breakdown or a non-finite residual */
   ALS_ETIMEOUT = 7     /* reserved: a bounded device-side wait gave up */
@@ -123,10 +123,13 @@ typedef struct {
 /* Fills *opt with the defaults listed above. */
 void als_default_options(als_options* opt);
 
-/* Setup (Secs. 5-6): copies the coefficients, assembles and factors the
- * vertex-star patch matrices of levels 1..L-1 in FP64 (stored as FP64 and
- * FP32 inverses), factors the coarsest A_gamma (dense FP64 Cholesky) and
- * forms the per-cell Schur-complement blocks of the finest level.
+/* Setup (Secs. 5-6): copies the coefficients, assembles and inverts the
+ * vertex-star patch matrices of levels 1..L-1 (stored as FP64 and FP32
+ * inverses), inverts the coarsest A_gamma (dense inverse, kept in FP64) and
+ * forms the per-cell Schur-complement blocks of the finest level.  Both
+ * inversions use the symmetric sweep; they run in FP64 in ALS_MODE_FP64 and in
+ * double-float arithmetic (FP32 pairs, about 48 significant bits) in
+ * ALS_MODE_MIXED, whose cycle uses the FP32 inverses.
  * stream: a cudaStream_t (NULL = legacy default stream).
  * Size limits (ALS_EINVAL): d (2n+1)^d velocity values, d 3^d n^d per-cell
  * outputs and d 3^d (n+1)^d vertex-star patch outputs (products over the axes)
