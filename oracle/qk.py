@@ -223,6 +223,11 @@ class LevelK:
         self.A = dirichlet_rows_cols((self.A_raw + self.G_raw).tocsr(), self.bdof)
         self.G = (f @ self.G_raw @ f).tocsr()
         self.B = (self.B_raw @ f).tocsr()
+        self.Bt = self.B.T.tocsr()
+        # pressure mass blocks for the Schur approximation (W = M_p, Eq. (P1P2))
+        self.W = "Mp"
+        self.Mp_mu_blocks = np.einsum("q,cq,qa,qb->cab", m.wdet, 1.0 / self.mu, m.ref.psi, m.ref.psi)
+        self.W_blocks = np.broadcast_to(m.M_elem, (m.ncells,) + m.M_elem.shape)
 
     def load_vector(self, f_qp):
         """F_(alpha,i) = sum_q w |J| f_alpha(x_q) phi_i(x_q); f_qp: (ncells, nq, d)."""
@@ -336,3 +341,57 @@ def two_level_error(fine: LevelK, coarse: LevelK, smoother="star", transfer="rob
     E = np.linalg.matrix_power(S, steps) @ C @ np.linalg.matrix_power(S, steps)
     f = fine.free
     return E[np.ix_(f, f)]
+
+
+class HierarchyK:
+    """Levels 0 (coarsest) .. L-1 of order k with the gamma-robust cycle of Sec. 5: s GMRES
+    steps right-preconditioned by the star PSC operator (smoother "gmres"; "jacobi" is the
+    point-Jacobi negative control), robust (or standard) prolongation, its transpose as
+    restriction, exact coarse solve; the interface the oracle's Stokes solver uses
+    (levels, cycle)."""
+
+    def __init__(self, d, n, k, mus, gamma, steps=5, smoother="gmres", transfer="robust"):
+        import scipy.linalg as sla
+        L = len(mus)
+        self.d, self.k, self.L, self.steps, self.smoother = d, k, L, steps, smoother
+        self.levels = []
+        for lvl in range(L):
+            f = 2 ** (L - 1 - lvl)
+            nl = tuple(v // f for v in ((n,) * d if np.isscalar(n) else n))
+            self.levels.append(LevelK(d, nl, k, mus[lvl], gamma))
+        self.patches = [None] + [star_patches_k(lv) if smoother != "jacobi" else None for lv in self.levels[1:]]
+        self.P = [None]
+        for lvl in range(1, L):
+            if transfer == "robust":
+                self.P.append(robust_prolongation_k(self.levels[lvl - 1].mesh, self.levels[lvl])[0])
+            else:
+                self.P.append(standard_prolongation_k(self.levels[lvl - 1].mesh, self.levels[lvl].mesh))
+        A0 = self.levels[0].A
+        self.coarse_free = np.flatnonzero(self.levels[0].free)
+        self._chol = sla.cho_factor(A0[self.coarse_free][:, self.coarse_free].toarray(), lower=True)
+
+    def Dinv(self, lvl):
+        if self.smoother == "jacobi":
+            dg = self.levels[lvl].A.diagonal()
+            return lambda r: r / dg
+        return self.patches[lvl].apply
+
+    def coarse_solve(self, b):
+        import scipy.linalg as sla
+        x = np.zeros_like(b)
+        x[self.coarse_free] = sla.cho_solve(self._chol, b[self.coarse_free])
+        return x
+
+    def vcycle(self, b, lvl=None):
+        from .mg import smooth_gmres
+        lvl = self.L - 1 if lvl is None else lvl
+        if lvl == 0:
+            return self.coarse_solve(b)
+        A = self.levels[lvl].A
+        x = smooth_gmres(A, self.Dinv(lvl), np.zeros_like(b), b, self.steps)
+        ec = self.vcycle(self.P[lvl].T @ (b - A @ x), lvl - 1)
+        x = x + self.P[lvl] @ ec
+        return smooth_gmres(A, self.Dinv(lvl), x, b, self.steps)
+
+    def cycle(self, b):
+        return self.vcycle(b)

@@ -50,7 +50,7 @@ def schur_blocks(level, variant="P1"):
 def pressure_nullvector(level):
     m = level.mesh
     n = np.zeros(m.npres)
-    n[:: m.d + 1] = 1.0
+    n[:: m.npres // m.ncells] = 1.0             # pressure coefficients per cell: d + 1 at k = 2
     return n
 
 
@@ -145,7 +145,7 @@ class StokesSolver:
         F = lv.load_vector(f_qp)
         r1 = F - lv.A_raw @ uD
         r2_tot = -(lv.B_raw @ uD) if r2 is None else np.asarray(r2, float) - lv.B_raw @ uD
-        winv_r2 = np.linalg.solve(lv.W_blocks, r2_tot.reshape(-1, lv.mesh.d + 1)[:, :, None])[:, :, 0]
+        winv_r2 = np.linalg.solve(lv.W_blocks, r2_tot.reshape(lv.mesh.ncells, -1)[:, :, None])[:, :, 0]
         rhs1 = r1 + lv.gamma * (lv.B_raw.T @ winv_r2.reshape(-1))
         rhs1[bd] = 0.0
         return np.concatenate([rhs1, r2_tot]), uD
@@ -155,7 +155,8 @@ class StokesSolver:
         x, its, hist = self.fgmres(b, rtol, maxit)
         u = x[: self.nu] + uD
         p = x[self.nu:].copy()
-        p[:: self.fine.mesh.d + 1] -= p[:: self.fine.mesh.d + 1].mean()
+        npr = self.fine.mesh.npres // self.fine.mesh.ncells
+        p[::npr] -= p[::npr].mean()
         return u, p, its, hist
 
 

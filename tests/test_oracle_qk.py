@@ -195,3 +195,46 @@ def test_two_level_q3_gamma_robust_and_standard_fails():
     std = [_rho(g, "jacobi", "standard") for g in (1.0, 1e2, 1e4)]
     assert max(rob) < 0.6 and max(rob) - min(rob) < 0.15, rob
     assert std[-1] > 0.99 and std[-1] > std[0], std
+
+
+def _sinker_qk(n, k, gamma, dr=1e4, seed=0, count=4):
+    from oracle.qk import HierarchyK
+    c = P.sinker_centres(seed, count, 2)
+
+    def pts(nl):
+        m = MeshK(2, nl, k)
+        return (m.cells[:, None, :] + 0.5 * (1.0 + m.ref.xq[None])) * np.array(m.h)
+
+    mus = [P.sinker_viscosity(pts(nl), c, 0.1, 200.0, dr) for nl in (n // 2, n)]
+    H = HierarchyK(2, n, k, mus, gamma, steps=5)
+    f = P.sinker_force(pts(n), c, 0.1, 200.0, 10.0)
+    return H, f, np.zeros((2, (k * n + 1) ** 2))
+
+
+def test_q3_fgmres_matches_direct_solve():
+    """FGMRES with the two-level gamma-robust cycle at k = 3 reaches the sparse direct
+    solution of the same augmented system."""
+    from oracle.stokes import StokesSolver, direct_solve
+    H, f, ubc = _sinker_qk(8, 3, 1e2)
+    u, p, its, _ = StokesSolver(H).solve(f, ubc, rtol=1e-10)
+    ud, pd = direct_solve(H.levels[-1], f, ubc)
+    npr = H.levels[-1].mesh.ref.npr
+    pd = pd.copy()
+    pd[::npr] -= pd[::npr].mean()
+    assert np.linalg.norm(u - ud) <= 1e-7 * np.linalg.norm(ud)
+    assert np.linalg.norm(p - pd) <= 1e-6 * np.linalg.norm(pd)
+
+
+def test_q3_iteration_trends_of_table_k():
+    """Table k's two trends at small scale (two levels, 2D, DR 1e4): at fixed gamma the
+    k = 3 solver needs no more iterations than k = 2, and larger gamma needs fewer."""
+    from oracle.stokes import StokesSolver
+    its = {}
+    for k in (2, 3):
+        for g in (0.0, 10.0, 1e3):
+            H, f, ubc = _sinker_qk(8, k, g)
+            its[k, g] = StokesSolver(H).solve(f, ubc, rtol=1e-8)[2]
+    for g in (0.0, 10.0, 1e3):
+        assert its[3, g] <= its[2, g], its
+    for k in (2, 3):
+        assert its[k, 1e3] <= its[k, 10.0] < its[k, 0.0], its
