@@ -74,10 +74,11 @@ __global__ void k_panel_gather(int npad, int p, const R* __restrict__ A, R* __re
 }
 
 // S = D^-1 for the diagonal block D = P[p*CT .. p*CT+CT) by the symmetric sweep
-// in shared memory (one CTA); a non-positive pivot is reported as ALS_ENOTSPD.
+// in shared memory (one CTA of 1024 threads, the block is on the setup's critical path);
+// a non-positive pivot is reported as ALS_ENOTSPD.
 // Every thread of the pivot column forms 1/pivot itself (no wait on one thread).
 template <typename R>
-__global__ void __launch_bounds__(256) k_diag_sweep(int p, const R* __restrict__ P, R* __restrict__ S,
+__global__ void __launch_bounds__(1024) k_diag_sweep(int p, const R* __restrict__ P, R* __restrict__ S,
                                                     DevStatus* st) {
   using O = RealOps<R>;
   __shared__ R D[CT][CT + 1];
@@ -242,7 +243,7 @@ static void coarse_sweep(const LevelDev& L, CoarseDev* C, DevStatus* st, cudaStr
   const unsigned pblocks = (unsigned)(((long long)npad * CT + 255) / 256);
   for (int p = 0; p < nt; ++p) {
     k_panel_gather<R><<<pblocks, 256, 0, s>>>(npad, p, A, P);
-    k_diag_sweep<R><<<1, 256, 0, s>>>(p, P, S, st);
+    k_diag_sweep<R><<<1, 1024, 0, s>>>(p, P, S, st);   // 4 entries of the 64x64 block per thread
     k_panel_mul<R><<<nt, 256, smem2, s>>>(P, S, U);
     k_sym_update<R><<<nt * (nt + 1) / 2, 256, smem2, s>>>(npad, nt, p, P, U, A);
     k_panel_write<R><<<pblocks, 256, 0, s>>>(npad, p, U, S, A);
