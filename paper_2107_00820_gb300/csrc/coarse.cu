@@ -254,6 +254,8 @@ static void coarse_sweep(const LevelDev& L, CoarseDev* C, DevStatus* st, cudaStr
 
 // Forms and factors the coarsest A_gamma with the current coefficients (stream-ordered).
 // df64: the sweep in double-float arithmetic (the inverse then carries about 48 bits).
+static void coarse_apply_prepare(int nfree);
+
 void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, cudaStream_t s, int df64) {
   const Geom& g = L.g;
   const int nfree = C->nfree;
@@ -264,6 +266,7 @@ void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, 
   count_launch(1);
   if (df64) coarse_sweep<DF64>(L, C, st, s);
   else coarse_sweep<double>(L, C, st, s);
+  coarse_apply_prepare(nfree);
 }
 
 // 32-bit form of free_dof for the apply (vector lengths stay below 2^31)
@@ -312,16 +315,22 @@ __global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const d
   if (lane == 0) x[free_dof32(g, r)] = (TV)acc;
 }
 
+constexpr size_t kCoarseStageMax = 200 * 1024;   // largest staged right-hand side (bytes)
+
+// shared-memory opt-in of the staged apply, set at setup (never while a cycle is captured)
+static void coarse_apply_prepare(int nfree) {
+  const size_t smem = (size_t)nfree * sizeof(double);
+  if (smem > 48 * 1024 && smem <= kCoarseStageMax) {
+    cudaFuncSetAttribute(k_coarse_apply<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_coarse_apply<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+}
+
 template <typename TV>
 static void launch_coarse_apply(const LevelDev& L, const CoarseDev& C, const TV* b, TV* x, cudaStream_t s) {
   const unsigned blocks = (unsigned)((C.nfree + 7) / 8);
   const size_t smem = (size_t)C.nfree * sizeof(double);
-  if (smem <= 200 * 1024) {
-    static size_t set = 0;   // largest opt-in applied so far
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_coarse_apply<TV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+  if (smem <= kCoarseStageMax) {   // opt-in above 48 KB set by coarse_apply_prepare at setup
     launch_pdl(k_coarse_apply<TV, true>, blocks, 256, smem, s, L.g, C.nfree, (const double*)C.inv, b, x);
   } else {
     launch_pdl(k_coarse_apply<TV, false>, blocks, 256, 0, s, L.g, C.nfree, (const double*)C.inv, b, x);
