@@ -206,28 +206,39 @@ class MeshK:
 
 
 class LevelK:
-    """Assembled FP64 operators of one level (scalar mu at the Gauss points, W = M_p)."""
+    """Assembled FP64 operators of one level (scalar mu at the Gauss points).
 
-    def __init__(self, d, n, k, mu, gamma):
+    W = "Mp": augmentation weight M_p (the P1 pairing); "Mp_mu": M_p(1/mu) in the
+    augmentation too, gamma B_K^T M_K(1/mu)^-1 B_K per cell (the P2 pairing, Eq. (P1P2)).
+    """
+
+    def __init__(self, d, n, k, mu, gamma, W="Mp"):
         self.mesh = m = MeshK(d, n, k)
         self.gamma = float(gamma)
         self.mu = np.asarray(mu, float)
         self.bdof = m.boundary_dof
         self.free = ~self.bdof
+        self.W = W
         dofs = m.cell_dofs
         pdofs = np.arange(m.npres).reshape(m.ncells, m.ref.npr)
+        self.Mp_mu_blocks = np.einsum("q,cq,qa,qb->cab", m.wdet, 1.0 / self.mu, m.ref.psi, m.ref.psi)
+        if W == "Mp":
+            G_elem = m.AL_elem(gamma)
+            self.W_blocks = np.broadcast_to(m.M_elem, (m.ncells,) + m.M_elem.shape)
+        elif W == "Mp_mu":
+            Bk = m.B_elem
+            G_elem = gamma * np.einsum("aj,cab,bk->cjk", Bk, np.linalg.inv(self.Mp_mu_blocks), Bk)
+            self.W_blocks = self.Mp_mu_blocks
+        else:
+            raise ValueError(W)
         self.A_raw = assemble(m, m.A_elem(self.mu), dofs, dofs, (m.nu, m.nu))
-        self.G_raw = assemble(m, m.AL_elem(gamma), dofs, dofs, (m.nu, m.nu))
+        self.G_raw = assemble(m, G_elem, dofs, dofs, (m.nu, m.nu))
         self.B_raw = assemble(m, m.B_elem, pdofs, dofs, (m.npres, m.nu))
         f = sp.diags(self.free.astype(float))
         self.A = dirichlet_rows_cols((self.A_raw + self.G_raw).tocsr(), self.bdof)
         self.G = (f @ self.G_raw @ f).tocsr()
         self.B = (self.B_raw @ f).tocsr()
         self.Bt = self.B.T.tocsr()
-        # pressure mass blocks for the Schur approximation (W = M_p, Eq. (P1P2))
-        self.W = "Mp"
-        self.Mp_mu_blocks = np.einsum("q,cq,qa,qb->cab", m.wdet, 1.0 / self.mu, m.ref.psi, m.ref.psi)
-        self.W_blocks = np.broadcast_to(m.M_elem, (m.ncells,) + m.M_elem.shape)
 
     def load_vector(self, f_qp):
         """F_(alpha,i) = sum_q w |J| f_alpha(x_q) phi_i(x_q); f_qp: (ncells, nq, d)."""
@@ -350,7 +361,7 @@ class HierarchyK:
     restriction, exact coarse solve; the interface the oracle's Stokes solver uses
     (levels, cycle)."""
 
-    def __init__(self, d, n, k, mus, gamma, steps=5, smoother="gmres", transfer="robust"):
+    def __init__(self, d, n, k, mus, gamma, steps=5, smoother="gmres", transfer="robust", W="Mp"):
         import scipy.linalg as sla
         L = len(mus)
         self.d, self.k, self.L, self.steps, self.smoother = d, k, L, steps, smoother
@@ -358,7 +369,7 @@ class HierarchyK:
         for lvl in range(L):
             f = 2 ** (L - 1 - lvl)
             nl = tuple(v // f for v in ((n,) * d if np.isscalar(n) else n))
-            self.levels.append(LevelK(d, nl, k, mus[lvl], gamma))
+            self.levels.append(LevelK(d, nl, k, mus[lvl], gamma, W))
         self.patches = [None] + [star_patches_k(lv) if smoother != "jacobi" else None for lv in self.levels[1:]]
         self.P = [None]
         for lvl in range(1, L):

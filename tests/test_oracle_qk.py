@@ -19,14 +19,15 @@ from oracle.qk import (LevelK, MeshK, all_vertices_k, lagrange_1d, lagrange_1d_d
 from synthetic import problems as P
 
 
-@pytest.mark.parametrize("d,n", [(2, 2), (2, (3, 2)), (3, 2)])
-def test_k2_equals_the_q2_oracle(d, n):
-    """At k = 2 the order-k definitions are the k = 2 oracle's, entry for entry."""
+@pytest.mark.parametrize("d,n,W", [(2, 2, "Mp"), (2, (3, 2), "Mp"), (3, 2, "Mp"), (2, 2, "Mp_mu"), (3, 2, "Mp_mu")])
+def test_k2_equals_the_q2_oracle(d, n, W):
+    """At k = 2 the order-k definitions are the k = 2 oracle's, entry for entry (both
+    augmentation weights)."""
     rng = np.random.default_rng(1)
     nc = int(np.prod((n,) * d if np.isscalar(n) else n))
     mu = np.exp(rng.standard_normal((nc, 3 ** d)))
-    a = LevelK(d, n, 2, mu, 7.0)
-    b = Level(d, n, mu, 7.0)
+    a = LevelK(d, n, 2, mu, 7.0, W)
+    b = Level(d, n, mu, 7.0, W=W)
     for x, y in ((a.A, b.A), (a.B, b.B), (a.G, b.G)):
         assert abs(x - y).max() <= 1e-12 * abs(y).max()
 
@@ -197,7 +198,7 @@ def test_two_level_q3_gamma_robust_and_standard_fails():
     assert std[-1] > 0.99 and std[-1] > std[0], std
 
 
-def _sinker_qk(n, k, gamma, dr=1e4, seed=0, count=4):
+def _sinker_qk(n, k, gamma, dr=1e4, seed=0, count=4, W="Mp"):
     from oracle.qk import HierarchyK
     c = P.sinker_centres(seed, count, 2)
 
@@ -206,7 +207,7 @@ def _sinker_qk(n, k, gamma, dr=1e4, seed=0, count=4):
         return (m.cells[:, None, :] + 0.5 * (1.0 + m.ref.xq[None])) * np.array(m.h)
 
     mus = [P.sinker_viscosity(pts(nl), c, 0.1, 200.0, dr) for nl in (n // 2, n)]
-    H = HierarchyK(2, n, k, mus, gamma, steps=5)
+    H = HierarchyK(2, n, k, mus, gamma, steps=5, W=W)
     f = P.sinker_force(pts(n), c, 0.1, 200.0, 10.0)
     return H, f, np.zeros((2, (k * n + 1) ** 2))
 
@@ -238,3 +239,19 @@ def test_q3_iteration_trends_of_table_k():
         assert its[3, g] <= its[2, g], its
     for k in (2, 3):
         assert its[k, 1e3] <= its[k, 10.0] < its[k, 0.0], its
+
+
+def test_q3_p2_pairing_as_in_table_k():
+    """Table k's configuration: the P2 pairing (W = M_p(1/mu), S^-1 ~ (1 + gamma) M_p(1/mu)^-1),
+    two levels.  At small scale the iteration counts fall with gamma and are no higher at
+    k = 3 than at k = 2."""
+    from oracle.stokes import StokesSolver
+    its = {}
+    for k in (2, 3):
+        for g in (10.0, 1e3):
+            H, f, ubc = _sinker_qk(8, k, g, dr=1e6, W="Mp_mu")
+            its[k, g] = StokesSolver(H, schur="P2").solve(f, ubc, rtol=1e-8)[2]
+    for g in (10.0, 1e3):
+        assert its[3, g] <= its[2, g], its
+    for k in (2, 3):
+        assert its[k, 1e3] <= its[k, 10.0], its
