@@ -255,3 +255,22 @@ def test_q3_p2_pairing_as_in_table_k():
         assert its[3, g] <= its[2, g], its
     for k in (2, 3):
         assert its[k, 1e3] <= its[k, 10.0], its
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_prolongation_1d_exact_rationals(k):
+    """The 1D coarse-to-fine weights of Q_k against exact rational Lagrange values."""
+    from fractions import Fraction as Fr
+    t = [Fr(-1) + Fr(2 * a, k) for a in range(k + 1)]
+    nf = 2 * k + 1
+    ref = np.zeros((nf, k + 1))
+    for f in range(nf):
+        x = Fr(f, 2 * k)                       # fine node in the coarse cell (0, 1)
+        xi = 2 * x - 1
+        for a in range(k + 1):
+            v = Fr(1)
+            for b in range(k + 1):
+                if b != a:
+                    v *= (xi - t[b]) / (t[a] - t[b])
+            ref[f, a] = float(v)
+    assert np.allclose(prolongation_1d_k(1, k), ref, atol=1e-15)
