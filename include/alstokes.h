@@ -290,7 +290,9 @@ als_status als_autotune_info(als_ctx* ctx, int level, int* variant, float* ms);
  * before the next capture); the captured cycles are dropped and recaptured. */
 als_status als_set_patch_kernel(als_ctx* ctx, int level, int variant);
 
-/* Last error message of the context (never NULL; "" when none). */
+/* Last error message of the context (never NULL; "" when none).  With ctx NULL:
+ * the message of the calling thread's last failed als_create or als_batch_create
+ * ("" when its last call succeeded). */
 const char* als_last_error(const als_ctx* ctx);
 
 #ifdef __cplusplus

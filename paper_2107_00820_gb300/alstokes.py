@@ -178,7 +178,7 @@ class Context:
         st = lib.als_create(byref(mesh), byref(coeff), self.gamma, byref(self.options),
                             c_void_p(stream) if stream else None, byref(out))
         if st != ALS_OK:
-            raise ALSError(st, "als_create failed (see stderr)")
+            raise ALSError(st, "als_create: " + lib.als_last_error(None).decode())
         self._ctx = out
         self._lib = lib
 
@@ -343,7 +343,7 @@ class Batch:
         out = c_void_p()
         st = lib.als_batch_create(k, meshes, coeffs, gammas, opts, c_void_p(stream) if stream else None, byref(out))
         if st != ALS_OK:
-            raise ALSError(st, "als_batch_create failed")
+            raise ALSError(st, "als_batch_create: " + lib.als_last_error(None).decode())
         self._b = out
         self._lib = lib
         self.count = k

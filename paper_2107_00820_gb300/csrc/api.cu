@@ -658,7 +658,10 @@ void als_default_options(als_options* opt) {
   opt->fact = ALS_FACT_FULL;
 }
 
-const char* als_last_error(const als_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+// message of the calling thread's last failed als_create (the context is gone by then)
+static thread_local std::string t_create_err;
+
+const char* als_last_error(const als_ctx* ctx) { return ctx ? ctx->err.c_str() : t_create_err.c_str(); }
 
 als_status als_destroy(als_ctx* ctx) {
   if (!ctx) return ALS_EINVAL;
@@ -814,18 +817,19 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
 
 als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
                       void* stream, als_ctx** out) {
-  if (!out) return ALS_EINVAL;
+  t_create_err.clear();
+  if (!out) {
+    t_create_err = "null output pointer";
+    return ALS_EINVAL;
+  }
   *out = nullptr;
   als_ctx* c = new als_ctx();
   c->user_stream = (cudaStream_t)stream;
   if (stream) cudaStreamSynchronize((cudaStream_t)stream);
   als_status st = create_impl(c, mesh, coeff, gamma, opt);
   if (st != ALS_OK) {
-    // keep the message for the caller through a static buffer: the context is gone
-    static thread_local std::string last;
-    last = c->err;
+    t_create_err = c->err;   // read back with als_last_error(NULL): the context is gone
     als_destroy(c);
-    fprintf(stderr, "als_create: %s\n", last.c_str());
     return st;
   }
   *out = c;
@@ -1180,13 +1184,17 @@ als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* 
                             const als_options* opts, void* stream, als_batch** out) {
   if (!out) return ALS_EINVAL;
   *out = nullptr;
-  if (count < 1 || !meshes || !coeffs || !gammas) return ALS_EINVAL;
+  if (count < 1 || !meshes || !coeffs || !gammas) {
+    t_create_err = "empty batch or null arrays";
+    return ALS_EINVAL;
+  }
   als_batch* b = new als_batch;
   b->user_stream = (cudaStream_t)stream;
   for (int i = 0; i < count; ++i) {
     als_ctx* c = nullptr;
     const als_status st = als_create(&meshes[i], &coeffs[i], gammas[i], opts ? &opts[i] : nullptr, stream, &c);
     if (st != ALS_OK) {
+      t_create_err = "instance " + std::to_string(i) + ": " + t_create_err;
       for (als_ctx* d : b->ctx) als_destroy(d);
       delete b;
       return st;

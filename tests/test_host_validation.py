@@ -1,0 +1,120 @@
+"""Host-side argument checks of the C ABI, on the CPU (no GPU is touched).
+
+als_create validates the mesh, the coefficients and every option before it creates a
+stream or allocates anything, so these run anywhere the library loads: each invalid
+argument is refused with ALS_EINVAL and a message that names it, readable through
+als_last_error(NULL) after the context is gone; every entry point refuses a NULL
+context; the documented defaults are what als_default_options fills in."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2107_00820_gb300 import alstokes as A
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_00820_gb300 import build as b
+    if not b.up_to_date():
+        import os
+        if not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build the library")
+        b.build()
+    return A.load()
+
+
+def test_default_options(lib):
+    o = A.als_options()
+    lib.als_default_options(ctypes.byref(o))
+    assert (o.smoother, o.sweeps, o.transfer, o.schur, o.mode) == \
+        (A.ALS_SMOOTH_GMRES, 5, A.ALS_TRANSFER_ROBUST, A.ALS_SCHUR_P1, A.ALS_MODE_FP64)
+    assert (o.cycle, o.fact, o.maxit) == (A.ALS_CYCLE_V, A.ALS_FACT_FULL, 300)
+    assert o.rtol == 1e-8 and o.tau == 0.0          # tau 0: 2^-d chosen at create
+
+
+@pytest.mark.parametrize("args,kw,words", [
+    ((4, (4, 4, 4), 1), {}, "dim"),
+    ((2, 4, 0), {}, "levels"),
+    ((2, 4, 13), {}, "levels"),
+    ((2, 6, 3), {}, "divisible"),
+    ((2, 4, 3), {}, "coarse cells"),
+    ((2, 4, 1), {"sweeps": 0}, "sweeps"),
+    ((2, 4, 1), {"sweeps": 65}, "sweeps"),
+    ((2, 4, 1), {"maxit": 0}, "maxit"),
+    ((2, 4, 1), {"schur": 2}, "Schur"),
+    ((2, 4, 1), {"cycle": 2}, "cycle"),
+    ((2, 4, 1), {"fact": 4}, "factorisation"),
+    ((2, 4, 1), {"smoother": 2}, "smoother"),
+    ((2, 4, 1), {"transfer": 2}, "transfer"),
+    ((2, 4, 1), {"mode": 2}, "mode"),
+    ((3, 1024, 2), {}, "too large"),
+    ((2, 46340, 2), {}, "too large"),
+])
+def test_create_rejects_invalid_arguments(lib, args, kw, words):
+    d, n, levels = args
+    mu = [np.zeros(1)] * levels           # never read: the arguments are refused first
+    with pytest.raises(A.ALSError) as e:
+        A.Context(d, n, levels, mu, 1.0, **kw)
+    assert e.value.status == A.ALS_EINVAL
+    assert words in str(e.value), str(e.value)
+    assert words in lib.als_last_error(None).decode()
+
+
+@pytest.mark.parametrize("gamma", [-1.0, float("nan"), float("inf")])
+def test_create_rejects_invalid_gamma(lib, gamma):
+    with pytest.raises(A.ALSError) as e:
+        A.Context(2, 4, 1, [np.ones((16, 9))], gamma)
+    assert e.value.status == A.ALS_EINVAL and "gamma" in str(e.value)
+
+
+def test_create_rejects_tensor_without_mu_eff(lib):
+    mesh = A.als_mesh(2, (ctypes.c_int * 3)(4, 4, 1), 1)
+    qp = (ctypes.c_void_p * 1)(ctypes.c_void_p(1))
+    coeff = A.als_coeff(A.ALS_COEFF_TENSOR, qp, None)
+    out = ctypes.c_void_p()
+    st = lib.als_create(ctypes.byref(mesh), ctypes.byref(coeff), 1.0, None, None, ctypes.byref(out))
+    assert st == A.ALS_EINVAL and out.value is None
+    assert "mu_eff" in lib.als_last_error(None).decode()
+    coeff = A.als_coeff(7, qp, None)
+    assert lib.als_create(ctypes.byref(mesh), ctypes.byref(coeff), 1.0, None, None, ctypes.byref(out)) == A.ALS_EINVAL
+    assert "kind" in lib.als_last_error(None).decode()
+    assert lib.als_create(ctypes.byref(mesh), None, 1.0, None, None, ctypes.byref(out)) == A.ALS_EINVAL
+    assert lib.als_create(ctypes.byref(mesh), ctypes.byref(coeff), 1.0, None, None, None) == A.ALS_EINVAL
+
+
+def test_batch_create_names_the_failing_instance(lib):
+    meshes = (A.als_mesh * 2)(A.als_mesh(2, (ctypes.c_int * 3)(4, 4, 1), 1),
+                              A.als_mesh(5, (ctypes.c_int * 3)(4, 4, 1), 1))
+    qp = (ctypes.c_void_p * 1)(ctypes.c_void_p(1))
+    coeffs = (A.als_coeff * 2)(A.als_coeff(A.ALS_COEFF_SCALAR, qp, None), A.als_coeff(A.ALS_COEFF_SCALAR, qp, None))
+    gammas = (ctypes.c_double * 2)(1.0, 1.0)
+    out = ctypes.c_void_p()
+    # instance 0 is valid but would need a GPU: give instance 0 an invalid gamma instead
+    gammas[0] = -1.0
+    st = lib.als_batch_create(2, meshes, coeffs, gammas, None, None, ctypes.byref(out))
+    assert st == A.ALS_EINVAL and out.value is None
+    msg = lib.als_last_error(None).decode()
+    assert msg.startswith("instance 0") and "gamma" in msg
+    assert lib.als_batch_create(0, meshes, coeffs, gammas, None, None, ctypes.byref(out)) == A.ALS_EINVAL
+
+
+def test_every_entry_point_refuses_a_null_context(lib):
+    N = None
+    d, i, ll = ctypes.c_double(), ctypes.c_int(), ctypes.c_longlong()
+    calls = {
+        "als_destroy": (N,), "als_apply_agamma": (N, 0, 0, N, N), "als_vcycle": (N, 0, N, N),
+        "als_star_smooth": (N, 1, 0, N, N), "als_prolong": (N, 1, 0, N, N), "als_restrict": (N, 1, 0, N, N),
+        "als_coarse_solve": (N, 0, N, N), "als_apply_stokes": (N, N, N, N, N),
+        "als_patch_inverse": (N, 0, 0, N), "als_solve": (N, N, N, N, N, N, N),
+        "als_update_coefficients": (N, N), "als_profile": (N, 1),
+        "als_profile_read": (N, ctypes.byref(d), ctypes.byref(ll)),
+        "als_profile_read_kernel": (N, 0, ctypes.byref(d), ctypes.byref(ll)),
+        "als_autotune_info": (N, 1, ctypes.byref(i), N), "als_set_patch_kernel": (N, 1, 0),
+        "als_batch_destroy": (N,), "als_batch_context": (N, 0, N), "als_batch_vcycle": (N, 0, N, N),
+        "als_batch_solve": (N, N, N, N, N, N, N), "als_measure_fma_peaks": (N, N, N),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == A.ALS_EINVAL, name
+    assert lib.als_star_smooth_static(4, N, 1, N, N, N, N) == A.ALS_EINVAL
+    assert lib.als_batch_last_error(None) == b"null batch"
