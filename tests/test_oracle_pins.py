@@ -142,6 +142,29 @@ def test_tensor_path_reduces_to_scalar(d):
     assert np.allclose(m.A_elem(C, "tensor"), m.A_elem(mu, "scalar"), atol=1e-12)
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_tensor_energy_closed_form(d):
+    """Anisotropic C (Eq. stokes-lin): for a linear field u = M x the strain is the constant
+    S = sym M, so u^T A u = int_(0,1)^d (C S) : S = s^T K s with s the Mandel vector of S
+    (diagonal entries, then sqrt2 times the off-diagonal ones in the documented order) and K
+    the full Mandel matrix whose upper triangle, row-major, is stored per point.  Fails for
+    a wrong packing order, a missing sqrt2 or an unsymmetrised upper triangle."""
+    m = Mesh(d, 2)
+    pairs = [(0, 0), (1, 1), (0, 1)] if d == 2 else [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    nm = len(pairs)
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((nm, nm))
+    K = R @ R.T + nm * np.eye(nm)                    # SPD, all entries distinct
+    iu = np.triu_indices(nm)
+    C = np.broadcast_to(K[iu], (m.ncells, 3 ** d, len(iu[0]))).copy()
+    lv = Level(d, 2, C, 0.0, kind="tensor", mu_eff=np.ones((m.ncells, 3 ** d)))
+    M = rng.standard_normal((d, d))
+    S = 0.5 * (M + M.T)
+    s = np.array([S[k, l] * (1.0 if k == l else math.sqrt(2.0)) for k, l in pairs])
+    u = _field_dofs(m, lambda x: x @ M.T)
+    assert abs(u @ lv.A_raw @ u - s @ K @ s) < 1e-11 * abs(s @ K @ s)
+
+
 @pytest.mark.parametrize("d,n", [(2, 4), (3, 2)])
 def test_Agamma_spd_and_AL_nullity(d, n):
     lv = Level(d, n, np.ones((n ** d, 3 ** d)), 10.0)
