@@ -601,6 +601,35 @@ def test_iteration_counts_flat_in_gamma():
     assert counts[-1] <= counts[0] and max(counts) <= 40, counts
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_weighted_pressure_mass_exact_integrals(d):
+    """M_p(1/mu) of Eq. (inv-visc-mass), the P2 Schur block and the W of the P2 pairing,
+    for a viscosity varying inside each cell: with 1/mu linear in x the 3-point Gauss rule is
+    exact, so every cell block equals the exact integral of (1/mu) psi_a psi_b over the cell,
+    psi = {1, xi_0, .., xi_(d-1)} in reference coordinates (computed symbolically here)."""
+    sympy = pytest.importorskip("sympy")
+    n = 2
+    xq = P.sample_points(d, n)
+    coef = np.array([1.0, 2.0, 0.5][:d])
+    mu = 1.0 / (1.0 + xq @ coef)
+    lv = Level(d, n, mu, 1.0, W="Mp_mu")
+    X = sympy.symbols("x0:%d" % d)
+    h = sympy.Rational(1, n)
+    cells = list(np.ndindex(*(n,) * d))
+    for cid, c in enumerate(c[::-1] for c in cells):   # cell index x-fastest
+        lo = [sympy.Rational(int(ci), n) for ci in c]
+        psi = [sympy.Integer(1)] + [2 * (X[k] - lo[k]) / h - 1 for k in range(d)]
+        w = 1 + sum(sympy.Rational(coef[k]).limit_denominator(4) * X[k] for k in range(d))
+        ref = np.zeros((d + 1, d + 1))
+        for a in range(d + 1):
+            for b in range(d + 1):
+                e = w * psi[a] * psi[b]
+                for k in range(d):
+                    e = sympy.integrate(e, (X[k], lo[k], lo[k] + h))
+                ref[a, b] = float(e)
+        assert np.allclose(lv.Mp_mu_blocks[cid], ref, rtol=1e-13, atol=1e-15), cid
+
+
 def test_schur_blocks_closed_form_constant_mu():
     lv = Level(2, 2, 2.0 * np.ones((4, 9)), 5.0)
     blk = schur_blocks(lv, "P1")[0]
