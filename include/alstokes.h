@@ -81,7 +81,7 @@ typedef struct {
 } als_mesh;
 
 /* Viscosity at the Gauss points of every level (rediscretisation on each
- * level, Sec. 6.1).  SCALAR: qp[l] is [cell][3^d] mu.  TENSOR: qp[l] is
+ * level, Sec. 5.1).  SCALAR: qp[l] is [cell][3^d] mu.  TENSOR: qp[l] is
  * [cell][3^d][6|21] Mandel C (Eq. (stokes-lin)) and mu_eff[l] is the
  * [cell][3^d] scalar used by the Schur-complement approximation. */
 typedef struct {
@@ -104,7 +104,7 @@ typedef struct {
   int maxit;      /* FGMRES iterations, no restart (default 300) */
   int cycle;      /* ALS_CYCLE_V (default) or ALS_CYCLE_F: the coarse correction on each
                      level is an F-cycle from zero followed by a V-cycle from its result
-                     (the textbook F-cycle; the paper runs an F-cycle, Sec. 7) */
+                     (the textbook F-cycle; the paper runs an F-cycle, Sec. 5.1) */
   int fact;       /* block factorisation of Eq. (precond): ALS_FACT_FULL (default, L D U,
                      two cycles per iteration); ALS_FACT_UPPER [[A, B^T], [0, -S]]^-1,
                      ALS_FACT_LOWER [[A, 0], [B, -S]]^-1, ALS_FACT_DIAG diag(A^-1, -S^-1):
@@ -123,7 +123,7 @@ typedef struct {
 /* Fills *opt with the defaults listed above. */
 void als_default_options(als_options* opt);
 
-/* Setup (Secs. 5-6): copies the coefficients, assembles and inverts the
+/* Setup (Secs. 4-5): copies the coefficients, assembles and inverts the
  * vertex-star patch matrices of levels 1..L-1 (stored as FP64 and FP32
  * inverses), inverts the coarsest A_gamma (dense inverse, kept in FP64) and
  * forms the per-cell Schur-complement blocks of the finest level.  Both
@@ -152,7 +152,7 @@ als_status als_apply_agamma(als_ctx* ctx, int level, int prec, const void* x, vo
 als_status als_vcycle(als_ctx* ctx, int prec, const void* b, void* x);
 
 /* Stage entry points (one step of the V-cycle each, device vectors):
- *   als_star_smooth : z = sum_v I_v A_v^-1 I_v^T r on `level` >= 1 (Sec. 5.1)
+ *   als_star_smooth : z = sum_v I_v A_v^-1 I_v^T r on `level` >= 1 (Sec. 4.1)
  *   als_prolong     : xf = P~ xc from level-1 to `level` (Eq. (Ptilde)),
  *                     or P_H xc when the context uses ALS_TRANSFER_STANDARD
  *   als_restrict    : rc = P~^T rf from `level` to level-1
@@ -189,7 +189,7 @@ als_status als_solve(als_ctx* ctx, const double* f_qp, const double* u_bc, const
 /* Re-runs the setup of als_create (patch factorisations, coarse Cholesky,
  * Schur blocks) for new coefficients of the same kind and sizes, reusing every
  * allocation and the captured V-cycle graphs: the per-linearisation setup of
- * a nonlinear (Newton) iteration, Sec. 6.3.  Host or device pointers. */
+ * a nonlinear (Newton) iteration, Sec. 5.3.  Host or device pointers. */
 als_status als_update_coefficients(als_ctx* ctx, const als_coeff* coeff);
 
 /* Live timing of the finest-level vertex-star patch kernel inside V-cycles:

@@ -15,7 +15,7 @@ Paper passages followed:
   * pressure mass matrices, Eq. (inv-visc-mass): [M_p(1/mu)]_ij = (mu^-1 psi_i, psi_j);
   * augmented system, Sec. 3, Eq. (augstokessys): A_gamma = A + gamma B^T W^-1 B with W = M_p;
   * tensor viscosity, Eq. (stokes-lin): the stress is C : eps(u) with a 4th-order C;
-  * spaces V_h^k x Q_h^(k-1) with k = 2 (Sec. 5), on uniform quad/hex meshes of (0,1)^d.
+  * spaces V_h^k x Q_h^(k-1) with k = 2 (Sec. 4), on uniform quad/hex meshes of (0,1)^d.
 
 Conventions (shared with the C ABI as a data contract, not as code):
   * node lattice (2n_k+1 nodes per direction), node index x-fastest;
@@ -261,7 +261,7 @@ class Level:
     """One multigrid level: mesh, coefficients and assembled FP64 operators.
 
     Level operators are obtained by rediscretising on the level's mesh with the
-    level's own coefficient samples (Sec. 6.1).
+    level's own coefficient samples (Sec. 5.1).
     """
 
     def __init__(self, d, n, coeff, gamma, kind="scalar", mu_eff=None, W="Mp"):

@@ -1,8 +1,8 @@
 """FP64 oracle: the gamma-robust multigrid V-cycle for A_gamma.
 
-TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  Plain restatement of Sec. 5:
+TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  Plain restatement of Sec. 4:
 
-  * PSC smoother (Sec. 5.1): u <- u + tau D^-1 r with
+  * PSC smoother (Sec. 4.1): u <- u + tau D^-1 r with
     D^-1 = sum_i I_i A_i^-1 I_i^*, A_i the restriction of the assembled
     A_(h,gamma) to V_i;
   * vertex-star space decomposition, Eq. (viim): V_i = {v in V_h : supp v in
@@ -13,15 +13,15 @@ TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  Plain restatement of Sec. 5:
     (the reading taken for the unstated preconditioning side); a damped
     Richardson variant and a point-Jacobi negative control are also here;
   * standard prolongation P_H = nested Q2 interpolation (coarse basis
-    functions evaluated at the fine nodes), Sec. 5.2;
+    functions evaluated at the fine nodes), Sec. 4.2;
   * robust prolongation, Eq. (Ptilde): P~ u_H = P_H u_H - u~ with u~ in V^_h
     solving a_(h,gamma)(u~, v^) = gamma (Pi div P_H u_H, Pi div v^) for all v^
     in V^_h (the AL-term right-hand side), V^_h = functions supported in one
     coarse cell; restriction is its transpose;
   * the coarsest level is solved by a dense Cholesky factorisation (the paper
-    uses a sparse direct solver there, Sec. 6.1).
+    uses a sparse direct solver there, Sec. 5.1).
 
-Patch matrices are taken from the ASSEMBLED matrix, as in Sec. 6.1.
+Patch matrices are taken from the ASSEMBLED matrix, as in Sec. 5.1.
 """
 from __future__ import annotations
 
@@ -212,7 +212,7 @@ class Hierarchy:
 
     smoother: "gmres" (default), "richardson" or "jacobi" (point Jacobi,
     the standard-multigrid negative control); transfer: "robust" or "standard";
-    cycle: "V" (default) or "F" (what the paper ran, Sec. 7).
+    cycle: "V" (default) or "F" (what the paper ran, Sec. 5.1).
     """
 
     def __init__(self, d, n, coeffs, gamma, kind="scalar", mu_eff=None,
@@ -267,7 +267,7 @@ class Hierarchy:
         return smooth_richardson(A, self.Dinv(lvl), x, b, self.steps, self.tau)
 
     def vcycle(self, b, lvl=None, x0=None):
-        """One V-cycle for A_(lvl) x = b from x = x0 (default 0) (Sec. 5, Fig. algo-outline)."""
+        """One V-cycle for A_(lvl) x = b from x = x0 (default 0) (Sec. 4, Fig. algo-outline)."""
         lvl = self.L - 1 if lvl is None else lvl
         if lvl == 0:
             return self.coarse_solve(b)
@@ -283,7 +283,7 @@ class Hierarchy:
     def fcycle(self, b, lvl=None):
         """One F-cycle for A_(lvl) x = b from x = 0.
 
-        The paper runs an F-cycle (Sec. 7) without defining it; this is the
+        The paper runs an F-cycle (Sec. 5.1) without defining it; this is the
         textbook recursion: as the V-cycle, but the coarse correction is an
         F-cycle on level lvl-1 from zero followed by a V-cycle on level lvl-1
         started from that result.  On the coarsest level both are the exact

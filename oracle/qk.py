@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  The same definitions as the
 k = 2 oracle, written for any order k >= 2, so that the higher-order study of
-Sec. 7 (Table k) has a reference before any kernel exists for it:
+Sec. 5.2.2 (Table k) has a reference before any kernel exists for it:
 
   * velocity: continuous Q_k, nodal basis on k + 1 equispaced nodes per axis and
     cell, node lattice of k n + 1 nodes per direction, x fastest;
@@ -13,13 +13,13 @@ Sec. 7 (Table k) has a reference before any kernel exists for it:
     viscous and mass terms);
   * A_gamma = A + gamma B^T M_p^-1 B (Sec. 3, Eq. (augstokessys), W = M_p), Dirichlet
     rows and columns replaced by the identity;
-  * vertex stars (Sec. 5.1, Eq. (viim)): the free nodes strictly inside star(v),
+  * vertex stars (Sec. 4.1, Eq. (viim)): the free nodes strictly inside star(v),
     (2k - 1)^d of them for an interior vertex;
   * P_H: coarse Q_k basis evaluated at the fine nodes; P~ = P_H - sum_K E_K A_K^-1
     E_K^T G P_H over the coarse-cell interiors (Eq. (Ptilde), the reading of
     oracle/mg.py); restriction by transposition.
 
-Reading: the paper states dim V_i = (k - 1)^d for the star spaces (Sec. 7, the
+Reading: the paper states dim V_i = (k - 1)^d for the star spaces (Sec. 5.2.2, the
 paragraph before Table k); the free nodes strictly inside a 2x2(x2)-cell star of
 Q_k number (2k - 1)^d per component, which is the space the smoother inverts for
 k = 2 as well (3^d nodes), so (2k - 1)^d is used.
@@ -332,7 +332,7 @@ def two_level_error(fine: LevelK, coarse: LevelK, smoother="star", transfer="rob
     """Dense error propagation of one two-level cycle on the free dofs: Richardson
     pre/post smoothing with D^-1 (the star PSC operator, or point Jacobi), the exact
     coarse solve on the rediscretised coarse operator, prolongation P~ or P_H and its
-    transpose as restriction (Sec. 5)."""
+    transpose as restriction (Sec. 4)."""
     A = fine.A.toarray()
     n = A.shape[0]
     if smoother == "star":
@@ -355,7 +355,7 @@ def two_level_error(fine: LevelK, coarse: LevelK, smoother="star", transfer="rob
 
 
 class HierarchyK:
-    """Levels 0 (coarsest) .. L-1 of order k with the gamma-robust cycle of Sec. 5: s GMRES
+    """Levels 0 (coarsest) .. L-1 of order k with the gamma-robust cycle of Sec. 4: s GMRES
     steps right-preconditioned by the star PSC operator (smoother "gmres"; "jacobi" is the
     point-Jacobi negative control), robust (or standard) prolongation, its transpose as
     restriction, exact coarse solve; the interface the oracle's Stokes solver uses

@@ -11,8 +11,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/fem.py).  Follows:
     "diag" = diag(A^-1, -S^-1), one (1,1) application each;
   * Eq. (P1P2): P1: S_gamma^-1 = M_p(1/mu)^-1 + gamma M_p^-1;
     P2: S_gamma^-1 = (1 + gamma) M_p(1/mu)^-1, both block diagonal (one
-    (d+1)x(d+1) block per cell, Sec. 6.1);
-  * flexible GMRES (Sec. 6.1), right preconditioned, classical Gram-Schmidt
+    (d+1)x(d+1) block per cell, Sec. 5.1);
+  * flexible GMRES (Sec. 5.1), right preconditioned, classical Gram-Schmidt
     applied twice, no restart, relative residual test on the l2 norm.
 
 Dirichlet data are lifted: r1 = F - A u_D and r2 = -B u_D on the
@@ -55,7 +55,7 @@ def pressure_nullvector(level):
 
 
 class StokesSolver:
-    """Block-preconditioned FGMRES on the augmented system (Secs. 3, 6.1)."""
+    """Block-preconditioned FGMRES on the augmented system (Secs. 3, 5.1)."""
 
     def __init__(self, hierarchy: Hierarchy, schur="P1", exact_A=False, fact="full"):
         if fact not in ("full", "upper", "lower", "diag"):

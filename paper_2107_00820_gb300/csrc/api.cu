@@ -680,7 +680,7 @@ als_status als_destroy(als_ctx* ctx) {
   return ALS_OK;
 }
 
-// Setup (Secs. 5-6) with the coefficients of every level: copies them, builds
+// Setup (Secs. 4-5) with the coefficients of every level: copies them, builds
 // the vertex-star patch inverses, the coarse factorisation and the Schur blocks.
 static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   const int NB = c->dim == 2 ? 9 : 27;
@@ -1047,7 +1047,7 @@ static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc
   op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);         // B^T gamma W^-1 r2
   vec_axpby(PREC_F64, c->nu, 1.0, c->tu2, 1.0, c->tu, s);
   bnd_mask(F.g, c->tu, rhs_u, 0, s);                                                   // zero boundary rows
-  // FGMRES (Sec. 6.1), right preconditioned, CGS2, x0 = 0
+  // FGMRES (Sec. 5.1), right preconditioned, CGS2, x0 = 0
   const int ldh = maxit + 1;
   vec_multidot(PREC_F64, c->n, 1, rhs, c->n, rhs, c->nrm2, c->partial, s);
   dev_init_g(maxit + 1, c->nrm2, c->g, c->beta, s);

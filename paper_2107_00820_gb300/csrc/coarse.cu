@@ -1,4 +1,4 @@
-// K7: coarse-grid solve (Sec. 6.1 uses a sparse direct solver on the coarsest
+// K7: coarse-grid solve (Sec. 5.1 uses a sparse direct solver on the coarsest
 // level; here the coarsest A_gamma is small and dense-inverted on the GPU).
 //
 // Setup: the free-dof block of the coarsest A_gamma is formed column by column

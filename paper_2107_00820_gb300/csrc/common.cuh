@@ -1,6 +1,6 @@
 // Shared device-side definitions for the AL-multigrid Stokes library.
 //
-// Discretisation: [Q2]^d x P1^disc on a uniform mesh of (0,1)^d (Sec. 5 of
+// Discretisation: [Q2]^d x P1^disc on a uniform mesh of (0,1)^d (Sec. 4 of
 // Shih, Stadler & Wechsung, "Robust multigrid techniques for augmented
 // Lagrangian preconditioning of incompressible Stokes equations with extreme
 // viscosity variations").  Velocity vectors hold d blocks of nodal values on

@@ -2,7 +2,7 @@
 // after patch_node / vertex_coords / mandel_of and df64.cuh).
 //
 // One CTA per vertex v assembles A_v, the restriction of A_(h,gamma) to the
-// d*3^d dofs of the vertex star (Sec. 5.1, Eq. viim), from the 2^d cells of the
+// d*3^d dofs of the vertex star (Sec. 4.1, Eq. viim), from the 2^d cells of the
 // star, and inverts it in the arithmetic R: FP64, or double-float (DF64, about 48
 // significant bits in FP32 pairs, see df64.cuh) when only the FP32 cycle needs the
 // inverse to FP32 accuracy.  A_v is symmetric, so only its upper triangle is

@@ -1,4 +1,4 @@
-// K2/K3/K4: vertex-star patches of the PSC smoother (Sec. 5.1, Eq. (viim)).
+// K2/K3/K4: vertex-star patches of the PSC smoother (Sec. 4.1, Eq. (viim)).
 //
 // For every vertex v the local space V_v = {v in V_h : supp v in star(v)} is
 // spanned by the free dofs at the 3^d Q2 nodes within half a cell of v.  Its

@@ -1,4 +1,4 @@
-// K5: standard Q2 prolongation P_H and its transpose (Sec. 5.2).
+// K5: standard Q2 prolongation P_H and its transpose (Sec. 4.2).
 //
 // V_H is a subspace of V_h, so P_H is nested interpolation: a fine node at a
 // coarse node takes its value; a fine node at a quarter point of a coarse cell

@@ -13,7 +13,7 @@ Sampling layout (the one the C ABI expects):
   * nodal arrays live on the Q2 node lattice ((2n+1) nodes per direction,
     x fastest), one array per velocity component.
 
-Workloads follow the multi-sinker benchmark of Sec. 6.2 (viscosity and
+Workloads follow the multi-sinker benchmark of Sec. 5.2 (viscosity and
 buoyancy law, DR(mu) = mu_max/mu_min with mu_max = DR^(1/2),
 mu_min = DR^(-1/2)) and the manufactured solution used for the convergence
 check.  The readings of the garbled sinker formula are stated in the
@@ -82,7 +82,7 @@ def node_points(d, n):
 
 
 # ----------------------------------------------------------------------------
-# multi-sinker benchmark (Sec. 6.2)
+# multi-sinker benchmark (Sec. 5.2)
 # ----------------------------------------------------------------------------
 def sinker_centres(seed, count, d):
     rng = np.random.default_rng(seed)

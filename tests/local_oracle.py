@@ -6,7 +6,7 @@ may, but every output of one operator step depends on a handful of cells:
 
   * a row of A_gamma x (Secs. 2-3, Eqs. stokessys/augstokessys) on the 2^d cells around
     its node;
-  * the vertex-star patch matrix A_v (Sec. 5.1, Eq. viim) on the 2^d cells around v;
+  * the vertex-star patch matrix A_v (Sec. 4.1, Eq. viim) on the 2^d cells around v;
   * an entry of z = sum_v I_v A_v^-1 I_v^T r on the <= 2^d stars that hold its node;
   * an entry of P~ e_c (Eq. Ptilde) on the one coarse cell that holds its node;
   * an entry of P~^T r_f on the coarse cells around its coarse node.
@@ -191,7 +191,7 @@ class LocalLevel:
 
 
 class LocalTransfer:
-    """P_H, P~ and P~^T between a coarse and a fine LocalLevel (Sec. 5.2, Eq. Ptilde)."""
+    """P_H, P~ and P~^T between a coarse and a fine LocalLevel (Sec. 4.2, Eq. Ptilde)."""
 
     def __init__(self, coarse: LocalLevel, fine: LocalLevel):
         self.c, self.f = coarse, fine

@@ -334,7 +334,7 @@ def test_discrete_divergence_at_roundoff():
 
 
 # --------------------------------------------------------------------------
-# Sec. 5: transfers, smoother, V-cycle
+# Sec. 4: transfers, smoother, V-cycle
 # --------------------------------------------------------------------------
 def test_prolongation_1d_closed_form():
     assert np.allclose(prolongation_1d(1), _golden("prolongation_1d.txt"), atol=0)
