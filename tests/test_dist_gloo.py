@@ -73,3 +73,25 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
 
     assert bench.reference_arm(Args(), bench._RankOnly()) is None
     assert calls == []                                # rank 1 did no work
+
+
+def test_reference_arm_json_contract():
+    """bench.py --impl reference on the host: one JSON line with the base contract's keys,
+    the oracle as the reference (kind, cores, sample) and an e2e without host transfers."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--workload", "sinker2d_128"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["value"] > 0 and rec["unit"] == "DoF/s"
+    assert rec["higher_is_better"] is True and rec["steps"] == 1 and rec["warmup"] == 0
+    assert rec["config"]["workload"] == "sinker2d_128"
+    cb = rec["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == rec["value"]
+    e2e = rec["e2e"]
+    assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
