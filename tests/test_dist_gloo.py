@@ -95,3 +95,29 @@ def test_reference_arm_json_contract():
     e2e = rec["e2e"]
     assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_sampler_parses_nvidia_smi_samples(tmp_path):
+    """The clocks record of the bench line: median SM clock under load, the maximum, and
+    every throttle reason seen Active in any sample (sw_power_cap kept, the others flagged)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    csv = tmp_path / "clocks.csv"
+    csv.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                   "0, 2010, 2070, 1350.2, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "garbage line\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = Done(), str(csv)
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2010 and rec["sm_max_mhz"] == 2070 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert not csv.exists()
