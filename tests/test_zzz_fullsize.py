@@ -229,7 +229,7 @@ def test_solve_in_bench_configuration(full):
     """a8-a10 at full size: the benchmark's mixed solve converges to 1e-8; its true
     residual, evaluated cell by cell by the oracle (scalar workloads), meets the same
     bound; the all-FP64 GPU solve needs at most 2 fewer iterations and the two
-    solutions agree (velocity 1e-6, pressure 1e-5, relative l2)."""
+    solutions agree (relative l2: 1e-7 on the 3D workloads, 1e-6 / 1e-5 in 2D)."""
     pb = full.pb
     u, p, info = full.ctx.solve(pb.f, pb.u_bc)
     assert info.converged == 1 and info.res_final <= bench.RTOL * info.res0
@@ -247,4 +247,8 @@ def test_solve_in_bench_configuration(full):
     assert info.iterations <= info64.iterations + 2, (info.iterations, info64.iterations)
     du = np.linalg.norm(u - u64) / np.linalg.norm(u64)
     dp = np.linalg.norm(p - p64) / np.linalg.norm(p64)
-    assert du <= 1e-6 and dp <= 1e-5, (du, dp)
+    # the mixed path's 1e-7 bar on the two 3D workloads (the benchmark measured 3e-9 / 4e-10
+    # and 9e-13 / 1e-11 there); the 2D workload, not yet measured at full size, gets the
+    # small-mesh bound of the mixed-solve parity test
+    bu, bp = (1e-7, 1e-7) if full.d == 3 else (1e-6, 1e-5)
+    assert du <= bu and dp <= bp, (du, dp)
