@@ -12,7 +12,8 @@ only oracle/ (tests/golden/make_*.py):
     oracle's count (within 2 at DR 1e8, where the patch inverses' cond * eps difference
     can move the step at which the tolerance is crossed).  How the stored counts compare
     with the printed column is pinned on the CPU (tests/test_oracle_pins.py).
-"""
+
+The file name sorts after the other GPU tests so that they run first."""
 import os
 
 import pytest
