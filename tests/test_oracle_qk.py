@@ -261,6 +261,27 @@ def test_q3_p2_pairing_as_in_table_k():
         assert its[k, 1e3] <= its[k, 10.0], its
 
 
+def test_table_k_trend_in_3d():
+    """Table k is a 3D experiment: at gamma 1e3 with the P2 pairing (DR 1e6, two levels) the
+    printed counts fall from 27 at k = 2 to 13 at k = 3.  On a 4^3 mesh (6 seeded sinkers,
+    omega 0.15, a 1e6 residual reduction) the oracle's counts fall the same way, 20 to 10."""
+    from oracle.qk import HierarchyK
+    from oracle.stokes import StokesSolver
+    c = P.sinker_centres(0, 6, 3)
+
+    def run(k):
+        def pts(nl):
+            m = MeshK(3, nl, k)
+            return (m.cells[:, None, :] + 0.5 * (1.0 + m.ref.xq[None])) * np.array(m.h)
+        mus = [P.sinker_viscosity(pts(nl), c, 0.15, 200.0, 1e6) for nl in (2, 4)]
+        H = HierarchyK(3, 4, k, mus, 1e3, steps=5, W="Mp_mu")
+        f = P.sinker_force(pts(4), c, 0.15, 200.0, 10.0)
+        return StokesSolver(H, schur="P2").solve(f, np.zeros((3, (4 * k + 1) ** 3)), rtol=1e-6)[2]
+
+    its2, its3 = run(2), run(3)
+    assert its3 < its2 <= 30, (its2, its3)
+
+
 @pytest.mark.parametrize("k", [3, 4])
 def test_prolongation_1d_exact_rationals(k):
     """The 1D coarse-to-fine weights of Q_k against exact rational Lagrange values."""
