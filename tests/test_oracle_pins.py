@@ -701,3 +701,37 @@ def test_schur_blocks_closed_form_constant_mu():
     assert np.allclose(schur_blocks(lv2, "P2")[0], 6.0 * 2.0 * np.diag([1.0, 3.0, 3.0]) / vol)
     # with constant mu, W = M_p(1/mu) = M_p / mu: the AL term scales by mu
     assert abs(lv2.G_raw - 2.0 * lv.G_raw).max() < 1e-12 * abs(lv.G_raw).max()
+
+
+def _round_patch_inverses(H, fn):
+    for ps in H.patches[1:]:
+        for key, (ids, idx, blocks, inv) in list(ps.groups.items()):
+            ps.groups[key] = (ids, idx, blocks, fn(inv))
+
+
+def _bf16(x):
+    b = x.astype(np.float32).view(np.uint32)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)   # round to nearest even
+    return b.view(np.float32).astype(np.float64)
+
+
+def test_reduced_precision_patch_storage():
+    """Storing the star-patch inverses in FP32 changes no FGMRES iteration count; storing them
+    in BF16 (8-bit mantissa, the scope's optional variant) holds at gamma 10 but loses the
+    convergence at gamma 1e3 (2D 32^2 sinker problem, DR 1e4, three levels, GMRES(5)): the
+    inverse of a star block of A_gamma resolves its small divergence-free eigenvalues beside
+    entries of order gamma, so a relative storage error eps perturbs the smoother by about
+    eps gamma on the kernel the star patches exist to capture (Sec. 4.1)."""
+    its = {}
+    for gamma in (10.0, 1e3):
+        pb = P.sinker_problem(2, 32, 3, 8, 0.1, 200.0, 1e4, 10.0, gamma, 0)
+        for store in ("fp64", "fp32", "bf16"):
+            H = Hierarchy(2, pb.n, pb.mu, gamma, steps=5)
+            if store == "fp32":
+                _round_patch_inverses(H, lambda x: x.astype(np.float32).astype(np.float64))
+            elif store == "bf16":
+                _round_patch_inverses(H, _bf16)
+            its[gamma, store] = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=1e-8, maxit=60)[2]
+    assert its[10.0, "fp32"] == its[10.0, "fp64"] and its[1e3, "fp32"] == its[1e3, "fp64"], its
+    assert its[10.0, "bf16"] <= its[10.0, "fp64"] + 2, its
+    assert its[1e3, "fp64"] < 20 and its[1e3, "bf16"] == 60, its           # 60 = not converged
