@@ -261,6 +261,40 @@ def test_q3_p2_pairing_as_in_table_k():
         assert its[k, 1e3] <= its[k, 10.0], its
 
 
+def test_table_linear_2d_pattern():
+    """Table linear's 2D block ([Q3]^2 x P2disc, P1 and P2, DR 1e6 and 1e10, 1e6 residual
+    reduction) at small scale (8^2 cells, two levels): at gamma = 0 both Schur blocks reduce
+    to M_p(1/mu)^-1, so P1 and P2 need the same count, with the Jacobi smoother and standard
+    transfer as with the robust ones, and at DR 1e10 the gamma = 0 solve does not converge
+    within 300 iterations (the table's dashes); with gamma > 0 the robust solver converges at
+    both contrasts, P1 needs no more iterations than P2 at gamma = 10, and gamma = 1e3 needs
+    no more than gamma = 10 (printed 11/22 and 19/27 at gamma 10, 13/15 and 12/16 at 1e3;
+    here 17/28, 33/152 and 10/15, 11/24)."""
+    from oracle.qk import HierarchyK
+    from oracle.stokes import StokesSolver
+    c = P.sinker_centres(0, 4, 2)
+
+    def run(g, dr, var, smoother="gmres", transfer="robust"):
+        def pts(nl):
+            m = MeshK(2, nl, 3)
+            return (m.cells[:, None, :] + 0.5 * (1.0 + m.ref.xq[None])) * np.array(m.h)
+        mus = [P.sinker_viscosity(pts(nl), c, 0.1, 200.0, dr) for nl in (4, 8)]
+        H = HierarchyK(2, 8, 3, mus, g, steps=5, W="Mp" if var == "P1" else "Mp_mu",
+                       smoother=smoother, transfer=transfer)
+        f = P.sinker_force(pts(8), c, 0.1, 200.0, 10.0)
+        return StokesSolver(H, schur=var).solve(f, np.zeros((2, 25 ** 2)), rtol=1e-6)[2]
+
+    assert run(0.0, 1e6, "P1", "jacobi", "standard") == run(0.0, 1e6, "P2", "jacobi", "standard")
+    assert run(0.0, 1e6, "P1") == run(0.0, 1e6, "P2") < 300
+    assert run(0.0, 1e10, "P1") == 300
+    for dr in (1e6, 1e10):
+        its = {(g, v): run(g, dr, v) for g in (10.0, 1e3) for v in ("P1", "P2")}
+        assert max(its.values()) < 300, (dr, its)
+        assert its[10.0, "P1"] <= its[10.0, "P2"], (dr, its)
+        for v in ("P1", "P2"):
+            assert its[1e3, v] <= its[10.0, v], (dr, its)
+
+
 def test_table_k_trend_in_3d():
     """Table k is a 3D experiment: at gamma 1e3 with the P2 pairing (DR 1e6, two levels) the
     printed counts fall from 27 at k = 2 to 13 at k = 3.  On a 4^3 mesh (6 seeded sinkers,
