@@ -121,3 +121,27 @@ def test_clock_sampler_parses_nvidia_smi_samples(tmp_path):
     assert rec["sm_mhz"] == 2010 and rec["sm_max_mhz"] == 2070 and rec["samples"] == 3
     assert rec["reasons"] == ["sw_power_cap"]
     assert not csv.exists()
+
+
+def test_roofline_inputs(tmp_path, monkeypatch):
+    """The roofline fields' inputs: the measured HBM peak from MEASURED_PEAKS.json (else the
+    stated 6.8 TB/s fallback), and the committed per-launch DRAM traffic, which is reported
+    only while the kernel source still has the hash it was captured on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak, kind = bench.measured_peak_hbm()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured" and 1000 < peak < 20000
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
+    assert bench.stored_traffic("k_patch_apply_f32_fine", "sinker3d_32") > 0
+    assert bench.stored_traffic("k_patch_apply_f32_fine", "no_such_workload") is None
+    # a source that no longer matches its recorded hash gives no traffic
+    fake = tmp_path / "profiles"
+    fake.mkdir()
+    (tmp_path / "src.cu").write_text("changed")
+    (fake / "traffic.txt").write_text("k w src.cu 0000000000000000 123\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.stored_traffic("k", "w") is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "nowhere"))
+    assert bench.measured_peak_hbm() == (6800.0, "fallback")
