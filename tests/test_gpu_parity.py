@@ -1,7 +1,7 @@
 """GPU parity: every C-ABI entry point against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative l2):
-  * FP64 operator applies, transfers, coarse solve: 1e-12 (spec bar);
+  * FP64 operator applies, transfers, coarse solve: 1e-12 (the FP64 parity bar);
   * FP64 patch inverses / smoother / V-cycle: the oracle factors each patch with
     LAPACK and the GPU with its own Cholesky, so the two inverses differ by
     O(cond(A_v) eps); the tests use well-conditioned cases at 1e-12 and a
