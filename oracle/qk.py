@@ -27,7 +27,6 @@ k = 2 as well (3^d nodes), so (2k - 1)^d is used.
 from __future__ import annotations
 
 import itertools
-import math
 from functools import cached_property
 
 import numpy as np

@@ -4,7 +4,7 @@ single-instance calls, which are themselves parity-tested against the oracle."""
 import numpy as np
 import pytest
 
-from gpu_helpers import context, dev, host, oracle, rel, sinker
+from gpu_helpers import context, dev, oracle, rel, sinker
 
 torch = pytest.importorskip("torch")
 from paper_2107_00820_gb300 import alstokes as A  # noqa: E402
