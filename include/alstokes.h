@@ -137,6 +137,8 @@ void als_default_options(als_options* opt);
 als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
                       void* stream, als_ctx** out);
 
+/* Waits for the context's stream, then frees everything the context owns (device
+ * buffers, captured graphs, events, its stream).  NULL: ALS_EINVAL. */
 als_status als_destroy(als_ctx* ctx);
 
 /* y = A_gamma x on `level` (Eq. (augstokessys); W = M_p, or M_p(1/mu) with
@@ -145,8 +147,8 @@ als_status als_destroy(als_ctx* ctx);
  * (ALS_PREC_FP64: double, ALS_PREC_FP32: float).  Boundary rows: y_D = x_D. */
 als_status als_apply_agamma(als_ctx* ctx, int level, int prec, const void* x, void* y);
 
-/* x = one V-cycle for A_gamma x = b on the finest level from x = 0
- * (pre-smoothing, robust restriction, recursion, coarse Cholesky solve,
+/* x = one V-cycle (Sec. 4, Fig. algo-outline) for A_gamma x = b on the finest level
+ * from x = 0 (pre-smoothing, robust restriction, recursion, coarse Cholesky solve,
  * robust prolongation, post-smoothing).  b, x: device, precision `prec`;
  * ALS_PREC_FP32 runs the whole cycle in FP32 except the FP64 coarse solve. */
 als_status als_vcycle(als_ctx* ctx, int prec, const void* b, void* x);
@@ -166,8 +168,9 @@ als_status als_coarse_solve(als_ctx* ctx, int prec, const void* b, void* x);
  * [yu; yp] = [[A_gamma, B^T], [B, 0]] [u; p] (device vectors). */
 als_status als_apply_stokes(als_ctx* ctx, const double* u, const double* p, double* yu, double* yp);
 
-/* Copies the FP64 inverse of the patch matrix of vertex `vertex` on `level`
- * as a full (d*3^d) x (d*3^d) row-major matrix to `out` (host or device).
+/* Copies the FP64 inverse of the patch matrix A_v (Sec. 4.1, Eq. (viim)) of
+ * vertex `vertex` on `level` as a full (d*3^d) x (d*3^d) row-major matrix to
+ * `out` (host or device).
  * In ALS_MODE_MIXED the patches are assembled and inverted in double-float
  * arithmetic (about 48 significant bits), else in FP64.
  * Patch dof order: component-major, node offsets (-1,0,1)^d x-fastest;
@@ -219,7 +222,7 @@ long long als_kernel_launches(void);
  * smooth -- code running inside a stream capture in global mode (where
  * cudaMalloc is not allowed), real-time loops that reserve all device memory
  * up front, or plugins whose host framework owns the allocator.  It computes
- * the same z = sum_v I_v A_v^-1 I_v^T r as als_star_smooth, but without a
+ * the same z = sum_v I_v A_v^-1 I_v^T r (Sec. 4.1) as als_star_smooth, but without a
  * context: the caller passes the mesh, the packed patch inverses, r and z
  * (all device memory it already owns), and the per-patch scratch the
  * smoother needs between its two kernels is a fixed device array of
