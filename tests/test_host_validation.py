@@ -118,3 +118,33 @@ def test_every_entry_point_refuses_a_null_context(lib):
         assert getattr(lib, name)(*args) == A.ALS_EINVAL, name
     assert lib.als_star_smooth_static(4, N, 1, N, N, N, N) == A.ALS_EINVAL
     assert lib.als_batch_last_error(None) == b"null batch"
+
+
+def test_binding_marshalling_checks(lib):
+    """The binding's own argument checks, before any call crosses the ABI: contiguous
+    arrays only, the dtype that matches the precision, CUDA tensors for the device entry
+    points, known option names, and readable status names in its errors."""
+    x = np.zeros((4, 4))
+    assert A._ptr(None) is None and A._ptr(x).value == x.ctypes.data
+    with pytest.raises(ValueError):
+        A._ptr(x[:, ::2])
+    with pytest.raises(TypeError):
+        A._ptr([1.0, 2.0])
+    A._check_dtype(np.zeros(2), A.ALS_PREC_FP64)
+    A._check_dtype(np.zeros(2, np.float32), A.ALS_PREC_FP32)
+    with pytest.raises(TypeError):
+        A._check_dtype(np.zeros(2, np.float32), A.ALS_PREC_FP64)
+    with pytest.raises(TypeError):
+        A._check_dtype(np.zeros(2), A.ALS_PREC_FP32)
+    with pytest.raises(TypeError):
+        A._cuda_tensor(np.zeros(2))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        A._cuda_tensor(torch.zeros(2))                         # a CPU tensor is refused too
+    with pytest.raises(ValueError):
+        A._ptr(torch.zeros(4, 4).t())
+    o = A.default_options(sweeps=3, mode=A.ALS_MODE_MIXED)
+    assert o.sweeps == 3 and o.mode == A.ALS_MODE_MIXED
+    with pytest.raises(KeyError):
+        A.default_options(no_such_option=1)
+    assert str(A.ALSError(A.ALS_ENOTSPD, "patch 7")) == "ALS_ENOTSPD: patch 7"
