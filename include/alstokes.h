@@ -59,7 +59,9 @@ typedef enum {
   ALS_ENOTSPD = 4,     /* non-positive pivot in the symmetric sweep of a patch or the coarse operator */
   ALS_ENOTCONV = 5,    /* FGMRES did not reach rtol within maxit iterations */
   ALS_EBREAKDOWN = 6,  /* Krylov breakdown or a non-finite residual */
-  ALS_ETIMEOUT = 7     /* reserved: a bounded device-side wait gave up */
+  ALS_ETIMEOUT = 7     /* a bounded device-side wait gave up: the FP32 star-smoother kernel's wait
+                          for its inverse blocks (als_set_wait_limit); the kernel records it, waits
+                          for its own copies in flight and returns, the context stays usable */
 } als_status;
 
 enum { ALS_COEFF_SCALAR = 0, ALS_COEFF_TENSOR = 1 };
@@ -70,6 +72,7 @@ enum { ALS_TRANSFER_ROBUST = 0, ALS_TRANSFER_STANDARD = 1 };
 enum { ALS_SCHUR_P1 = 0, ALS_SCHUR_P2 = 1 };
 enum { ALS_CYCLE_V = 0, ALS_CYCLE_F = 1 };
 enum { ALS_FACT_FULL = 0, ALS_FACT_UPPER = 1, ALS_FACT_LOWER = 2, ALS_FACT_DIAG = 3 };
+enum { ALS_SETUP_AUTO = 0, ALS_SETUP_FP64 = 1 };
 
 /* Unit box (0,1)^dim with n[k] cells per direction on the finest level;
  * n[k] must be divisible by 2^(levels-1) and the coarsest level must have
@@ -109,6 +112,10 @@ typedef struct {
                      two cycles per iteration); ALS_FACT_UPPER [[A, B^T], [0, -S]]^-1,
                      ALS_FACT_LOWER [[A, 0], [B, -S]]^-1, ALS_FACT_DIAG diag(A^-1, -S^-1):
                      one cycle per iteration */
+  int setup;      /* arithmetic of the patch and coarse inverses: ALS_SETUP_AUTO (default) =
+                     FP64 in ALS_MODE_FP64 and double-float (FP32 pairs, about 48 bits) in
+                     ALS_MODE_MIXED; ALS_SETUP_FP64 = FP64 in both modes (the mixed cycle then
+                     runs on the FP32 roundings of FP64-computed inverses) */
 } als_options;
 
 typedef struct {
@@ -129,7 +136,15 @@ void als_default_options(als_options* opt);
  * forms the per-cell Schur-complement blocks of the finest level.  Both
  * inversions use the symmetric sweep; they run in FP64 in ALS_MODE_FP64 and in
  * double-float arithmetic (FP32 pairs, about 48 significant bits) in
- * ALS_MODE_MIXED, whose cycle uses the FP32 inverses.
+ * ALS_MODE_MIXED unless options.setup = ALS_SETUP_FP64; the mixed cycle uses the
+ * FP32 inverses.
+ * levels = 1: no multigrid; the (1,1) block of the preconditioner is then solved
+ * exactly by the dense inverse of A_gamma on the mesh (the exact-A study of Sec. 3,
+ * Table exacttopleft); the dense inverse takes (d prod(2n-1))^2 doubles.
+ * Mixed mode with the P1 pairing (W = M_p) returns ALS_EINVAL when
+ * 2^-24 gamma / mu_min > 0.1 (mu_min: the smallest viscosity, or mu_eff, of all
+ * levels' points): the FP32 cycle does not converge there; the P2 pairing has no such
+ * limit.
  * stream: a cudaStream_t (NULL = legacy default stream).
  * Size limits (ALS_EINVAL): d (2n+1)^d velocity values, d 3^d n^d per-cell
  * outputs and d 3^d (n+1)^d vertex-star patch outputs (products over the axes)
@@ -178,8 +193,9 @@ als_status als_apply_stokes(als_ctx* ctx, const double* u, const double* p, doub
 als_status als_patch_inverse(als_ctx* ctx, int level, long long vertex, double* out);
 
 /* Solve the augmented Stokes system (Eqs. (stokessys), (augstokessys)) on the
- * finest level with FGMRES preconditioned by the block-LDU preconditioner of
- * Eq. (precond): V-cycle for A_gamma, P1 Schur approximation.
+ * finest level with FGMRES preconditioned by the block factorisation of
+ * Eq. (precond) chosen by options.fact: the multigrid cycle of options.cycle for
+ * A_gamma, and the Schur approximation of options.schur (P1 or P2, Eq. (P1P2)).
  *   f_qp : [cell][3^d][d] body force at the Gauss points (required)
  *   u_bc : [d][N] nodal Dirichlet values, only boundary entries are read (NULL = 0)
  *   r2   : [cell][d+1] divergence right-hand side (NULL = 0)
@@ -192,7 +208,9 @@ als_status als_solve(als_ctx* ctx, const double* f_qp, const double* u_bc, const
 /* Re-runs the setup of als_create (patch factorisations, coarse Cholesky,
  * Schur blocks) for new coefficients of the same kind and sizes, reusing every
  * allocation and the captured V-cycle graphs: the per-linearisation setup of
- * a nonlinear (Newton) iteration, Sec. 5.3.  Host or device pointers. */
+ * a nonlinear (Newton) iteration, Sec. 5.3.  Host or device pointers.
+ * The mixed-mode range check of als_create applies; when it refuses, the context
+ * holds the new coefficients but stale inverses: call again with valid ones. */
 als_status als_update_coefficients(als_ctx* ctx, const als_coeff* coeff);
 
 /* Live timing of the finest-level vertex-star patch kernel inside V-cycles:
@@ -213,20 +231,48 @@ als_status als_profile_read(als_ctx* ctx, double* total_ms, long long* launches)
  * accumulates separately and is reset by its own read.  ALS_EINVAL for another kind. */
 als_status als_profile_read_kernel(als_ctx* ctx, int kind, double* total_ms, long long* launches);
 
+/* Factor injection (tests and inspection): replace the setup's inverses by the
+ * caller's, so that the cycle can be compared with another implementation on
+ * identical factors (Sec. 4.1 patches, Sec. 5.1 coarse solve).
+ *   als_load_patch_inverses: `packed` (host or device) holds, for every vertex of
+ *     `level` (1 <= level < levels, vertex index x-fastest), the FP64 inverse of its
+ *     patch matrix in the layout of als_star_smooth_static's `inv` (upper triangle by
+ *     diagonals, padded to a multiple of 4 entries; identity rows at absent and
+ *     boundary nodes); the FP32 copies of the cycle are rounded from it.
+ *   als_load_coarse_inverse: `inv` (host or device) is the nfree x nfree row-major
+ *     inverse of the coarsest A_gamma on its free dofs, nfree = d prod(2 n_0 - 1),
+ *     free dofs ordered component-major, then interior nodes x-fastest.
+ * Both copy synchronously; als_update_coefficients overwrites them again. */
+als_status als_load_patch_inverses(als_ctx* ctx, int level, const double* packed);
+als_status als_load_coarse_inverse(als_ctx* ctx, const double* inv);
+
+/* Test switch: poll limit of the FP32 star-smoother kernel's wait for its inverse
+ * blocks (polls < 0 restores the default, about a second of polling).  With 0 the
+ * first wait of every CTA gives up at once: the call that ran the smoother then
+ * returns ALS_ETIMEOUT (after the kernel has waited, at the default limit, for the
+ * copies it had issued), and the next call with the default limit works normally.
+ * Drops the captured cycles (they embed the limit). */
+als_status als_set_wait_limit(als_ctx* ctx, int polls);
+
+/* Residual history of the context's last solve: out[0] = |b| of the augmented,
+ * lifted system, out[k] = the FGMRES residual estimate after iteration k.  Copies
+ * min(cap, count) values; *count gets the length (iterations + 1). */
+als_status als_solve_history(const als_ctx* ctx, double* out, int cap, int* count);
+
 /* Process-wide number of kernels this library has launched (a replay of a
  * captured V-cycle counts its kernel nodes). */
 long long als_kernel_launches(void);
 
 /* Allocation-free star smoother.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they
- * smooth -- code running inside a stream capture in global mode (where
- * cudaMalloc is not allowed), real-time loops that reserve all device memory
- * up front, or plugins whose host framework owns the allocator.  It computes
- * the same z = sum_v I_v A_v^-1 I_v^T r (Sec. 4.1) as als_star_smooth, but without a
- * context: the caller passes the mesh, the packed patch inverses, r and z
- * (all device memory it already owns), and the per-patch scratch the
- * smoother needs between its two kernels is a fixed device array of
- * ALS_STATIC_SCRATCH_BYTES inside this library.
+ * smooth -- real-time loops that reserve all device memory up front, plugins
+ * whose host framework owns the allocator, or code where the implicit device
+ * synchronisation of an allocation is not acceptable.  It computes the same z as
+ * als_star_smooth, but without a context: the caller passes the mesh, the packed
+ * patch inverses, r and z (all device memory it already owns), and the per-patch
+ * scratch the smoother needs between its two kernels is a fixed device array of
+ * ALS_STATIC_SCRATCH_BYTES inside this library, which every GPU that loads the
+ * library holds until the process exits.
  *   dim, n : mesh of the level (n[k] cells per direction, n[2] ignored in 2D)
  *   prec   : ALS_PREC_FP64 (double inv/r/z) or ALS_PREC_FP32 (float)
  *   inv    : device, one block per vertex (vertex index x-fastest), each block
@@ -236,10 +282,11 @@ long long als_kernel_launches(void);
  *   r, z   : device velocity vectors of the level (boundary entries of z = 0)
  *   stream : cudaStream_t the two kernels are queued on; the call returns
  *            without waiting for them
- * Returns ALS_EINVAL if (n+1)^d * d*3^d * sizeof(element) exceeds
- * ALS_STATIC_SCRATCH_BYTES (32 MiB: e.g. up to 32^3 hexes in FP64, 45^3 in
- * FP32).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Returns ALS_EINVAL for n[k] outside [1, 4096] or when
+ * (n+1)^d * d*3^d * sizeof(element) exceeds ALS_STATIC_SCRATCH_BYTES (32 MiB: e.g.
+ * up to 32^3 hexes in FP64, 45^3 in FP32), and ALS_ECUDA when a launch fails.
+ * The first call on a device (with that device current) looks up the array's
+ * device address and the SM count; make that first call before any stream capture.
  * Nothing is allocated and nothing needs to start at zero, but every call
  * shares the one array: calls that overlap on the GPU race. */
 #define ALS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -27,6 +27,8 @@ ALS_TRANSFER_ROBUST, ALS_TRANSFER_STANDARD = 0, 1
 ALS_SCHUR_P1, ALS_SCHUR_P2 = 0, 1
 ALS_CYCLE_V, ALS_CYCLE_F = 0, 1
 ALS_FACT_FULL, ALS_FACT_UPPER, ALS_FACT_LOWER, ALS_FACT_DIAG = 0, 1, 2, 3
+ALS_SETUP_AUTO, ALS_SETUP_FP64 = 0, 1
+ALS_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class als_mesh(Structure):
@@ -40,7 +42,7 @@ class als_coeff(Structure):
 class als_options(Structure):
     _fields_ = [("smoother", c_int), ("sweeps", c_int), ("tau", c_double), ("transfer", c_int),
                 ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int),
-                ("cycle", c_int), ("fact", c_int)]
+                ("cycle", c_int), ("fact", c_int), ("setup", c_int)]
 
 
 class als_solve_info(Structure):
@@ -81,6 +83,10 @@ SIGNATURES = {
     "als_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "als_autotune_info": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(ctypes.c_float)]),
     "als_set_patch_kernel": (c_int, [c_void_p, c_int, c_int]),
+    "als_load_patch_inverses": (c_int, [c_void_p, c_int, c_void_p]),
+    "als_load_coarse_inverse": (c_int, [c_void_p, c_void_p]),
+    "als_set_wait_limit": (c_int, [c_void_p, c_int]),
+    "als_solve_history": (c_int, [c_void_p, POINTER(c_double), c_int, POINTER(c_int)]),
 }
 
 _LIB = None
@@ -278,6 +284,27 @@ class Context:
     def set_patch_kernel(self, level, variant):
         self._call("als_set_patch_kernel", c_int(level), c_int(variant))
 
+    def load_patch_inverses(self, level, packed):
+        """Replace the patch inverses of `level` by FP64 ones packed by diagonals
+        (nverts x stride, host or device); the FP32 copies are rounded from them."""
+        self._call("als_load_patch_inverses", c_int(level), _ptr(packed))
+
+    def load_coarse_inverse(self, inv):
+        """Replace the coarse inverse (nfree x nfree FP64, host or device)."""
+        self._call("als_load_coarse_inverse", _ptr(inv))
+
+    def set_wait_limit(self, polls):
+        """Test switch: poll limit of the FP32 smoother kernel's waits (< 0: default)."""
+        self._call("als_set_wait_limit", c_int(polls))
+
+    def solve_history(self):
+        """Residual history of the last solve: |b|, then the estimate after each iteration."""
+        cnt = c_int()
+        self._call("als_solve_history", None, 0, byref(cnt))
+        out = (c_double * max(cnt.value, 1))()
+        self._call("als_solve_history", out, cnt.value, byref(cnt))
+        return np.array(out[: cnt.value])
+
     def profile_read_kernel(self, kind):
         """(total ms, launches) of kernel class `kind` (0 patch kernel, 1 operator apply)."""
         ms, n = c_double(), c_longlong()
@@ -425,7 +452,26 @@ def als_kernel_launches():
 
 
 def als_star_smooth_static(dim, n, prec, inv, r, z, stream=None):
-    """Allocation-free smoother (scratch in a fixed device array); queued on `stream`."""
+    """Allocation-free smoother (scratch in a fixed device array); queued on `stream`.
+
+    inv, r and z must be CUDA tensors of the precision's dtype holding at least
+    (n+1)^d packed inverses and d (2n+1)^d vector entries (checked here, so that no host
+    pointer or short buffer reaches the kernels)."""
+    for a in (inv, r, z):
+        _cuda_tensor(a)
+        _check_dtype(a, prec)
+    if dim in (2, 3) and len(n) >= dim and all(1 <= int(v) <= 4096 for v in n[:dim]):
+        np_ = dim * 3 ** dim
+        stride = ((np_ * (np_ + 1) // 2) + 3) & ~3
+        nverts = int(np.prod([int(v) + 1 for v in n[:dim]]))
+        nu = dim * int(np.prod([2 * int(v) + 1 for v in n[:dim]]))
+        elt = 8 if prec == ALS_PREC_FP64 else 4
+        if nverts * np_ * elt > ALS_STATIC_SCRATCH_BYTES:
+            pass                    # beyond the fixed scratch: the library refuses it (ALS_EINVAL)
+        elif inv.numel() < nverts * stride:
+            raise ValueError(f"inv holds {inv.numel()} entries, the mesh needs {nverts * stride}")
+        elif r.numel() < nu or z.numel() < nu:
+            raise ValueError(f"r and z need {nu} entries")
     n = (list(n) + [1, 1, 1])[:3]
     st = load().als_star_smooth_static(dim, (c_int * 3)(*n), prec, _ptr(inv), _ptr(r), _ptr(z),
                                        c_void_p(stream) if stream else None)

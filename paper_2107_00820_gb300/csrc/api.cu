@@ -105,7 +105,9 @@ struct als_ctx {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double* u = nullptr;
     double* p = nullptr;
+    std::vector<double> hist;   // |b|, then the FGMRES residual estimate after each iteration
   } run;
+  unsigned long long* minbits = nullptr;   // device scratch of the smallest-viscosity check
 };
 
 namespace {
@@ -656,6 +658,7 @@ void als_default_options(als_options* opt) {
   opt->maxit = 300;
   opt->cycle = ALS_CYCLE_V;
   opt->fact = ALS_FACT_FULL;
+  opt->setup = ALS_SETUP_AUTO;
 }
 
 // message of the calling thread's last failed als_create (the context is gone by then)
@@ -682,8 +685,41 @@ als_status als_destroy(als_ctx* ctx) {
 
 // Setup (Secs. 4-5) with the coefficients of every level: copies them, builds
 // the vertex-star patch inverses, the coarse factorisation and the Schur blocks.
+// Smallest viscosity of all levels' points (mu, or mu_eff for tensor coefficients).
+// The FP32 cycle of the P1 pairing (augmentation weight W = M_p) evaluates the AL
+// term gamma div u beside viscous terms of size mu_min in single precision; once
+// 2^-24 gamma / mu_min exceeds 0.1 it no longer converges (measured on the 3D 32^3
+// sinker problem at DR 1e6 and 1e8), so mixed mode refuses that pairing there; the
+// P2 pairing (W = M_p(1/mu)) scales the AL term with mu and has no such limit.
+static als_status check_mixed_range(als_ctx* c) {
+  if (c->opt.mode != ALS_MODE_MIXED || c->opt.schur != ALS_SCHUR_P1 || c->gamma == 0.0) return ALS_OK;
+  const int NB = c->dim == 2 ? 9 : 27;
+  const unsigned long long inf_bits = 0x7ff0000000000000ull;
+  cudaMemcpyAsync(c->minbits, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, c->stream);
+  for (int l = 0; l < c->L; ++l)
+    vec_min_positive(c->lev[l].g.ncells * NB, c->lev[l].mu64, c->minbits, c->stream);
+  unsigned long long bits = inf_bits;
+  if (cudaMemcpyAsync(&bits, c->minbits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_check(c, "viscosity range");
+  double mu_min;
+  memcpy(&mu_min, &bits, sizeof(mu_min));
+  const double lim = 0.1 / std::ldexp(1.0, -24);   // gamma / mu_min above which the FP32 P1 cycle fails
+  if (c->gamma / mu_min > lim) {
+    char buf[320];
+    snprintf(buf, sizeof(buf),
+             "mixed precision with the P1 pairing needs 2^-24 gamma / mu_min <= 0.1 (gamma / mu_min = %.3g > %.3g): "
+             "use ALS_SCHUR_P2 (W = M_p(1/mu)) or ALS_MODE_FP64",
+             c->gamma / mu_min, lim);
+    return fail(c, ALS_EINVAL, buf);
+  }
+  return ALS_OK;
+}
+
 static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   const int NB = c->dim == 2 ? 9 : 27;
+  // FP64 or double-float arithmetic for the patch and coarse inverses
+  const int df64 = c->opt.mode == ALS_MODE_MIXED && c->opt.setup != ALS_SETUP_FP64 ? 1 : 0;
   for (int l = 0; l < c->L; ++l) {
     LevelDev& Lv = c->lev[l];
     const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
@@ -697,16 +733,20 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
       if (cudaMemcpyAsync(Lv.mu64, coeff->mu_eff[l], nq * sizeof(double), cudaMemcpyDefault, c->stream) != cudaSuccess)
         return cuda_check(c, "copy mu_eff");
     }
+  }
+  ALS_TRY(check_mixed_range(c));
+  for (int l = 0; l < c->L; ++l) {
+    LevelDev& Lv = c->lev[l];
     if (Lv.winv64) {
       schur_setup(Lv.g, c->gamma, Lv.mu64, nullptr, c->st, c->stream, 1, Lv.winv64, Lv.winv32);
       ALS_TRY(cuda_check(c, "mass blocks"));
     }
     if (l > 0) {
-      patch_setup(Lv, c->gamma, 1, c->opt.mode == ALS_MODE_MIXED ? 1 : 0, c->st, c->stream);
+      patch_setup(Lv, c->gamma, 1, df64, c->st, c->stream);
       ALS_TRY(cuda_check(c, "patch setup"));
     }
   }
-  coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream, c->opt.mode == ALS_MODE_MIXED ? 1 : 0);
+  coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream, df64);
   ALS_TRY(cuda_check(c, "coarse setup"));
   const LevelDev& F = c->lev[c->L - 1];
   schur_setup(F.g, c->gamma, F.mu64, c->schur, c->st, c->stream, c->opt.schur == ALS_SCHUR_P2 ? 1 : 0);
@@ -740,6 +780,8 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.transfer != ALS_TRANSFER_ROBUST && c->opt.transfer != ALS_TRANSFER_STANDARD)
     return fail(c, ALS_EINVAL, "unknown transfer");
   if (c->opt.mode != ALS_MODE_FP64 && c->opt.mode != ALS_MODE_MIXED) return fail(c, ALS_EINVAL, "unknown mode");
+  if (c->opt.setup != ALS_SETUP_AUTO && c->opt.setup != ALS_SETUP_FP64)
+    return fail(c, ALS_EINVAL, "unknown setup arithmetic");
   const int f = 1 << (c->L - 1);
   for (int k = 0; k < c->dim; ++k) {
     if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
@@ -764,6 +806,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     return cuda_check(c, "event create");
   ALS_TRY(dalloc(c, &c->st, 1));
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+  ALS_TRY(dalloc(c, &c->minbits, 1));
   const int NB = c->dim == 2 ? 9 : 27;
   const int NC = c->dim == 2 ? 6 : 21;
   c->lev.resize(c->L);
@@ -1003,6 +1046,44 @@ als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* ou
   return ALS_OK;
 }
 
+als_status als_load_patch_inverses(als_ctx* c, int level, const double* packed) {
+  ALS_TRY(check_level(c, level, PREC_F64));
+  if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no patches");
+  if (!packed) return fail(c, ALS_EINVAL, "null inverses");
+  const LevelDev& Lv = c->lev[level];
+  begin(c);
+  if (cudaMemcpyAsync(Lv.inv64, packed, sizeof(double) * Lv.g.nverts * Lv.pstride, cudaMemcpyDefault, c->stream) !=
+      cudaSuccess)
+    return cuda_check(c, "load patch inverses");
+  patch_derive32(Lv, c->stream);
+  return finish(c, "load patch inverses");
+}
+
+als_status als_load_coarse_inverse(als_ctx* c, const double* inv) {
+  if (!c || !inv) return c ? fail(c, ALS_EINVAL, "null inverse") : ALS_EINVAL;
+  const size_t n = (size_t)c->coarse.nfree;
+  begin(c);
+  if (cudaMemcpyAsync(c->coarse.inv, inv, sizeof(double) * n * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+    return cuda_check(c, "load coarse inverse");
+  return finish(c, "load coarse inverse");
+}
+
+als_status als_set_wait_limit(als_ctx* c, int polls) {
+  if (!c) return ALS_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  free_graphs(c);   // the captured cycles embed the limit as a kernel argument
+  for (LevelDev& Lv : c->lev) Lv.wait_polls = polls < 0 ? kWaitPolls : polls;
+  return ALS_OK;
+}
+
+als_status als_solve_history(const als_ctx* c, double* out, int cap, int* count) {
+  if (!c || !count || (cap > 0 && !out)) return ALS_EINVAL;
+  const std::vector<double>& h = c->run.hist;
+  *count = (int)h.size();
+  for (int i = 0; i < cap && i < (int)h.size(); ++i) out[i] = h[i];
+  return ALS_OK;
+}
+
 // ---- the outer solve in stages, so that a batch can interleave the FGMRES
 // iterations of several contexts (each on its own stream) with one host wait
 // per round: start (inputs, lifted rhs, |b| on its way to the host), then rounds
@@ -1063,6 +1144,7 @@ static als_status solve_rhs_done(als_ctx* c) {
   ALS_TRY(check_status(c, "solve rhs"));
   R.beta = c->host_res[1];
   R.resid = R.beta;
+  R.hist.assign(1, R.beta);
   R.converged = R.beta == 0.0;
   R.done = R.converged || c->opt.maxit <= 0;
   return ALS_OK;
@@ -1094,6 +1176,7 @@ static als_status solve_iter_done(als_ctx* c) {
   als_ctx::SolveRun& R = c->run;
   R.its = ++R.k;
   R.resid = c->host_res[0];
+  R.hist.push_back(R.resid);
   if (!std::isfinite(R.resid)) {
     R.done = true;
     ALS_TRY(check_status(c, "fgmres"));

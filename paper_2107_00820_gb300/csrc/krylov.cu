@@ -661,3 +661,33 @@ void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cuda
 }
 
 }  // namespace als
+
+namespace als {
+
+// Smallest positive entry of x (the bit patterns of positive doubles order like their
+// values, so an unsigned 64-bit atomic minimum finds it); entries <= 0 or NaN are skipped.
+// *out_bits must hold the bits of +inf before the first call.
+__global__ void k_min_positive(long long n, const double* __restrict__ x, unsigned long long* __restrict__ out_bits) {
+  unsigned long long best = 0x7ff0000000000000ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (v > 0.0) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+      best = b < best ? b : best;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+    best = other < best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(out_bits, best);
+}
+
+void vec_min_positive(long long n, const double* x, unsigned long long* out_bits, cudaStream_t s) {
+  if (n <= 0) return;
+  const long long want = (n + 255) / 256, blocks = want < 152LL * 8 ? want : 152LL * 8;
+  k_min_positive<<<(unsigned)blocks, 256, 0, s>>>(n, x, out_bits);
+  count_launch(1);
+}
+
+}  // namespace als

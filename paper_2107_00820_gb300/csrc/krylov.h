@@ -15,6 +15,8 @@ void dev_backsolve(int k, const double* H, int ldh, const double* g, double* y, 
 void dev_init_g(int m, const double* nrm2, double* g, double* beta, cudaStream_t s);
 void schur_apply(long long ncells, int npr, const double* S, const double* t, double* z, cudaStream_t s);
 void project_constant(long long ncells, int npr, double* p, double* partial, cudaStream_t s);
+// atomic minimum of the positive entries of x into *out_bits (the bits of a double; start at +inf)
+void vec_min_positive(long long n, const double* x, unsigned long long* out_bits, cudaStream_t s);
 
 // coarse.cu
 struct CoarseDev {

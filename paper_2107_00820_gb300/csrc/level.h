@@ -8,6 +8,10 @@
 
 namespace als {
 
+// Poll limit of the bounded mbarrier waits in the FP32 star-smoother kernel (each
+// poll backs off ~256 ns, so the default gives up after well over a second).
+constexpr int kWaitPolls = 1 << 22;
+
 struct LevelDev {
   Geom g;
   int tensor;            // 0: scalar mu per point, 1: Mandel tensor per point
@@ -28,6 +32,7 @@ struct LevelDev {
   int patch_kernel;      // FP32 patch-kernel variant picked by patch_autotune (-1: not yet tuned)
   float tune_ms[3];      // measured time per launch of each variant (ms)
   void* setup_tab;       // reference tables of the patch setup (setup_tab_bytes)
+  int wait_polls = kWaitPolls;   // poll limit of the smoother kernel's pipeline waits
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
@@ -76,6 +81,9 @@ void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y,
 // holds setup_tab_bytes(dim) bytes of scratch for the level's reference tables.
 void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s);
 size_t setup_tab_bytes(int dim);
+// the FP32 block-packed inverses (inv32) of every patch from the FP64 ones (inv64);
+// the setup calls it, and so does the loading of caller-supplied FP64 inverses
+void patch_derive32(const LevelDev& L, cudaStream_t s);
 // e0/e1 (optional) are recorded immediately before and after the patch kernel
 // den (optional device scalar of precision prec): z = D^-1 r / den (0 where den == 0)
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,

@@ -1,13 +1,13 @@
 // Allocation-free variant of the vertex-star smoother apply.
 //
 // Who this is for: code that must not allocate device memory at the moment it
-// smooths -- for example a caller that is itself inside a CUDA stream capture
-// in global mode (cudaMalloc is illegal there), a hard real-time loop that has
-// budgeted all device memory in advance, or a plugin whose host framework owns
-// the allocator and forbids direct cudaMalloc.  Such callers hold the patch
-// inverses and the vectors already; what they cannot provide is the per-patch
-// scratch buffer (one d*3^d vector per vertex) that the two-step,
-// deterministic smoother needs between its patch kernel and its gather kernel.
+// smooths -- a hard real-time loop that has budgeted all device memory in
+// advance, a plugin whose host framework owns the allocator and forbids direct
+// cudaMalloc, or a caller on a path where the implicit device synchronisation of
+// an allocation is not acceptable.  Such callers hold the patch inverses and the
+// vectors already; what they cannot provide is the per-patch scratch buffer (one
+// d*3^d vector per vertex) that the two-step, deterministic smoother needs
+// between its patch kernel and its gather kernel.
 //
 // This file keeps that scratch in one file-scope device array of fixed size
 // (ALS_STATIC_SCRATCH_BYTES).  Every GPU that loads the library reserves it
@@ -17,6 +17,8 @@
 // earlier in the same call, so nothing has to start at zero.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "../../include/alstokes.h"
 #include "common.cuh"
 
@@ -25,9 +27,14 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_star_scratch[ALS_STATIC_SCRATCH_BYTES];
 
-// device address of g_star_scratch, looked up once per device
+// Per device, looked up once by the first call made with that device current: the
+// device address of g_star_scratch (in host code the symbol itself is only a host-side
+// stand-in) and the SM count that sizes the patch kernel's grid.  Atomic, because
+// host threads may call concurrently; a cudaDeviceReset reloads the module, after
+// which these values are stale (the call is not meant to outlive the context).
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_addr[kMaxDevices];
+std::atomic<int> g_sm_count[kMaxDevices];
 
 template <int DIM>
 __device__ __forceinline__ bool star_node(const Geom& g, int vx, int vy, int vz, int o, long long& nd) {
@@ -109,12 +116,23 @@ __global__ void k_star_static_gather(Geom g, const T* __restrict__ out, T* __res
 }
 
 template <typename T, int DIM>
-void launch(const Geom& g, const void* inv, const void* r, void* z, void* scratch, cudaStream_t s) {
+cudaError_t launch(Geom g, const void* inv, const void* r, void* z, void* scratch, int sms, cudaStream_t s) {
   const long long blocks = (g.nverts + 7) / 8;
-  k_star_static<T, DIM><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
-      g, (const T*)inv, packed_stride(Sz<DIM>::NP), (const T*)r, (T*)scratch);
+  const long long cap = 16LL * sms;
+  int pstride = packed_stride(Sz<DIM>::NP);
+  const T* inv_t = (const T*)inv;
+  const T* r_t = (const T*)r;
+  T* out_t = (T*)scratch;
+  T* z_t = (T*)z;
+  void* a1[] = {&g, &inv_t, &pstride, &r_t, &out_t};
+  cudaError_t e = cudaLaunchKernel((const void*)k_star_static<T, DIM>, dim3((unsigned)(blocks < cap ? blocks : cap)),
+                                   dim3(256), a1, 0, s);
+  if (e != cudaSuccess) return e;
   const long long tot = g.N * DIM;
-  k_star_static_gather<T, DIM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, (const T*)scratch, (T*)z);
+  const T* sc_t = (const T*)scratch;
+  void* a2[] = {&g, &sc_t, &z_t};
+  return cudaLaunchKernel((const void*)k_star_static_gather<T, DIM>, dim3((unsigned)((tot + 255) / 256)), dim3(256),
+                          a2, 0, s);
 }
 
 }  // namespace
@@ -125,11 +143,14 @@ extern "C" als_status als_star_smooth_static(int dim, const int* n, int prec, co
   using namespace als;
   if ((dim != 2 && dim != 3) || !n || !inv || !r || !z) return ALS_EINVAL;
   if (prec != ALS_PREC_FP64 && prec != ALS_PREC_FP32) return ALS_EINVAL;
+  // every axis is bounded before any product is formed, so none of them can wrap
+  constexpr int kMaxCells = 4096;
+  for (int k = 0; k < dim; ++k)
+    if (n[k] < 1 || n[k] > kMaxCells) return ALS_EINVAL;
   Geom g{};
   g.dim = dim;
   for (int k = 0; k < 3; ++k) {
     const bool act = k < dim;
-    if (act && n[k] < 1) return ALS_EINVAL;
     g.n[k] = act ? n[k] : 1;
     g.nn[k] = act ? 2 * n[k] + 1 : 1;
     g.nv[k] = act ? n[k] + 1 : 1;
@@ -139,23 +160,30 @@ extern "C" als_status als_star_smooth_static(int dim, const int* n, int prec, co
   g.ncells = (long long)g.n[0] * g.n[1] * g.n[2];
   g.nverts = (long long)g.nv[0] * g.nv[1] * g.nv[2];
   const long long np = dim == 2 ? 18 : 81;
-  const long long need = g.nverts * np * (prec == ALS_PREC_FP64 ? 8 : 4);
+  const long long need = g.nverts * np * (prec == ALS_PREC_FP64 ? 8 : 4);   // < 4097^3 * 648, no overflow
   if (need > (long long)ALS_STATIC_SCRATCH_BYTES) return ALS_EINVAL;  // mesh too large for the fixed scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ALS_ECUDA;
-  if (!g_scratch_addr[dev]) {
+  void* scratch = g_scratch_addr[dev].load();
+  int sms = g_sm_count[dev].load();
+  if (!scratch || sms <= 0) {
+    // set-up of this device: the array's device address and the SM count
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_star_scratch) != cudaSuccess || !p) return ALS_ECUDA;
-    g_scratch_addr[dev] = p;
+    int count = 0;
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0)
+      return ALS_ECUDA;
+    g_scratch_addr[dev].store(p);
+    g_sm_count[dev].store(count);
+    scratch = p;
+    sms = count;
   }
   const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
   if (prec == ALS_PREC_FP64) {
-    if (dim == 2) launch<double, 2>(g, inv, r, z, g_scratch_addr[dev], s);
-    else launch<double, 3>(g, inv, r, z, g_scratch_addr[dev], s);
+    e = dim == 2 ? launch<double, 2>(g, inv, r, z, scratch, sms, s) : launch<double, 3>(g, inv, r, z, scratch, sms, s);
   } else {
-    if (dim == 2) launch<float, 2>(g, inv, r, z, g_scratch_addr[dev], s);
-    else launch<float, 3>(g, inv, r, z, g_scratch_addr[dev], s);
+    e = dim == 2 ? launch<float, 2>(g, inv, r, z, scratch, sms, s) : launch<float, 3>(g, inv, r, z, scratch, sms, s);
   }
-  if (cudaGetLastError() != cudaSuccess) return ALS_ECUDA;
-  return ALS_OK;
+  return e == cudaSuccess ? ALS_OK : ALS_ECUDA;
 }

@@ -129,7 +129,7 @@ __global__ void k_setup_tables(SetupGeo sg, R* __restrict__ tab) {
 template <int DIM, bool TENSOR, typename R>
 __global__ void __launch_bounds__(SetupCfg<DIM, TENSOR>::THREADS, TENSOR ? 2 : (std::is_same<R, DF64>::value ? 4 : 3))
 k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, const double* __restrict__ coef,
-              double* __restrict__ inv64, float* __restrict__ inv32, int pstride, DevStatus* st,
+              double* __restrict__ inv64, int pstride, DevStatus* st,
               const double* __restrict__ winv) {
   using C = SetupCfg<DIM, TENSOR>;
   using O = RealOps<R>;
@@ -337,17 +337,11 @@ k_patch_setup(Geom g, double gamma_d, SetupGeo sg, const R* __restrict__ tab, co
     }
     __syncthreads();
   }
-  // A_v^-1 = -M, packed by diagonals in FP64 and block-packed in FP32
-  if (inv32) {
-    constexpr BlockLayout BLp = BlockLayout(NP);
-    for (int e = 44 * BLp.nbp + BLp.nbp + tid; e < BLp.q2; e += nt) inv32[v * pstride + e] = 0.f;
-  }
+  // A_v^-1 = -M, packed by diagonals in FP64 (the FP32 copies are derived from it)
   for (int e = tid; e < C::NPK; e += nt) {
     int t = 0;
     while (diag_start(NP, t + 1) <= e) ++t;
-    const int i = e - diag_start(NP, t), j = i + t;
-    const R val = -M[tri_row(NP, i) + t];
-    if (inv64) inv64[v * pstride + e] = O::to_double(val);
-    if (inv32) inv32[v * pstride + BlockLayout(NP).index(i, j)] = O::to_float(val);
+    const int i = e - diag_start(NP, t);
+    inv64[v * pstride + e] = O::to_double(-M[tri_row(NP, i) + t]);
   }
 }

@@ -111,9 +111,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: ~2^22 polls with back-off (well over a second), false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// bounded wait: at most `polls` polls with back-off (the default, kWaitPolls = 2^22, is
+// well over a second), false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls = kWaitPolls) {
+  for (int it = 0; it < polls; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(256);
   }
@@ -312,7 +313,7 @@ __device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const
 template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
-                                                  DevStatus* st) {
+                                                  DevStatus* st, int wait_polls) {
   using C = TmaCfg<DIM, NST>;
   constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     } else {
       gather(grp + gridDim.x, rpre);
     }
-    if (!tma::mbar_wait(&bars[stage], parity)) {
+    if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
       if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
     }
     __syncthreads();                        // (A) r and the stage are visible
@@ -482,7 +483,8 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   }
   pdl_trigger();
   if (s_fail && tid == ISSUER) {
-    // drain: wait (bounded) for every copy this CTA issued and did not consume
+    // drain: wait (bounded, at the default limit whatever wait_polls is) for every copy
+    // this CTA issued and did not consume, so that none is in flight when the CTA exits
     int k = it;
     for (int grp = blockIdx.x + it * gridDim.x; grp < ngroups && k < it + NSTAGE; grp += gridDim.x, ++k)
       tma::mbar_wait(&bars[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1));
@@ -627,7 +629,7 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
   launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
-             (int)count, r, out, mode, st);
+             (int)count, r, out, mode, st, L.wait_polls);
   count_launch(1);
 }
 
@@ -667,9 +669,9 @@ static void patch_setup_impl(const LevelDev& L, double gamma, int store32, DevSt
   R* tab = static_cast<R*>(L.setup_tab);
   k_setup_tables<DIM, R><<<1, 256, 0, s>>>(sg, tab);
   k_patch_setup<DIM, TENSOR, R><<<(unsigned)L.g.nverts, C::THREADS, smem, s>>>(
-      L.g, gamma, sg, tab, TENSOR ? L.coef64 : L.mu64, L.inv64, store32 ? L.inv32 : nullptr, L.pstride, st,
-      L.winv64);
+      L.g, gamma, sg, tab, TENSOR ? L.coef64 : L.mu64, L.inv64, L.pstride, st, L.winv64);
   count_launch(2);
+  if (store32) patch_derive32(L, s);
 }
 
 template <int DIM, bool TENSOR>
@@ -689,6 +691,31 @@ void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStat
     if (L.tensor) patch_setup_arith<3, true>(L, gamma, store32, df64, st, s);
     else patch_setup_arith<3, false>(L, gamma, store32, df64, st, s);
   }
+}
+
+// FP32 block-packed copy (BlockLayout) of every FP64 inverse packed by diagonals: one
+// CTA per vertex, entry (i, i+t) of diagonal t rounded to the nearest float; the
+// padding slots of the layout are zeroed.
+template <int NP>
+__global__ void __launch_bounds__(128) k_derive32(long long nverts, int pstride, const double* __restrict__ inv64,
+                                                  float* __restrict__ inv32) {
+  constexpr BlockLayout BL = BlockLayout(NP);
+  const long long v = blockIdx.x;
+  if (v >= nverts) return;
+  const double* src = inv64 + v * pstride;
+  float* dst = inv32 + v * pstride;
+  for (int e = 44 * BL.nbp + BL.nbp + (int)threadIdx.x; e < BL.q2; e += blockDim.x) dst[e] = 0.f;
+  for (int t = 0; t < NP; ++t) {
+    const int base = diag_start(NP, t);
+    for (int i = threadIdx.x; i + t < NP; i += blockDim.x) dst[BL.index(i, i + t)] = (float)src[base + i];
+  }
+}
+
+void patch_derive32(const LevelDev& L, cudaStream_t s) {
+  if (L.g.nverts <= 0) return;
+  if (L.np == 81) k_derive32<81><<<(unsigned)L.g.nverts, 128, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
+  else k_derive32<18><<<(unsigned)L.g.nverts, 128, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
+  count_launch(1);
 }
 
 size_t setup_tab_bytes(int dim) {

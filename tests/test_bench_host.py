@@ -65,14 +65,19 @@ def test_roofline_inputs(tmp_path, monkeypatch):
         assert kind == "measured" and 1000 < peak < 20000
     else:
         assert (peak, kind) == (6800.0, "fallback")
-    assert bench.stored_traffic("k_patch_apply_f32_fine", "sinker3d_32") > 0
+    live = bench.stored_traffic("k_patch_apply_f32_fine", "sinker3d_32")
+    assert live is None or live > 0          # None once the kernel source has changed
     assert bench.stored_traffic("k_patch_apply_f32_fine", "no_such_workload") is None
-    # a source that no longer matches its recorded hash gives no traffic
+    # a source that matches its recorded hash gives the traffic; a changed one gives none
+    import hashlib
     fake = tmp_path / "profiles"
     fake.mkdir()
-    (tmp_path / "src.cu").write_text("changed")
-    (fake / "traffic.txt").write_text("k w src.cu 0000000000000000 123\n")
+    (tmp_path / "src.cu").write_text("kernel")
+    sha = hashlib.sha256(b"kernel").hexdigest()[:16]
+    (fake / "traffic.txt").write_text(f"k w src.cu {sha} 123\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.stored_traffic("k", "w") == 123.0
+    (tmp_path / "src.cu").write_text("changed")
     assert bench.stored_traffic("k", "w") is None
     monkeypatch.setattr(bench, "ROOT", str(tmp_path / "nowhere"))
     assert bench.measured_peak_hbm() == (6800.0, "fallback")

@@ -36,11 +36,14 @@ def _check_patches(ctx, H, d, picks, factor):
     return worst
 
 
-@pytest.mark.parametrize("d,n,gamma,dr", [(2, 8, 1e4, 1e6), (3, 4, 1e2, 1e4), (3, 4, 1e3, 1e8)])
-def test_mixed_patch_inverses_double_float(d, n, gamma, dr):
+@pytest.mark.parametrize("d,n,gamma,dr,schur", [(2, 8, 1e2, 1e6, A.ALS_SCHUR_P1), (2, 8, 1e4, 1e6, A.ALS_SCHUR_P2),
+                                                (3, 4, 1e2, 1e4, A.ALS_SCHUR_P1), (3, 4, 1e3, 1e8, A.ALS_SCHUR_P2)])
+def test_mixed_patch_inverses_double_float(d, n, gamma, dr, schur):
+    """(Mixed mode refuses the P1 pairing beyond 2^-24 gamma / mu_min = 0.1, so the extreme
+    cases use P2, whose augmentation weight W = M_p(1/mu) enters the patch matrices.)"""
     pb = sinker(d, n, 2, gamma, dr, seed=61)
-    ctx = context(pb, mode=A.ALS_MODE_MIXED)
-    H = oracle(pb, smoother="richardson", steps=1)
+    ctx = context(pb, mode=A.ALS_MODE_MIXED, schur=schur)
+    H = oracle(pb, smoother="richardson", steps=1, W="Mp_mu" if schur == A.ALS_SCHUR_P2 else "Mp")
     nverts = len(all_vertices(H.levels[1].mesh))
     picks = list(np.random.default_rng(62).choice(nverts, size=min(12, nverts), replace=False)) + [0, nverts - 1]
     _check_patches(ctx, H, d, picks, 40.0)

@@ -137,3 +137,54 @@ def test_fused_patch_gather_bitwise(tmp_path):
         outs.append(np.load(path))
     assert np.all(np.isfinite(outs[0]))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("d,n", [(2, 16), (3, 4)])
+def test_smoother_wait_timeout_is_reported_and_recoverable(d, n):
+    """ALS_ETIMEOUT: with the poll limit of the FP32 smoother kernel's wait for its
+    inverse blocks set to 0, every CTA's first wait gives up at once; the kernel records
+    the status, waits (at the default limit) for the bulk copies it had issued, and
+    returns.  The call reports ALS_ETIMEOUT, and after the default limit is restored the
+    context smooths exactly as before (same bits as a call that never timed out)."""
+    pb = sinker(d, n, 2, 1e2, dr=1e3, seed=61)
+    ctx = context(pb)
+    for lvl in range(1, pb.levels):
+        ctx.set_patch_kernel(lvl, 0)             # the TMA-ring variant: the one that waits
+    r = dev(np.random.default_rng(62).standard_normal(ctx.nu()), torch.float32)
+    z0 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z0, A.ALS_PREC_FP32)
+    ctx.set_wait_limit(0)
+    with pytest.raises(A.ALSError) as e:
+        ctx.star_smooth(1, r, torch.zeros_like(r), A.ALS_PREC_FP32)
+    assert e.value.status == A.ALS_ETIMEOUT
+    ctx.set_wait_limit(-1)
+    z1 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z1, A.ALS_PREC_FP32)
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z1)
+
+
+def test_mixed_p1_refused_beyond_its_range():
+    """Mixed mode with the P1 pairing refuses gamma / mu_min above 0.1 / 2^-24 (the FP32
+    cycle's measured limit), naming the pairing that works; P2 and FP64 mode accept the
+    same problem."""
+    pb = sinker(2, 16, 3, 1e4, dr=1e8, seed=63)      # gamma / mu_min = 1e8
+    with pytest.raises(A.ALSError) as e:
+        context(pb, mode=A.ALS_MODE_MIXED)
+    assert e.value.status == A.ALS_EINVAL and "ALS_SCHUR_P2" in str(e.value)
+    context(pb, mode=A.ALS_MODE_MIXED, schur=A.ALS_SCHUR_P2).close()
+    context(pb).close()
+    ok = sinker(2, 16, 3, 1e2, dr=1e8, seed=63)      # gamma / mu_min = 1e6: within range
+    context(ok, mode=A.ALS_MODE_MIXED).close()
+
+
+def test_solve_history():
+    """The residual history: |b| first, one estimate per iteration, the last one the
+    info's res_final, falling below rtol |b| at the end."""
+    pb = sinker(2, 16, 3, 1e2, dr=1e4, seed=64)
+    ctx = context(pb, rtol=1e-8)
+    _, _, info = ctx.solve(pb.f, pb.u_bc)
+    h = ctx.solve_history()
+    assert len(h) == info.iterations + 1
+    assert h[0] == info.res0 and h[-1] == info.res_final
+    assert h[-1] <= 1e-8 * h[0] < h[-2]

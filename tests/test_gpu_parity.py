@@ -346,17 +346,35 @@ def test_solve_manufactured_config():
     assert rel(u, uo) <= 1e-9
 
 
+def _mixed_error_bars(ref_u, ref_p, u8, p8):
+    """Error bars of a mixed solve stopped at rtol 1e-8, against the converged FP64
+    solution (ref_u, ref_p): 1e-7, or twice the error of the FP64 iterate that stopped
+    at the same rtol (u8, p8), whichever is larger.  A relative residual of 1e-8 leaves a
+    solution error of up to cond * 1e-8 in any precision; on these problems the FP64
+    oracle's own 1e-8 iterate is 2e-8 .. 1e-5 away from its converged solution."""
+    return max(1e-7, 2 * rel(u8, ref_u)), max(1e-7, 2 * rel(p8, ref_p))
+
+
 @pytest.mark.parametrize("d,n,levels", [(2, 32, 4), (3, 8, 2)])
 def test_solve_mixed_precision(d, n, levels):
+    """The mixed path (FP32 cycle inside FP64 FGMRES) reaches rtol 1e-8 within +2
+    iterations of the FP64 path, no further from the converged FP64 oracle solution than
+    the oracle's own 1e-8 iterate (within a factor 2, or 1e-7), and, run on to rtol
+    1e-11, within 1e-7 of the oracle solution in velocity and pressure."""
     pb = sinker(d, n, levels, 1e3, dr=1e6, seed=21)
     ref = context(pb, rtol=1e-8)
-    mixed = context(pb, rtol=1e-8, mode=A.ALS_MODE_MIXED)
     s = StokesSolver(oracle(pb))
-    uo, po, its, _ = s.solve(pb.f, pb.u_bc, rtol=1e-10)
-    u, p, info = mixed.solve(pb.f, pb.u_bc)
+    uo, po, _, _ = s.solve(pb.f, pb.u_bc, rtol=1e-12)
+    uo8, po8, its8, _ = s.solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = context(pb, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
     _, _, info64 = ref.solve(pb.f, pb.u_bc)
+    assert info64.iterations == its8
     assert info.converged and info.iterations <= info64.iterations + 2
-    assert rel(u, uo) <= 1e-7 * 10 and rel(p, po) <= 1e-6 * 10
+    bu, bp = _mixed_error_bars(uo, po, uo8, po8)
+    assert rel(u, uo) <= bu and rel(p, po) <= bp, (rel(u, uo), rel(p, po), bu, bp)
+    u, p, info = context(pb, rtol=1e-11, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
+    assert info.converged
+    assert rel(u, uo) <= 1e-7 and rel(p, po) <= 1e-7, (rel(u, uo), rel(p, po))
 
 
 def test_solve_device_buffers():
@@ -447,16 +465,35 @@ def test_tensor_vcycle_fp64(d, n, levels):
 
 @pytest.mark.parametrize("d,n,levels,gamma", [(2, 24, 3, 1e3), (3, 6, 2, 1e2)])
 def test_tensor_solve_fp64_and_mixed(d, n, levels, gamma):
+    """Tensor coefficients (C with a contrast of ~1e9).  FP64: the GPU's own patch and
+    coarse inverses differ from LAPACK's by cond * eps (cond ~ 1e12 here), which may move
+    the step at which rtol is crossed by one; with the oracle's inverses injected into
+    the context the iteration count is the oracle's exactly, and the solution matches.
+    Mixed: within +2 iterations of FP64 and within the mixed error bars of the converged
+    FP64 solution."""
     pb = _tensor_problem(d, n, levels, gamma)
     from oracle.stokes import StokesSolver
-    uo, po, its, _ = StokesSolver(_tensor_oracle(pb)).solve(pb.f, pb.u_bc, rtol=1e-8)
-    u, p, info = _tensor_ctx(pb, rtol=1e-8).solve(pb.f, pb.u_bc)
+    from injection import inject, load_into
+    H = _tensor_oracle(pb)
+    uo, po, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=1e-8)
+    ctx = _tensor_ctx(pb, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
     assert info.converged and abs(info.iterations - its) <= 1, (info.iterations, its)
     assert rel(u, uo) <= 1e-7 and rel(p, po) <= 1e-5
+    load_into(ctx, H, inject(H))
+    uo, po, its, _ = StokesSolver(H).solve(pb.f, pb.u_bc, rtol=1e-8)
+    u, p, info = ctx.solve(pb.f, pb.u_bc)
+    assert info.converged and info.iterations == its, (info.iterations, its)
+    assert rel(u, uo) <= 1e-9 and rel(p, po) <= 1e-8, (rel(u, uo), rel(p, po))
     pb10 = _tensor_problem(d, n, levels, 10.0)
+    s10 = StokesSolver(_tensor_oracle(pb10))
+    uc, pc, _, _ = s10.solve(pb10.f, pb10.u_bc, rtol=1e-12)
+    u8, p8, _, _ = s10.solve(pb10.f, pb10.u_bc, rtol=1e-8)
     _, _, i64 = _tensor_ctx(pb10, rtol=1e-8).solve(pb10.f, pb10.u_bc)
     um, pm, im = _tensor_ctx(pb10, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb10.f, pb10.u_bc)
     assert im.converged and im.iterations <= i64.iterations + 2
+    bu, bp = _mixed_error_bars(uc, pc, u8, p8)
+    assert rel(um, uc) <= bu and rel(pm, pc) <= bp, (rel(um, uc), rel(pm, pc), bu, bp)
 
 
 # --------------------------------------------------------------------------
@@ -487,8 +524,39 @@ def test_solve_p2_fp64_matches_oracle(d, n, levels):
 
 def test_mixed_p2_at_extreme_contrast_and_gamma():
     """With W = M_p(1/mu) the AL term scales with mu, so the FP32 V-cycle keeps
-    working where the P1 pairing (W = M_p) loses it (gamma / mu_min = 1e7)."""
+    working where the P1 pairing (W = M_p) loses it (gamma / mu_min = 1e7): +2 iterations
+    at most, the mixed error bars against the converged FP64 solution at rtol 1e-8, and
+    1e-7 when the mixed solve runs on to rtol 1e-11."""
     pb = sinker(3, 8, 2, 1e3, dr=1e8, seed=11)
-    _, _, i64 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8).solve(pb.f, pb.u_bc)
+    uc, pc, ic = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-12).solve(pb.f, pb.u_bc)
+    u8, p8, i64 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8).solve(pb.f, pb.u_bc)
     u32, p32, i32 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
-    assert i64.converged and i32.converged and i32.iterations <= i64.iterations + 2, (i32.iterations, i64.iterations)
+    assert ic.converged and i64.converged and i32.converged
+    assert i32.iterations <= i64.iterations + 2, (i32.iterations, i64.iterations)
+    bu, bp = _mixed_error_bars(uc, pc, u8, p8)
+    assert rel(u32, uc) <= bu and rel(p32, pc) <= bp, (rel(u32, uc), rel(p32, pc), bu, bp)
+    u11, p11, i11 = context(pb, schur=A.ALS_SCHUR_P2, rtol=1e-11, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
+    assert i11.converged and rel(u11, uc) <= 1e-7 and rel(p11, pc) <= 1e-7, (rel(u11, uc), rel(p11, pc))
+
+
+@pytest.mark.parametrize("d,n,levels,gamma,dr,schur", [(2, 32, 4, 1e2, 1e6, A.ALS_SCHUR_P1),
+                                                      (3, 8, 2, 1e3, 1e8, A.ALS_SCHUR_P2)])
+def test_mixed_with_fp64_setup(d, n, levels, gamma, dr, schur):
+    """options.setup = ALS_SETUP_FP64 keeps the FP32 cycle but computes the patch and
+    coarse inverses in FP64: its FP32 inverses are the FP64 context's rounded to float,
+    and it converges with the iteration count of the double-float setup (within one) and
+    the same solution within the mixed error bars."""
+    pb = sinker(d, n, levels, gamma, dr, seed=71)
+    s64 = context(pb, schur=schur, rtol=1e-8)
+    df = context(pb, schur=schur, rtol=1e-8, mode=A.ALS_MODE_MIXED)
+    f64 = context(pb, schur=schur, rtol=1e-8, mode=A.ALS_MODE_MIXED, setup=A.ALS_SETUP_FP64)
+    assert np.array_equal(f64.patch_inverse(levels - 1, 5), s64.patch_inverse(levels - 1, 5))
+    uc, pc, _ = context(pb, schur=schur, rtol=1e-12).solve(pb.f, pb.u_bc)
+    u8, p8, i64 = s64.solve(pb.f, pb.u_bc)
+    ud, pd, idf = df.solve(pb.f, pb.u_bc)
+    uf, pf, if64 = f64.solve(pb.f, pb.u_bc)
+    assert idf.converged and if64.converged and abs(idf.iterations - if64.iterations) <= 1
+    assert if64.iterations <= i64.iterations + 2
+    bu, bp = _mixed_error_bars(uc, pc, u8, p8)
+    for u, p in ((ud, pd), (uf, pf)):
+        assert rel(u, uc) <= bu and rel(p, pc) <= bp, (rel(u, uc), rel(p, pc), bu, bp)

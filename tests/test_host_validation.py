@@ -31,6 +31,7 @@ def test_default_options(lib):
         (A.ALS_SMOOTH_GMRES, 5, A.ALS_TRANSFER_ROBUST, A.ALS_SCHUR_P1, A.ALS_MODE_FP64)
     assert (o.cycle, o.fact, o.maxit) == (A.ALS_CYCLE_V, A.ALS_FACT_FULL, 300)
     assert o.rtol == 1e-8 and o.tau == 0.0          # tau 0: 2^-d chosen at create
+    assert o.setup == A.ALS_SETUP_AUTO
 
 
 @pytest.mark.parametrize("args,kw,words", [
@@ -48,6 +49,7 @@ def test_default_options(lib):
     ((2, 4, 1), {"smoother": 2}, "smoother"),
     ((2, 4, 1), {"transfer": 2}, "transfer"),
     ((2, 4, 1), {"mode": 2}, "mode"),
+    ((2, 4, 1), {"setup": 2}, "setup"),
     ((3, 1024, 2), {}, "too large"),
     ((2, 46340, 2), {}, "too large"),
 ])
@@ -113,6 +115,8 @@ def test_every_entry_point_refuses_a_null_context(lib):
         "als_autotune_info": (N, 1, ctypes.byref(i), N), "als_set_patch_kernel": (N, 1, 0),
         "als_batch_destroy": (N,), "als_batch_context": (N, 0, N), "als_batch_vcycle": (N, 0, N, N),
         "als_batch_solve": (N, N, N, N, N, N, N), "als_measure_fma_peaks": (N, N, N),
+        "als_load_patch_inverses": (N, 1, N), "als_load_coarse_inverse": (N, N),
+        "als_set_wait_limit": (N, 0), "als_solve_history": (N, N, 0, ctypes.byref(i)),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == A.ALS_EINVAL, name
@@ -148,3 +152,26 @@ def test_binding_marshalling_checks(lib):
     with pytest.raises(KeyError):
         A.default_options(no_such_option=1)
     assert str(A.ALSError(A.ALS_ENOTSPD, "patch 7")) == "ALS_ENOTSPD: patch 7"
+
+
+@pytest.mark.parametrize("n", [[2 ** 31 - 2] * 2, [4097, 4], [0, 4], [-3, 4], [64, 64, 64]])
+def test_static_smoother_refuses_sizes_before_any_launch(lib, n):
+    """The allocation-free smoother bounds every axis before it forms a product (no
+    wrap-around for huge n) and refuses meshes whose per-patch outputs exceed its fixed
+    scratch array; it returns ALS_EINVAL before touching the GPU (here: none)."""
+    dim = len(n)
+    arr = (ctypes.c_int * 3)(*(n + [1] * (3 - dim)))
+    fake = ctypes.c_void_p(16)                      # never dereferenced: refused first
+    for prec in (A.ALS_PREC_FP64, A.ALS_PREC_FP32):
+        assert lib.als_star_smooth_static(dim, arr, prec, fake, fake, fake, None) == A.ALS_EINVAL
+
+
+def test_static_smoother_binding_checks(lib):
+    """The binding hands the allocation-free smoother only CUDA tensors of the precision's
+    dtype that are long enough for the mesh (host arrays, CPU tensors, the wrong dtype or
+    short buffers are refused before the call)."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        A.als_star_smooth_static(2, [4, 4], A.ALS_PREC_FP64, np.zeros(8), np.zeros(8), np.zeros(8))
+    with pytest.raises(TypeError):
+        A.als_star_smooth_static(2, [4, 4], A.ALS_PREC_FP64, torch.zeros(8), torch.zeros(8), torch.zeros(8))
