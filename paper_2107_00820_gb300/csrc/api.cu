@@ -401,8 +401,15 @@ void cycle_level(als_ctx* c, MGWork& w, int l, bool fcycle, bool zero_guess) {
   }
   const LevelDev& Lv = c->lev[l];
   const long long len = Lv.g.N * c->dim;
-  if (fused_gmres(c)) {
+  if (fused_gmres(c) && w.prec == PREC_F32) {
     smooth_fused(c, w, l, zero_guess, w.t[l]);                           // x, and t = b - A x
+  } else if (fused_gmres(c)) {
+    // FP64: the residual is formed explicitly, as the method states it, not from the
+    // Arnoldi relation; at extreme contrast (gamma / mu_min ~ 1e8) the recurrence drifts
+    // from b - A x by far more than the rounding of b - A x itself
+    smooth_fused(c, w, l, zero_guess, nullptr);
+    op_apply(Lv, w.prec, OP_VISC | OP_AL, c->gamma, w.x[l], w.t[l], nullptr, nullptr, s);
+    vec_axpby(w.prec, len, 1.0, w.b[l], -1.0, w.t[l], s);                // t = b - A x
   } else {
     if (zero_guess) vec_zero(w.prec, len, w.x[l], s);
     smooth(c, w, l, zero_guess && c->opt.smoother == ALS_SMOOTH_GMRES);
