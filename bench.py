@@ -40,6 +40,10 @@ WORKLOADS = {
     # 3D multi-sinker, 32^3 hexes, 4 levels (coarse 4^3), 16 sinkers, omega 0.15, delta 200, DR 1e8
     "sinker3d_32": dict(d=3, n=32, levels=4, count=16, omega=0.15, delta=200.0, dr=1e8, beta=10.0,
                         gamma=10.0, seed=0, sweeps=5),
+    # the same 3D problem at the large gamma the AL method is built for, gamma 1e4, with the
+    # P2 pairing (W = M_p(1/mu)): mixed mode refuses P1 there (2^-24 gamma / mu_min = 6e4)
+    "sinker3d_32_g1e4": dict(d=3, n=32, levels=4, count=16, omega=0.15, delta=200.0, dr=1e8, beta=10.0,
+                             gamma=1e4, seed=0, sweeps=5, schur="P2"),
     # 2D multi-sinker, 128^2 quads, 5 levels (coarse 8^2), 8 sinkers, omega 0.1, delta 200, DR 1e6;
     # gamma 1e2 of the set {1, 1e2, 1e4}: with the P1 pairing the FP32 cycle holds while
     # eps32 gamma / mu_min stays below about 0.1, and mu_min = 1e-3 here (1e4 would give 0.6)
@@ -53,6 +57,7 @@ WORKLOADS = {
 SAMPLES = {
     "sinker3d_32": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
     "sinker2d_128": dict(cpu_baseline=dict(n=64, levels=4), reference=dict(n=32, levels=3)),
+    "sinker3d_32_g1e4": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
     "viscoplastic3d_48": dict(cpu_baseline=dict(n=8, levels=2), reference=dict(n=8, levels=2)),
 }
 RTOL = 1e-8
@@ -228,8 +233,33 @@ def cpu_worker(args):
     print(json.dumps({"runs": out}))
 
 
-def run_oracle_subprocess(workload, kind, reps):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+def host_cpu():
+    """(logical cores, CPU model) of this host, read only."""
+    cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model == "unknown":
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:  # noqa: BLE001
+            pass
+    return cores, model
+
+
+def run_oracle_subprocess(workload, kind, reps, threads=1):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
                         "--sample-kind", kind, "--reps", str(reps)], capture_output=True, text=True, env=env)
@@ -239,14 +269,20 @@ def run_oracle_subprocess(workload, kind, reps):
 
 
 def cpu_baseline(workload):
+    """The oracle on a bounded sample, on one thread and with BLAS on every core of the
+    host (SciPy's sparse products stay single-threaded either way)."""
     smp = SAMPLES[workload]["cpu_baseline"]
-    runs = run_oracle_subprocess(workload, "cpu_baseline", 1)
-    dof, dt, its = runs[0]
     spec = WORKLOADS[workload]
+    cores, model = host_cpu()
+    dof, dt, its = run_oracle_subprocess(workload, "cpu_baseline", 1)[0]
+    dof_a, dt_a, _ = run_oracle_subprocess(workload, "cpu_baseline", 1, threads=cores)[0]
     return {"value": dof / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
             "sample": f"same law, {spec['d']}D {smp['n']}^{spec['d']} cells, {smp['levels']} levels, "
                       f"setup+solve to {RTOL:g} ({its} FGMRES its, {dt:.1f} s, {dof} DoFs), FP64 NumPy/SciPy, "
-                      f"1 thread"}
+                      f"1 thread",
+            "all_cores": {"value": dof_a / dt_a, "cores": cores, "s": dt_a,
+                          "note": "BLAS threads = all cores; SciPy sparse products are single-threaded"},
+            "host": {"logical_cores": cores, "cpu_model": model}}
 
 
 def reference_arm(args, dist):
@@ -404,6 +440,71 @@ def ours(args, dist):
     err_p = float(torch.linalg.norm(p_d - p64) / torch.linalg.norm(p64))
     ctx64.close()
 
+    # the same mixed step with the patch and coarse inverses computed in FP64 instead of
+    # double-float (options.setup = ALS_SETUP_FP64): setup time, iterations, solution
+    # difference from the double-float setup's solution
+    setup_fp64 = None
+    if not args.quick:
+        ctxf = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_MIXED,
+                       rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, setup=A.ALS_SETUP_FP64)
+        uf, pf = torch.zeros_like(u_d), torch.zeros_like(p_d)
+        ctxf.solve(f_d, ubc_d, None, uf, pf)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(2):
+            ctxf.update_coefficients(mu_d, mue_d)
+        e1.record()
+        torch.cuda.synchronize()
+        t_setf = e0.elapsed_time(e1) / 2 / 1e3
+        e0.record()
+        info_f = ctxf.solve(f_d, ubc_d, None, uf, pf)[2]
+        e1.record()
+        torch.cuda.synchronize()
+        setup_fp64 = {"setup_ms": t_setf * 1e3, "setup_ms_double_float": t_setup * 1e3,
+                      "solve_ms": e0.elapsed_time(e1), "iterations": info_f.iterations,
+                      "iterations_double_float": info_s.iterations,
+                      "rel_diff_vs_double_float": {
+                          "u": float(torch.linalg.norm(uf - u_d) / torch.linalg.norm(u_d)),
+                          "p": float(torch.linalg.norm(pf - p_d) / torch.linalg.norm(p_d))}}
+        ctxf.close()
+
+    # the AL method at large gamma: the same workload at gamma 1e4 with the P2 pairing
+    # (W = M_p(1/mu); mixed mode refuses P1 there), mixed against FP64: step time,
+    # iterations, solution difference at rtol 1e-8, and the mixed solve run on to 1e-11
+    # against the FP64 solve run to 1e-12 (the 1e-7 error bar)
+    gamma_large = None
+    if not tensor and not args.quick:
+        spec4 = dict(spec, gamma=1e4)
+        pb4 = make_problem(spec4)
+        mu4 = [dev(m) for m in pb4.mu]
+        f4, ub4 = dev(pb4.f), dev(pb4.u_bc)
+        res = {}
+        for name, mode, rtol in (("mixed", A.ALS_MODE_MIXED, RTOL), ("fp64", A.ALS_MODE_FP64, RTOL),
+                                 ("mixed_1e-11", A.ALS_MODE_MIXED, 1e-11), ("fp64_1e-12", A.ALS_MODE_FP64, 1e-12)):
+            c4 = Context(pb4.d, pb4.n, pb4.levels, mu4, pb4.gamma, stream=stream, mode=mode, rtol=rtol, maxit=300,
+                         sweeps=spec["sweeps"], schur=A.ALS_SCHUR_P2)
+            u4, p4 = torch.zeros_like(u_d), torch.zeros_like(p_d)
+            c4.solve(f4, ub4, None, u4, p4)
+            torch.cuda.synchronize()
+            e0.record()
+            c4.update_coefficients(mu4)
+            inf4 = c4.solve(f4, ub4, None, u4, p4)[2]
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = (e0.elapsed_time(e1) / 1e3, inf4, u4, p4)
+            c4.close()
+        rd = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))  # noqa: E731
+        gamma_large = {
+            "gamma": 1e4, "schur": "P2", "value": dofs / res["mixed"][0], "unit": "DoF/s",
+            "ms_per_step": res["mixed"][0] * 1e3, "iterations": res["mixed"][1].iterations,
+            "fp64": {"solve_dof_per_s": dofs / res["fp64"][0], "ms_per_step": res["fp64"][0] * 1e3,
+                     "iterations": res["fp64"][1].iterations},
+            "mixed_vs_fp64_speedup": res["fp64"][0] / res["mixed"][0],
+            "mixed_vs_fp64_rel_err": {"u": rd(res["mixed"][2], res["fp64"][2]), "p": rd(res["mixed"][3], res["fp64"][3])},
+            "mixed_1e-11_vs_fp64_1e-12_rel_err": {"u": rd(res["mixed_1e-11"][2], res["fp64_1e-12"][2]),
+                                                  "p": rd(res["mixed_1e-11"][3], res["fp64_1e-12"][3]),
+                                                  "iterations": res["mixed_1e-11"][1].iterations}}
+
     # end to end through the C ABI with host buffers
     mu_h = [np.ascontiguousarray(m) for m in pb.mu]
     mue_h = [np.ascontiguousarray(m) for m in pb.meta["mu_eff"]] if tensor else None
@@ -427,12 +528,15 @@ def ours(args, dist):
     t_e2e = dist.max(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / args.steps)
     ctx.close()
 
-    # roofline of the dominant kernel: finest-level patch kernel
+    # roofline of the dominant kernel: the finest-level interior-star patch kernel (the
+    # boundary stars, with 1/3 .. 1/27 of the dofs, run in their own small kernel): per
+    # interior vertex its packed FP32 inverse and its output row, plus r read once
     F = pb.n
     nverts = math.prod(v + 1 for v in F)
+    nint = math.prod(v - 1 for v in F)
     npatch = pb.d * 3 ** pb.d
     packed = npatch * (npatch + 1) // 2
-    bytes_per_launch = nverts * (packed * 4 + npatch * 4) + nu * 4
+    bytes_per_launch = nint * (packed * 4 + npatch * 4) + nu * 4
     k4_launch_s = (k4_ms / max(k4_n, 1)) / 1e3
     achieved = bytes_per_launch / k4_launch_s / 1e9 if k4_n else None
     peak, peak_kind = measured_peak_hbm()
@@ -480,12 +584,16 @@ def ours(args, dist):
                  "vcycles_per_s": vcyc64_s},
         "mixed_vs_fp64_speedup": t64 / t_step,
         "mixed_vs_fp64_rel_err": {"u": err_u, "p": err_p},
+        "setup_fp64": setup_fp64,
+        "gamma_1e4": gamma_large,
         "e2e": {"value": dist.world * dofs / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "kernel": "k_patch_tma<%d> (FP32 star smoother, finest level)" % pb.d,
+        "roofline": {"bound": "hbm", "kernel": "k_patch_tma<%d> (FP32 interior-star smoother, finest level)" % pb.d,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,
+                     "units": {"interior_stars": nint, "bytes_per_star": packed * 4 + npatch * 4,
+                               "r_bytes": nu * 4},
                      "traffic": stored_traffic("k_patch_apply_f32_fine", args.workload)},
         "roofline_apply": roofline_apply,
         "phases": {"setup_ms": t_setup * 1e3, "solve_ms": t_solve * 1e3,
@@ -613,6 +721,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sinker3d_32", choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64-setup and gamma 1e4 side measurements")
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--sample-kind", default="cpu_baseline")
     ap.add_argument("--reps", type=int, default=1)

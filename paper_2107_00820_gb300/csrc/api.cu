@@ -761,6 +761,48 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   return check_status(c, "setup");
 }
 
+// FP32 star storage of a smoothed level: block-packed inverses of the interior
+// vertices, and the boundary vertices' compact inverses (free dofs only: 1/3, 1/9 and
+// 1/27 of an interior star's dofs at faces, edges and corners in 3D) with their vertex
+// ids and offsets, enumerated here on the host.
+static als_status alloc_star_storage(als_ctx* c, LevelDev& Lv) {
+  const Geom& g = Lv.g;
+  const int d = c->dim;
+  Lv.nint = 1;
+  for (int k = 0; k < d; ++k) Lv.nint *= g.nv[k] - 2;
+  std::vector<int> bvid;
+  std::vector<long long> boff;
+  long long total = 0;
+  for (long long v = 0; v < g.nverts; ++v) {
+    const int vc[3] = {(int)(v % g.nv[0]), (int)((v / g.nv[0]) % g.nv[1]),
+                       (int)(v / ((long long)g.nv[0] * g.nv[1]))};
+    int m = d;
+    bool bnd = false;
+    for (int k = 0; k < d; ++k) {
+      const bool edge = vc[k] == 0 || vc[k] == g.nv[k] - 1;
+      bnd = bnd || edge;
+      m *= edge ? 1 : 3;
+    }
+    if (!bnd) continue;
+    bvid.push_back((int)v);
+    boff.push_back(total);
+    total += (long long)m * (m + 1) / 2;
+  }
+  Lv.nbnd = (long long)bvid.size();
+  ALS_TRY(dalloc(c, &Lv.inv32, (size_t)Lv.nint * Lv.pstride));
+  ALS_TRY(dalloc(c, &Lv.bnd32, (size_t)total));
+  ALS_TRY(dalloc(c, &Lv.bvid, bvid.size()));
+  ALS_TRY(dalloc(c, &Lv.boff, boff.size()));
+  if (!bvid.empty() &&
+      (cudaMemcpyAsync(Lv.bvid, bvid.data(), bvid.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(Lv.boff, boff.data(), boff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(c->stream) != cudaSuccess))
+    return cuda_check(c, "boundary star tables");
+  return ALS_OK;
+}
+
 static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff* coeff, double gamma,
                                const als_options* opt) {
   if (!mesh || !coeff || !coeff->qp) return fail(c, ALS_EINVAL, "null mesh or coefficients");
@@ -851,7 +893,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     }
     if (l > 0) {
       ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
-      ALS_TRY(dalloc(c, &Lv.inv32, (size_t)Lv.g.nverts * Lv.pstride));
+      ALS_TRY(alloc_star_storage(c, Lv));
     }
   }
   if (coarse_alloc(c->lev[0], &c->coarse) != 0) {

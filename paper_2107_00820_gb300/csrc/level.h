@@ -19,9 +19,17 @@ struct LevelDev {
   double* coef64;        // [cell][3^d][ncoef]
   float* coef32;
   double* mu64;          // scalar viscosity per point (mu or mu_eff), FP64
-  // vertex-star patch inverses, packed symmetric by diagonals, one per vertex
+  // vertex-star patch inverses: FP64 packed symmetric by diagonals, one per vertex
+  // (identity rows at absent and Dirichlet nodes); FP32 block-packed (BlockLayout) for
+  // the interior vertices only (1 <= v_k <= n_k - 1, interior index x-fastest), and for
+  // the boundary vertices a compact FP32 copy restricted to the free dofs of the star
   double* inv64;
   float* inv32;
+  float* bnd32;          // boundary stars: packed upper triangle by rows, m x m, m = free dofs
+  int* bvid;             // boundary vertex ids (nbnd), ascending
+  long long* boff;       // offset of each boundary star's compact inverse in bnd32
+  long long nint;        // interior vertices, prod(n_k - 1)
+  long long nbnd;        // boundary vertices, nverts - nint
   int np;                // patch size d*3^d
   int pstride;           // entries per patch (padded)
   DevStatus* status;     // where kernels of this level record device-side failures

@@ -47,6 +47,41 @@ __device__ __forceinline__ void vertex_coords(const Geom& g, long long v, int& v
   vz = (DIM == 3) ? (int)(r / g.nv[1]) : 0;
 }
 
+// Free node offsets of a boundary vertex's star along each axis: all three offsets
+// (0, 1, 2) where the vertex is interior along the axis, only the inward one where it
+// lies on the boundary (2 at v = 0, 0 at v = n); entries of the star with an offset
+// outside [lo, lo + cnt) on some axis are absent or Dirichlet nodes.
+template <int DIM>
+struct StarAxes {
+  int lo[3], cnt[3], m;   // m = free dofs = DIM cnt0 cnt1 cnt2
+  __device__ __forceinline__ StarAxes(const Geom& g, int vx, int vy, int vz) {
+    const int v[3] = {vx, vy, vz};
+    m = DIM;
+    for (int k = 0; k < 3; ++k) {
+      if (k >= DIM) { lo[k] = 0; cnt[k] = 1; continue; }
+      if (v[k] == 0) { lo[k] = 2; cnt[k] = 1; }
+      else if (v[k] == g.nv[k] - 1) { lo[k] = 0; cnt[k] = 1; }
+      else { lo[k] = 0; cnt[k] = 3; }
+      m *= cnt[k];
+    }
+  }
+  // patch entry (component-major, offsets x-fastest) of free dof a
+  __device__ __forceinline__ int entry(int a) const {
+    constexpr int NB = Sz<DIM>::NB;
+    const int ix = a % cnt[0], q = a / cnt[0], iy = q % cnt[1], q2 = q / cnt[1], iz = q2 % cnt[2], c = q2 / cnt[2];
+    return c * NB + (lo[0] + ix) + 3 * (lo[1] + iy) + 9 * (lo[2] + iz);
+  }
+  // free dof of patch entry i, or -1
+  __device__ __forceinline__ int free_index(int i) const {
+    constexpr int NB = Sz<DIM>::NB;
+    const int c = i / NB, o = i - c * NB;
+    const int ix = o % 3 - lo[0], iy = (o / 3) % 3 - lo[1], iz = o / 9 - lo[2];
+    if (ix < 0 || ix >= cnt[0] || iy < 0 || iy >= cnt[1] || iz < 0 || iz >= cnt[2]) return -1;
+    return ((c * cnt[2] + iz) * cnt[1] + iy) * cnt[0] + ix;
+  }
+};
+__device__ __forceinline__ int tri_pos(int m, int a, int b) { return a * m - (a * (a - 1)) / 2 + (b - a); }  // a <= b
+
 // ---------------------------------------------------------------------------
 // K2 + K3: assemble, factor and invert one patch per CTA (FP64)
 // ---------------------------------------------------------------------------
@@ -221,18 +256,20 @@ struct TmaCfg {
   static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
 };
 
-// vertex id of slot p of the work list (all vertices, or the centres 2K+1 of
-// coarse cells) and its lattice coordinates; -1 past the end
+// Slot p of the work list of the FP32 interior-patch kernels -- all interior vertices
+// (1 <= v_k <= n_k - 1), or the centres 2K+1 of the coarse cells, which are interior --
+// as its lattice coordinates and its index in the interior-only FP32 storage (inv32);
+// -1 past the end.  Every node of an interior vertex's star is a free node.
 template <int DIM>
 __device__ __forceinline__ int work_vertex(const Geom& g, int interior, int p, int count, int& vx, int& vy,
                                            int& vz) {
   if (p >= count) return -1;
+  const int nix = g.nv[0] - 2, niy = g.nv[1] - 2;
   if (!interior) {
-    const int nvx = g.nv[0], nvy = g.nv[1];
-    vx = p % nvx;
-    const int q = p / nvx;
-    vy = q % nvy;
-    vz = DIM == 3 ? q / nvy : 0;
+    vx = p % nix + 1;
+    const int q = p / nix;
+    vy = q % niy + 1;
+    vz = DIM == 3 ? q / niy + 1 : 0;
     return p;
   }
   const int ncx = g.n[0] >> 1, ncy = g.n[1] >> 1;
@@ -240,7 +277,7 @@ __device__ __forceinline__ int work_vertex(const Geom& g, int interior, int p, i
   vx = 2 * kx + 1;
   vy = 2 * ky + 1;
   vz = DIM == 3 ? 2 * kz + 1 : 0;
-  return vx + g.nv[0] * (vy + g.nv[1] * vz);
+  return (vx - 1) + nix * ((vy - 1) + (DIM == 3 ? niy * (vz - 1) : 0));
 }
 
 // r at patch entry i of the vertex (absent nodes give 0)
@@ -587,6 +624,61 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
   count_launch(1);
 }
 
+// ---------------------------------------------------------------------------
+// K4 (FP32), boundary stars: y_v = A_v^-1 r|_v restricted to the free dofs of the
+// star (a face, edge or corner vertex has 1/3, 1/9 or 1/27 of the interior star's free
+// dofs in 3D), from the compact packed inverses, one warp per boundary vertex; every
+// entry of the vertex's scratch row is written (0 at absent and Dirichlet nodes).
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
+                                                   const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                   long long nb, const float* __restrict__ r, float* __restrict__ out) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6;
+  __shared__ float rs[8][MMAX];
+  __shared__ float ys[8][MMAX];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  pdl_wait();
+  for (long long b = (long long)blockIdx.x * 8 + w; b < nb; b += (long long)gridDim.x * 8) {
+    const int v = bvid[b];
+    int vx, vy, vz;
+    vertex_coords<DIM>(g, v, vx, vy, vz);
+    const StarAxes<DIM> ax(g, vx, vy, vz);
+    const int m = ax.m;
+    if (lane < m) {
+      long long nd;
+      const int i = ax.entry(lane);
+      rs[w][lane] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
+    }
+    __syncwarp();
+    if (lane < m) {
+      const float* S = bnd32 + boff[b];
+      float acc = 0.f;
+      for (int c = 0; c < m; ++c) {
+        const int lo = lane < c ? lane : c, hi = lane < c ? c : lane;
+        acc += __ldg(S + tri_pos(m, lo, hi)) * rs[w][c];
+      }
+      ys[w][lane] = acc;
+    }
+    __syncwarp();
+    for (int i = lane; i < NP; i += 32) {
+      const int a = ax.free_index(i);
+      out[patch_out_index<DIM>(g, vx, vy, vz, i)] = a >= 0 ? ys[w][a] : 0.f;
+    }
+    __syncwarp();
+  }
+  pdl_trigger();
+}
+
+template <int DIM>
+static void launch_patch_bnd(const LevelDev& L, const float* r, float* out, cudaStream_t s) {
+  if (L.nbnd <= 0) return;
+  const long long want = (L.nbnd + 7) / 8, cap = 152LL * 8;
+  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 256, 0, s, L.g, (const float*)L.bnd32,
+             (const int*)L.bvid, (const long long*)L.boff, L.nbnd, r, out);
+  count_launch(1);
+}
+
 // FP32 patch-product kernel variants: 0 = TMA ring with 2 stages, 1 = TMA ring
 // with 3 stages, 2 = direct 16-byte loads.  A level uses L.patch_kernel (picked by
 // patch_autotune); the environment variable ALS_PATCH_KERNEL = tma2 | tma3 | direct
@@ -693,17 +785,22 @@ void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStat
   }
 }
 
-// FP32 block-packed copy (BlockLayout) of every FP64 inverse packed by diagonals: one
-// CTA per vertex, entry (i, i+t) of diagonal t rounded to the nearest float; the
-// padding slots of the layout are zeroed.
-template <int NP>
-__global__ void __launch_bounds__(128) k_derive32(long long nverts, int pstride, const double* __restrict__ inv64,
+// ---------------------------------------------------------------------------
+// FP32 copies of the FP64 inverses (packed by diagonals, every vertex)
+// ---------------------------------------------------------------------------
+// interior vertices: block-packed (BlockLayout) FP32 copy, one CTA per interior vertex,
+// entry (i, i+t) of diagonal t rounded to the nearest float; padding slots zeroed
+template <int DIM>
+__global__ void __launch_bounds__(128) k_derive32(Geom g, int pstride, const double* __restrict__ inv64,
                                                   float* __restrict__ inv32) {
+  constexpr int NP = Sz<DIM>::NP;
   constexpr BlockLayout BL = BlockLayout(NP);
-  const long long v = blockIdx.x;
-  if (v >= nverts) return;
+  const long long iv = blockIdx.x;
+  const int nix = g.nv[0] - 2, niy = g.nv[1] - 2;
+  const long long vx = iv % nix + 1, q = iv / nix, vy = q % niy + 1, vz = DIM == 3 ? q / niy + 1 : 0;
+  const long long v = vx + g.nv[0] * (vy + (long long)g.nv[1] * vz);
   const double* src = inv64 + v * pstride;
-  float* dst = inv32 + v * pstride;
+  float* dst = inv32 + iv * pstride;
   for (int e = 44 * BL.nbp + BL.nbp + (int)threadIdx.x; e < BL.q2; e += blockDim.x) dst[e] = 0.f;
   for (int t = 0; t < NP; ++t) {
     const int base = diag_start(NP, t);
@@ -711,11 +808,45 @@ __global__ void __launch_bounds__(128) k_derive32(long long nverts, int pstride,
   }
 }
 
+// boundary vertices: the free-dof block of the inverse, packed upper triangle by rows,
+// rounded to float; one warp per boundary vertex
+template <int DIM>
+__global__ void __launch_bounds__(256) k_derive32_bnd(Geom g, int pstride, const double* __restrict__ inv64,
+                                                      const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                      long long nb, float* __restrict__ bnd32) {
+  constexpr int NP = Sz<DIM>::NP;
+  const long long b = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= nb) return;
+  const int v = bvid[b];
+  int vx, vy, vz;
+  vertex_coords<DIM>(g, v, vx, vy, vz);
+  const StarAxes<DIM> ax(g, vx, vy, vz);
+  const double* src = inv64 + (long long)v * pstride;
+  float* dst = bnd32 + boff[b];
+  const int m = ax.m;
+  for (int e = lane; e < m * m; e += 32) {
+    const int a = e / m, c = e - a * m;
+    if (c < a) continue;
+    const int i = ax.entry(a), j = ax.entry(c);   // i <= j: entry() increases with the free index
+    dst[tri_pos(m, a, c)] = (float)src[diag_start(NP, j - i) + i];
+  }
+}
+
 void patch_derive32(const LevelDev& L, cudaStream_t s) {
-  if (L.g.nverts <= 0) return;
-  if (L.np == 81) k_derive32<81><<<(unsigned)L.g.nverts, 128, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
-  else k_derive32<18><<<(unsigned)L.g.nverts, 128, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
-  count_launch(1);
+  if (L.nint > 0) {
+    if (L.g.dim == 3) k_derive32<3><<<(unsigned)L.nint, 128, 0, s>>>(L.g, L.pstride, L.inv64, L.inv32);
+    else k_derive32<2><<<(unsigned)L.nint, 128, 0, s>>>(L.g, L.pstride, L.inv64, L.inv32);
+    count_launch(1);
+  }
+  if (L.nbnd > 0) {
+    const unsigned blocks = (unsigned)((L.nbnd + 7) / 8);
+    if (L.g.dim == 3)
+      k_derive32_bnd<3><<<blocks, 256, 0, s>>>(L.g, L.pstride, L.inv64, L.bvid, L.boff, L.nbnd, L.bnd32);
+    else
+      k_derive32_bnd<2><<<blocks, 256, 0, s>>>(L.g, L.pstride, L.inv64, L.bvid, L.boff, L.nbnd, L.bnd32);
+    count_launch(1);
+  }
 }
 
 size_t setup_tab_bytes(int dim) {
@@ -863,8 +994,9 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
 template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
                        cudaEvent_t e1, const void* den) {
+  launch_patch_bnd<DIM>(L, (const float*)r, (float*)scratch, s);
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  launch_patch_variant<DIM>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+  launch_patch_variant<DIM>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
                             L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   launch_pdl(k_patch_gather<float, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const float*)scratch,
@@ -874,12 +1006,14 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
 
 void patch_products(const LevelDev& L, const void* r, void* scratch, cudaStream_t s, cudaEvent_t e0,
                     cudaEvent_t e1) {
+  if (L.g.dim == 2) launch_patch_bnd<2>(L, (const float*)r, (float*)scratch, s);
+  else launch_patch_bnd<3>(L, (const float*)r, (float*)scratch, s);
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   if (L.g.dim == 2)
-    launch_patch_variant<2>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+    launch_patch_variant<2>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
                             L.status, s);
   else
-    launch_patch_variant<3>(patch_variant(L), L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+    launch_patch_variant<3>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
                             L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
 }
@@ -973,9 +1107,9 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
   for (int v = 0; v < 3; ++v) {
     for (int rep = 0; rep < 4; ++rep) {
       if (rep == 1) cudaEventRecord(e0, s);
-      if (L.g.dim == 2) launch_patch_variant<2>(v, L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH,
+      if (L.g.dim == 2) launch_patch_variant<2>(v, L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
                                                 L.status, s);
-      else launch_patch_variant<3>(v, L, 0, L.g.nverts, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+      else launch_patch_variant<3>(v, L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
     }
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
