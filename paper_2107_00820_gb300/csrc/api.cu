@@ -786,7 +786,7 @@ static als_status alloc_star_storage(als_ctx* c, LevelDev& Lv) {
     if (!bnd) continue;
     bvid.push_back((int)v);
     boff.push_back(total);
-    total += (long long)m * (m + 1) / 2;
+    total += ((long long)m * (m + 1) / 2 + 3) & ~3LL;   // 16-byte aligned blocks (bulk copies)
   }
   Lv.nbnd = (long long)bvid.size();
   ALS_TRY(dalloc(c, &Lv.inv32, (size_t)Lv.nint * Lv.pstride));

@@ -347,10 +347,20 @@ __device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const
   return true;
 }
 
+// The boundary stars' compact inverses (StarAxes, tri_pos; offsets multiples of 4 floats),
+// handled by the 3D TMA kernel as work items after its interior stars (nb = 0: none).
+struct BndIn {
+  const float* bnd32;
+  const int* bvid;
+  const long long* boff;
+  int nb;
+};
+__host__ __device__ __forceinline__ int bnd_stride(int m) { return ((m * (m + 1) / 2) + 3) & ~3; }
+
 template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
-                                                  DevStatus* st, int wait_polls) {
+                                                  DevStatus* st, int wait_polls, BndIn bi) {
   using C = TmaCfg<DIM, NST>;
   constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
@@ -364,9 +374,20 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   float* part = rs + PPI * NP;                            // [PPI][NP][NBR]
   __shared__ int s_fail;
   const int tid = threadIdx.x;
-  const int ngroups = (count + PPI - 1) / PPI;
+  // work items: the interior stars in groups of PPI, then (3D, PPI = 1) one boundary star each
+  const int nigroups = (count + PPI - 1) / PPI;
+  const int ngroups = nigroups + (PPI == 1 ? bi.nb : 0);
 
   auto issue = [&](int grp, int stage) {   // one bulk copy per patch of the group
+    if (PPI == 1 && grp >= nigroups) {     // a boundary star: its compact block
+      const int b = grp - nigroups;
+      int vx, vy, vz;
+      vertex_coords<DIM>(g, bi.bvid[b], vx, vy, vz);
+      const uint32_t bytes = (uint32_t)bnd_stride(StarAxes<DIM>(g, vx, vy, vz).m) * 4u;
+      tma::mbar_expect_tx(&bars[stage], bytes);
+      tma::bulk_load(stages + stage * C::stage_floats, bi.bnd32 + bi.boff[b], bytes, &bars[stage]);
+      return;
+    }
     uint32_t bytes = 0;
     int vids[PPI];
     for (int ps = 0; ps < PPI; ++ps) {
@@ -435,6 +456,47 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
     const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
+    if (PPI == 1 && grp >= nigroups) {
+      // boundary star: r at its free dofs (read directly), the rows of its compact
+      // inverse from the stage, then every entry of its scratch row (0 at absent nodes);
+      // the same two barriers as an interior star, so the ring advances alike
+      int vx, vy, vz;
+      vertex_coords<DIM>(g, bi.bvid[grp - nigroups], vx, vy, vz);
+      const StarAxes<DIM> ax(g, vx, vy, vz);
+      const int m = ax.m;
+      if (tid < m) {
+        long long nd;
+        const int i = ax.entry(tid);
+        rs[tid] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
+      }
+      if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
+        if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
+      }
+      __syncthreads();                      // (A)
+      if (s_fail) break;
+      if (tid < m) {
+        const float* S = stages + stage * C::stage_floats;
+        float acc = 0.f;
+        for (int c = 0; c < m; ++c) {
+          const int lo = tid < c ? tid : c, hi = tid < c ? c : tid;
+          acc += S[tri_pos(m, lo, hi)] * rs[c];
+        }
+        part[tid] = acc;
+      }
+      __syncthreads();                      // (B)
+      if (tid == ISSUER) {
+        const int nxt = grp + NSTAGE * gridDim.x;
+        if (nxt < ngroups) {
+          tma::fence_async();
+          issue(nxt, stage);
+        }
+      }
+      for (int i = tid; i < NP; i += THREADS) {
+        const int a = ax.free_index(i);
+        out[patch_out_index<DIM>(g, vx, vy, vz, i)] = a >= 0 ? part[a] : 0.f;
+      }
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int e = tid + k * THREADS;
@@ -718,10 +780,14 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
     if (per_sm < 1) per_sm = 1;
   }
   const long long cap = 152LL * per_sm;
-  const long long grid = groups < cap ? groups : cap;
-  if (grid <= 0) return;
-  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
-             (int)count, r, out, mode, st, L.wait_polls);
+  // 3D smoother products: the boundary stars ride along as extra work items
+  BndIn bi{L.bnd32, L.bvid, L.boff, 0};
+  if (DIM == 3 && !interior && mode == OUT_SCRATCH) bi.nb = (int)L.nbnd;
+  const long long items = groups + bi.nb;
+  const long long grid2 = items < cap ? items : cap;
+  if (grid2 <= 0) return;
+  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid2, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
+             (int)count, r, out, mode, st, L.wait_polls, bi);
   count_launch(1);
 }
 
@@ -991,14 +1057,23 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
   count_launch(2);
 }
 
+// All star products y_v = A_v^-1 r|_v of a level into the scratch rows (FP32) with kernel
+// variant v: the interior stars in the variant's kernel; the boundary stars inside the 3D
+// TMA kernels' work list, else (2D, or the direct variant) in k_patch_bnd, launched first.
+// e0/e1 (optional) bracket the interior-star kernel.
+template <int DIM>
+static void star_products(int v, const LevelDev& L, const float* r, float* scratch, cudaStream_t s, cudaEvent_t e0,
+                          cudaEvent_t e1) {
+  if (DIM == 2 || v == 2) launch_patch_bnd<DIM>(L, r, scratch, s);
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  launch_patch_variant<DIM>(v, L, 0, L.nint, r, scratch, OUT_SCRATCH, L.status, s);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+}
+
 template <int DIM>
 static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch, cudaStream_t s, cudaEvent_t e0,
                        cudaEvent_t e1, const void* den) {
-  launch_patch_bnd<DIM>(L, (const float*)r, (float*)scratch, s);
-  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  launch_patch_variant<DIM>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
-                            L.status, s);
-  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  star_products<DIM>(patch_variant(L), L, (const float*)r, (float*)scratch, s, e0, e1);
   launch_pdl(k_patch_gather<float, DIM>, row_gather_blocks(L.g, DIM), 256, 0, s, L.g, (const float*)scratch,
              (float*)z, (const float*)den);
   count_launch(1);
@@ -1006,16 +1081,8 @@ static void smooth_tma(const LevelDev& L, const void* r, void* z, void* scratch,
 
 void patch_products(const LevelDev& L, const void* r, void* scratch, cudaStream_t s, cudaEvent_t e0,
                     cudaEvent_t e1) {
-  if (L.g.dim == 2) launch_patch_bnd<2>(L, (const float*)r, (float*)scratch, s);
-  else launch_patch_bnd<3>(L, (const float*)r, (float*)scratch, s);
-  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  if (L.g.dim == 2)
-    launch_patch_variant<2>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
-                            L.status, s);
-  else
-    launch_patch_variant<3>(patch_variant(L), L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
-                            L.status, s);
-  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  if (L.g.dim == 2) star_products<2>(patch_variant(L), L, (const float*)r, (float*)scratch, s, e0, e1);
+  else star_products<3>(patch_variant(L), L, (const float*)r, (float*)scratch, s, e0, e1);
 }
 
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
@@ -1098,6 +1165,7 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
 // by the caller) and stores the fastest in L.patch_kernel.  Runs outside any
 // stream capture; waits for its own work.  Returns the chosen variant.
 int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out) {
+  const long long launches0 = launch_count();
   if (forced_patch_kernel() >= 0) { L.patch_kernel = forced_patch_kernel(); return L.patch_kernel; }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1107,9 +1175,8 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
   for (int v = 0; v < 3; ++v) {
     for (int rep = 0; rep < 4; ++rep) {
       if (rep == 1) cudaEventRecord(e0, s);
-      if (L.g.dim == 2) launch_patch_variant<2>(v, L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH,
-                                                L.status, s);
-      else launch_patch_variant<3>(v, L, 0, L.nint, (const float*)r, (float*)scratch, OUT_SCRATCH, L.status, s);
+      if (L.g.dim == 2) star_products<2>(v, L, (const float*)r, (float*)scratch, s, nullptr, nullptr);
+      else star_products<3>(v, L, (const float*)r, (float*)scratch, s, nullptr, nullptr);
     }
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
@@ -1118,7 +1185,7 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
     if (ms_out) ms_out[v] = ms / 3.f;
     if (ms < best_ms) { best_ms = ms; best = v; }
   }
-  count_launch(-12);   // tuning launches are not work of the caller's step
+  count_launch(-(launch_count() - launches0));   // tuning launches are not work of the caller's step
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   L.patch_kernel = best;
