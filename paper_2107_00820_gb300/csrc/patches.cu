@@ -357,6 +357,19 @@ struct BndIn {
 };
 __host__ __device__ __forceinline__ int bnd_stride(int m) { return ((m * (m + 1) / 2) + 3) & ~3; }
 
+// Work item i of ngroups, nb of them boundary stars spread evenly through the list (item i
+// is a boundary star when floor((i+1) nb / ngroups) > floor(i nb / ngroups)), so that
+// their latency-bound products overlap the other CTAs' streaming of interior stars:
+// returns 1 and idx = boundary index, or 0 and idx = interior group (i - boundary items
+// before i).  A bijection onto both index ranges.
+__device__ __forceinline__ int item_of(int i, int ngroups, int nb, int& idx) {
+  if (nb == 0) { idx = i; return 0; }
+  const long long b0 = (long long)i * nb / ngroups, b1 = (long long)(i + 1) * nb / ngroups;
+  if (b1 > b0) { idx = (int)b0; return 1; }
+  idx = i - (int)b0;
+  return 0;
+}
+
 template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
@@ -378,9 +391,10 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   const int nigroups = (count + PPI - 1) / PPI;
   const int ngroups = nigroups + (PPI == 1 ? bi.nb : 0);
 
-  auto issue = [&](int grp, int stage) {   // one bulk copy per patch of the group
-    if (PPI == 1 && grp >= nigroups) {     // a boundary star: its compact block
-      const int b = grp - nigroups;
+  auto issue = [&](int item, int stage) {  // one bulk copy per patch of the group
+    int grp;
+    if (PPI == 1 && item_of(item, ngroups, bi.nb, grp)) {   // a boundary star: its compact block
+      const int b = grp;
       int vx, vy, vz;
       vertex_coords<DIM>(g, bi.bvid[b], vx, vy, vz);
       const uint32_t bytes = (uint32_t)bnd_stride(StarAxes<DIM>(g, vx, vy, vz).m) * 4u;
@@ -441,8 +455,16 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   pdl_wait();
   float rpre[RPT];
   PatchPos qcur{}, qnext{};
+  // the interior group of this CTA's first interior item at or after `item` (nigroups if none)
+  auto next_interior = [&](int item) {
+    for (; item < ngroups; item += gridDim.x) {
+      int gi;
+      if (!item_of(item, ngroups, PPI == 1 ? bi.nb : 0, gi)) return gi;
+    }
+    return nigroups;
+  };
   if constexpr (PPI == 1) {
-    qnext = patch_pos<DIM>(g, interior, blockIdx.x, count);
+    qnext = patch_pos<DIM>(g, interior, next_interior(blockIdx.x), count);
     gather1(qnext, rpre);
   } else {
     gather(blockIdx.x, rpre);
@@ -453,15 +475,16 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   bool diag = false;
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
   int it = 0;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+  for (int item = blockIdx.x; item < ngroups; item += gridDim.x, ++it) {
     const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
-    if (PPI == 1 && grp >= nigroups) {
+    int grp;   // interior group, or boundary index
+    if (PPI == 1 && item_of(item, ngroups, bi.nb, grp)) {
       // boundary star: r at its free dofs (read directly), the rows of its compact
       // inverse from the stage, then every entry of its scratch row (0 at absent nodes);
       // the same two barriers as an interior star, so the ring advances alike
       int vx, vy, vz;
-      vertex_coords<DIM>(g, bi.bvid[grp - nigroups], vx, vy, vz);
+      vertex_coords<DIM>(g, bi.bvid[grp], vx, vy, vz);
       const StarAxes<DIM> ax(g, vx, vy, vz);
       const int m = ax.m;
       if (tid < m) {
@@ -470,7 +493,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
         rs[tid] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
       }
       if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
-        if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
+        if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, item); s_fail = 1; }
       }
       __syncthreads();                      // (A)
       if (s_fail) break;
@@ -485,7 +508,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       }
       __syncthreads();                      // (B)
       if (tid == ISSUER) {
-        const int nxt = grp + NSTAGE * gridDim.x;
+        const int nxt = item + NSTAGE * gridDim.x;
         if (nxt < ngroups) {
           tma::fence_async();
           issue(nxt, stage);
@@ -505,13 +528,13 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // next group's r: in flight while this one is computed
     if constexpr (PPI == 1) {
       qcur = qnext;
-      qnext = patch_pos<DIM>(g, interior, grp + gridDim.x, count);
+      qnext = patch_pos<DIM>(g, interior, next_interior(item + gridDim.x), count);
       gather1(qnext, rpre);
     } else {
       gather(grp + gridDim.x, rpre);
     }
     if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
-      if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
+      if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, item); s_fail = 1; }
     }
     __syncthreads();                        // (A) r and the stage are visible
     if (s_fail) break;
@@ -533,8 +556,8 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       }
     }
     __syncthreads();                        // (B) the stage is consumed, the partials are complete
-    if (tid == ISSUER) {                    // refill the stage NSTAGE groups ahead
-      const int nxt = grp + NSTAGE * gridDim.x;
+    if (tid == ISSUER) {                    // refill the stage NSTAGE items ahead
+      const int nxt = item + NSTAGE * gridDim.x;
       if (nxt < ngroups) {
         tma::fence_async();
         issue(nxt, stage);
