@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
 
   auto issue = [&](int item, int stage) {  // one bulk copy per patch of the group
     int grp;
-    if (PPI == 1 && item_of(item, ngroups, bi.nb, grp)) {   // a boundary star: its compact block
+    if (item_of(item, ngroups, PPI == 1 ? bi.nb : 0, grp)) {   // a boundary star: its compact block
       const int b = grp;
       int vx, vy, vz;
       vertex_coords<DIM>(g, bi.bvid[b], vx, vy, vz);
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
     int grp;   // interior group, or boundary index
-    if (PPI == 1 && item_of(item, ngroups, bi.nb, grp)) {
+    if (item_of(item, ngroups, PPI == 1 ? bi.nb : 0, grp)) {
       // boundary star: r at its free dofs (read directly), the rows of its compact
       // inverse from the stage, then every entry of its scratch row (0 at absent nodes);
       // the same two barriers as an interior star, so the ring advances alike
