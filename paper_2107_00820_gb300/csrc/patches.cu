@@ -347,33 +347,10 @@ __device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const
   return true;
 }
 
-// The boundary stars' compact inverses (StarAxes, tri_pos; offsets multiples of 4 floats),
-// handled by the 3D TMA kernel as work items after its interior stars (nb = 0: none).
-struct BndIn {
-  const float* bnd32;
-  const int* bvid;
-  const long long* boff;
-  int nb;
-};
-__host__ __device__ __forceinline__ int bnd_stride(int m) { return ((m * (m + 1) / 2) + 3) & ~3; }
-
-// Work item i of ngroups, nb of them boundary stars spread evenly through the list (item i
-// is a boundary star when floor((i+1) nb / ngroups) > floor(i nb / ngroups)), so that
-// their latency-bound products overlap the other CTAs' streaming of interior stars:
-// returns 1 and idx = boundary index, or 0 and idx = interior group (i - boundary items
-// before i).  A bijection onto both index ranges.
-__device__ __forceinline__ int item_of(int i, int ngroups, int nb, int& idx) {
-  if (nb == 0) { idx = i; return 0; }
-  const long long b0 = (long long)i * nb / ngroups, b1 = (long long)(i + 1) * nb / ngroups;
-  if (b1 > b0) { idx = (int)b0; return 1; }
-  idx = i - (int)b0;
-  return 0;
-}
-
 template <int DIM, int NST>
 __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
-                                                  DevStatus* st, int wait_polls, BndIn bi) {
+                                                  DevStatus* st, int wait_polls, int early_trigger) {
   using C = TmaCfg<DIM, NST>;
   constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
@@ -387,21 +364,9 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   float* part = rs + PPI * NP;                            // [PPI][NP][NBR]
   __shared__ int s_fail;
   const int tid = threadIdx.x;
-  // work items: the interior stars in groups of PPI, then (3D, PPI = 1) one boundary star each
-  const int nigroups = (count + PPI - 1) / PPI;
-  const int ngroups = nigroups + (PPI == 1 ? bi.nb : 0);
+  const int ngroups = (count + PPI - 1) / PPI;
 
-  auto issue = [&](int item, int stage) {  // one bulk copy per patch of the group
-    int grp;
-    if (item_of(item, ngroups, PPI == 1 ? bi.nb : 0, grp)) {   // a boundary star: its compact block
-      const int b = grp;
-      int vx, vy, vz;
-      vertex_coords<DIM>(g, bi.bvid[b], vx, vy, vz);
-      const uint32_t bytes = (uint32_t)bnd_stride(StarAxes<DIM>(g, vx, vy, vz).m) * 4u;
-      tma::mbar_expect_tx(&bars[stage], bytes);
-      tma::bulk_load(stages + stage * C::stage_floats, bi.bnd32 + bi.boff[b], bytes, &bars[stage]);
-      return;
-    }
+  auto issue = [&](int grp, int stage) {   // one bulk copy per patch of the group
     uint32_t bytes = 0;
     int vids[PPI];
     for (int ps = 0; ps < PPI; ++ps) {
@@ -453,18 +418,13 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   // the first inverse blocks (written only by the setup) are in flight; r comes from
   // the preceding kernel of the cycle
   pdl_wait();
+  // early_trigger: the successor (the boundary-star kernel, which needs nothing this
+  // kernel writes) may start now and run beside this one
+  if (early_trigger) pdl_trigger();
   float rpre[RPT];
   PatchPos qcur{}, qnext{};
-  // the interior group of this CTA's first interior item at or after `item` (nigroups if none)
-  auto next_interior = [&](int item) {
-    for (; item < ngroups; item += gridDim.x) {
-      int gi;
-      if (!item_of(item, ngroups, PPI == 1 ? bi.nb : 0, gi)) return gi;
-    }
-    return nigroups;
-  };
   if constexpr (PPI == 1) {
-    qnext = patch_pos<DIM>(g, interior, next_interior(blockIdx.x), count);
+    qnext = patch_pos<DIM>(g, interior, blockIdx.x, count);
     gather1(qnext, rpre);
   } else {
     gather(blockIdx.x, rpre);
@@ -475,51 +435,9 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   bool diag = false;
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
   int it = 0;
-  for (int item = blockIdx.x; item < ngroups; item += gridDim.x, ++it) {
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
     const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
-    int grp;   // interior group, or boundary index
-    if (item_of(item, ngroups, PPI == 1 ? bi.nb : 0, grp)) {
-      // boundary star: r at its free dofs (read directly), the rows of its compact
-      // inverse from the stage, then every entry of its scratch row (0 at absent nodes);
-      // the same two barriers as an interior star, so the ring advances alike
-      int vx, vy, vz;
-      vertex_coords<DIM>(g, bi.bvid[grp], vx, vy, vz);
-      const StarAxes<DIM> ax(g, vx, vy, vz);
-      const int m = ax.m;
-      if (tid < m) {
-        long long nd;
-        const int i = ax.entry(tid);
-        rs[tid] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
-      }
-      if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
-        if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, item); s_fail = 1; }
-      }
-      __syncthreads();                      // (A)
-      if (s_fail) break;
-      if (tid < m) {
-        const float* S = stages + stage * C::stage_floats;
-        float acc = 0.f;
-        for (int c = 0; c < m; ++c) {
-          const int lo = tid < c ? tid : c, hi = tid < c ? c : tid;
-          acc += S[tri_pos(m, lo, hi)] * rs[c];
-        }
-        part[tid] = acc;
-      }
-      __syncthreads();                      // (B)
-      if (tid == ISSUER) {
-        const int nxt = item + NSTAGE * gridDim.x;
-        if (nxt < ngroups) {
-          tma::fence_async();
-          issue(nxt, stage);
-        }
-      }
-      for (int i = tid; i < NP; i += THREADS) {
-        const int a = ax.free_index(i);
-        out[patch_out_index<DIM>(g, vx, vy, vz, i)] = a >= 0 ? part[a] : 0.f;
-      }
-      continue;
-    }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int e = tid + k * THREADS;
@@ -528,13 +446,13 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // next group's r: in flight while this one is computed
     if constexpr (PPI == 1) {
       qcur = qnext;
-      qnext = patch_pos<DIM>(g, interior, next_interior(item + gridDim.x), count);
+      qnext = patch_pos<DIM>(g, interior, grp + gridDim.x, count);
       gather1(qnext, rpre);
     } else {
       gather(grp + gridDim.x, rpre);
     }
     if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
-      if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, item); s_fail = 1; }
+      if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
     }
     __syncthreads();                        // (A) r and the stage are visible
     if (s_fail) break;
@@ -556,8 +474,8 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
       }
     }
     __syncthreads();                        // (B) the stage is consumed, the partials are complete
-    if (tid == ISSUER) {                    // refill the stage NSTAGE items ahead
-      const int nxt = item + NSTAGE * gridDim.x;
+    if (tid == ISSUER) {                    // refill the stage NSTAGE groups ahead
+      const int nxt = grp + NSTAGE * gridDim.x;
       if (nxt < ngroups) {
         tma::fence_async();
         issue(nxt, stage);
@@ -603,7 +521,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // rewritten after (B); the partials are read after (B) and rewritten only after
     // barrier (A) of the next iteration, which every thread reaches after its reads
   }
-  pdl_trigger();
+  if (!early_trigger) pdl_trigger();
   if (s_fail && tid == ISSUER) {
     // drain: wait (bounded, at the default limit whatever wait_polls is) for every copy
     // this CTA issued and did not consume, so that none is in flight when the CTA exits
@@ -714,6 +632,12 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
 // star (a face, edge or corner vertex has 1/3, 1/9 or 1/27 of the interior star's free
 // dofs in 3D), from the compact packed inverses, one warp per boundary vertex; every
 // entry of the vertex's scratch row is written (0 at absent and Dirichlet nodes).
+//
+// It is launched right after the interior-star kernel of the same products and runs
+// beside it: that kernel lets it start once its own dependency wait has returned (r is
+// then complete, and this kernel reads it from L2), the two write disjoint scratch
+// rows, and this kernel waits for its predecessor only at its end, so that its
+// successor, which waits for it, sees both kernels' rows.
 // ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
@@ -723,7 +647,6 @@ __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restri
   __shared__ float rs[8][MMAX];
   __shared__ float ys[8][MMAX];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  pdl_wait();
   for (long long b = (long long)blockIdx.x * 8 + w; b < nb; b += (long long)gridDim.x * 8) {
     const int v = bvid[b];
     int vx, vy, vz;
@@ -733,7 +656,7 @@ __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restri
     if (lane < m) {
       long long nd;
       const int i = ax.entry(lane);
-      rs[w][lane] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldg(r + (i / NB) * g.N + nd) : 0.f;
+      rs[w][lane] = patch_node<DIM>(g, vx, vy, vz, i % NB, nd) ? __ldcg(r + (i / NB) * g.N + nd) : 0.f;
     }
     __syncwarp();
     if (lane < m) {
@@ -752,6 +675,7 @@ __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restri
     }
     __syncwarp();
   }
+  pdl_wait();
   pdl_trigger();
 }
 
@@ -803,14 +727,11 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
     if (per_sm < 1) per_sm = 1;
   }
   const long long cap = 152LL * per_sm;
-  // 3D smoother products: the boundary stars ride along as extra work items
-  BndIn bi{L.bnd32, L.bvid, L.boff, 0};
-  if (DIM == 3 && !interior && mode == OUT_SCRATCH) bi.nb = (int)L.nbnd;
-  const long long items = groups + bi.nb;
-  const long long grid2 = items < cap ? items : cap;
-  if (grid2 <= 0) return;
-  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid2, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
-             (int)count, r, out, mode, st, L.wait_polls, bi);
+  const long long grid = groups < cap ? groups : cap;
+  if (grid <= 0) return;
+  const int early = (!interior && mode == OUT_SCRATCH && L.nbnd > 0) ? 1 : 0;   // the boundary kernel follows
+  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
+             (int)count, r, out, mode, st, L.wait_polls, early);
   count_launch(1);
 }
 
@@ -1081,16 +1002,15 @@ static void smooth_impl(const LevelDev& L, const TF* inv, const void* r, void* z
 }
 
 // All star products y_v = A_v^-1 r|_v of a level into the scratch rows (FP32) with kernel
-// variant v: the interior stars in the variant's kernel; the boundary stars inside the 3D
-// TMA kernels' work list, else (2D, or the direct variant) in k_patch_bnd, launched first.
-// e0/e1 (optional) bracket the interior-star kernel.
+// variant v: the interior stars in the variant's kernel (bracketed by e0/e1 when given),
+// then the boundary stars in k_patch_bnd, which runs beside it (see k_patch_bnd).
 template <int DIM>
 static void star_products(int v, const LevelDev& L, const float* r, float* scratch, cudaStream_t s, cudaEvent_t e0,
                           cudaEvent_t e1) {
-  if (DIM == 2 || v == 2) launch_patch_bnd<DIM>(L, r, scratch, s);
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   launch_patch_variant<DIM>(v, L, 0, L.nint, r, scratch, OUT_SCRATCH, L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  launch_patch_bnd<DIM>(L, r, scratch, s);
 }
 
 template <int DIM>
