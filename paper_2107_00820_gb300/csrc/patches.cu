@@ -639,15 +639,17 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
 // rows, and this kernel waits for its predecessor only at its end, so that its
 // successor, which waits for it, sees both kernels' rows.
 // ---------------------------------------------------------------------------
+// Two warps per CTA and one CTA per SM: small enough (registers, threads) to be resident
+// beside the interior kernel's persistent CTAs.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
-                                                   const int* __restrict__ bvid, const long long* __restrict__ boff,
-                                                   long long nb, const float* __restrict__ r, float* __restrict__ out) {
+__global__ void __launch_bounds__(64) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
+                                                  const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                  long long nb, const float* __restrict__ r, float* __restrict__ out) {
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6;
-  __shared__ float rs[8][MMAX];
-  __shared__ float ys[8][MMAX];
+  __shared__ float rs[2][MMAX];
+  __shared__ float ys[2][MMAX];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long b = (long long)blockIdx.x * 8 + w; b < nb; b += (long long)gridDim.x * 8) {
+  for (long long b = (long long)blockIdx.x * 2 + w; b < nb; b += (long long)gridDim.x * 2) {
     const int v = bvid[b];
     int vx, vy, vz;
     vertex_coords<DIM>(g, v, vx, vy, vz);
@@ -682,8 +684,8 @@ __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restri
 template <int DIM>
 static void launch_patch_bnd(const LevelDev& L, const float* r, float* out, cudaStream_t s) {
   if (L.nbnd <= 0) return;
-  const long long want = (L.nbnd + 7) / 8, cap = 152LL * 8;
-  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 256, 0, s, L.g, (const float*)L.bnd32,
+  const long long want = (L.nbnd + 1) / 2, cap = 152LL;
+  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 64, 0, s, L.g, (const float*)L.bnd32,
              (const int*)L.bvid, (const long long*)L.boff, L.nbnd, r, out);
   count_launch(1);
 }
