@@ -57,6 +57,7 @@ struct StarAxes {
   __device__ __forceinline__ StarAxes(const Geom& g, int vx, int vy, int vz) {
     const int v[3] = {vx, vy, vz};
     m = DIM;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (k >= DIM) { lo[k] = 0; cnt[k] = 1; continue; }
       if (v[k] == 0) { lo[k] = 2; cnt[k] = 1; }
@@ -639,22 +640,28 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
 // rows, and this kernel waits for its predecessor only at its end, so that its
 // successor, which waits for it, sees both kernels' rows.
 // ---------------------------------------------------------------------------
-// Two warps per CTA and one CTA per SM: small enough (registers, threads) to be resident
-// beside the interior kernel's persistent CTAs.
+// Three warps per CTA and one CTA per SM (at most 42 registers a thread): small enough to
+// stay resident beside the interior kernel's persistent CTAs (6 of 64 threads x 160
+// registers per SM), so the boundary stars are done while the interior ones stream.
+// Each warp first stages its star's packed block and r in shared memory with all lanes
+// (independent loads), then forms the rows from shared memory.
 template <int DIM>
-__global__ void __launch_bounds__(64) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
-                                                  const int* __restrict__ bvid, const long long* __restrict__ boff,
-                                                  long long nb, const float* __restrict__ r, float* __restrict__ out) {
-  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6;
-  __shared__ float rs[2][MMAX];
-  __shared__ float ys[2][MMAX];
+__global__ void __launch_bounds__(96, 16) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
+                                                      const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                      long long nb, const float* __restrict__ r, float* __restrict__ out) {
+  constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6, SMAX = MMAX * (MMAX + 1) / 2;
+  __shared__ float Ss[3][SMAX];
+  __shared__ float rs[3][MMAX];
+  __shared__ float ys[3][MMAX];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long b = (long long)blockIdx.x * 2 + w; b < nb; b += (long long)gridDim.x * 2) {
-    const int v = bvid[b];
+  for (long long b = (long long)blockIdx.x * 3 + w; b < nb; b += (long long)gridDim.x * 3) {
+    const int v = __ldg(bvid + b);
+    const float* S = bnd32 + __ldg(boff + b);
     int vx, vy, vz;
     vertex_coords<DIM>(g, v, vx, vy, vz);
     const StarAxes<DIM> ax(g, vx, vy, vz);
-    const int m = ax.m;
+    const int m = ax.m, sz = m * (m + 1) / 2;
+    for (int e = lane; e < sz; e += 32) Ss[w][e] = __ldg(S + e);
     if (lane < m) {
       long long nd;
       const int i = ax.entry(lane);
@@ -662,11 +669,11 @@ __global__ void __launch_bounds__(64) k_patch_bnd(Geom g, const float* __restric
     }
     __syncwarp();
     if (lane < m) {
-      const float* S = bnd32 + boff[b];
       float acc = 0.f;
+#pragma unroll 4
       for (int c = 0; c < m; ++c) {
         const int lo = lane < c ? lane : c, hi = lane < c ? c : lane;
-        acc += __ldg(S + tri_pos(m, lo, hi)) * rs[w][c];
+        acc += Ss[w][tri_pos(m, lo, hi)] * rs[w][c];
       }
       ys[w][lane] = acc;
     }
@@ -684,8 +691,8 @@ __global__ void __launch_bounds__(64) k_patch_bnd(Geom g, const float* __restric
 template <int DIM>
 static void launch_patch_bnd(const LevelDev& L, const float* r, float* out, cudaStream_t s) {
   if (L.nbnd <= 0) return;
-  const long long want = (L.nbnd + 1) / 2, cap = 152LL;
-  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 64, 0, s, L.g, (const float*)L.bnd32,
+  const long long want = (L.nbnd + 2) / 3, cap = 152LL;
+  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 96, 0, s, L.g, (const float*)L.bnd32,
              (const int*)L.bvid, (const long long*)L.boff, L.nbnd, r, out);
   count_launch(1);
 }
