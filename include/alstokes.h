@@ -40,7 +40,12 @@
  * kernel instead of replaying a captured CUDA graph; ALS_PDL=0 launches without
  * programmatic dependent launch; ALS_PATCH_KERNEL=tma2|tma3|direct forces one FP32
  * star-patch kernel variant on every level; ALS_FUSE_GATHER=0 keeps the separate
- * patch-gather kernel in the FP32 3D smoother (bitwise the same results).
+ * patch-gather kernel in the FP32 3D smoother (bitwise the same results);
+ * ALS_SPLIT_STARS=1 / 0 makes every smoothed level store its FP32 star inverses split
+ * (interior stars block-packed, boundary stars restricted to their free dofs, applied by a
+ * second kernel) or whole (every star padded to d 3^d dofs); by default levels with at
+ * least 32768 vertices are split (the FP32 results differ in the rounding of the boundary
+ * stars' sums).
  */
 #ifndef ALSTOKES_H
 #define ALSTOKES_H

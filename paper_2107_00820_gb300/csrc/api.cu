@@ -761,15 +761,31 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   return check_status(c, "setup");
 }
 
-// FP32 star storage of a smoothed level: block-packed inverses of the interior
-// vertices, and the boundary vertices' compact inverses (free dofs only: 1/3, 1/9 and
-// 1/27 of an interior star's dofs at faces, edges and corners in 3D) with their vertex
-// ids and offsets, enumerated here on the host.
+// FP32 star storage of a smoothed level.  Levels of at least kSplitVertices vertices use
+// split storage: block-packed inverses of the interior vertices, and the boundary vertices'
+// compact inverses (free dofs only: 1/3, 1/9 and 1/27 of an interior star's dofs at faces,
+// edges and corners in 3D) with their vertex ids and offsets, enumerated here on the host;
+// the smoother streams 15-20 % fewer bytes there and applies the boundary stars in a
+// small second kernel.  Smaller levels, whose cycle time is launch latency rather than
+// bytes, keep every vertex's block-packed inverse (identity rows at absent nodes) and one
+// kernel.
+constexpr long long kSplitVertices = 32768;
+
 static als_status alloc_star_storage(als_ctx* c, LevelDev& Lv) {
   const Geom& g = Lv.g;
   const int d = c->dim;
   Lv.nint = 1;
   for (int k = 0; k < d; ++k) Lv.nint *= g.nv[k] - 2;
+  static int forced = -2;   // ALS_SPLIT_STARS=1 / 0 forces split / full storage on every level
+  if (forced == -2) {
+    const char* e = getenv("ALS_SPLIT_STARS");
+    forced = (e && e[0] == '1') ? 1 : ((e && e[0] == '0') ? 0 : -1);
+  }
+  Lv.split = forced >= 0 ? forced : (g.nverts >= kSplitVertices ? 1 : 0);
+  if (!Lv.split) {
+    Lv.nbnd = 0;
+    return dalloc(c, &Lv.inv32, (size_t)g.nverts * Lv.pstride);
+  }
   std::vector<int> bvid;
   std::vector<long long> boff;
   long long total = 0;

@@ -21,10 +21,12 @@ struct LevelDev {
   double* mu64;          // scalar viscosity per point (mu or mu_eff), FP64
   // vertex-star patch inverses: FP64 packed symmetric by diagonals, one per vertex
   // (identity rows at absent and Dirichlet nodes); FP32 block-packed (BlockLayout) for
-  // the interior vertices only (1 <= v_k <= n_k - 1, interior index x-fastest), and for
-  // the boundary vertices a compact FP32 copy restricted to the free dofs of the star
+  // every vertex, or, with split storage (large levels), for the interior vertices only
+  // (1 <= v_k <= n_k - 1, interior index x-fastest) and a compact FP32 copy of each
+  // boundary vertex's star restricted to its free dofs
   double* inv64;
   float* inv32;
+  int split;             // split storage (see above)
   float* bnd32;          // boundary stars: packed upper triangle by rows, m x m, m = free dofs
   int* bvid;             // boundary vertex ids (nbnd), ascending
   long long* boff;       // offset of each boundary star's compact inverse in bnd32

@@ -257,20 +257,24 @@ struct TmaCfg {
   static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
 };
 
-// Slot p of the work list of the FP32 interior-patch kernels -- all interior vertices
-// (1 <= v_k <= n_k - 1), or the centres 2K+1 of the coarse cells, which are interior --
-// as its lattice coordinates and its index in the interior-only FP32 storage (inv32);
-// -1 past the end.  Every node of an interior vertex's star is a free node.
+// Work list of the FP32 star kernels, wl = bit 0 | bit 1: bit 0 clear = the star products
+// of the smoother, set = the local solves on the coarse-cell interiors (the stars of the
+// fine vertices 2K+1 at the coarse-cell centres, which are interior vertices); bit 1 set =
+// split storage, where inv32 holds the interior vertices only (interior index x-fastest)
+// and the smoother's list is the interior vertices, else inv32 holds every vertex (identity
+// rows at absent nodes) and the smoother's list is every vertex.  Returns the index of slot
+// p's inverse in inv32 and its lattice coordinates; -1 past the end.
 template <int DIM>
-__device__ __forceinline__ int work_vertex(const Geom& g, int interior, int p, int count, int& vx, int& vy,
-                                           int& vz) {
+__device__ __forceinline__ int work_vertex(const Geom& g, int wl, int p, int count, int& vx, int& vy, int& vz) {
   if (p >= count) return -1;
+  const bool split = (wl & 2) != 0;
   const int nix = g.nv[0] - 2, niy = g.nv[1] - 2;
-  if (!interior) {
-    vx = p % nix + 1;
-    const int q = p / nix;
-    vy = q % niy + 1;
-    vz = DIM == 3 ? q / niy + 1 : 0;
+  if (!(wl & 1)) {
+    const int ox = split ? 1 : 0, nx = split ? nix : g.nv[0], ny = split ? niy : g.nv[1];
+    vx = p % nx + ox;
+    const int q = p / nx;
+    vy = q % ny + ox;
+    vz = DIM == 3 ? q / ny + ox : 0;
     return p;
   }
   const int ncx = g.n[0] >> 1, ncy = g.n[1] >> 1;
@@ -278,7 +282,8 @@ __device__ __forceinline__ int work_vertex(const Geom& g, int interior, int p, i
   vx = 2 * kx + 1;
   vy = 2 * ky + 1;
   vz = DIM == 3 ? 2 * kz + 1 : 0;
-  return (vx - 1) + nix * ((vy - 1) + (DIM == 3 ? niy * (vz - 1) : 0));
+  if (split) return (vx - 1) + nix * ((vy - 1) + (DIM == 3 ? niy * (vz - 1) : 0));
+  return vx + g.nv[0] * (vy + g.nv[1] * vz);
 }
 
 // r at patch entry i of the vertex (absent nodes give 0)
@@ -624,7 +629,8 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
   const long long cap = 152LL * 8;
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  launch_pdl(k_patch_direct<DIM>, (unsigned)grid, C::THREADS, 0, s, L.g, L.inv32, interior, (int)count, r, out, mode);
+  launch_pdl(k_patch_direct<DIM>, (unsigned)grid, C::THREADS, 0, s, L.g, L.inv32, interior | (L.split ? 2 : 0),
+             (int)count, r, out, mode);
   count_launch(1);
 }
 
@@ -640,21 +646,18 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
 // rows, and this kernel waits for its predecessor only at its end, so that its
 // successor, which waits for it, sees both kernels' rows.
 // ---------------------------------------------------------------------------
-// Three warps per CTA and one CTA per SM (at most 42 registers a thread): small enough to
-// stay resident beside the interior kernel's persistent CTAs (6 of 64 threads x 160
-// registers per SM), so the boundary stars are done while the interior ones stream.
-// Each warp first stages its star's packed block and r in shared memory with all lanes
-// (independent loads), then forms the rows from shared memory.
+// One warp per boundary star (8 per CTA): the star's packed block and r are staged in
+// shared memory by all lanes (independent loads), then the rows are formed from there.
 template <int DIM>
-__global__ void __launch_bounds__(96, 16) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
-                                                      const int* __restrict__ bvid, const long long* __restrict__ boff,
-                                                      long long nb, const float* __restrict__ r, float* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
+                                                   const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                   long long nb, const float* __restrict__ r, float* __restrict__ out) {
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6, SMAX = MMAX * (MMAX + 1) / 2;
-  __shared__ float Ss[3][SMAX];
-  __shared__ float rs[3][MMAX];
-  __shared__ float ys[3][MMAX];
+  __shared__ float Ss[8][SMAX];
+  __shared__ float rs[8][MMAX];
+  __shared__ float ys[8][MMAX];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long b = (long long)blockIdx.x * 3 + w; b < nb; b += (long long)gridDim.x * 3) {
+  for (long long b = (long long)blockIdx.x * 8 + w; b < nb; b += (long long)gridDim.x * 8) {
     const int v = __ldg(bvid + b);
     const float* S = bnd32 + __ldg(boff + b);
     int vx, vy, vz;
@@ -691,8 +694,8 @@ __global__ void __launch_bounds__(96, 16) k_patch_bnd(Geom g, const float* __res
 template <int DIM>
 static void launch_patch_bnd(const LevelDev& L, const float* r, float* out, cudaStream_t s) {
   if (L.nbnd <= 0) return;
-  const long long want = (L.nbnd + 2) / 3, cap = 152LL;
-  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 96, 0, s, L.g, (const float*)L.bnd32,
+  const long long want = (L.nbnd + 7) / 8, cap = 152LL * 16;
+  launch_pdl(k_patch_bnd<DIM>, (unsigned)(want < cap ? want : cap), 256, 0, s, L.g, (const float*)L.bnd32,
              (const int*)L.bvid, (const long long*)L.boff, L.nbnd, r, out);
   count_launch(1);
 }
@@ -738,9 +741,9 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
   const long long cap = 152LL * per_sm;
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  const int early = (!interior && mode == OUT_SCRATCH && L.nbnd > 0) ? 1 : 0;   // the boundary kernel follows
-  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32, interior,
-             (int)count, r, out, mode, st, L.wait_polls, early);
+  const int early = (!interior && mode == OUT_SCRATCH && L.split && L.nbnd > 0) ? 1 : 0;   // boundary kernel next
+  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32,
+             interior | (L.split ? 2 : 0), (int)count, r, out, mode, st, L.wait_polls, early);
   count_launch(1);
 }
 
@@ -807,17 +810,21 @@ void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStat
 // ---------------------------------------------------------------------------
 // FP32 copies of the FP64 inverses (packed by diagonals, every vertex)
 // ---------------------------------------------------------------------------
-// interior vertices: block-packed (BlockLayout) FP32 copy, one CTA per interior vertex,
-// entry (i, i+t) of diagonal t rounded to the nearest float; padding slots zeroed
+// block-packed (BlockLayout) FP32 copy, one CTA per vertex of inv32 (the interior vertices
+// with split storage, else every vertex), entry (i, i+t) of diagonal t rounded to the
+// nearest float; padding slots zeroed
 template <int DIM>
-__global__ void __launch_bounds__(128) k_derive32(Geom g, int pstride, const double* __restrict__ inv64,
+__global__ void __launch_bounds__(128) k_derive32(Geom g, int pstride, int split, const double* __restrict__ inv64,
                                                   float* __restrict__ inv32) {
   constexpr int NP = Sz<DIM>::NP;
   constexpr BlockLayout BL = BlockLayout(NP);
   const long long iv = blockIdx.x;
-  const int nix = g.nv[0] - 2, niy = g.nv[1] - 2;
-  const long long vx = iv % nix + 1, q = iv / nix, vy = q % niy + 1, vz = DIM == 3 ? q / niy + 1 : 0;
-  const long long v = vx + g.nv[0] * (vy + (long long)g.nv[1] * vz);
+  long long v = iv;
+  if (split) {
+    const int nix = g.nv[0] - 2, niy = g.nv[1] - 2;
+    const long long vx = iv % nix + 1, q = iv / nix, vy = q % niy + 1, vz = DIM == 3 ? q / niy + 1 : 0;
+    v = vx + g.nv[0] * (vy + (long long)g.nv[1] * vz);
+  }
   const double* src = inv64 + v * pstride;
   float* dst = inv32 + iv * pstride;
   for (int e = 44 * BL.nbp + BL.nbp + (int)threadIdx.x; e < BL.q2; e += blockDim.x) dst[e] = 0.f;
@@ -853,9 +860,10 @@ __global__ void __launch_bounds__(256) k_derive32_bnd(Geom g, int pstride, const
 }
 
 void patch_derive32(const LevelDev& L, cudaStream_t s) {
-  if (L.nint > 0) {
-    if (L.g.dim == 3) k_derive32<3><<<(unsigned)L.nint, 128, 0, s>>>(L.g, L.pstride, L.inv64, L.inv32);
-    else k_derive32<2><<<(unsigned)L.nint, 128, 0, s>>>(L.g, L.pstride, L.inv64, L.inv32);
+  const long long nv32 = L.split ? L.nint : L.g.nverts;
+  if (nv32 > 0) {
+    if (L.g.dim == 3) k_derive32<3><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, L.inv32);
+    else k_derive32<2><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, L.inv32);
     count_launch(1);
   }
   if (L.nbnd > 0) {
@@ -1017,9 +1025,9 @@ template <int DIM>
 static void star_products(int v, const LevelDev& L, const float* r, float* scratch, cudaStream_t s, cudaEvent_t e0,
                           cudaEvent_t e1) {
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  launch_patch_variant<DIM>(v, L, 0, L.nint, r, scratch, OUT_SCRATCH, L.status, s);
+  launch_patch_variant<DIM>(v, L, 0, L.split ? L.nint : L.g.nverts, r, scratch, OUT_SCRATCH, L.status, s);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  launch_patch_bnd<DIM>(L, r, scratch, s);
+  if (L.split) launch_patch_bnd<DIM>(L, r, scratch, s);
 }
 
 template <int DIM>
