@@ -210,6 +210,43 @@ als_status als_patch_inverse(als_ctx* ctx, int level, long long vertex, double* 
 als_status als_solve(als_ctx* ctx, const double* f_qp, const double* u_bc, const double* r2, double* u,
                      double* p, als_solve_info* info);
 
+/* ---- Newton's method for the viscoplastic rheology (Sec. 5.3.1) -------------
+ * Solves -div(2 mu(eps_II(u)) eps(u)) + grad p = f, -div u = 0 with u = u_D on the
+ * boundary, mu(eps_II) = mu_ref tau_y / (2 mu_ref eps_II + tau_y), eps_II = sqrt(eps:eps/2).
+ * Starting from u = u_D on the boundary (0 inside) and p = 0, each step linearises at the
+ * iterate (the fourth-order coefficient 2 mu [I - (eps (x) T)_sym / (2 eps_II max(tau_y,
+ * T_II))], T = 2 mu eps, and mu, evaluated at every level's Gauss points from the finest
+ * velocity: rediscretisation, Sec. 5.1), re-runs the setup with it, solves the linearised
+ * AL-augmented system for the step with the context's FGMRES to an absolute tolerance of
+ * 1e-12 |R_0| (relative at most 1e-2), and backtracks by halving until the residual norm
+ * |(R_u, R_p)| falls by a factor (1 - 1e-4 alpha) (after max_halvings failed tries the
+ * last halved step is taken).  Stops when |R| <= rtol |R_0|.
+ * The context must have tensor coefficients (ALS_COEFF_TENSOR; its initial ones are
+ * replaced) and options.schur = ALS_SCHUR_P2 (W = M_p(1/mu), Sec. 5.3.2); either mode.
+ *   f_qp : [cell][3^d][d] body force at the finest Gauss points; u_bc : [d][N] nodal
+ *          Dirichlet data (boundary entries read; NULL = 0); u, p : outputs (host or device)
+ * Returns ALS_ENOTCONV if rtol was not reached within maxit steps (u, p: last iterate). */
+typedef struct {
+  double mu_ref;      /* reference viscosity (default 1) */
+  double tau_y;       /* yield stress (default 1) */
+  double rtol;        /* nonlinear residual reduction (default 1e-10) */
+  int maxit;          /* Newton steps (default 30) */
+  int max_halvings;   /* backtracking halvings per step (default 12) */
+} als_newton_params;
+typedef struct {
+  int iterations;         /* Newton steps taken */
+  int linear_iterations;  /* FGMRES iterations over all steps */
+  int converged;
+  double res0;            /* |(R_u, R_p)| at the initial iterate */
+  double res_final;       /* at the last iterate */
+} als_newton_info;
+void als_newton_default_params(als_newton_params* prm);
+als_status als_newton_solve(als_ctx* ctx, const als_newton_params* prm, const double* f_qp, const double* u_bc,
+                            double* u, double* p, als_newton_info* info);
+/* Residual norm after each step of the last Newton solve (res[0] at the initial iterate)
+ * and the FGMRES iterations of each step (linear_its[0] = 0); copies min(cap, count). */
+als_status als_newton_history(const als_ctx* ctx, double* res, int* linear_its, int cap, int* count);
+
 /* Re-runs the setup of als_create (patch factorisations, coarse Cholesky,
  * Schur blocks) for new coefficients of the same kind and sizes, reusing every
  * allocation and the captured V-cycle graphs: the per-linearisation setup of

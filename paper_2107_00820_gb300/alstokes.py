@@ -45,6 +45,16 @@ class als_options(Structure):
                 ("cycle", c_int), ("fact", c_int), ("setup", c_int)]
 
 
+class als_newton_params(Structure):
+    _fields_ = [("mu_ref", c_double), ("tau_y", c_double), ("rtol", c_double), ("maxit", c_int),
+                ("max_halvings", c_int)]
+
+
+class als_newton_info(Structure):
+    _fields_ = [("iterations", c_int), ("linear_iterations", c_int), ("converged", c_int), ("res0", c_double),
+                ("res_final", c_double)]
+
+
 class als_solve_info(Structure):
     _fields_ = [("iterations", c_int), ("vcycles", c_int), ("converged", c_int), ("res0", c_double),
                 ("res_final", c_double), ("solve_ms", c_double)]
@@ -87,6 +97,10 @@ SIGNATURES = {
     "als_load_coarse_inverse": (c_int, [c_void_p, c_void_p]),
     "als_set_wait_limit": (c_int, [c_void_p, c_int]),
     "als_solve_history": (c_int, [c_void_p, POINTER(c_double), c_int, POINTER(c_int)]),
+    "als_newton_default_params": (None, [POINTER(als_newton_params)]),
+    "als_newton_solve": (c_int, [c_void_p, POINTER(als_newton_params), c_void_p, c_void_p, c_void_p, c_void_p,
+                                 POINTER(als_newton_info)]),
+    "als_newton_history": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int, POINTER(c_int)]),
 }
 
 _LIB = None
@@ -304,6 +318,33 @@ class Context:
         out = (c_double * max(cnt.value, 1))()
         self._call("als_solve_history", out, cnt.value, byref(cnt))
         return np.array(out[: cnt.value])
+
+    def newton_solve(self, f_qp, u_bc=None, u=None, p=None, check=True, **params):
+        """Newton's method for the viscoplastic rheology (als_newton_solve); params are the
+        fields of als_newton_params (mu_ref, tau_y, rtol, maxit, max_halvings).  Returns
+        (u, p, info); inputs/outputs may be host (NumPy) or device (torch) arrays."""
+        prm = als_newton_params()
+        self._lib.als_newton_default_params(byref(prm))
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise KeyError(k)
+            setattr(prm, k, v)
+        u = np.zeros(self.nu()) if u is None else u
+        p = np.zeros(self.npres()) if p is None else p
+        info = als_newton_info()
+        st = self._lib.als_newton_solve(self._ctx, byref(prm), _ptr(f_qp), _ptr(u_bc), _ptr(u), _ptr(p), byref(info))
+        if st != ALS_OK and (check or st != ALS_ENOTCONV):
+            raise ALSError(st, self._lib.als_last_error(self._ctx).decode())
+        return u, p, info
+
+    def newton_history(self):
+        """(residual norms, FGMRES iterations per step) of the last Newton solve."""
+        cnt = c_int()
+        self._call("als_newton_history", None, None, 0, byref(cnt))
+        res = (c_double * max(cnt.value, 1))()
+        its = (c_int * max(cnt.value, 1))()
+        self._call("als_newton_history", res, its, cnt.value, byref(cnt))
+        return np.array(res[: cnt.value]), list(its[: cnt.value])
 
     def profile_read_kernel(self, kind):
         """(total ms, launches) of kernel class `kind` (0 patch kernel, 1 operator apply)."""

@@ -108,6 +108,16 @@ struct als_ctx {
     std::vector<double> hist;   // |b|, then the FGMRES residual estimate after each iteration
   } run;
   unsigned long long* minbits = nullptr;   // device scratch of the smallest-viscosity check
+  // Newton's method (als_newton_solve): iterate, step, trial point, residual, load vector,
+  // viscosity at the finest points, and the linearised coefficients of every level
+  struct NewtonBuf {
+    bool ready = false;
+    double *u = nullptr, *p = nullptr, *du = nullptr, *dp = nullptr, *ut = nullptr, *pt = nullptr;
+    double *Ru = nullptr, *Rp = nullptr, *F = nullptr, *mu = nullptr;
+    std::vector<double*> C, mul;
+    std::vector<double> hist;
+    std::vector<int> lin;
+  } nw;
 };
 
 namespace {
@@ -1154,6 +1164,20 @@ als_status als_solve_history(const als_ctx* c, double* out, int cap, int* count)
 // per round: start (inputs, lifted rhs, |b| on its way to the host), then rounds
 // of launch-iteration / iteration-done, then finish.
 
+// FGMRES (Sec. 5.1), right preconditioned, CGS2, x0 = 0, for the right-hand side in
+// c->V[0]: |b| (on its way to the host), V[0] = b / |b|
+static als_status fgmres_begin(als_ctx* c) {
+  const cudaStream_t s = c->stream;
+  const int maxit = c->opt.maxit, ldh = maxit + 1;
+  double* rhs = c->V;
+  vec_multidot(PREC_F64, c->n, 1, rhs, c->n, rhs, c->nrm2, c->partial, s);
+  dev_init_g(maxit + 1, c->nrm2, c->g, c->beta, s);
+  vec_scale_dev(PREC_F64, c->n, nullptr, c->beta, rhs, rhs, s);
+  cudaMemsetAsync(c->H, 0, sizeof(double) * ldh * maxit, s);
+  cudaMemcpyAsync(c->host_res + 1, c->beta, sizeof(double), cudaMemcpyDeviceToHost, s);
+  return cuda_check(c, "solve rhs");
+}
+
 // queue the inputs, the lifted augmented right-hand side and |b| (no wait)
 static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u,
                               double* p) {
@@ -1193,14 +1217,7 @@ static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc
   op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);         // B^T gamma W^-1 r2
   vec_axpby(PREC_F64, c->nu, 1.0, c->tu2, 1.0, c->tu, s);
   bnd_mask(F.g, c->tu, rhs_u, 0, s);                                                   // zero boundary rows
-  // FGMRES (Sec. 5.1), right preconditioned, CGS2, x0 = 0
-  const int ldh = maxit + 1;
-  vec_multidot(PREC_F64, c->n, 1, rhs, c->n, rhs, c->nrm2, c->partial, s);
-  dev_init_g(maxit + 1, c->nrm2, c->g, c->beta, s);
-  vec_scale_dev(PREC_F64, c->n, nullptr, c->beta, rhs, rhs, s);
-  cudaMemsetAsync(c->H, 0, sizeof(double) * ldh * maxit, s);
-  cudaMemcpyAsync(c->host_res + 1, c->beta, sizeof(double), cudaMemcpyDeviceToHost, s);
-  return cuda_check(c, "solve rhs");
+  return fgmres_begin(c);
 }
 
 // after the stream has drained: read |b|
@@ -1301,6 +1318,196 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
   return solve_finish(c, info);
 }
 
+
+// ============================================================================
+// Newton's method for the viscoplastic rheology (Sec. 5.3.1), on the GPU.
+// Each step linearises at the current iterate (newton.cu: the fourth-order coefficient
+// and mu at every level's Gauss points), re-runs the setup with it (als_update_coefficients),
+// solves [J B^T; B 0] [du; dp] = -[R_u; R_p] (the AL-augmented, W = M_p(1/mu) form) with
+// the context's FGMRES to an absolute tolerance of 1e-12 |R_0| (relative 1e-2 at most),
+// and backtracks by halving until the residual norm decreases by 1e-4 alpha.  The residual
+// R_u = A(mu(u)) u + B^T p - F (Dirichlet rows 0), R_p = B u is evaluated with the scalar
+// viscosity mu(eps_II(u)) at the finest points.
+// ============================================================================
+static als_status newton_alloc(als_ctx* c) {
+  als_ctx::NewtonBuf& W = c->nw;
+  if (W.ready) return ALS_OK;
+  const LevelDev& F = c->lev[c->L - 1];
+  const int NB = c->dim == 2 ? 9 : 27, NC = c->dim == 2 ? 6 : 21;
+  for (double** q : {&W.u, &W.ut, &W.du, &W.Ru, &W.F}) ALS_TRY(dalloc(c, q, c->nu));
+  for (double** q : {&W.p, &W.pt, &W.dp, &W.Rp}) ALS_TRY(dalloc(c, q, c->np));
+  ALS_TRY(dalloc(c, &W.mu, (size_t)F.g.ncells * NB));
+  W.C.assign(c->L, nullptr);
+  W.mul.assign(c->L, nullptr);
+  for (int l = 0; l < c->L; ++l) {
+    ALS_TRY(dalloc(c, &W.C[l], (size_t)c->lev[l].g.ncells * NB * NC));
+    ALS_TRY(dalloc(c, &W.mul[l], (size_t)c->lev[l].g.ncells * NB));
+  }
+  W.ready = true;
+  return ALS_OK;
+}
+
+// |(R_u, R_p)| at (u, p); R_u and R_p are left in c->nw
+static als_status newton_residual(als_ctx* c, const als_newton_params& prm, const double* u, const double* p,
+                                  double* norm) {
+  als_ctx::NewtonBuf& W = c->nw;
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  newton_coeffs(F.g, F.g, u, prm.mu_ref, prm.tau_y, nullptr, W.mu, s);
+  LevelDev Lm = F;                        // the finest level with the scalar viscosity mu(u)
+  Lm.tensor = 0;
+  Lm.ncoef = 1;
+  Lm.coef64 = W.mu;
+  Lm.coef32 = nullptr;
+  Lm.mu64 = W.mu;
+  Lm.winv64 = nullptr;
+  Lm.winv32 = nullptr;
+  op_apply(Lm, PREC_F64, OP_VISC | OP_BT | OP_B | OP_RAW, 0.0, u, W.Ru, p, W.Rp, s);   // A(mu) u + B^T p, B u
+  vec_axpby(PREC_F64, c->nu, -1.0, W.F, 1.0, W.Ru, s);                                  // - F
+  bnd_mask(F.g, W.Ru, W.Ru, 0, s);                                                      // Dirichlet rows 0
+  vec_multidot(PREC_F64, c->nu, 1, W.Ru, c->nu, W.Ru, c->h2, c->partial, s);
+  vec_multidot(PREC_F64, c->np, 1, W.Rp, c->np, W.Rp, c->h2 + 1, c->partial, s);
+  if (cudaMemcpyAsync(c->host_res, c->h2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_check(c, "newton residual");
+  *norm = std::sqrt(c->host_res[0] + c->host_res[1]);
+  return ALS_OK;
+}
+
+// one FGMRES solve of the linearised system for the step (du, dp), to relative tolerance rtol
+static als_status newton_step_solve(als_ctx* c, double rtol, int* its) {
+  als_ctx::NewtonBuf& W = c->nw;
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  double* rhs_u = c->V;
+  double* rhs_p = c->V + c->nu;
+  // r2 = -R_p; rhs_u = -R_u + B^T gamma W^-1 r2 with Dirichlet rows 0
+  vec_axpby(PREC_F64, c->np, -1.0, W.Rp, 0.0, rhs_p, s);
+  winv_scale(F.g, c->gamma, rhs_p, c->tp2, s, F.winv64);
+  op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);
+  vec_axpby(PREC_F64, c->nu, -1.0, W.Ru, 1.0, c->tu2, s);
+  bnd_mask(F.g, c->tu2, rhs_u, 0, s);
+  als_ctx::SolveRun& R = c->run;
+  R = als_ctx::SolveRun{};
+  R.u = W.du;
+  R.p = W.dp;
+  cudaEventCreate(&R.e0);
+  cudaEventCreate(&R.e1);
+  cudaEventRecord(R.e0, s);
+  cudaMemsetAsync(c->uD, 0, sizeof(double) * c->nu, s);
+  ALS_TRY(fgmres_begin(c));
+  const double saved = c->opt.rtol;
+  c->opt.rtol = rtol;
+  als_status st = ALS_OK;
+  if (cudaStreamSynchronize(s) != cudaSuccess) st = cuda_check(c, "newton step");
+  if (st == ALS_OK) st = solve_rhs_done(c);
+  while (st == ALS_OK && !c->run.done) {
+    st = solve_iter_launch(c);
+    if (st == ALS_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_check(c, "newton step");
+    if (st == ALS_OK) st = solve_iter_done(c);
+  }
+  if (st == ALS_OK) st = solve_finish(c, nullptr);
+  c->opt.rtol = saved;
+  *its = c->run.its;
+  return st;
+}
+
+extern "C" {
+
+void als_newton_default_params(als_newton_params* prm) {
+  if (!prm) return;
+  prm->mu_ref = 1.0;
+  prm->tau_y = 1.0;
+  prm->rtol = 1e-10;
+  prm->maxit = 30;
+  prm->max_halvings = 12;
+}
+
+als_status als_newton_solve(als_ctx* c, const als_newton_params* prm, const double* f_qp, const double* u_bc,
+                            double* u, double* p, als_newton_info* info) {
+  if (!c) return ALS_EINVAL;
+  if (!prm || !f_qp || !u || !p) return fail(c, ALS_EINVAL, "parameters, f_qp, u and p are required");
+  if (!c->lev[0].tensor || c->opt.schur != ALS_SCHUR_P2)
+    return fail(c, ALS_EINVAL, "Newton needs a context with tensor coefficients and the P2 pairing");
+  if (!(prm->mu_ref > 0.0) || !(prm->tau_y > 0.0) || !(prm->rtol > 0.0) || prm->maxit < 0 || prm->max_halvings < 0)
+    return fail(c, ALS_EINVAL, "mu_ref, tau_y and rtol must be positive, maxit and max_halvings >= 0");
+  ALS_TRY(alloc_solve(c, c->opt.maxit));
+  ALS_TRY(newton_alloc(c));
+  als_ctx::NewtonBuf& W = c->nw;
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  const int NB = c->dim == 2 ? 9 : 27;
+  begin(c);
+  // inputs: u = u_D on the boundary, 0 inside; p = 0; the load vector F
+  cudaMemcpyAsync(c->f_dev, f_qp, sizeof(double) * F.g.ncells * NB * c->dim, cudaMemcpyDefault, s);
+  if (u_bc) cudaMemcpyAsync(c->ubc_dev, u_bc, sizeof(double) * c->nu, cudaMemcpyDefault, s);
+  else cudaMemsetAsync(c->ubc_dev, 0, sizeof(double) * c->nu, s);
+  ALS_TRY(cuda_check(c, "newton inputs"));
+  bnd_mask(F.g, c->ubc_dev, W.u, 1, s);
+  cudaMemsetAsync(W.p, 0, sizeof(double) * c->np, s);
+  op_load_vector(F, c->f_dev, W.F, s);
+  double r = 0.0;
+  ALS_TRY(newton_residual(c, *prm, W.u, W.p, &r));
+  W.hist.assign(1, r);
+  W.lin.clear();
+  int lin_total = 0;
+  bool converged = r == 0.0;
+  for (int k = 0; k < prm->maxit && !converged; ++k) {
+    if (W.hist.back() <= prm->rtol * W.hist[0]) { converged = true; break; }
+    const double eta = std::min(1e-2, std::max(1e-12, 1e-12 * W.hist[0] / W.hist.back()));
+    // linearise at u: coefficients of every level, setup
+    for (int l = 0; l < c->L; ++l) newton_coeffs(F.g, c->lev[l].g, W.u, prm->mu_ref, prm->tau_y, W.C[l], W.mul[l], s);
+    std::vector<const double*> qp(W.C.begin(), W.C.end()), me(W.mul.begin(), W.mul.end());
+    const als_coeff cf{ALS_COEFF_TENSOR, qp.data(), me.data()};
+    ALS_TRY(run_setup(c, &cf));
+    ALS_TRY(newton_residual(c, *prm, W.u, W.p, &r));       // R at u (for the right-hand side)
+    int its = 0;
+    const als_status st = newton_step_solve(c, eta, &its);
+    if (st != ALS_OK && st != ALS_ENOTCONV) return st;
+    W.lin.push_back(its);
+    lin_total += its;
+    // backtracking: halve alpha until |R| < (1 - 1e-4 alpha) |R_k|
+    double alpha = 1.0, rt = 0.0;
+    for (int h = 0; h < prm->max_halvings; ++h) {
+      cudaMemcpyAsync(W.ut, W.u, sizeof(double) * c->nu, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(W.pt, W.p, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, s);
+      vec_axpby(PREC_F64, c->nu, alpha, W.du, 1.0, W.ut, s);
+      vec_axpby(PREC_F64, c->np, alpha, W.dp, 1.0, W.pt, s);
+      ALS_TRY(newton_residual(c, *prm, W.ut, W.pt, &rt));
+      if (rt < (1.0 - 1e-4 * alpha) * W.hist.back()) break;
+      alpha *= 0.5;
+    }
+    vec_axpby(PREC_F64, c->nu, alpha, W.du, 1.0, W.u, s);    // the step actually taken
+    vec_axpby(PREC_F64, c->np, alpha, W.dp, 1.0, W.p, s);
+    W.hist.push_back(rt);
+  }
+  if (!converged && W.hist.back() <= prm->rtol * W.hist[0]) converged = true;
+  cudaMemcpyAsync(u, W.u, sizeof(double) * c->nu, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(p, W.p, sizeof(double) * c->np, cudaMemcpyDefault, s);
+  ALS_TRY(finish(c, "newton"));
+  if (info) {
+    info->iterations = (int)W.hist.size() - 1;
+    info->linear_iterations = lin_total;
+    info->converged = converged ? 1 : 0;
+    info->res0 = W.hist[0];
+    info->res_final = W.hist.back();
+  }
+  if (!converged) return fail(c, ALS_ENOTCONV, "Newton did not reach rtol within maxit steps");
+  return ALS_OK;
+}
+
+als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, int cap, int* count) {
+  if (!c || !count || (cap > 0 && (!res || !linear_its))) return ALS_EINVAL;
+  const als_ctx::NewtonBuf& W = c->nw;
+  *count = (int)W.hist.size();
+  for (int i = 0; i < cap && i < (int)W.hist.size(); ++i) {
+    res[i] = W.hist[i];
+    linear_its[i] = i == 0 ? 0 : W.lin[i - 1];
+  }
+  return ALS_OK;
+}
+
+}  // extern "C"
 
 // ============================================================================
 // Batches of independent instances (uneven sizes, dimensions and parameters).

@@ -111,6 +111,12 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
 void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract,
                           cudaStream_t s);
 
+// ---- newton.cu
+// Coefficients of the Newton linearisation at the finest-level velocity u, at the Gauss
+// points of `level` ([cell][3^d] mu, and [cell][3^d][6|21] Mandel C unless C is NULL)
+void newton_coeffs(const Geom& fine, const Geom& level, const double* u, double mu_ref, double tau_y, double* C,
+                   double* mu, cudaStream_t s);
+
 // ---- transfer.cu
 // xf = P_H xc; if xadd, also xadd += P_H xc
 void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf,

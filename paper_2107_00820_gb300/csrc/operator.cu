@@ -652,6 +652,10 @@ static void dispatch_mode(const LevelDev& L, int mode, double gamma, const void*
             break;
           case OP_B | OP_RAW:
             launch_apply<T, DIM, TENSOR, OP_B | OP_RAW>(L, gamma, x, y, p_in, p_out, nvec, vstride, s); break;
+          case OP_VISC | OP_BT | OP_B | OP_RAW:   // the nonlinear residual's operators (Newton)
+            launch_apply<T, DIM, TENSOR, OP_VISC | OP_BT | OP_B | OP_RAW>(L, gamma, x, y, p_in, p_out, nvec, vstride,
+                                                                          s);
+            break;
           default: break;
         }
       }
