@@ -121,6 +121,11 @@ typedef struct {
                      FP64 in ALS_MODE_FP64 and double-float (FP32 pairs, about 48 bits) in
                      ALS_MODE_MIXED; ALS_SETUP_FP64 = FP64 in both modes (the mixed cycle then
                      runs on the FP32 roundings of FP64-computed inverses) */
+  int order;      /* polynomial order of the velocity: 2 (default, [Q2]^d x P1disc) or 3
+                     ([Q3]^2 x P2disc, the higher-order study of Sec. 5.2.2, Table k: 2D, scalar
+                     viscosity; nodes 3n+1 per direction, 4 x 4 Gauss points per cell (point
+                     data [cell][16]), pressure [cell][6] coefficients of {1, xi, eta, xi^2,
+                     xi eta, eta^2}, vertex stars of 5 x 5 nodes (50 dofs) inverted in FP64) */
 } als_options;
 
 typedef struct {

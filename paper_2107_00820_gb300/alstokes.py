@@ -42,7 +42,7 @@ class als_coeff(Structure):
 class als_options(Structure):
     _fields_ = [("smoother", c_int), ("sweeps", c_int), ("tau", c_double), ("transfer", c_int),
                 ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int),
-                ("cycle", c_int), ("fact", c_int), ("setup", c_int)]
+                ("cycle", c_int), ("fact", c_int), ("setup", c_int), ("order", c_int)]
 
 
 class als_newton_params(Structure):
@@ -207,12 +207,17 @@ class Context:
         f = 2 ** (self.levels - 1 - level)
         return tuple(v // f for v in self.n)
 
+    @property
+    def order(self):
+        return int(getattr(self, "options", None).order) if getattr(self, "options", None) is not None else 2
+
     def nu(self, level=None):
         nl = self.level_n(self.levels - 1 if level is None else level)
-        return self.dim * int(np.prod([2 * v + 1 for v in nl]))
+        return self.dim * int(np.prod([self.order * v + 1 for v in nl]))
 
     def npres(self):
-        return (self.dim + 1) * int(np.prod(self.n))
+        per_cell = 6 if self.order == 3 else self.dim + 1
+        return per_cell * int(np.prod(self.n))
 
     # calls -----------------------------------------------------------------
     def _call(self, name, *args):
@@ -252,7 +257,7 @@ class Context:
         self._call("als_apply_stokes", _ptr(u), _ptr(p), _ptr(yu), _ptr(yp))
 
     def patch_inverse(self, level, vertex):
-        np_ = self.dim * 3 ** self.dim
+        np_ = self.dim * (2 * self.order - 1) ** self.dim
         out = np.zeros((np_, np_))
         self._call("als_patch_inverse", level, int(vertex), _ptr(out))
         return out

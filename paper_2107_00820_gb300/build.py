@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libalstokes.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["operator.cu", "patches.cu", "transfer.cu", "krylov.cu", "coarse.cu", "api.cu", "noalloc.cu", "peaks.cu", "newton.cu"]
+SOURCES = ["operator.cu", "patches.cu", "transfer.cu", "krylov.cu", "coarse.cu", "api.cu", "noalloc.cu", "peaks.cu", "newton.cu", "qk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -63,7 +63,7 @@ def build(force=False, verbose=False, extra_flags=()):
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

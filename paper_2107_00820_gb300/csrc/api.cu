@@ -75,6 +75,9 @@ struct als_ctx {
   cudaStream_t user_stream = nullptr;  // caller's stream: work is ordered after it
   cudaEvent_t order_ev = nullptr;
   int dim = 0, L = 0;
+  int k = 2;             // polynomial order of the velocity (2, or 3: [Q3]^2 x P2disc)
+  int npr = 0;           // pressure unknowns per cell
+  int nq = 0;            // Gauss points per cell
   double gamma = 0.0;
   als_options opt{};
   std::vector<LevelDev> lev;
@@ -152,13 +155,13 @@ als_status dalloc(als_ctx* c, T** p, size_t count) {
     if (_s != ALS_OK) return _s;      \
   } while (0)
 
-Geom make_geom(int dim, const int n[3]) {
+Geom make_geom(int dim, const int n[3], int order = 2) {
   Geom g{};
   g.dim = dim;
   for (int k = 0; k < 3; ++k) {
     const bool act = k < dim;
     g.n[k] = act ? n[k] : 1;
-    g.nn[k] = act ? 2 * n[k] + 1 : 1;
+    g.nn[k] = act ? order * n[k] + 1 : 1;
     g.nv[k] = act ? n[k] + 1 : 1;
     g.h[k] = act ? 1.0 / n[k] : 0.0;
   }
@@ -271,7 +274,7 @@ static thread_local int t_prof_counter = 0;
 // Gram-Schmidt update carries the Givens step, and the final update also forms
 // the residual b - A x from the Arnoldi relation when `t` is given.
 bool fused_gmres(const als_ctx* c) {
-  return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB;
+  return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB && c->k == 2;
 }
 
 // FP32 3D cycles form Z_j inside the operator's cell kernel from the patch outputs
@@ -548,7 +551,7 @@ als_status alloc_solve(als_ctx* c, int maxit) {
   if (c->maxit_alloc > 0) return fail(c, ALS_EINVAL, "maxit larger than the first solve's is not supported");
   const LevelDev& F = c->lev[c->L - 1];
   c->nu = F.g.N * c->dim;
-  c->np = F.g.ncells * (c->dim + 1);
+  c->np = F.g.ncells * c->npr;
   c->n = c->nu + c->np;
   const int ldh = maxit + 1;
   ALS_TRY(dalloc(c, &c->V, (size_t)(maxit + 1) * c->n));
@@ -564,7 +567,7 @@ als_status alloc_solve(als_ctx* c, int maxit) {
   ALS_TRY(dalloc(c, &c->nrm2, 1));
   ALS_TRY(dalloc(c, &c->partial, multidot_partial_doubles(maxit + 1)));
   cudaMemsetAsync(c->partial, 0, sizeof(double) * multidot_partial_doubles(maxit + 1), c->stream);
-  ALS_TRY(dalloc(c, &c->f_dev, (size_t)F.g.ncells * (c->dim == 2 ? 9 : 27) * c->dim));
+  ALS_TRY(dalloc(c, &c->f_dev, (size_t)F.g.ncells * c->nq * c->dim));
   ALS_TRY(dalloc(c, &c->ubc_dev, c->nu));
   ALS_TRY(dalloc(c, &c->r2_dev, c->np));
   ALS_TRY(dalloc(c, &c->uD, c->nu));
@@ -602,7 +605,7 @@ als_status precondition(als_ctx* c, const double* v, double* z) {
   if (c->opt.fact != ALS_FACT_FULL) {
     // the factorisation types with one (1,1) application (oracle: StokesSolver.precondition)
     if (c->opt.fact == ALS_FACT_UPPER) {                        // [[A, B^T], [0, -S]]^-1
-      schur_apply(F.g.ncells, c->dim + 1, c->schur, gp, z2, s);                      // z2 = -S^-1 g
+      schur_apply(F.g.ncells, c->npr, c->schur, gp, z2, s);                      // z2 = -S^-1 g
       op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, z2, nullptr, s);         // tu2 = B^T z2
       vec_axpby(PREC_F64, c->nu, 1.0, f, -1.0, c->tu2, s);                             // tu2 = f - tu2
       ALS_TRY(apply_Ahat(c, c->tu2, x1));                                              // x1 = A^-1 tu2
@@ -611,12 +614,12 @@ als_status precondition(als_ctx* c, const double* v, double* z) {
       if (c->opt.fact == ALS_FACT_LOWER) {                      // [[A, 0], [B, -S]]^-1
         op_apply(F, PREC_F64, OP_B, c->gamma, x1, nullptr, nullptr, c->tp, s);        // tp = B x1
         vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                           // tp = g - B x1
-        schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                   // z2 = -S^-1 tp
+        schur_apply(F.g.ncells, c->npr, c->schur, c->tp, z2, s);                   // z2 = -S^-1 tp
       } else {                                                  // diag(A^-1, -S^-1)
-        schur_apply(F.g.ncells, c->dim + 1, c->schur, gp, z2, s);                      // z2 = -S^-1 g
+        schur_apply(F.g.ncells, c->npr, c->schur, gp, z2, s);                      // z2 = -S^-1 g
       }
     }
-    project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+    project_constant(F.g.ncells, c->npr, z2, c->partial, s);
     return ALS_OK;
   }
   if (c->opt.mode == ALS_MODE_MIXED) {
@@ -631,23 +634,23 @@ als_status precondition(als_ctx* c, const double* v, double* z) {
     op_apply(F, PREC_F32, OP_B, c->gamma, w.x[l], nullptr, nullptr, c->tp32, s);     // B z1 (FP32)
     vec_cast(c->np, c->tp32, PREC_F32, c->tp, PREC_F64, s);
     vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                             // tp = g - B z1
-    schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                     // z2 = -S^-1 tp
+    schur_apply(F.g.ncells, c->npr, c->schur, c->tp, z2, s);                     // z2 = -S^-1 tp
     vec_cast(c->np, z2, PREC_F64, c->tp32, PREC_F32, s);
     op_apply(F, PREC_F32, OP_BT, c->gamma, nullptr, w.b[l], c->tp32, nullptr, s);    // B^T z2 (FP32)
     ALS_TRY(run_vcycle(c, w));                                                       // A^-1 B^T z2 (FP32)
     vec_cast(c->nu, w.x[l], PREC_F32, x1, PREC_F64, s);
     vec_axpby(PREC_F64, c->nu, 1.0, c->tu, -1.0, x1, s);                             // x1 = z1 - x1
-    project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+    project_constant(F.g.ncells, c->npr, z2, c->partial, s);
     return ALS_OK;
   }
   ALS_TRY(apply_Ahat(c, f, c->tu));                                                  // z1 = A^-1 f
   op_apply(F, PREC_F64, OP_B, c->gamma, c->tu, nullptr, nullptr, c->tp, s);          // tp = B z1
   vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                               // tp = g - B z1
-  schur_apply(F.g.ncells, c->dim + 1, c->schur, c->tp, z2, s);                       // z2 = -S^-1 tp
+  schur_apply(F.g.ncells, c->npr, c->schur, c->tp, z2, s);                       // z2 = -S^-1 tp
   op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, z2, nullptr, s);           // tu2 = B^T z2
   ALS_TRY(apply_Ahat(c, c->tu2, x1));                                                // x1 = A^-1 B^T z2
   vec_axpby(PREC_F64, c->nu, 1.0, c->tu, -1.0, x1, s);                               // x1 = z1 - x1
-  project_constant(F.g.ncells, c->dim + 1, z2, c->partial, s);
+  project_constant(F.g.ncells, c->npr, z2, c->partial, s);
   return ALS_OK;
 }
 
@@ -676,6 +679,7 @@ void als_default_options(als_options* opt) {
   opt->cycle = ALS_CYCLE_V;
   opt->fact = ALS_FACT_FULL;
   opt->setup = ALS_SETUP_AUTO;
+  opt->order = 2;
 }
 
 // message of the calling thread's last failed als_create (the context is gone by then)
@@ -710,7 +714,7 @@ als_status als_destroy(als_ctx* ctx) {
 // P2 pairing (W = M_p(1/mu)) scales the AL term with mu and has no such limit.
 static als_status check_mixed_range(als_ctx* c) {
   if (c->opt.mode != ALS_MODE_MIXED || c->opt.schur != ALS_SCHUR_P1 || c->gamma == 0.0) return ALS_OK;
-  const int NB = c->dim == 2 ? 9 : 27;
+  const int NB = c->nq;
   const unsigned long long inf_bits = 0x7ff0000000000000ull;
   cudaMemcpyAsync(c->minbits, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, c->stream);
   for (int l = 0; l < c->L; ++l)
@@ -734,7 +738,7 @@ static als_status check_mixed_range(als_ctx* c) {
 }
 
 static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
-  const int NB = c->dim == 2 ? 9 : 27;
+  const int NB = c->nq;
   // FP64 or double-float arithmetic for the patch and coarse inverses
   const int df64 = c->opt.mode == ALS_MODE_MIXED && c->opt.setup != ALS_SETUP_FP64 ? 1 : 0;
   for (int l = 0; l < c->L; ++l) {
@@ -752,6 +756,20 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
     }
   }
   ALS_TRY(check_mixed_range(c));
+  if (c->k == 3) {
+    // order 3: per-cell W^-1 of every level (the AL term of the operator and the stars) and
+    // the finest level's Schur blocks, then the stars (FP64) and the coarse inverse
+    const int p2 = c->opt.schur == ALS_SCHUR_P2 ? 1 : 0;
+    for (int l = 0; l < c->L; ++l) {
+      LevelDev& Lv = c->lev[l];
+      qk_mass_setup(Lv, c->gamma, p2, p2, Lv.winv64, Lv.winv32, l == c->L - 1 ? c->schur : nullptr, c->st, c->stream);
+      if (l > 0) patch_setup(Lv, c->gamma, 1, 0, c->st, c->stream);
+      ALS_TRY(cuda_check(c, "order-3 setup"));
+    }
+    coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream, df64);
+    ALS_TRY(cuda_check(c, "coarse setup"));
+    return check_status(c, "setup");
+  }
   for (int l = 0; l < c->L; ++l) {
     LevelDev& Lv = c->lev[l];
     if (Lv.winv64) {
@@ -784,6 +802,11 @@ constexpr long long kSplitVertices = 32768;
 static als_status alloc_star_storage(als_ctx* c, LevelDev& Lv) {
   const Geom& g = Lv.g;
   const int d = c->dim;
+  if (c->k == 3) {   // order 3: one packed-by-diagonals FP32 copy of every star
+    Lv.split = 0;
+    Lv.nbnd = 0;
+    return dalloc(c, &Lv.inv32, (size_t)g.nverts * Lv.pstride);
+  }
   Lv.nint = 1;
   for (int k = 0; k < d; ++k) Lv.nint *= g.nv[k] - 2;
   static int forced = -2;   // ALS_SPLIT_STARS=1 / 0 forces split / full storage on every level
@@ -857,6 +880,12 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.mode != ALS_MODE_FP64 && c->opt.mode != ALS_MODE_MIXED) return fail(c, ALS_EINVAL, "unknown mode");
   if (c->opt.setup != ALS_SETUP_AUTO && c->opt.setup != ALS_SETUP_FP64)
     return fail(c, ALS_EINVAL, "unknown setup arithmetic");
+  if (c->opt.order != 2 && c->opt.order != 3) return fail(c, ALS_EINVAL, "order must be 2 or 3");
+  if (c->opt.order == 3 && (c->dim != 2 || coeff->kind != ALS_COEFF_SCALAR))
+    return fail(c, ALS_EINVAL, "order 3 is built for 2D meshes with scalar viscosity");
+  c->k = c->opt.order;
+  c->npr = c->k == 3 ? 6 : c->dim + 1;
+  c->nq = c->k == 3 ? 16 : (c->dim == 2 ? 9 : 27);
   const int f = 1 << (c->L - 1);
   for (int k = 0; k < c->dim; ++k) {
     if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
@@ -864,14 +893,14 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   }
   {
     long long nu = c->dim;   // vector kernels index velocity entries with 32 bits
-    for (int k = 0; k < c->dim; ++k) nu *= 2LL * mesh->n[k] + 1;
-    if (nu >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d (2n+1)^d must stay below 2^31");
-    long long ne = c->dim * (c->dim == 2 ? 9 : 27);   // per-cell output buffer, 32-bit offsets
+    for (int k = 0; k < c->dim; ++k) nu *= (long long)c->k * mesh->n[k] + 1;
+    if (nu >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d (k n+1)^d must stay below 2^31");
+    long long ne = (long long)c->dim * c->nq;   // per-cell output buffer, 32-bit offsets
     for (int k = 0; k < c->dim; ++k) ne *= mesh->n[k];
-    if (ne >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d 3^d n^d must stay below 2^31");
-    long long np = c->dim * (c->dim == 2 ? 9 : 27);   // vertex-star patch outputs, 32-bit offsets
-    for (int k = 0; k < c->dim; ++k) np *= mesh->n[k] + 1LL;
-    if (np >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d 3^d (n+1)^d must stay below 2^31");
+    if (ne >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d (k+1)^d n^d must stay below 2^31");
+    long long np = c->dim;   // vertex-star patch outputs, 32-bit offsets
+    for (int k = 0; k < c->dim; ++k) np *= (2LL * c->k - 1) * (mesh->n[k] + 1LL);
+    if (np >= (1LL << 31)) return fail(c, ALS_EINVAL, "mesh too large: d (2k-1)^d (n+1)^d must stay below 2^31");
   }
   const char* ng = getenv("ALS_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');
@@ -882,19 +911,25 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   ALS_TRY(dalloc(c, &c->st, 1));
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
   ALS_TRY(dalloc(c, &c->minbits, 1));
-  const int NB = c->dim == 2 ? 9 : 27;
+  const int NB = c->nq;
   const int NC = c->dim == 2 ? 6 : 21;
+  int nstar = c->dim;   // star dofs: d (2k-1)^d
+  for (int k = 0; k < c->dim; ++k) nstar *= 2 * c->k - 1;
+  if (c->k == 3) qk_tables();
   c->lev.resize(c->L);
   for (int l = 0; l < c->L; ++l) {
     int nl[3] = {1, 1, 1};
     for (int k = 0; k < c->dim; ++k) nl[k] = mesh->n[k] >> (c->L - 1 - l);
     LevelDev& Lv = c->lev[l];
     Lv = LevelDev{};
-    Lv.g = make_geom(c->dim, nl);
+    Lv.g = make_geom(c->dim, nl, c->k);
+    Lv.k = c->k;
+    Lv.npr = c->npr;
+    Lv.nq = c->nq;
     Lv.patch_kernel = -1;
     Lv.tensor = coeff->kind == ALS_COEFF_TENSOR;
     Lv.ncoef = Lv.tensor ? NC : 1;
-    Lv.np = c->dim * NB;
+    Lv.np = nstar;
     Lv.pstride = packed_stride(Lv.np);
     Lv.status = c->st;
     const size_t ncq = (size_t)Lv.g.ncells * NB * Lv.ncoef;
@@ -912,8 +947,8 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
       ALS_TRY(dalloc(c, &e, (size_t)Lv.g.ncells * NB * c->dim));
       Lv.ebuf = e;
     }
-    if (c->opt.schur == ALS_SCHUR_P2) {   // P2 pairs the augmentation weight W = M_p(1/mu)
-      const size_t nb2 = (size_t)Lv.g.ncells * (c->dim + 1) * (c->dim + 1);
+    if (c->opt.schur == ALS_SCHUR_P2 || c->k == 3) {   // P2: W = M_p(1/mu); order 3: per-cell W^-1 always
+      const size_t nb2 = (size_t)Lv.g.ncells * c->npr * c->npr;
       ALS_TRY(dalloc(c, &Lv.winv64, nb2));
       ALS_TRY(dalloc(c, &Lv.winv32, nb2));
     }
@@ -927,7 +962,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     return fail(c, ALS_ENOMEM, "coarse setup allocation failed");
   }
   const LevelDev& F = c->lev[c->L - 1];
-  ALS_TRY(dalloc(c, &c->schur, (size_t)F.g.ncells * (c->dim + 1) * (c->dim + 1)));
+  ALS_TRY(dalloc(c, &c->schur, (size_t)F.g.ncells * c->npr * c->npr));
   ALS_TRY(alloc_work(c, c->w64, PREC_F64));
   ALS_TRY(alloc_work(c, c->w32, PREC_F32));
   return run_setup(c, coeff);
@@ -1190,7 +1225,7 @@ static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc
   ALS_TRY(alloc_solve(c, maxit));
   const LevelDev& F = c->lev[c->L - 1];
   const cudaStream_t s = c->stream;
-  const int NB = c->dim == 2 ? 9 : 27;
+  const int NB = c->nq;
   begin(c);
   cudaEventCreate(&R.e0);
   cudaEventCreate(&R.e1);
@@ -1213,7 +1248,7 @@ static als_status solve_start(als_ctx* c, const double* f_qp, const double* u_bc
   op_apply(F, PREC_F64, OP_B | OP_RAW, c->gamma, c->uD, nullptr, nullptr, c->tp, s);   // B u_D
   vec_axpby(PREC_F64, c->np, 1.0, c->r2_dev, -1.0, c->tp, s);                          // r2 - B u_D
   cudaMemcpyAsync(rhs_p, c->tp, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, s);
-  winv_scale(F.g, c->gamma, c->r2_dev, c->tp2, s, F.winv64);                           // gamma W^-1 r2 (user part)
+  winv_scale(F.g, c->gamma, c->r2_dev, c->tp2, s, F.winv64, c->npr);                   // gamma W^-1 r2 (user part)
   op_apply(F, PREC_F64, OP_BT, c->gamma, nullptr, c->tu2, c->tp2, nullptr, s);         // B^T gamma W^-1 r2
   vec_axpby(PREC_F64, c->nu, 1.0, c->tu2, 1.0, c->tu, s);
   bnd_mask(F.g, c->tu, rhs_u, 0, s);                                                   // zero boundary rows
@@ -1281,7 +1316,7 @@ static als_status solve_finish(als_ctx* c, als_solve_info* info) {
     vec_multiaxpy(PREC_F64, c->n, R.its, c->Z, c->n, c->y, c->xsol, s, 1.0);
   }
   vec_axpby(PREC_F64, c->nu, 1.0, c->uD, 1.0, c->xsol, s);
-  project_constant(F.g.ncells, c->dim + 1, c->xsol + c->nu, c->partial, s);
+  project_constant(F.g.ncells, c->npr, c->xsol + c->nu, c->partial, s);
   cudaMemcpyAsync(R.u, c->xsol, sizeof(double) * c->nu, cudaMemcpyDefault, s);
   cudaMemcpyAsync(R.p, c->xsol + c->nu, sizeof(double) * c->np, cudaMemcpyDefault, s);
   cudaEventRecord(R.e1, s);

@@ -9,6 +9,7 @@
 // the pivot row/column set to U (A_KK to -S).  After every block the matrix holds
 // -A^-1.  A is SPD, so every pivot is a Schur complement and positive.  Each
 // V-cycle then applies the stored inverse as a dense matrix-vector product.
+#include "cell.cuh"
 #include "df64.cuh"
 #include "krylov.h"
 #include "level.h"
@@ -262,7 +263,13 @@ void coarse_setup(const LevelDev& L, double gamma, CoarseDev* C, DevStatus* st, 
   const long long len = g.N * g.dim;
   const long long tot = (long long)nfree * len;
   k_unit_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nfree, len, C->X);
-  op_apply_multi(L, gamma, C->X, C->Y, nfree, len, s);
+  if (L.k == 3) {   // the order-3 operator, one column at a time
+    for (int c = 0; c < nfree; ++c)
+      op_apply(L, PREC_F64, OP_VISC | OP_AL, gamma, C->X + (long long)c * len, C->Y + (long long)c * len, nullptr,
+               nullptr, s);
+  } else {
+    op_apply_multi(L, gamma, C->X, C->Y, nfree, len, s);
+  }
   count_launch(1);
   if (df64) coarse_sweep<DF64>(L, C, st, s);
   else coarse_sweep<double>(L, C, st, s);

@@ -647,9 +647,11 @@ __global__ void k_winv_block(long long ncells, int npr, double gamma, const doub
   }
 }
 
-void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cudaStream_t s, const double* winv) {
+void winv_scale(const Geom& g, double gamma, const double* r2, double* out, cudaStream_t s, const double* winv,
+                int npr) {
   if (winv) {
-    k_winv_block<<<(unsigned)((g.ncells + 255) / 256), 256, 0, s>>>(g.ncells, g.dim + 1, gamma, winv, r2, out);
+    k_winv_block<<<(unsigned)((g.ncells + 255) / 256), 256, 0, s>>>(g.ncells, npr > 0 ? npr : g.dim + 1, gamma, winv, r2,
+                                                                    out);
     count_launch(1);
     return;
   }

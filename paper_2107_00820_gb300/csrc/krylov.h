@@ -46,5 +46,5 @@ void schur_setup(const struct Geom& g, double gamma, const double* mu, double* S
                  int variant = 0, double* winv64 = nullptr, float* winv32 = nullptr);
 void bnd_mask(const struct Geom& g, const double* x, double* y, int keep_boundary, cudaStream_t s);
 void winv_scale(const struct Geom& g, double gamma, const double* r2, double* out, cudaStream_t s,
-                const double* winv = nullptr);
+                const double* winv = nullptr, int npr = 0);
 }  // namespace als

@@ -14,6 +14,9 @@ constexpr int kWaitPolls = 1 << 22;
 
 struct LevelDev {
   Geom g;
+  int k = 2;             // polynomial order of the velocity: 2 ([Q2]^d x P1disc) or 3 ([Q3]^2 x P2disc, qk.cu)
+  int npr = 0;           // pressure unknowns per cell (d + 1, or 6 at order 3)
+  int nq = 0;            // Gauss points per cell ((k + 1)^d)
   int tensor;            // 0: scalar mu per point, 1: Mandel tensor per point
   int ncoef;             // values per point (1 or NC)
   double* coef64;        // [cell][3^d][ncoef]
@@ -110,6 +113,25 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
 //                        mode 1: out -= sum_K E_K A_K^-1 E_K^T in
 void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract,
                           cudaStream_t s);
+
+// ---- qk.cu: the order-3 discretisation ([Q3]^2 x P2disc); the dispatchers of
+// operator.cu, patches.cu, transfer.cu and coarse.cu call these when L.k == 3
+void qk_tables();
+void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+              cudaStream_t s);
+void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
+// per-cell W^-1 (w_mu: W = M_p(1/mu), else M_p) into winv64/winv32 and, if S, the Schur blocks
+// of Eq. (P1P2) (variant 0: P1, 1: P2)
+void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
+                   DevStatus* st, cudaStream_t s);
+void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s);
+void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
+                     cudaStream_t s);
+void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s);
+void qk_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
+                void* xadd);
+void qk_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
+                 const void* sub);
 
 // ---- newton.cu
 // Coefficients of the Newton linearisation at the finest-level velocity u, at the Gauss

@@ -686,6 +686,10 @@ static void op_dispatch(const LevelDev& L, int prec, int mode, double gamma, con
 
 void op_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y,
               const void* p_in, void* p_out, cudaStream_t s) {
+  if (L.k == 3) {
+    qk_apply(L, prec, mode, gamma, x, y, p_in, p_out, s);
+    return;
+  }
   op_dispatch(L, prec, mode, gamma, x, y, p_in, p_out, 1, 0, s);
 }
 
@@ -785,6 +789,10 @@ __global__ void k_load(Geom g, Colour col, double wdet, const double* __restrict
 }
 
 void op_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
+  if (L.k == 3) {
+    qk_load_vector(L, f_qp, F, s);
+    return;
+  }
   const Geom& g = L.g;
   double wdet = 1.0;
   for (int k = 0; k < g.dim; ++k) wdet *= 0.5 * g.h[k];

@@ -796,6 +796,10 @@ static void patch_setup_arith(const LevelDev& L, double gamma, int store32, int 
 }
 
 void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s) {
+  if (L.k == 3) {   // FP64 assembly and inversion, FP64 and FP32 copies
+    qk_patch_setup(L, gamma, st, s);
+    return;
+  }
   // shared-memory limit of the FP32 patch kernel, set here, before any graph capture
   if (L.g.dim == 2) set_tma_smem<2>(); else set_tma_smem<3>();
   if (L.g.dim == 2) {
@@ -860,6 +864,10 @@ __global__ void __launch_bounds__(256) k_derive32_bnd(Geom g, int pstride, const
 }
 
 void patch_derive32(const LevelDev& L, cudaStream_t s) {
+  if (L.k == 3) {   // the same packed-by-diagonals layout in both precisions
+    vec_cast(L.g.nverts * L.pstride, L.inv64, PREC_F64, L.inv32, PREC_F32, s);
+    return;
+  }
   const long long nv32 = L.split ? L.nint : L.g.nverts;
   if (nv32 > 0) {
     if (L.g.dim == 3) k_derive32<3><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, L.inv32);
@@ -1047,6 +1055,12 @@ void patch_products(const LevelDev& L, const void* r, void* scratch, cudaStream_
 
 void patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, cudaStream_t s,
                   cudaEvent_t e0, cudaEvent_t e1, const void* den) {
+  if (L.k == 3) {
+    if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+    qk_patch_smooth(L, prec, r, z, scratch, den, s);
+    if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    return;
+  }
   if (prec == PREC_F64) {
     if (L.g.dim == 2) smooth_impl<double, double, 2>(L, L.inv64, r, z, scratch, s, e0, e1, den);
     else smooth_impl<double, double, 3>(L, L.inv64, r, z, scratch, s, e0, e1, den);
@@ -1107,6 +1121,10 @@ static void interior_impl(const LevelDev& L, const TF* inv, const void* in, void
 }
 
 void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s) {
+  if (fine.k == 3) {
+    qk_interior_solve(fine, prec, in, out, subtract, s);
+    return;
+  }
   if (prec == PREC_F64) {
     if (fine.g.dim == 2) interior_impl<double, double, 2>(fine, fine.inv64, in, out, subtract, s);
     else interior_impl<double, double, 3>(fine, fine.inv64, in, out, subtract, s);
@@ -1126,6 +1144,7 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
 // stream capture; waits for its own work.  Returns the chosen variant.
 int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, float* ms_out) {
   const long long launches0 = launch_count();
+  if (L.k == 3) { L.patch_kernel = 0; return 0; }   // one star kernel at order 3
   if (forced_patch_kernel() >= 0) { L.patch_kernel = forced_patch_kernel(); return L.patch_kernel; }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

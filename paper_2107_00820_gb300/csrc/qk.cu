@@ -1,0 +1,655 @@
+// The higher-order discretisation of the paper's Table k (Sec. 5.2.2): [Q3]^2 x P2^disc
+// on uniform quad meshes, FP64 and FP32, the whole hot path -- A_gamma / Stokes operator
+// applies, vertex-star patch setup and smoother, robust transfers, coarse images, mass and
+// Schur blocks -- so that the context's multigrid cycle and FGMRES run on it unchanged.
+//
+// Velocity: continuous Q3, nodal basis on the 4 equispaced nodes -1, -1/3, 1/3, 1 per
+// axis and cell, node lattice 3n + 1 per direction, x fastest.  Pressure: discontinuous
+// P2, the monomials xi^a eta^b (a + b <= 2) in reference coordinates, ordered by total
+// degree, xi before eta: {1, xi, eta, xi^2, xi eta, eta^2}; 6 per cell.  Quadrature:
+// 4 x 4 Gauss-Legendre points per cell.  Vertex stars: the free nodes at lattice offsets
+// -2..2 from 3v in each direction (5 x 5 nodes, 50 dofs at an interior vertex); the
+// interior of a coarse cell is the star of the fine vertex at its centre (Eq. (Ptilde)).
+// Deterministic: per-cell and per-star outputs are staged and summed per node in a
+// fixed order.
+#include <math.h>
+
+#include <type_traits>
+
+#include "cell.cuh"
+#include "krylov.h"
+#include "level.h"
+
+namespace als {
+namespace qk {
+
+constexpr int K = 3;           // polynomial order
+constexpr int N1 = K + 1;      // nodes (and Gauss points) per axis and cell
+constexpr int NB = N1 * N1;    // nodes per cell
+constexpr int NQ = NB;         // Gauss points per cell
+constexpr int NE = 2 * NB;     // velocity dofs per cell
+constexpr int NPR = 6;         // pressure monomials per cell
+constexpr int S1 = 2 * K - 1;  // star nodes per axis
+constexpr int NS = 2 * S1 * S1;   // star dofs (50)
+
+// 1D tables at the Gauss points: L[q][a] = l_a(g_q), D[q][a] = l_a'(g_q), W[q]; the 2D
+// pressure monomials at the points PSI[q][p]; the prolongation weights PW[f][a] = l_a(xi_f)
+// at xi_f = f / 3 - 1, f = 0..6 (the fine nodes of a coarse cell per axis)
+__constant__ double cL[N1][N1], cD[N1][N1], cW[N1], cPSI[NQ][NPR], cPW[2 * K + 1][N1];
+
+static void host_tables(double L[N1][N1], double D[N1][N1], double W[N1], double PSI[NQ][NPR],
+                        double PW[2 * K + 1][N1]) {
+  // 4-point Gauss-Legendre rule: +-sqrt(3/7 -+ 2/7 sqrt(6/5)), weights (18 +- sqrt(30)) / 36
+  const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+  const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+  const double g[N1] = {-b, -a, a, b};
+  const double w[N1] = {wb, wa, wa, wb};
+  const double t[N1] = {-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0};   // Lagrange nodes
+  auto lag = [&](int i, double x) {
+    double v = 1.0;
+    for (int j = 0; j < N1; ++j)
+      if (j != i) v *= (x - t[j]) / (t[i] - t[j]);
+    return v;
+  };
+  auto dlag = [&](int i, double x) {
+    double s = 0.0;
+    for (int m = 0; m < N1; ++m) {
+      if (m == i) continue;
+      double v = 1.0 / (t[i] - t[m]);
+      for (int j = 0; j < N1; ++j)
+        if (j != i && j != m) v *= (x - t[j]) / (t[i] - t[j]);
+      s += v;
+    }
+    return s;
+  };
+  for (int q = 0; q < N1; ++q) {
+    W[q] = w[q];
+    for (int i = 0; i < N1; ++i) {
+      L[q][i] = lag(i, g[q]);
+      D[q][i] = dlag(i, g[q]);
+    }
+  }
+  const int ex[NPR][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+  for (int q = 0; q < NQ; ++q) {
+    const double xi = g[q % N1], eta = g[q / N1];
+    for (int p = 0; p < NPR; ++p) PSI[q][p] = pow(xi, ex[p][0]) * pow(eta, ex[p][1]);
+  }
+  for (int f = 0; f <= 2 * K; ++f)
+    for (int i = 0; i < N1; ++i) PW[f][i] = lag(i, (double)f / K - 1.0);
+}
+
+// uploaded once per process (before any context of order 3 captures a cycle)
+void ensure_tables() {
+  static bool done = false;
+  if (done) return;
+  double L[N1][N1], D[N1][N1], W[N1], PSI[NQ][NPR], PW[2 * K + 1][N1];
+  host_tables(L, D, W, PSI, PW);
+  cudaMemcpyToSymbol(cL, L, sizeof(L));
+  cudaMemcpyToSymbol(cD, D, sizeof(D));
+  cudaMemcpyToSymbol(cW, W, sizeof(W));
+  cudaMemcpyToSymbol(cPSI, PSI, sizeof(PSI));
+  cudaMemcpyToSymbol(cPW, PW, sizeof(PW));
+  done = true;
+}
+
+// derivative of node basis a at point q along axis j, physical (2 / h_j scaling)
+__device__ __forceinline__ double dphi(int q, int a, int j, double sx, double sy) {
+  const int qx = q % N1, qy = q / N1, ax = a % N1, ay = a / N1;
+  return j == 0 ? cD[qx][ax] * cL[qy][ay] * sx : cL[qx][ax] * cD[qy][ay] * sy;
+}
+__device__ __forceinline__ double phi(int q, int a) { return cL[q % N1][a % N1] * cL[q / N1][a / N1]; }
+
+// ---------------------------------------------------------------------------
+// operator apply: one warp per cell, lanes 0..15 = Gauss points, then = nodes
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T* __restrict__ x, const T* __restrict__ mu,
+                                                  const T* __restrict__ winv, const T* __restrict__ p_in,
+                                                  T* __restrict__ p_out, T* __restrict__ ebuf) {
+  constexpr bool RAW = (MODE & OP_RAW) != 0, VISC = (MODE & OP_VISC) != 0, AL = (MODE & OP_AL) != 0;
+  constexpr bool BT = (MODE & OP_BT) != 0, BO = (MODE & OP_B) != 0;
+  constexpr bool NEED_U = VISC || AL || BO, NEED_FLUX = VISC || AL || BT;
+  __shared__ T us[8][2][NB];
+  __shared__ T ss[8][NQ][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * 8 + w;
+  if (cell >= g.ncells) return;
+  const int cx = (int)(cell % g.n[0]), cy = (int)(cell / g.n[0]);
+  const double sx = 2.0 / g.h[0], sy = 2.0 / g.h[1], wdet = 0.25 * g.h[0] * g.h[1];
+  if (lane < NB) {
+    const int i = K * cx + lane % N1, j = K * cy + lane / N1;
+    const bool bnd = i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1;
+    const long long nd = (long long)i + (long long)g.nn[0] * j;
+    for (int c = 0; c < 2; ++c) us[w][c][lane] = (NEED_U && (RAW || !bnd)) ? x[c * g.N + nd] : T(0);
+  }
+  __syncwarp();
+  const int q = lane;
+  double G[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  if (NEED_U && q < NQ) {
+    for (int a = 0; a < NB; ++a) {
+      const double dx = dphi(q, a, 0, sx, sy), dy = dphi(q, a, 1, sx, sy);
+      for (int c = 0; c < 2; ++c) {
+        G[c][0] += (double)us[w][c][a] * dx;
+        G[c][1] += (double)us[w][c][a] * dy;
+      }
+    }
+  }
+  const double div = G[0][0] + G[1][1];
+  double P = 0.0;   // the pressure-like field at the point: gamma pi + p_in
+  if (AL || BO) {
+    double bu[NPR];   // (B u)_p = -sum_q w |J| psi_p div u
+    for (int p = 0; p < NPR; ++p) {
+      double v = q < NQ ? -cW[q % N1] * cW[q / N1] * wdet * cPSI[q][p] * div : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      bu[p] = v;
+    }
+    if (BO && lane == 0)
+      for (int p = 0; p < NPR; ++p) p_out[cell * NPR + p] = (T)bu[p];
+    if (AL && q < NQ) {
+      const T* Wc = winv + cell * NPR * NPR;
+      double pi = 0.0;
+      for (int p = 0; p < NPR; ++p) {
+        double sp = 0.0;
+        for (int r = 0; r < NPR; ++r) sp += (double)Wc[p * NPR + r] * bu[r];
+        pi += cPSI[q][p] * sp;
+      }
+      P += gamma * pi;
+    }
+  }
+  if (BT && q < NQ)
+    for (int p = 0; p < NPR; ++p) P += cPSI[q][p] * (double)p_in[cell * NPR + p];
+  if (!NEED_FLUX) return;
+  if (q < NQ) {
+    const double m = VISC ? (double)mu[cell * NQ + q] : 0.0;
+    const double e01 = 0.5 * (G[0][1] + G[1][0]);
+    const double wq = cW[q % N1] * cW[q / N1] * wdet;
+    ss[w][q][0] = (T)(wq * (2.0 * m * G[0][0] - P));
+    ss[w][q][1] = (T)(wq * (2.0 * m * e01));
+    ss[w][q][2] = (T)(wq * (2.0 * m * e01));
+    ss[w][q][3] = (T)(wq * (2.0 * m * G[1][1] - P));
+  }
+  __syncwarp();
+  if (lane < NB) {
+    const int a = lane;
+    double y0 = 0.0, y1 = 0.0;
+    for (int qq = 0; qq < NQ; ++qq) {
+      const double dx = dphi(qq, a, 0, sx, sy), dy = dphi(qq, a, 1, sx, sy);
+      y0 += (double)ss[w][qq][0] * dx + (double)ss[w][qq][1] * dy;
+      y1 += (double)ss[w][qq][2] * dx + (double)ss[w][qq][3] * dy;
+    }
+    ebuf[(cell * 2 + 0) * NB + a] = (T)y0;
+    ebuf[(cell * 2 + 1) * NB + a] = (T)y1;
+  }
+}
+
+// the cells (and local index) containing lattice index i along an axis of n cells
+__device__ __forceinline__ int cells_of(int i, int n, int (&c)[2], int (&a)[2]) {
+  int m = 0;
+  const int c0 = i / K, r = i - K * c0;
+  if (r == 0 && c0 > 0) { c[m] = c0 - 1; a[m] = K; ++m; }
+  if (c0 < n) { c[m] = c0; a[m] = r; ++m; }
+  return m;
+}
+
+// y(node) = sum of the staged cell outputs of the cells containing it, fixed order;
+// keep_bnd: y = x at Dirichlet nodes; raw: no Dirichlet treatment
+template <typename T>
+__global__ void k_qk_gather(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y, int keep_bnd,
+                            int raw) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.N) return;
+  const int comp = (int)(t / g.N);
+  const long long nd = t - comp * g.N;
+  const int i = (int)(nd % g.nn[0]), j = (int)(nd / g.nn[0]);
+  const bool bnd = i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1;
+  if (bnd && !raw) {
+    y[t] = keep_bnd ? x[t] : T(0);
+    return;
+  }
+  int cxs[2], axs[2], cys[2], ays[2];
+  const int mx = cells_of(i, g.n[0], cxs, axs), my = cells_of(j, g.n[1], cys, ays);
+  T acc = T(0);
+  for (int b = 0; b < my; ++b)
+    for (int a = 0; a < mx; ++a) {
+      const long long cell = (long long)cxs[a] + (long long)g.n[0] * cys[b];
+      acc += ebuf[(cell * 2 + comp) * NB + axs[a] + N1 * ays[b]];
+    }
+  y[t] = acc;
+}
+
+template <typename T, int MODE>
+static void apply_mode(const LevelDev& L, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+                       cudaStream_t s) {
+  constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
+  const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
+  const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
+  k_qk_cells<T, MODE><<<(unsigned)((L.g.ncells + 7) / 8), 256, 0, s>>>(L.g, gamma, (const T*)x, mu, winv,
+                                                                      (const T*)p_in, (T*)p_out, (T*)L.ebuf);
+  if (NEED_FLUX) {
+    const int keep = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
+    k_qk_gather<T><<<(unsigned)((2 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const T*)L.ebuf, (const T*)x, (T*)y,
+                                                                        keep, (MODE & OP_RAW) ? 1 : 0);
+  }
+  count_launch(NEED_FLUX ? 2 : 1);
+}
+
+template <typename T>
+static void apply_t(const LevelDev& L, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+                    cudaStream_t s) {
+  switch (mode) {
+    case OP_VISC | OP_AL: apply_mode<T, OP_VISC | OP_AL>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_AL: apply_mode<T, OP_AL>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_B: apply_mode<T, OP_B>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_BT: apply_mode<T, OP_BT>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_VISC | OP_AL | OP_BT | OP_B: apply_mode<T, OP_VISC | OP_AL | OP_BT | OP_B>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_VISC | OP_AL | OP_RAW: apply_mode<T, OP_VISC | OP_AL | OP_RAW>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_B | OP_RAW: apply_mode<T, OP_B | OP_RAW>(L, gamma, x, y, p_in, p_out, s); break;
+    default: break;
+  }
+}
+
+// F_(c,a) = sum_q |J| w_q f_c(x_q) phi_a(x_q), staged per cell, summed per node
+__global__ void k_qk_load(Geom g, const double* __restrict__ f, double* __restrict__ ebuf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.ncells * NE) return;
+  const long long cell = t / NE;
+  const int e = (int)(t % NE), comp = e / NB, a = e % NB;
+  const double wdet = 0.25 * g.h[0] * g.h[1];
+  double acc = 0.0;
+  for (int q = 0; q < NQ; ++q) acc += cW[q % N1] * cW[q / N1] * wdet * f[(cell * NQ + q) * 2 + comp] * phi(q, a);
+  ebuf[(cell * 2 + comp) * NB + a] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// per-cell mass blocks: M_K(1/mu)^-1 and M_K^-1 (6 x 6, Gauss-Jordan), the augmentation
+// weight's inverse W^-1 (W = M_p or M_p(1/mu)) and the Schur blocks S of Eq. (P1P2):
+// P1: M_K(1/mu)^-1 + gamma M_K^-1, P2: (1 + gamma) M_K(1/mu)^-1.  One thread per cell.
+// ---------------------------------------------------------------------------
+__device__ void inv6(double (&A)[NPR][NPR], DevStatus* st, long long where) {
+  double Iv[NPR][NPR];
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j < NPR; ++j) Iv[i][j] = i == j ? 1.0 : 0.0;
+  for (int k = 0; k < NPR; ++k) {
+    const double pv = A[k][k];
+    if (!(pv > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, where); return; }
+    const double ip = 1.0 / pv;
+    for (int j = 0; j < NPR; ++j) { A[k][j] *= ip; Iv[k][j] *= ip; }
+    for (int i = 0; i < NPR; ++i) {
+      if (i == k) continue;
+      const double f = A[i][k];
+      for (int j = 0; j < NPR; ++j) { A[i][j] -= f * A[k][j]; Iv[i][j] -= f * Iv[k][j]; }
+    }
+  }
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j < NPR; ++j) A[i][j] = Iv[i][j];
+}
+
+__global__ void k_qk_mass(Geom g, double gamma, const double* __restrict__ mu, int w_mu, int variant,
+                          double* __restrict__ winv64, float* __restrict__ winv32, double* __restrict__ S, DevStatus* st) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncells) return;
+  const double wdet = 0.25 * g.h[0] * g.h[1];
+  double Mm[NPR][NPR], M[NPR][NPR];
+  for (int p = 0; p < NPR; ++p)
+    for (int r = 0; r < NPR; ++r) { Mm[p][r] = 0.0; M[p][r] = 0.0; }
+  for (int q = 0; q < NQ; ++q) {
+    const double wq = cW[q % N1] * cW[q / N1] * wdet;
+    const double im = 1.0 / mu[cell * NQ + q];
+    for (int p = 0; p < NPR; ++p)
+      for (int r = 0; r < NPR; ++r) {
+        M[p][r] += wq * cPSI[q][p] * cPSI[q][r];
+        Mm[p][r] += wq * im * cPSI[q][p] * cPSI[q][r];
+      }
+  }
+  inv6(Mm, st, cell);
+  inv6(M, st, cell);
+  for (int p = 0; p < NPR; ++p)
+    for (int r = 0; r < NPR; ++r) {
+      const double wv = w_mu ? Mm[p][r] : M[p][r];
+      if (winv64) winv64[cell * NPR * NPR + p * NPR + r] = wv;
+      if (winv32) winv32[cell * NPR * NPR + p * NPR + r] = (float)wv;
+      if (S) S[cell * NPR * NPR + p * NPR + r] = variant == 0 ? Mm[p][r] + gamma * M[p][r] : (1.0 + gamma) * Mm[p][r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vertex stars: setup (assembly from the star's cells, Gauss-Jordan inversion in shared
+// memory, FP64 packed-by-diagonals and its FP32 rounding), products, node gather
+// ---------------------------------------------------------------------------
+// star entry e = comp * 25 + (ox + 2) + 5 (oy + 2) of vertex v: node (3 vx + ox, 3 vy + oy)
+__device__ __forceinline__ bool star_node(const Geom& g, int vx, int vy, int e, long long& nd) {
+  const int o = e % (S1 * S1), ox = o % S1 - (K - 1), oy = o / S1 - (K - 1);
+  const int i = K * vx + ox, j = K * vy + oy;
+  if (i <= 0 || i >= g.nn[0] - 1 || j <= 0 || j >= g.nn[1] - 1) return false;
+  nd = (long long)i + (long long)g.nn[0] * j;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, const double* __restrict__ mu,
+                                                       const double* __restrict__ winv, double* __restrict__ inv64,
+                                                       float* __restrict__ inv32, int pstride, DevStatus* st) {
+  __shared__ double M[NS][NS + 1];
+  __shared__ double Ae[NE][NE + 1];
+  __shared__ double Bm[NPR][NE], WB[NPR][NE];
+  __shared__ double rowk[NS], colk[NS];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long v = blockIdx.x;
+  const int vx = (int)(v % (g.n[0] + 1)), vy = (int)(v / (g.n[0] + 1));
+  const double sx = 2.0 / g.h[0], sy = 2.0 / g.h[1], wdet = 0.25 * g.h[0] * g.h[1];
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < NS * NS; e += nt) M[e / NS][e % NS] = 0.0;
+  // B_K (the same on every cell): B[p][(c, a)] = -sum_q w |J| psi_p d_c phi_a
+  for (int e = tid; e < NPR * NE; e += nt) {
+    const int p = e / NE, c = (e % NE) / NB, a = e % NB;
+    double acc = 0.0;
+    for (int q = 0; q < NQ; ++q) acc -= cW[q % N1] * cW[q / N1] * wdet * cPSI[q][p] * dphi(q, a, c, sx, sy);
+    Bm[p][e % NE] = acc;
+  }
+  __syncthreads();
+  for (int cy = vy - 1; cy <= vy; ++cy)
+    for (int cx = vx - 1; cx <= vx; ++cx) {
+      if (cx < 0 || cy < 0 || cx >= g.n[0] || cy >= g.n[1]) continue;
+      const long long cell = (long long)cx + (long long)g.n[0] * cy;
+      const double* Wc = winv + cell * NPR * NPR;
+      for (int e = tid; e < NPR * NE; e += nt) {   // W^-1 B
+        const int p = e / NE, j = e % NE;
+        double acc = 0.0;
+        for (int r = 0; r < NPR; ++r) acc += Wc[p * NPR + r] * Bm[r][j];
+        WB[p][j] = acc;
+      }
+      __syncthreads();
+      // element A_gamma: 2 mu eps(phi_i) : eps(phi_j) + gamma B^T W^-1 B
+      for (int e = tid; e < NE * NE; e += nt) {
+        const int i = e / NE, j = e % NE, ci = i / NB, ai = i % NB, cj = j / NB, aj = j % NB;
+        double acc = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+          const double wq = cW[q % N1] * cW[q / N1] * wdet * 2.0 * mu[cell * NQ + q];
+          const double gi0 = dphi(q, ai, 0, sx, sy), gi1 = dphi(q, ai, 1, sx, sy);
+          const double gj0 = dphi(q, aj, 0, sx, sy), gj1 = dphi(q, aj, 1, sx, sy);
+          // eps(phi_i e_ci) : eps(phi_j e_cj) = (delta gi.gj + d_cj phi_i d_ci phi_j) / 2
+          const double dot = (ci == cj ? gi0 * gj0 + gi1 * gj1 : 0.0) + (cj == 0 ? gi0 : gi1) * (ci == 0 ? gj0 : gj1);
+          acc += wq * 0.5 * dot;
+        }
+        double al = 0.0;
+        for (int p = 0; p < NPR; ++p) al += Bm[p][i] * WB[p][j];
+        Ae[i][j] = acc + gamma * al;
+      }
+      __syncthreads();
+      // scatter into the star matrix: element node (3cx + ax, 3cy + ay) at offset (.. - 3v)
+      for (int e = tid; e < NE * NE; e += nt) {
+        const int i = e / NE, j = e % NE, ci = i / NB, ai = i % NB, cj = j / NB, aj = j % NB;
+        const int oxi = K * cx + ai % N1 - K * vx, oyi = K * cy + ai / N1 - K * vy;
+        const int oxj = K * cx + aj % N1 - K * vx, oyj = K * cy + aj / N1 - K * vy;
+        if (oxi < -(K - 1) || oxi > K - 1 || oyi < -(K - 1) || oyi > K - 1) continue;
+        if (oxj < -(K - 1) || oxj > K - 1 || oyj < -(K - 1) || oyj > K - 1) continue;
+        const int si = ci * S1 * S1 + (oxi + K - 1) + S1 * (oyi + K - 1);
+        const int sj = cj * S1 * S1 + (oxj + K - 1) + S1 * (oyj + K - 1);
+        M[si][sj] += Ae[i][j];
+      }
+      __syncthreads();
+    }
+  // identity rows and columns at absent and Dirichlet nodes
+  for (int e = tid; e < NS * NS; e += nt) {
+    const int i = e / NS, j = e % NS;
+    long long nd;
+    const bool fi = star_node(g, vx, vy, i % (S1 * S1), nd), fj = star_node(g, vx, vy, j % (S1 * S1), nd);
+    if (!fi || !fj) M[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan inversion (SPD: pivots are the Schur complements, no pivoting)
+  for (int k = 0; k < NS; ++k) {
+    const double pv = M[k][k];
+    if (!(pv > 0.0)) {
+      if (tid == 0 && !s_bad) { report(st, 4 /* ALS_ENOTSPD */, v); s_bad = 1; }
+    }
+    const double ip = pv > 0.0 ? 1.0 / pv : 1.0;
+    if (tid < NS) {
+      rowk[tid] = M[k][tid] * ip;
+      colk[tid] = M[tid][k];
+    }
+    __syncthreads();
+    for (int e = tid; e < NS * NS; e += nt) {
+      const int i = e / NS, j = e % NS;
+      if (i == k && j == k) M[i][j] = ip;
+      else if (i == k) M[i][j] = rowk[j];
+      else if (j == k) M[i][j] = -colk[i] * ip;
+      else M[i][j] -= colk[i] * rowk[j];
+    }
+    __syncthreads();
+  }
+  // upper triangle by diagonals (entry (i, i+t)), symmetrised
+  for (int t = 0; t < NS; ++t) {
+    const int base = diag_start(NS, t);
+    for (int i = tid; i + t < NS; i += nt) {
+      const double val = 0.5 * (M[i][i + t] + M[i + t][i]);
+      inv64[v * pstride + base + i] = val;
+      inv32[v * pstride + base + i] = (float)val;
+    }
+  }
+}
+
+// y_v = A_v^-1 r|_v: one warp per star (vertex), entries by lanes, diagonals in order;
+// interior: the stars of the fine vertices 2K+1 at the coarse-cell centres, written (mode 1)
+// or subtracted (mode 2) straight into the nodes; else into the scratch rows [vertex][50]
+template <typename T>
+__global__ void __launch_bounds__(256) k_qk_star_apply(Geom g, const T* __restrict__ inv, int pstride, int interior,
+                                                       int mode, const T* __restrict__ r, T* __restrict__ out) {
+  constexpr int R = (NS + 31) / 32;
+  __shared__ T rs[8][NS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long count = interior ? (long long)(g.n[0] / 2) * (g.n[1] / 2) : (long long)(g.n[0] + 1) * (g.n[1] + 1);
+  const long long item = (long long)blockIdx.x * 8 + w;
+  if (item >= count) return;
+  int vx, vy;
+  if (interior) { vx = 2 * (int)(item % (g.n[0] / 2)) + 1; vy = 2 * (int)(item / (g.n[0] / 2)) + 1; }
+  else { vx = (int)(item % (g.n[0] + 1)); vy = (int)(item / (g.n[0] + 1)); }
+  const long long v = (long long)vx + (long long)(g.n[0] + 1) * vy;
+  for (int e = lane; e < NS; e += 32) {
+    long long nd;
+    rs[w][e] = star_node(g, vx, vy, e, nd) ? r[(e / (S1 * S1)) * g.N + nd] : T(0);
+  }
+  __syncwarp();
+  T acc[R];
+  for (int k = 0; k < R; ++k) acc[k] = T(0);
+  const T* S = inv + v * pstride;
+  for (int t = 0; t < NS; ++t) {
+    const T* d = S + diag_start(NS, t);
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < NS) {
+        if (i + t < NS) acc[k] += d[i] * rs[w][i + t];
+        if (t > 0 && i >= t) acc[k] += d[i - t] * rs[w][i - t];
+      }
+    }
+  }
+  for (int k = 0; k < R; ++k) {
+    const int i = lane + 32 * k;
+    if (i >= NS) continue;
+    if (!interior) {
+      out[v * NS + i] = acc[k];
+    } else {
+      long long nd;
+      if (star_node(g, vx, vy, i, nd)) {
+        T* o = out + (i / (S1 * S1)) * g.N + nd;
+        *o = mode == 2 ? *o - acc[k] : acc[k];
+      }
+    }
+  }
+}
+
+// z(node) = sum over the stars containing the node (vertices v with |i - 3v| <= 2 per
+// axis), fixed order; 0 at Dirichlet nodes; divided by den[0] when den is given
+template <typename T>
+__global__ void k_qk_star_gather(Geom g, const T* __restrict__ sc, T* __restrict__ z, const T* __restrict__ den) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.N) return;
+  const int comp = (int)(t / g.N);
+  const long long nd = t - comp * g.N;
+  const int i = (int)(nd % g.nn[0]), j = (int)(nd / g.nn[0]);
+  if (i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1) { z[t] = T(0); return; }
+  int vxs[2], oxs[2], vys[2], oys[2], mx = 0, my = 0;
+  { const int v0 = i / K, r = i - K * v0; vxs[mx] = v0; oxs[mx++] = r; if (r != 0) { vxs[mx] = v0 + 1; oxs[mx++] = r - K; } }
+  { const int v0 = j / K, r = j - K * v0; vys[my] = v0; oys[my++] = r; if (r != 0) { vys[my] = v0 + 1; oys[my++] = r - K; } }
+  T acc = T(0);
+  for (int b = 0; b < my; ++b)
+    for (int a = 0; a < mx; ++a) {
+      const long long v = (long long)vxs[a] + (long long)(g.n[0] + 1) * vys[b];
+      const int e = comp * S1 * S1 + (oxs[a] + K - 1) + S1 * (oys[b] + K - 1);
+      acc += sc[v * NS + e];
+    }
+  if (den) acc = den[0] != T(0) ? acc / den[0] : T(0);
+  z[t] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// transfers: P_H (coarse Q3 basis at the fine nodes, tensor product of 1D weights; each fine
+// node belongs to the coarse cell min(f div 6, nc - 1)) and its transpose, as gathers;
+// fine Dirichlet rows and coarse Dirichlet columns are zero
+// ---------------------------------------------------------------------------
+// coarse cell of fine lattice index f and its row of 1D weights
+__device__ __forceinline__ int owner(int f, int nc, int& fr) {
+  int c = f / (2 * K);
+  if (c > nc - 1) c = nc - 1;
+  fr = f - 2 * K * c;
+  return c;
+}
+
+template <typename T>
+__global__ void k_qk_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * gf.N) return;
+  const int comp = (int)(t / gf.N);
+  const long long nd = t - comp * gf.N;
+  const int i = (int)(nd % gf.nn[0]), j = (int)(nd / gf.nn[0]);
+  T v = T(0);
+  if (!(i == 0 || i == gf.nn[0] - 1 || j == 0 || j == gf.nn[1] - 1)) {
+    int fx, fy;
+    const int cx = owner(i, gc.n[0], fx), cy = owner(j, gc.n[1], fy);
+    double acc = 0.0;
+    for (int b = 0; b < N1; ++b)
+      for (int a = 0; a < N1; ++a) {
+        const int I = K * cx + a, J = K * cy + b;
+        if (I == 0 || I == gc.nn[0] - 1 || J == 0 || J == gc.nn[1] - 1) continue;
+        acc += cPW[fx][a] * cPW[fy][b] * (double)xc[comp * gc.N + I + (long long)gc.nn[0] * J];
+      }
+    v = (T)acc;
+  }
+  xf[t] = v;
+  if (xadd) xadd[t] += v;
+}
+
+// rc = P_H^T (rf - sub): coarse node J gathers the fine nodes owned by the coarse cells that
+// contain it, weighted by its basis function there
+template <typename T>
+__global__ void k_qk_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub, T* __restrict__ rc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * gc.N) return;
+  const int comp = (int)(t / gc.N);
+  const long long nd = t - comp * gc.N;
+  const int I = (int)(nd % gc.nn[0]), J = (int)(nd / gc.nn[0]);
+  if (I == 0 || I == gc.nn[0] - 1 || J == 0 || J == gc.nn[1] - 1) { rc[t] = T(0); return; }
+  int cxs[2], axs[2], cys[2], ays[2];
+  const int mx = cells_of(I, gc.n[0], cxs, axs), my = cells_of(J, gc.n[1], cys, ays);
+  double acc = 0.0;
+  for (int b = 0; b < my; ++b)
+    for (int a = 0; a < mx; ++a)
+      for (int fy = 0; fy <= 2 * K; ++fy) {
+        const int j = 2 * K * cys[b] + fy;
+        if (fy == 2 * K && cys[b] != gc.n[1] - 1) continue;   // owned by the next coarse cell
+        if (j == 0 || j == gf.nn[1] - 1) continue;
+        const double wy = cPW[fy][ays[b]];
+        if (wy == 0.0) continue;
+        for (int fx = 0; fx <= 2 * K; ++fx) {
+          const int i = 2 * K * cxs[a] + fx;
+          if (fx == 2 * K && cxs[a] != gc.n[0] - 1) continue;
+          if (i == 0 || i == gf.nn[0] - 1) continue;
+          const double wx = cPW[fx][axs[a]];
+          if (wx == 0.0) continue;
+          const long long fn = comp * gf.N + i + (long long)gf.nn[0] * j;
+          acc += wx * wy * (double)(sub ? rf[fn] - sub[fn] : rf[fn]);
+        }
+      }
+  rc[t] = (T)acc;
+}
+
+}  // namespace qk
+
+// ---------------------------------------------------------------------------
+// entry points used by the dispatchers of operator.cu, patches.cu, transfer.cu, coarse.cu
+// ---------------------------------------------------------------------------
+void qk_tables() { qk::ensure_tables(); }
+
+void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+              cudaStream_t s) {
+  if (prec == PREC_F64) qk::apply_t<double>(L, mode, gamma, x, y, p_in, p_out, s);
+  else qk::apply_t<float>(L, mode, gamma, x, y, p_in, p_out, s);
+}
+
+void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
+  const long long tot = L.g.ncells * qk::NE;
+  qk::k_qk_load<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, f_qp, (double*)L.ebuf);
+  qk::k_qk_gather<double><<<(unsigned)((2 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const double*)L.ebuf, nullptr, F,
+                                                                             0, 1);
+  count_launch(2);
+}
+
+void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
+                   DevStatus* st, cudaStream_t s) {
+  qk::k_qk_mass<<<(unsigned)((L.g.ncells + 127) / 128), 128, 0, s>>>(L.g, gamma, L.mu64, w_mu, variant, winv64, winv32,
+                                                                     S, st);
+  count_launch(1);
+}
+
+void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s) {
+  qk::k_qk_star_setup<<<(unsigned)L.g.nverts, 256, 0, s>>>(L.g, gamma, L.mu64, L.winv64, L.inv64, L.inv32, L.pstride,
+                                                           st);
+  count_launch(1);
+}
+
+void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
+                     cudaStream_t s) {
+  const unsigned b1 = (unsigned)((L.g.nverts + 7) / 8), b2 = (unsigned)((2 * L.g.N + 255) / 256);
+  if (prec == PREC_F64) {
+    qk::k_qk_star_apply<double><<<b1, 256, 0, s>>>(L.g, L.inv64, L.pstride, 0, 0, (const double*)r, (double*)scratch);
+    qk::k_qk_star_gather<double><<<b2, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
+  } else {
+    qk::k_qk_star_apply<float><<<b1, 256, 0, s>>>(L.g, L.inv32, L.pstride, 0, 0, (const float*)r, (float*)scratch);
+    qk::k_qk_star_gather<float><<<b2, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
+  }
+  count_launch(2);
+}
+
+void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s) {
+  const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2);
+  const size_t es = prec == PREC_F64 ? 8 : 4;
+  if (!subtract) cudaMemsetAsync(out, 0, es * 2 * fine.g.N, s);
+  const unsigned b = (unsigned)((nc + 7) / 8);
+  if (prec == PREC_F64)
+    qk::k_qk_star_apply<double><<<b, 256, 0, s>>>(fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1,
+                                                  (const double*)in, (double*)out);
+  else
+    qk::k_qk_star_apply<float><<<b, 256, 0, s>>>(fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1,
+                                                 (const float*)in, (float*)out);
+  count_launch(1);
+}
+
+void qk_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
+                void* xadd) {
+  const unsigned b = (unsigned)((2 * fine.g.N + 255) / 256);
+  if (prec == PREC_F64)
+    qk::k_qk_prolong<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
+  else qk::k_qk_prolong<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+  count_launch(1);
+}
+
+void qk_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
+                 const void* sub) {
+  const unsigned b = (unsigned)((2 * coarse.g.N + 255) / 256);
+  if (prec == PREC_F64)
+    qk::k_qk_restrict<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
+  else qk::k_qk_restrict<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
+  count_launch(1);
+}
+
+}  // namespace als

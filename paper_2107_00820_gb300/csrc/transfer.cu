@@ -129,6 +129,10 @@ __global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* 
 
 void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
                  void* xadd) {
+  if (fine.k == 3) {
+    qk_prolong(coarse, fine, prec, xc, xf, s, xadd);
+    return;
+  }
   const long long tot = fine.g.N * fine.g.dim;
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {
@@ -145,6 +149,10 @@ void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const v
 
 void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
                   const void* sub) {
+  if (fine.k == 3) {
+    qk_restrict(coarse, fine, prec, rf, rc, s, sub);
+    return;
+  }
   const long long tot = coarse.g.N * coarse.g.dim;
   const unsigned b = (unsigned)((tot + 255) / 256);
   if (prec == PREC_F64) {

@@ -73,6 +73,36 @@ def sample_points(d, n):
     return x
 
 
+def sample_points_k(d, n, k):
+    """Physical coordinates of the (k+1)^d Gauss-Legendre points of every cell (the
+    quadrature of the order-k discretisation), shape (ncells, (k+1)^d, d), cells and
+    points x fastest."""
+    n = _as_tuple(n, d)
+    g = np.polynomial.legendre.leggauss(k + 1)[0]
+    axes = [((np.arange(n[a])[:, None] + 0.5 * (1.0 + g[None, :])) / n[a]) for a in range(d)]
+    cells = np.stack(np.meshgrid(*[np.arange(v) for v in n], indexing="ij"), -1)
+    cells = cells.transpose(*reversed(range(d)), d).reshape(-1, d)
+    pts = np.stack(np.meshgrid(*[np.arange(k + 1)] * d, indexing="ij"), -1)
+    pts = pts.transpose(*reversed(range(d)), d).reshape(-1, d)
+    x = np.empty((cells.shape[0], pts.shape[0], d))
+    for a in range(d):
+        x[:, :, a] = axes[a][cells[:, a][:, None], pts[:, a][None, :]]
+    return x
+
+
+def sinker_problem_k(n, levels, k, count, omega, delta, dr, beta=10.0, gamma=1e2, seed=0):
+    """The 2D multi-sinker problem sampled at the order-k Gauss points of every level
+    (rediscretisation): mu per level [cell][(k+1)^2], f at the finest points, u_D = 0."""
+    c = sinker_centres(seed, count, 2)
+    sizes = [tuple(v // 2 ** (levels - 1 - l) for v in _as_tuple(n, 2)) for l in range(levels)]
+    mus = [sinker_viscosity(sample_points_k(2, nl, k), c, omega, delta, dr) for nl in sizes]
+    f = sinker_force(sample_points_k(2, n, k), c, omega, delta, beta)
+    nn = tuple(k * v + 1 for v in _as_tuple(n, 2))
+    u_bc = np.zeros((2, nn[0] * nn[1]))
+    return Problem(f"sinker2d_q{k}", 2, _as_tuple(n, 2), levels, gamma, mus, f, u_bc,
+                   {"centres": c, "order": k, "dr": dr})
+
+
 def node_points(d, n):
     """Coordinates of the Q2 node lattice, shape ((2n+1)^d, d), x fastest."""
     n = _as_tuple(n, d)
