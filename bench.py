@@ -49,6 +49,11 @@ WORKLOADS = {
     # eps32 gamma / mu_min stays below about 0.1, and mu_min = 1e-3 here (1e4 would give 0.6)
     "sinker2d_128": dict(d=2, n=128, levels=5, count=8, omega=0.1, delta=200.0, dr=1e6, beta=10.0,
                          gamma=1e2, seed=0, sweeps=5),
+    # 2D multi-sinker with the order-3 discretisation of Table k ([Q3]^2 x P2disc), 128^2 quads
+    # (394,754 velocity + pressure DoFs: the size of Table exacttopleft), 5 levels, 8 sinkers,
+    # DR 1e6, gamma 1e2, P1 pairing
+    "sinker2d_q3_128": dict(d=2, n=128, levels=5, count=8, omega=0.1, delta=200.0, dr=1e6, beta=10.0,
+                            gamma=1e2, seed=0, sweeps=5, order=3),
     # 3D anisotropic viscoplastic linearisation, 48^3 hexes, 4 levels (coarse 6^3): per-point
     # 4th-order tensor C (21 Mandel entries), mu_eff contrast ~1e10, gamma 1e3, P2 Schur pairing
     "viscoplastic3d_48": dict(kind="tensor", d=3, n=48, levels=4, gamma=1e3, seed=0, sweeps=5, schur="P2"),
@@ -58,6 +63,7 @@ SAMPLES = {
     "sinker3d_32": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
     "sinker2d_128": dict(cpu_baseline=dict(n=64, levels=4), reference=dict(n=32, levels=3)),
     "sinker3d_32_g1e4": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
+    "sinker2d_q3_128": dict(cpu_baseline=dict(n=32, levels=3), reference=dict(n=16, levels=3)),
     "viscoplastic3d_48": dict(cpu_baseline=dict(n=8, levels=2), reference=dict(n=8, levels=2)),
 }
 RTOL = 1e-8
@@ -67,7 +73,10 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 def make_problem(spec, n=None, levels=None):
-    from synthetic.problems import sinker_problem, viscoplastic_problem
+    from synthetic.problems import sinker_problem, sinker_problem_k, viscoplastic_problem
+    if spec.get("order", 2) == 3:
+        return sinker_problem_k(n or spec["n"], levels or spec["levels"], 3, spec["count"], spec["omega"],
+                                spec["delta"], spec["dr"], spec["beta"], spec["gamma"], spec["seed"])
     if spec.get("kind") == "tensor":
         return viscoplastic_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["gamma"], spec["seed"])
     return sinker_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["count"], spec["omega"],
@@ -76,8 +85,9 @@ def make_problem(spec, n=None, levels=None):
 
 def problem_dofs(pb):
     """Free velocity DoFs + pressure DoFs of the finest level."""
-    free_nodes = math.prod(2 * v - 1 for v in pb.n)
-    return pb.d * free_nodes + (pb.d + 1) * math.prod(pb.n)
+    k = pb.meta.get("order", 2)
+    free_nodes = math.prod(k * v - 1 for v in pb.n)
+    return pb.d * free_nodes + (6 if k == 3 else pb.d + 1) * math.prod(pb.n)
 
 
 # --------------------------------------------------------------------------
@@ -215,8 +225,12 @@ def oracle_sample_step(spec, n, levels):
     pb = make_problem(spec, n, levels)
     t0 = time.perf_counter()
     p2 = spec.get("schur") == "P2"
-    H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"], kind=spec.get("kind", "scalar"),
-                  mu_eff=pb.meta.get("mu_eff"), W="Mp_mu" if p2 else "Mp")
+    if spec.get("order", 2) == 3:
+        from oracle.qk import HierarchyK
+        H = HierarchyK(2, pb.n, 3, pb.mu, pb.gamma, steps=spec["sweeps"], W="Mp_mu" if p2 else "Mp")
+    else:
+        H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"], kind=spec.get("kind", "scalar"),
+                      mu_eff=pb.meta.get("mu_eff"), W="Mp_mu" if p2 else "Mp")
     u, p, its, _ = StokesSolver(H, schur="P2" if p2 else "P1").solve(pb.f, pb.u_bc, rtol=RTOL)
     dt = time.perf_counter() - t0
     return problem_dofs(pb), dt, its
@@ -335,13 +349,14 @@ def ours(args, dist):
     mue_d = [dev(m) for m in pb.meta["mu_eff"]] if tensor else None
     schur = A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1
     f_d, ubc_d = dev(pb.f), dev(pb.u_bc)
-    nu = pb.d * math.prod(2 * v + 1 for v in pb.n)
-    npres = (pb.d + 1) * math.prod(pb.n)
+    order = spec.get("order", 2)
+    nu = pb.d * math.prod(order * v + 1 for v in pb.n)
+    npres = (6 if order == 3 else pb.d + 1) * math.prod(pb.n)
     u_d = torch.zeros(nu, dtype=torch.float64, device="cuda")
     p_d = torch.zeros(npres, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     ctx = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_MIXED,
-                  rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur)
+                  rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, order=order)
 
     def step():
         ctx.update_coefficients(mu_d, mue_d)
@@ -420,7 +435,7 @@ def ours(args, dist):
 
     # all-FP64 GPU path on the same problem
     ctx64 = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_FP64,
-                    rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur)
+                    rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, order=order)
     u64 = torch.zeros_like(u_d)
     p64 = torch.zeros_like(p_d)
     ctx64.solve(f_d, ubc_d, None, u64, p64)
@@ -444,7 +459,7 @@ def ours(args, dist):
     # double-float (options.setup = ALS_SETUP_FP64): setup time, iterations, solution
     # difference from the double-float setup's solution
     setup_fp64 = None
-    if not args.quick:
+    if not args.quick and order == 2:
         ctxf = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_MIXED,
                        rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, setup=A.ALS_SETUP_FP64)
         uf, pf = torch.zeros_like(u_d), torch.zeros_like(p_d)
@@ -473,7 +488,7 @@ def ours(args, dist):
     # iterations, solution difference at rtol 1e-8, and the mixed solve run on to 1e-11
     # against the FP64 solve run to 1e-12 (the 1e-7 error bar)
     gamma_large = None
-    if not tensor and not args.quick:
+    if not tensor and not args.quick and order == 2:
         spec4 = dict(spec, gamma=1e4)
         pb4 = make_problem(spec4)
         mu4 = [dev(m) for m in pb4.mu]
@@ -533,8 +548,10 @@ def ours(args, dist):
     # interior vertex its packed FP32 inverse and its output row, plus r read once
     F = pb.n
     nverts = math.prod(v + 1 for v in F)
-    nint = math.prod(v - 1 for v in F)
-    npatch = pb.d * 3 ** pb.d
+    # split star storage on levels of >= 32768 vertices at order 2 (interior stars only in the
+    # interior-star kernel); order 3 streams every star's packed inverse in its one star kernel
+    nint = math.prod(v - 1 for v in F) if (order == 2 and nverts >= 32768) else nverts
+    npatch = pb.d * (2 * order - 1) ** pb.d
     packed = npatch * (npatch + 1) // 2
     bytes_per_launch = nint * (packed * 4 + npatch * 4) + nu * 4
     k4_launch_s = (k4_ms / max(k4_n, 1)) / 1e3
@@ -569,14 +586,14 @@ def ours(args, dist):
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "dim": pb.d, "cells": list(pb.n), "levels": pb.levels,
+        "config": {"workload": args.workload, "dim": pb.d, "cells": list(pb.n), "levels": pb.levels, "order": order,
                    "gamma": pb.gamma, "dr": spec.get("dr", pb.meta.get("contrast")),
                    "sinkers": spec.get("count"), "coefficients": "tensor C (21 per point)" if tensor else "scalar mu",
                    "schur": spec.get("schur", "P1"), "dofs": dofs,
                    "smoother": f"GMRES({spec['sweeps']}) x vertex-star PSC", "rtol": RTOL,
                    "step": "setup (patch factorisation, coarse Cholesky, Schur) + mixed FGMRES solve",
                    "l2": "inputs larger than L2 (fine-level FP32+FP64 patch inverses %.1f GB)"
-                         % (math.prod(v + 1 for v in pb.n) * 12 * (pb.d * 3 ** pb.d) * (pb.d * 3 ** pb.d + 1) / 2 / 1e9),
+                         % (math.prod(v + 1 for v in pb.n) * 12 * npatch * (npatch + 1) / 2 / 1e9),
                    "parallelism": f"replicas x{dist.world}"},
         "iterations": its[-1] if its else None,
         "vcycles_per_s": vcyc_s,
@@ -588,11 +605,13 @@ def ours(args, dist):
         "gamma_1e4": gamma_large,
         "e2e": {"value": dist.world * dofs / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "kernel": "k_patch_tma<%d> (FP32 interior-star smoother, finest level)" % pb.d,
+        "roofline": {"bound": "hbm",
+                     "kernel": ("k_patch_tma<%d> (FP32 interior-star smoother, finest level)" % pb.d) if order == 2
+                     else "k_qk_star_apply<float> + k_qk_star_gather (FP32 order-3 star smoother, finest level)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,
-                     "units": {"interior_stars": nint, "bytes_per_star": packed * 4 + npatch * 4,
+                     "units": {"stars_streamed": nint, "bytes_per_star": packed * 4 + npatch * 4,
                                "r_bytes": nu * 4},
                      "traffic": stored_traffic("k_patch_apply_f32_fine", args.workload)},
         "roofline_apply": roofline_apply,
