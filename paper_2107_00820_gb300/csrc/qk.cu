@@ -97,6 +97,25 @@ __device__ __forceinline__ double dphi(int q, int a, int j, double sx, double sy
   const int qx = q % N1, qy = q / N1, ax = a % N1, ay = a / N1;
   return j == 0 ? cD[qx][ax] * cL[qy][ay] * sx : cL[qx][ax] * cD[qy][ay] * sy;
 }
+
+// The tables in shared memory, in precision T: lanes index them by their own point or node,
+// which the constant cache would serialise.  wq = the quadrature weight times |J|;
+// gx, gy = the physical derivatives of every node basis at every point.
+template <typename T>
+struct SharedTables {
+  T gx[NQ][NB], gy[NQ][NB], wq[NQ], psi[NQ][NPR];
+};
+template <typename T>
+__device__ __forceinline__ void load_tables(SharedTables<T>& t, double sx, double sy, double wdet) {
+  for (int e = threadIdx.x; e < NQ * NB; e += blockDim.x) {
+    const int q = e / NB, a = e % NB;
+    t.gx[q][a] = (T)dphi(q, a, 0, sx, sy);
+    t.gy[q][a] = (T)dphi(q, a, 1, sx, sy);
+  }
+  for (int e = threadIdx.x; e < NQ * NPR; e += blockDim.x) t.psi[e / NPR][e % NPR] = (T)cPSI[e / NPR][e % NPR];
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) t.wq[q] = (T)(cW[q % N1] * cW[q / N1] * wdet);
+  __syncthreads();
+}
 __device__ __forceinline__ double phi(int q, int a) { return cL[q % N1][a % N1] * cL[q / N1][a / N1]; }
 
 // ---------------------------------------------------------------------------
@@ -109,13 +128,14 @@ __global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T*
   constexpr bool RAW = (MODE & OP_RAW) != 0, VISC = (MODE & OP_VISC) != 0, AL = (MODE & OP_AL) != 0;
   constexpr bool BT = (MODE & OP_BT) != 0, BO = (MODE & OP_B) != 0;
   constexpr bool NEED_U = VISC || AL || BO, NEED_FLUX = VISC || AL || BT;
+  __shared__ SharedTables<T> tb;
   __shared__ T us[8][2][NB];
   __shared__ T ss[8][NQ][4];
+  load_tables<T>(tb, 2.0 / g.h[0], 2.0 / g.h[1], 0.25 * g.h[0] * g.h[1]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long cell = (long long)blockIdx.x * 8 + w;
   if (cell >= g.ncells) return;
   const int cx = (int)(cell % g.n[0]), cy = (int)(cell / g.n[0]);
-  const double sx = 2.0 / g.h[0], sy = 2.0 / g.h[1], wdet = 0.25 * g.h[0] * g.h[1];
   if (lane < NB) {
     const int i = K * cx + lane % N1, j = K * cy + lane / N1;
     const bool bnd = i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1;
@@ -123,62 +143,67 @@ __global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T*
     for (int c = 0; c < 2; ++c) us[w][c][lane] = (NEED_U && (RAW || !bnd)) ? x[c * g.N + nd] : T(0);
   }
   __syncwarp();
-  const int q = lane;
-  double G[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  if (NEED_U && q < NQ) {
+  const int q = lane < NQ ? lane : 0;
+  T G00 = T(0), G01 = T(0), G10 = T(0), G11 = T(0);
+  if (NEED_U && lane < NQ) {
+#pragma unroll 4
     for (int a = 0; a < NB; ++a) {
-      const double dx = dphi(q, a, 0, sx, sy), dy = dphi(q, a, 1, sx, sy);
-      for (int c = 0; c < 2; ++c) {
-        G[c][0] += (double)us[w][c][a] * dx;
-        G[c][1] += (double)us[w][c][a] * dy;
-      }
+      const T dx = tb.gx[q][a], dy = tb.gy[q][a], u0 = us[w][0][a], u1 = us[w][1][a];
+      G00 += u0 * dx;
+      G01 += u0 * dy;
+      G10 += u1 * dx;
+      G11 += u1 * dy;
     }
   }
-  const double div = G[0][0] + G[1][1];
-  double P = 0.0;   // the pressure-like field at the point: gamma pi + p_in
+  const T div = G00 + G11;
+  T P = T(0);   // the pressure-like field at the point: gamma pi + p_in
   if (AL || BO) {
-    double bu[NPR];   // (B u)_p = -sum_q w |J| psi_p div u
+    T bu[NPR];   // (B u)_p = -sum_q w |J| psi_p div u
+#pragma unroll
     for (int p = 0; p < NPR; ++p) {
-      double v = q < NQ ? -cW[q % N1] * cW[q / N1] * wdet * cPSI[q][p] * div : 0.0;
+      T v = lane < NQ ? -tb.wq[q] * tb.psi[q][p] * div : T(0);
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       bu[p] = v;
     }
     if (BO && lane == 0)
-      for (int p = 0; p < NPR; ++p) p_out[cell * NPR + p] = (T)bu[p];
-    if (AL && q < NQ) {
+      for (int p = 0; p < NPR; ++p) p_out[cell * NPR + p] = bu[p];
+    if (AL && lane < NQ) {
       const T* Wc = winv + cell * NPR * NPR;
-      double pi = 0.0;
+      T pi = T(0);
+#pragma unroll
       for (int p = 0; p < NPR; ++p) {
-        double sp = 0.0;
-        for (int r = 0; r < NPR; ++r) sp += (double)Wc[p * NPR + r] * bu[r];
-        pi += cPSI[q][p] * sp;
+        T sp = T(0);
+#pragma unroll
+        for (int r = 0; r < NPR; ++r) sp += Wc[p * NPR + r] * bu[r];
+        pi += tb.psi[q][p] * sp;
       }
-      P += gamma * pi;
+      P += (T)gamma * pi;
     }
   }
-  if (BT && q < NQ)
-    for (int p = 0; p < NPR; ++p) P += cPSI[q][p] * (double)p_in[cell * NPR + p];
+  if (BT && lane < NQ)
+    for (int p = 0; p < NPR; ++p) P += tb.psi[q][p] * p_in[cell * NPR + p];
   if (!NEED_FLUX) return;
-  if (q < NQ) {
-    const double m = VISC ? (double)mu[cell * NQ + q] : 0.0;
-    const double e01 = 0.5 * (G[0][1] + G[1][0]);
-    const double wq = cW[q % N1] * cW[q / N1] * wdet;
-    ss[w][q][0] = (T)(wq * (2.0 * m * G[0][0] - P));
-    ss[w][q][1] = (T)(wq * (2.0 * m * e01));
-    ss[w][q][2] = (T)(wq * (2.0 * m * e01));
-    ss[w][q][3] = (T)(wq * (2.0 * m * G[1][1] - P));
+  if (lane < NQ) {
+    const T m2 = VISC ? T(2) * mu[cell * NQ + q] : T(0);
+    const T e01 = T(0.5) * (G01 + G10);
+    const T wq = tb.wq[q];
+    ss[w][q][0] = wq * (m2 * G00 - P);
+    ss[w][q][1] = wq * (m2 * e01);
+    ss[w][q][2] = wq * (m2 * e01);
+    ss[w][q][3] = wq * (m2 * G11 - P);
   }
   __syncwarp();
   if (lane < NB) {
     const int a = lane;
-    double y0 = 0.0, y1 = 0.0;
+    T y0 = T(0), y1 = T(0);
+#pragma unroll 4
     for (int qq = 0; qq < NQ; ++qq) {
-      const double dx = dphi(qq, a, 0, sx, sy), dy = dphi(qq, a, 1, sx, sy);
-      y0 += (double)ss[w][qq][0] * dx + (double)ss[w][qq][1] * dy;
-      y1 += (double)ss[w][qq][2] * dx + (double)ss[w][qq][3] * dy;
+      const T dx = tb.gx[qq][a], dy = tb.gy[qq][a];
+      y0 += ss[w][qq][0] * dx + ss[w][qq][1] * dy;
+      y1 += ss[w][qq][2] * dx + ss[w][qq][3] * dy;
     }
-    ebuf[(cell * 2 + 0) * NB + a] = (T)y0;
-    ebuf[(cell * 2 + 1) * NB + a] = (T)y1;
+    ebuf[(cell * 2 + 0) * NB + a] = y0;
+    ebuf[(cell * 2 + 1) * NB + a] = y1;
   }
 }
 
@@ -333,17 +358,18 @@ __global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, con
   __shared__ double Bm[NPR][NE], WB[NPR][NE];
   __shared__ double rowk[NS], colk[NS];
   __shared__ int s_bad;
+  __shared__ SharedTables<double> tb;
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long v = blockIdx.x;
   const int vx = (int)(v % (g.n[0] + 1)), vy = (int)(v / (g.n[0] + 1));
-  const double sx = 2.0 / g.h[0], sy = 2.0 / g.h[1], wdet = 0.25 * g.h[0] * g.h[1];
+  load_tables<double>(tb, 2.0 / g.h[0], 2.0 / g.h[1], 0.25 * g.h[0] * g.h[1]);
   if (tid == 0) s_bad = 0;
   for (int e = tid; e < NS * NS; e += nt) M[e / NS][e % NS] = 0.0;
   // B_K (the same on every cell): B[p][(c, a)] = -sum_q w |J| psi_p d_c phi_a
   for (int e = tid; e < NPR * NE; e += nt) {
     const int p = e / NE, c = (e % NE) / NB, a = e % NB;
     double acc = 0.0;
-    for (int q = 0; q < NQ; ++q) acc -= cW[q % N1] * cW[q / N1] * wdet * cPSI[q][p] * dphi(q, a, c, sx, sy);
+    for (int q = 0; q < NQ; ++q) acc -= tb.wq[q] * tb.psi[q][p] * (c == 0 ? tb.gx[q][a] : tb.gy[q][a]);
     Bm[p][e % NE] = acc;
   }
   __syncthreads();
@@ -364,9 +390,9 @@ __global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, con
         const int i = e / NE, j = e % NE, ci = i / NB, ai = i % NB, cj = j / NB, aj = j % NB;
         double acc = 0.0;
         for (int q = 0; q < NQ; ++q) {
-          const double wq = cW[q % N1] * cW[q / N1] * wdet * 2.0 * mu[cell * NQ + q];
-          const double gi0 = dphi(q, ai, 0, sx, sy), gi1 = dphi(q, ai, 1, sx, sy);
-          const double gj0 = dphi(q, aj, 0, sx, sy), gj1 = dphi(q, aj, 1, sx, sy);
+          const double wq = tb.wq[q] * 2.0 * mu[cell * NQ + q];
+          const double gi0 = tb.gx[q][ai], gi1 = tb.gy[q][ai];
+          const double gj0 = tb.gx[q][aj], gj1 = tb.gy[q][aj];
           // eps(phi_i e_ci) : eps(phi_j e_cj) = (delta gi.gj + d_cj phi_i d_ci phi_j) / 2
           const double dot = (ci == cj ? gi0 * gj0 + gi1 * gj1 : 0.0) + (cj == 0 ? gi0 : gi1) * (ci == 0 ? gj0 : gj1);
           acc += wq * 0.5 * dot;
