@@ -479,6 +479,7 @@ __global__ void __launch_bounds__(256) k_qk_star_apply(Geom g, const T* __restri
   T acc[R];
   for (int k = 0; k < R; ++k) acc[k] = T(0);
   const T* S = inv + v * pstride;
+#pragma unroll 5
   for (int t = 0; t < NS; ++t) {
     const T* d = S + diag_start(NS, t);
     for (int k = 0; k < R; ++k) {
