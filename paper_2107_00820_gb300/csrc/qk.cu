@@ -457,20 +457,33 @@ __global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, con
 
 // y_v = A_v^-1 r|_v: one warp per star (vertex), entries by lanes, diagonals in order;
 // interior: the stars of the fine vertices 2K+1 at the coarse-cell centres, written (mode 1)
-// or subtracted (mode 2) straight into the nodes; else into the scratch rows [vertex][50]
+// or subtracted (mode 2) straight into the nodes; else into the scratch rows [vertex][50].
+// The warp first copies its star's packed inverse (pstride = 1276 entries) into shared
+// memory with 16-byte loads from all lanes, all in flight at once, then forms the rows from
+// there: one memory latency per star instead of one per diagonal.
+constexpr int kStarStride = 1276;   // packed_stride(50)
 template <typename T>
-__global__ void __launch_bounds__(256) k_qk_star_apply(Geom g, const T* __restrict__ inv, int pstride, int interior,
-                                                       int mode, const T* __restrict__ r, T* __restrict__ out) {
-  constexpr int R = (NS + 31) / 32;
-  __shared__ T rs[8][NS];
+__host__ __device__ constexpr int star_warps() { return sizeof(T) == 4 ? 8 : 4; }   // 41 KB of shared memory a block
+
+template <typename T>
+__global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, const T* __restrict__ inv, int pstride,
+                                                                       int interior, int mode, const T* __restrict__ r,
+                                                                       T* __restrict__ out) {
+  constexpr int R = (NS + 31) / 32, WPB = star_warps<T>();
+  constexpr int NV = kStarStride * (int)sizeof(T) / 16;   // 16-byte words of one star
+  __shared__ T rs[WPB][NS];
+  __shared__ uint4 sbuf[WPB][NV];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long count = interior ? (long long)(g.n[0] / 2) * (g.n[1] / 2) : (long long)(g.n[0] + 1) * (g.n[1] + 1);
-  const long long item = (long long)blockIdx.x * 8 + w;
-  if (item >= count) return;
+  const long long item = (long long)blockIdx.x * WPB + w;
+  if (item >= count || pstride != kStarStride) return;
   int vx, vy;
   if (interior) { vx = 2 * (int)(item % (g.n[0] / 2)) + 1; vy = 2 * (int)(item / (g.n[0] / 2)) + 1; }
   else { vx = (int)(item % (g.n[0] + 1)); vy = (int)(item / (g.n[0] + 1)); }
   const long long v = (long long)vx + (long long)(g.n[0] + 1) * vy;
+  const uint4* src = reinterpret_cast<const uint4*>(inv + v * kStarStride);
+#pragma unroll 4
+  for (int e = lane; e < NV; e += 32) sbuf[w][e] = __ldg(src + e);
   for (int e = lane; e < NS; e += 32) {
     long long nd;
     rs[w][e] = star_node(g, vx, vy, e, nd) ? r[(e / (S1 * S1)) * g.N + nd] : T(0);
@@ -478,7 +491,7 @@ __global__ void __launch_bounds__(256) k_qk_star_apply(Geom g, const T* __restri
   __syncwarp();
   T acc[R];
   for (int k = 0; k < R; ++k) acc[k] = T(0);
-  const T* S = inv + v * pstride;
+  const T* S = reinterpret_cast<const T*>(&sbuf[w][0]);
 #pragma unroll 5
   for (int t = 0; t < NS; ++t) {
     const T* d = S + diag_start(NS, t);
@@ -636,12 +649,15 @@ void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t
 
 void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
                      cudaStream_t s) {
-  const unsigned b1 = (unsigned)((L.g.nverts + 7) / 8), b2 = (unsigned)((2 * L.g.N + 255) / 256);
+  const unsigned b2 = (unsigned)((2 * L.g.N + 255) / 256);
+  constexpr int W64 = qk::star_warps<double>(), W32 = qk::star_warps<float>();
   if (prec == PREC_F64) {
-    qk::k_qk_star_apply<double><<<b1, 256, 0, s>>>(L.g, L.inv64, L.pstride, 0, 0, (const double*)r, (double*)scratch);
+    qk::k_qk_star_apply<double><<<(unsigned)((L.g.nverts + W64 - 1) / W64), 32 * W64, 0, s>>>(
+        L.g, L.inv64, L.pstride, 0, 0, (const double*)r, (double*)scratch);
     qk::k_qk_star_gather<double><<<b2, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
   } else {
-    qk::k_qk_star_apply<float><<<b1, 256, 0, s>>>(L.g, L.inv32, L.pstride, 0, 0, (const float*)r, (float*)scratch);
+    qk::k_qk_star_apply<float><<<(unsigned)((L.g.nverts + W32 - 1) / W32), 32 * W32, 0, s>>>(
+        L.g, L.inv32, L.pstride, 0, 0, (const float*)r, (float*)scratch);
     qk::k_qk_star_gather<float><<<b2, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
   }
   count_launch(2);
@@ -651,13 +667,13 @@ void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out
   const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2);
   const size_t es = prec == PREC_F64 ? 8 : 4;
   if (!subtract) cudaMemsetAsync(out, 0, es * 2 * fine.g.N, s);
-  const unsigned b = (unsigned)((nc + 7) / 8);
+  constexpr int W64 = qk::star_warps<double>(), W32 = qk::star_warps<float>();
   if (prec == PREC_F64)
-    qk::k_qk_star_apply<double><<<b, 256, 0, s>>>(fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1,
-                                                  (const double*)in, (double*)out);
+    qk::k_qk_star_apply<double><<<(unsigned)((nc + W64 - 1) / W64), 32 * W64, 0, s>>>(
+        fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
   else
-    qk::k_qk_star_apply<float><<<b, 256, 0, s>>>(fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1,
-                                                 (const float*)in, (float*)out);
+    qk::k_qk_star_apply<float><<<(unsigned)((nc + W32 - 1) / W32), 32 * W32, 0, s>>>(
+        fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
   count_launch(1);
 }
 
