@@ -352,11 +352,12 @@ als_status als_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void*
  * count, coefficients, gamma and options (2D and 3D may be mixed); instance i
  * is a full context (als_batch_context gives it for the per-instance calls).
  * als_batch_solve runs all solves together: each round queues one FGMRES
- * iteration of every unfinished instance, each on its own stream, then waits
- * once, so the instances' kernels run concurrently; results are bitwise those
- * of als_solve on the same instance.  als_batch_vcycle applies one multigrid
- * cycle to every instance with a single graph launch whose independent branches
- * are the instances' captured cycles.
+ * iteration of every unfinished instance (the instances' own FGMRES kernels on
+ * their own streams, the preconditioner's cycles in the batch's cycle form, see
+ * ALS_BATCH_MERGED), then waits once; results are bitwise those of als_solve on
+ * the same instance.  als_batch_vcycle applies one multigrid cycle to every
+ * instance in the batch's cycle form (FP64 cycles: always the graph of the
+ * instances' captured cycles).
  * Arrays are indexed by instance: meshes/coeffs/gammas[count]; opts[count] or
  * NULL (defaults); f_qp, u_bc, r2, u, p, b, x: arrays of count pointers with
  * the meaning and layout of the single-instance calls (u_bc, r2 may be NULL
@@ -374,6 +375,41 @@ als_status als_batch_solve(als_batch* batch, const double* const* f_qp, const do
                            const double* const* r2, double* const* u, double* const* p, als_solve_info* infos);
 als_status als_batch_vcycle(als_batch* batch, int prec, const void* const* b, void* const* x);
 const char* als_batch_last_error(const als_batch* batch);
+
+/* Execution form of a batch's FP32 multigrid cycles (those of als_batch_vcycle with
+ * prec FP32, and the preconditioner cycles of a mixed-mode als_batch_solve):
+ *   ALS_BATCH_MERGED    one launch per level operation for all instances: every
+ *                       operator apply, star-product sweep, transfer, GMRES step and
+ *                       the coarse solve of the instances' V-cycles runs as one merged
+ *                       kernel launch whose grid is the flattened (instance, tile) work
+ *                       list; the hierarchies are aligned at their coarsest level, the
+ *                       whole merged cycle is captured as one CUDA graph, and an
+ *                       autotuner picks the star-kernel variant of every merged level
+ *                       operation (each instance's cycle of Sec. 4 unchanged).
+ *   ALS_BATCH_BRANCHES  one graph launch whose independent branches are the
+ *                       instances' own captured cycles (solves: one stream each).
+ * Every instance's results are bitwise those of its single-instance calls in both
+ * forms.  MERGED needs, in every instance: order 2, scalar viscosity, the GMRES
+ * smoother with at most 8 steps, the V-cycle, kernel timing off, and the sweeps and
+ * transfer of instance 0; a mixed-mode solve also needs the full block factorisation
+ * (ALS_FACT_FULL), else the solve runs in the BRANCHES form.  als_batch_create picks
+ * MERGED when every instance qualifies.  als_batch_set_mode returns ALS_EINVAL for an
+ * unknown mode or, for MERGED, when an instance does not qualify (the message says
+ * which and why).  als_batch_get_mode reads the mode. */
+enum { ALS_BATCH_MERGED = 0, ALS_BATCH_BRANCHES = 1 };
+als_status als_batch_set_mode(als_batch* batch, int mode);
+als_status als_batch_get_mode(const als_batch* batch, int* mode);
+
+/* Autotuner record of the merged cycle (built on the first merged FP32 cycle or
+ * solve): for level index `level` (0 = coarsest, 1 <= level < the largest level
+ * count), the star-kernel variant chosen for the merged star products and for the
+ * merged interior solves (0: TMA ring, 2 stages; 1: 3 stages; 2: direct loads) and,
+ * if ms is not NULL, the measured time per launch of each variant (ms[0..2]:
+ * products, ms[3..5]: interior solves).  *kernels (optional): kernel launches of one
+ * merged cycle.  ALS_EINVAL: NULL batch or outputs, level out of range, or no merged
+ * cycle built yet. */
+als_status als_batch_merged_tune(const als_batch* batch, int level, int* products_variant, int* interior_variant,
+                                 float* ms, long long* kernels);
 
 /* Autotuner record of a smoothed level (1 <= level < levels).  Before the FP32
  * cycle is first captured, each level times its FP32 star-patch kernel variants

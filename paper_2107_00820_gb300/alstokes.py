@@ -22,6 +22,7 @@ STATUS_NAMES = ["ALS_OK", "ALS_EINVAL", "ALS_ENOMEM", "ALS_ECUDA", "ALS_ENOTSPD"
 ALS_COEFF_SCALAR, ALS_COEFF_TENSOR = 0, 1
 ALS_PREC_FP64, ALS_PREC_FP32 = 0, 1
 ALS_MODE_FP64, ALS_MODE_MIXED = 0, 1
+ALS_BATCH_MERGED, ALS_BATCH_BRANCHES = 0, 1
 ALS_SMOOTH_GMRES, ALS_SMOOTH_RICHARDSON = 0, 1
 ALS_TRANSFER_ROBUST, ALS_TRANSFER_STANDARD = 0, 1
 ALS_SCHUR_P1, ALS_SCHUR_P2 = 0, 1
@@ -91,6 +92,10 @@ SIGNATURES = {
                                 POINTER(c_void_p), POINTER(c_void_p), POINTER(als_solve_info)]),
     "als_batch_vcycle": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_void_p)]),
     "als_batch_last_error": (ctypes.c_char_p, [c_void_p]),
+    "als_batch_set_mode": (c_int, [c_void_p, c_int]),
+    "als_batch_get_mode": (c_int, [c_void_p, POINTER(c_int)]),
+    "als_batch_merged_tune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_float),
+                                      POINTER(ctypes.c_longlong)]),
     "als_autotune_info": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(ctypes.c_float)]),
     "als_set_patch_kernel": (c_int, [c_void_p, c_int, c_int]),
     "als_load_patch_inverses": (c_int, [c_void_p, c_int, c_void_p]),
@@ -443,6 +448,23 @@ class Batch:
         k = self.count
         self._check(self._lib.als_batch_vcycle(self._b, prec, (c_void_p * k)(*[_ptr(t) for t in b]),
                                                (c_void_p * k)(*[_ptr(t) for t in x])))
+
+    @property
+    def mode(self):
+        """ALS_BATCH_MERGED or ALS_BATCH_BRANCHES (the execution form of the FP32 cycles)."""
+        m = c_int()
+        self._check(self._lib.als_batch_get_mode(self._b, byref(m)))
+        return m.value
+
+    def set_mode(self, mode):
+        self._check(self._lib.als_batch_set_mode(self._b, int(mode)))
+
+    def merged_tune(self, level):
+        """(products variant, interior variant, ms[6], kernels per merged cycle) of level index `level`."""
+        pv, iv, kern = c_int(), c_int(), ctypes.c_longlong()
+        ms = (ctypes.c_float * 6)()
+        self._check(self._lib.als_batch_merged_tune(self._b, int(level), byref(pv), byref(iv), ms, byref(kern)))
+        return pv.value, iv.value, list(ms), kern.value
 
     def instance(self, i):
         """Instance i as a Context (owned by the batch: closing it does nothing)."""

@@ -1267,16 +1267,15 @@ static als_status solve_rhs_done(als_ctx* c) {
   return ALS_OK;
 }
 
-// queue FGMRES iteration k (no wait); the residual estimate is on its way to the host
-static als_status solve_iter_launch(als_ctx* c) {
+// the FGMRES iteration after its preconditioner application z_k = P v_k: w = A z_k,
+// Gram-Schmidt, Givens step, residual estimate on its way to the host
+static void solve_iter_tail(als_ctx* c) {
   als_ctx::SolveRun& R = c->run;
   const cudaStream_t s = c->stream;
   const int k = R.k, ldh = c->opt.maxit + 1;
-  double* vk = c->V + (size_t)k * c->n;
   double* zk = c->Z + (size_t)k * c->n;
   double* w = c->V + (size_t)(k + 1) * c->n;
   double* hcol = c->H + (size_t)k * ldh;
-  ALS_TRY(precondition(c, vk, zk));
   matvec(c, zk, w);
   vec_multidot(PREC_F64, c->n, k + 1, c->V, c->n, w, hcol, c->partial, s);
   vec_multiaxpy(PREC_F64, c->n, k + 1, c->V, c->n, hcol, w, s, -1.0);
@@ -1285,6 +1284,48 @@ static als_status solve_iter_launch(als_ctx* c) {
   vec_scale_dev(PREC_F64, c->n, nullptr, c->nrm2, w, w, s, 1);
   dev_hess_givens(k, c->H, ldh, c->h2, c->nrm2, c->cs, c->sn, c->g, c->res, s);
   cudaMemcpyAsync(c->host_res, c->res, sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+// The mixed-mode full-factorisation preconditioner of iteration k split at its two
+// FP32 cycles (the steps of precondition, in its order), so that a batch can run the
+// cycles of all its instances as merged launches: phase 0 loads the first cycle's
+// right-hand side, phase 1 runs between the cycles, phase 2 finishes z_k and the
+// iteration.
+static void precond_mixed_phase(als_ctx* c, int phase) {
+  const LevelDev& F = c->lev[c->L - 1];
+  const cudaStream_t s = c->stream;
+  const int k = c->run.k;
+  const double* v = c->V + (size_t)k * c->n;
+  double* z = c->Z + (size_t)k * c->n;
+  const double* f = v;
+  const double* gp = v + c->nu;
+  double* x1 = z;
+  double* z2 = z + c->nu;
+  MGWork& w = work_for(c, PREC_F32);
+  const int l = c->L - 1;
+  if (phase == 0) {
+    vec_cast(c->nu, f, PREC_F64, w.b[l], PREC_F32, s);
+  } else if (phase == 1) {
+    vec_cast(c->nu, w.x[l], PREC_F32, c->tu, PREC_F64, s);
+    op_apply(F, PREC_F32, OP_B, c->gamma, w.x[l], nullptr, nullptr, c->tp32, s);     // B z1 (FP32)
+    vec_cast(c->np, c->tp32, PREC_F32, c->tp, PREC_F64, s);
+    vec_axpby(PREC_F64, c->np, 1.0, gp, -1.0, c->tp, s);                             // tp = g - B z1
+    schur_apply(F.g.ncells, c->npr, c->schur, c->tp, z2, s);                         // z2 = -S^-1 tp
+    vec_cast(c->np, z2, PREC_F64, c->tp32, PREC_F32, s);
+    op_apply(F, PREC_F32, OP_BT, c->gamma, nullptr, w.b[l], c->tp32, nullptr, s);    // B^T z2 (FP32)
+  } else {
+    vec_cast(c->nu, w.x[l], PREC_F32, x1, PREC_F64, s);
+    vec_axpby(PREC_F64, c->nu, 1.0, c->tu, -1.0, x1, s);                             // x1 = z1 - x1
+    project_constant(F.g.ncells, c->npr, z2, c->partial, s);
+    solve_iter_tail(c);
+  }
+}
+
+// queue FGMRES iteration k (no wait); the residual estimate is on its way to the host
+static als_status solve_iter_launch(als_ctx* c) {
+  const int k = c->run.k;
+  ALS_TRY(precondition(c, c->V + (size_t)k * c->n, c->Z + (size_t)k * c->n));
+  solve_iter_tail(c);
   return ALS_OK;
 }
 
@@ -1555,13 +1596,282 @@ als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, in
 // ============================================================================
 }  // extern "C"
 
+namespace {
+
+// ----------------------------------------------------------------------------
+// Merged FP32 cycles: the V-cycles of all instances of a set, issued as one launch per
+// level operation (the merged launches of batch.cuh).  The instances' hierarchies are
+// aligned at the coarsest level: level index l (0 = coarsest) of the merged cycle runs
+// the smoothing, transfer and GMRES operations of every instance that has a level l,
+// so the coarse solves of all instances form one launch, and the sequence of
+// operations each instance sees is exactly that of its own cycle_level (same kernels,
+// same arithmetic, same order).  Only the patch-kernel variant of the star products and
+// of the interior solves is chosen per merged operation, by merged_tune.
+// ----------------------------------------------------------------------------
+struct MergedCycle {
+  std::vector<als_ctx*> inst;
+  int Lmax = 0;
+  std::vector<int> var_prod, var_int;     // per level index (>= 1)
+  std::vector<float> ms_prod, ms_int;     // per level index x 3 variants (ms per launch)
+  cudaGraph_t tmpl = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  bool tuned = false;
+};
+
+// why instance c cannot take part in merged cycles ("" if it can)
+std::string merged_ineligible(const als_ctx* c, const als_ctx* first) {
+  if (c->k != 2) return "order 3";
+  if (c->lev[0].tensor) return "tensor coefficients";
+  if (!fused_gmres(c)) return "smoother other than GMRES(s <= 8)";
+  if (c->opt.cycle != ALS_CYCLE_V) return "F-cycle";
+  if (c->prof.on) return "kernel timing on";
+  if (first && std::max(1, c->opt.sweeps) != std::max(1, first->opt.sweeps)) return "sweeps differ from instance 0";
+  if (first && c->opt.transfer != first->opt.transfer) return "transfer differs from instance 0";
+  return "";
+}
+
+void merged_free(MergedCycle& M) {
+  if (M.exec) cudaGraphExecDestroy(M.exec);
+  if (M.tmpl) cudaGraphDestroy(M.tmpl);
+  M.exec = nullptr;
+  M.tmpl = nullptr;
+  M.kernels = 0;
+}
+
+// instances with a level l (l >= 0)
+std::vector<als_ctx*> at_level(const MergedCycle& M, int l) {
+  std::vector<als_ctx*> out;
+  for (als_ctx* c : M.inst)
+    if (l < c->L) out.push_back(c);
+  return out;
+}
+
+// smooth_fused on level l of every instance that has it (x_is_zero: x starts at 0;
+// residual: t = b - A x from the Arnoldi relation, as the pre-smoothing does)
+void merged_smooth(MergedCycle& M, int l, bool x_is_zero, bool residual, cudaStream_t s) {
+  const std::vector<als_ctx*> S = at_level(M, l);
+  if (S.empty()) return;
+  const int steps = std::max(1, S[0]->opt.sweeps);
+  SmallLayout sl(steps);
+  std::vector<BGmres> g;
+  std::vector<BApply> ap;
+  for (als_ctx* c : S) {
+    MGWork& w = c->w32;
+    const long long len = c->lev[l].g.N * c->dim;
+    BGmres it{};
+    it.n = len;
+    it.b = w.b[l];
+    it.Z = w.Z[l];
+    it.V = w.V[l];
+    it.ld = len;
+    it.partial = w.partial;
+    it.st = sl.dev(w.small[l]);
+    it.x = w.x[l];
+    it.x_zero = x_is_zero ? 1 : 0;
+    it.t = residual ? w.t[l] : nullptr;
+    g.push_back(it);
+    ap.push_back(BApply{&c->lev[l], c->gamma, w.x[l], w.V[l],
+                        ApplyEpi{w.b[l], -1.0, 0, nullptr, 0, nullptr, 1, it.st, w.partial}});
+  }
+  if (x_is_zero) batch_gm_start(g, s);     // V0 = b
+  else batch_apply_epi(ap, s);             // V0 = b - A x
+  for (int j = 0; j < steps; ++j) {
+    std::vector<BPatch> prod, gath;
+    std::vector<BApply> az;
+    for (size_t i = 0; i < S.size(); ++i) {
+      als_ctx* c = S[i];
+      MGWork& w = c->w32;
+      const long long len = c->lev[l].g.N * c->dim;
+      void* Vj = vptr(w.V[l], w.es, (long long)j * len);
+      void* Vn = vptr(w.V[l], w.es, (long long)(j + 1) * len);
+      void* Zj = vptr(w.Z[l], w.es, (long long)j * len);
+      const void* den = vptr(w.small[l], w.es, sl.hn + j);
+      prod.push_back(BPatch{&c->lev[l], Vj, w.scratch[l], nullptr, nullptr});
+      ApplyEpi e{nullptr, 1.0, j + 1, w.V[l], len, vptr(w.small[l], w.es, sl.H + (long long)j * sl.ldh), 0, g[i].st,
+                 w.partial};
+      if (fuse_patch_gather(c, PREC_F32)) {
+        e.pout = w.scratch[l];
+        e.pden = den;
+      } else {
+        gath.push_back(BPatch{&c->lev[l], nullptr, w.scratch[l], den, Zj});
+      }
+      az.push_back(BApply{&c->lev[l], c->gamma, Zj, Vn, e});
+      g[i].j = j;
+    }
+    batch_star_products(M.var_prod[l], prod, s);    // scratch rows = A_v^-1 V_j|_v
+    if (!gath.empty()) batch_patch_gather(gath, s);  // Z_j = D^-1 v_j (unfused instances)
+    batch_apply_epi(az, s);                          // A Z_j, H[0..j][j]
+    batch_gm_orth(g, s);                             // V_{j+1}, Givens step j
+  }
+  batch_gm_update(g, s);
+}
+
+void merged_restrict(MergedCycle& M, int l, cudaStream_t s) {
+  const std::vector<als_ctx*> S = at_level(M, l);
+  std::vector<BPatch> isv;
+  std::vector<BApply> ap;
+  std::vector<BTransfer> tr;
+  const bool robust = S[0]->opt.transfer == ALS_TRANSFER_ROBUST;
+  for (als_ctx* c : S) {
+    MGWork& w = c->w32;
+    isv.push_back(BPatch{&c->lev[l], w.t[l], w.t2[l], nullptr, nullptr});
+    ap.push_back(BApply{&c->lev[l], c->gamma, w.t2[l], w.t3[l], ApplyEpi{}});
+    tr.push_back(BTransfer{&c->lev[l - 1], &c->lev[l], w.t[l], w.b[l - 1], robust ? w.t3[l] : nullptr});
+  }
+  if (robust) {
+    batch_interior_solve(M.var_int[l], isv, 0, s);   // t2 = sum_K E_K A_K^-1 E_K^T t
+    batch_apply_al(ap, s);                           // t3 = G t2
+  }
+  batch_restrict(tr, s);                             // b_{l-1} = P_H^T (t - t3)
+}
+
+void merged_prolong(MergedCycle& M, int l, cudaStream_t s) {
+  const std::vector<als_ctx*> S = at_level(M, l);
+  std::vector<BPatch> isv;
+  std::vector<BApply> ap;
+  std::vector<BTransfer> tr;
+  const bool robust = S[0]->opt.transfer == ALS_TRANSFER_ROBUST;
+  for (als_ctx* c : S) {
+    MGWork& w = c->w32;
+    tr.push_back(BTransfer{&c->lev[l - 1], &c->lev[l], w.x[l - 1], w.t[l], w.x[l]});
+    ap.push_back(BApply{&c->lev[l], c->gamma, w.t[l], w.t3[l], ApplyEpi{}});
+    isv.push_back(BPatch{&c->lev[l], w.t3[l], w.x[l], nullptr, nullptr});
+  }
+  batch_prolong(tr, s);                              // t = P_H x_{l-1}, x += t
+  if (robust) {
+    batch_apply_al(ap, s);                           // t3 = G t
+    batch_interior_solve(M.var_int[l], isv, 1, s);   // x -= sum_K E_K A_K^-1 E_K^T t3
+  }
+}
+
+// one merged V-cycle: w32.b[L-1] -> w32.x[L-1] of every instance
+void merged_cycle(MergedCycle& M, cudaStream_t s) {
+  for (int l = M.Lmax - 1; l >= 1; --l) {
+    merged_smooth(M, l, true, true, s);
+    merged_restrict(M, l, s);
+  }
+  std::vector<BCoarse> co;
+  for (als_ctx* c : M.inst) co.push_back(BCoarse{&c->lev[0], &c->coarse, c->w32.b[0], c->w32.x[0]});
+  batch_coarse_apply(co, s);
+  for (int l = 1; l < M.Lmax; ++l) {
+    merged_prolong(M, l, s);
+    merged_smooth(M, l, false, false, s);
+  }
+}
+
+// Autotuner of the merged cycle: for every level index, time the three patch-kernel
+// variants of the merged star products and of the merged interior solves (one warm-up
+// and three timed launches each, CUDA events) and keep the fastest.  Inputs: the
+// instances' zeroed V_0 of that level; outputs go to scratch the cycle overwrites.
+void merged_tune(MergedCycle& M, cudaStream_t s) {
+  const long long launches0 = launch_count();
+  M.var_prod.assign(M.Lmax, 0);
+  M.var_int.assign(M.Lmax, 0);
+  M.ms_prod.assign(3 * M.Lmax, 0.f);
+  M.ms_int.assign(3 * M.Lmax, 0.f);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int l = 1; l < M.Lmax; ++l) {
+    std::vector<BPatch> prod, isv;
+    for (als_ctx* c : at_level(M, l)) {
+      MGWork& w = c->w32;
+      vec_zero(PREC_F32, c->lev[l].g.N * c->dim, w.V[l], s);
+      prod.push_back(BPatch{&c->lev[l], w.V[l], w.scratch[l], nullptr, nullptr});
+      isv.push_back(BPatch{&c->lev[l], w.V[l], w.t2[l], nullptr, nullptr});
+    }
+    for (int kind = 0; kind < 2; ++kind) {
+      float best = 1e30f;
+      for (int v = 0; v < 3; ++v) {
+        for (int rep = 0; rep < 4; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, s);
+          if (kind == 0) batch_star_products(v, prod, s);
+          else batch_interior_solve(v, isv, 1, s);
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        (kind == 0 ? M.ms_prod : M.ms_int)[3 * l + v] = ms;
+        if (ms < best) {
+          best = ms;
+          (kind == 0 ? M.var_prod : M.var_int)[l] = v;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  count_launch(-(launch_count() - launches0));   // tuning launches are not work of a step
+  M.tuned = true;
+}
+
+// capture the merged cycle (tuning first, once) and instantiate it
+als_status merged_build(MergedCycle& M, cudaStream_t s, std::string& err) {
+  if (M.exec) return ALS_OK;
+  M.Lmax = 0;
+  for (als_ctx* c : M.inst) M.Lmax = std::max(M.Lmax, c->L);
+  static bool prepared = false;
+  if (!prepared) {
+    batch_patch_prepare();
+    batch_coarse_prepare();
+    prepared = true;
+  }
+  if (!M.tuned) merged_tune(M, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    err = std::string("merged cycle tuning: ") + cudaGetErrorString(cudaGetLastError());
+    return ALS_ECUDA;
+  }
+  const long long c0 = launch_count();
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    err = "merged cycle: begin capture";
+    cudaGetLastError();
+    return ALS_ECUDA;
+  }
+  merged_cycle(M, s);
+  const cudaError_t ec = cudaStreamEndCapture(s, &M.tmpl);
+  M.kernels = launch_count() - c0;
+  count_launch(-M.kernels);
+  if (ec != cudaSuccess || cudaGraphInstantiate(&M.exec, M.tmpl, 0) != cudaSuccess) {
+    err = std::string("merged cycle: capture/instantiate: ") + cudaGetErrorString(cudaGetLastError());
+    merged_free(M);
+    return ALS_ECUDA;
+  }
+  return ALS_OK;
+}
+
+}  // namespace
+
 struct als_batch {
   std::vector<als_ctx*> ctx;
   cudaStream_t user_stream = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   std::string err;
+  int mode = ALS_BATCH_BRANCHES;
+  MergedCycle merged;                // every instance (als_batch_vcycle)
+  MergedCycle live;                  // the unfinished instances of a batched solve
+  std::vector<cudaEvent_t> ev;       // per instance: joins of the merged cycles of a solve
+  cudaEvent_t mev = nullptr;
+  cudaStream_t mstream = nullptr;    // where the merged cycles run
 };
+
+// stream and events of the merged cycles (created on first use)
+static als_status batch_merged_init(als_batch* b) {
+  if (b->mstream) return ALS_OK;
+  if (cudaStreamCreateWithFlags(&b->mstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->mstream = nullptr;
+    b->err = "batch stream creation failed";
+    return ALS_ECUDA;
+  }
+  b->ev.assign(b->ctx.size(), nullptr);
+  for (cudaEvent_t& e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&b->mev, cudaEventDisableTiming);
+  return ALS_OK;
+}
 
 static als_status batch_fail(als_batch* b, als_status code, const std::string& msg) {
   if (b) b->err = msg;
@@ -1591,16 +1901,27 @@ als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* 
     }
     b->ctx.push_back(c);
   }
+  bool all = true;
+  for (als_ctx* c : b->ctx) all = all && merged_ineligible(c, b->ctx[0]).empty();
+  b->mode = all ? ALS_BATCH_MERGED : ALS_BATCH_BRANCHES;
+  b->merged.inst = b->ctx;
   *out = b;
   return ALS_OK;
 }
 
 als_status als_batch_destroy(als_batch* b) {
   if (!b) return ALS_EINVAL;
+  for (als_ctx* c : b->ctx) cudaStreamSynchronize(c->stream);
+  if (b->mstream) cudaStreamSynchronize(b->mstream);
   for (int k = 0; k < 2; ++k) {
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
     if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
   }
+  merged_free(b->merged);
+  merged_free(b->live);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->mev) cudaEventDestroy(b->mev);
+  if (b->mstream) cudaStreamDestroy(b->mstream);
   for (als_ctx* c : b->ctx) als_destroy(c);
   delete b;
   return ALS_OK;
@@ -1629,13 +1950,65 @@ als_status als_batch_solve(als_batch* b, const double* const* f_qp, const double
     else st[i] = solve_rhs_done(b->ctx[i]);
     live[i] = st[i] == ALS_OK;
   }
+  // merged cycles: every instance mixed, with the full block factorisation (two cycles
+  // per preconditioner application, see precond_mixed_phase)
+  bool merged = b->mode == ALS_BATCH_MERGED;
+  for (als_ctx* c : b->ctx) merged = merged && c->opt.mode == ALS_MODE_MIXED && c->opt.fact == ALS_FACT_FULL;
+  if (merged) {
+    const als_status ms = batch_merged_init(b);
+    if (ms != ALS_OK) return ms;
+  }
   for (;;) {
     bool any = false;
-    for (int i = 0; i < n; ++i) {
-      if (!live[i] || b->ctx[i]->run.done) continue;
-      st[i] = solve_iter_launch(b->ctx[i]);
-      if (st[i] != ALS_OK) live[i] = false;
-      else any = true;
+    if (merged) {
+      std::vector<int> act;
+      for (int i = 0; i < n; ++i)
+        if (live[i] && !b->ctx[i]->run.done) act.push_back(i);
+      if (act.empty()) break;
+      std::vector<als_ctx*> set;
+      for (int i : act) set.push_back(b->ctx[i]);
+      const cudaStream_t ms = b->mstream;
+      if (!b->merged.tuned) {     // the full set's tuning serves every live subset
+        b->merged.Lmax = 0;
+        for (als_ctx* c : b->merged.inst) b->merged.Lmax = std::max(b->merged.Lmax, c->L);
+        batch_patch_prepare();
+        batch_coarse_prepare();
+        merged_tune(b->merged, ms);
+      }
+      if (set != b->live.inst) {
+        merged_free(b->live);
+        b->live.inst = set;
+        b->live.var_prod = b->merged.var_prod;
+        b->live.var_int = b->merged.var_int;
+        b->live.tuned = true;
+      }
+      const als_status bs = merged_build(b->live, ms, b->err);
+      if (bs != ALS_OK) return bs;
+      for (int phase = 0; phase < 2; ++phase) {
+        for (int i : act) {
+          als_ctx* c = b->ctx[i];
+          if (phase > 0) cudaStreamWaitEvent(c->stream, b->mev, 0);
+          precond_mixed_phase(c, phase);
+          cudaEventRecord(b->ev[i], c->stream);
+          cudaStreamWaitEvent(ms, b->ev[i], 0);
+        }
+        if (cudaGraphLaunch(b->live.exec, ms) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
+        count_launch(b->live.kernels);
+        cudaEventRecord(b->mev, ms);
+      }
+      for (int i : act) {
+        als_ctx* c = b->ctx[i];
+        cudaStreamWaitEvent(c->stream, b->mev, 0);
+        precond_mixed_phase(c, 2);
+      }
+      any = true;
+    } else {
+      for (int i = 0; i < n; ++i) {
+        if (!live[i] || b->ctx[i]->run.done) continue;
+        st[i] = solve_iter_launch(b->ctx[i]);
+        if (st[i] != ALS_OK) live[i] = false;
+        else any = true;
+      }
     }
     if (!any) break;
     for (int i = 0; i < n; ++i) {
@@ -1662,6 +2035,39 @@ als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void*
   if (prec != PREC_F64 && prec != PREC_F32) return batch_fail(b, ALS_EINVAL, "prec must be FP64 or FP32");
   const int n = (int)b->ctx.size();
   const int k = prec == PREC_F64 ? 0 : 1;
+  for (int i = 0; i < n; ++i)
+    if (!bv[i] || !xv[i]) return batch_fail(b, ALS_EINVAL, "null vector");
+  if (prec == PREC_F32 && b->mode == ALS_BATCH_MERGED) {
+    // one merged launch per level operation for all instances
+    ALS_TRY(batch_merged_init(b));
+    for (int i = 0; i < n; ++i) cudaStreamSynchronize(b->ctx[i]->stream);
+    const cudaStream_t s = b->mstream;
+    cudaEventRecord(b->ctx[0]->order_ev, b->user_stream);
+    cudaStreamWaitEvent(s, b->ctx[0]->order_ev, 0);
+    const als_status st = merged_build(b->merged, s, b->err);
+    if (st != ALS_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      als_ctx* c = b->ctx[i];
+      const int l = c->L - 1;
+      cudaMemcpyAsync(c->w32.b[l], bv[i], (size_t)(c->lev[l].g.N * c->dim) * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    if (cudaGraphLaunch(b->merged.exec, s) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
+    count_launch(b->merged.kernels);
+    for (int i = 0; i < n; ++i) {
+      als_ctx* c = b->ctx[i];
+      const int l = c->L - 1;
+      cudaMemcpyAsync(xv[i], c->w32.x[l], (size_t)(c->lev[l].g.N * c->dim) * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      const cudaError_t e = cudaGetLastError();
+      return batch_fail(b, ALS_ECUDA, std::string("merged cycle: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n; ++i) {
+      const als_status cs = check_status(b->ctx[i], "merged cycle");
+      if (cs != ALS_OK) return batch_fail(b, cs, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    return ALS_OK;
+  }
   if (!b->exec[k]) {
     // one graph: the instances' captured cycle graphs as independent child graphs
     auto drop = [&](als_status st, const std::string& msg) {
@@ -1722,6 +2128,41 @@ als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void*
 }
 
 const char* als_batch_last_error(const als_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+als_status als_batch_set_mode(als_batch* b, int mode) {
+  if (!b) return ALS_EINVAL;
+  if (mode != ALS_BATCH_MERGED && mode != ALS_BATCH_BRANCHES) return batch_fail(b, ALS_EINVAL, "unknown batch mode");
+  if (mode == ALS_BATCH_MERGED)
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+      const std::string why = merged_ineligible(b->ctx[i], b->ctx[0]);
+      if (!why.empty())
+        return batch_fail(b, ALS_EINVAL, "instance " + std::to_string(i) + " cannot run merged cycles: " + why);
+    }
+  b->mode = mode;
+  return ALS_OK;
+}
+
+als_status als_batch_get_mode(const als_batch* b, int* mode) {
+  if (!b || !mode) return ALS_EINVAL;
+  *mode = b->mode;
+  return ALS_OK;
+}
+
+als_status als_batch_merged_tune(const als_batch* b, int level, int* products_variant, int* interior_variant,
+                                 float* ms, long long* kernels) {
+  if (!b || !products_variant || !interior_variant) return ALS_EINVAL;
+  const MergedCycle& M = b->merged;
+  if (!M.tuned || level < 1 || level >= M.Lmax) return ALS_EINVAL;
+  *products_variant = M.var_prod[level];
+  *interior_variant = M.var_int[level];
+  if (ms)
+    for (int v = 0; v < 3; ++v) {
+      ms[v] = M.ms_prod[3 * level + v];
+      ms[3 + v] = M.ms_int[3 * level + v];
+    }
+  if (kernels) *kernels = M.exec ? M.kernels : (b->live.exec ? b->live.kernels : 0);
+  return ALS_OK;
+}
 
 als_status als_set_patch_kernel(als_ctx* c, int level, int variant) {
   if (!c) return ALS_EINVAL;

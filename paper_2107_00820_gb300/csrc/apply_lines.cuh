@@ -105,11 +105,11 @@ __device__ __forceinline__ void patch_line(const Geom& g, const PatchIn<T>& pin,
 }
 
 template <typename T, bool TENSOR, int MODE, bool STAGED, bool ZP = false>
-__global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
-                                                     T* __restrict__ y, const T* __restrict__ coef,
-                                                     const T* __restrict__ p_in, T* __restrict__ p_out,
-                                                     long long vstride, T* __restrict__ ebuf,
-                                                     const T* __restrict__ winv, PatchIn<T> pin) {
+__device__ __forceinline__ void apply_lines_body(unsigned bx, const Geom& g, const Colour& col, const CellConst<T>& cc,
+                                                 const T* __restrict__ x, T* __restrict__ y,
+                                                 const T* __restrict__ coef, const T* __restrict__ p_in,
+                                                 T* __restrict__ p_out, long long vstride, T* __restrict__ ebuf,
+                                                 const T* __restrict__ winv, const PatchIn<T>& pin) {
   constexpr int NB = 27, NPR = 4;
   constexpr int NCQ = TENSOR ? Sz<3>::NC : 1;
   constexpr bool RAW = (MODE & OP_RAW) != 0;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
   const int c = lane_ok ? lane / 9 : 0;      // velocity component of the line stages
   const int r = lane_ok ? lane % 9 : 0;
   const int b1 = r % 3, b2 = r / 3;          // the two fixed indices of the lane's line
-  const long long t = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+  const long long t = (long long)bx * (blockDim.x >> 5) + w;
   int cx = 0, cy = 0, cz = 0;
   const bool act = colour_cell(col, t, cx, cy, cz);
   // no node of the cell on the boundary: the per-node Dirichlet tests are skipped (warp-uniform)
@@ -391,4 +391,13 @@ __global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellCon
     }
   }  // NEED_FLUX
   pdl_trigger();
+}
+template <typename T, bool TENSOR, int MODE, bool STAGED, bool ZP = false>
+__global__ void __launch_bounds__(256) k_apply_lines(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
+                                                     T* __restrict__ y, const T* __restrict__ coef,
+                                                     const T* __restrict__ p_in, T* __restrict__ p_out,
+                                                     long long vstride, T* __restrict__ ebuf,
+                                                     const T* __restrict__ winv, PatchIn<T> pin) {
+  apply_lines_body<T, TENSOR, MODE, STAGED, ZP>(blockIdx.x, g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf, winv,
+                                                pin);
 }

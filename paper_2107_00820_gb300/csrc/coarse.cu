@@ -9,11 +9,14 @@
 // the pivot row/column set to U (A_KK to -S).  After every block the matrix holds
 // -A^-1.  A is SPD, so every pivot is a Schur complement and positive.  Each
 // V-cycle then applies the stored inverse as a dense matrix-vector product.
+#include "batch.cuh"
 #include "cell.cuh"
 #include "df64.cuh"
 #include "krylov.h"
 #include "level.h"
 #include "pdl.cuh"
+
+#include <algorithm>
 
 namespace als {
 
@@ -295,8 +298,8 @@ __device__ __forceinline__ int free_dof32(const Geom& g, int f) {
 // Four independent FP64 partial sums per lane (dependent FP64 adds are slow on
 // this GPU), combined in a fixed order.
 template <typename TV, bool STAGE>
-__global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const double* __restrict__ inv,
-                                                      const TV* __restrict__ b, TV* __restrict__ x) {
+__device__ __forceinline__ void coarse_apply_body(unsigned bx, const Geom& g, int nfree, const double* __restrict__ inv,
+                                                  const TV* __restrict__ b, TV* __restrict__ x) {
   extern __shared__ double bs[];
   pdl_wait();
   if (STAGE) {
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const d
     __syncthreads();
   }
   const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int r = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= nfree) return;
   const double* row = inv + (long long)r * nfree;
   auto bv = [&](int c) { return STAGE ? bs[c] : (double)b[free_dof32(g, c)]; };
@@ -320,6 +323,26 @@ __global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const d
   double acc = (a0 + a1) + (a2 + a3);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) x[free_dof32(g, r)] = (TV)acc;
+}
+template <typename TV, bool STAGE>
+__global__ void __launch_bounds__(256) k_coarse_apply(Geom g, int nfree, const double* __restrict__ inv,
+                                                      const TV* __restrict__ b, TV* __restrict__ x) {
+  coarse_apply_body<TV, STAGE>(blockIdx.x, g, nfree, inv, b, x);
+}
+
+// merged launch (batch.cuh), FP32
+struct CoarseArgs {
+  Geom g;
+  int nfree;
+  const double* inv;
+  const float* b;
+  float* x;
+};
+template <bool STAGE>
+__global__ void __launch_bounds__(256) k_coarse_apply_b(const __grid_constant__ BatchTab<CoarseArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const CoarseArgs& a = tb.a[i];
+  coarse_apply_body<float, STAGE>(blockIdx.x - tb.start[i], a.g, a.nfree, a.inv, a.b, a.x);
 }
 
 constexpr size_t kCoarseStageMax = 200 * 1024;   // largest staged right-hand side (bytes)
@@ -350,6 +373,33 @@ void coarse_apply(const LevelDev& L, const CoarseDev& C, int prec, const void* b
   if (prec == PREC_F64) launch_coarse_apply<double>(L, C, (const double*)b, (double*)x, s);
   else launch_coarse_apply<float>(L, C, (const float*)b, (float*)x, s);
   count_launch(1);
+}
+
+// merged: x = 0, then x_free = inv b_free for every item (the staged form when every
+// item's right-hand side fits the staging limit, with room for the largest)
+int batch_coarse_apply(const std::vector<BCoarse>& items, cudaStream_t s) {
+  std::vector<BZero> z;
+  std::vector<CoarseArgs> a;
+  std::vector<unsigned> nb;
+  int maxfree = 0;
+  for (const BCoarse& it : items) {
+    z.push_back(BZero{it.x, it.L->g.N * it.L->g.dim});
+    a.push_back(CoarseArgs{it.L->g, it.C->nfree, (const double*)it.C->inv, (const float*)it.b, (float*)it.x});
+    nb.push_back((unsigned)((it.C->nfree + 7) / 8));
+    maxfree = std::max(maxfree, it.C->nfree);
+  }
+  const int nz = batch_zero(z, s);
+  const size_t smem = (size_t)maxfree * sizeof(double);
+  int n = 0;
+  if (smem <= kCoarseStageMax) n = launch_batch(k_coarse_apply_b<true>, a, nb, 256, smem, s);
+  else n = launch_batch(k_coarse_apply_b<false>, a, nb, 256, 0, s);
+  count_launch(n);
+  return nz + n;
+}
+
+// shared-memory opt-in of the merged staged apply (before any capture)
+void batch_coarse_prepare() {
+  cudaFuncSetAttribute(k_coarse_apply_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseStageMax);
 }
 
 void coarse_free(CoarseDev* C) {

@@ -8,6 +8,7 @@
 
 #include <atomic>
 
+#include "batch.cuh"
 #include "krylov.h"
 #include "level.h"
 #include "reduce.cuh"
@@ -209,13 +210,14 @@ void vec_scale_dev(int prec, long long n, const double* num, const double* den, 
 constexpr int GM_PER = 4;
 
 // V0 = b, |b|^2 -> gmres_start
+// (bx, nb: the block's index and the blocks of this reduction, see batch.cuh)
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* __restrict__ b, T* __restrict__ V0,
-                                                          double* __restrict__ partial, GmresDev sd) {
+__device__ __forceinline__ void gm_start_body(unsigned bx, unsigned nb, unsigned n, const T* __restrict__ b,
+                                              T* __restrict__ V0, double* __restrict__ partial, GmresDev sd) {
   __shared__ T nrm2_s[1];
   const GmresView<T> st = gmres_view<T>(sd);
   T* rows = reinterpret_cast<T*>(partial + 1);
-  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  const unsigned base = bx * (RED_THREADS * GM_PER) + threadIdx.x;
   pdl_wait();
   T v[GM_PER];
 #pragma unroll
@@ -231,24 +233,29 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* _
     acc[0] += v[q] * v[q];
   }
   pdl_trigger();
-  block_partials<T, T>(acc, 1, rows + blockIdx.x);
-  if (last_block(partial)) {
-    finish_sums<T>(partial, 1, nrm2_s);
+  block_partials<T, T>(acc, 1, rows + bx);
+  if (last_block(partial, nb)) {
+    finish_sums_n<T>(partial, 1, nrm2_s, nullptr, (int)nb);
     if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_start(unsigned n, const T* __restrict__ b, T* __restrict__ V0,
+                                                          double* __restrict__ partial, GmresDev sd) {
+  gm_start_body<T>(blockIdx.x, gridDim.x, n, b, V0, partial, sd);
 }
 
 // Gram-Schmidt update of the new column w = V_{j+1} against columns 0..j with the
 // coefficients H[0..j][j] / hn[i], then |w|^2 -> gmres_step(j)
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, const T* __restrict__ V, long long ld,
-                                                         double* __restrict__ partial, GmresDev sd) {
+__device__ __forceinline__ void gm_orth_body(unsigned bx, unsigned nb, unsigned n, int j, const T* __restrict__ V,
+                                             long long ld, double* __restrict__ partial, GmresDev sd) {
   __shared__ T coef[KMAXB];
   __shared__ T nrm2_s[1];
   const GmresView<T> st = gmres_view<T>(sd);
   T* rows = reinterpret_cast<T*>(partial + 1);
   T* w = const_cast<T*>(V) + (long long)(j + 1) * ld;
-  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  const unsigned base = bx * (RED_THREADS * GM_PER) + threadIdx.x;
   T a[GM_PER];
   T vc[GM_PER][KMAXB];
   // columns 0..j come from earlier kernels of the chain (complete before this launch
@@ -280,14 +287,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
     acc[0] += a[q] * a[q];
   }
   pdl_trigger();
-  block_partials<T, T>(acc, 1, rows + blockIdx.x);
-  if (last_block(partial)) {
-    finish_sums<T>(partial, 1, nrm2_s);
+  block_partials<T, T>(acc, 1, rows + bx);
+  if (last_block(partial, nb)) {
+    finish_sums_n<T>(partial, 1, nrm2_s, nullptr, (int)nb);
     if (threadIdx.x == 0) {
       gmres_step(st, j, nrm2_s[0]);
       if (j == st.m - 2) gmres_coeffs(st, j + 1);   // last step: the update's coefficients, once
     }
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, const T* __restrict__ V, long long ld,
+                                                         double* __restrict__ partial, GmresDev sd) {
+  gm_orth_body<T>(blockIdx.x, gridDim.x, n, j, V, ld, partial, sd);
 }
 
 // x = (x_zero ? 0 : x) + sum_j Z_j y_j with y = R^-1 g, and, if t != NULL, the
@@ -295,12 +307,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_orth(unsigned n, int j, cons
 // Arnoldi relation (Q = product of the Givens rotations), no operator apply.  y and
 // u were formed once by the last block of the last k_gm_orth (gmres_coeffs).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, const T* __restrict__ Z,
-                                                           const T* __restrict__ V, long long ld, GmresDev sd,
-                                                           T* __restrict__ x, int x_zero, T* __restrict__ t) {
+__device__ __forceinline__ void gm_update_body(unsigned bx, unsigned n, int k, const T* __restrict__ Z,
+                                               const T* __restrict__ V, long long ld, GmresDev sd,
+                                               T* __restrict__ x, int x_zero, T* __restrict__ t) {
   __shared__ T y[KMAXB], u[KMAXB + 1];
   const GmresView<T> st = gmres_view<T>(sd);
-  const unsigned base = blockIdx.x * (RED_THREADS * GM_PER) + threadIdx.x;
+  const unsigned base = bx * (RED_THREADS * GM_PER) + threadIdx.x;
   // Z, x and V_0..V_{k-1} come from earlier kernels of the chain (complete before this
   // launch began): read through L2 before the wait; V_k and the coefficients come
   // from the predecessor (the last Gram-Schmidt step)
@@ -343,6 +355,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, co
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_gm_update(unsigned n, int k, const T* __restrict__ Z,
+                                                           const T* __restrict__ V, long long ld, GmresDev sd,
+                                                           T* __restrict__ x, int x_zero, T* __restrict__ t) {
+  gm_update_body<T>(blockIdx.x, n, k, Z, V, ld, sd, x, x_zero, t);
+}
 
 static unsigned full_grid(long long n) {
   return (unsigned)((n + RED_THREADS * GM_PER - 1) / (RED_THREADS * GM_PER));
@@ -374,6 +392,82 @@ void gm_update(int prec, long long n, int k, const void* Z, const void* V, long 
     launch_pdl(k_gm_update<float>, full_grid(n), RED_THREADS, 0, s, (unsigned)n, k, (const float*)Z, (const float*)V, ld,
                                                               st, (float*)x, x_zero, (float*)t);
   count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// merged launches (batch.cuh): the same bodies, one launch for all instances
+// ---------------------------------------------------------------------------
+struct GmArgs {
+  unsigned n;
+  int j;
+  const float* b;
+  const float* Z;
+  float* V;
+  long long ld;
+  double* partial;
+  GmresDev st;
+  float* x;
+  int x_zero;
+  float* t;
+};
+
+__global__ void __launch_bounds__(RED_THREADS) k_gm_start_b(const __grid_constant__ BatchTab<GmArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const GmArgs& a = tb.a[i];
+  gm_start_body<float>(blockIdx.x - tb.start[i], tb.start[i + 1] - tb.start[i], a.n, a.b, a.V, a.partial, a.st);
+}
+__global__ void __launch_bounds__(RED_THREADS) k_gm_orth_b(const __grid_constant__ BatchTab<GmArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const GmArgs& a = tb.a[i];
+  gm_orth_body<float>(blockIdx.x - tb.start[i], tb.start[i + 1] - tb.start[i], a.n, a.j, a.V, a.ld, a.partial, a.st);
+}
+__global__ void __launch_bounds__(RED_THREADS) k_gm_update_b(const __grid_constant__ BatchTab<GmArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const GmArgs& a = tb.a[i];
+  gm_update_body<float>(blockIdx.x - tb.start[i], a.n, a.st.s, a.Z, a.V, a.ld, a.st, a.x, a.x_zero, a.t);
+}
+
+struct ZeroArgs {
+  float* x;
+  unsigned n;
+};
+__global__ void __launch_bounds__(256) k_zero_b(const __grid_constant__ BatchTab<ZeroArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const ZeroArgs& a = tb.a[i];
+  pdl_wait();
+  const unsigned e = (blockIdx.x - tb.start[i]) * 1024u + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (e + 256u * q < a.n) a.x[e + 256u * q] = 0.f;
+  pdl_trigger();
+}
+
+static int batch_gm(void (*k)(BatchTab<GmArgs>), const std::vector<BGmres>& items, cudaStream_t s) {
+  std::vector<GmArgs> a;
+  std::vector<unsigned> nb;
+  for (const BGmres& it : items) {
+    a.push_back(GmArgs{(unsigned)it.n, it.j, (const float*)it.b, (const float*)it.Z, (float*)it.V, it.ld, it.partial,
+                       it.st, (float*)it.x, it.x_zero, (float*)it.t});
+    nb.push_back(full_grid(it.n));
+  }
+  const int n = launch_batch(k, a, nb, RED_THREADS, 0, s);
+  count_launch(n);
+  return n;
+}
+int batch_gm_start(const std::vector<BGmres>& items, cudaStream_t s) { return batch_gm(k_gm_start_b, items, s); }
+int batch_gm_orth(const std::vector<BGmres>& items, cudaStream_t s) { return batch_gm(k_gm_orth_b, items, s); }
+int batch_gm_update(const std::vector<BGmres>& items, cudaStream_t s) { return batch_gm(k_gm_update_b, items, s); }
+
+int batch_zero(const std::vector<BZero>& items, cudaStream_t s) {
+  std::vector<ZeroArgs> a;
+  std::vector<unsigned> nb;
+  for (const BZero& it : items) {
+    a.push_back(ZeroArgs{(float*)it.x, (unsigned)it.n});
+    nb.push_back((unsigned)((it.n + 1023) / 1024));
+  }
+  const int n = launch_batch(k_zero_b, a, nb, 256, 0, s);
+  count_launch(n);
+  return n;
 }
 
 // workspace of the smoother's fused reductions: one partial row of KMAXB per block

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace als {
 
 void vec_multiaxpy(int prec, long long n, int k, const void* V, long long ld, const double* h, void* w,
@@ -36,6 +38,15 @@ void coarse_setup(const struct LevelDev& L, double gamma, CoarseDev* C, struct D
                   int df64);
 void coarse_apply(const struct LevelDev& L, const CoarseDev& C, int prec, const void* b, void* x, cudaStream_t s);
 void coarse_free(CoarseDev* C);
+// merged launches over the instances of a batch (FP32; see level.h): coarse_apply of every item
+struct BCoarse {
+  const struct LevelDev* L;
+  const CoarseDev* C;
+  const void* b;
+  void* x;
+};
+int batch_coarse_apply(const std::vector<BCoarse>& items, cudaStream_t s);
+void batch_coarse_prepare();   // before the first capture of a merged coarse apply
 
 }  // namespace als
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -175,5 +177,66 @@ void gm_orth(int prec, long long n, int j, const void* V, long long ld, double* 
 void gm_update(int prec, long long n, int k, const void* Z, const void* V, long long ld, const GmresDev& st,
                void* x, int x_zero, void* t, cudaStream_t s);
 size_t multidot_partial_doubles(int k);
+
+// ---- merged launches over the instances of a batch (batch.cuh).  FP32, order 2, scalar
+// viscosity.  Each call runs one level operation for every item, in one launch per kernel
+// the single-instance operation uses (plus one per kBatchMax items beyond the first
+// kBatchMax), with each item's arithmetic exactly that of the single-instance call named
+// beside it.  Every call returns the number of launches it made.
+struct BApply {            // op_apply_epi (e used), or op_apply(OP_AL) (e ignored)
+  const LevelDev* L;
+  double gamma;
+  const void* x;
+  void* y;
+  ApplyEpi e;
+};
+int batch_apply_epi(const std::vector<BApply>& items, cudaStream_t s);
+int batch_apply_al(const std::vector<BApply>& items, cudaStream_t s);
+struct BPatch {            // star products of the smoother (r -> scratch rows), or the local
+  const LevelDev* L;       // solves on the coarse-cell interiors (r = in, out)
+  const void* r;
+  void* out;
+  const void* den;         // the gather's divisor (batch_patch_gather), may be NULL
+  void* z;                 // the gather's output (batch_patch_gather)
+};
+// variant: the patch-kernel variant of patch_autotune (0 = TMA ring, 2 stages; 1 = 3 stages;
+// 2 = direct loads); every item's interior stars run in it
+int batch_star_products(int variant, const std::vector<BPatch>& items, cudaStream_t s);      // patch_products
+int batch_patch_gather(const std::vector<BPatch>& items, cudaStream_t s);   // the node sums of patch_smooth
+int batch_interior_solve(int variant, const std::vector<BPatch>& items, int subtract, cudaStream_t s);
+struct BTransfer {
+  const LevelDev* coarse;
+  const LevelDev* fine;
+  const void* in;
+  void* out;
+  const void* aux;         // prolong: xadd (out added to it, may be NULL); restrict: sub (may be NULL)
+};
+int batch_prolong(const std::vector<BTransfer>& items, cudaStream_t s);     // prolong_std
+int batch_restrict(const std::vector<BTransfer>& items, cudaStream_t s);    // restrict_std
+struct BGmres {            // gm_start (b, V), gm_orth (V, j), gm_update (Z, V, x, t, x_zero)
+  long long n;
+  const void* b;
+  const void* Z;
+  void* V;
+  long long ld;
+  int j;
+  double* partial;
+  GmresDev st;
+  void* x;
+  int x_zero;
+  void* t;
+};
+int batch_gm_start(const std::vector<BGmres>& items, cudaStream_t s);
+int batch_gm_orth(const std::vector<BGmres>& items, cudaStream_t s);
+int batch_gm_update(const std::vector<BGmres>& items, cudaStream_t s);
+struct BZero {
+  void* x;
+  long long n;             // floats
+};
+int batch_zero(const std::vector<BZero>& items, cudaStream_t s);
+// resident CTAs per SM of a merged star kernel (variant 0, 1, 2 as above; 3: boundary stars)
+int batch_patch_occupancy(int variant);
+// shared-memory opt-ins of the merged star kernels; call before the first capture
+void batch_patch_prepare();
 
 }  // namespace als

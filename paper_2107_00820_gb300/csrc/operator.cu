@@ -10,6 +10,7 @@
 // the identity (y_D = x_D) and Dirichlet columns are masked (x_D treated as 0),
 // which is the constrained operator of Eq. (augstokessys) in the form Firedrake
 // and PETSc use.  B u (Eq. (stokessys)) is cell-local and written directly.
+#include "batch.cuh"
 #include "cell.cuh"
 #include "level.h"
 #include "reduce.cuh"
@@ -99,11 +100,10 @@ __device__ __forceinline__ bool colour_cell(const Colour& col, long long t, int&
 // pressure part of the stress is formed at every point before the transposed
 // contractions take the fluxes back to the nodes.
 template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
-__global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
-                                               T* __restrict__ y, const T* __restrict__ coef,
-                                               const T* __restrict__ p_in, T* __restrict__ p_out,
-                                               long long vstride, T* __restrict__ ebuf,
-                                               const T* __restrict__ winv) {
+__device__ __forceinline__ void apply_body(unsigned bx, const Geom& g, const Colour& col, const CellConst<T>& cc,
+                                           const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ coef,
+                                           const T* __restrict__ p_in, T* __restrict__ p_out, long long vstride,
+                                           T* __restrict__ ebuf, const T* __restrict__ winv) {
   constexpr int NB = Sz<DIM>::NB, NPR = Sz<DIM>::NPR;
   constexpr int CPW = DIM == 2 ? 3 : 1;        // cells per warp
   constexpr int NCQ = TENSOR ? Sz<DIM>::NC : 1;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
   const int base = grp * NB;
   T (*SA)[27] = sh[w][0];
   T (*SB)[27] = sh[w][1];
-  const long long t = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * CPW + grp;
+  const long long t = ((long long)bx * (blockDim.x >> 5) + w) * CPW + grp;
   int cx = 0, cy = 0, cz = 0;
   const bool act = lane_ok && colour_cell(col, t, cx, cy, cz);
   const long long cell = (long long)(unsigned)(cx + g.n[0] * (cy + g.n[1] * cz));
@@ -414,6 +414,14 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> 
   }  // NEED_FLUX
   pdl_trigger();
 }
+template <typename T, int DIM, bool TENSOR, int MODE, bool STAGED>
+__global__ void __launch_bounds__(256) k_apply(Geom g, Colour col, CellConst<T> cc, const T* __restrict__ x,
+                                               T* __restrict__ y, const T* __restrict__ coef,
+                                               const T* __restrict__ p_in, T* __restrict__ p_out,
+                                               long long vstride, T* __restrict__ ebuf,
+                                               const T* __restrict__ winv) {
+  apply_body<T, DIM, TENSOR, MODE, STAGED>(blockIdx.x, g, col, cc, x, y, coef, p_in, p_out, vstride, ebuf, winv);
+}
 
 // y_D = x_D (identity rows) when keep_bnd, else 0; interior rows zeroed.
 template <typename T>
@@ -495,16 +503,21 @@ __device__ __forceinline__ void gather_chunk(const Geom& g, const T* __restrict_
 }
 
 template <typename T, int DIM>
-__global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
-                               int keep_bnd, int raw) {
+__device__ __forceinline__ void gather_cells_body(unsigned bx, const Geom& g, const T* __restrict__ ebuf,
+                                                  const T* __restrict__ x, T* __restrict__ y, int keep_bnd, int raw) {
   pdl_wait();
   RowChunk rc;
-  if (!row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) return;
+  if (!row_chunk(g, DIM, bx * blockDim.x + threadIdx.x, rc)) return;
   T out[GX];
   gather_chunk<T, DIM>(g, ebuf, x, rc, keep_bnd, raw, out);
 #pragma unroll
   for (int q = 0; q < GX; ++q)
     if (GX * rc.j + q < g.nn[0]) y[rc.t0 + q] = out[q];
+}
+template <typename T, int DIM>
+__global__ void k_gather_cells(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
+                               int keep_bnd, int raw) {
+  gather_cells_body<T, DIM>(blockIdx.x, g, ebuf, x, y, keep_bnd, raw);
 }
 
 static unsigned gather_threads(const Geom& g) {
@@ -516,12 +529,11 @@ static unsigned gather_threads(const Geom& g) {
 //   start: |y|^2 starts a GMRES cycle.  Fixed grid and order: reproducible.
 // All sums run in T (in FP32 the GMRES state is float too, see GmresView).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __restrict__ ebuf,
-                                                            const T* __restrict__ x, T* __restrict__ y,
-                                                            const T* __restrict__ b, double sigma, int k,
-                                                            const T* __restrict__ V, long long ld,
-                                                            T* __restrict__ out, int start, GmresDev sd,
-                                                            double* __restrict__ partial) {
+__device__ __forceinline__ void gather_epi_body(unsigned bx, unsigned nb, const Geom& g, const T* __restrict__ ebuf,
+                                                const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ b,
+                                                double sigma, int k, const T* __restrict__ V, long long ld,
+                                                T* __restrict__ out, int start, GmresDev sd,
+                                                double* __restrict__ partial) {
   __shared__ T nrm2_s[1];
   const GmresView<T> st = gmres_view<T>(sd);
   T* rows = reinterpret_cast<T*>(partial + 1);
@@ -530,7 +542,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
 #pragma unroll
   for (int j = 0; j < KMAXB; ++j) acc[j] = T(0);
   RowChunk rc;
-  const bool have = row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc);
+  const bool have = row_chunk(g, DIM, bx * blockDim.x + threadIdx.x, rc);
   // The basis columns come from earlier kernels of the chain, which completed before
   // this launch began (every kernel waits on its predecessor before it lets its
   // successor start): they are read through L2 while the preceding kernel finishes.
@@ -561,15 +573,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __r
     }
   }
   pdl_trigger();
-  block_partials<T, T>(acc, kk, rows + (long long)blockIdx.x * kk);
-  if (last_block(partial)) {
+  block_partials<T, T>(acc, kk, rows + (long long)bx * kk);
+  if (last_block(partial, nb)) {
     if (start) {
-      finish_sums<T>(partial, 1, nrm2_s);
+      finish_sums_n<T>(partial, 1, nrm2_s, nullptr, (int)nb);
       if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
     } else {
-      finish_sums<T>(partial, k, out, st.hn);
+      finish_sums_n<T>(partial, k, out, st.hn, (int)nb);
     }
   }
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(RED_THREADS) k_gather_epi(Geom g, const T* __restrict__ ebuf,
+                                                            const T* __restrict__ x, T* __restrict__ y,
+                                                            const T* __restrict__ b, double sigma, int k,
+                                                            const T* __restrict__ V, long long ld,
+                                                            T* __restrict__ out, int start, GmresDev sd,
+                                                            double* __restrict__ partial) {
+  gather_epi_body<T, DIM>(blockIdx.x, gridDim.x, g, ebuf, x, y, b, sigma, k, V, ld, out, start, sd, partial);
 }
 
 #include "apply_lines.cuh"
@@ -744,6 +765,143 @@ void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void
       else launch_apply_epi<float, 3, false>(L, gamma, x, y, e, s, e0, e1);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// merged launches (batch.cuh): FP32, scalar viscosity, 2D and 3D instances in one launch
+// (the line form for 3D items, the point form for 2D items, as for a single instance)
+// ---------------------------------------------------------------------------
+struct CellArgs {
+  Geom g;
+  Colour col;
+  CellConst<float> cc;
+  const float* x;
+  float* y;
+  const float* coef;
+  float* ebuf;
+  const float* winv;
+  PatchIn<float> pin;
+};
+// ZP: 3D items form x from their star-patch outputs (PatchIn), as op_apply_epi does with
+// ApplyEpi::pout; 2D items never do
+template <int MODE, bool ZP>
+__global__ void __launch_bounds__(256) k_cells_b(const __grid_constant__ BatchTab<CellArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const CellArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i];
+  if (a.g.dim == 3)
+    apply_lines_body<float, false, MODE, true, ZP>(bx, a.g, a.col, a.cc, a.x, a.y, a.coef, nullptr, nullptr, 0,
+                                                   a.ebuf, a.winv, a.pin);
+  else
+    apply_body<float, 2, false, MODE, true>(bx, a.g, a.col, a.cc, a.x, a.y, a.coef, nullptr, nullptr, 0, a.ebuf,
+                                            a.winv);
+}
+
+struct GatherArgs {
+  Geom g;
+  const float* ebuf;
+  const float* x;
+  float* y;
+  const float* b;
+  double sigma;
+  int k, start, keep_bnd;
+  const float* V;
+  long long ld;
+  float* out;
+  GmresDev st;
+  double* partial;
+};
+__global__ void __launch_bounds__(RED_THREADS) k_gather_epi_b(const __grid_constant__ BatchTab<GatherArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const GatherArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i], nb = tb.start[i + 1] - tb.start[i];
+  if (a.g.dim == 3)
+    gather_epi_body<float, 3>(bx, nb, a.g, a.ebuf, a.x, a.y, a.b, a.sigma, a.k, a.V, a.ld, a.out, a.start, a.st,
+                              a.partial);
+  else
+    gather_epi_body<float, 2>(bx, nb, a.g, a.ebuf, a.x, a.y, a.b, a.sigma, a.k, a.V, a.ld, a.out, a.start, a.st,
+                              a.partial);
+}
+__global__ void __launch_bounds__(256) k_gather_cells_b(const __grid_constant__ BatchTab<GatherArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const GatherArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i];
+  if (a.g.dim == 3) gather_cells_body<float, 3>(bx, a.g, a.ebuf, a.x, a.y, a.keep_bnd, 0);
+  else gather_cells_body<float, 2>(bx, a.g, a.ebuf, a.x, a.y, a.keep_bnd, 0);
+}
+
+static CellArgs cell_args(const BApply& it, bool zp) {
+  const LevelDev& L = *it.L;
+  CellArgs a{};
+  a.g = L.g;
+  a.col = all_cells(L.g);
+  a.cc = cell_const<float>(L.g, it.gamma);
+  a.x = (const float*)it.x;
+  a.y = (float*)it.y;
+  a.coef = L.coef32;
+  a.ebuf = (float*)L.ebuf;
+  a.winv = L.winv32;
+  if (zp) a.pin = PatchIn<float>{(const float*)it.e.pout, (const float*)it.e.pden, (float*)it.x};
+  return a;
+}
+static unsigned cell_blocks(const Geom& g) {
+  const long long cpb = g.dim == 2 ? 24 : 8;
+  return (unsigned)((g.ncells + cpb - 1) / cpb);
+}
+
+// the cell kernels of every item: 3D items with star-patch input (e.pout) in the ZP
+// kernel together with the 2D items, the other 3D items in the plain kernel
+template <int MODE>
+static int batch_cells(const std::vector<BApply>& items, bool use_pout, cudaStream_t s) {
+  std::vector<CellArgs> zp, plain;
+  std::vector<unsigned> nzp, nplain;
+  bool any_zp = false;
+  for (const BApply& it : items) any_zp |= use_pout && it.L->g.dim == 3 && it.e.pout;
+  for (const BApply& it : items) {
+    const bool z3 = use_pout && it.L->g.dim == 3 && it.e.pout;
+    if (z3 || (any_zp && it.L->g.dim == 2)) { zp.push_back(cell_args(it, z3)); nzp.push_back(cell_blocks(it.L->g)); }
+    else { plain.push_back(cell_args(it, false)); nplain.push_back(cell_blocks(it.L->g)); }
+  }
+  int n = 0;
+  if (!zp.empty()) n += launch_batch(k_cells_b<MODE, true>, zp, nzp, 256, 0, s);
+  if (!plain.empty()) n += launch_batch(k_cells_b<MODE, false>, plain, nplain, 256, 0, s);
+  return n;
+}
+
+int batch_apply_epi(const std::vector<BApply>& items, cudaStream_t s) {
+  int n = batch_cells<OP_VISC | OP_AL>(items, true, s);
+  std::vector<GatherArgs> a;
+  std::vector<unsigned> nb;
+  for (const BApply& it : items) {
+    const LevelDev& L = *it.L;
+    a.push_back(GatherArgs{L.g, (const float*)L.ebuf, (const float*)it.x, (float*)it.y, (const float*)it.e.b,
+                           it.e.sigma, it.e.k, it.e.start, 1, (const float*)it.e.V, it.e.ld, (float*)it.e.out,
+                           it.e.st, it.e.partial});
+    nb.push_back((gather_threads(L.g) + RED_THREADS - 1) / RED_THREADS);
+  }
+  n += launch_batch(k_gather_epi_b, a, nb, RED_THREADS, 0, s);
+  count_launch(n);
+  return n;
+}
+
+int batch_apply_al(const std::vector<BApply>& items, cudaStream_t s) {
+  int n = batch_cells<OP_AL>(items, false, s);
+  std::vector<GatherArgs> a;
+  std::vector<unsigned> nb;
+  for (const BApply& it : items) {
+    const LevelDev& L = *it.L;
+    GatherArgs g{};
+    g.g = L.g;
+    g.ebuf = (const float*)L.ebuf;
+    g.x = (const float*)it.x;
+    g.y = (float*)it.y;
+    g.keep_bnd = 0;   // OP_AL alone: zero Dirichlet rows, as op_apply
+    a.push_back(g);
+    nb.push_back((gather_threads(L.g) + 255) / 256);
+  }
+  n += launch_batch(k_gather_cells_b, a, nb, 256, 0, s);
+  count_launch(n);
+  return n;
 }
 
 // Several independent FP64 applies of A_gamma (used to form the coarse matrix

@@ -23,6 +23,7 @@
 
 #include "df64.cuh"
 #include "level.h"
+#include "batch.cuh"
 #include "pdl.cuh"
 
 namespace als {
@@ -353,10 +354,12 @@ __device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const
   return true;
 }
 
+// (bx, gx: the block's index and the blocks of this instance, see batch.cuh)
 template <int DIM, int NST>
-__global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
-                                                  const float* __restrict__ r, float* __restrict__ out, int mode,
-                                                  DevStatus* st, int wait_polls, int early_trigger) {
+__device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const Geom& g, const float* __restrict__ inv,
+                                               int interior, int count, const float* __restrict__ r,
+                                               float* __restrict__ out, int mode, DevStatus* st, int wait_polls,
+                                               int early_trigger) {
   using C = TmaCfg<DIM, NST>;
   constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   __syncthreads();
   if (tid == ISSUER)
     for (int i = 0; i < NSTAGE; ++i) {
-      const int grp = blockIdx.x + i * gridDim.x;
+      const int grp = bx + i * gx;
       if (grp < ngroups) issue(grp, i);
     }
   // the first inverse blocks (written only by the setup) are in flight; r comes from
@@ -430,10 +433,10 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   float rpre[RPT];
   PatchPos qcur{}, qnext{};
   if constexpr (PPI == 1) {
-    qnext = patch_pos<DIM>(g, interior, blockIdx.x, count);
+    qnext = patch_pos<DIM>(g, interior, bx, count);
     gather1(qnext, rpre);
   } else {
-    gather(blockIdx.x, rpre);
+    gather(bx, rpre);
   }
 
   const int ps = tid / TPP, b = tid % TPP;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
   bool diag = false;
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
   int it = 0;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+  for (int grp = bx; grp < ngroups; grp += gx, ++it) {
     const int stage = it % NSTAGE;
     const uint32_t parity = (uint32_t)((it / NSTAGE) & 1);
 #pragma unroll
@@ -452,10 +455,10 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // next group's r: in flight while this one is computed
     if constexpr (PPI == 1) {
       qcur = qnext;
-      qnext = patch_pos<DIM>(g, interior, grp + gridDim.x, count);
+      qnext = patch_pos<DIM>(g, interior, grp + gx, count);
       gather1(qnext, rpre);
     } else {
-      gather(grp + gridDim.x, rpre);
+      gather(grp + gx, rpre);
     }
     if (!tma::mbar_wait(&bars[stage], parity, wait_polls)) {
       if (tid == ISSUER) { report(st, 7 /* ALS_ETIMEOUT */, grp); s_fail = 1; }
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     }
     __syncthreads();                        // (B) the stage is consumed, the partials are complete
     if (tid == ISSUER) {                    // refill the stage NSTAGE groups ahead
-      const int nxt = grp + NSTAGE * gridDim.x;
+      const int nxt = grp + NSTAGE * gx;
       if (nxt < ngroups) {
         tma::fence_async();
         issue(nxt, stage);
@@ -532,9 +535,16 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
     // drain: wait (bounded, at the default limit whatever wait_polls is) for every copy
     // this CTA issued and did not consume, so that none is in flight when the CTA exits
     int k = it;
-    for (int grp = blockIdx.x + it * gridDim.x; grp < ngroups && k < it + NSTAGE; grp += gridDim.x, ++k)
+    for (int grp = bx + it * gx; grp < ngroups && k < it + NSTAGE; grp += gx, ++k)
       tma::mbar_wait(&bars[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1));
   }
+}
+
+template <int DIM, int NST>
+__global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
+                                                  const float* __restrict__ r, float* __restrict__ out, int mode,
+                                                  DevStatus* st, int wait_polls, int early_trigger) {
+  patch_tma_body<DIM, NST>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode, st, wait_polls, early_trigger);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,9 +578,9 @@ __device__ __forceinline__ void gather9(const Geom& g, const float* __restrict__
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __restrict__ inv, int interior, int count,
-                                                      const float* __restrict__ r, float* __restrict__ out,
-                                                      int mode) {
+__device__ __forceinline__ void patch_direct_body(unsigned bx, unsigned gx, const Geom& g, const float* __restrict__ inv,
+                                                  int interior, int count, const float* __restrict__ r,
+                                                  float* __restrict__ out, int mode) {
   using C = DirCfg<DIM>;
   constexpr int NP = C::NP, NB = Sz<DIM>::NB, PPC = C::PPC, TPP = C::TPP, NBR = C::NBR;
   constexpr BlockLayout BL = BlockLayout(NP);
@@ -582,7 +592,7 @@ __global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __res
   bool diag = false;
   if (b < BL.nbp) block_of(BL, b, I, J, diag);
   pdl_wait();
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
+  for (int grp = bx; grp < ngroups; grp += gx, buf ^= 1) {
     if (b < BL.nbp) {
       int vx, vy, vz;
       const int v = work_vertex<DIM>(g, interior, grp * PPC + ps, count, vx, vy, vz);
@@ -622,6 +632,13 @@ __global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __res
 }
 
 template <int DIM>
+__global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __restrict__ inv, int interior, int count,
+                                                      const float* __restrict__ r, float* __restrict__ out,
+                                                      int mode) {
+  patch_direct_body<DIM>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode);
+}
+
+template <int DIM>
 static void launch_patch_direct(const LevelDev& L, int interior, long long count, const float* r, float* out, int mode,
                                 cudaStream_t s) {
   using C = DirCfg<DIM>;
@@ -649,15 +666,15 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
 // One warp per boundary star (8 per CTA): the star's packed block and r are staged in
 // shared memory by all lanes (independent loads), then the rows are formed from there.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
-                                                   const int* __restrict__ bvid, const long long* __restrict__ boff,
-                                                   long long nb, const float* __restrict__ r, float* __restrict__ out) {
+__device__ __forceinline__ void patch_bnd_body(unsigned bx, unsigned gx, const Geom& g, const float* __restrict__ bnd32,
+                                               const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                               long long nb, const float* __restrict__ r, float* __restrict__ out) {
   constexpr int NP = Sz<DIM>::NP, NB = Sz<DIM>::NB, MMAX = DIM == 3 ? 27 : 6, SMAX = MMAX * (MMAX + 1) / 2;
   __shared__ float Ss[8][SMAX];
   __shared__ float rs[8][MMAX];
   __shared__ float ys[8][MMAX];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long b = (long long)blockIdx.x * 8 + w; b < nb; b += (long long)gridDim.x * 8) {
+  for (long long b = (long long)bx * 8 + w; b < nb; b += (long long)gx * 8) {
     const int v = __ldg(bvid + b);
     const float* S = bnd32 + __ldg(boff + b);
     int vx, vy, vz;
@@ -689,6 +706,13 @@ __global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restri
   }
   pdl_wait();
   pdl_trigger();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_patch_bnd(Geom g, const float* __restrict__ bnd32,
+                                                   const int* __restrict__ bvid, const long long* __restrict__ boff,
+                                                   long long nb, const float* __restrict__ r, float* __restrict__ out) {
+  patch_bnd_body<DIM>(blockIdx.x, gridDim.x, g, bnd32, bvid, boff, nb, r, out);
 }
 
 template <int DIM>
@@ -944,8 +968,8 @@ __global__ void __launch_bounds__(256) k_patch_apply(Geom g, const TF* __restric
 // first; 4j+1: second and third; 4j+2: fourth; 4j+3: fifth and sixth).  Fixed
 // order; Dirichlet nodes get 0; divided by den[0] when den is given.
 template <typename TV, int DIM>
-__global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
-                               const TV* __restrict__ den) {
+__device__ __forceinline__ void patch_gather_body(unsigned bx, const Geom& g, const TV* __restrict__ out,
+                                                  TV* __restrict__ z, const TV* __restrict__ den) {
   __shared__ TV inv_den;
   pdl_wait();
   if (den) {                        // one division per block, not per entry
@@ -953,7 +977,7 @@ __global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restric
     __syncthreads();
   }
   RowChunk rc;
-  if (!row_chunk(g, DIM, blockIdx.x * blockDim.x + threadIdx.x, rc)) return;
+  if (!row_chunk(g, DIM, bx * blockDim.x + threadIdx.x, rc)) return;
   const int nn0 = g.nn[0];
   TV acc[GX];
 #pragma unroll
@@ -1001,6 +1025,12 @@ __global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restric
     if (den) vq *= inv_den;
     z[rc.t0 + q] = vq;
   }
+}
+
+template <typename TV, int DIM>
+__global__ void k_patch_gather(Geom g, const TV* __restrict__ out, TV* __restrict__ z,
+                               const TV* __restrict__ den) {
+  patch_gather_body<TV, DIM>(blockIdx.x, g, out, z, den);
 }
 
 static unsigned row_gather_blocks(const Geom& g, int dim) {
@@ -1136,6 +1166,198 @@ void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* 
     if (fine.g.dim == 2) launch_patch_variant<2>(v, fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
     else launch_patch_variant<3>(v, fine, 1, nc, (const float*)in, (float*)out, md, fine.status, s);
   }
+}
+
+// ---------------------------------------------------------------------------
+// merged launches (batch.cuh): FP32, 2D and 3D instances in one launch.  The
+// persistent kernels (TMA ring, direct loads, boundary stars) give every instance a
+// share of the launch's blocks in proportion to its star groups, so that the launch
+// fills the resident CTAs of the GPU once; within its share an instance's blocks
+// stride over its groups exactly as a single-instance launch does over its grid.
+// ---------------------------------------------------------------------------
+struct PatchArgs {
+  Geom g;
+  const float* inv;
+  int wl, count;
+  const float* r;
+  float* out;
+  int mode;
+  DevStatus* st;
+  int wait_polls, early;
+  // boundary stars
+  const float* bnd32;
+  const int* bvid;
+  const long long* boff;
+  long long nb;
+  // gather
+  const float* den;
+};
+
+template <int NST>
+__global__ void __launch_bounds__(64) k_patch_tma_b(const __grid_constant__ BatchTab<PatchArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const PatchArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i], gx = tb.start[i + 1] - tb.start[i];
+  if (a.g.dim == 3) patch_tma_body<3, NST>(bx, gx, a.g, a.inv, a.wl, a.count, a.r, a.out, a.mode, a.st, a.wait_polls, a.early);
+  else patch_tma_body<2, NST>(bx, gx, a.g, a.inv, a.wl, a.count, a.r, a.out, a.mode, a.st, a.wait_polls, a.early);
+}
+__global__ void __launch_bounds__(128) k_patch_direct_b(const __grid_constant__ BatchTab<PatchArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const PatchArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i], gx = tb.start[i + 1] - tb.start[i];
+  if (a.g.dim == 3) patch_direct_body<3>(bx, gx, a.g, a.inv, a.wl, a.count, a.r, a.out, a.mode);
+  else patch_direct_body<2>(bx, gx, a.g, a.inv, a.wl, a.count, a.r, a.out, a.mode);
+}
+__global__ void __launch_bounds__(256) k_patch_bnd_b(const __grid_constant__ BatchTab<PatchArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const PatchArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i], gx = tb.start[i + 1] - tb.start[i];
+  if (a.g.dim == 3) patch_bnd_body<3>(bx, gx, a.g, a.bnd32, a.bvid, a.boff, a.nb, a.r, a.out);
+  else patch_bnd_body<2>(bx, gx, a.g, a.bnd32, a.bvid, a.boff, a.nb, a.r, a.out);
+}
+__global__ void __launch_bounds__(256) k_patch_gather_b(const __grid_constant__ BatchTab<PatchArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const PatchArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i];
+  if (a.g.dim == 3) patch_gather_body<float, 3>(bx, a.g, a.r, a.out, a.den);
+  else patch_gather_body<float, 2>(bx, a.g, a.r, a.out, a.den);
+}
+
+template <int NST>
+static size_t tma_b_smem() {
+  return std::max(TmaCfg<2, NST>::smem_bytes, TmaCfg<3, NST>::smem_bytes);
+}
+
+// resident CTAs per SM of a merged patch kernel (variant 0, 1: TMA ring; 2: direct; 3: boundary)
+static int batch_per_sm(int variant) {
+  static int cache[4] = {-1, -1, -1, -1};
+  if (cache[variant] >= 0) return cache[variant];
+  int v = 0;
+  cudaError_t e = cudaSuccess;
+  if (variant == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_patch_tma_b<2>, 64, tma_b_smem<2>());
+  else if (variant == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_patch_tma_b<3>, 64, tma_b_smem<3>());
+  else if (variant == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_patch_direct_b, 128, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_patch_bnd_b, 256, 0);
+  if (e != cudaSuccess) { cudaGetLastError(); v = 1; }
+  cache[variant] = v < 1 ? 1 : v;
+  return cache[variant];
+}
+int batch_patch_occupancy(int variant) { return batch_per_sm(variant); }
+
+// shared-memory opt-in of the merged TMA-ring kernels (before any capture)
+void batch_patch_prepare() {
+  cudaFuncSetAttribute(k_patch_tma_b<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_b_smem<2>());
+  cudaFuncSetAttribute(k_patch_tma_b<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_b_smem<3>());
+  for (int v = 0; v < 4; ++v) batch_per_sm(v);
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+  }
+  return n;
+}
+
+// stars per iteration of a variant's CTA for an instance of dimension dim
+static int stars_per_group(int variant, int dim) {
+  if (variant == 2) return dim == 3 ? DirCfg<3>::PPC : DirCfg<2>::PPC;
+  return dim == 3 ? TmaCfg<3, 2>::PPI : TmaCfg<2, 2>::PPI;
+}
+
+// one merged launch of a variant's kernel over (item, wl, count, mode); early: the
+// boundary-star launch follows
+static int launch_patch_b(int variant, const std::vector<PatchArgs>& a, cudaStream_t s) {
+  std::vector<long long> work;
+  for (const PatchArgs& x : a) {
+    const int ppg = stars_per_group(variant, x.g.dim);
+    work.push_back(((long long)x.count + ppg - 1) / ppg);
+  }
+  const long long per_sm = batch_per_sm(variant);
+  const long long cap = (long long)sm_count() * (variant == 2 ? 8 : per_sm);
+  const std::vector<unsigned> nb = persistent_shares(work, (long long)sm_count() * per_sm, cap);
+  if (variant == 2) return launch_batch(k_patch_direct_b, a, nb, 128, 0, s);
+  if (variant == 1) return launch_batch(k_patch_tma_b<3>, a, nb, 64, tma_b_smem<3>(), s);
+  return launch_batch(k_patch_tma_b<2>, a, nb, 64, tma_b_smem<2>(), s);
+}
+
+static PatchArgs patch_args(const LevelDev& L, int wl, long long count, const void* r, void* out, int mode) {
+  PatchArgs a{};
+  a.g = L.g;
+  a.inv = L.inv32;
+  a.wl = wl | (L.split ? 2 : 0);
+  a.count = (int)count;
+  a.r = (const float*)r;
+  a.out = (float*)out;
+  a.mode = mode;
+  a.st = L.status;
+  a.wait_polls = L.wait_polls;
+  a.bnd32 = L.bnd32;
+  a.bvid = L.bvid;
+  a.boff = L.boff;
+  a.nb = L.nbnd;
+  return a;
+}
+
+int batch_star_products(int variant, const std::vector<BPatch>& items, cudaStream_t s) {
+  std::vector<PatchArgs> a, bnd;
+  std::vector<long long> bwork;
+  for (const BPatch& it : items) {
+    const LevelDev& L = *it.L;
+    a.push_back(patch_args(L, 0, L.split ? L.nint : L.g.nverts, it.r, it.out, OUT_SCRATCH));
+    if (L.split && L.nbnd > 0) {
+      bnd.push_back(a.back());
+      bwork.push_back((L.nbnd + 7) / 8);
+    }
+  }
+  // the TMA-ring kernel lets the boundary-star kernel start once its dependency wait returned
+  if (variant != 2 && !bnd.empty())
+    for (PatchArgs& x : a) x.early = 1;
+  int n = launch_patch_b(variant, a, s);
+  if (!bnd.empty()) {
+    const std::vector<unsigned> nb = persistent_shares(bwork, (long long)sm_count() * batch_per_sm(3), 152LL * 16);
+    n += launch_batch(k_patch_bnd_b, bnd, nb, 256, 0, s);
+  }
+  count_launch(n);
+  return n;
+}
+
+int batch_patch_gather(const std::vector<BPatch>& items, cudaStream_t s) {
+  std::vector<PatchArgs> a;
+  std::vector<unsigned> nb;
+  for (const BPatch& it : items) {
+    PatchArgs x{};
+    x.g = it.L->g;
+    x.r = (const float*)it.out;   // the scratch rows of the star products
+    x.out = (float*)it.z;
+    x.den = (const float*)it.den;
+    a.push_back(x);
+    nb.push_back(row_gather_blocks(it.L->g, it.L->g.dim));
+  }
+  const int n = launch_batch(k_patch_gather_b, a, nb, 256, 0, s);
+  count_launch(n);
+  return n;
+}
+
+int batch_interior_solve(int variant, const std::vector<BPatch>& items, int subtract, cudaStream_t s) {
+  std::vector<PatchArgs> a;
+  std::vector<BZero> z;
+  for (const BPatch& it : items) {
+    const Geom& g = it.L->g;
+    const long long nc = (long long)(g.n[0] / 2) * (g.n[1] / 2) * (g.dim == 3 ? g.n[2] / 2 : 1);
+    a.push_back(patch_args(*it.L, 1, nc, it.r, it.out, subtract ? OUT_SUBTRACT : OUT_WRITE));
+    if (!subtract) z.push_back(BZero{it.out, g.N * g.dim});
+  }
+  int n = 0;
+  if (!z.empty()) n += batch_zero(z, s);   // counted there
+  const int m = launch_patch_b(variant, a, s);
+  count_launch(m);
+  return n + m;
 }
 
 // Autotuner: times each FP32 patch-kernel variant on this level (one warm-up and

@@ -50,24 +50,25 @@ __device__ __forceinline__ void block_partials(const A (&acc)[KMAXB], int kk, R*
   __syncthreads();
 }
 
-// called right after block_partials (whose writers fenced their partials)
-__device__ __forceinline__ bool last_block(double* ws) {
+// called right after block_partials (whose writers fenced their partials); nb = the
+// blocks taking part in this reduction (the grid, or an instance's share of a merged launch)
+__device__ __forceinline__ bool last_block(double* ws, unsigned nb) {
   __shared__ bool is_last;
-  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned int*>(ws), 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned int*>(ws), 1u) == nb - 1;
   __syncthreads();
   return is_last;
 }
+__device__ __forceinline__ bool last_block(double* ws) { return last_block(ws, gridDim.x); }
 
 // Run by every thread of the last block: out[j] = (sum over blocks of column j) / div[j]
 // (div NULL: no division; div[j] == 0 gives 0).  The partials (type R, rows from
 // ws + 1) are read through L2 (other blocks wrote them), each thread over a fixed
 // strided subset, then one fixed block reduction per group of KMAXB columns, in R.
 template <typename R = double>
-__device__ __forceinline__ void finish_sums(double* ws, int k, R* out, const R* div = nullptr) {
+__device__ __forceinline__ void finish_sums_n(double* ws, int k, R* out, const R* div, int nb) {
   if (threadIdx.x == 0) __threadfence();
   __syncthreads();
   const R* partial = reinterpret_cast<const R*>(ws + 1);
-  const int nb = gridDim.x;
   for (int j0 = 0; j0 < k; j0 += KMAXB) {
     const int kk = (k - j0) < KMAXB ? (k - j0) : KMAXB;
     R acc[KMAXB];
@@ -90,6 +91,10 @@ __device__ __forceinline__ void finish_sums(double* ws, int k, R* out, const R* 
     __syncthreads();
   }
   if (threadIdx.x == 0) *reinterpret_cast<unsigned int*>(ws) = 0u;
+}
+template <typename R = double>
+__device__ __forceinline__ void finish_sums(double* ws, int k, R* out, const R* div = nullptr) {
+  finish_sums_n<R>(ws, k, out, div, (int)gridDim.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 // (-1/8, 3/4, 3/8) at 3/4, tensorised over the axes.  Dirichlet rows (fine
 // boundary) and columns (coarse boundary) are zero.  Both directions are
 // gathers (one thread per output value), so they need no atomics.
+#include "batch.cuh"
 #include "level.h"
 #include "pdl.cuh"
 
@@ -56,9 +57,10 @@ __device__ __forceinline__ void decode(const Geom& g, unsigned t, int dim, int& 
 // The 1D weights are dyadic (1, 3/4, 3/8, -1/8), so they and their products are
 // exact in either precision; the sums run in the vector's precision T.
 template <typename T, int DIM>
-__global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+__device__ __forceinline__ void prolong_body(unsigned bx, const Geom& gc, const Geom& gf, const T* __restrict__ xc,
+                                             T* __restrict__ xf, T* __restrict__ xadd) {
   pdl_wait();
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned t = bx * blockDim.x + threadIdx.x;
   if (t >= (unsigned)(gf.N * DIM)) return;
   int c, i, j, k;
   decode(gf, t, DIM, c, i, j, k);
@@ -87,11 +89,16 @@ __global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restr
   xf[t] = acc;
   if (xadd) xadd[t] += acc;
 }
+template <typename T, int DIM>
+__global__ void k_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+  prolong_body<T, DIM>(blockIdx.x, gc, gf, xc, xf, xadd);
+}
 
 template <typename T, int DIM>
-__global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub, T* __restrict__ rc) {
+__device__ __forceinline__ void restrict_body(unsigned bx, const Geom& gc, const Geom& gf, const T* __restrict__ rf,
+                                              const T* __restrict__ sub, T* __restrict__ rc) {
   pdl_wait();
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned t = bx * blockDim.x + threadIdx.x;
   if (t >= (unsigned)(gc.N * DIM)) return;
   int c, i, j, k;
   decode(gc, t, DIM, c, i, j, k);
@@ -125,6 +132,32 @@ __global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* 
       acc += wy[cy] * wz[cz] * part;
     }
   rc[t] = acc;
+}
+template <typename T, int DIM>
+__global__ void k_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub, T* __restrict__ rc) {
+  restrict_body<T, DIM>(blockIdx.x, gc, gf, rf, sub, rc);
+}
+
+// merged launches (batch.cuh), FP32, 2D and 3D instances together
+struct TransferArgs {
+  Geom gc, gf;
+  const float* in;
+  float* out;
+  float* aux;
+};
+__global__ void __launch_bounds__(256) k_prolong_b(const __grid_constant__ BatchTab<TransferArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const TransferArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i];
+  if (a.gf.dim == 3) prolong_body<float, 3>(bx, a.gc, a.gf, a.in, a.out, a.aux);
+  else prolong_body<float, 2>(bx, a.gc, a.gf, a.in, a.out, a.aux);
+}
+__global__ void __launch_bounds__(256) k_restrict_b(const __grid_constant__ BatchTab<TransferArgs> tb) {
+  const int i = batch_slot(tb, blockIdx.x);
+  const TransferArgs& a = tb.a[i];
+  const unsigned bx = blockIdx.x - tb.start[i];
+  if (a.gf.dim == 3) restrict_body<float, 3>(bx, a.gc, a.gf, a.in, a.aux, a.out);
+  else restrict_body<float, 2>(bx, a.gc, a.gf, a.in, a.aux, a.out);
 }
 
 void prolong_std(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
@@ -165,6 +198,30 @@ void restrict_std(const LevelDev& coarse, const LevelDev& fine, int prec, const 
     else launch_pdl(k_restrict<float, 3>, b, 256, 0, s, coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
   }
   count_launch(1);
+}
+
+int batch_prolong(const std::vector<BTransfer>& items, cudaStream_t s) {
+  std::vector<TransferArgs> a;
+  std::vector<unsigned> nb;
+  for (const BTransfer& it : items) {
+    a.push_back(TransferArgs{it.coarse->g, it.fine->g, (const float*)it.in, (float*)it.out, (float*)it.aux});
+    nb.push_back((unsigned)((it.fine->g.N * it.fine->g.dim + 255) / 256));
+  }
+  const int n = launch_batch(k_prolong_b, a, nb, 256, 0, s);
+  count_launch(n);
+  return n;
+}
+
+int batch_restrict(const std::vector<BTransfer>& items, cudaStream_t s) {
+  std::vector<TransferArgs> a;
+  std::vector<unsigned> nb;
+  for (const BTransfer& it : items) {
+    a.push_back(TransferArgs{it.coarse->g, it.fine->g, (const float*)it.in, (float*)it.out, (float*)it.aux});
+    nb.push_back((unsigned)((it.coarse->g.N * it.coarse->g.dim + 255) / 256));
+  }
+  const int n = launch_batch(k_restrict_b, a, nb, 256, 0, s);
+  count_launch(n);
+  return n;
 }
 
 }  // namespace als

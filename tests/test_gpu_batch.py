@@ -23,11 +23,14 @@ def _instances(mode):
     return pbs, ins, opts
 
 
+@pytest.mark.parametrize("bmode", [A.ALS_BATCH_MERGED, A.ALS_BATCH_BRANCHES])
 @pytest.mark.parametrize("mode", [A.ALS_MODE_FP64, A.ALS_MODE_MIXED])
-def test_batch_solve_equals_single_solves(mode):
+def test_batch_solve_equals_single_solves(mode, bmode):
     from paper_2107_00820_gb300 import Batch
     pbs, ins, opts = _instances(mode)
     batch = Batch(ins)
+    assert batch.mode == A.ALS_BATCH_MERGED   # every instance qualifies
+    batch.set_mode(bmode)
     ub, pb_, infos = batch.solve([pb.f for pb in pbs], [pb.u_bc for pb in pbs])
     for i, pb in enumerate(pbs):
         ctx = context(pb, **opts)
@@ -45,11 +48,13 @@ def test_batch_solve_equals_single_solves(mode):
     batch.close()
 
 
+@pytest.mark.parametrize("bmode", [A.ALS_BATCH_MERGED, A.ALS_BATCH_BRANCHES])
 @pytest.mark.parametrize("prec", [A.ALS_PREC_FP64, A.ALS_PREC_FP32])
-def test_batch_cycle_equals_single_cycles(prec):
+def test_batch_cycle_equals_single_cycles(prec, bmode):
     from paper_2107_00820_gb300 import Batch
     pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
     batch = Batch(ins)
+    batch.set_mode(bmode)
     dt = torch.float64 if prec == A.ALS_PREC_FP64 else torch.float32
     rng = np.random.default_rng(35)
     bs = [dev(rng.standard_normal(s[0]), dt) for s in batch.shapes]
@@ -65,4 +70,57 @@ def test_batch_cycle_equals_single_cycles(prec):
     xs2 = [torch.zeros_like(b) for b in bs]
     batch.vcycle(bs, xs2, prec)
     assert all(torch.equal(a, b) for a, b in zip(xs, xs2))
+    batch.close()
+
+
+def test_merged_cycle_launches_and_tuning():
+    """The merged FP32 cycle issues one launch per level operation for all instances:
+    far fewer kernels than the instances' own cycles together, each level index's
+    star-kernel variants timed and the fastest kept."""
+    from paper_2107_00820_gb300 import Batch
+    pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
+    batch = Batch(ins)
+    rng = np.random.default_rng(36)
+    bs = [dev(rng.standard_normal(s[0]), torch.float32) for s in batch.shapes]
+    xs = [torch.zeros_like(b) for b in bs]
+    n0 = A.als_kernel_launches()
+    batch.vcycle(bs, xs, A.ALS_PREC_FP32)
+    merged = A.als_kernel_launches() - n0
+    lmax = max(pb.levels for pb in pbs)
+    for level in range(1, lmax):
+        pv, iv, ms, kern = batch.merged_tune(level)
+        assert pv in (0, 1, 2) and iv in (0, 1, 2)
+        assert ms[pv] == min(ms[:3]) and ms[3 + iv] == min(ms[3:])
+        assert kern == merged
+    with pytest.raises(A.ALSError):
+        batch.merged_tune(lmax)
+    batch.set_mode(A.ALS_BATCH_BRANCHES)
+    n0 = A.als_kernel_launches()
+    batch.vcycle(bs, xs, A.ALS_PREC_FP32)
+    branches = A.als_kernel_launches() - n0
+    # one launch per operation and level index, against one per operation, level and instance
+    assert merged < branches / 2, (merged, branches)
+    batch.close()
+
+
+def test_merged_mode_refused_for_an_ineligible_instance():
+    from paper_2107_00820_gb300 import Batch
+    pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
+    ins[2] = dict(ins[2], options=dict(opts, cycle=A.ALS_CYCLE_F))
+    batch = Batch(ins)
+    assert batch.mode == A.ALS_BATCH_BRANCHES
+    with pytest.raises(A.ALSError, match="instance 2 cannot run merged cycles: F-cycle"):
+        batch.set_mode(A.ALS_BATCH_MERGED)
+    with pytest.raises(A.ALSError, match="unknown batch mode"):
+        batch.set_mode(7)
+    # the F-cycle instance still cycles (as a graph branch) like its own context
+    rng = np.random.default_rng(37)
+    bs = [dev(rng.standard_normal(s[0]), torch.float32) for s in batch.shapes]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch.vcycle(bs, xs, A.ALS_PREC_FP32)
+    ctx = context(pbs[2], **dict(opts, cycle=A.ALS_CYCLE_F))
+    x = torch.zeros_like(bs[2])
+    ctx.vcycle(bs[2], x, A.ALS_PREC_FP32)
+    assert torch.equal(x, xs[2])
+    ctx.close()
     batch.close()
