@@ -33,6 +33,11 @@ import sys
 import tempfile
 import time
 
+# A batch runs its instances' FGMRES kernels on one stream per instance and its merged
+# cycles on one stream per group; with the default 8 hardware work queues those streams
+# share queues and wait behind one another's event waits.  Set before CUDA starts.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -635,8 +640,11 @@ def ours(args, dist):
 def ours_batch(args, dist):
     """Serving-style sweep: 64 independent multi-sinker instances (32 2D, 32 3D, uneven
     sizes, contrasts 1e4..1e8, gamma 1e2 / 1e4), mixed precision with the P2 Schur
-    pairing.  Batched solves (interleaved FGMRES rounds, one wait per round) and
-    batched cycles (one graph launch) against one-at-a-time calls on the same contexts."""
+    pairing.  Batched solves (interleaved FGMRES rounds, one wait per round) whose
+    preconditioner cycles run as one merged launch per level operation for all live
+    instances (the headline), against the same batch with the instances' own cycle
+    graphs as concurrent branches, and against one-at-a-time calls on the same contexts;
+    the same three forms for bare FP32 cycles."""
     import numpy as np
     import torch
 
@@ -674,6 +682,7 @@ def ours_batch(args, dist):
         torch.cuda.synchronize()
         return max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - w0) / reps
 
+    merged_mode = batch.mode == A.ALS_BATCH_MERGED
     clocks = ClockSampler(dist.local)
     clocks.start()
     launches0 = A.als_kernel_launches()
@@ -683,17 +692,39 @@ def ours_batch(args, dist):
     infos = batch.solve(f, ubc, None, u, p)[2]
     u_b = [x.clone() for x in u]
 
+    # the same batch with the instances' own cycle graphs as concurrent branches
+    batch.set_mode(A.ALS_BATCH_BRANCHES)
+    batch.solve(f, ubc, None, u, p)                            # captures the instances' graphs
+    t_branch = dist.max(timed(lambda: batch.solve(f, ubc, None, u, p), 1))
+    same_branch = all(torch.equal(a, b) for a, b in zip(u_b, u))
+
     def one_at_a_time():
         for i, c in enumerate(ctxs):
             c.solve(f[i], ubc[i], None, u[i], p[i])
     t_seq = dist.max(timed(one_at_a_time, 1))
     same = all(torch.equal(a, b) for a, b in zip(u_b, u))
 
-    # cycles: one batched graph launch against the instances' own graph launches
+    # FP32 cycles: merged launches, the graph of the instances' cycle graphs, one at a time
     b32 = [torch.randn(s[0], dtype=torch.float32, device="cuda") for s in batch.shapes]
     x32 = [torch.zeros_like(t) for t in b32]
     batch.vcycle(b32, x32, A.ALS_PREC_FP32)
     t_bcyc = timed(lambda: batch.vcycle(b32, x32, A.ALS_PREC_FP32), 5)
+    t_mcyc, merged_kernels, merged_tune = None, None, {}
+    if merged_mode:
+        batch.set_mode(A.ALS_BATCH_MERGED)
+        batch.vcycle(b32, x32, A.ALS_PREC_FP32)
+        t_mcyc = timed(lambda: batch.vcycle(b32, x32, A.ALS_PREC_FP32), 5)
+        grouping, groups, gms, merged_kernels = batch.merged_plan()
+        names = ("one group", "by dimension", "by dimension and levels")
+        merged_tune = {"grouping": names[grouping], "groups": groups,
+                       "cycle_ms_per_grouping": {names[k]: (round(v, 3) if v >= 0 else None) for k, v in enumerate(gms)},
+                       "variants": {}}
+        vn = ("tma2", "tma3", "direct")
+        for g in range(groups):
+            members = batch.merged_tune(g, 1)[3]
+            for lvl in range(1, max(pbs[i].levels for i in members)):
+                pv, iv, ms, _ = batch.merged_tune(g, lvl)
+                merged_tune["variants"][f"group{g}/level{lvl}"] = f"{vn[pv]}/{vn[iv]}"
 
     def seq_cycles():
         for i, c in enumerate(ctxs):
@@ -714,14 +745,21 @@ def ours_batch(args, dist):
         "config": {"workload": "batch64", "instances": len(pbs), "dim_mix": "32 2D (16^2..256^2) + 32 3D (8^3..32^3)",
                    "dr": "10^U[4,8]", "gamma": "{1e2, 1e4}", "schur": "P2 (W = M_p(1/mu))", "rtol": RTOL,
                    "total_dofs": total, "step": "batched FGMRES solves of all instances (setup excluded)",
+                   "cycle_form": "merged (one launch per level operation)" if merged_mode else "branches",
                    "l2": "inputs larger than L2 (all instances' patch inverses ~10^10 B)",
                    "parallelism": f"replicas x{dist.world}"},
+        "branches": {"ms": t_branch * 1e3, "dof_per_s": total / t_branch, "bitwise_equal_to_merged": same_branch},
         "one_at_a_time": {"ms": t_seq * 1e3, "dof_per_s": total / t_seq, "bitwise_equal_to_batched": same},
         "batched_vs_one_at_a_time": t_seq / t_batch,
-        "cycles": {"batched_ms": t_bcyc * 1e3, "one_at_a_time_ms": t_scyc * 1e3, "speedup": t_scyc / t_bcyc,
-                   "prec": "fp32"},
+        "merged_vs_branches": t_branch / t_batch,
+        "cycles": {"merged_ms": t_mcyc * 1e3 if t_mcyc else None, "branches_ms": t_bcyc * 1e3,
+                   "one_at_a_time_ms": t_scyc * 1e3,
+                   "merged_vs_one_at_a_time": t_scyc / t_mcyc if t_mcyc else None,
+                   "branches_vs_one_at_a_time": t_scyc / t_bcyc,
+                   "merged_kernels_per_cycle": merged_kernels, "prec": "fp32"},
         "iterations": {"min": min(its), "max": max(its), "mean": statistics.mean(its),
                        "all_converged": all(int(x.converged) == 1 for x in infos)},
+        "merged_autotuner": merged_tune,
         "autotuner_choices": {("tma2", "tma3", "direct")[k]: v for k, v in sorted(tuned.items())},
         "create_s": t_create,
         "gpu_launches": launches,

@@ -378,38 +378,53 @@ const char* als_batch_last_error(const als_batch* batch);
 
 /* Execution form of a batch's FP32 multigrid cycles (those of als_batch_vcycle with
  * prec FP32, and the preconditioner cycles of a mixed-mode als_batch_solve):
- *   ALS_BATCH_MERGED    one launch per level operation for all instances: every
- *                       operator apply, star-product sweep, transfer, GMRES step and
- *                       the coarse solve of the instances' V-cycles runs as one merged
+ *   ALS_BATCH_MERGED    one launch per level operation for each group of instances:
+ *                       every operator apply, star-product sweep, transfer, GMRES step
+ *                       and the coarse solve of the group's V-cycles runs as one merged
  *                       kernel launch whose grid is the flattened (instance, tile) work
- *                       list; the hierarchies are aligned at their coarsest level, the
- *                       whole merged cycle is captured as one CUDA graph, and an
- *                       autotuner picks the star-kernel variant of every merged level
- *                       operation (each instance's cycle of Sec. 4 unchanged).
+ *                       list; the hierarchies of a group are aligned at their coarsest
+ *                       level, each group's merged cycle is captured as a CUDA graph and
+ *                       the groups run as independent branches of one graph (see
+ *                       als_batch_merged_plan for the grouping and the autotuner); each
+ *                       instance's cycle of Sec. 4 is unchanged.
  *   ALS_BATCH_BRANCHES  one graph launch whose independent branches are the
  *                       instances' own captured cycles (solves: one stream each).
  * Every instance's results are bitwise those of its single-instance calls in both
  * forms.  MERGED needs, in every instance: order 2, scalar viscosity, the GMRES
  * smoother with at most 8 steps, the V-cycle, kernel timing off, and the sweeps and
  * transfer of instance 0; a mixed-mode solve also needs the full block factorisation
- * (ALS_FACT_FULL), else the solve runs in the BRANCHES form.  als_batch_create picks
- * MERGED when every instance qualifies.  als_batch_set_mode returns ALS_EINVAL for an
- * unknown mode or, for MERGED, when an instance does not qualify (the message says
- * which and why).  als_batch_get_mode reads the mode. */
+ * (ALS_FACT_FULL), else the solve runs in the BRANCHES form.  A merged solve joins
+ * each group's cycles with its instances' own streams by events, so a batch wants
+ * more hardware work queues than the default 8 (CUDA_DEVICE_MAX_CONNECTIONS=32 in
+ * the environment before CUDA starts).  als_batch_create picks MERGED when every
+ * instance qualifies.  als_batch_set_mode returns ALS_EINVAL for an unknown mode or,
+ * for MERGED, when an instance does not qualify (the message says which and why).
+ * als_batch_get_mode reads the mode. */
 enum { ALS_BATCH_MERGED = 0, ALS_BATCH_BRANCHES = 1 };
 als_status als_batch_set_mode(als_batch* batch, int mode);
 als_status als_batch_get_mode(const als_batch* batch, int* mode);
 
-/* Autotuner record of the merged cycle (built on the first merged FP32 cycle or
- * solve): for level index `level` (0 = coarsest, 1 <= level < the largest level
- * count), the star-kernel variant chosen for the merged star products and for the
- * merged interior solves (0: TMA ring, 2 stages; 1: 3 stages; 2: direct loads) and,
- * if ms is not NULL, the measured time per launch of each variant (ms[0..2]:
- * products, ms[3..5]: interior solves).  *kernels (optional): kernel launches of one
- * merged cycle.  ALS_EINVAL: NULL batch or outputs, level out of range, or no merged
- * cycle built yet. */
-als_status als_batch_merged_tune(const als_batch* batch, int level, int* products_variant, int* interior_variant,
-                                 float* ms, long long* kernels);
+/* Plan of the merged cycles (made on the first merged FP32 cycle or mixed solve):
+ * the instances are split into groups, each group's cycles merged into one launch
+ * per level operation, and the groups' captured cycles run as independent branches
+ * of one graph, so that one group's latency-bound coarse levels overlap another's
+ * bandwidth-bound fine levels.  The autotuner builds and times (three cycles, CUDA
+ * events) each grouping that gives a distinct partition -- 0: one group, 1: by
+ * dimension, 2: by dimension and level count -- and keeps the fastest; within a
+ * group it times the three star-kernel variants of every merged star-product and
+ * interior-solve launch (0: TMA ring, 2 stages; 1: 3 stages; 2: direct loads).
+ * als_batch_merged_plan: the chosen grouping, the number of groups, ms[3] (optional)
+ * the measured time per cycle of each grouping (-1: not built, same partition as an
+ * earlier one), *kernels (optional) the kernel launches of one merged cycle of the
+ * whole batch.  als_batch_merged_tune: for group `group` and level index `level`
+ * (0 = coarsest, 1 <= level < the group's largest level count), the variants chosen
+ * for the merged star products and interior solves, ms[6] (optional) the time per
+ * launch of each variant (products, then interior solves), and instances (optional,
+ * room for count entries) the batch indices of the group's instances in order.
+ * ALS_EINVAL: NULL batch or required output, index out of range, or no plan yet. */
+als_status als_batch_merged_plan(const als_batch* batch, int* grouping, int* groups, float* ms, long long* kernels);
+als_status als_batch_merged_tune(const als_batch* batch, int group, int level, int* products_variant,
+                                 int* interior_variant, float* ms, int* instances);
 
 /* Autotuner record of a smoothed level (1 <= level < levels).  Before the FP32
  * cycle is first captured, each level times its FP32 star-patch kernel variants

@@ -94,8 +94,10 @@ SIGNATURES = {
     "als_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "als_batch_set_mode": (c_int, [c_void_p, c_int]),
     "als_batch_get_mode": (c_int, [c_void_p, POINTER(c_int)]),
-    "als_batch_merged_tune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_float),
+    "als_batch_merged_plan": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_float),
                                       POINTER(ctypes.c_longlong)]),
+    "als_batch_merged_tune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_int),
+                                      POINTER(ctypes.c_float), POINTER(c_int)]),
     "als_autotune_info": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(ctypes.c_float)]),
     "als_set_patch_kernel": (c_int, [c_void_p, c_int, c_int]),
     "als_load_patch_inverses": (c_int, [c_void_p, c_int, c_void_p]),
@@ -459,12 +461,20 @@ class Batch:
     def set_mode(self, mode):
         self._check(self._lib.als_batch_set_mode(self._b, int(mode)))
 
-    def merged_tune(self, level):
-        """(products variant, interior variant, ms[6], kernels per merged cycle) of level index `level`."""
-        pv, iv, kern = c_int(), c_int(), ctypes.c_longlong()
+    def merged_plan(self):
+        """(grouping, groups, ms per grouping [3], kernels of one merged cycle of the batch)."""
+        g, n, kern = c_int(), c_int(), ctypes.c_longlong()
+        ms = (ctypes.c_float * 3)()
+        self._check(self._lib.als_batch_merged_plan(self._b, byref(g), byref(n), ms, byref(kern)))
+        return g.value, n.value, list(ms), kern.value
+
+    def merged_tune(self, group, level):
+        """(products variant, interior variant, ms[6], batch indices of the group's instances)."""
+        pv, iv = c_int(), c_int()
         ms = (ctypes.c_float * 6)()
-        self._check(self._lib.als_batch_merged_tune(self._b, int(level), byref(pv), byref(iv), ms, byref(kern)))
-        return pv.value, iv.value, list(ms), kern.value
+        idx = (c_int * self.count)(*([-1] * self.count))
+        self._check(self._lib.als_batch_merged_tune(self._b, int(group), int(level), byref(pv), byref(iv), ms, idx))
+        return pv.value, iv.value, list(ms), [i for i in idx if i >= 0]
 
     def instance(self, i):
         """Instance i as a Context (owned by the batch: closing it does nothing)."""

@@ -1842,6 +1842,80 @@ als_status merged_build(MergedCycle& M, cudaStream_t s, std::string& err) {
   return ALS_OK;
 }
 
+// A plan of merged cycles: the instances split into groups, each group's cycles merged
+// (one launch per level operation for the group), the groups' captured cycles run as
+// independent branches of one graph, so that one group's latency-bound levels overlap
+// another's bandwidth-bound ones.  Groupings: 0 = one group, 1 = by dimension, 2 = by
+// dimension and level count.
+constexpr int kGroupings = 3;
+struct MergedPlan {
+  int grouping = -1;
+  std::vector<MergedCycle> g;
+  cudaGraph_t tmpl = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+std::vector<std::vector<int>> plan_groups(const std::vector<als_ctx*>& inst, int grouping) {
+  std::vector<std::vector<int>> out;
+  std::vector<long long> keys;
+  for (int i = 0; i < (int)inst.size(); ++i) {
+    const long long key = grouping == 0 ? 0 : (grouping == 1 ? inst[i]->dim : 100LL * inst[i]->dim + inst[i]->L);
+    size_t k = 0;
+    while (k < keys.size() && keys[k] != key) ++k;
+    if (k == keys.size()) {
+      keys.push_back(key);
+      out.emplace_back();
+    }
+    out[k].push_back(i);
+  }
+  return out;
+}
+
+void plan_free(MergedPlan& P) {
+  for (MergedCycle& M : P.g) merged_free(M);
+  P.g.clear();
+  if (P.exec) cudaGraphExecDestroy(P.exec);
+  if (P.tmpl) cudaGraphDestroy(P.tmpl);
+  P.exec = nullptr;
+  P.tmpl = nullptr;
+  P.kernels = 0;
+  P.grouping = -1;
+}
+
+// build (tune, capture) every group of a grouping and the graph of their branches
+als_status plan_build(MergedPlan& P, const std::vector<als_ctx*>& inst, int grouping, cudaStream_t s,
+                      std::string& err) {
+  plan_free(P);
+  P.grouping = grouping;
+  for (const std::vector<int>& grp : plan_groups(inst, grouping)) {
+    P.g.emplace_back();
+    for (int i : grp) P.g.back().inst.push_back(inst[i]);
+  }
+  for (MergedCycle& M : P.g) ALS_TRY(merged_build(M, s, err));
+  if (cudaGraphCreate(&P.tmpl, 0) != cudaSuccess) {
+    err = "merged plan: graph create";
+    cudaGetLastError();
+    return ALS_ECUDA;
+  }
+  for (MergedCycle& M : P.g) {
+    cudaGraphNode_t node;
+    if (cudaGraphAddChildGraphNode(&node, P.tmpl, nullptr, 0, M.tmpl) != cudaSuccess) {
+      err = "merged plan: child graph node";
+      cudaGetLastError();
+      return ALS_ECUDA;
+    }
+    P.kernels += M.kernels;
+  }
+  if (cudaGraphInstantiate(&P.exec, P.tmpl, 0) != cudaSuccess) {
+    err = "merged plan: graph instantiate";
+    cudaGetLastError();
+    P.exec = nullptr;
+    return ALS_ECUDA;
+  }
+  return ALS_OK;
+}
+
 }  // namespace
 
 struct als_batch {
@@ -1851,14 +1925,16 @@ struct als_batch {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   std::string err;
   int mode = ALS_BATCH_BRANCHES;
-  MergedCycle merged;                // every instance (als_batch_vcycle)
-  MergedCycle live;                  // the unfinished instances of a batched solve
+  MergedPlan plan;                   // every instance (als_batch_vcycle), grouping chosen by time
+  float plan_ms[kGroupings] = {-1.f, -1.f, -1.f};   // measured cycle time of each grouping
+  std::vector<MergedCycle> live;     // per group of the plan: its unfinished instances (solves)
   std::vector<cudaEvent_t> ev;       // per instance: joins of the merged cycles of a solve
-  cudaEvent_t mev = nullptr;
-  cudaStream_t mstream = nullptr;    // where the merged cycles run
+  std::vector<cudaEvent_t> gev;      // per group
+  std::vector<cudaStream_t> gs;      // per group: where its merged cycles run
+  cudaStream_t mstream = nullptr;    // where the plan's graph runs
 };
 
-// stream and events of the merged cycles (created on first use)
+// streams and events of the merged cycles (created on first use)
 static als_status batch_merged_init(als_batch* b) {
   if (b->mstream) return ALS_OK;
   if (cudaStreamCreateWithFlags(&b->mstream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1869,7 +1945,72 @@ static als_status batch_merged_init(als_batch* b) {
   }
   b->ev.assign(b->ctx.size(), nullptr);
   for (cudaEvent_t& e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&b->mev, cudaEventDisableTiming);
+  return ALS_OK;
+}
+
+// The plan of the batch's merged cycles (first use): every grouping that gives a new
+// partition is built and timed over three cycles (CUDA events, after one warm-up
+// cycle) on the instances' current right-hand sides, and the fastest is kept.
+static als_status batch_plan(als_batch* b) {
+  if (b->plan.exec) return ALS_OK;
+  ALS_TRY(batch_merged_init(b));
+  const cudaStream_t s = b->mstream;
+  static bool prepared = false;
+  if (!prepared) {
+    batch_patch_prepare();
+    batch_coarse_prepare();
+    prepared = true;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<size_t> seen;
+  float best = 1e30f;
+  int best_g = 0;
+  for (int grouping = 0; grouping < kGroupings; ++grouping) {
+    const size_t ng = plan_groups(b->ctx, grouping).size();
+    if (std::find(seen.begin(), seen.end(), ng) != seen.end()) continue;   // the same partition
+    seen.push_back(ng);
+    MergedPlan P;
+    als_status st = plan_build(P, b->ctx, grouping, s, b->err);
+    if (st == ALS_OK) {
+      for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        if (cudaGraphLaunch(P.exec, s) != cudaSuccess) st = ALS_ECUDA;
+      }
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = ALS_ECUDA;
+    }
+    if (st != ALS_OK) {
+      plan_free(P);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (b->err.empty()) b->err = "merged plan tuning failed";
+      return st == ALS_OK ? ALS_ECUDA : st;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->plan_ms[grouping] = ms / 3.f;
+    if (ms < best) {
+      best = ms;
+      best_g = grouping;
+    }
+    plan_free(P);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ALS_TRY(plan_build(b->plan, b->ctx, best_g, s, b->err));
+  b->gev.assign(b->plan.g.size(), nullptr);
+  b->gs.assign(b->plan.g.size(), nullptr);
+  for (size_t k = 0; k < b->plan.g.size(); ++k) {
+    cudaEventCreateWithFlags(&b->gev[k], cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&b->gs[k], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      b->err = "batch stream creation failed";
+      return ALS_ECUDA;
+    }
+  }
+  b->live.assign(b->plan.g.size(), MergedCycle{});
   return ALS_OK;
 }
 
@@ -1904,7 +2045,6 @@ als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* 
   bool all = true;
   for (als_ctx* c : b->ctx) all = all && merged_ineligible(c, b->ctx[0]).empty();
   b->mode = all ? ALS_BATCH_MERGED : ALS_BATCH_BRANCHES;
-  b->merged.inst = b->ctx;
   *out = b;
   return ALS_OK;
 }
@@ -1917,10 +2057,15 @@ als_status als_batch_destroy(als_batch* b) {
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
     if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
   }
-  merged_free(b->merged);
-  merged_free(b->live);
+  for (cudaStream_t gs : b->gs)
+    if (gs) cudaStreamSynchronize(gs);
+  plan_free(b->plan);
+  for (MergedCycle& M : b->live) merged_free(M);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
-  if (b->mev) cudaEventDestroy(b->mev);
+  for (cudaEvent_t e : b->gev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t gs : b->gs)
+    if (gs) cudaStreamDestroy(gs);
   if (b->mstream) cudaStreamDestroy(b->mstream);
   for (als_ctx* c : b->ctx) als_destroy(c);
   delete b;
@@ -1954,54 +2099,70 @@ als_status als_batch_solve(als_batch* b, const double* const* f_qp, const double
   // per preconditioner application, see precond_mixed_phase)
   bool merged = b->mode == ALS_BATCH_MERGED;
   for (als_ctx* c : b->ctx) merged = merged && c->opt.mode == ALS_MODE_MIXED && c->opt.fact == ALS_FACT_FULL;
+  std::vector<MergedCycle*> cur;   // per group: the graph its cycles run in (the plan's, at first)
   if (merged) {
-    const als_status ms = batch_merged_init(b);
-    if (ms != ALS_OK) return ms;
+    const als_status ps = batch_plan(b);
+    if (ps != ALS_OK) return ps;
+    for (MergedCycle& F : b->plan.g) cur.push_back(&F);
   }
   for (;;) {
     bool any = false;
     if (merged) {
-      std::vector<int> act;
-      for (int i = 0; i < n; ++i)
-        if (live[i] && !b->ctx[i]->run.done) act.push_back(i);
-      if (act.empty()) break;
-      std::vector<als_ctx*> set;
-      for (int i : act) set.push_back(b->ctx[i]);
-      const cudaStream_t ms = b->mstream;
-      if (!b->merged.tuned) {     // the full set's tuning serves every live subset
-        b->merged.Lmax = 0;
-        for (als_ctx* c : b->merged.inst) b->merged.Lmax = std::max(b->merged.Lmax, c->L);
-        batch_patch_prepare();
-        batch_coarse_prepare();
-        merged_tune(b->merged, ms);
-      }
-      if (set != b->live.inst) {
-        merged_free(b->live);
-        b->live.inst = set;
-        b->live.var_prod = b->merged.var_prod;
-        b->live.var_int = b->merged.var_int;
-        b->live.tuned = true;
-      }
-      const als_status bs = merged_build(b->live, ms, b->err);
-      if (bs != ALS_OK) return bs;
-      for (int phase = 0; phase < 2; ++phase) {
+      // per group of the plan: its unfinished instances' two merged cycles, on the
+      // group's stream, joined with those instances' own streams by events
+      for (size_t k = 0; k < b->plan.g.size(); ++k) {
+        std::vector<als_ctx*> set;
+        std::vector<int> act;
+        for (als_ctx* c : b->plan.g[k].inst) {
+          const int i = (int)(std::find(b->ctx.begin(), b->ctx.end(), c) - b->ctx.begin());
+          if (live[i] && !c->run.done) {
+            set.push_back(c);
+            act.push_back(i);
+          }
+        }
+        if (set.empty()) continue;
+        // The group's graph is re-captured for its unfinished instances only once the
+        // finished ones it still cycles (their results unused) hold more than a quarter
+        // of its fine-level unknowns: capture and instantiation cost milliseconds, and
+        // instances finish one by one.  The group's tuning serves every subset of it.
+        long long all = 0, done = 0;
+        for (als_ctx* c : cur[k]->inst) {
+          const long long w = c->lev[c->L - 1].g.N;
+          all += w;
+          if (std::find(set.begin(), set.end(), c) == set.end()) done += w;
+        }
+        const cudaStream_t gs = b->gs[k];
+        if (4 * done > all) {
+          MergedCycle& M = b->live[k];
+          merged_free(M);
+          M.inst = set;
+          M.var_prod = b->plan.g[k].var_prod;
+          M.var_int = b->plan.g[k].var_int;
+          M.tuned = true;
+          const als_status bs = merged_build(M, gs, b->err);
+          if (bs != ALS_OK) return bs;
+          cur[k] = &M;
+        }
+        const MergedCycle& M = *cur[k];
+        for (int phase = 0; phase < 2; ++phase) {
+          for (int i : act) {
+            als_ctx* c = b->ctx[i];
+            if (phase > 0) cudaStreamWaitEvent(c->stream, b->gev[k], 0);
+            precond_mixed_phase(c, phase);
+            cudaEventRecord(b->ev[i], c->stream);
+            cudaStreamWaitEvent(gs, b->ev[i], 0);
+          }
+          if (cudaGraphLaunch(M.exec, gs) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
+          count_launch(M.kernels);
+          cudaEventRecord(b->gev[k], gs);
+        }
         for (int i : act) {
           als_ctx* c = b->ctx[i];
-          if (phase > 0) cudaStreamWaitEvent(c->stream, b->mev, 0);
-          precond_mixed_phase(c, phase);
-          cudaEventRecord(b->ev[i], c->stream);
-          cudaStreamWaitEvent(ms, b->ev[i], 0);
+          cudaStreamWaitEvent(c->stream, b->gev[k], 0);
+          precond_mixed_phase(c, 2);
         }
-        if (cudaGraphLaunch(b->live.exec, ms) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
-        count_launch(b->live.kernels);
-        cudaEventRecord(b->mev, ms);
+        any = true;
       }
-      for (int i : act) {
-        als_ctx* c = b->ctx[i];
-        cudaStreamWaitEvent(c->stream, b->mev, 0);
-        precond_mixed_phase(c, 2);
-      }
-      any = true;
     } else {
       for (int i = 0; i < n; ++i) {
         if (!live[i] || b->ctx[i]->run.done) continue;
@@ -2044,15 +2205,15 @@ als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void*
     const cudaStream_t s = b->mstream;
     cudaEventRecord(b->ctx[0]->order_ev, b->user_stream);
     cudaStreamWaitEvent(s, b->ctx[0]->order_ev, 0);
-    const als_status st = merged_build(b->merged, s, b->err);
-    if (st != ALS_OK) return st;
     for (int i = 0; i < n; ++i) {
       als_ctx* c = b->ctx[i];
       const int l = c->L - 1;
       cudaMemcpyAsync(c->w32.b[l], bv[i], (size_t)(c->lev[l].g.N * c->dim) * 4, cudaMemcpyDeviceToDevice, s);
     }
-    if (cudaGraphLaunch(b->merged.exec, s) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
-    count_launch(b->merged.kernels);
+    const als_status st = batch_plan(b);   // first call: groupings built and timed (the cycle reads b only)
+    if (st != ALS_OK) return st;
+    if (cudaGraphLaunch(b->plan.exec, s) != cudaSuccess) return batch_fail(b, ALS_ECUDA, "merged cycle launch");
+    count_launch(b->plan.kernels);
     for (int i = 0; i < n; ++i) {
       als_ctx* c = b->ctx[i];
       const int l = c->L - 1;
@@ -2148,11 +2309,23 @@ als_status als_batch_get_mode(const als_batch* b, int* mode) {
   return ALS_OK;
 }
 
-als_status als_batch_merged_tune(const als_batch* b, int level, int* products_variant, int* interior_variant,
-                                 float* ms, long long* kernels) {
+als_status als_batch_merged_plan(const als_batch* b, int* grouping, int* groups, float* ms, long long* kernels) {
+  if (!b || !grouping || !groups) return ALS_EINVAL;
+  if (!b->plan.exec) return ALS_EINVAL;
+  *grouping = b->plan.grouping;
+  *groups = (int)b->plan.g.size();
+  if (ms)
+    for (int k = 0; k < kGroupings; ++k) ms[k] = b->plan_ms[k];
+  if (kernels) *kernels = b->plan.kernels;
+  return ALS_OK;
+}
+
+als_status als_batch_merged_tune(const als_batch* b, int group, int level, int* products_variant,
+                                 int* interior_variant, float* ms, int* instances) {
   if (!b || !products_variant || !interior_variant) return ALS_EINVAL;
-  const MergedCycle& M = b->merged;
-  if (!M.tuned || level < 1 || level >= M.Lmax) return ALS_EINVAL;
+  if (!b->plan.exec || group < 0 || group >= (int)b->plan.g.size()) return ALS_EINVAL;
+  const MergedCycle& M = b->plan.g[group];
+  if (level < 1 || level >= M.Lmax) return ALS_EINVAL;
   *products_variant = M.var_prod[level];
   *interior_variant = M.var_int[level];
   if (ms)
@@ -2160,7 +2333,9 @@ als_status als_batch_merged_tune(const als_batch* b, int level, int* products_va
       ms[v] = M.ms_prod[3 * level + v];
       ms[3 + v] = M.ms_int[3 * level + v];
     }
-  if (kernels) *kernels = M.exec ? M.kernels : (b->live.exec ? b->live.kernels : 0);
+  if (instances)
+    for (size_t i = 0; i < M.inst.size(); ++i)
+      instances[i] = (int)(std::find(b->ctx.begin(), b->ctx.end(), M.inst[i]) - b->ctx.begin());
   return ALS_OK;
 }
 

@@ -74,9 +74,10 @@ def test_batch_cycle_equals_single_cycles(prec, bmode):
 
 
 def test_merged_cycle_launches_and_tuning():
-    """The merged FP32 cycle issues one launch per level operation for all instances:
-    far fewer kernels than the instances' own cycles together, each level index's
-    star-kernel variants timed and the fastest kept."""
+    """The merged FP32 cycle issues one launch per level operation for each group of
+    instances: far fewer kernels than the instances' own cycles together.  The plan's
+    tuner timed every distinct grouping and kept the fastest; within each group every
+    level's star-kernel variants were timed and the fastest kept."""
     from paper_2107_00820_gb300 import Batch
     pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
     batch = Batch(ins)
@@ -86,20 +87,41 @@ def test_merged_cycle_launches_and_tuning():
     n0 = A.als_kernel_launches()
     batch.vcycle(bs, xs, A.ALS_PREC_FP32)
     merged = A.als_kernel_launches() - n0
-    lmax = max(pb.levels for pb in pbs)
-    for level in range(1, lmax):
-        pv, iv, ms, kern = batch.merged_tune(level)
-        assert pv in (0, 1, 2) and iv in (0, 1, 2)
-        assert ms[pv] == min(ms[:3]) and ms[3 + iv] == min(ms[3:])
-        assert kern == merged
-    with pytest.raises(A.ALSError):
-        batch.merged_tune(lmax)
-    batch.set_mode(A.ALS_BATCH_BRANCHES)
-    n0 = A.als_kernel_launches()
-    batch.vcycle(bs, xs, A.ALS_PREC_FP32)
-    branches = A.als_kernel_launches() - n0
-    # one launch per operation and level index, against one per operation, level and instance
-    assert merged < branches / 2, (merged, branches)
+    grouping, groups, ms, kern = batch.merged_plan()
+    assert kern == merged
+    # SPECS: two dimensions, four distinct (dimension, levels) pairs
+    assert [x > 0 for x in ms] == [True, True, True]
+    assert ms[grouping] == min(ms) and groups == (1, 2, 4)[grouping]
+    seen = []
+    for g in range(groups):
+        members = batch.merged_tune(g, 1)[3]
+        seen += members
+        lmax = max(pbs[i].levels for i in members)
+        for level in range(1, lmax):
+            pv, iv, t, _ = batch.merged_tune(g, level)
+            assert pv in (0, 1, 2) and iv in (0, 1, 2)
+            assert t[pv] == min(t[:3]) and t[3 + iv] == min(t[3:])
+        with pytest.raises(A.ALSError):
+            batch.merged_tune(g, lmax)
+    assert sorted(seen) == list(range(len(pbs)))
+    # one launch per operation and level index per group: a group costs the kernels of
+    # its deepest instance's own cycle, plus the zeroing launches that replace the
+    # single-instance memsets (coarse solve, one interior solve per level)
+    single = []
+    for i in range(len(pbs)):
+        ctx = batch.instance(i)
+        x = torch.zeros_like(bs[i])
+        ctx.vcycle(bs[i], x, A.ALS_PREC_FP32)
+        n0 = A.als_kernel_launches()
+        ctx.vcycle(bs[i], x, A.ALS_PREC_FP32)
+        single.append(A.als_kernel_launches() - n0)
+    bound = 0
+    for g in range(groups):
+        members = batch.merged_tune(g, 1)[3]
+        bound += max(single[i] for i in members) + max(pbs[i].levels for i in members) + 1
+    assert merged <= bound, (merged, bound, single)
+    if groups < len(pbs):
+        assert bound < sum(single), (bound, single)
     batch.close()
 
 
