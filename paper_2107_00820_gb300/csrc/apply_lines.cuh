@@ -144,6 +144,30 @@ __device__ __forceinline__ void apply_lines_body(unsigned bx, const Geom& g, con
 #pragma unroll
     for (int k = 0; k < 3; ++k) grad[a][k] = T(0);
   pdl_wait();
+  // Tensor C (FP32): the cell's 27 x 21 Mandel entries are contiguous; the warp stages them
+  // in shared memory with coalesced loads (issued here, beside stage X's loads), and the
+  // point stage reads its 21 entries from there (stride 21: every lane a different bank)
+  // instead of each lane loading 21 words 84 bytes apart.  (FP64 would exceed the 48 KB
+  // of static shared memory per block; it keeps the direct loads.)
+  constexpr bool STAGE_C = TENSOR && VISC && sizeof(T) == 4;
+  constexpr int CSZ = NB * NCQ;
+  __shared__ T shC[STAGE_C ? 8 : 1][STAGE_C ? CSZ : 1];
+  if constexpr (STAGE_C) {
+    if (act) {
+      const T* src = coef + cell * CSZ;
+      T v[(CSZ + 31) / 32];
+#pragma unroll
+      for (int k = 0; k < (CSZ + 31) / 32; ++k) {
+        const int e = lane + 32 * k;
+        v[k] = e < CSZ ? __ldg(src + e) : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < (CSZ + 31) / 32; ++k) {
+        const int e = lane + 32 * k;
+        if (e < CSZ) shC[w][e] = v[k];
+      }
+    }
+  }
 
   if constexpr (NEED_U) {
     // stage X: lane (c, ay = b1, az = b2) loads the x-line of component c
@@ -279,7 +303,10 @@ __device__ __forceinline__ void apply_lines_body(unsigned bx, const Geom& g, con
     for (int q = 0; q < NPR; ++q) iso += pi[q] * psi[q];
     T sg[3][3];
     if constexpr (VISC) {
-      if (act && lane_ok) stress<T, 3, TENSOR>(coef + (cell * NB + p) * NCQ, grad, iso, sg);
+      if (act && lane_ok) {
+        if constexpr (STAGE_C) stress<T, 3, true>(&shC[w][p * NCQ], grad, iso, sg);
+        else stress<T, 3, TENSOR>(coef + (cell * NB + p) * NCQ, grad, iso, sg);
+      }
       else {
 #pragma unroll
         for (int a = 0; a < 3; ++a)

@@ -70,6 +70,29 @@ def test_apply_agamma_tensor_fp64(d):
     assert rel(host(y), lv.A @ x) <= 1e-12
 
 
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 5)])
+def test_apply_agamma_tensor_fp32(d, n):
+    """a2 in FP32 (the mixed cycle's operator): the 3D cell kernel stages each cell's
+    27 x 21 coefficients in shared memory; element-wise against the oracle on the same
+    FP32-rounded input, at FP32 rounding."""
+    rng = np.random.default_rng(17)
+    nm = 3 if d == 2 else 6
+    ncells, nq = n ** d, 3 ** d
+    M = rng.standard_normal((ncells, nq, nm, nm))
+    C = np.einsum("cqij,cqkj->cqik", M, M) + 0.5 * np.eye(nm)
+    iu = np.triu_indices(nm)
+    Cp = np.ascontiguousarray(C[:, :, iu[0], iu[1]])
+    mu_eff = np.ascontiguousarray(C[:, :, 0, 0] / 2)
+    from paper_2107_00820_gb300 import Context
+    ctx = Context(d, n, 1, [Cp], 10.0, mu_eff=[mu_eff])
+    lv = Level(d, n, Cp, 10.0, kind="tensor", mu_eff=mu_eff)
+    x = rng.standard_normal(lv.mesh.nu)
+    y = torch.zeros(lv.mesh.nu, dtype=torch.float32, device="cuda")
+    ctx.apply_agamma(dev(x, torch.float32), y, 0, A.ALS_PREC_FP32)
+    ref = lv.A @ x.astype(np.float32).astype(np.float64)
+    assert rel(host(y), ref) <= 2e-5
+
+
 @pytest.mark.parametrize("d,n", [(2, 8), (3, 4)])
 def test_apply_stokes_fp64(d, n):
     pb = sinker(d, n, 2, 1e2, dr=1e4, seed=4)
