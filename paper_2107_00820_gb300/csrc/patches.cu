@@ -915,6 +915,14 @@ size_t setup_tab_bytes(int dim) {
 // ---------------------------------------------------------------------------
 // K4: y_v = A_v^-1 r|_v, one warp per patch; rows by lanes, diagonals in order
 // ---------------------------------------------------------------------------
+// y = A r for a symmetric A packed by diagonals, one warp, rows by lanes, over the
+// wrapped diagonals t = 0 .. NP-1: row i takes the entry (i, (i + t) mod NP), which is
+// entry i of diagonal t while i + t < NP and entry i + t - NP of diagonal NP - t after
+// (the symmetric partner), so every (i, j) is used exactly once and every lane of a row
+// chunk does useful work at every t (NP^2 products for NP^2 lane-FMAs, where a pass over
+// the NP diagonals in both directions would issue 2 NP^2 with half the lanes idle; the FP64
+// pipe is this kernel's bound).  Both segments of a wrapped diagonal are contiguous, so the
+// loads stay coalesced.
 template <typename TF, typename TV, int DIM>
 __device__ __forceinline__ void patch_gemv(const TF* __restrict__ S, const TV* rs, int lane, TV (&acc)[(Sz<DIM>::NP + 31) / 32]) {
   constexpr int NP = Sz<DIM>::NP, R = (NP + 31) / 32;
@@ -922,13 +930,15 @@ __device__ __forceinline__ void patch_gemv(const TF* __restrict__ S, const TV* r
   for (int k = 0; k < R; ++k) acc[k] = TV(0);
 #pragma unroll 3
   for (int t = 0; t < NP; ++t) {
-    const TF* d = S + diag_start(NP, t);
+    const TF* du = S + diag_start(NP, t);                                 // (i, i + t), i < NP - t
+    const TF* dl = S + (t > 0 ? diag_start(NP, NP - t) - (NP - t) : 0);  // (i + t - NP, i), i >= NP - t
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int i = lane + 32 * k;
       if (i < NP) {
-        if (i + t < NP) acc[k] += (TV)d[i] * rs[i + t];
-        if (t > 0 && i >= t) acc[k] += (TV)d[i - t] * rs[i - t];
+        const int j = i + t;
+        const bool up = j < NP;
+        acc[k] += (TV)(up ? du[i] : dl[i]) * rs[up ? j : j - NP];
       }
     }
   }
