@@ -78,6 +78,7 @@ enum { ALS_SCHUR_P1 = 0, ALS_SCHUR_P2 = 1 };
 enum { ALS_CYCLE_V = 0, ALS_CYCLE_F = 1 };
 enum { ALS_FACT_FULL = 0, ALS_FACT_UPPER = 1, ALS_FACT_LOWER = 2, ALS_FACT_DIAG = 3 };
 enum { ALS_SETUP_AUTO = 0, ALS_SETUP_FP64 = 1 };
+enum { ALS_STORE_FP32 = 0, ALS_STORE_BF16 = 1 };
 
 /* Unit box (0,1)^dim with n[k] cells per direction on the finest level;
  * n[k] must be divisible by 2^(levels-1) and the coarsest level must have
@@ -126,6 +127,18 @@ typedef struct {
                      viscosity; nodes 3n+1 per direction, 4 x 4 Gauss points per cell (point
                      data [cell][16]), pressure [cell][6] coefficients of {1, xi, eta, xi^2,
                      xi eta, eta^2}, vertex stars of 5 x 5 nodes (50 dofs) inverted in FP64) */
+  int store;      /* storage of the star inverses the FP32 cycle streams: ALS_STORE_FP32
+                     (default), or ALS_STORE_BF16: the block-packed stars (every star, or the
+                     interior ones on levels stored split) rounded to bfloat16 to nearest,
+                     widened to FP32 on load, every product and sum in FP32 (the optional
+                     reduced-precision variant of the scope); boundary stars of split levels,
+                     the FP64 cycle and the setup are unchanged.  It halves the smoother's
+                     bytes but keeps about 3 significant digits of each inverse, so it is
+                     an opt-in for mild problems: with the P2 pairing the FGMRES counts held
+                     at DR 1e4 (2D and 3D) and, in 2D, up to DR 1e8 at gamma 1e3 (+3), but
+                     the 3D 32^3 solve at DR 1e8, gamma 1e4 did not converge; with P1 it
+                     costs a few iterations at DR 1e4 and does not converge from DR 1e6.
+                     Order 2 only. */
 } als_options;
 
 typedef struct {

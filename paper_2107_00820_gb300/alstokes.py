@@ -29,6 +29,7 @@ ALS_SCHUR_P1, ALS_SCHUR_P2 = 0, 1
 ALS_CYCLE_V, ALS_CYCLE_F = 0, 1
 ALS_FACT_FULL, ALS_FACT_UPPER, ALS_FACT_LOWER, ALS_FACT_DIAG = 0, 1, 2, 3
 ALS_SETUP_AUTO, ALS_SETUP_FP64 = 0, 1
+ALS_STORE_FP32, ALS_STORE_BF16 = 0, 1
 ALS_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -43,7 +44,7 @@ class als_coeff(Structure):
 class als_options(Structure):
     _fields_ = [("smoother", c_int), ("sweeps", c_int), ("tau", c_double), ("transfer", c_int),
                 ("schur", c_int), ("mode", c_int), ("rtol", c_double), ("maxit", c_int),
-                ("cycle", c_int), ("fact", c_int), ("setup", c_int), ("order", c_int)]
+                ("cycle", c_int), ("fact", c_int), ("setup", c_int), ("order", c_int), ("store", c_int)]
 
 
 class als_newton_params(Structure):

@@ -680,6 +680,7 @@ void als_default_options(als_options* opt) {
   opt->fact = ALS_FACT_FULL;
   opt->setup = ALS_SETUP_AUTO;
   opt->order = 2;
+  opt->store = ALS_STORE_FP32;
 }
 
 // message of the calling thread's last failed als_create (the context is gone by then)
@@ -880,6 +881,10 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.mode != ALS_MODE_FP64 && c->opt.mode != ALS_MODE_MIXED) return fail(c, ALS_EINVAL, "unknown mode");
   if (c->opt.setup != ALS_SETUP_AUTO && c->opt.setup != ALS_SETUP_FP64)
     return fail(c, ALS_EINVAL, "unknown setup arithmetic");
+  if (c->opt.store != ALS_STORE_FP32 && c->opt.store != ALS_STORE_BF16)
+    return fail(c, ALS_EINVAL, "unknown star storage");
+  if (c->opt.store == ALS_STORE_BF16 && c->opt.order != 2)
+    return fail(c, ALS_EINVAL, "bfloat16 star storage is built for order 2");
   if (c->opt.order != 2 && c->opt.order != 3) return fail(c, ALS_EINVAL, "order must be 2 or 3");
   if (c->opt.order == 3 && (c->dim != 2 || coeff->kind != ALS_COEFF_SCALAR))
     return fail(c, ALS_EINVAL, "order 3 is built for 2D meshes with scalar viscosity");
@@ -955,6 +960,11 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     if (l > 0) {
       ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
       ALS_TRY(alloc_star_storage(c, Lv));
+      if (c->opt.store == ALS_STORE_BF16) {   // the block-packed stars again, in bfloat16
+        uint16_t* p16 = nullptr;
+        ALS_TRY(dalloc(c, &p16, (size_t)(Lv.split ? Lv.nint : Lv.g.nverts) * block_stride_bf16(Lv.np)));
+        Lv.inv16 = p16;
+      }
     }
   }
   if (coarse_alloc(c->lev[0], &c->coarse) != 0) {
@@ -1623,6 +1633,7 @@ struct MergedCycle {
 std::string merged_ineligible(const als_ctx* c, const als_ctx* first) {
   if (c->k != 2) return "order 3";
   if (c->lev[0].tensor) return "tensor coefficients";
+  if (c->opt.store != ALS_STORE_FP32) return "bfloat16 star storage";
   if (!fused_gmres(c)) return "smoother other than GMRES(s <= 8)";
   if (c->opt.cycle != ALS_CYCLE_V) return "F-cycle";
   if (c->prof.on) return "kernel timing on";

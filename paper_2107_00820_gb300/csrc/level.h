@@ -31,6 +31,9 @@ struct LevelDev {
   // boundary vertex's star restricted to its free dofs
   double* inv64;
   float* inv32;
+  // ALS_STORE_BF16: the same block-packed stars as inv32 rounded to bfloat16 (stride
+  // rounded to 8 entries), which the FP32 star kernels then stream instead; NULL otherwise
+  void* inv16 = nullptr;
   int split;             // split storage (see above)
   float* bnd32;          // boundary stars: packed upper triangle by rows, m x m, m = free dofs
   int* bvid;             // boundary vertex ids (nbnd), ascending
@@ -96,6 +99,8 @@ void op_apply_multi(const LevelDev& L, double gamma, const double* X, double* Y,
 // holds setup_tab_bytes(dim) bytes of scratch for the level's reference tables.
 void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s);
 size_t setup_tab_bytes(int dim);
+// entries per star of the bfloat16 block-packed copy (inv16)
+int block_stride_bf16(int np);
 // the FP32 block-packed inverses (inv32) of every patch from the FP64 ones (inv64);
 // the setup calls it, and so does the loading of caller-supplied FP64 inverses
 void patch_derive32(const LevelDev& L, cudaStream_t s);

@@ -15,6 +15,7 @@
 // then the <= 2^d patch values that contain a node are summed in a fixed order (no
 // floating-point atomics) by the patch gather or, in the FP32 3D smoother, by the
 // operator's cell kernel that consumes z.
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <stdlib.h>
 
@@ -166,6 +167,8 @@ enum PatchOut { OUT_SCRATCH = 0, OUT_WRITE = 1, OUT_SUBTRACT = 2 };
 
 // S_IJ r_J -> yI and S_IJ^T r_I -> yJ for block b of one block-packed patch at S
 // (global or shared memory).  Diagonal blocks use the symmetric upper triangle.
+// Storage of the block-packed FP32-cycle inverses: float, or bfloat16 (the opt-in
+// ALS_STORE_BF16) widened to float on load; every product and sum runs in float.
 template <bool GLOBAL>
 __device__ __forceinline__ float4 ld4(const float* p) {
   if constexpr (GLOBAL) return __ldg(reinterpret_cast<const float4*>(p));
@@ -176,9 +179,30 @@ __device__ __forceinline__ float ld1(const float* p) {
   if constexpr (GLOBAL) return __ldg(p);
   else return *p;
 }
-
 template <bool GLOBAL>
-__device__ __forceinline__ void block_product(const BlockLayout& BL, const float* __restrict__ S, int b, bool diag,
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {   // four entries, one 8-byte load
+  uint2 u;
+  if constexpr (GLOBAL) u = __ldg(reinterpret_cast<const uint2*>(p));
+  else u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, c.x, c.y);
+}
+template <bool GLOBAL>
+__device__ __forceinline__ float ld1(const __nv_bfloat16* p) {
+  if constexpr (GLOBAL) return __bfloat162float(__ldg(p));
+  else return __bfloat162float(*p);
+}
+
+// entries per patch of the block-packed layout in storage TS: the packed size rounded to
+// 16 bytes (bulk copies and vector loads need 16-byte aligned rows)
+template <typename TS>
+__host__ __device__ constexpr int block_stride(int np) {
+  return sizeof(TS) == 4 ? packed_stride(np) : (packed_size(np) + 7) & ~7;
+}
+
+template <bool GLOBAL, typename TS = float>
+__device__ __forceinline__ void block_product(const BlockLayout& BL, const TS* __restrict__ S, int b, bool diag,
                                               const float (&rI)[9], const float (&rJ)[9], float (&yI)[9],
                                               float (&yJ)[9]) {
   float e[84];
@@ -237,7 +261,7 @@ __device__ __forceinline__ void block_of(const BlockLayout& BL, int b, int& I, i
   }
 }
 
-template <int DIM, int NST>
+template <int DIM, int NST, typename TS = float>
 struct TmaCfg {
   static constexpr int NP = Sz<DIM>::NP;
   static constexpr int NB = Sz<DIM>::NB;
@@ -245,17 +269,18 @@ struct TmaCfg {
   static constexpr int TPP = DIM == 3 ? 64 : 4;        // threads per patch (>= blocks per patch)
   static constexpr int PPI = THREADS / TPP;            // patches per iteration
   static constexpr int NSTAGE = NST;
-  static constexpr int STRIDE = packed_stride(NP);     // floats per patch
+  static constexpr int STRIDE = block_stride<TS>(NP);  // entries per patch
   static constexpr int NBR = NP / 9;
   static constexpr int RPT = (PPI * NP + THREADS - 1) / THREADS;   // r values gathered per thread
-  static constexpr size_t stage_floats = (size_t)PPI * STRIDE;
+  static constexpr size_t stage_elems = (size_t)PPI * STRIDE;
+  static constexpr size_t stage_bytes = stage_elems * sizeof(TS);
   // dynamic shared memory: [mbarriers | stages | r | partials]; the barriers need
   // 8-byte and the bulk-copy destinations 16-byte alignment
   static constexpr size_t bar_bytes = 128;
   static constexpr size_t smem_bytes =
-      bar_bytes + NSTAGE * stage_floats * 4 + (size_t)PPI * NP * 4 + (size_t)PPI * NP * NBR * 4;
+      bar_bytes + NSTAGE * stage_bytes + (size_t)PPI * NP * 4 + (size_t)PPI * NP * NBR * 4;
   static_assert(NSTAGE * 8 <= bar_bytes, "mbarrier area too small");
-  static_assert((STRIDE * 4) % 16 == 0 && (stage_floats * 4) % 16 == 0, "bulk copies need 16-byte alignment");
+  static_assert((STRIDE * sizeof(TS)) % 16 == 0 && stage_bytes % 16 == 0, "bulk copies need 16-byte alignment");
 };
 
 // Work list of the FP32 star kernels, wl = bit 0 | bit 1: bit 0 clear = the star products
@@ -355,12 +380,12 @@ __device__ __forceinline__ bool entry_in(const Geom& g, const PatchPos& q, const
 }
 
 // (bx, gx: the block's index and the blocks of this instance, see batch.cuh)
-template <int DIM, int NST>
-__device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const Geom& g, const float* __restrict__ inv,
+template <int DIM, int NST, typename TS = float>
+__device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const Geom& g, const TS* __restrict__ inv,
                                                int interior, int count, const float* __restrict__ r,
                                                float* __restrict__ out, int mode, DevStatus* st, int wait_polls,
                                                int early_trigger) {
-  using C = TmaCfg<DIM, NST>;
+  using C = TmaCfg<DIM, NST, TS>;
   constexpr int NP = C::NP, NB = C::NB, PPI = C::PPI, TPP = C::TPP, NSTAGE = C::NSTAGE, NBR = C::NBR;
   constexpr int RPT = C::RPT, THREADS = C::THREADS;
   constexpr BlockLayout BL = BlockLayout(NP);
@@ -368,8 +393,8 @@ __device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const G
   static_assert(ISSUER % TPP >= BlockLayout(NP).nbp, "the issuing thread must not own a block");
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
-  float* stages = reinterpret_cast<float*>(smraw + C::bar_bytes);
-  float* rs = stages + NSTAGE * C::stage_floats;          // [PPI][NP]
+  TS* stages = reinterpret_cast<TS*>(smraw + C::bar_bytes);
+  float* rs = reinterpret_cast<float*>(smraw + C::bar_bytes + NSTAGE * C::stage_bytes);   // [PPI][NP]
   float* part = rs + PPI * NP;                            // [PPI][NP][NBR]
   __shared__ int s_fail;
   const int tid = threadIdx.x;
@@ -381,13 +406,13 @@ __device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const G
     for (int ps = 0; ps < PPI; ++ps) {
       int vx, vy, vz;
       vids[ps] = work_vertex<DIM>(g, interior, grp * PPI + ps, count, vx, vy, vz);
-      if (vids[ps] >= 0) bytes += C::STRIDE * 4;
+      if (vids[ps] >= 0) bytes += C::STRIDE * sizeof(TS);
     }
     tma::mbar_expect_tx(&bars[stage], bytes);
     for (int ps = 0; ps < PPI; ++ps)
       if (vids[ps] >= 0)
-        tma::bulk_load(stages + stage * C::stage_floats + (size_t)ps * C::STRIDE,
-                       inv + (long long)vids[ps] * C::STRIDE, C::STRIDE * 4, &bars[stage]);
+        tma::bulk_load(stages + stage * C::stage_elems + (size_t)ps * C::STRIDE,
+                       inv + (long long)vids[ps] * C::STRIDE, C::STRIDE * sizeof(TS), &bars[stage]);
   };
   auto gather = [&](int grp, float (&v)[RPT]) {
 #pragma unroll
@@ -466,14 +491,14 @@ __device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const G
     __syncthreads();                        // (A) r and the stage are visible
     if (s_fail) break;
     if (b < BL.nbp) {
-      const float* S = stages + stage * C::stage_floats + (size_t)ps * C::STRIDE;
+      const TS* S = stages + stage * C::stage_elems + (size_t)ps * C::STRIDE;
       float rI[9], rJ[9], yI[9], yJ[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         rI[k] = rs[ps * NP + 9 * I + k];
         rJ[k] = rs[ps * NP + 9 * J + k];
       }
-      block_product<false>(BL, S, b, diag, rI, rJ, yI, yJ);
+      block_product<false, TS>(BL, S, b, diag, rI, rJ, yI, yJ);
       float* pp = part + ps * NP * NBR;
 #pragma unroll
       for (int k = 0; k < 9; ++k) pp[(9 * I + k) * NBR + J] = yI[k];
@@ -540,11 +565,12 @@ __device__ __forceinline__ void patch_tma_body(unsigned bx, unsigned gx, const G
   }
 }
 
-template <int DIM, int NST>
-__global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restrict__ inv, int interior, int count,
+template <int DIM, int NST, typename TS = float>
+__global__ void __launch_bounds__(64) k_patch_tma(Geom g, const TS* __restrict__ inv, int interior, int count,
                                                   const float* __restrict__ r, float* __restrict__ out, int mode,
                                                   DevStatus* st, int wait_polls, int early_trigger) {
-  patch_tma_body<DIM, NST>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode, st, wait_polls, early_trigger);
+  patch_tma_body<DIM, NST, TS>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode, st, wait_polls,
+                               early_trigger);
 }
 
 // ---------------------------------------------------------------------------
@@ -554,14 +580,14 @@ __global__ void __launch_bounds__(64) k_patch_tma(Geom g, const float* __restric
 // itself, and the block partials are reduced through double-buffered shared
 // memory: one barrier per iteration, 2 (3D) or 32 (2D) patches per 128-thread CTA.
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename TS = float>
 struct DirCfg {
   static constexpr int NP = Sz<DIM>::NP;
   static constexpr int THREADS = 128;
   static constexpr int TPP = DIM == 3 ? 64 : 4;
   static constexpr int PPC = THREADS / TPP;
   static constexpr int NBR = NP / 9;
-  static constexpr int STRIDE = packed_stride(NP);
+  static constexpr int STRIDE = block_stride<TS>(NP);
 };
 
 // r at entry 9*IB + k (k < 9) of the patch of vertex (vx, vy, vz)
@@ -577,11 +603,11 @@ __device__ __forceinline__ void gather9(const Geom& g, const float* __restrict__
   }
 }
 
-template <int DIM>
-__device__ __forceinline__ void patch_direct_body(unsigned bx, unsigned gx, const Geom& g, const float* __restrict__ inv,
+template <int DIM, typename TS = float>
+__device__ __forceinline__ void patch_direct_body(unsigned bx, unsigned gx, const Geom& g, const TS* __restrict__ inv,
                                                   int interior, int count, const float* __restrict__ r,
                                                   float* __restrict__ out, int mode) {
-  using C = DirCfg<DIM>;
+  using C = DirCfg<DIM, TS>;
   constexpr int NP = C::NP, NB = Sz<DIM>::NB, PPC = C::PPC, TPP = C::TPP, NBR = C::NBR;
   constexpr BlockLayout BL = BlockLayout(NP);
   __shared__ float part[2][PPC][NP][NBR];
@@ -600,7 +626,7 @@ __device__ __forceinline__ void patch_direct_body(unsigned bx, unsigned gx, cons
         float rI[9], rJ[9], yI[9], yJ[9];
         gather9<DIM>(g, r, vx, vy, vz, I, rI);
         gather9<DIM>(g, r, vx, vy, vz, J, rJ);
-        block_product<true>(BL, inv + (long long)v * C::STRIDE, b, diag, rI, rJ, yI, yJ);
+        block_product<true, TS>(BL, inv + (long long)v * C::STRIDE, b, diag, rI, rJ, yI, yJ);
 #pragma unroll
         for (int k = 0; k < 9; ++k) part[buf][ps][9 * I + k][J] = yI[k];
         if (!diag) {
@@ -631,11 +657,11 @@ __device__ __forceinline__ void patch_direct_body(unsigned bx, unsigned gx, cons
   }
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(128) k_patch_direct(Geom g, const float* __restrict__ inv, int interior, int count,
+template <int DIM, typename TS = float>
+__global__ void __launch_bounds__(128) k_patch_direct(Geom g, const TS* __restrict__ inv, int interior, int count,
                                                       const float* __restrict__ r, float* __restrict__ out,
                                                       int mode) {
-  patch_direct_body<DIM>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode);
+  patch_direct_body<DIM, TS>(blockIdx.x, gridDim.x, g, inv, interior, count, r, out, mode);
 }
 
 template <int DIM>
@@ -646,8 +672,12 @@ static void launch_patch_direct(const LevelDev& L, int interior, long long count
   const long long cap = 152LL * 8;
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
-  launch_pdl(k_patch_direct<DIM>, (unsigned)grid, C::THREADS, 0, s, L.g, L.inv32, interior | (L.split ? 2 : 0),
-             (int)count, r, out, mode);
+  if (L.inv16)
+    launch_pdl(k_patch_direct<DIM, __nv_bfloat16>, (unsigned)grid, C::THREADS, 0, s, L.g,
+               (const __nv_bfloat16*)L.inv16, interior | (L.split ? 2 : 0), (int)count, r, out, mode);
+  else
+    launch_pdl(k_patch_direct<DIM>, (unsigned)grid, C::THREADS, 0, s, L.g, L.inv32, interior | (L.split ? 2 : 0),
+               (int)count, r, out, mode);
   count_launch(1);
 }
 
@@ -746,16 +776,16 @@ static int patch_variant(const LevelDev& L) {
   return L.patch_kernel >= 0 ? L.patch_kernel : 0;
 }
 
-template <int DIM, int NST>
-static void launch_patch_tma_n(const LevelDev& L, int interior, long long count, const float* r, float* out,
-                               int mode, DevStatus* st, cudaStream_t s) {
-  using C = TmaCfg<DIM, NST>;
+template <int DIM, int NST, typename TS>
+static void launch_patch_tma_ts(const LevelDev& L, const TS* inv, int interior, long long count, const float* r,
+                                float* out, int mode, DevStatus* st, cudaStream_t s) {
+  using C = TmaCfg<DIM, NST, TS>;
   const long long groups = (count + C::PPI - 1) / C::PPI;
   // the grid is persistent (grid-stride over the patches): every CTA must be resident,
   // so size it by the occupancy the registers and shared memory actually allow
   static int per_sm = -1;
   if (per_sm < 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_tma<DIM, NST>, C::THREADS,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_tma<DIM, NST, TS>, C::THREADS,
                                                       C::smem_bytes) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 1;
@@ -766,9 +796,19 @@ static void launch_patch_tma_n(const LevelDev& L, int interior, long long count,
   const long long grid = groups < cap ? groups : cap;
   if (grid <= 0) return;
   const int early = (!interior && mode == OUT_SCRATCH && L.split && L.nbnd > 0) ? 1 : 0;   // boundary kernel next
-  launch_pdl(k_patch_tma<DIM, NST>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, L.inv32,
+  launch_pdl(k_patch_tma<DIM, NST, TS>, (unsigned)grid, C::THREADS, C::smem_bytes, s, L.g, inv,
              interior | (L.split ? 2 : 0), (int)count, r, out, mode, st, L.wait_polls, early);
   count_launch(1);
+}
+
+// the level's block-packed inverses: bfloat16 when the level stores them so, else float
+template <int DIM, int NST>
+static void launch_patch_tma_n(const LevelDev& L, int interior, long long count, const float* r, float* out,
+                               int mode, DevStatus* st, cudaStream_t s) {
+  if (L.inv16)
+    launch_patch_tma_ts<DIM, NST>(L, (const __nv_bfloat16*)L.inv16, interior, count, r, out, mode, st, s);
+  else
+    launch_patch_tma_ts<DIM, NST>(L, L.inv32, interior, count, r, out, mode, st, s);
 }
 
 template <int DIM>
@@ -779,16 +819,18 @@ static void launch_patch_variant(int v, const LevelDev& L, int interior, long lo
   else launch_patch_tma_n<DIM, 2>(L, interior, count, r, out, mode, st, s);
 }
 
-template <int DIM, int NST>
+template <int DIM, int NST, typename TS>
 static void set_tma_smem_n() {
-  cudaFuncSetAttribute(k_patch_tma<DIM, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaCfg<DIM, NST>::smem_bytes);
+  cudaFuncSetAttribute(k_patch_tma<DIM, NST, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaCfg<DIM, NST, TS>::smem_bytes);
 }
 
 template <int DIM>
 static void set_tma_smem() {
-  set_tma_smem_n<DIM, 2>();
-  set_tma_smem_n<DIM, 3>();
+  set_tma_smem_n<DIM, 2, float>();
+  set_tma_smem_n<DIM, 3, float>();
+  set_tma_smem_n<DIM, 2, __nv_bfloat16>();
+  set_tma_smem_n<DIM, 3, __nv_bfloat16>();
 }
 
 template <int DIM, bool TENSOR, typename R>
@@ -841,9 +883,12 @@ void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStat
 // block-packed (BlockLayout) FP32 copy, one CTA per vertex of inv32 (the interior vertices
 // with split storage, else every vertex), entry (i, i+t) of diagonal t rounded to the
 // nearest float; padding slots zeroed
-template <int DIM>
+__device__ __forceinline__ void store_as(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __double2bfloat16(v); }
+
+template <int DIM, typename TS = float>
 __global__ void __launch_bounds__(128) k_derive32(Geom g, int pstride, int split, const double* __restrict__ inv64,
-                                                  float* __restrict__ inv32) {
+                                                  TS* __restrict__ inv32) {
   constexpr int NP = Sz<DIM>::NP;
   constexpr BlockLayout BL = BlockLayout(NP);
   const long long iv = blockIdx.x;
@@ -853,12 +898,14 @@ __global__ void __launch_bounds__(128) k_derive32(Geom g, int pstride, int split
     const long long vx = iv % nix + 1, q = iv / nix, vy = q % niy + 1, vz = DIM == 3 ? q / niy + 1 : 0;
     v = vx + g.nv[0] * (vy + (long long)g.nv[1] * vz);
   }
+  constexpr int OSTRIDE = block_stride<TS>(NP);
   const double* src = inv64 + v * pstride;
-  float* dst = inv32 + iv * pstride;
-  for (int e = 44 * BL.nbp + BL.nbp + (int)threadIdx.x; e < BL.q2; e += blockDim.x) dst[e] = 0.f;
+  TS* dst = inv32 + iv * OSTRIDE;
+  for (int e = 44 * BL.nbp + BL.nbp + (int)threadIdx.x; e < BL.q2; e += blockDim.x) store_as(dst + e, 0.0);
+  for (int e = packed_stride(NP) + (int)threadIdx.x; e < OSTRIDE; e += blockDim.x) store_as(dst + e, 0.0);
   for (int t = 0; t < NP; ++t) {
     const int base = diag_start(NP, t);
-    for (int i = threadIdx.x; i + t < NP; i += blockDim.x) dst[BL.index(i, i + t)] = (float)src[base + i];
+    for (int i = threadIdx.x; i + t < NP; i += blockDim.x) store_as(dst + BL.index(i, i + t), src[base + i]);
   }
 }
 
@@ -897,6 +944,12 @@ void patch_derive32(const LevelDev& L, cudaStream_t s) {
     if (L.g.dim == 3) k_derive32<3><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, L.inv32);
     else k_derive32<2><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, L.inv32);
     count_launch(1);
+    if (L.inv16) {   // the bfloat16 copy the FP32 cycle streams (ALS_STORE_BF16)
+      __nv_bfloat16* d16 = (__nv_bfloat16*)L.inv16;
+      if (L.g.dim == 3) k_derive32<3, __nv_bfloat16><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, d16);
+      else k_derive32<2, __nv_bfloat16><<<(unsigned)nv32, 128, 0, s>>>(L.g, L.pstride, L.split, L.inv64, d16);
+      count_launch(1);
+    }
   }
   if (L.nbnd > 0) {
     const unsigned blocks = (unsigned)((L.nbnd + 7) / 8);
@@ -907,6 +960,8 @@ void patch_derive32(const LevelDev& L, cudaStream_t s) {
     count_launch(1);
   }
 }
+
+int block_stride_bf16(int np) { return block_stride<__nv_bfloat16>(np); }
 
 size_t setup_tab_bytes(int dim) {
   return (size_t)(dim == 2 ? SetupTab<2>::total : SetupTab<3>::total) * sizeof(double);

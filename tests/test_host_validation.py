@@ -32,6 +32,7 @@ def test_default_options(lib):
     assert (o.cycle, o.fact, o.maxit) == (A.ALS_CYCLE_V, A.ALS_FACT_FULL, 300)
     assert o.rtol == 1e-8 and o.tau == 0.0          # tau 0: 2^-d chosen at create
     assert o.setup == A.ALS_SETUP_AUTO
+    assert (o.order, o.store) == (2, A.ALS_STORE_FP32)
 
 
 @pytest.mark.parametrize("args,kw,words", [
@@ -50,6 +51,8 @@ def test_default_options(lib):
     ((2, 4, 1), {"transfer": 2}, "transfer"),
     ((2, 4, 1), {"mode": 2}, "mode"),
     ((2, 4, 1), {"setup": 2}, "setup"),
+    ((2, 4, 1), {"store": 2}, "star storage"),
+    ((2, 4, 1), {"store": 1, "order": 3}, "bfloat16 star storage"),
     ((3, 1024, 2), {}, "too large"),
     ((2, 46340, 2), {}, "too large"),
 ])
