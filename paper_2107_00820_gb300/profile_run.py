@@ -42,7 +42,7 @@ def main():
     tensor = spec.get("kind") == "tensor"
     mue = [torch.as_tensor(m, device="cuda") for m in pb.meta["mu_eff"]] if tensor else None
     ctx = Context(pb.d, pb.n, pb.levels, mu, pb.gamma, mu_eff=mue, mode=A.ALS_MODE_MIXED, sweeps=spec["sweeps"],
-                  schur=A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1)
+                  schur=A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1, order=spec.get("order", 2))
     nu = ctx.nu()
     vecs = {}
     if args.prec in ("fp32", "both"):

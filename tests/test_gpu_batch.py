@@ -146,3 +146,30 @@ def test_merged_mode_refused_for_an_ineligible_instance():
     assert torch.equal(x, xs[2])
     ctx.close()
     batch.close()
+
+
+def test_merged_cycles_beyond_one_launch_table():
+    """More instances than one merged launch's parameter table holds (64): every level
+    operation splits into several launches, and every instance still gets bitwise its own
+    cycle."""
+    from paper_2107_00820_gb300 import Batch
+    # one (dimension, levels) class, so that every grouping is a single group of 70
+    specs = [(2, 8, 2, 10.0 if i % 2 == 0 else 1e2, 1e2 if i % 3 == 0 else 1e4, 100 + i) for i in range(70)]
+    pbs = [sinker(d, n, L, g, dr, seed) for d, n, L, g, dr, seed in specs]
+    opts = {"mode": A.ALS_MODE_MIXED, "schur": A.ALS_SCHUR_P2}
+    ins = [{"dim": pb.d, "n": pb.n, "levels": pb.levels, "coeffs": pb.mu, "gamma": pb.gamma, "options": opts}
+           for pb in pbs]
+    batch = Batch(ins)
+    assert batch.mode == A.ALS_BATCH_MERGED
+    rng = np.random.default_rng(38)
+    bs = [dev(rng.standard_normal(s[0]), torch.float32) for s in batch.shapes]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch.vcycle(bs, xs, A.ALS_PREC_FP32)
+    assert batch.merged_plan()[1] == 1
+    for i in (0, 1, 63, 64, 68, 69):
+        ctx = context(pbs[i], **opts)
+        x = torch.zeros_like(bs[i])
+        ctx.vcycle(bs[i], x, A.ALS_PREC_FP32)
+        assert torch.equal(x, xs[i]), i
+        ctx.close()
+    batch.close()
