@@ -274,7 +274,7 @@ static thread_local int t_prof_counter = 0;
 // Gram-Schmidt update carries the Givens step, and the final update also forms
 // the residual b - A x from the Arnoldi relation when `t` is given.
 bool fused_gmres(const als_ctx* c) {
-  return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB && c->k == 2;
+  return c->opt.smoother == ALS_SMOOTH_GMRES && std::max(1, c->opt.sweeps) <= KMAXB;
 }
 
 // FP32 3D cycles form Z_j inside the operator's cell kernel from the patch outputs

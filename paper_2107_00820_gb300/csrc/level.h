@@ -127,6 +127,9 @@ void qk_tables();
 void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
               cudaStream_t s);
 void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
+// op_apply_epi at order 3 (the GMRES smoother's Arnoldi step)
+void qk_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                  cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1);
 // per-cell W^-1 (w_mu: W = M_p(1/mu), else M_p) into winv64/winv32 and, if S, the Schur blocks
 // of Eq. (P1P2) (variant 0: P1, 1: P2)
 void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,

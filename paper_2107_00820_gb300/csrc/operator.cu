@@ -748,6 +748,10 @@ static void launch_apply_epi(const LevelDev& L, double gamma, const void* x, voi
 
 void op_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (L.k == 3) {
+    qk_apply_epi(L, prec, gamma, x, y, e, s, e0, e1);
+    return;
+  }
   if (prec == PREC_F64) {
     if (L.g.dim == 2) {
       if (L.tensor) launch_apply_epi<double, 2, true>(L, gamma, x, y, e, s, e0, e1);

@@ -219,18 +219,13 @@ __device__ __forceinline__ int cells_of(int i, int n, int (&c)[2], int (&a)[2]) 
 // y(node) = sum of the staged cell outputs of the cells containing it, fixed order;
 // keep_bnd: y = x at Dirichlet nodes; raw: no Dirichlet treatment
 template <typename T>
-__global__ void k_qk_gather(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y, int keep_bnd,
-                            int raw) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * g.N) return;
+__device__ __forceinline__ T qk_gather_value(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
+                                             long long t, int keep_bnd, int raw) {
   const int comp = (int)(t / g.N);
   const long long nd = t - comp * g.N;
   const int i = (int)(nd % g.nn[0]), j = (int)(nd / g.nn[0]);
   const bool bnd = i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1;
-  if (bnd && !raw) {
-    y[t] = keep_bnd ? x[t] : T(0);
-    return;
-  }
+  if (bnd && !raw) return keep_bnd ? x[t] : T(0);
   int cxs[2], axs[2], cys[2], ays[2];
   const int mx = cells_of(i, g.n[0], cxs, axs), my = cells_of(j, g.n[1], cys, ays);
   T acc = T(0);
@@ -239,7 +234,56 @@ __global__ void k_qk_gather(Geom g, const T* __restrict__ ebuf, const T* __restr
       const long long cell = (long long)cxs[a] + (long long)g.n[0] * cys[b];
       acc += ebuf[(cell * 2 + comp) * NB + axs[a] + N1 * ays[b]];
     }
-  y[t] = acc;
+  return acc;
+}
+
+template <typename T>
+__global__ void k_qk_gather(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y, int keep_bnd,
+                            int raw) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.N) return;
+  y[t] = qk_gather_value<T>(g, ebuf, x, t, keep_bnd, raw);
+}
+
+// The gather fused with the reduction that consumes its result, as for order 2 (the
+// GMRES smoother's Arnoldi step): y = b + sigma A x (b NULL: sigma A x; Dirichlet rows of
+// A x are x, the identity);  start = 0: out[j] = (V_j . y) / hn[j], j < k;  start = 1:
+// |y|^2 starts the GMRES cycle.  Block partials in a fixed order: reproducible.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_qk_gather_epi(Geom g, const T* __restrict__ ebuf,
+                                                               const T* __restrict__ x, T* __restrict__ y,
+                                                               const T* __restrict__ b, double sigma, int k,
+                                                               const T* __restrict__ V, long long ld,
+                                                               T* __restrict__ out, int start, GmresDev sd,
+                                                               double* __restrict__ partial) {
+  __shared__ T nrm2_s[1];
+  const GmresView<T> st = gmres_view<T>(sd);
+  T* rows = reinterpret_cast<T*>(partial + 1);
+  const int kk = start ? 1 : k;
+  T acc[KMAXB];
+#pragma unroll
+  for (int jj = 0; jj < KMAXB; ++jj) acc[jj] = T(0);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 2 * g.N) {
+    const T v = (b ? b[t] : T(0)) + (T)sigma * qk_gather_value<T>(g, ebuf, x, t, 1, 0);
+    y[t] = v;
+    if (start) {
+      acc[0] = v * v;
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < KMAXB; ++jj)
+        if (jj < k) acc[jj] = V[(long long)jj * ld + t] * v;
+    }
+  }
+  block_partials<T, T>(acc, kk, rows + (long long)blockIdx.x * kk);
+  if (last_block(partial)) {
+    if (start) {
+      finish_sums<T>(partial, 1, nrm2_s);
+      if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
+    } else {
+      finish_sums<T>(partial, k, out, st.hn);
+    }
+  }
 }
 
 template <typename T, int MODE>
@@ -624,6 +668,30 @@ void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x
               cudaStream_t s) {
   if (prec == PREC_F64) qk::apply_t<double>(L, mode, gamma, x, y, p_in, p_out, s);
   else qk::apply_t<float>(L, mode, gamma, x, y, p_in, p_out, s);
+}
+
+// op_apply_epi for order 3: the cell kernel of A_gamma (viscous + AL) into the staged
+// outputs, then the gather with the Arnoldi epilogue
+template <typename T>
+static void apply_epi_t(const LevelDev& L, double gamma, const void* x, void* y, const ApplyEpi& e, cudaStream_t s,
+                        cudaEvent_t e0, cudaEvent_t e1) {
+  const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
+  const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
+  // External records become event-record nodes when the stream is being captured
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  qk::k_qk_cells<T, OP_VISC | OP_AL><<<(unsigned)((L.g.ncells + 7) / 8), 256, 0, s>>>(
+      L.g, gamma, (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  qk::k_qk_gather_epi<T><<<(unsigned)((2 * L.g.N + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0, s>>>(
+      L.g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out, e.start,
+      e.st, e.partial);
+  count_launch(2);
+}
+
+void qk_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                  cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (prec == PREC_F64) apply_epi_t<double>(L, gamma, x, y, e, s, e0, e1);
+  else apply_epi_t<float>(L, gamma, x, y, e, s, e0, e1);
 }
 
 void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
