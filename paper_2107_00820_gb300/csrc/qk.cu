@@ -535,15 +535,20 @@ __global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, 
   __syncwarp();
   T acc[R];
   for (int k = 0; k < R; ++k) acc[k] = T(0);
+  // symmetric product over the wrapped diagonals: row i takes entry (i, (i + t) mod NS),
+  // entry i of diagonal t while i + t < NS, else entry i + t - NS of diagonal NS - t (its
+  // symmetric partner), so every lane of a row chunk multiplies at every t
   const T* S = reinterpret_cast<const T*>(&sbuf[w][0]);
 #pragma unroll 5
   for (int t = 0; t < NS; ++t) {
-    const T* d = S + diag_start(NS, t);
+    const T* du = S + diag_start(NS, t);
+    const T* dl = S + (t > 0 ? diag_start(NS, NS - t) - (NS - t) : 0);
     for (int k = 0; k < R; ++k) {
       const int i = lane + 32 * k;
       if (i < NS) {
-        if (i + t < NS) acc[k] += d[i] * rs[w][i + t];
-        if (t > 0 && i >= t) acc[k] += d[i - t] * rs[w][i - t];
+        const int j = i + t;
+        const bool up = j < NS;
+        acc[k] += (up ? du[i] : dl[i]) * rs[w][up ? j : j - NS];
       }
     }
   }
