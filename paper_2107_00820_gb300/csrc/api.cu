@@ -1600,9 +1600,12 @@ als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, in
 // Each instance is a full context with its own stream.  A batched solve
 // interleaves the instances' FGMRES iterations: every round queues one
 // iteration of every unfinished instance on its own stream and then waits once
-// for all of them, so the kernels of different instances run concurrently.  A
-// batched cycle launches one graph whose branches are the instances' captured
-// cycle graphs (no edges between them), so all cycles run as one launch.
+// for all of them, so the kernels of different instances run concurrently.  The
+// FP32 cycles run in one of two forms (als_batch_set_mode): merged launches, one
+// per level operation for each group of instances (MergedCycle, MergedPlan above;
+// in a solve each group's cycles are joined with its instances' streams by
+// events), or one graph whose branches are the instances' own captured cycle
+// graphs (no edges between them).
 // ============================================================================
 }  // extern "C"
 

@@ -1,4 +1,4 @@
-"""Profiling driver: setup plus a few V-cycles of a benchmark workload inside a
+"""Profiling harness: setup plus a few V-cycles of a benchmark workload inside a
 cudaProfilerStart/Stop region, for `ncu --profile-from-start off`.
 
     python -m paper_2107_00820_gb300.profile_run --workload sinker3d_32 --vcycles 1 --prec fp32
