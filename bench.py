@@ -768,7 +768,7 @@ def ours_batch(args, dist):
         batch.vcycle(b32, x32, A.ALS_PREC_FP32)
         t_mcyc = timed(lambda: batch.vcycle(b32, x32, A.ALS_PREC_FP32), 5)
         grouping, groups, gms, merged_kernels = batch.merged_plan()
-        names = ("one group", "by dimension", "by dimension and levels")
+        names = ("one group", "by dimension", "by dimension and levels", "by shape", "by shape, chunks of 4")
         merged_tune = {"grouping": names[grouping], "groups": groups,
                        "cycle_ms_per_grouping": {names[k]: (round(v, 3) if v >= 0 else None) for k, v in enumerate(gms)},
                        "variants": {}}

@@ -423,10 +423,11 @@ als_status als_batch_get_mode(const als_batch* batch, int* mode);
  * of one graph, so that one group's latency-bound coarse levels overlap another's
  * bandwidth-bound fine levels.  The autotuner builds and times (three cycles, CUDA
  * events) each grouping that gives a distinct partition -- 0: one group, 1: by
- * dimension, 2: by dimension and level count -- and keeps the fastest; within a
+ * dimension, 2: by dimension and level count, 3: by shape (dimension, cells, levels),
+ * 4: by shape in chunks of at most four instances -- and keeps the fastest; within a
  * group it times the three star-kernel variants of every merged star-product and
  * interior-solve launch (0: TMA ring, 2 stages; 1: 3 stages; 2: direct loads).
- * als_batch_merged_plan: the chosen grouping, the number of groups, ms[3] (optional)
+ * als_batch_merged_plan: the chosen grouping, the number of groups, ms[5] (optional)
  * the measured time per cycle of each grouping (-1: not built, same partition as an
  * earlier one), *kernels (optional) the kernel launches of one merged cycle of the
  * whole batch.  als_batch_merged_tune: for group `group` and level index `level`
@@ -436,6 +437,10 @@ als_status als_batch_get_mode(const als_batch* batch, int* mode);
  * room for count entries) the batch indices of the group's instances in order.
  * ALS_EINVAL: NULL batch or required output, index out of range, or no plan yet. */
 als_status als_batch_merged_plan(const als_batch* batch, int* grouping, int* groups, float* ms, long long* kernels);
+/* Fixes the grouping of the merged cycles (0 .. 4 as above) or, with -1, lets the
+ * tuner choose again; drops the current plan (made again on the next merged call).
+ * ALS_EINVAL for a NULL batch or a grouping out of range. */
+als_status als_batch_set_grouping(als_batch* batch, int grouping);
 als_status als_batch_merged_tune(const als_batch* batch, int group, int level, int* products_variant,
                                  int* interior_variant, float* ms, int* instances);
 

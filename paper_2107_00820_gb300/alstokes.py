@@ -97,6 +97,7 @@ SIGNATURES = {
     "als_batch_get_mode": (c_int, [c_void_p, POINTER(c_int)]),
     "als_batch_merged_plan": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_float),
                                       POINTER(ctypes.c_longlong)]),
+    "als_batch_set_grouping": (c_int, [c_void_p, c_int]),
     "als_batch_merged_tune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_int),
                                       POINTER(ctypes.c_float), POINTER(c_int)]),
     "als_autotune_info": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(ctypes.c_float)]),
@@ -463,11 +464,15 @@ class Batch:
         self._check(self._lib.als_batch_set_mode(self._b, int(mode)))
 
     def merged_plan(self):
-        """(grouping, groups, ms per grouping [3], kernels of one merged cycle of the batch)."""
+        """(grouping, groups, ms per grouping [5], kernels of one merged cycle of the batch)."""
         g, n, kern = c_int(), c_int(), ctypes.c_longlong()
-        ms = (ctypes.c_float * 3)()
+        ms = (ctypes.c_float * 5)()
         self._check(self._lib.als_batch_merged_plan(self._b, byref(g), byref(n), ms, byref(kern)))
         return g.value, n.value, list(ms), kern.value
+
+    def set_grouping(self, grouping):
+        """Fix the merged cycles' grouping (0 .. 4), or -1 to let the tuner choose."""
+        self._check(self._lib.als_batch_set_grouping(self._b, int(grouping)))
 
     def merged_tune(self, group, level):
         """(products variant, interior variant, ms[6], batch indices of the group's instances)."""

@@ -1860,8 +1860,9 @@ als_status merged_build(MergedCycle& M, cudaStream_t s, std::string& err) {
 // (one launch per level operation for the group), the groups' captured cycles run as
 // independent branches of one graph, so that one group's latency-bound levels overlap
 // another's bandwidth-bound ones.  Groupings: 0 = one group, 1 = by dimension, 2 = by
-// dimension and level count.
-constexpr int kGroupings = 3;
+// dimension and level count, 3 = by shape (dimension, cells, levels), 4 = by shape in
+// chunks of at most four instances.
+constexpr int kGroupings = 5;
 struct MergedPlan {
   int grouping = -1;
   std::vector<MergedCycle> g;
@@ -1873,15 +1874,24 @@ struct MergedPlan {
 std::vector<std::vector<int>> plan_groups(const std::vector<als_ctx*>& inst, int grouping) {
   std::vector<std::vector<int>> out;
   std::vector<long long> keys;
+  std::vector<int> fill;   // grouping 4: members of the current chunk of each shape
   for (int i = 0; i < (int)inst.size(); ++i) {
-    const long long key = grouping == 0 ? 0 : (grouping == 1 ? inst[i]->dim : 100LL * inst[i]->dim + inst[i]->L);
-    size_t k = 0;
-    while (k < keys.size() && keys[k] != key) ++k;
+    const als_ctx* c = inst[i];
+    const long long shape = (100LL * c->dim + c->L) * 100000LL + c->lev[c->L - 1].g.n[0];
+    long long key = 0;
+    if (grouping == 1) key = c->dim;
+    else if (grouping == 2) key = 100LL * c->dim + c->L;
+    else if (grouping >= 3) key = shape;
+    size_t k = keys.size();
+    for (size_t q = 0; q < keys.size(); ++q)
+      if (keys[q] == key && (grouping != 4 || fill[q] < 4)) { k = q; break; }
     if (k == keys.size()) {
       keys.push_back(key);
+      fill.push_back(0);
       out.emplace_back();
     }
     out[k].push_back(i);
+    ++fill[k];
   }
   return out;
 }
@@ -1940,7 +1950,8 @@ struct als_batch {
   std::string err;
   int mode = ALS_BATCH_BRANCHES;
   MergedPlan plan;                   // every instance (als_batch_vcycle), grouping chosen by time
-  float plan_ms[kGroupings] = {-1.f, -1.f, -1.f};   // measured cycle time of each grouping
+  int forced_grouping = -1;          // als_batch_set_grouping: a fixed grouping, -1 = tuned
+  float plan_ms[kGroupings] = {-1.f, -1.f, -1.f, -1.f, -1.f};   // measured cycle time of each grouping
   std::vector<MergedCycle> live;     // per group of the plan: its unfinished instances (solves)
   std::vector<cudaEvent_t> ev;       // per instance: joins of the merged cycles of a solve
   std::vector<cudaEvent_t> gev;      // per group
@@ -1978,13 +1989,14 @@ static als_status batch_plan(als_batch* b) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  std::vector<size_t> seen;
+  std::vector<std::vector<std::vector<int>>> seen;
   float best = 1e30f;
   int best_g = 0;
   for (int grouping = 0; grouping < kGroupings; ++grouping) {
-    const size_t ng = plan_groups(b->ctx, grouping).size();
-    if (std::find(seen.begin(), seen.end(), ng) != seen.end()) continue;   // the same partition
-    seen.push_back(ng);
+    if (b->forced_grouping >= 0 && grouping != b->forced_grouping) continue;
+    const std::vector<std::vector<int>> part = plan_groups(b->ctx, grouping);
+    if (std::find(seen.begin(), seen.end(), part) != seen.end()) continue;   // the same partition
+    seen.push_back(part);
     MergedPlan P;
     als_status st = plan_build(P, b->ctx, grouping, s, b->err);
     if (st == ALS_OK) {
@@ -2314,6 +2326,27 @@ als_status als_batch_set_mode(als_batch* b, int mode) {
         return batch_fail(b, ALS_EINVAL, "instance " + std::to_string(i) + " cannot run merged cycles: " + why);
     }
   b->mode = mode;
+  return ALS_OK;
+}
+
+als_status als_batch_set_grouping(als_batch* b, int grouping) {
+  if (!b) return ALS_EINVAL;
+  if (grouping < -1 || grouping >= kGroupings) return batch_fail(b, ALS_EINVAL, "grouping must be -1 .. 4");
+  for (als_ctx* c : b->ctx) cudaStreamSynchronize(c->stream);
+  for (cudaStream_t gs : b->gs)
+    if (gs) cudaStreamSynchronize(gs);
+  if (b->mstream) cudaStreamSynchronize(b->mstream);
+  plan_free(b->plan);
+  for (MergedCycle& M : b->live) merged_free(M);
+  b->live.clear();
+  for (cudaEvent_t e : b->gev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t gs : b->gs)
+    if (gs) cudaStreamDestroy(gs);
+  b->gev.clear();
+  b->gs.clear();
+  for (float& t : b->plan_ms) t = -1.f;
+  b->forced_grouping = grouping;
   return ALS_OK;
 }
 

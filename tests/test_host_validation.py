@@ -121,7 +121,7 @@ def test_every_entry_point_refuses_a_null_context(lib):
         "als_load_patch_inverses": (N, 1, N), "als_load_coarse_inverse": (N, N),
         "als_set_wait_limit": (N, 0), "als_solve_history": (N, N, 0, ctypes.byref(i)),
         "als_batch_set_mode": (N, 0), "als_batch_get_mode": (N, ctypes.byref(i)),
-        "als_batch_merged_plan": (N, ctypes.byref(i), ctypes.byref(i), N, N),
+        "als_batch_merged_plan": (N, ctypes.byref(i), ctypes.byref(i), N, N), "als_batch_set_grouping": (N, 0),
         "als_batch_merged_tune": (N, 0, 1, ctypes.byref(i), ctypes.byref(i), N, N),
     }
     for name, args in calls.items():
