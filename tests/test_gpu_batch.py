@@ -126,6 +126,20 @@ def test_merged_cycle_launches_and_tuning():
     batch.close()
 
 
+@pytest.mark.parametrize("change,why", [({"sweeps": 3}, "sweeps differ from instance 0"),
+                                        ({"store": A.ALS_STORE_BF16}, "bfloat16 star storage"),
+                                        ({"transfer": A.ALS_TRANSFER_STANDARD}, "transfer differs from instance 0")])
+def test_merged_mode_refusal_reasons(change, why):
+    from paper_2107_00820_gb300 import Batch
+    pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
+    ins[1] = dict(ins[1], options=dict(opts, **change))
+    batch = Batch(ins)
+    assert batch.mode == A.ALS_BATCH_BRANCHES
+    with pytest.raises(A.ALSError, match="instance 1 cannot run merged cycles: " + why):
+        batch.set_mode(A.ALS_BATCH_MERGED)
+    batch.close()
+
+
 def test_merged_mode_refused_for_an_ineligible_instance():
     from paper_2107_00820_gb300 import Batch
     pbs, ins, opts = _instances(A.ALS_MODE_MIXED)
