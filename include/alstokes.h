@@ -123,10 +123,16 @@ typedef struct {
                      ALS_MODE_MIXED; ALS_SETUP_FP64 = FP64 in both modes (the mixed cycle then
                      runs on the FP32 roundings of FP64-computed inverses) */
   int order;      /* polynomial order of the velocity: 2 (default, [Q2]^d x P1disc) or 3
-                     ([Q3]^2 x P2disc, the higher-order study of Sec. 5.2.2, Table k: 2D, scalar
-                     viscosity; nodes 3n+1 per direction, 4 x 4 Gauss points per cell (point
-                     data [cell][16]), pressure [cell][6] coefficients of {1, xi, eta, xi^2,
-                     xi eta, eta^2}, vertex stars of 5 x 5 nodes (50 dofs) inverted in FP64) */
+                     ([Q3]^d x P2disc, the element of the paper's sinker runs, Table linear,
+                     and of its higher-order study, Sec. 5.2.2, Table k; scalar viscosity;
+                     nodes 3n+1 per direction; 4^d Gauss points per cell (point data
+                     [cell][16] in 2D, [cell][64] in 3D, points x-fastest); pressure per cell
+                     the coefficients of the monomials of degree <= 2 in reference
+                     coordinates, by degree, x before y before z: {1, xi, eta, xi^2, xi eta,
+                     eta^2} in 2D, {1, xi, eta, zeta, xi^2, xi eta, xi zeta, eta^2, eta zeta,
+                     zeta^2} in 3D; vertex stars of 5^d nodes (50 / 375 dofs) assembled and
+                     inverted in FP64 in both modes.  3D stars take 564 KB (FP64) + 282 KB
+                     (FP32) per vertex and about 57 M FP64 multiply-adds each to set up) */
   int store;      /* storage of the star inverses the FP32 cycle streams: ALS_STORE_FP32
                      (default), or ALS_STORE_BF16: the block-packed stars (every star, or the
                      interior ones on levels stored split) rounded to bfloat16 to nearest,
@@ -207,12 +213,13 @@ als_status als_coarse_solve(als_ctx* ctx, int prec, const void* b, void* x);
 als_status als_apply_stokes(als_ctx* ctx, const double* u, const double* p, double* yu, double* yp);
 
 /* Copies the FP64 inverse of the patch matrix A_v (Sec. 4.1, Eq. (viim)) of
- * vertex `vertex` on `level` as a full (d*3^d) x (d*3^d) row-major matrix to
- * `out` (host or device).
- * In ALS_MODE_MIXED the patches are assembled and inverted in double-float
- * arithmetic (about 48 significant bits), else in FP64.
- * Patch dof order: component-major, node offsets (-1,0,1)^d x-fastest;
- * rows of nodes outside the domain or on the boundary are identity rows. */
+ * vertex `vertex` on `level` as a full m x m row-major matrix to `out` (host or
+ * device), m = d*3^d at order 2 and d*5^d at order 3.
+ * In ALS_MODE_MIXED the order-2 patches are assembled and inverted in double-float
+ * arithmetic (about 48 significant bits) unless options.setup = ALS_SETUP_FP64,
+ * else (and at order 3) in FP64.
+ * Patch dof order: component-major, node offsets (-1,0,1)^d (order 3: -2..2)
+ * x-fastest; rows of nodes outside the domain or on the boundary are identity rows. */
 als_status als_patch_inverse(als_ctx* ctx, int level, long long vertex, double* out);
 
 /* Solve the augmented Stokes system (Eqs. (stokessys), (augstokessys)) on the

@@ -225,7 +225,7 @@ class Context:
         return self.dim * int(np.prod([self.order * v + 1 for v in nl]))
 
     def npres(self):
-        per_cell = 6 if self.order == 3 else self.dim + 1
+        per_cell = (6 if self.dim == 2 else 10) if self.order == 3 else self.dim + 1
         return per_cell * int(np.prod(self.n))
 
     # calls -----------------------------------------------------------------

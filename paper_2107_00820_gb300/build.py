@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libalstokes.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["operator.cu", "patches.cu", "transfer.cu", "krylov.cu", "coarse.cu", "api.cu", "noalloc.cu", "peaks.cu", "newton.cu", "qk.cu"]
+SOURCES = ["operator.cu", "patches.cu", "transfer.cu", "krylov.cu", "coarse.cu", "api.cu", "noalloc.cu", "peaks.cu", "newton.cu", "qk.cu", "qk3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -285,7 +285,7 @@ bool fuse_patch_gather(const als_ctx* c, int prec) {
     const char* e = getenv("ALS_FUSE_GATHER");
     v = (e && e[0] == '0') ? 0 : 1;
   }
-  return v == 1 && prec == PREC_F32 && c->dim == 3;
+  return v == 1 && prec == PREC_F32 && c->dim == 3 && c->k == 2;
 }
 
 void smooth_fused(als_ctx* c, MGWork& w, int l, bool x_is_zero, void* t) {
@@ -886,11 +886,11 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
   if (c->opt.store == ALS_STORE_BF16 && c->opt.order != 2)
     return fail(c, ALS_EINVAL, "bfloat16 star storage is built for order 2");
   if (c->opt.order != 2 && c->opt.order != 3) return fail(c, ALS_EINVAL, "order must be 2 or 3");
-  if (c->opt.order == 3 && (c->dim != 2 || coeff->kind != ALS_COEFF_SCALAR))
-    return fail(c, ALS_EINVAL, "order 3 is built for 2D meshes with scalar viscosity");
+  if (c->opt.order == 3 && coeff->kind != ALS_COEFF_SCALAR)
+    return fail(c, ALS_EINVAL, "order 3 is built for scalar viscosity");
   c->k = c->opt.order;
-  c->npr = c->k == 3 ? 6 : c->dim + 1;
-  c->nq = c->k == 3 ? 16 : (c->dim == 2 ? 9 : 27);
+  c->npr = c->k == 3 ? (c->dim == 2 ? 6 : 10) : c->dim + 1;   // C(k - 1 + d, d)
+  c->nq = c->k == 3 ? (c->dim == 2 ? 16 : 64) : (c->dim == 2 ? 9 : 27);
   const int f = 1 << (c->L - 1);
   for (int k = 0; k < c->dim; ++k) {
     if (mesh->n[k] < 2 || mesh->n[k] % f != 0 || mesh->n[k] / f < 2)
@@ -965,6 +965,15 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
         ALS_TRY(dalloc(c, &p16, (size_t)(Lv.split ? Lv.nint : Lv.g.nverts) * block_stride_bf16(Lv.np)));
         Lv.inv16 = p16;
       }
+    }
+  }
+  if (c->k == 3 && c->dim == 3 && c->L > 1) {   // one star-setup workspace for all levels
+    const int ctas = qk3_setup_ctas(c->lev[c->L - 1].g.nverts);
+    double* ws = nullptr;
+    ALS_TRY(dalloc(c, &ws, qk3_setup_ws_doubles(ctas)));
+    for (int l = 1; l < c->L; ++l) {
+      c->lev[l].qk_ws = ws;
+      c->lev[l].qk_ws_ctas = ctas;
     }
   }
   if (coarse_alloc(c->lev[0], &c->coarse) != 0) {

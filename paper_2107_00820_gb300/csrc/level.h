@@ -16,8 +16,8 @@ constexpr int kWaitPolls = 1 << 22;
 
 struct LevelDev {
   Geom g;
-  int k = 2;             // polynomial order of the velocity: 2 ([Q2]^d x P1disc) or 3 ([Q3]^2 x P2disc, qk.cu)
-  int npr = 0;           // pressure unknowns per cell (d + 1, or 6 at order 3)
+  int k = 2;             // polynomial order of the velocity: 2 ([Q2]^d x P1disc) or 3 ([Q3]^d x P2disc, qk.cu, qk3.cu)
+  int npr = 0;           // pressure unknowns per cell (d + 1, or 6 / 10 at order 3 in 2D / 3D)
   int nq = 0;            // Gauss points per cell ((k + 1)^d)
   int tensor;            // 0: scalar mu per point, 1: Mandel tensor per point
   int ncoef;             // values per point (1 or NC)
@@ -51,6 +51,10 @@ struct LevelDev {
   float tune_ms[3];      // measured time per launch of each variant (ms)
   void* setup_tab;       // reference tables of the patch setup (setup_tab_bytes)
   int wait_polls = kWaitPolls;   // poll limit of the smoother kernel's pipeline waits
+  // order 3 in 3D: workspace of the star setup (qk3_setup_ws_doubles(qk_ws_ctas) doubles,
+  // shared by the levels, whose setups run one after another on the context's stream)
+  double* qk_ws = nullptr;
+  int qk_ws_ctas = 0;
 };
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1 };
@@ -121,8 +125,9 @@ int patch_autotune(LevelDev& L, const void* r, void* scratch, cudaStream_t s, fl
 void patch_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract,
                           cudaStream_t s);
 
-// ---- qk.cu: the order-3 discretisation ([Q3]^2 x P2disc); the dispatchers of
-// operator.cu, patches.cu, transfer.cu and coarse.cu call these when L.k == 3
+// ---- qk.cu: the order-3 discretisation ([Q3]^d x P2disc); the dispatchers of
+// operator.cu, patches.cu, transfer.cu and coarse.cu call these when L.k == 3, and they
+// pass 3D levels on to qk3.cu's qk3_* functions of the same arguments
 void qk_tables();
 void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
               cudaStream_t s);
@@ -142,6 +147,27 @@ void qk_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const vo
                 void* xadd);
 void qk_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
                  const void* sub);
+// ---- qk3.cu: [Q3]^3 x P2disc
+void qk3_tables();
+void qk3_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in,
+               void* p_out, cudaStream_t s);
+void qk3_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s);
+void qk3_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1);
+void qk3_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
+                    DevStatus* st, cudaStream_t s);
+// the star setup's CTAs for a level of nverts vertices, and the workspace they need
+// (doubles; one 375 x 376 FP64 star matrix per CTA), held in LevelDev::qk_ws
+int qk3_setup_ctas(long long nverts);
+size_t qk3_setup_ws_doubles(int ctas);
+void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s);
+void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
+                      cudaStream_t s);
+void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s);
+void qk3_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
+                 void* xadd);
+void qk3_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
+                  const void* sub);
 
 // ---- newton.cu
 // Coefficients of the Newton linearisation at the finest-level velocity u, at the Gauss

@@ -19,6 +19,7 @@
 #include "cell.cuh"
 #include "krylov.h"
 #include "level.h"
+#include "qk_tables.h"
 
 namespace als {
 namespace qk {
@@ -39,43 +40,13 @@ __constant__ double cL[N1][N1], cD[N1][N1], cW[N1], cPSI[NQ][NPR], cPW[2 * K + 1
 
 static void host_tables(double L[N1][N1], double D[N1][N1], double W[N1], double PSI[NQ][NPR],
                         double PW[2 * K + 1][N1]) {
-  // 4-point Gauss-Legendre rule: +-sqrt(3/7 -+ 2/7 sqrt(6/5)), weights (18 +- sqrt(30)) / 36
-  const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
-  const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
-  const double g[N1] = {-b, -a, a, b};
-  const double w[N1] = {wb, wa, wa, wb};
-  const double t[N1] = {-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0};   // Lagrange nodes
-  auto lag = [&](int i, double x) {
-    double v = 1.0;
-    for (int j = 0; j < N1; ++j)
-      if (j != i) v *= (x - t[j]) / (t[i] - t[j]);
-    return v;
-  };
-  auto dlag = [&](int i, double x) {
-    double s = 0.0;
-    for (int m = 0; m < N1; ++m) {
-      if (m == i) continue;
-      double v = 1.0 / (t[i] - t[m]);
-      for (int j = 0; j < N1; ++j)
-        if (j != i && j != m) v *= (x - t[j]) / (t[i] - t[j]);
-      s += v;
-    }
-    return s;
-  };
-  for (int q = 0; q < N1; ++q) {
-    W[q] = w[q];
-    for (int i = 0; i < N1; ++i) {
-      L[q][i] = lag(i, g[q]);
-      D[q][i] = dlag(i, g[q]);
-    }
-  }
+  double g[N1];
+  qk_tab::tables_1d(g, L, D, W, PW);
   const int ex[NPR][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
   for (int q = 0; q < NQ; ++q) {
     const double xi = g[q % N1], eta = g[q / N1];
     for (int p = 0; p < NPR; ++p) PSI[q][p] = pow(xi, ex[p][0]) * pow(eta, ex[p][1]);
   }
-  for (int f = 0; f <= 2 * K; ++f)
-    for (int i = 0; i < N1; ++i) PW[f][i] = lag(i, (double)f / K - 1.0);
 }
 
 // uploaded once per process (before any context of order 3 captures a cycle)
@@ -667,10 +638,14 @@ __global__ void k_qk_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const 
 // ---------------------------------------------------------------------------
 // entry points used by the dispatchers of operator.cu, patches.cu, transfer.cu, coarse.cu
 // ---------------------------------------------------------------------------
-void qk_tables() { qk::ensure_tables(); }
+void qk_tables() {
+  qk::ensure_tables();
+  qk3_tables();
+}
 
 void qk_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
               cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_apply(L, prec, mode, gamma, x, y, p_in, p_out, s);
   if (prec == PREC_F64) qk::apply_t<double>(L, mode, gamma, x, y, p_in, p_out, s);
   else qk::apply_t<float>(L, mode, gamma, x, y, p_in, p_out, s);
 }
@@ -695,11 +670,13 @@ static void apply_epi_t(const LevelDev& L, double gamma, const void* x, void* y,
 
 void qk_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (L.g.dim == 3) return qk3_apply_epi(L, prec, gamma, x, y, e, s, e0, e1);
   if (prec == PREC_F64) apply_epi_t<double>(L, gamma, x, y, e, s, e0, e1);
   else apply_epi_t<float>(L, gamma, x, y, e, s, e0, e1);
 }
 
 void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_load_vector(L, f_qp, F, s);
   const long long tot = L.g.ncells * qk::NE;
   qk::k_qk_load<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, f_qp, (double*)L.ebuf);
   qk::k_qk_gather<double><<<(unsigned)((2 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const double*)L.ebuf, nullptr, F,
@@ -709,12 +686,14 @@ void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream
 
 void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
                    DevStatus* st, cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_mass_setup(L, gamma, w_mu, variant, winv64, winv32, S, st, s);
   qk::k_qk_mass<<<(unsigned)((L.g.ncells + 127) / 128), 128, 0, s>>>(L.g, gamma, L.mu64, w_mu, variant, winv64, winv32,
                                                                      S, st);
   count_launch(1);
 }
 
 void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_patch_setup(L, gamma, st, s);
   qk::k_qk_star_setup<<<(unsigned)L.g.nverts, 256, 0, s>>>(L.g, gamma, L.mu64, L.winv64, L.inv64, L.inv32, L.pstride,
                                                            st);
   count_launch(1);
@@ -722,6 +701,7 @@ void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t
 
 void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
                      cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_patch_smooth(L, prec, r, z, scratch, den, s);
   const unsigned b2 = (unsigned)((2 * L.g.N + 255) / 256);
   constexpr int W64 = qk::star_warps<double>(), W32 = qk::star_warps<float>();
   if (prec == PREC_F64) {
@@ -737,6 +717,7 @@ void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* 
 }
 
 void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s) {
+  if (fine.g.dim == 3) return qk3_interior_solve(fine, prec, in, out, subtract, s);
   const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2);
   const size_t es = prec == PREC_F64 ? 8 : 4;
   if (!subtract) cudaMemsetAsync(out, 0, es * 2 * fine.g.N, s);
@@ -752,6 +733,7 @@ void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out
 
 void qk_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
                 void* xadd) {
+  if (fine.g.dim == 3) return qk3_prolong(coarse, fine, prec, xc, xf, s, xadd);
   const unsigned b = (unsigned)((2 * fine.g.N + 255) / 256);
   if (prec == PREC_F64)
     qk::k_qk_prolong<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
@@ -761,6 +743,7 @@ void qk_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const vo
 
 void qk_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
                  const void* sub) {
+  if (fine.g.dim == 3) return qk3_restrict(coarse, fine, prec, rf, rc, s, sub);
   const unsigned b = (unsigned)((2 * coarse.g.N + 255) / 256);
   if (prec == PREC_F64)
     qk::k_qk_restrict<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);

@@ -1,0 +1,959 @@
+// The order-3 discretisation in three dimensions: [Q3]^3 x P2^disc on uniform hexahedral
+// meshes (the discretisation of the 3D sinker runs, Table linear, and the k = 3 column of
+// Table k, Sec. 5.2.2), FP64 and FP32: operator applies, vertex-star setup and smoother,
+// robust transfers, coarse images, mass and Schur blocks, so that the context's cycle and
+// FGMRES run on it unchanged (qk.cu's entry points dispatch here for 3D levels).
+//
+// Velocity: continuous Q3, nodal basis on the 4 equispaced nodes -1, -1/3, 1/3, 1 per axis
+// and cell, node lattice 3n + 1 per direction, x fastest; local node a = ax + 4 ay + 16 az.
+// Pressure: discontinuous P2, the monomials in reference coordinates ordered by total
+// degree, then x before y before z: {1, xi, eta, zeta, xi^2, xi eta, xi zeta, eta^2,
+// eta zeta, zeta^2}; 10 per cell.  Quadrature: 4 x 4 x 4 Gauss-Legendre points, point
+// q = qx + 4 qy + 16 qz.  Vertex stars: the free nodes at lattice offsets -2..2 from 3v in
+// each direction (125 nodes, 375 dofs at an interior vertex); the interior of a coarse cell
+// is the star of the fine vertex at its centre (Eq. (Ptilde)).
+//
+// The cell kernel factorises the tensor-product basis (sum factorisation: three 4-point
+// contractions per direction instead of the 64 x 64 point-node products), one 64-thread
+// group per cell.  The 375 x 375 star matrices do not fit in shared memory: each CTA of the
+// persistent setup kernel assembles its star in a global workspace row block and inverts it
+// by block Gauss-Jordan elimination (16 pivots per pass, the pivot block and the panels in
+// shared memory).  Deterministic: per-cell and per-star outputs are staged and summed per
+// node in a fixed order.
+#include <math.h>
+
+#include <type_traits>
+
+#include "cell.cuh"
+#include "krylov.h"
+#include "level.h"
+#include "qk_tables.h"
+
+namespace als {
+namespace qk3 {
+
+constexpr int K = 3;
+constexpr int N1 = K + 1;          // nodes (and Gauss points) per axis and cell
+constexpr int NB = N1 * N1 * N1;   // nodes per cell (64)
+constexpr int NQ = NB;             // Gauss points per cell
+constexpr int NPR = 10;            // pressure monomials per cell
+constexpr int S1 = 2 * K - 1;      // star nodes per axis (5)
+constexpr int SN = S1 * S1 * S1;   // star nodes (125)
+constexpr int NS = 3 * SN;         // star dofs (375)
+constexpr int NF = 2 * K + 1;      // fine lattice nodes per coarse cell and axis (7)
+constexpr int CPB = 4;             // cells per block of the cell kernel (64 threads each)
+
+__constant__ double cL[N1][N1], cD[N1][N1], cW[N1], cPSI[NQ][NPR], cPW[NF][N1];
+
+void ensure_tables() {
+  static bool done = false;
+  if (done) return;
+  double G[N1], L[N1][N1], D[N1][N1], W[N1], PW[NF][N1], PSI[NQ][NPR];
+  qk_tab::tables_1d(G, L, D, W, PW);
+  const int ex[NPR][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                          {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+  for (int q = 0; q < NQ; ++q) {
+    const double x[3] = {G[q % N1], G[(q / N1) % N1], G[q / (N1 * N1)]};
+    for (int p = 0; p < NPR; ++p) PSI[q][p] = pow(x[0], ex[p][0]) * pow(x[1], ex[p][1]) * pow(x[2], ex[p][2]);
+  }
+  cudaMemcpyToSymbol(cL, L, sizeof(L));
+  cudaMemcpyToSymbol(cD, D, sizeof(D));
+  cudaMemcpyToSymbol(cW, W, sizeof(W));
+  cudaMemcpyToSymbol(cPSI, PSI, sizeof(PSI));
+  cudaMemcpyToSymbol(cPW, PW, sizeof(PW));
+  done = true;
+}
+
+__device__ __forceinline__ bool bnd_node(const Geom& g, int i, int j, int k) {
+  return i == 0 || i == g.nn[0] - 1 || j == 0 || j == g.nn[1] - 1 || k == 0 || k == g.nn[2] - 1;
+}
+__device__ __forceinline__ double wq_of(int q, double wdet) {
+  return cW[q % N1] * cW[(q / N1) % N1] * cW[q / (N1 * N1)] * wdet;
+}
+
+// ---------------------------------------------------------------------------
+// operator apply: 64 threads per cell.  Forward: u at the 64 nodes -> the 3 x 3 velocity
+// gradient at the 64 points by contractions along x, y, z; then the pressure moments
+// (B u)_p = -sum_q w |J| psi_p div u (a 64-thread reduction), the AL field
+// gamma psi . W^-1 B u and the flux s_cj = w |J| (2 mu eps_cj - P delta_cj) (2 / h_j);
+// backward: y_c(a) = sum_q sum_j s_cj d_j phi_a by the transposed contractions z, y, x.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CellShared {
+  T L[N1][N1], D[N1][N1];
+  T psi[NQ][NPR];
+  T wq[NQ];
+  T b0[CPB][9][NB];
+  T b1[CPB][9][NB];
+  T red[CPB][2][NPR];
+  T sp[CPB][NPR];
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(64 * CPB) k_qk3_cells(Geom g, double gamma, const T* __restrict__ x,
+                                                        const T* __restrict__ mu, const T* __restrict__ winv,
+                                                        const T* __restrict__ p_in, T* __restrict__ p_out,
+                                                        T* __restrict__ ebuf) {
+  constexpr bool RAW = (MODE & OP_RAW) != 0, VISC = (MODE & OP_VISC) != 0, AL = (MODE & OP_AL) != 0;
+  constexpr bool BT = (MODE & OP_BT) != 0, BO = (MODE & OP_B) != 0;
+  constexpr bool NEED_U = VISC || AL || BO, NEED_FLUX = VISC || AL || BT;
+  __shared__ CellShared<T> sh;
+  const int tid = threadIdx.x;
+  const double wdet = 0.125 * g.h[0] * g.h[1] * g.h[2];
+  if (tid < N1 * N1) {
+    sh.L[tid / N1][tid % N1] = (T)cL[tid / N1][tid % N1];
+    sh.D[tid / N1][tid % N1] = (T)cD[tid / N1][tid % N1];
+  }
+  for (int e = tid; e < NQ * NPR; e += blockDim.x) sh.psi[e / NPR][e % NPR] = (T)cPSI[e / NPR][e % NPR];
+  if (tid < NQ) sh.wq[tid] = (T)wq_of(tid, wdet);
+  const int w = tid >> 6, t = tid & 63, t0 = t & 3, t1 = (t >> 2) & 3, t2 = t >> 4;
+  const long long cell = (long long)blockIdx.x * CPB + w;
+  const bool valid = cell < g.ncells;
+  const int cx = valid ? (int)(cell % g.n[0]) : 0;
+  const int cy = valid ? (int)((cell / g.n[0]) % g.n[1]) : 0;
+  const int cz = valid ? (int)(cell / ((long long)g.n[0] * g.n[1])) : 0;
+  const T sx = (T)(2.0 / g.h[0]), sy = (T)(2.0 / g.h[1]), sz = (T)(2.0 / g.h[2]);
+  T(*b0)[NB] = sh.b0[w];
+  T(*b1)[NB] = sh.b1[w];
+  {
+    const int i = K * cx + t0, j = K * cy + t1, k = K * cz + t2;
+    const bool bnd = bnd_node(g, i, j, k);
+    const long long nd = node_id(g, i, j, k);
+    for (int c = 0; c < 3; ++c) b0[c][t] = (valid && NEED_U && (RAW || !bnd)) ? x[c * g.N + nd] : T(0);
+  }
+  __syncthreads();
+  // x: (ax, ay, az) -> (qx, ay, az): A = L u, B = D u
+  {
+    const int qx = t0, base = N1 * t1 + N1 * N1 * t2;
+    for (int c = 0; c < 3; ++c) {
+      T a = T(0), b = T(0);
+#pragma unroll
+      for (int ax = 0; ax < N1; ++ax) {
+        const T u = b0[c][base + ax];
+        a += sh.L[qx][ax] * u;
+        b += sh.D[qx][ax] * u;
+      }
+      b1[c][t] = a;
+      b1[3 + c][t] = b;
+    }
+  }
+  __syncthreads();
+  // y: (qx, ay, az) -> (qx, qy, az): AL = L A, AD = D A, BL = L B
+  {
+    const int qy = t1, base = t0 + N1 * N1 * t2;
+    for (int c = 0; c < 3; ++c) {
+      T al = T(0), ad = T(0), bl = T(0);
+#pragma unroll
+      for (int ay = 0; ay < N1; ++ay) {
+        const T a = b1[c][base + N1 * ay], b = b1[3 + c][base + N1 * ay];
+        al += sh.L[qy][ay] * a;
+        ad += sh.D[qy][ay] * a;
+        bl += sh.L[qy][ay] * b;
+      }
+      b0[c][t] = al;
+      b0[3 + c][t] = ad;
+      b0[6 + c][t] = bl;
+    }
+  }
+  __syncthreads();
+  // z: (qx, qy, az) -> (qx, qy, qz): the gradient G[c][j] at point q = t
+  T G[3][3];
+  {
+    const int qz = t2, base = t0 + N1 * t1;
+    for (int c = 0; c < 3; ++c) {
+      T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+      for (int az = 0; az < N1; ++az) {
+        const int o = base + N1 * N1 * az;
+        gx += sh.L[qz][az] * b0[6 + c][o];
+        gy += sh.L[qz][az] * b0[3 + c][o];
+        gz += sh.D[qz][az] * b0[c][o];
+      }
+      G[c][0] = gx * sx;
+      G[c][1] = gy * sy;
+      G[c][2] = gz * sz;
+    }
+  }
+  const int q = t;
+  const T div = G[0][0] + G[1][1] + G[2][2];
+  T P = T(0);   // gamma pi + p_in at the point
+  if (AL || BO) {
+    // (B u)_p over the cell's 64 points: warp sums, then the two warps in a fixed order
+    T bu[NPR];
+#pragma unroll
+    for (int p = 0; p < NPR; ++p) {
+      T v = -sh.wq[q] * sh.psi[q][p] * div;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      bu[p] = v;
+    }
+    if ((t & 31) == 0)
+      for (int p = 0; p < NPR; ++p) sh.red[w][t >> 5][p] = bu[p];
+    __syncthreads();
+    for (int p = 0; p < NPR; ++p) bu[p] = sh.red[w][0][p] + sh.red[w][1][p];
+    if (BO && valid && t == 0)
+      for (int p = 0; p < NPR; ++p) p_out[cell * NPR + p] = bu[p];
+    if (AL) {
+      if (valid && t < NPR) {
+        const T* Wc = winv + cell * NPR * NPR;
+        T s = T(0);
+        for (int r = 0; r < NPR; ++r) s += Wc[t * NPR + r] * bu[r];
+        sh.sp[w][t] = s;
+      }
+      __syncthreads();
+      T pi = T(0);
+      if (valid)
+        for (int p = 0; p < NPR; ++p) pi += sh.psi[q][p] * sh.sp[w][p];
+      P += (T)gamma * pi;
+    }
+  }
+  if (BT && valid)
+    for (int p = 0; p < NPR; ++p) P += sh.psi[q][p] * p_in[cell * NPR + p];
+  if (!NEED_FLUX) return;   // uniform over the block
+  {
+    const T m2 = (VISC && valid) ? T(2) * mu[cell * NQ + q] : T(0);
+    const T wq = sh.wq[q];
+    const T sj[3] = {sx, sy, sz};
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j) {
+        const T eps = T(0.5) * (G[c][j] + G[j][c]);
+        b1[3 * c + j][t] = wq * (m2 * eps - (c == j ? P : T(0))) * sj[j];
+      }
+  }
+  __syncthreads();
+  // z^T: (qx, qy, qz) -> (qx, qy, az): T0 = L s_c0, T1 = L s_c1, T2 = D s_c2
+  {
+    const int az = t2, base = t0 + N1 * t1;
+    for (int c = 0; c < 3; ++c) {
+      T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+      for (int qz = 0; qz < N1; ++qz) {
+        const int o = base + N1 * N1 * qz;
+        s0 += sh.L[qz][az] * b1[3 * c][o];
+        s1 += sh.L[qz][az] * b1[3 * c + 1][o];
+        s2 += sh.D[qz][az] * b1[3 * c + 2][o];
+      }
+      b0[3 * c][t] = s0;
+      b0[3 * c + 1][t] = s1;
+      b0[3 * c + 2][t] = s2;
+    }
+  }
+  __syncthreads();
+  // y^T: (qx, qy, az) -> (qx, ay, az): V = L T0 (x derivative still to come), W = D T1 + L T2
+  {
+    const int ay = t1, base = t0 + N1 * N1 * t2;
+    for (int c = 0; c < 3; ++c) {
+      T v = T(0), wv = T(0);
+#pragma unroll
+      for (int qy = 0; qy < N1; ++qy) {
+        const int o = base + N1 * qy;
+        v += sh.L[qy][ay] * b0[3 * c][o];
+        wv += sh.D[qy][ay] * b0[3 * c + 1][o] + sh.L[qy][ay] * b0[3 * c + 2][o];
+      }
+      b1[c][t] = v;
+      b1[3 + c][t] = wv;
+    }
+  }
+  __syncthreads();
+  // x^T: (qx, ay, az) -> (ax, ay, az): y_c = D V + L W
+  if (valid) {
+    const int ax = t0, base = N1 * t1 + N1 * N1 * t2;
+    for (int c = 0; c < 3; ++c) {
+      T y = T(0);
+#pragma unroll
+      for (int qx = 0; qx < N1; ++qx) y += sh.D[qx][ax] * b1[c][base + qx] + sh.L[qx][ax] * b1[3 + c][base + qx];
+      ebuf[(cell * 3 + c) * NB + t] = y;
+    }
+  }
+}
+
+// the cells (and local index) containing lattice index i along an axis of n cells
+__device__ __forceinline__ int cells_of(int i, int n, int (&c)[2], int (&a)[2]) {
+  int m = 0;
+  const int c0 = i / K, r = i - K * c0;
+  if (r == 0 && c0 > 0) { c[m] = c0 - 1; a[m] = K; ++m; }
+  if (c0 < n) { c[m] = c0; a[m] = r; ++m; }
+  return m;
+}
+
+// y(node) = sum of the staged cell outputs of the (up to 8) cells containing it, fixed
+// order; keep_bnd: y = x at Dirichlet nodes; raw: no Dirichlet treatment
+template <typename T>
+__device__ __forceinline__ T gather_value(const Geom& g, const T* __restrict__ ebuf, const T* __restrict__ x,
+                                          long long t, int keep_bnd, int raw) {
+  const int comp = (int)(t / g.N);
+  const long long nd = t - comp * g.N;
+  const int i = (int)(nd % g.nn[0]);
+  const long long r = nd / g.nn[0];
+  const int j = (int)(r % g.nn[1]), k = (int)(r / g.nn[1]);
+  if (bnd_node(g, i, j, k) && !raw) return keep_bnd ? x[t] : T(0);
+  int cxs[2], axs[2], cys[2], ays[2], czs[2], azs[2];
+  const int mx = cells_of(i, g.n[0], cxs, axs), my = cells_of(j, g.n[1], cys, ays), mz = cells_of(k, g.n[2], czs, azs);
+  T acc = T(0);
+  for (int c = 0; c < mz; ++c)
+    for (int b = 0; b < my; ++b)
+      for (int a = 0; a < mx; ++a) {
+        const long long cell = (long long)cxs[a] + (long long)g.n[0] * ((long long)cys[b] + (long long)g.n[1] * czs[c]);
+        acc += ebuf[(cell * 3 + comp) * NB + axs[a] + N1 * ays[b] + N1 * N1 * azs[c]];
+      }
+  return acc;
+}
+
+template <typename T>
+__global__ void k_qk3_gather(Geom g, const T* __restrict__ ebuf, const T* __restrict__ x, T* __restrict__ y,
+                             int keep_bnd, int raw) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * g.N) return;
+  y[t] = gather_value<T>(g, ebuf, x, t, keep_bnd, raw);
+}
+
+// the gather fused with the GMRES smoother's Arnoldi reduction (as for the other
+// discretisations): y = b + sigma A x; start = 0: out[j] = (V_j . y) / hn[j], j < k;
+// start = 1: |y|^2 starts the GMRES cycle.  Block partials in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_qk3_gather_epi(Geom g, const T* __restrict__ ebuf,
+                                                                const T* __restrict__ x, T* __restrict__ y,
+                                                                const T* __restrict__ b, double sigma, int k,
+                                                                const T* __restrict__ V, long long ld,
+                                                                T* __restrict__ out, int start, GmresDev sd,
+                                                                double* __restrict__ partial) {
+  __shared__ T nrm2_s[1];
+  const GmresView<T> st = gmres_view<T>(sd);
+  T* rows = reinterpret_cast<T*>(partial + 1);
+  const int kk = start ? 1 : k;
+  T acc[KMAXB];
+#pragma unroll
+  for (int jj = 0; jj < KMAXB; ++jj) acc[jj] = T(0);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 3 * g.N) {
+    const T v = (b ? b[t] : T(0)) + (T)sigma * gather_value<T>(g, ebuf, x, t, 1, 0);
+    y[t] = v;
+    if (start) {
+      acc[0] = v * v;
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < KMAXB; ++jj)
+        if (jj < k) acc[jj] = V[(long long)jj * ld + t] * v;
+    }
+  }
+  block_partials<T, T>(acc, kk, rows + (long long)blockIdx.x * kk);
+  if (last_block(partial)) {
+    if (start) {
+      finish_sums<T>(partial, 1, nrm2_s);
+      if (threadIdx.x == 0) gmres_start(st, nrm2_s[0]);
+    } else {
+      finish_sums<T>(partial, k, out, st.hn);
+    }
+  }
+}
+
+template <typename T, int MODE>
+static void apply_mode(const LevelDev& L, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+                       cudaStream_t s) {
+  constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
+  const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
+  const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
+  k_qk3_cells<T, MODE><<<(unsigned)((L.g.ncells + CPB - 1) / CPB), 64 * CPB, 0, s>>>(
+      L.g, gamma, (const T*)x, mu, winv, (const T*)p_in, (T*)p_out, (T*)L.ebuf);
+  if (NEED_FLUX) {
+    const int keep = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
+    k_qk3_gather<T><<<(unsigned)((3 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const T*)L.ebuf, (const T*)x, (T*)y,
+                                                                         keep, (MODE & OP_RAW) ? 1 : 0);
+  }
+  count_launch(NEED_FLUX ? 2 : 1);
+}
+
+template <typename T>
+static void apply_t(const LevelDev& L, int mode, double gamma, const void* x, void* y, const void* p_in, void* p_out,
+                    cudaStream_t s) {
+  switch (mode) {
+    case OP_VISC | OP_AL: apply_mode<T, OP_VISC | OP_AL>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_AL: apply_mode<T, OP_AL>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_B: apply_mode<T, OP_B>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_BT: apply_mode<T, OP_BT>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_VISC | OP_AL | OP_BT | OP_B: apply_mode<T, OP_VISC | OP_AL | OP_BT | OP_B>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_VISC | OP_AL | OP_RAW: apply_mode<T, OP_VISC | OP_AL | OP_RAW>(L, gamma, x, y, p_in, p_out, s); break;
+    case OP_B | OP_RAW: apply_mode<T, OP_B | OP_RAW>(L, gamma, x, y, p_in, p_out, s); break;
+    default: break;
+  }
+}
+
+template <typename T>
+static void apply_epi_t(const LevelDev& L, double gamma, const void* x, void* y, const ApplyEpi& e, cudaStream_t s,
+                        cudaEvent_t e0, cudaEvent_t e1) {
+  const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
+  const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
+  // External records become event-record nodes when the stream is being captured
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  k_qk3_cells<T, OP_VISC | OP_AL><<<(unsigned)((L.g.ncells + CPB - 1) / CPB), 64 * CPB, 0, s>>>(
+      L.g, gamma, (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  k_qk3_gather_epi<T><<<(unsigned)((3 * L.g.N + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0, s>>>(
+      L.g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out, e.start,
+      e.st, e.partial);
+  count_launch(2);
+}
+
+// F_(c,a) = sum_q |J| w_q f_c(x_q) phi_a(x_q), staged per cell, summed per node; f is
+// [cell][q][3]
+__global__ void k_qk3_load(Geom g, const double* __restrict__ f, double* __restrict__ ebuf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.ncells * 3 * NB) return;
+  const long long cell = t / (3 * NB);
+  const int e = (int)(t % (3 * NB)), comp = e / NB, a = e % NB;
+  const int ax = a % N1, ay = (a / N1) % N1, az = a / (N1 * N1);
+  const double wdet = 0.125 * g.h[0] * g.h[1] * g.h[2];
+  double acc = 0.0;
+  for (int q = 0; q < NQ; ++q) {
+    const double phi = cL[q % N1][ax] * cL[(q / N1) % N1][ay] * cL[q / (N1 * N1)][az];
+    acc += wq_of(q, wdet) * f[(cell * NQ + q) * 3 + comp] * phi;
+  }
+  ebuf[(cell * 3 + comp) * NB + a] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// per-cell mass blocks: M_K(1/mu)^-1 and M_K^-1 (10 x 10, Gauss-Jordan), the augmentation
+// weight's inverse W^-1 (W = M_p or M_p(1/mu)) and the Schur blocks S of Eq. (P1P2):
+// P1: M_K(1/mu)^-1 + gamma M_K^-1, P2: (1 + gamma) M_K(1/mu)^-1.  One thread per cell.
+// ---------------------------------------------------------------------------
+__device__ void inv10(double (&A)[NPR][NPR], DevStatus* st, long long where) {
+  double Iv[NPR][NPR];
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j < NPR; ++j) Iv[i][j] = i == j ? 1.0 : 0.0;
+  for (int k = 0; k < NPR; ++k) {
+    const double pv = A[k][k];
+    if (!(pv > 0.0)) { report(st, 4 /* ALS_ENOTSPD */, where); return; }
+    const double ip = 1.0 / pv;
+    for (int j = 0; j < NPR; ++j) { A[k][j] *= ip; Iv[k][j] *= ip; }
+    for (int i = 0; i < NPR; ++i) {
+      if (i == k) continue;
+      const double f = A[i][k];
+      for (int j = 0; j < NPR; ++j) { A[i][j] -= f * A[k][j]; Iv[i][j] -= f * Iv[k][j]; }
+    }
+  }
+  for (int i = 0; i < NPR; ++i)
+    for (int j = 0; j < NPR; ++j) A[i][j] = Iv[i][j];
+}
+
+__global__ void k_qk3_mass(Geom g, double gamma, const double* __restrict__ mu, int w_mu, int variant,
+                           double* __restrict__ winv64, float* __restrict__ winv32, double* __restrict__ S,
+                           DevStatus* st) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncells) return;
+  const double wdet = 0.125 * g.h[0] * g.h[1] * g.h[2];
+  double Mm[NPR][NPR], M[NPR][NPR];
+  for (int p = 0; p < NPR; ++p)
+    for (int r = 0; r < NPR; ++r) { Mm[p][r] = 0.0; M[p][r] = 0.0; }
+  for (int q = 0; q < NQ; ++q) {
+    const double wq = wq_of(q, wdet);
+    const double im = 1.0 / mu[cell * NQ + q];
+    for (int p = 0; p < NPR; ++p)
+      for (int r = 0; r < NPR; ++r) {
+        M[p][r] += wq * cPSI[q][p] * cPSI[q][r];
+        Mm[p][r] += wq * im * cPSI[q][p] * cPSI[q][r];
+      }
+  }
+  inv10(Mm, st, cell);
+  inv10(M, st, cell);
+  for (int p = 0; p < NPR; ++p)
+    for (int r = 0; r < NPR; ++r) {
+      const double wv = w_mu ? Mm[p][r] : M[p][r];
+      if (winv64) winv64[cell * NPR * NPR + p * NPR + r] = wv;
+      if (winv32) winv32[cell * NPR * NPR + p * NPR + r] = (float)wv;
+      if (S) S[cell * NPR * NPR + p * NPR + r] = variant == 0 ? Mm[p][r] + gamma * M[p][r] : (1.0 + gamma) * Mm[p][r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vertex stars: setup (assembly from the star's 8 cells into a workspace row block in
+// global memory, block Gauss-Jordan inversion, FP64 packed-by-diagonals and its FP32
+// rounding), products, node gather
+// ---------------------------------------------------------------------------
+// star entry e = comp * 125 + (ox + 2) + 5 (oy + 2) + 25 (oz + 2) of vertex v: node 3v + o
+__device__ __forceinline__ bool star_node(const Geom& g, int vx, int vy, int vz, int e, long long& nd) {
+  const int o = e % SN;
+  const int i = K * vx + o % S1 - (K - 1), j = K * vy + (o / S1) % S1 - (K - 1), k = K * vz + o / (S1 * S1) - (K - 1);
+  if (i <= 0 || i >= g.nn[0] - 1 || j <= 0 || j >= g.nn[1] - 1 || k <= 0 || k >= g.nn[2] - 1) return false;
+  nd = node_id(g, i, j, k);
+  return true;
+}
+
+constexpr int LDM = NS + 1;   // row stride of a star matrix in the workspace (doubles)
+constexpr int BB = 16;        // pivots per Gauss-Jordan pass
+constexpr int SETUP_THREADS = 256;
+// shared memory of the setup kernel (doubles): the assembly's tables or the elimination's
+// pivot block and panels, whichever is larger
+constexpr int ASM_DOUBLES = NQ * 27 * 3 + NQ + 2 * NPR * 81 + 8 * 3 * 3;
+constexpr int GJ_DOUBLES = BB * BB + 2 * BB * NS + 2 * BB;
+constexpr int SETUP_DOUBLES = ASM_DOUBLES > GJ_DOUBLES ? ASM_DOUBLES : GJ_DOUBLES;
+constexpr size_t SETUP_SMEM = sizeof(double) * SETUP_DOUBLES + 16;
+
+// One CTA per star at a time (persistent over the stars v = blockIdx.x, += gridDim.x), its
+// star matrix in ws + blockIdx.x * NS * LDM.
+__global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double gamma, const double* __restrict__ mu,
+                                                                  const double* __restrict__ winv,
+                                                                  double* __restrict__ ws, double* __restrict__ inv64,
+                                                                  float* __restrict__ inv32, int pstride,
+                                                                  DevStatus* st) {
+  extern __shared__ double smem[];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* M = ws + (long long)blockIdx.x * NS * LDM;
+  const double sx = 2.0 / g.h[0], sy = 2.0 / g.h[1], sz = 2.0 / g.h[2];
+  const double wdet = 0.125 * g.h[0] * g.h[1] * g.h[2];
+  for (long long v = blockIdx.x; v < g.nverts; v += gridDim.x) {
+    const int vx = (int)(v % g.nv[0]), vy = (int)((v / g.nv[0]) % g.nv[1]), vz = (int)(v / ((long long)g.nv[0] * g.nv[1]));
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < NS * LDM; e += nt) M[e] = 0.0;
+    __syncthreads();
+    // ---- assembly: the cells (cx, cy, cz) in {v-1, v}^3 inside the mesh
+    double* gq = smem;                      // [q][n][3]: d_j phi_n at q, the cell's 27 star nodes n
+    double* wm = gq + NQ * 27 * 3;          // [q]: w |J| mu
+    double* Bm = wm + NQ;                   // [p][c * 27 + n]: -sum_q w |J| psi_p d_c phi_n
+    double* WB = Bm + NPR * 81;             // W^-1 Bm
+    for (int cc = 0; cc < 8; ++cc) {
+      const int cx = vx - 1 + (cc & 1), cy = vy - 1 + ((cc >> 1) & 1), cz = vz - 1 + (cc >> 2);
+      if (cx < 0 || cy < 0 || cz < 0 || cx >= g.n[0] || cy >= g.n[1] || cz >= g.n[2]) continue;   // uniform
+      const long long cell = (long long)cx + (long long)g.n[0] * ((long long)cy + (long long)g.n[1] * cz);
+      // the star's nodes in this cell: local index a = m + off per axis, m = 0..2
+      const int offx = cx == vx - 1 ? 1 : 0, offy = cy == vy - 1 ? 1 : 0, offz = cz == vz - 1 ? 1 : 0;
+      for (int e = tid; e < NQ * 27; e += nt) {
+        const int q = e / 27, n = e % 27;
+        const int ax = n % 3 + offx, ay = (n / 3) % 3 + offy, az = n / 9 + offz;
+        const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
+        gq[e * 3 + 0] = cD[qx][ax] * cL[qy][ay] * cL[qz][az] * sx;
+        gq[e * 3 + 1] = cL[qx][ax] * cD[qy][ay] * cL[qz][az] * sy;
+        gq[e * 3 + 2] = cL[qx][ax] * cL[qy][ay] * cD[qz][az] * sz;
+      }
+      for (int q = tid; q < NQ; q += nt) wm[q] = wq_of(q, wdet) * mu[cell * NQ + q];
+      __syncthreads();
+      for (int e = tid; e < NPR * 81; e += nt) {
+        const int p = e / 81, j = e % 81, c = j / 27, n = j % 27;
+        double acc = 0.0;
+        for (int q = 0; q < NQ; ++q) acc -= wq_of(q, wdet) * cPSI[q][p] * gq[(q * 27 + n) * 3 + c];
+        Bm[e] = acc;
+      }
+      __syncthreads();
+      const double* Wc = winv + cell * NPR * NPR;
+      for (int e = tid; e < NPR * 81; e += nt) {
+        const int p = e / 81, j = e % 81;
+        double acc = 0.0;
+        for (int r = 0; r < NPR; ++r) acc += Wc[p * NPR + r] * Bm[r * 81 + j];
+        WB[e] = acc;
+      }
+      __syncthreads();
+      // node pairs: H[a][b] = sum_q w |J| mu d_a phi_ni d_b phi_nj; the element entry of
+      // (ci, ni), (cj, nj) is 2 mu eps(phi_ni e_ci) : eps(phi_nj e_cj) integrated,
+      // = delta_(ci cj) trace H + H[cj][ci], plus gamma (B^T W^-1 B)
+      for (int e = tid; e < 27 * 27; e += nt) {
+        const int ni = e / 27, nj = e % 27;
+        double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int q = 0; q < NQ; ++q) {
+          const double* gi = gq + (q * 27 + ni) * 3;
+          const double* gj = gq + (q * 27 + nj) * 3;
+          const double wv = wm[q];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const double wa = wv * gi[a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) H[a][b] += wa * gj[b];
+          }
+        }
+        const double tr = H[0][0] + H[1][1] + H[2][2];
+        const int sni = (ni % 3 + offx + K * cx - K * vx + 2) + S1 * ((ni / 3) % 3 + offy + K * cy - K * vy + 2) +
+                        S1 * S1 * (ni / 9 + offz + K * cz - K * vz + 2);
+        const int snj = (nj % 3 + offx + K * cx - K * vx + 2) + S1 * ((nj / 3) % 3 + offy + K * cy - K * vy + 2) +
+                        S1 * S1 * (nj / 9 + offz + K * cz - K * vz + 2);
+        for (int ci = 0; ci < 3; ++ci)
+          for (int cj = 0; cj < 3; ++cj) {
+            double al = 0.0;
+            for (int p = 0; p < NPR; ++p) al += Bm[p * 81 + ci * 27 + ni] * WB[p * 81 + cj * 27 + nj];
+            M[(long long)(ci * SN + sni) * LDM + cj * SN + snj] += (ci == cj ? tr : 0.0) + H[cj][ci] + gamma * al;
+          }
+      }
+      __syncthreads();
+    }
+    // identity rows and columns at absent and Dirichlet nodes
+    for (int e = tid; e < NS * NS; e += nt) {
+      const int i = e / NS, j = e % NS;
+      long long nd;
+      const bool fi = star_node(g, vx, vy, vz, i, nd), fj = star_node(g, vx, vy, vz, j, nd);
+      if (!fi || !fj) M[(long long)i * LDM + j] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // ---- block Gauss-Jordan inversion in place (SPD: the pivot blocks are Schur
+    // complements, no pivoting).  Per pass over pivots K = [k0, k0 + b): Dk = M_KK^-1,
+    // R = Dk M_K. (row panel), C = M_.K (column panel); then M_KK = Dk, M_Kj = R_j,
+    // M_iK = -C_i Dk, M_ij -= C_i R_j.
+    double* Dk = smem;                  // [BB][BB]
+    double* R = Dk + BB * BB;           // [BB][NS]
+    double* C = R + BB * NS;            // [NS][BB]
+    double* rowk = C + NS * BB;         // [BB]
+    double* colk = rowk + BB;           // [BB]
+    for (int k0 = 0; k0 < NS; k0 += BB) {
+      const int b = NS - k0 < BB ? NS - k0 : BB;
+      for (int e = tid; e < BB * BB; e += nt) {
+        const int m = e / BB, l = e % BB;
+        Dk[e] = (m < b && l < b) ? M[(long long)(k0 + m) * LDM + k0 + l] : (m == l ? 1.0 : 0.0);
+      }
+      __syncthreads();
+      for (int kk = 0; kk < b; ++kk) {   // scalar Gauss-Jordan on the pivot block
+        const double pv = Dk[kk * BB + kk];
+        if (!(pv > 0.0) && tid == 0 && !s_bad) { report(st, 4 /* ALS_ENOTSPD */, v); s_bad = 1; }
+        const double ip = pv > 0.0 ? 1.0 / pv : 1.0;
+        if (tid < BB) {
+          rowk[tid] = Dk[kk * BB + tid] * ip;
+          colk[tid] = Dk[tid * BB + kk];
+        }
+        __syncthreads();
+        if (tid < BB * BB) {
+          const int m = tid / BB, l = tid % BB;
+          double val;
+          if (m == kk && l == kk) val = ip;
+          else if (m == kk) val = rowk[l];
+          else if (l == kk) val = -colk[m] * ip;
+          else val = Dk[tid] - colk[m] * rowk[l];
+          Dk[tid] = val;
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < NS * BB; e += nt) {
+        const int i = e / BB, l = e % BB;
+        C[e] = l < b ? M[(long long)i * LDM + k0 + l] : 0.0;
+      }
+      for (int e = tid; e < BB * NS; e += nt) {
+        const int m = e / NS, j = e % NS;
+        double acc = 0.0;
+        if (m < b)
+          for (int l = 0; l < b; ++l) acc += Dk[m * BB + l] * M[(long long)(k0 + l) * LDM + j];
+        R[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < NS * NS; e += nt) {
+        const int i = e / NS, j = e % NS;
+        const int mi = i - k0, mj = j - k0;
+        const bool ik = mi >= 0 && mi < b, jk = mj >= 0 && mj < b;
+        double* p = M + (long long)i * LDM + j;
+        const double* ci = C + i * BB;
+        if (ik && jk) {
+          *p = Dk[mi * BB + mj];
+        } else if (ik) {
+          *p = R[mi * NS + j];
+        } else if (jk) {
+          double acc = 0.0;
+#pragma unroll
+          for (int l = 0; l < BB; ++l) acc += ci[l] * Dk[l * BB + mj];
+          *p = -acc;
+        } else {
+          double acc = *p;
+#pragma unroll
+          for (int l = 0; l < BB; ++l) acc -= ci[l] * R[l * NS + j];
+          *p = acc;
+        }
+      }
+      __syncthreads();
+    }
+    // upper triangle by diagonals (entry (i, i + t)), symmetrised
+    for (int t = 0; t < NS; ++t) {
+      const long long base = v * pstride + diag_start(NS, t);
+      for (int i = tid; i + t < NS; i += nt) {
+        const double val = 0.5 * (M[(long long)i * LDM + i + t] + M[(long long)(i + t) * LDM + i]);
+        inv64[base + i] = val;
+        inv32[base + i] = (float)val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y_v = A_v^-1 r|_v: one CTA of STAR_THREADS per star (vertex), rows by threads, over the
+// wrapped diagonals (row i takes entry (i, (i + t) mod NS): entry i of diagonal t while
+// i + t < NS, else entry i + t - NS of diagonal NS - t, its symmetric partner), so every
+// thread multiplies at every t and each diagonal is read by consecutive threads.
+// interior: the stars of the fine vertices 2c + 1 at the coarse-cell centres, written
+// (mode 1) or subtracted (mode 2) straight into the nodes; else into the rows [vertex][375].
+constexpr int STAR_THREADS = 128;
+constexpr int STAR_ROWS = (NS + STAR_THREADS - 1) / STAR_THREADS;
+
+template <typename T>
+__global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply(Geom g, const T* __restrict__ inv, int pstride,
+                                                                 int interior, int mode, const T* __restrict__ r,
+                                                                 T* __restrict__ out) {
+  __shared__ T rs[NS];
+  const int tid = threadIdx.x;
+  const int ic[3] = {g.n[0] / 2, g.n[1] / 2, g.n[2] / 2};
+  const long long count = interior ? (long long)ic[0] * ic[1] * ic[2] : g.nverts;
+  const long long item = blockIdx.x;
+  if (item >= count) return;   // uniform over the block
+  int vx, vy, vz;
+  if (interior) {
+    vx = 2 * (int)(item % ic[0]) + 1;
+    vy = 2 * (int)((item / ic[0]) % ic[1]) + 1;
+    vz = 2 * (int)(item / ((long long)ic[0] * ic[1])) + 1;
+  } else {
+    vx = (int)(item % g.nv[0]);
+    vy = (int)((item / g.nv[0]) % g.nv[1]);
+    vz = (int)(item / ((long long)g.nv[0] * g.nv[1]));
+  }
+  const long long v = (long long)vx + (long long)g.nv[0] * ((long long)vy + (long long)g.nv[1] * vz);
+  for (int e = tid; e < NS; e += STAR_THREADS) {
+    long long nd;
+    rs[e] = star_node(g, vx, vy, vz, e, nd) ? r[(e / SN) * g.N + nd] : T(0);
+  }
+  __syncthreads();
+  const T* S = inv + v * pstride;
+  T acc[STAR_ROWS];
+#pragma unroll
+  for (int k = 0; k < STAR_ROWS; ++k) acc[k] = T(0);
+#pragma unroll 4
+  for (int t = 0; t < NS; ++t) {
+    const T* du = S + diag_start(NS, t);
+    const T* dl = S + (t > 0 ? diag_start(NS, NS - t) - (NS - t) : 0);
+#pragma unroll
+    for (int k = 0; k < STAR_ROWS; ++k) {
+      const int i = tid + STAR_THREADS * k;
+      if (i < NS) {
+        const int j = i + t;
+        const bool up = j < NS;
+        const T* p = up ? du + i : dl + i;   // one load, from the selected diagonal
+        acc[k] += __ldg(p) * rs[up ? j : j - NS];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < STAR_ROWS; ++k) {
+    const int i = tid + STAR_THREADS * k;
+    if (i >= NS) continue;
+    if (!interior) {
+      out[v * NS + i] = acc[k];
+    } else {
+      long long nd;
+      if (star_node(g, vx, vy, vz, i, nd)) {
+        T* o = out + (i / SN) * g.N + nd;
+        *o = mode == 2 ? *o - acc[k] : acc[k];
+      }
+    }
+  }
+}
+
+// z(node) = sum over the (up to 8) stars containing the node (vertices v with
+// |i - 3v| <= 2 per axis), fixed order; 0 at Dirichlet nodes; divided by den[0] when given
+template <typename T>
+__global__ void k_qk3_star_gather(Geom g, const T* __restrict__ sc, T* __restrict__ z, const T* __restrict__ den) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * g.N) return;
+  const int comp = (int)(t / g.N);
+  const long long nd = t - comp * g.N;
+  const int i = (int)(nd % g.nn[0]);
+  const long long rr = nd / g.nn[0];
+  const int j = (int)(rr % g.nn[1]), k = (int)(rr / g.nn[1]);
+  if (bnd_node(g, i, j, k)) { z[t] = T(0); return; }
+  int vs[3][2], os[3][2], m[3];
+  const int ijk[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    const int v0 = ijk[a] / K, r = ijk[a] - K * v0;
+    m[a] = 0;
+    vs[a][m[a]] = v0; os[a][m[a]++] = r;
+    if (r != 0) { vs[a][m[a]] = v0 + 1; os[a][m[a]++] = r - K; }
+  }
+  T acc = T(0);
+  for (int c = 0; c < m[2]; ++c)
+    for (int b = 0; b < m[1]; ++b)
+      for (int a = 0; a < m[0]; ++a) {
+        const long long v = (long long)vs[0][a] + (long long)g.nv[0] * ((long long)vs[1][b] + (long long)g.nv[1] * vs[2][c]);
+        const int e = comp * SN + (os[0][a] + K - 1) + S1 * (os[1][b] + K - 1) + S1 * S1 * (os[2][c] + K - 1);
+        acc += sc[v * NS + e];
+      }
+  if (den) acc = den[0] != T(0) ? acc / den[0] : T(0);
+  z[t] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// transfers: P_H (the coarse Q3 basis at the fine nodes, tensor product of 1D weights;
+// each fine node belongs to the coarse cell min(f div 6, nc - 1) per axis) and its
+// transpose, as gathers; fine Dirichlet rows and coarse Dirichlet columns are zero
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int owner(int f, int nc, int& fr) {
+  int c = f / (2 * K);
+  if (c > nc - 1) c = nc - 1;
+  fr = f - 2 * K * c;
+  return c;
+}
+
+template <typename T>
+__global__ void k_qk3_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * gf.N) return;
+  const int comp = (int)(t / gf.N);
+  const long long nd = t - comp * gf.N;
+  const int i = (int)(nd % gf.nn[0]);
+  const long long rr = nd / gf.nn[0];
+  const int j = (int)(rr % gf.nn[1]), k = (int)(rr / gf.nn[1]);
+  T v = T(0);
+  if (!bnd_node(gf, i, j, k)) {
+    int fx, fy, fz;
+    const int cx = owner(i, gc.n[0], fx), cy = owner(j, gc.n[1], fy), cz = owner(k, gc.n[2], fz);
+    double acc = 0.0;
+    for (int c = 0; c < N1; ++c)
+      for (int b = 0; b < N1; ++b)
+        for (int a = 0; a < N1; ++a) {
+          const int I = K * cx + a, J = K * cy + b, Kz = K * cz + c;
+          if (bnd_node(gc, I, J, Kz)) continue;
+          acc += cPW[fx][a] * cPW[fy][b] * cPW[fz][c] * (double)xc[comp * gc.N + node_id(gc, I, J, Kz)];
+        }
+    v = (T)acc;
+  }
+  xf[t] = v;
+  if (xadd) xadd[t] += v;
+}
+
+// rc = P_H^T (rf - sub): coarse node J gathers the fine nodes owned by the coarse cells
+// that contain it, weighted by its basis function there
+template <typename T>
+__global__ void k_qk3_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub,
+                               T* __restrict__ rc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * gc.N) return;
+  const int comp = (int)(t / gc.N);
+  const long long nd = t - comp * gc.N;
+  const int I = (int)(nd % gc.nn[0]);
+  const long long rr = nd / gc.nn[0];
+  const int J = (int)(rr % gc.nn[1]), Kz = (int)(rr / gc.nn[1]);
+  if (bnd_node(gc, I, J, Kz)) { rc[t] = T(0); return; }
+  int cs[3][2], as[3][2], m[3];
+  m[0] = cells_of(I, gc.n[0], cs[0], as[0]);
+  m[1] = cells_of(J, gc.n[1], cs[1], as[1]);
+  m[2] = cells_of(Kz, gc.n[2], cs[2], as[2]);
+  double acc = 0.0;
+  for (int c = 0; c < m[2]; ++c)
+    for (int b = 0; b < m[1]; ++b)
+      for (int a = 0; a < m[0]; ++a)
+        for (int fz = 0; fz < NF; ++fz) {
+          if (fz == NF - 1 && cs[2][c] != gc.n[2] - 1) continue;   // owned by the next coarse cell
+          const int k = 2 * K * cs[2][c] + fz;
+          if (k == 0 || k == gf.nn[2] - 1) continue;
+          const double wz = cPW[fz][as[2][c]];
+          if (wz == 0.0) continue;
+          for (int fy = 0; fy < NF; ++fy) {
+            if (fy == NF - 1 && cs[1][b] != gc.n[1] - 1) continue;
+            const int j = 2 * K * cs[1][b] + fy;
+            if (j == 0 || j == gf.nn[1] - 1) continue;
+            const double wy = cPW[fy][as[1][b]];
+            if (wy == 0.0) continue;
+            for (int fx = 0; fx < NF; ++fx) {
+              if (fx == NF - 1 && cs[0][a] != gc.n[0] - 1) continue;
+              const int i = 2 * K * cs[0][a] + fx;
+              if (i == 0 || i == gf.nn[0] - 1) continue;
+              const double wx = cPW[fx][as[0][a]];
+              if (wx == 0.0) continue;
+              const long long fn = comp * gf.N + node_id(gf, i, j, k);
+              acc += wx * wy * wz * (double)(sub ? rf[fn] - sub[fn] : rf[fn]);
+            }
+          }
+        }
+  rc[t] = (T)acc;
+}
+
+}  // namespace qk3
+
+// ---------------------------------------------------------------------------
+// entry points, called by qk.cu's dispatchers for 3D levels
+// ---------------------------------------------------------------------------
+void qk3_tables() { qk3::ensure_tables(); }
+
+void qk3_apply(const LevelDev& L, int prec, int mode, double gamma, const void* x, void* y, const void* p_in,
+               void* p_out, cudaStream_t s) {
+  if (prec == PREC_F64) qk3::apply_t<double>(L, mode, gamma, x, y, p_in, p_out, s);
+  else qk3::apply_t<float>(L, mode, gamma, x, y, p_in, p_out, s);
+}
+
+void qk3_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void* y, const ApplyEpi& e,
+                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (prec == PREC_F64) qk3::apply_epi_t<double>(L, gamma, x, y, e, s, e0, e1);
+  else qk3::apply_epi_t<float>(L, gamma, x, y, e, s, e0, e1);
+}
+
+void qk3_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
+  const long long tot = L.g.ncells * 3 * qk3::NB;
+  qk3::k_qk3_load<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g, f_qp, (double*)L.ebuf);
+  qk3::k_qk3_gather<double><<<(unsigned)((3 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const double*)L.ebuf, nullptr,
+                                                                               F, 0, 1);
+  count_launch(2);
+}
+
+void qk3_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
+                    DevStatus* st, cudaStream_t s) {
+  qk3::k_qk3_mass<<<(unsigned)((L.g.ncells + 127) / 128), 128, 0, s>>>(L.g, gamma, L.mu64, w_mu, variant, winv64,
+                                                                       winv32, S, st);
+  count_launch(1);
+}
+
+// CTAs of the star setup (each holds one 375 x 376 FP64 star matrix in the workspace)
+int qk3_setup_ctas(long long nverts) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = 2LL * sms;
+  return (int)(nverts < want ? nverts : want);
+}
+size_t qk3_setup_ws_doubles(int ctas) { return (size_t)ctas * qk3::NS * qk3::LDM; }
+
+void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(qk3::k_qk3_star_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qk3::SETUP_SMEM);
+    attr = true;
+  }
+  const int ctas = L.qk_ws_ctas < L.g.nverts ? L.qk_ws_ctas : (int)L.g.nverts;
+  qk3::k_qk3_star_setup<<<(unsigned)ctas, qk3::SETUP_THREADS, qk3::SETUP_SMEM, s>>>(
+      L.g, gamma, L.mu64, L.winv64, L.qk_ws, L.inv64, L.inv32, L.pstride, st);
+  count_launch(1);
+}
+
+void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
+                      cudaStream_t s) {
+  const unsigned b3 = (unsigned)((3 * L.g.N + 255) / 256);
+  const unsigned nv = (unsigned)L.g.nverts;
+  if (prec == PREC_F64) {
+    qk3::k_qk3_star_apply<double><<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv64, L.pstride, 0, 0, (const double*)r,
+                                                                   (double*)scratch);
+    qk3::k_qk3_star_gather<double><<<b3, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
+  } else {
+    qk3::k_qk3_star_apply<float><<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv32, L.pstride, 0, 0, (const float*)r,
+                                                                  (float*)scratch);
+    qk3::k_qk3_star_gather<float><<<b3, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
+  }
+  count_launch(2);
+}
+
+void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s) {
+  const long long nc = (long long)(fine.g.n[0] / 2) * (fine.g.n[1] / 2) * (fine.g.n[2] / 2);
+  const size_t es = prec == PREC_F64 ? 8 : 4;
+  if (!subtract) cudaMemsetAsync(out, 0, es * 3 * fine.g.N, s);
+  if (prec == PREC_F64)
+    qk3::k_qk3_star_apply<double><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
+        fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
+  else
+    qk3::k_qk3_star_apply<float><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
+        fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
+  count_launch(1);
+}
+
+void qk3_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
+                 void* xadd) {
+  const unsigned b = (unsigned)((3 * fine.g.N + 255) / 256);
+  if (prec == PREC_F64)
+    qk3::k_qk3_prolong<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
+  else qk3::k_qk3_prolong<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+  count_launch(1);
+}
+
+void qk3_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
+                  const void* sub) {
+  const unsigned b = (unsigned)((3 * coarse.g.N + 255) / 256);
+  if (prec == PREC_F64)
+    qk3::k_qk3_restrict<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
+  else qk3::k_qk3_restrict<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
+  count_launch(1);
+}
+
+}  // namespace als

@@ -90,16 +90,16 @@ def sample_points_k(d, n, k):
     return x
 
 
-def sinker_problem_k(n, levels, k, count, omega, delta, dr, beta=10.0, gamma=1e2, seed=0):
-    """The 2D multi-sinker problem sampled at the order-k Gauss points of every level
-    (rediscretisation): mu per level [cell][(k+1)^2], f at the finest points, u_D = 0."""
-    c = sinker_centres(seed, count, 2)
-    sizes = [tuple(v // 2 ** (levels - 1 - l) for v in _as_tuple(n, 2)) for l in range(levels)]
-    mus = [sinker_viscosity(sample_points_k(2, nl, k), c, omega, delta, dr) for nl in sizes]
-    f = sinker_force(sample_points_k(2, n, k), c, omega, delta, beta)
-    nn = tuple(k * v + 1 for v in _as_tuple(n, 2))
-    u_bc = np.zeros((2, nn[0] * nn[1]))
-    return Problem(f"sinker2d_q{k}", 2, _as_tuple(n, 2), levels, gamma, mus, f, u_bc,
+def sinker_problem_k(n, levels, k, count, omega, delta, dr, beta=10.0, gamma=1e2, seed=0, d=2):
+    """The multi-sinker problem in d dimensions sampled at the order-k Gauss points of every
+    level (rediscretisation): mu per level [cell][(k+1)^d], f at the finest points, u_D = 0."""
+    c = sinker_centres(seed, count, d)
+    sizes = [tuple(v // 2 ** (levels - 1 - l) for v in _as_tuple(n, d)) for l in range(levels)]
+    mus = [sinker_viscosity(sample_points_k(d, nl, k), c, omega, delta, dr) for nl in sizes]
+    f = sinker_force(sample_points_k(d, n, k), c, omega, delta, beta)
+    nn = tuple(k * v + 1 for v in _as_tuple(n, d))
+    u_bc = np.zeros((d, int(np.prod(nn))))
+    return Problem(f"sinker{d}d_q{k}", d, _as_tuple(n, d), levels, gamma, mus, f, u_bc,
                    {"centres": c, "order": k, "dr": dr})
 
 
