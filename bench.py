@@ -59,6 +59,11 @@ WORKLOADS = {
     # DR 1e6, gamma 1e2, P1 pairing
     "sinker2d_q3_128": dict(d=2, n=128, levels=5, count=8, omega=0.1, delta=200.0, dr=1e6, beta=10.0,
                             gamma=1e2, seed=0, sweeps=5, order=3),
+    # 3D multi-sinker with [Q3]^3 x P2disc, the element of the 3D runs of Table linear: 24^3
+    # hexes (1,167,051 velocity + 138,240 pressure DoFs), 4 levels (coarse 3^3), 24 sinkers,
+    # DR 1e8, gamma 1e3, P2 pairing (mixed mode refuses P1 there: 2^-24 gamma / mu_min = 0.6)
+    "sinker3d_q3_24": dict(d=3, n=24, levels=4, count=24, omega=0.1, delta=200.0, dr=1e8, beta=10.0,
+                           gamma=1e3, seed=0, sweeps=5, order=3, schur="P2"),
     # 3D anisotropic viscoplastic linearisation, 48^3 hexes, 4 levels (coarse 6^3): per-point
     # 4th-order tensor C (21 Mandel entries), mu_eff contrast ~1e10, gamma 1e3, P2 Schur pairing
     "viscoplastic3d_48": dict(kind="tensor", d=3, n=48, levels=4, gamma=1e3, seed=0, sweeps=5, schur="P2"),
@@ -69,6 +74,7 @@ SAMPLES = {
     "sinker2d_128": dict(cpu_baseline=dict(n=64, levels=4), reference=dict(n=32, levels=3)),
     "sinker3d_32_g1e4": dict(cpu_baseline=dict(n=12, levels=2), reference=dict(n=8, levels=3)),
     "sinker2d_q3_128": dict(cpu_baseline=dict(n=32, levels=3), reference=dict(n=16, levels=3)),
+    "sinker3d_q3_24": dict(cpu_baseline=dict(n=4, levels=2), reference=dict(n=4, levels=2)),
     "viscoplastic3d_48": dict(cpu_baseline=dict(n=8, levels=2), reference=dict(n=8, levels=2)),
 }
 RTOL = 1e-8
@@ -81,7 +87,7 @@ def make_problem(spec, n=None, levels=None):
     from synthetic.problems import sinker_problem, sinker_problem_k, viscoplastic_problem
     if spec.get("order", 2) == 3:
         return sinker_problem_k(n or spec["n"], levels or spec["levels"], 3, spec["count"], spec["omega"],
-                                spec["delta"], spec["dr"], spec["beta"], spec["gamma"], spec["seed"])
+                                spec["delta"], spec["dr"], spec["beta"], spec["gamma"], spec["seed"], d=spec["d"])
     if spec.get("kind") == "tensor":
         return viscoplastic_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["gamma"], spec["seed"])
     return sinker_problem(spec["d"], n or spec["n"], levels or spec["levels"], spec["count"], spec["omega"],
@@ -92,7 +98,12 @@ def problem_dofs(pb):
     """Free velocity DoFs + pressure DoFs of the finest level."""
     k = pb.meta.get("order", 2)
     free_nodes = math.prod(k * v - 1 for v in pb.n)
-    return pb.d * free_nodes + (6 if k == 3 else pb.d + 1) * math.prod(pb.n)
+    return pb.d * free_nodes + pressure_per_cell(pb.d, k) * math.prod(pb.n)
+
+
+def pressure_per_cell(d, k):
+    """Dimension of P_(k-1)^disc on a cell: C(k - 1 + d, d)."""
+    return math.comb(k - 1 + d, d)
 
 
 # --------------------------------------------------------------------------
@@ -232,7 +243,7 @@ def oracle_sample_step(spec, n, levels):
     p2 = spec.get("schur") == "P2"
     if spec.get("order", 2) == 3:
         from oracle.qk import HierarchyK
-        H = HierarchyK(2, pb.n, 3, pb.mu, pb.gamma, steps=spec["sweeps"], W="Mp_mu" if p2 else "Mp")
+        H = HierarchyK(pb.d, pb.n, 3, pb.mu, pb.gamma, steps=spec["sweeps"], W="Mp_mu" if p2 else "Mp")
     else:
         H = Hierarchy(pb.d, pb.n, pb.mu, pb.gamma, steps=spec["sweeps"], kind=spec.get("kind", "scalar"),
                       mu_eff=pb.meta.get("mu_eff"), W="Mp_mu" if p2 else "Mp")
@@ -336,6 +347,11 @@ METRIC = "AL-MG V-cycles/s & solve DoF/s to 1e-8 rel. residual, mixed vs FP64, 1
 # flops per cell of the sum-factorised A_gamma apply (scalar mu): forward
 # gradients, point-wise stress and AL projection, transposed contractions
 APPLY_FLOPS_PER_CELL = {2: 1100, 3: 8000}
+# order 3 (scalar mu), as the kernels compute it: 2D, products over the 16 x 16 point-node
+# pairs (gradient 1,024 + transposed 1,024 FMAs, pressure 228 FMAs, stress ~190 flops);
+# 3D, sum-factorised (contractions 6,144 forward + 6,144 transposed FMAs, pressure 1,380
+# FMAs, stress ~2,900 flops)
+APPLY_FLOPS_PER_CELL_Q3 = {2: 4700, 3: 30200}
 
 
 def ours(args, dist):
@@ -356,7 +372,7 @@ def ours(args, dist):
     f_d, ubc_d = dev(pb.f), dev(pb.u_bc)
     order = spec.get("order", 2)
     nu = pb.d * math.prod(order * v + 1 for v in pb.n)
-    npres = (6 if order == 3 else pb.d + 1) * math.prod(pb.n)
+    npres = pressure_per_cell(pb.d, order) * math.prod(pb.n)
     u_d = torch.zeros(nu, dtype=torch.float64, device="cuda")
     p_d = torch.zeros(npres, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
@@ -464,9 +480,10 @@ def ours(args, dist):
     # double-float (options.setup = ALS_SETUP_FP64): setup time, iterations, solution
     # difference from the double-float setup's solution
     setup_fp64 = None
-    if not args.quick and order == 2:
+    if not args.quick and (order == 2 or pb.d == 3):   # 2D order 3 sets up in FP64 in both modes
         ctxf = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, mu_eff=mue_d, stream=stream, mode=A.ALS_MODE_MIXED,
-                       rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, setup=A.ALS_SETUP_FP64)
+                       rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, setup=A.ALS_SETUP_FP64,
+                       order=order)
         uf, pf = torch.zeros_like(u_d), torch.zeros_like(p_d)
         ctxf.solve(f_d, ubc_d, None, uf, pf)
         torch.cuda.synchronize()
@@ -606,22 +623,31 @@ def ours(args, dist):
     nint = math.prod(v - 1 for v in F) if (order == 2 and nverts >= 32768) else nverts
     npatch = pb.d * (2 * order - 1) ** pb.d
     packed = npatch * (npatch + 1) // 2
-    bytes_per_launch = nint * (packed * 4 + npatch * 4) + nu * 4
+    if order == 2:
+        bytes_per_launch = nint * (packed * 4 + npatch * 4) + nu * 4
+    else:
+        # order 3 times the star products and their node gather together: packed inverse
+        # read, output rows written and read back, r read, z written
+        bytes_per_launch = nint * (packed * 4 + 2 * npatch * 4) + 2 * nu * 4
     k4_launch_s = (k4_ms / max(k4_n, 1)) / 1e3
     achieved = bytes_per_launch / k4_launch_s / 1e9 if k4_n else None
     peak, peak_kind = measured_peak_hbm()
     # operator apply (K1 cell kernel) on the finest level, timed live inside the smoother
     ncells = math.prod(F)
-    nq = 3 ** pb.d
+    nq = (order + 1) ** pb.d
     ncq = (6 if pb.d == 2 else 21) if tensor else 1
-    fused = pb.d == 3 and os.environ.get("ALS_FUSE_GATHER", "1") != "0"
+    fused = pb.d == 3 and order == 2 and os.environ.get("ALS_FUSE_GATHER", "1") != "0"
     if fused:
         # the 3D smoother's cell kernel also forms Z_j from the star-patch outputs: read the
         # patch outputs, write Z_j and the staged cell outputs, read mu or C (FP32)
         k1_bytes = nverts * npatch * 4 + nu * 4 + ncells * nq * pb.d * 4 + ncells * nq * ncq * 4
     else:
         k1_bytes = nu * 4 * 2 + ncells * nq * ncq * 4      # read x, write y, read mu or C (FP32)
-    k1_flops = ncells * (APPLY_FLOPS_PER_CELL[pb.d] + (nq * 2 * 2 * ncq if tensor else 0))
+    if order == 3:   # the cell kernel reads x, mu and W^-1 and stages its outputs per cell (FP32)
+        k1_bytes = nu * 4 + ncells * nq * 4 + ncells * pressure_per_cell(pb.d, 3) ** 2 * 4 + \
+            ncells * nq * pb.d * 4
+    k1_flops = ncells * ((APPLY_FLOPS_PER_CELL_Q3 if order == 3 else APPLY_FLOPS_PER_CELL)[pb.d] +
+                         (nq * 2 * 2 * ncq if tensor else 0))
     k1_s = (k1_ms / max(k1_n, 1)) / 1e3
     roofline_apply = None
     if k1_n:
@@ -634,8 +660,9 @@ def ours(args, dist):
         roofline_apply = dict(hbm if tensor else alu)
         roofline_apply.update({
             "bound": "hbm" if tensor else "alu",
-            "kernel": "k_apply_lines (FP32 A_gamma cell kernel%s, finest level)"
-                      % (" with the fused patch gather" if fused else ""),
+            "kernel": ("k_apply_lines (FP32 A_gamma cell kernel%s, finest level)"
+                       % (" with the fused patch gather" if fused else "")) if order == 2 else
+                      "k_qk%s_cells<float> (FP32 order-3 A_gamma cell kernel, finest level)" % ("3" if pb.d == 3 else ""),
             ("alu" if tensor else "hbm"): alu if tensor else hbm,
             "us_per_launch": k1_s * 1e6, "launches_timed": k1_n,
             "bytes_per_launch": k1_bytes, "flops_per_launch": k1_flops})
@@ -665,7 +692,8 @@ def ours(args, dist):
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm",
                      "kernel": ("k_patch_tma<%d> (FP32 interior-star smoother, finest level)" % pb.d) if order == 2
-                     else "k_qk_star_apply<float> + k_qk_star_gather (FP32 order-3 star smoother, finest level)",
+                     else "k_qk%s_star_apply<float> + k_qk%s_star_gather (FP32 order-3 star smoother, finest level)"
+                     % (("3", "3") if pb.d == 3 else ("", "")),
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "bytes_per_launch": bytes_per_launch, "launches_timed": k4_n,

@@ -130,9 +130,11 @@ typedef struct {
                      the coefficients of the monomials of degree <= 2 in reference
                      coordinates, by degree, x before y before z: {1, xi, eta, xi^2, xi eta,
                      eta^2} in 2D, {1, xi, eta, zeta, xi^2, xi eta, xi zeta, eta^2, eta zeta,
-                     zeta^2} in 3D; vertex stars of 5^d nodes (50 / 375 dofs) assembled and
-                     inverted in FP64 in both modes.  3D stars take 564 KB (FP64) + 282 KB
-                     (FP32) per vertex and about 57 M FP64 multiply-adds each to set up) */
+                     zeta^2} in 3D; vertex stars of 5^d nodes (50 / 375 dofs) assembled in
+                     FP64 and inverted in FP64, except 3D stars under the setup option's
+                     double-float arithmetic (ALS_MODE_MIXED with ALS_SETUP_AUTO); 3D stars
+                     take 564 KB (FP64) + 282 KB (FP32) per vertex and about 57 M
+                     multiply-adds each to set up) */
   int store;      /* storage of the star inverses the FP32 cycle streams: ALS_STORE_FP32
                      (default), or ALS_STORE_BF16: the block-packed stars (every star, or the
                      interior ones on levels stored split) rounded to bfloat16 to nearest,

@@ -759,12 +759,13 @@ static als_status run_setup(als_ctx* c, const als_coeff* coeff) {
   ALS_TRY(check_mixed_range(c));
   if (c->k == 3) {
     // order 3: per-cell W^-1 of every level (the AL term of the operator and the stars) and
-    // the finest level's Schur blocks, then the stars (FP64) and the coarse inverse
+    // the finest level's Schur blocks, then the stars (FP64 assembly; the 3D elimination in
+    // double-float when df64, else FP64) and the coarse inverse
     const int p2 = c->opt.schur == ALS_SCHUR_P2 ? 1 : 0;
     for (int l = 0; l < c->L; ++l) {
       LevelDev& Lv = c->lev[l];
       qk_mass_setup(Lv, c->gamma, p2, p2, Lv.winv64, Lv.winv32, l == c->L - 1 ? c->schur : nullptr, c->st, c->stream);
-      if (l > 0) patch_setup(Lv, c->gamma, 1, 0, c->st, c->stream);
+      if (l > 0) patch_setup(Lv, c->gamma, 1, df64, c->st, c->stream);
       ALS_TRY(cuda_check(c, "order-3 setup"));
     }
     coarse_setup(c->lev[0], c->gamma, &c->coarse, c->st, c->stream, df64);

@@ -139,7 +139,8 @@ void qk_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void
 // of Eq. (P1P2) (variant 0: P1, 1: P2)
 void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, double* winv64, float* winv32, double* S,
                    DevStatus* st, cudaStream_t s);
-void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s);
+// df64: 3D levels eliminate in double-float (2D order 3 is FP64 throughout)
+void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64);
 void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
                      cudaStream_t s);
 void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s);
@@ -160,7 +161,8 @@ void qk3_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, doub
 // (doubles; one 375 x 376 FP64 star matrix per CTA), held in LevelDev::qk_ws
 int qk3_setup_ctas(long long nverts);
 size_t qk3_setup_ws_doubles(int ctas);
-void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s);
+// df64: the elimination in double-float arithmetic (the assembly stays FP64)
+void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64);
 void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
                       cudaStream_t s);
 void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s);

@@ -862,8 +862,8 @@ static void patch_setup_arith(const LevelDev& L, double gamma, int store32, int 
 }
 
 void patch_setup(const LevelDev& L, double gamma, int store32, int df64, DevStatus* st, cudaStream_t s) {
-  if (L.k == 3) {   // FP64 assembly and inversion, FP64 and FP32 copies
-    qk_patch_setup(L, gamma, st, s);
+  if (L.k == 3) {   // FP64 assembly; FP64 (3D mixed: double-float) inversion; FP64 and FP32 copies
+    qk_patch_setup(L, gamma, st, s, df64);
     return;
   }
   // shared-memory limit of the FP32 patch kernel, set here, before any graph capture

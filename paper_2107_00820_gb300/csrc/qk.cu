@@ -692,8 +692,8 @@ void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, doubl
   count_launch(1);
 }
 
-void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s) {
-  if (L.g.dim == 3) return qk3_patch_setup(L, gamma, st, s);
+void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64) {
+  if (L.g.dim == 3) return qk3_patch_setup(L, gamma, st, s, df64);
   qk::k_qk_star_setup<<<(unsigned)L.g.nverts, 256, 0, s>>>(L.g, gamma, L.mu64, L.winv64, L.inv64, L.inv32, L.pstride,
                                                            st);
   count_launch(1);

@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "cell.cuh"
+#include "df64.cuh"
 #include "krylov.h"
 #include "level.h"
 #include "qk_tables.h"
@@ -489,11 +490,16 @@ constexpr size_t SETUP_SMEM = sizeof(double) * SETUP_DOUBLES + 16;
 
 // One CTA per star at a time (persistent over the stars v = blockIdx.x, += gridDim.x), its
 // star matrix in ws + blockIdx.x * NS * LDM.
+// RM: the arithmetic of the elimination, double or DF64 (double-float, about 48 bits, on
+// the FP32 pipes; the assembly is FP64 either way)
+template <typename RM>
 __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double gamma, const double* __restrict__ mu,
                                                                   const double* __restrict__ winv,
                                                                   double* __restrict__ ws, double* __restrict__ inv64,
                                                                   float* __restrict__ inv32, int pstride,
                                                                   DevStatus* st) {
+  static_assert(sizeof(RM) == sizeof(double), "the workspace holds 8-byte entries");
+  using Ops = RealOps<RM>;
   extern __shared__ double smem[];
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -572,34 +578,40 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
       }
       __syncthreads();
     }
-    // identity rows and columns at absent and Dirichlet nodes
+    // identity rows and columns at absent and Dirichlet nodes; the entries in the
+    // elimination's arithmetic R from here on (each thread converts its own entries)
+    RM* Mr = reinterpret_cast<RM*>(M);
     for (int e = tid; e < NS * NS; e += nt) {
       const int i = e / NS, j = e % NS;
       long long nd;
       const bool fi = star_node(g, vx, vy, vz, i, nd), fj = star_node(g, vx, vy, vz, j, nd);
-      if (!fi || !fj) M[(long long)i * LDM + j] = i == j ? 1.0 : 0.0;
+      double* p = M + (long long)i * LDM + j;
+      const double val = (!fi || !fj) ? (i == j ? 1.0 : 0.0) : *p;
+      Mr[(long long)i * LDM + j] = Ops::from(val);
     }
     __syncthreads();
     // ---- block Gauss-Jordan inversion in place (SPD: the pivot blocks are Schur
     // complements, no pivoting).  Per pass over pivots K = [k0, k0 + b): Dk = M_KK^-1,
     // R = Dk M_K. (row panel), C = M_.K (column panel); then M_KK = Dk, M_Kj = R_j,
     // M_iK = -C_i Dk, M_ij -= C_i R_j.
-    double* Dk = smem;                  // [BB][BB]
-    double* R = Dk + BB * BB;           // [BB][NS]
-    double* C = R + BB * NS;            // [NS][BB]
-    double* rowk = C + NS * BB;         // [BB]
-    double* colk = rowk + BB;           // [BB]
+    RM* Dk = reinterpret_cast<RM*>(smem);   // [BB][BB]
+    RM* Rp = Dk + BB * BB;                  // [BB][NS]
+    RM* C = Rp + BB * NS;                   // [NS][BB]
+    RM* rowk = C + NS * BB;                 // [BB]
+    RM* colk = rowk + BB;                   // [BB]
+    const RM zero = Ops::from(0.0), one = Ops::from(1.0);
     for (int k0 = 0; k0 < NS; k0 += BB) {
       const int b = NS - k0 < BB ? NS - k0 : BB;
       for (int e = tid; e < BB * BB; e += nt) {
         const int m = e / BB, l = e % BB;
-        Dk[e] = (m < b && l < b) ? M[(long long)(k0 + m) * LDM + k0 + l] : (m == l ? 1.0 : 0.0);
+        Dk[e] = (m < b && l < b) ? Mr[(long long)(k0 + m) * LDM + k0 + l] : (m == l ? one : zero);
       }
       __syncthreads();
       for (int kk = 0; kk < b; ++kk) {   // scalar Gauss-Jordan on the pivot block
-        const double pv = Dk[kk * BB + kk];
-        if (!(pv > 0.0) && tid == 0 && !s_bad) { report(st, 4 /* ALS_ENOTSPD */, v); s_bad = 1; }
-        const double ip = pv > 0.0 ? 1.0 / pv : 1.0;
+        const RM pv = Dk[kk * BB + kk];
+        const bool ok = pv > 0.0f;
+        if (!ok && tid == 0 && !s_bad) { report(st, 4 /* ALS_ENOTSPD */, v); s_bad = 1; }
+        const RM ip = ok ? one / pv : one;
         if (tid < BB) {
           rowk[tid] = Dk[kk * BB + tid] * ip;
           colk[tid] = Dk[tid * BB + kk];
@@ -607,46 +619,46 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
         __syncthreads();
         if (tid < BB * BB) {
           const int m = tid / BB, l = tid % BB;
-          double val;
+          RM val;
           if (m == kk && l == kk) val = ip;
           else if (m == kk) val = rowk[l];
-          else if (l == kk) val = -colk[m] * ip;
-          else val = Dk[tid] - colk[m] * rowk[l];
+          else if (l == kk) val = -(colk[m] * ip);
+          else val = Ops::sub_prod(Dk[tid], colk[m], rowk[l]);
           Dk[tid] = val;
         }
         __syncthreads();
       }
       for (int e = tid; e < NS * BB; e += nt) {
         const int i = e / BB, l = e % BB;
-        C[e] = l < b ? M[(long long)i * LDM + k0 + l] : 0.0;
+        C[e] = l < b ? Mr[(long long)i * LDM + k0 + l] : zero;
       }
       for (int e = tid; e < BB * NS; e += nt) {
         const int m = e / NS, j = e % NS;
-        double acc = 0.0;
+        RM acc = zero;
         if (m < b)
-          for (int l = 0; l < b; ++l) acc += Dk[m * BB + l] * M[(long long)(k0 + l) * LDM + j];
-        R[e] = acc;
+          for (int l = 0; l < b; ++l) acc = Ops::add_prod(acc, Dk[m * BB + l], Mr[(long long)(k0 + l) * LDM + j]);
+        Rp[e] = acc;
       }
       __syncthreads();
       for (int e = tid; e < NS * NS; e += nt) {
         const int i = e / NS, j = e % NS;
         const int mi = i - k0, mj = j - k0;
         const bool ik = mi >= 0 && mi < b, jk = mj >= 0 && mj < b;
-        double* p = M + (long long)i * LDM + j;
-        const double* ci = C + i * BB;
+        RM* p = Mr + (long long)i * LDM + j;
+        const RM* ci = C + i * BB;
         if (ik && jk) {
           *p = Dk[mi * BB + mj];
         } else if (ik) {
-          *p = R[mi * NS + j];
+          *p = Rp[mi * NS + j];
         } else if (jk) {
-          double acc = 0.0;
+          RM acc = zero;
 #pragma unroll
-          for (int l = 0; l < BB; ++l) acc += ci[l] * Dk[l * BB + mj];
+          for (int l = 0; l < BB; ++l) acc = Ops::add_prod(acc, ci[l], Dk[l * BB + mj]);
           *p = -acc;
         } else {
-          double acc = *p;
+          RM acc = *p;
 #pragma unroll
-          for (int l = 0; l < BB; ++l) acc -= ci[l] * R[l * NS + j];
+          for (int l = 0; l < BB; ++l) acc = Ops::sub_prod(acc, ci[l], Rp[l * NS + j]);
           *p = acc;
         }
       }
@@ -656,7 +668,8 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
     for (int t = 0; t < NS; ++t) {
       const long long base = v * pstride + diag_start(NS, t);
       for (int i = tid; i + t < NS; i += nt) {
-        const double val = 0.5 * (M[(long long)i * LDM + i + t] + M[(long long)(i + t) * LDM + i]);
+        const double val = 0.5 * (Ops::to_double(Mr[(long long)i * LDM + i + t]) +
+                                  Ops::to_double(Mr[(long long)(i + t) * LDM + i]));
         inv64[base + i] = val;
         inv32[base + i] = (float)val;
       }
@@ -666,9 +679,9 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
 }
 
 // y_v = A_v^-1 r|_v: one CTA of STAR_THREADS per star (vertex), rows by threads, over the
-// wrapped diagonals (row i takes entry (i, (i + t) mod NS): entry i of diagonal t while
-// i + t < NS, else entry i + t - NS of diagonal NS - t, its symmetric partner), so every
-// thread multiplies at every t and each diagonal is read by consecutive threads.
+// wrapped diagonals (row i takes entry (i, (i + t) mod NS) at step t: entry i of diagonal t
+// while i + t < NS, else entry i + t - NS of diagonal NS - t, its symmetric partner), so
+// every thread multiplies at every step and each diagonal is read by consecutive threads.
 // interior: the stars of the fine vertices 2c + 1 at the coarse-cell centres, written
 // (mode 1) or subtracted (mode 2) straight into the nodes; else into the rows [vertex][375].
 constexpr int STAR_THREADS = 128;
@@ -704,18 +717,31 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply(Geom g, const T
   T acc[STAR_ROWS];
 #pragma unroll
   for (int k = 0; k < STAR_ROWS; ++k) acc[k] = T(0);
-#pragma unroll 4
-  for (int t = 0; t < NS; ++t) {
-    const T* du = S + diag_start(NS, t);
-    const T* dl = S + (t > 0 ? diag_start(NS, NS - t) - (NS - t) : 0);
+  // steps t and NS - t in the same iteration (NS is odd): both read the same two diagonals
+  // (t and NS - t), each entry once for its row and once for its symmetric partner's, so
+  // the second read of an entry follows the first within the iteration and hits in L1
+  // instead of coming back from HBM
+#pragma unroll
+  for (int k = 0; k < STAR_ROWS; ++k) {
+    const int i = tid + STAR_THREADS * k;
+    if (i < NS) acc[k] += __ldg(S + i) * rs[i];   // t = 0: the main diagonal
+  }
+#pragma unroll 2
+  for (int t = 1; t <= NS / 2; ++t) {
+    const int u = NS - t;
+    const T* dt = S + diag_start(NS, t);   // diagonal t (NS - t entries)
+    const T* du = S + diag_start(NS, u);   // diagonal NS - t (t entries)
 #pragma unroll
     for (int k = 0; k < STAR_ROWS; ++k) {
       const int i = tid + STAR_THREADS * k;
       if (i < NS) {
-        const int j = i + t;
-        const bool up = j < NS;
-        const T* p = up ? du + i : dl + i;   // one load, from the selected diagonal
-        acc[k] += __ldg(p) * rs[up ? j : j - NS];
+        // step t: entry (i, i + t) on diagonal t, else (i + t - NS, i) on diagonal NS - t;
+        // step NS - t: entry (i, i + NS - t) on diagonal NS - t, else (i - t, i) on diagonal t
+        const bool a = i < u, b = i < t;
+        const T* p1 = a ? dt + i : du + (i - u);   // one load each, from the selected diagonal
+        const T* p2 = b ? du + i : dt + (i - t);
+        acc[k] += __ldg(p1) * rs[a ? i + t : i - u];
+        acc[k] += __ldg(p2) * rs[b ? i + u : i - t];
       }
     }
   }
@@ -897,15 +923,22 @@ int qk3_setup_ctas(long long nverts) {
 }
 size_t qk3_setup_ws_doubles(int ctas) { return (size_t)ctas * qk3::NS * qk3::LDM; }
 
-void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s) {
+void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(qk3::k_qk3_star_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qk3::SETUP_SMEM);
+    cudaFuncSetAttribute(qk3::k_qk3_star_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)qk3::SETUP_SMEM);
+    cudaFuncSetAttribute(qk3::k_qk3_star_setup<DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)qk3::SETUP_SMEM);
     attr = true;
   }
   const int ctas = L.qk_ws_ctas < L.g.nverts ? L.qk_ws_ctas : (int)L.g.nverts;
-  qk3::k_qk3_star_setup<<<(unsigned)ctas, qk3::SETUP_THREADS, qk3::SETUP_SMEM, s>>>(
-      L.g, gamma, L.mu64, L.winv64, L.qk_ws, L.inv64, L.inv32, L.pstride, st);
+  if (df64)
+    qk3::k_qk3_star_setup<DF64><<<(unsigned)ctas, qk3::SETUP_THREADS, qk3::SETUP_SMEM, s>>>(
+        L.g, gamma, L.mu64, L.winv64, L.qk_ws, L.inv64, L.inv32, L.pstride, st);
+  else
+    qk3::k_qk3_star_setup<double><<<(unsigned)ctas, qk3::SETUP_THREADS, qk3::SETUP_SMEM, s>>>(
+        L.g, gamma, L.mu64, L.winv64, L.qk_ws, L.inv64, L.inv32, L.pstride, st);
   count_launch(1);
 }
 

@@ -92,6 +92,27 @@ def test_q3_3d_star_inverses_sampled():
         assert np.allclose(full[np.ix_(other, other)], np.eye(len(other)))
 
 
+def test_q3_3d_star_inverses_double_float():
+    """Mixed mode eliminates the 3D stars in double-float (unit roundoff 2^-48): the inverses
+    stay within the a-priori bound of elimination, n cond u (n = 375 pivots, u = 2^-48),
+    of the oracle's; ALS_SETUP_FP64 meets the FP64 form of the same bound, and the
+    double-float error is the larger one (it is the arithmetic, not the assembly)."""
+    pb = _problem(4, 2, 1e3, 1e6)
+    lv = LevelK(3, pb.n, 3, pb.mu[1], pb.gamma)
+    verts = all_vertices_k(lv.mesh)
+    vid = int(np.flatnonzero(np.all(verts == 2, axis=1))[0])
+    idx = star_dofs_k(lv.mesh, verts[vid])
+    Av = lv.A[idx][:, idx].toarray()
+    ref = np.linalg.inv(Av)
+    cond = np.linalg.cond(Av)
+    errs = {}
+    for setup, eps in ((A.ALS_SETUP_AUTO, 2.0 ** -48), (A.ALS_SETUP_FP64, 2.0 ** -53)):
+        full = _ctx(pb, mode=A.ALS_MODE_MIXED, setup=setup).patch_inverse(1, vid)
+        errs[setup] = np.linalg.norm(full - ref) / np.linalg.norm(ref)
+        assert errs[setup] <= 375 * cond * eps, (setup, errs[setup], cond)
+    assert errs[A.ALS_SETUP_FP64] < errs[A.ALS_SETUP_AUTO], errs
+
+
 @pytest.mark.parametrize("prec", [A.ALS_PREC_FP64, A.ALS_PREC_FP32])
 def test_q3_3d_star_smoother(prec):
     pb = _problem(4, 2, 1e2, 1e3)
