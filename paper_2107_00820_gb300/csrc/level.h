@@ -161,6 +161,10 @@ void qk3_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, doub
 // (doubles; one 375 x 376 FP64 star matrix per CTA), held in LevelDev::qk_ws
 int qk3_setup_ctas(long long nverts);
 size_t qk3_setup_ws_doubles(int ctas);
+// FP32 entries per star of a 3D order-3 level (inv32 holds the stars in wrapped rows), and
+// inv32 formed from inv64
+size_t qk3_star32_floats();
+void qk3_derive32(const LevelDev& L, cudaStream_t s);
 // df64: the elimination in double-float arithmetic (the assembly stays FP64)
 void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64);
 void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,

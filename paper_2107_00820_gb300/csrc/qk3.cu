@@ -479,6 +479,12 @@ __device__ __forceinline__ bool star_node(const Geom& g, int vx, int vy, int vz,
 }
 
 constexpr int LDM = NS + 1;   // row stride of a star matrix in the workspace (doubles)
+// FP32 star storage in wrapped rows (k_qk3_star_apply_w): WT rows of WLD entries
+constexpr int WT = (NS + 1) / 2;   // 188
+constexpr int WLD = 376;
+constexpr int WSTRIDE = WT * WLD;
+static_assert(NS % 2 == 1 && WLD % 4 == 0 && WLD >= NS, "wrapped-row layout");
+static_assert(WT % 2 == 0, "rows are streamed in pairs");
 constexpr int BB = 16;        // pivots per Gauss-Jordan pass
 constexpr int SETUP_THREADS = 256;
 // shared memory of the setup kernel (doubles): the assembly's tables or the elimination's
@@ -640,39 +646,58 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
         Rp[e] = acc;
       }
       __syncthreads();
-      for (int e = tid; e < NS * NS; e += nt) {
-        const int i = e / NS, j = e % NS;
-        const int mi = i - k0, mj = j - k0;
-        const bool ik = mi >= 0 && mi < b, jk = mj >= 0 && mj < b;
-        RM* p = Mr + (long long)i * LDM + j;
-        const RM* ci = C + i * BB;
-        if (ik && jk) {
-          *p = Dk[mi * BB + mj];
-        } else if (ik) {
-          *p = Rp[mi * NS + j];
-        } else if (jk) {
-          RM acc = zero;
+      // EPT entries per thread at a time, EPT independent chains: the chain of one entry
+      // is a sequence of dependent operations (16 double-float updates of ~15 FP32
+      // instructions each), so the entries of a thread interleave to hide its latency.
+      // Column block (jk): the chain on the column of Dk from 0 gives -C_i Dk; row block
+      // (ik) and pivot block take their value from Rp and Dk instead.
+      constexpr int EPT = 4;
+      for (int e0 = tid; e0 < NS * NS; e0 += EPT * nt) {
+        RM acc[EPT];
+        const RM* col[EPT];
+        int stride[EPT];
+        const RM* ci[EPT];
 #pragma unroll
-          for (int l = 0; l < BB; ++l) acc = Ops::add_prod(acc, ci[l], Dk[l * BB + mj]);
-          *p = -acc;
-        } else {
-          RM acc = *p;
+        for (int q = 0; q < EPT; ++q) {
+          const int e = e0 + q * nt;
+          const int ee = e < NS * NS ? e : 0;
+          const int i = ee / NS, j = ee % NS;
+          const int mj = j - k0;
+          const bool jk = mj >= 0 && mj < b;
+          ci[q] = C + i * BB;
+          col[q] = jk ? Dk + mj : Rp + j;
+          stride[q] = jk ? BB : NS;
+          acc[q] = jk ? zero : Mr[(long long)i * LDM + j];
+        }
 #pragma unroll
-          for (int l = 0; l < BB; ++l) acc = Ops::sub_prod(acc, ci[l], Rp[l * NS + j]);
-          *p = acc;
+        for (int l = 0; l < BB; ++l)
+#pragma unroll
+          for (int q = 0; q < EPT; ++q) acc[q] = Ops::sub_prod(acc[q], ci[q][l], col[q][l * stride[q]]);
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int e = e0 + q * nt;
+          if (e >= NS * NS) continue;
+          const int i = e / NS, j = e % NS;
+          const int mi = i - k0, mj = j - k0;
+          const bool ik = mi >= 0 && mi < b, jk = mj >= 0 && mj < b;
+          Mr[(long long)i * LDM + j] = (ik && jk) ? Dk[mi * BB + mj] : (ik ? Rp[mi * NS + j] : acc[q]);
         }
       }
       __syncthreads();
     }
-    // upper triangle by diagonals (entry (i, i + t)), symmetrised
+    // FP64: upper triangle by diagonals (entry (i, i + t)); FP32: the wrapped rows; both
+    // symmetrised
     for (int t = 0; t < NS; ++t) {
       const long long base = v * pstride + diag_start(NS, t);
-      for (int i = tid; i + t < NS; i += nt) {
-        const double val = 0.5 * (Ops::to_double(Mr[(long long)i * LDM + i + t]) +
-                                  Ops::to_double(Mr[(long long)(i + t) * LDM + i]));
-        inv64[base + i] = val;
-        inv32[base + i] = (float)val;
-      }
+      for (int i = tid; i + t < NS; i += nt)
+        inv64[base + i] = 0.5 * (Ops::to_double(Mr[(long long)i * LDM + i + t]) +
+                                 Ops::to_double(Mr[(long long)(i + t) * LDM + i]));
+    }
+    for (int e = tid; e < WSTRIDE; e += nt) {
+      const int t = e / WLD, i = e % WLD, j = i + t < NS ? i + t : i + t - NS;
+      inv32[v * WSTRIDE + e] = i < NS ? (float)(0.5 * (Ops::to_double(Mr[(long long)i * LDM + j]) +
+                                                       Ops::to_double(Mr[(long long)j * LDM + i])))
+                                      : 0.f;
     }
     __syncthreads();
   }
@@ -761,6 +786,121 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply(Geom g, const T
   }
 }
 
+// FP32 star storage, "wrapped rows": for odd NS every unordered pair {i, j}, i != j, has a
+// circular distance t = (j - i) mod NS or NS - t in 1..(NS - 1) / 2, so the symmetric
+// matrix is the WT = (NS + 1) / 2 rows W_t[i] = A(i, (i + t) mod NS), t = 0..WT - 1, each
+// padded to WLD = 376 entries (16-byte rows) -- 70,688 floats per star against 70,500 for
+// the packed triangle.  The product y_i = sum_t W_t[i] r_(i+t) + sum_(t>0) W_t[i-t] r_(i-t)
+// (indices mod NS) then reads each row once, coalesced, 16 bytes a thread.
+
+// y_v = A_v^-1 r|_v from the wrapped rows: one CTA per star, rows by threads; the rows of
+// W stream through shared memory two at a time (double-buffered, the next pair's 16-byte
+// loads in flight while the current pair is used); r is held twice over so that
+// r_((i + t) mod NS) needs no wrap.  interior / mode as k_qk3_star_apply.
+constexpr int WV = WLD / 4;   // float4 per row (94)
+__global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const float* __restrict__ inv,
+                                                                   int interior, int mode,
+                                                                   const float* __restrict__ r,
+                                                                   float* __restrict__ out) {
+  __shared__ float rs2[2 * NS];
+  __shared__ __align__(16) float wsh[2][2][WLD];
+  const int tid = threadIdx.x;
+  const int ic[3] = {g.n[0] / 2, g.n[1] / 2, g.n[2] / 2};
+  const long long count = interior ? (long long)ic[0] * ic[1] * ic[2] : g.nverts;
+  const long long item = blockIdx.x;
+  if (item >= count) return;   // uniform over the block
+  int vx, vy, vz;
+  if (interior) {
+    vx = 2 * (int)(item % ic[0]) + 1;
+    vy = 2 * (int)((item / ic[0]) % ic[1]) + 1;
+    vz = 2 * (int)(item / ((long long)ic[0] * ic[1])) + 1;
+  } else {
+    vx = (int)(item % g.nv[0]);
+    vy = (int)((item / g.nv[0]) % g.nv[1]);
+    vz = (int)(item / ((long long)g.nv[0] * g.nv[1]));
+  }
+  const long long v = (long long)vx + (long long)g.nv[0] * ((long long)vy + (long long)g.nv[1] * vz);
+  const float4* W = reinterpret_cast<const float4*>(inv + v * WSTRIDE);
+  // a pair of rows is 2 * WV = 188 float4: thread tid takes float4 tid and tid + 128
+  constexpr int PAIR = 2 * WV;
+  float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+  f0 = __ldg(W + tid);
+  if (tid + STAR_THREADS < PAIR) f1 = __ldg(W + tid + STAR_THREADS);
+  for (int e = tid; e < NS; e += STAR_THREADS) {
+    long long nd;
+    const float val = star_node(g, vx, vy, vz, e, nd) ? r[(e / SN) * g.N + nd] : 0.f;
+    rs2[e] = val;
+    rs2[e + NS] = val;
+  }
+  float acc[STAR_ROWS];
+#pragma unroll
+  for (int k = 0; k < STAR_ROWS; ++k) acc[k] = 0.f;
+  float* w0 = &wsh[0][0][0];
+  reinterpret_cast<float4*>(w0)[tid] = f0;
+  if (tid + STAR_THREADS < PAIR) reinterpret_cast<float4*>(w0)[tid + STAR_THREADS] = f1;
+  __syncthreads();
+  for (int pr = 0; pr < WT / 2; ++pr) {
+    const int cur = pr & 1;
+    if (pr + 1 < WT / 2) {   // the next pair's loads, in flight during this pair's products
+      const float4* Wn = W + (long long)(pr + 1) * PAIR;
+      f0 = __ldg(Wn + tid);
+      if (tid + STAR_THREADS < PAIR) f1 = __ldg(Wn + tid + STAR_THREADS);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = 2 * pr + h;
+      const float* wr = wsh[cur][h];
+#pragma unroll
+      for (int k = 0; k < STAR_ROWS; ++k) {
+        const int i = tid + STAR_THREADS * k;
+        if (i < NS) {
+          acc[k] += wr[i] * rs2[i + t];
+          if (t > 0) {
+            const int m = i - t < 0 ? i - t + NS : i - t;   // row m = i - t (mod NS) holds A(m, i)
+            acc[k] += wr[m] * rs2[m];
+          }
+        }
+      }
+    }
+    if (pr + 1 < WT / 2) {
+      float* wn = &wsh[cur ^ 1][0][0];
+      reinterpret_cast<float4*>(wn)[tid] = f0;
+      if (tid + STAR_THREADS < PAIR) reinterpret_cast<float4*>(wn)[tid + STAR_THREADS] = f1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < STAR_ROWS; ++k) {
+    const int i = tid + STAR_THREADS * k;
+    if (i >= NS) continue;
+    if (!interior) {
+      out[v * NS + i] = acc[k];
+    } else {
+      long long nd;
+      if (star_node(g, vx, vy, vz, i, nd)) {
+        float* o = out + (i / SN) * g.N + nd;
+        *o = mode == 2 ? *o - acc[k] : acc[k];
+      }
+    }
+  }
+}
+
+// the wrapped FP32 rows from the FP64 packed diagonals (loading caller-supplied inverses)
+__global__ void k_qk3_wrap32(long long nverts, int pstride, const double* __restrict__ inv64,
+                             float* __restrict__ inv32) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nverts * WSTRIDE) return;
+  const long long v = e / WSTRIDE;
+  const int r = (int)(e % WSTRIDE), t = r / WLD, i = r % WLD;
+  float val = 0.f;
+  if (i < NS) {
+    const int j = i + t;
+    const double* S = inv64 + v * pstride;
+    val = (float)(j < NS ? S[diag_start(NS, t) + i] : S[diag_start(NS, NS - t) + (j - NS)]);
+  }
+  inv32[e] = val;
+}
+
 // z(node) = sum over the (up to 8) stars containing the node (vertices v with
 // |i - 3v| <= 2 per axis), fixed order; 0 at Dirichlet nodes; divided by den[0] when given
 template <typename T>
@@ -832,51 +972,62 @@ __global__ void k_qk3_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __r
   if (xadd) xadd[t] += v;
 }
 
-// rc = P_H^T (rf - sub): coarse node J gathers the fine nodes owned by the coarse cells
-// that contain it, weighted by its basis function there
+// rc = P_H^T (rf - sub) in two steps.  Per coarse cell (one CTA): the 7^3 fine values it
+// owns (a fine node on the face shared with the next coarse cell belongs to that cell;
+// Dirichlet fine nodes are zero) contracted with the 1D weights along x, y, z into the
+// cell's 64 node values, staged per cell; then k_qk3_gather sums the staged values of the
+// cells containing each coarse node (zero at Dirichlet nodes).  A fine node outside the
+// cells of a coarse node lies where that node's basis function vanishes, so the owner
+// rule gives exactly P_H^T.
+constexpr int RS_THREADS = 128;
 template <typename T>
-__global__ void k_qk3_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const T* __restrict__ sub,
-                               T* __restrict__ rc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * gc.N) return;
-  const int comp = (int)(t / gc.N);
-  const long long nd = t - comp * gc.N;
-  const int I = (int)(nd % gc.nn[0]);
-  const long long rr = nd / gc.nn[0];
-  const int J = (int)(rr % gc.nn[1]), Kz = (int)(rr / gc.nn[1]);
-  if (bnd_node(gc, I, J, Kz)) { rc[t] = T(0); return; }
-  int cs[3][2], as[3][2], m[3];
-  m[0] = cells_of(I, gc.n[0], cs[0], as[0]);
-  m[1] = cells_of(J, gc.n[1], cs[1], as[1]);
-  m[2] = cells_of(Kz, gc.n[2], cs[2], as[2]);
-  double acc = 0.0;
-  for (int c = 0; c < m[2]; ++c)
-    for (int b = 0; b < m[1]; ++b)
-      for (int a = 0; a < m[0]; ++a)
-        for (int fz = 0; fz < NF; ++fz) {
-          if (fz == NF - 1 && cs[2][c] != gc.n[2] - 1) continue;   // owned by the next coarse cell
-          const int k = 2 * K * cs[2][c] + fz;
-          if (k == 0 || k == gf.nn[2] - 1) continue;
-          const double wz = cPW[fz][as[2][c]];
-          if (wz == 0.0) continue;
-          for (int fy = 0; fy < NF; ++fy) {
-            if (fy == NF - 1 && cs[1][b] != gc.n[1] - 1) continue;
-            const int j = 2 * K * cs[1][b] + fy;
-            if (j == 0 || j == gf.nn[1] - 1) continue;
-            const double wy = cPW[fy][as[1][b]];
-            if (wy == 0.0) continue;
-            for (int fx = 0; fx < NF; ++fx) {
-              if (fx == NF - 1 && cs[0][a] != gc.n[0] - 1) continue;
-              const int i = 2 * K * cs[0][a] + fx;
-              if (i == 0 || i == gf.nn[0] - 1) continue;
-              const double wx = cPW[fx][as[0][a]];
-              if (wx == 0.0) continue;
-              const long long fn = comp * gf.N + node_id(gf, i, j, k);
-              acc += wx * wy * wz * (double)(sub ? rf[fn] - sub[fn] : rf[fn]);
-            }
-          }
-        }
-  rc[t] = (T)acc;
+__global__ void __launch_bounds__(RS_THREADS) k_qk3_restrict_cells(Geom gc, Geom gf, const T* __restrict__ rf,
+                                                                   const T* __restrict__ sub, T* __restrict__ stage) {
+  __shared__ T v[3][NF * NF * NF];
+  __shared__ T t1[3][N1 * NF * NF];
+  __shared__ T t2[3][N1 * N1 * NF];
+  __shared__ T pw[NF][N1];
+  const int tid = threadIdx.x;
+  const long long cell = blockIdx.x;
+  const int cx = (int)(cell % gc.n[0]), cy = (int)((cell / gc.n[0]) % gc.n[1]),
+            cz = (int)(cell / ((long long)gc.n[0] * gc.n[1]));
+  if (tid < NF * N1) pw[tid / N1][tid % N1] = (T)cPW[tid / N1][tid % N1];
+  for (int e = tid; e < NF * NF * NF; e += RS_THREADS) {
+    const int fx = e % NF, fy = (e / NF) % NF, fz = e / (NF * NF);
+    const bool own = (fx < NF - 1 || cx == gc.n[0] - 1) && (fy < NF - 1 || cy == gc.n[1] - 1) &&
+                     (fz < NF - 1 || cz == gc.n[2] - 1);
+    const int i = 2 * K * cx + fx, j = 2 * K * cy + fy, k = 2 * K * cz + fz;
+    const bool use = own && !bnd_node(gf, i, j, k);
+    const long long nd = node_id(gf, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+      const long long fn = c * gf.N + nd;
+      v[c][e] = use ? (sub ? rf[fn] - sub[fn] : rf[fn]) : T(0);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * N1 * NF * NF; e += RS_THREADS) {   // x: (fx, fy, fz) -> (ax, fy, fz)
+    const int c = e / (N1 * NF * NF), r = e % (N1 * NF * NF), ax = r % N1, yz = r / N1;
+    T acc = T(0);
+#pragma unroll
+    for (int fx = 0; fx < NF; ++fx) acc += pw[fx][ax] * v[c][fx + NF * yz];
+    t1[c][r] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * N1 * N1 * NF; e += RS_THREADS) {   // y: (ax, fy, fz) -> (ax, ay, fz)
+    const int c = e / (N1 * N1 * NF), r = e % (N1 * N1 * NF), ax = r % N1, ay = (r / N1) % N1, fz = r / (N1 * N1);
+    T acc = T(0);
+#pragma unroll
+    for (int fy = 0; fy < NF; ++fy) acc += pw[fy][ay] * t1[c][ax + N1 * (fy + NF * fz)];
+    t2[c][r] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * NB; e += RS_THREADS) {              // z: (ax, ay, fz) -> (ax, ay, az)
+    const int c = e / NB, a = e % NB, axy = a % (N1 * N1), az = a / (N1 * N1);
+    T acc = T(0);
+#pragma unroll
+    for (int fz = 0; fz < NF; ++fz) acc += pw[fz][az] * t2[c][axy + N1 * N1 * fz];
+    stage[(cell * 3 + c) * NB + a] = acc;
+  }
 }
 
 }  // namespace qk3
@@ -922,6 +1073,13 @@ int qk3_setup_ctas(long long nverts) {
   return (int)(nverts < want ? nverts : want);
 }
 size_t qk3_setup_ws_doubles(int ctas) { return (size_t)ctas * qk3::NS * qk3::LDM; }
+size_t qk3_star32_floats() { return qk3::WSTRIDE; }
+
+void qk3_derive32(const LevelDev& L, cudaStream_t s) {
+  const long long tot = L.g.nverts * qk3::WSTRIDE;
+  qk3::k_qk3_wrap32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
+  count_launch(1);
+}
 
 void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64) {
   static bool attr = false;
@@ -951,8 +1109,7 @@ void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void*
                                                                    (double*)scratch);
     qk3::k_qk3_star_gather<double><<<b3, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
   } else {
-    qk3::k_qk3_star_apply<float><<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv32, L.pstride, 0, 0, (const float*)r,
-                                                                  (float*)scratch);
+    qk3::k_qk3_star_apply_w<<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r, (float*)scratch);
     qk3::k_qk3_star_gather<float><<<b3, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
   }
   count_launch(2);
@@ -966,8 +1123,8 @@ void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* ou
     qk3::k_qk3_star_apply<double><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
         fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
   else
-    qk3::k_qk3_star_apply<float><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
-        fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
+    qk3::k_qk3_star_apply_w<<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(fine.g, fine.inv32, 1, subtract ? 2 : 1,
+                                                                       (const float*)in, (float*)out);
   count_launch(1);
 }
 
@@ -980,13 +1137,21 @@ void qk3_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const v
   count_launch(1);
 }
 
+// the coarse level's per-cell output buffer stages the cell contributions (the coarse
+// level's own applies, which use it too, come after the restriction on the stream)
 void qk3_restrict(const LevelDev& coarse, const LevelDev& fine, int prec, const void* rf, void* rc, cudaStream_t s,
                   const void* sub) {
-  const unsigned b = (unsigned)((3 * coarse.g.N + 255) / 256);
-  if (prec == PREC_F64)
-    qk3::k_qk3_restrict<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)rf, (const double*)sub, (double*)rc);
-  else qk3::k_qk3_restrict<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)rf, (const float*)sub, (float*)rc);
-  count_launch(1);
+  const unsigned nc = (unsigned)coarse.g.ncells, b = (unsigned)((3 * coarse.g.N + 255) / 256);
+  if (prec == PREC_F64) {
+    qk3::k_qk3_restrict_cells<double><<<nc, qk3::RS_THREADS, 0, s>>>(coarse.g, fine.g, (const double*)rf,
+                                                                    (const double*)sub, (double*)coarse.ebuf);
+    qk3::k_qk3_gather<double><<<b, 256, 0, s>>>(coarse.g, (const double*)coarse.ebuf, nullptr, (double*)rc, 0, 0);
+  } else {
+    qk3::k_qk3_restrict_cells<float><<<nc, qk3::RS_THREADS, 0, s>>>(coarse.g, fine.g, (const float*)rf,
+                                                                   (const float*)sub, (float*)coarse.ebuf);
+    qk3::k_qk3_gather<float><<<b, 256, 0, s>>>(coarse.g, (const float*)coarse.ebuf, nullptr, (float*)rc, 0, 0);
+  }
+  count_launch(2);
 }
 
 }  // namespace als

@@ -3,6 +3,7 @@ cudaProfilerStart/Stop region, for `ncu --profile-from-start off`.
 
     python -m paper_2107_00820_gb300.profile_run --workload sinker3d_32 --vcycles 1 --prec fp32
     python -m paper_2107_00820_gb300.profile_run --workload batch64 --vcycles 1 --batch-mode merged
+    python -m paper_2107_00820_gb300.profile_run --workload sinker3d_q3_24 --n 12 --levels 3 --setup
 
 Only the region (the V-cycles, optionally one setup) is profiled; problem
 generation and the context's own setup run before it.  batch64: the 64 uneven
@@ -32,12 +33,14 @@ def main():
     ap.add_argument("--vcycles", type=int, default=1)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "both"])
     ap.add_argument("--setup", action="store_true", help="profile one coefficient setup instead")
+    ap.add_argument("--n", type=int, default=None, help="cells per direction (default: the workload's)")
+    ap.add_argument("--levels", type=int, default=None, help="levels (default: the workload's)")
     args = ap.parse_args()
     if args.workload == "batch64":
         batch_region(args)
         return
     spec = bench.WORKLOADS[args.workload]
-    pb = bench.make_problem(spec)
+    pb = bench.make_problem(spec, args.n, args.levels)
     mu = [torch.as_tensor(m, device="cuda") for m in pb.mu]
     tensor = spec.get("kind") == "tensor"
     mue = [torch.as_tensor(m, device="cuda") for m in pb.meta["mu_eff"]] if tensor else None

@@ -179,3 +179,45 @@ def test_q3_3d_fgmres_counts_equal_the_oracle(schur, W, gamma, dr):
     um, pm, im = _ctx(pb, schur=schur, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
     assert im.converged and im.iterations <= its + 2, (im.iterations, its)
     assert _true_residual(s, pb, um, pm) <= 1.5e-8
+
+
+def test_q3_3d_loaded_inverses_give_the_same_fp32_smoother():
+    """Caller-supplied FP64 inverses (packed by diagonals) are rounded into the FP32 wrapped
+    rows by the same rule as the setup's: reloading the context's own inverses leaves the
+    FP32 smoother's output bit for bit unchanged, and loading the oracle's inverses gives the
+    oracle's smoother within FP32 rounding."""
+    pb = _problem(4, 2, 1e2, 1e3)
+    ctx = _ctx(pb)
+    lv = LevelK(3, pb.n, 3, pb.mu[1], pb.gamma)
+    nverts = 5 ** 3
+    np_ = 375
+    stride = (np_ * (np_ + 1) // 2 + 3) // 4 * 4
+    starts = [t * np_ - t * (t - 1) // 2 for t in range(np_)]
+
+    def pack(full):
+        return np.concatenate([np.diag(full, t) for t in range(np_)] + [np.zeros(stride - starts[-1] - 1)])
+
+    r = dev(_free(lv, 13), torch.float32)
+    z0 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z0, A.ALS_PREC_FP32)
+    own = np.concatenate([pack(ctx.patch_inverse(1, v)) for v in range(nverts)])
+    ctx.load_patch_inverses(1, own)
+    z1 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z1, A.ALS_PREC_FP32)
+    assert torch.equal(z0, z1)
+    m = lv.mesh
+    verts = all_vertices_k(m)
+    offs = np.array([[o % 5, (o // 5) % 5, o // 25] for o in range(125)]) - 2
+    packs = []
+    for v in verts:
+        idx = star_dofs_k(m, v)
+        g = 3 * v + offs
+        free = np.all(g > 0, axis=1) & np.all(g < np.array(m.nn) - 1, axis=1)
+        keep = [a * 125 + o for a in range(3) for o in range(125) if free[o]]
+        full = np.eye(np_)
+        full[np.ix_(keep, keep)] = np.linalg.inv(lv.A[idx][:, idx].toarray())
+        packs.append(pack(0.5 * (full + full.T)))
+    ctx.load_patch_inverses(1, np.concatenate(packs))
+    z2 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z2, A.ALS_PREC_FP32)
+    assert rel(host(z2), star_patches_k(lv).apply(host(r).astype(np.float64))) <= 1e-5
