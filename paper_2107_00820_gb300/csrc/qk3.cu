@@ -494,6 +494,23 @@ constexpr int GJ_DOUBLES = BB * BB + 2 * BB * NS + 2 * BB;
 constexpr int SETUP_DOUBLES = ASM_DOUBLES > GJ_DOUBLES ? ASM_DOUBLES : GJ_DOUBLES;
 constexpr size_t SETUP_SMEM = sizeof(double) * SETUP_DOUBLES + 16;
 
+// entry e (0 <= e < N (N + 1) / 2) of the upper triangle of an N x N matrix, N odd, as
+// (i, j), i <= j: the rows are taken in pairs (p, N - 1 - p), p < (N - 1) / 2, of N + 1
+// entries together, then the middle row (consecutive e: consecutive j)
+template <int N>
+__device__ __forceinline__ void tri_entry(int e, int& i, int& j) {
+  static_assert(N % 2 == 1, "odd order");
+  constexpr int HALF = (N - 1) / 2;
+  const int p = e / (N + 1), off = e - p * (N + 1);
+  if (p < HALF) {
+    if (off < N - p) { i = p; j = p + off; }
+    else { i = N - 1 - p; j = i + off - (N - p); }
+  } else {
+    i = HALF;
+    j = HALF + off;
+  }
+}
+
 // One CTA per star at a time (persistent over the stars v = blockIdx.x, += gridDim.x), its
 // star matrix in ws + blockIdx.x * NS * LDM.
 // RM: the arithmetic of the elimination, double or DF64 (double-float, about 48 bits, on
@@ -556,8 +573,9 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
       // node pairs: H[a][b] = sum_q w |J| mu d_a phi_ni d_b phi_nj; the element entry of
       // (ci, ni), (cj, nj) is 2 mu eps(phi_ni e_ci) : eps(phi_nj e_cj) integrated,
       // = delta_(ci cj) trace H + H[cj][ci], plus gamma (B^T W^-1 B)
-      for (int e = tid; e < 27 * 27; e += nt) {
-        const int ni = e / 27, nj = e % 27;
+      for (int e = tid; e < 27 * 28 / 2; e += nt) {   // unordered node pairs ni <= nj
+        int ni, nj;
+        tri_entry<27>(e, ni, nj);
         double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         for (int q = 0; q < NQ; ++q) {
           const double* gi = gq + (q * 27 + ni) * 3;
@@ -575,42 +593,58 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
                         S1 * S1 * (ni / 9 + offz + K * cz - K * vz + 2);
         const int snj = (nj % 3 + offx + K * cx - K * vx + 2) + S1 * ((nj / 3) % 3 + offy + K * cy - K * vy + 2) +
                         S1 * S1 * (nj / 9 + offz + K * cz - K * vz + 2);
+        // the 9 entries of the node block (ni, nj), each into the upper triangle (the
+        // block (nj, ni) holds their transposes; for ni == nj only ci <= cj)
         for (int ci = 0; ci < 3; ++ci)
           for (int cj = 0; cj < 3; ++cj) {
+            if (ni == nj && ci > cj) continue;
             double al = 0.0;
             for (int p = 0; p < NPR; ++p) al += Bm[p * 81 + ci * 27 + ni] * WB[p * 81 + cj * 27 + nj];
-            M[(long long)(ci * SN + sni) * LDM + cj * SN + snj] += (ci == cj ? tr : 0.0) + H[cj][ci] + gamma * al;
+            const int si = ci * SN + sni, sj = cj * SN + snj;
+            const int lo = si < sj ? si : sj, hi = si < sj ? sj : si;
+            M[(long long)lo * LDM + hi] += (ci == cj ? tr : 0.0) + H[cj][ci] + gamma * al;
           }
       }
       __syncthreads();
     }
     // identity rows and columns at absent and Dirichlet nodes; the entries in the
-    // elimination's arithmetic R from here on (each thread converts its own entries)
+    // elimination's arithmetic RM from here on (each thread converts its own entries).
+    // From here only the upper triangle i <= j is kept (see the elimination below).
     RM* Mr = reinterpret_cast<RM*>(M);
-    for (int e = tid; e < NS * NS; e += nt) {
-      const int i = e / NS, j = e % NS;
+    for (int e = tid; e < NS * (NS + 1) / 2; e += nt) {
+      int i, j;
+      tri_entry<NS>(e, i, j);
       long long nd;
       const bool fi = star_node(g, vx, vy, vz, i, nd), fj = star_node(g, vx, vy, vz, j, nd);
-      double* p = M + (long long)i * LDM + j;
-      const double val = (!fi || !fj) ? (i == j ? 1.0 : 0.0) : *p;
+      const double val = (!fi || !fj) ? (i == j ? 1.0 : 0.0) : M[(long long)i * LDM + j];
       Mr[(long long)i * LDM + j] = Ops::from(val);
     }
     __syncthreads();
-    // ---- block Gauss-Jordan inversion in place (SPD: the pivot blocks are Schur
-    // complements, no pivoting).  Per pass over pivots K = [k0, k0 + b): Dk = M_KK^-1,
-    // R = Dk M_K. (row panel), C = M_.K (column panel); then M_KK = Dk, M_Kj = R_j,
-    // M_iK = -C_i Dk, M_ij -= C_i R_j.
+    // ---- block Gauss-Jordan inversion in place on the upper triangle (SPD: the pivot
+    // blocks are Schur complements, no pivoting).  Per pass over pivots K = [k0, k0 + b):
+    // Dk = M_KK^-1, C = M_.K (column panel), R = Dk M_K. (row panel); then M_KK = Dk,
+    // M_Kj = R_j, M_iK = -C_i Dk, M_ij -= C_i R_j.  With s_x = -1 for the indices swept
+    // so far and +1 for the others, every pass keeps M_ji = s_i s_j M_ij, so the upper
+    // triangle determines the rest: X_x = M(min(x, K), max(x, K)) is C_x, and the raw row
+    // panel is sigma_x X_x (sigma_x = -1 for x < k0, +1 beyond K).  With Y_x = Dk X_x the
+    // pass sets M_ij -= sigma_j X_i . Y_j (i <= j outside K), M_iK = -Y_i (i < k0),
+    // M_Kj = Y_j (j beyond K), M_KK = Dk; at the end all signs agree and M is A^-1.
     RM* Dk = reinterpret_cast<RM*>(smem);   // [BB][BB]
-    RM* Rp = Dk + BB * BB;                  // [BB][NS]
-    RM* C = Rp + BB * NS;                   // [NS][BB]
+    RM* Yp = Dk + BB * BB;                  // [BB][NS]
+    RM* C = Yp + BB * NS;                   // [NS][BB]: X
     RM* rowk = C + NS * BB;                 // [BB]
     RM* colk = rowk + BB;                   // [BB]
     const RM zero = Ops::from(0.0), one = Ops::from(1.0);
     for (int k0 = 0; k0 < NS; k0 += BB) {
       const int b = NS - k0 < BB ? NS - k0 : BB;
       for (int e = tid; e < BB * BB; e += nt) {
-        const int m = e / BB, l = e % BB;
-        Dk[e] = (m < b && l < b) ? Mr[(long long)(k0 + m) * LDM + k0 + l] : (m == l ? one : zero);
+        const int m = e / BB, l = e % BB, lo = m < l ? m : l, hi = m < l ? l : m;
+        Dk[e] = (m < b && l < b) ? Mr[(long long)(k0 + lo) * LDM + k0 + hi] : (m == l ? one : zero);
+      }
+      for (int e = tid; e < NS * BB; e += nt) {
+        const int x = e / BB, l = e % BB, k = k0 + l;
+        const bool inK = x >= k0 && x < k0 + b;
+        C[e] = (l < b && !inK) ? (x < k ? Mr[(long long)x * LDM + k] : Mr[(long long)k * LDM + x]) : zero;
       }
       __syncthreads();
       for (int kk = 0; kk < b; ++kk) {   // scalar Gauss-Jordan on the pivot block
@@ -634,74 +668,70 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_qk3_star_setup(Geom g, double
         }
         __syncthreads();
       }
-      for (int e = tid; e < NS * BB; e += nt) {
-        const int i = e / BB, l = e % BB;
-        C[e] = l < b ? Mr[(long long)i * LDM + k0 + l] : zero;
-      }
       for (int e = tid; e < BB * NS; e += nt) {
-        const int m = e / NS, j = e % NS;
+        const int m = e / NS, x = e % NS;
         RM acc = zero;
         if (m < b)
-          for (int l = 0; l < b; ++l) acc = Ops::add_prod(acc, Dk[m * BB + l], Mr[(long long)(k0 + l) * LDM + j]);
-        Rp[e] = acc;
+          for (int l = 0; l < b; ++l) acc = Ops::add_prod(acc, Dk[m * BB + l], C[x * BB + l]);
+        Yp[e] = acc;
       }
       __syncthreads();
       // EPT entries per thread at a time, EPT independent chains: the chain of one entry
       // is a sequence of dependent operations (16 double-float updates of ~15 FP32
-      // instructions each), so the entries of a thread interleave to hide its latency.
-      // Column block (jk): the chain on the column of Dk from 0 gives -C_i Dk; row block
-      // (ik) and pivot block take their value from Rp and Dk instead.
+      // instructions each), so the entries of a thread interleave to hide its latency
       constexpr int EPT = 4;
-      for (int e0 = tid; e0 < NS * NS; e0 += EPT * nt) {
+      constexpr int NT = NS * (NS + 1) / 2;
+      for (int e0 = tid; e0 < NT; e0 += EPT * nt) {
         RM acc[EPT];
-        const RM* col[EPT];
-        int stride[EPT];
-        const RM* ci[EPT];
+        const RM* xi[EPT];
+        int jj[EPT];
+        bool neg[EPT];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
           const int e = e0 + q * nt;
-          const int ee = e < NS * NS ? e : 0;
-          const int i = ee / NS, j = ee % NS;
-          const int mj = j - k0;
-          const bool jk = mj >= 0 && mj < b;
-          ci[q] = C + i * BB;
-          col[q] = jk ? Dk + mj : Rp + j;
-          stride[q] = jk ? BB : NS;
-          acc[q] = jk ? zero : Mr[(long long)i * LDM + j];
+          int i, j;
+          tri_entry<NS>(e < NT ? e : 0, i, j);
+          xi[q] = C + i * BB;
+          jj[q] = j;
+          neg[q] = j < k0;   // sigma_j = -1: the chain runs on -M_ij and is negated back
+          const RM m = Mr[(long long)i * LDM + j];
+          acc[q] = neg[q] ? -m : m;
         }
 #pragma unroll
         for (int l = 0; l < BB; ++l)
 #pragma unroll
-          for (int q = 0; q < EPT; ++q) acc[q] = Ops::sub_prod(acc[q], ci[q][l], col[q][l * stride[q]]);
+          for (int q = 0; q < EPT; ++q) acc[q] = Ops::sub_prod(acc[q], xi[q][l], Yp[l * NS + jj[q]]);
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
           const int e = e0 + q * nt;
-          if (e >= NS * NS) continue;
-          const int i = e / NS, j = e % NS;
+          if (e >= NT) continue;
+          int i, j;
+          tri_entry<NS>(e, i, j);
           const int mi = i - k0, mj = j - k0;
           const bool ik = mi >= 0 && mi < b, jk = mj >= 0 && mj < b;
-          Mr[(long long)i * LDM + j] = (ik && jk) ? Dk[mi * BB + mj] : (ik ? Rp[mi * NS + j] : acc[q]);
+          RM val = neg[q] ? -acc[q] : acc[q];
+          if (ik && jk) val = Dk[mi * BB + mj];
+          else if (jk) val = -Yp[mj * NS + i];
+          else if (ik) val = Yp[mi * NS + j];
+          Mr[(long long)i * LDM + j] = val;
         }
       }
       __syncthreads();
     }
-    // FP64: upper triangle by diagonals (entry (i, i + t)); FP32: the wrapped rows; both
-    // symmetrised
+    // FP64: upper triangle by diagonals (entry (i, i + t)); FP32: the wrapped rows
     for (int t = 0; t < NS; ++t) {
       const long long base = v * pstride + diag_start(NS, t);
-      for (int i = tid; i + t < NS; i += nt)
-        inv64[base + i] = 0.5 * (Ops::to_double(Mr[(long long)i * LDM + i + t]) +
-                                 Ops::to_double(Mr[(long long)(i + t) * LDM + i]));
+      for (int i = tid; i + t < NS; i += nt) inv64[base + i] = Ops::to_double(Mr[(long long)i * LDM + i + t]);
     }
     for (int e = tid; e < WSTRIDE; e += nt) {
       const int t = e / WLD, i = e % WLD, j = i + t < NS ? i + t : i + t - NS;
-      inv32[v * WSTRIDE + e] = i < NS ? (float)(0.5 * (Ops::to_double(Mr[(long long)i * LDM + j]) +
-                                                       Ops::to_double(Mr[(long long)j * LDM + i])))
-                                      : 0.f;
+      const int lo = i < j ? i : j, hi = i < j ? j : i;
+      inv32[v * WSTRIDE + e] = i < NS ? (float)Ops::to_double(Mr[(long long)lo * LDM + hi]) : 0.f;
     }
     __syncthreads();
   }
 }
+
 
 // y_v = A_v^-1 r|_v: one CTA of STAR_THREADS per star (vertex), rows by threads, over the
 // wrapped diagonals (row i takes entry (i, (i + t) mod NS) at step t: entry i of diagonal t
