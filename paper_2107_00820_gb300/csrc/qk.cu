@@ -37,6 +37,34 @@ constexpr int NS = 2 * S1 * S1;   // star dofs (50)
 // pressure monomials at the points PSI[q][p]; the prolongation weights PW[f][a] = l_a(xi_f)
 // at xi_f = f / 3 - 1, f = 0..6 (the fine nodes of a coarse cell per axis)
 __constant__ double cL[N1][N1], cD[N1][N1], cW[N1], cPSI[NQ][NPR], cPW[2 * K + 1][N1];
+// the FP32 cycle's copies (an FP64 operation, a conversion included, costs ~70 FP32 ones
+// on this GPU) and the 2D point weights w_qx w_qy in both precisions
+__constant__ float cLf[N1][N1], cDf[N1][N1], cPSIf[NQ][NPR], cPWf[2 * K + 1][N1], cW2f[NQ];
+__constant__ double cW2[NQ];
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double L(int q, int a) { return cL[q][a]; }
+  static __device__ __forceinline__ double D(int q, int a) { return cD[q][a]; }
+  static __device__ __forceinline__ double psi(int q, int p) { return cPSI[q][p]; }
+  static __device__ __forceinline__ double pw(int f, int a) { return cPW[f][a]; }
+  static __device__ __forceinline__ double w2(int q) { return cW2[q]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float L(int q, int a) { return cLf[q][a]; }
+  static __device__ __forceinline__ float D(int q, int a) { return cDf[q][a]; }
+  static __device__ __forceinline__ float psi(int q, int p) { return cPSIf[q][p]; }
+  static __device__ __forceinline__ float pw(int f, int a) { return cPWf[f][a]; }
+  static __device__ __forceinline__ float w2(int q) { return cW2f[q]; }
+};
+// per-level scalars of the cell kernel in its precision, formed on the host
+template <typename T>
+struct CellScal {
+  T sx, sy, wdet, gamma;
+};
+template <typename T>
+static CellScal<T> cell_scal(const Geom& g, double gamma) {
+  return CellScal<T>{(T)(2.0 / g.h[0]), (T)(2.0 / g.h[1]), (T)(0.25 * g.h[0] * g.h[1]), (T)gamma};
+}
 
 static void host_tables(double L[N1][N1], double D[N1][N1], double W[N1], double PSI[NQ][NPR],
                         double PW[2 * K + 1][N1]) {
@@ -60,13 +88,24 @@ void ensure_tables() {
   cudaMemcpyToSymbol(cW, W, sizeof(W));
   cudaMemcpyToSymbol(cPSI, PSI, sizeof(PSI));
   cudaMemcpyToSymbol(cPW, PW, sizeof(PW));
+  float Lf[N1][N1], Df[N1][N1], PSIf[NQ][NPR], PWf[2 * K + 1][N1], W2f[NQ];
+  double W2[NQ];
+  for (int q = 0; q < N1; ++q)
+    for (int a = 0; a < N1; ++a) { Lf[q][a] = (float)L[q][a]; Df[q][a] = (float)D[q][a]; }
+  for (int q = 0; q < NQ; ++q) {
+    for (int p = 0; p < NPR; ++p) PSIf[q][p] = (float)PSI[q][p];
+    W2[q] = W[q % N1] * W[q / N1];
+    W2f[q] = (float)W2[q];
+  }
+  for (int f = 0; f <= 2 * K; ++f)
+    for (int a = 0; a < N1; ++a) PWf[f][a] = (float)PW[f][a];
+  cudaMemcpyToSymbol(cLf, Lf, sizeof(Lf));
+  cudaMemcpyToSymbol(cDf, Df, sizeof(Df));
+  cudaMemcpyToSymbol(cPSIf, PSIf, sizeof(PSIf));
+  cudaMemcpyToSymbol(cPWf, PWf, sizeof(PWf));
+  cudaMemcpyToSymbol(cW2f, W2f, sizeof(W2f));
+  cudaMemcpyToSymbol(cW2, W2, sizeof(W2));
   done = true;
-}
-
-// derivative of node basis a at point q along axis j, physical (2 / h_j scaling)
-__device__ __forceinline__ double dphi(int q, int a, int j, double sx, double sy) {
-  const int qx = q % N1, qy = q / N1, ax = a % N1, ay = a / N1;
-  return j == 0 ? cD[qx][ax] * cL[qy][ay] * sx : cL[qx][ax] * cD[qy][ay] * sy;
 }
 
 // The tables in shared memory, in precision T: lanes index them by their own point or node,
@@ -77,14 +116,14 @@ struct SharedTables {
   T gx[NQ][NB], gy[NQ][NB], wq[NQ], psi[NQ][NPR];
 };
 template <typename T>
-__device__ __forceinline__ void load_tables(SharedTables<T>& t, double sx, double sy, double wdet) {
+__device__ __forceinline__ void load_tables(SharedTables<T>& t, T sx, T sy, T wdet) {
   for (int e = threadIdx.x; e < NQ * NB; e += blockDim.x) {
-    const int q = e / NB, a = e % NB;
-    t.gx[q][a] = (T)dphi(q, a, 0, sx, sy);
-    t.gy[q][a] = (T)dphi(q, a, 1, sx, sy);
+    const int q = e / NB, a = e % NB, qx = q % N1, qy = q / N1, ax = a % N1, ay = a / N1;
+    t.gx[q][a] = Tab<T>::D(qx, ax) * Tab<T>::L(qy, ay) * sx;
+    t.gy[q][a] = Tab<T>::L(qx, ax) * Tab<T>::D(qy, ay) * sy;
   }
-  for (int e = threadIdx.x; e < NQ * NPR; e += blockDim.x) t.psi[e / NPR][e % NPR] = (T)cPSI[e / NPR][e % NPR];
-  for (int q = threadIdx.x; q < NQ; q += blockDim.x) t.wq[q] = (T)(cW[q % N1] * cW[q / N1] * wdet);
+  for (int e = threadIdx.x; e < NQ * NPR; e += blockDim.x) t.psi[e / NPR][e % NPR] = Tab<T>::psi(e / NPR, e % NPR);
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) t.wq[q] = Tab<T>::w2(q) * wdet;
   __syncthreads();
 }
 __device__ __forceinline__ double phi(int q, int a) { return cL[q % N1][a % N1] * cL[q / N1][a / N1]; }
@@ -93,7 +132,7 @@ __device__ __forceinline__ double phi(int q, int a) { return cL[q % N1][a % N1] 
 // operator apply: one warp per cell, lanes 0..15 = Gauss points, then = nodes
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T* __restrict__ x, const T* __restrict__ mu,
+__global__ void __launch_bounds__(256) k_qk_cells(Geom g, CellScal<T> cs, const T* __restrict__ x, const T* __restrict__ mu,
                                                   const T* __restrict__ winv, const T* __restrict__ p_in,
                                                   T* __restrict__ p_out, T* __restrict__ ebuf) {
   constexpr bool RAW = (MODE & OP_RAW) != 0, VISC = (MODE & OP_VISC) != 0, AL = (MODE & OP_AL) != 0;
@@ -102,7 +141,7 @@ __global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T*
   __shared__ SharedTables<T> tb;
   __shared__ T us[8][2][NB];
   __shared__ T ss[8][NQ][4];
-  load_tables<T>(tb, 2.0 / g.h[0], 2.0 / g.h[1], 0.25 * g.h[0] * g.h[1]);
+  load_tables<T>(tb, cs.sx, cs.sy, cs.wdet);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long cell = (long long)blockIdx.x * 8 + w;
   if (cell >= g.ncells) return;
@@ -148,7 +187,7 @@ __global__ void __launch_bounds__(256) k_qk_cells(Geom g, double gamma, const T*
         for (int r = 0; r < NPR; ++r) sp += Wc[p * NPR + r] * bu[r];
         pi += tb.psi[q][p] * sp;
       }
-      P += (T)gamma * pi;
+      P += cs.gamma * pi;
     }
   }
   if (BT && lane < NQ)
@@ -263,7 +302,7 @@ static void apply_mode(const LevelDev& L, double gamma, const void* x, void* y, 
   constexpr bool NEED_FLUX = (MODE & (OP_VISC | OP_AL | OP_BT)) != 0;
   const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
   const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
-  k_qk_cells<T, MODE><<<(unsigned)((L.g.ncells + 7) / 8), 256, 0, s>>>(L.g, gamma, (const T*)x, mu, winv,
+  k_qk_cells<T, MODE><<<(unsigned)((L.g.ncells + 7) / 8), 256, 0, s>>>(L.g, cell_scal<T>(L.g, gamma), (const T*)x, mu, winv,
                                                                       (const T*)p_in, (T*)p_out, (T*)L.ebuf);
   if (NEED_FLUX) {
     const int keep = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
@@ -377,7 +416,7 @@ __global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, con
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long v = blockIdx.x;
   const int vx = (int)(v % (g.n[0] + 1)), vy = (int)(v / (g.n[0] + 1));
-  load_tables<double>(tb, 2.0 / g.h[0], 2.0 / g.h[1], 0.25 * g.h[0] * g.h[1]);
+  load_tables<double>(tb, 2.0 / g.h[0], 2.0 / g.h[1], 0.25 * g.h[0] * g.h[1]);   // FP64 setup
   if (tid == 0) s_bad = 0;
   for (int e = tid; e < NS * NS; e += nt) M[e / NS][e % NS] = 0.0;
   // B_K (the same on every cell): B[p][(c, a)] = -sum_q w |J| psi_p d_c phi_a
@@ -586,14 +625,14 @@ __global__ void k_qk_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __re
   if (!(i == 0 || i == gf.nn[0] - 1 || j == 0 || j == gf.nn[1] - 1)) {
     int fx, fy;
     const int cx = owner(i, gc.n[0], fx), cy = owner(j, gc.n[1], fy);
-    double acc = 0.0;
+    T acc = T(0);
     for (int b = 0; b < N1; ++b)
       for (int a = 0; a < N1; ++a) {
         const int I = K * cx + a, J = K * cy + b;
         if (I == 0 || I == gc.nn[0] - 1 || J == 0 || J == gc.nn[1] - 1) continue;
-        acc += cPW[fx][a] * cPW[fy][b] * (double)xc[comp * gc.N + I + (long long)gc.nn[0] * J];
+        acc += Tab<T>::pw(fx, a) * Tab<T>::pw(fy, b) * xc[comp * gc.N + I + (long long)gc.nn[0] * J];
       }
-    v = (T)acc;
+    v = acc;
   }
   xf[t] = v;
   if (xadd) xadd[t] += v;
@@ -611,26 +650,26 @@ __global__ void k_qk_restrict(Geom gc, Geom gf, const T* __restrict__ rf, const 
   if (I == 0 || I == gc.nn[0] - 1 || J == 0 || J == gc.nn[1] - 1) { rc[t] = T(0); return; }
   int cxs[2], axs[2], cys[2], ays[2];
   const int mx = cells_of(I, gc.n[0], cxs, axs), my = cells_of(J, gc.n[1], cys, ays);
-  double acc = 0.0;
+  T acc = T(0);
   for (int b = 0; b < my; ++b)
     for (int a = 0; a < mx; ++a)
       for (int fy = 0; fy <= 2 * K; ++fy) {
         const int j = 2 * K * cys[b] + fy;
         if (fy == 2 * K && cys[b] != gc.n[1] - 1) continue;   // owned by the next coarse cell
         if (j == 0 || j == gf.nn[1] - 1) continue;
-        const double wy = cPW[fy][ays[b]];
-        if (wy == 0.0) continue;
+        const T wy = Tab<T>::pw(fy, ays[b]);
+        if (wy == T(0)) continue;
         for (int fx = 0; fx <= 2 * K; ++fx) {
           const int i = 2 * K * cxs[a] + fx;
           if (fx == 2 * K && cxs[a] != gc.n[0] - 1) continue;
           if (i == 0 || i == gf.nn[0] - 1) continue;
-          const double wx = cPW[fx][axs[a]];
-          if (wx == 0.0) continue;
+          const T wx = Tab<T>::pw(fx, axs[a]);
+          if (wx == T(0)) continue;
           const long long fn = comp * gf.N + i + (long long)gf.nn[0] * j;
-          acc += wx * wy * (double)(sub ? rf[fn] - sub[fn] : rf[fn]);
+          acc += wx * wy * (sub ? rf[fn] - sub[fn] : rf[fn]);
         }
       }
-  rc[t] = (T)acc;
+  rc[t] = acc;
 }
 
 }  // namespace qk
@@ -660,7 +699,7 @@ static void apply_epi_t(const LevelDev& L, double gamma, const void* x, void* y,
   // External records become event-record nodes when the stream is being captured
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   qk::k_qk_cells<T, OP_VISC | OP_AL><<<(unsigned)((L.g.ncells + 7) / 8), 256, 0, s>>>(
-      L.g, gamma, (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
+      L.g, qk::cell_scal<T>(L.g, gamma), (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   qk::k_qk_gather_epi<T><<<(unsigned)((2 * L.g.N + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0, s>>>(
       L.g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out, e.start,

@@ -45,6 +45,39 @@ constexpr int NF = 2 * K + 1;      // fine lattice nodes per coarse cell and axi
 constexpr int CPB = 4;             // cells per block of the cell kernel (64 threads each)
 
 __constant__ double cL[N1][N1], cD[N1][N1], cW[N1], cPSI[NQ][NPR], cPW[NF][N1];
+// the FP32 cycle's copies (an FP64 operation costs ~70 FP32 ones here, conversions included)
+// and the 3D point weights w_qx w_qy w_qz in both precisions
+__constant__ float cLf[N1][N1], cDf[N1][N1], cPSIf[NQ][NPR], cPWf[NF][N1], cW3f[NQ];
+__constant__ double cW3[NQ];
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double L(int q, int a) { return cL[q][a]; }
+  static __device__ __forceinline__ double D(int q, int a) { return cD[q][a]; }
+  static __device__ __forceinline__ double psi(int q, int p) { return cPSI[q][p]; }
+  static __device__ __forceinline__ double pw(int f, int a) { return cPW[f][a]; }
+  static __device__ __forceinline__ double w3(int q) { return cW3[q]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float L(int q, int a) { return cLf[q][a]; }
+  static __device__ __forceinline__ float D(int q, int a) { return cDf[q][a]; }
+  static __device__ __forceinline__ float psi(int q, int p) { return cPSIf[q][p]; }
+  static __device__ __forceinline__ float pw(int f, int a) { return cPWf[f][a]; }
+  static __device__ __forceinline__ float w3(int q) { return cW3f[q]; }
+};
+// per-level scalars of the cell kernel in its precision, formed on the host: the reference
+// to physical derivative scales 2 / h_j, |J| = h0 h1 h2 / 8, and gamma
+template <typename T>
+struct CellScal {
+  T s[3], wdet, gamma;
+};
+template <typename T>
+static CellScal<T> cell_scal(const Geom& g, double gamma) {
+  CellScal<T> c;
+  for (int j = 0; j < 3; ++j) c.s[j] = (T)(2.0 / g.h[j]);
+  c.wdet = (T)(0.125 * g.h[0] * g.h[1] * g.h[2]);
+  c.gamma = (T)gamma;
+  return c;
+}
 
 void ensure_tables() {
   static bool done = false;
@@ -62,6 +95,23 @@ void ensure_tables() {
   cudaMemcpyToSymbol(cW, W, sizeof(W));
   cudaMemcpyToSymbol(cPSI, PSI, sizeof(PSI));
   cudaMemcpyToSymbol(cPW, PW, sizeof(PW));
+  float Lf[N1][N1], Df[N1][N1], PSIf[NQ][NPR], PWf[NF][N1], W3f[NQ];
+  double W3[NQ];
+  for (int q = 0; q < N1; ++q)
+    for (int a = 0; a < N1; ++a) { Lf[q][a] = (float)L[q][a]; Df[q][a] = (float)D[q][a]; }
+  for (int q = 0; q < NQ; ++q) {
+    for (int p = 0; p < NPR; ++p) PSIf[q][p] = (float)PSI[q][p];
+    W3[q] = W[q % N1] * W[(q / N1) % N1] * W[q / (N1 * N1)];
+    W3f[q] = (float)W3[q];
+  }
+  for (int f = 0; f < NF; ++f)
+    for (int a = 0; a < N1; ++a) PWf[f][a] = (float)PW[f][a];
+  cudaMemcpyToSymbol(cLf, Lf, sizeof(Lf));
+  cudaMemcpyToSymbol(cDf, Df, sizeof(Df));
+  cudaMemcpyToSymbol(cPSIf, PSIf, sizeof(PSIf));
+  cudaMemcpyToSymbol(cPWf, PWf, sizeof(PWf));
+  cudaMemcpyToSymbol(cW3f, W3f, sizeof(W3f));
+  cudaMemcpyToSymbol(cW3, W3, sizeof(W3));
   done = true;
 }
 
@@ -91,7 +141,7 @@ struct CellShared {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(64 * CPB) k_qk3_cells(Geom g, double gamma, const T* __restrict__ x,
+__global__ void __launch_bounds__(64 * CPB) k_qk3_cells(Geom g, CellScal<T> cs, const T* __restrict__ x,
                                                         const T* __restrict__ mu, const T* __restrict__ winv,
                                                         const T* __restrict__ p_in, T* __restrict__ p_out,
                                                         T* __restrict__ ebuf) {
@@ -100,20 +150,19 @@ __global__ void __launch_bounds__(64 * CPB) k_qk3_cells(Geom g, double gamma, co
   constexpr bool NEED_U = VISC || AL || BO, NEED_FLUX = VISC || AL || BT;
   __shared__ CellShared<T> sh;
   const int tid = threadIdx.x;
-  const double wdet = 0.125 * g.h[0] * g.h[1] * g.h[2];
   if (tid < N1 * N1) {
-    sh.L[tid / N1][tid % N1] = (T)cL[tid / N1][tid % N1];
-    sh.D[tid / N1][tid % N1] = (T)cD[tid / N1][tid % N1];
+    sh.L[tid / N1][tid % N1] = Tab<T>::L(tid / N1, tid % N1);
+    sh.D[tid / N1][tid % N1] = Tab<T>::D(tid / N1, tid % N1);
   }
-  for (int e = tid; e < NQ * NPR; e += blockDim.x) sh.psi[e / NPR][e % NPR] = (T)cPSI[e / NPR][e % NPR];
-  if (tid < NQ) sh.wq[tid] = (T)wq_of(tid, wdet);
+  for (int e = tid; e < NQ * NPR; e += blockDim.x) sh.psi[e / NPR][e % NPR] = Tab<T>::psi(e / NPR, e % NPR);
+  if (tid < NQ) sh.wq[tid] = Tab<T>::w3(tid) * cs.wdet;
   const int w = tid >> 6, t = tid & 63, t0 = t & 3, t1 = (t >> 2) & 3, t2 = t >> 4;
   const long long cell = (long long)blockIdx.x * CPB + w;
   const bool valid = cell < g.ncells;
   const int cx = valid ? (int)(cell % g.n[0]) : 0;
   const int cy = valid ? (int)((cell / g.n[0]) % g.n[1]) : 0;
   const int cz = valid ? (int)(cell / ((long long)g.n[0] * g.n[1])) : 0;
-  const T sx = (T)(2.0 / g.h[0]), sy = (T)(2.0 / g.h[1]), sz = (T)(2.0 / g.h[2]);
+  const T sx = cs.s[0], sy = cs.s[1], sz = cs.s[2];
   T(*b0)[NB] = sh.b0[w];
   T(*b1)[NB] = sh.b1[w];
   {
@@ -204,7 +253,7 @@ __global__ void __launch_bounds__(64 * CPB) k_qk3_cells(Geom g, double gamma, co
       T pi = T(0);
       if (valid)
         for (int p = 0; p < NPR; ++p) pi += sh.psi[q][p] * sh.sp[w][p];
-      P += (T)gamma * pi;
+      P += cs.gamma * pi;
     }
   }
   if (BT && valid)
@@ -354,7 +403,7 @@ static void apply_mode(const LevelDev& L, double gamma, const void* x, void* y, 
   const T* mu = std::is_same<T, double>::value ? (const T*)L.coef64 : (const T*)L.coef32;
   const T* winv = std::is_same<T, double>::value ? (const T*)L.winv64 : (const T*)L.winv32;
   k_qk3_cells<T, MODE><<<(unsigned)((L.g.ncells + CPB - 1) / CPB), 64 * CPB, 0, s>>>(
-      L.g, gamma, (const T*)x, mu, winv, (const T*)p_in, (T*)p_out, (T*)L.ebuf);
+      L.g, cell_scal<T>(L.g, gamma), (const T*)x, mu, winv, (const T*)p_in, (T*)p_out, (T*)L.ebuf);
   if (NEED_FLUX) {
     const int keep = ((MODE & OP_VISC) && !(MODE & OP_RAW)) ? 1 : 0;
     k_qk3_gather<T><<<(unsigned)((3 * L.g.N + 255) / 256), 256, 0, s>>>(L.g, (const T*)L.ebuf, (const T*)x, (T*)y,
@@ -386,7 +435,7 @@ static void apply_epi_t(const LevelDev& L, double gamma, const void* x, void* y,
   // External records become event-record nodes when the stream is being captured
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   k_qk3_cells<T, OP_VISC | OP_AL><<<(unsigned)((L.g.ncells + CPB - 1) / CPB), 64 * CPB, 0, s>>>(
-      L.g, gamma, (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
+      L.g, cell_scal<T>(L.g, gamma), (const T*)x, mu, winv, nullptr, nullptr, (T*)L.ebuf);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   k_qk3_gather_epi<T><<<(unsigned)((3 * L.g.N + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0, s>>>(
       L.g, (const T*)L.ebuf, (const T*)x, (T*)y, (const T*)e.b, e.sigma, e.k, (const T*)e.V, e.ld, (T*)e.out, e.start,
@@ -966,40 +1015,63 @@ __global__ void k_qk3_star_gather(Geom g, const T* __restrict__ sc, T* __restric
 // ---------------------------------------------------------------------------
 // transfers: P_H (the coarse Q3 basis at the fine nodes, tensor product of 1D weights;
 // each fine node belongs to the coarse cell min(f div 6, nc - 1) per axis) and its
-// transpose, as gathers; fine Dirichlet rows and coarse Dirichlet columns are zero
+// transpose, by per-coarse-cell contractions; fine Dirichlet rows and coarse Dirichlet
+// columns are zero
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int owner(int f, int nc, int& fr) {
-  int c = f / (2 * K);
-  if (c > nc - 1) c = nc - 1;
-  fr = f - 2 * K * c;
-  return c;
-}
 
+// xf = P_H xc (and xadd += xf): per coarse cell (one CTA) its 64 coarse values (zero at
+// Dirichlet coarse nodes) contracted with the 1D weights along x, y, z into the 7^3 fine
+// values, each written by the cell that owns the fine node (the owner rule of the
+// restriction below; Dirichlet fine nodes get zero)
 template <typename T>
-__global__ void k_qk3_prolong(Geom gc, Geom gf, const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xadd) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * gf.N) return;
-  const int comp = (int)(t / gf.N);
-  const long long nd = t - comp * gf.N;
-  const int i = (int)(nd % gf.nn[0]);
-  const long long rr = nd / gf.nn[0];
-  const int j = (int)(rr % gf.nn[1]), k = (int)(rr / gf.nn[1]);
-  T v = T(0);
-  if (!bnd_node(gf, i, j, k)) {
-    int fx, fy, fz;
-    const int cx = owner(i, gc.n[0], fx), cy = owner(j, gc.n[1], fy), cz = owner(k, gc.n[2], fz);
-    double acc = 0.0;
-    for (int c = 0; c < N1; ++c)
-      for (int b = 0; b < N1; ++b)
-        for (int a = 0; a < N1; ++a) {
-          const int I = K * cx + a, J = K * cy + b, Kz = K * cz + c;
-          if (bnd_node(gc, I, J, Kz)) continue;
-          acc += cPW[fx][a] * cPW[fy][b] * cPW[fz][c] * (double)xc[comp * gc.N + node_id(gc, I, J, Kz)];
-        }
-    v = (T)acc;
+__global__ void __launch_bounds__(128) k_qk3_prolong_cells(Geom gc, Geom gf, const T* __restrict__ xc,
+                                                           T* __restrict__ xf, T* __restrict__ xadd) {
+  __shared__ T u[3][NB];
+  __shared__ T t1[3][NF * N1 * N1];
+  __shared__ T t2[3][NF * NF * N1];
+  __shared__ T pw[NF][N1];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long cell = blockIdx.x;
+  const int cx = (int)(cell % gc.n[0]), cy = (int)((cell / gc.n[0]) % gc.n[1]),
+            cz = (int)(cell / ((long long)gc.n[0] * gc.n[1]));
+  if (tid < NF * N1) pw[tid / N1][tid % N1] = Tab<T>::pw(tid / N1, tid % N1);
+  for (int e = tid; e < 3 * NB; e += nt) {
+    const int c = e / NB, a = e % NB;
+    const int I = K * cx + a % N1, J = K * cy + (a / N1) % N1, Kz = K * cz + a / (N1 * N1);
+    u[c][a] = bnd_node(gc, I, J, Kz) ? T(0) : xc[c * gc.N + node_id(gc, I, J, Kz)];
   }
-  xf[t] = v;
-  if (xadd) xadd[t] += v;
+  __syncthreads();
+  for (int e = tid; e < 3 * NF * N1 * N1; e += nt) {   // x: (ax, ay, az) -> (fx, ay, az)
+    const int c = e / (NF * N1 * N1), r = e % (NF * N1 * N1), fx = r % NF, yz = r / NF;
+    T acc = T(0);
+#pragma unroll
+    for (int ax = 0; ax < N1; ++ax) acc += pw[fx][ax] * u[c][ax + N1 * yz];
+    t1[c][r] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * NF * NF * N1; e += nt) {   // y: (fx, ay, az) -> (fx, fy, az)
+    const int c = e / (NF * NF * N1), r = e % (NF * NF * N1), fx = r % NF, fy = (r / NF) % NF, az = r / (NF * NF);
+    T acc = T(0);
+#pragma unroll
+    for (int ay = 0; ay < N1; ++ay) acc += pw[fy][ay] * t1[c][fx + NF * (ay + N1 * az)];
+    t2[c][r] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * NF * NF * NF; e += nt) {   // z: (fx, fy, az) -> (fx, fy, fz), owned nodes
+    const int c = e / (NF * NF * NF), r = e % (NF * NF * NF), fxy = r % (NF * NF), fx = r % NF, fy = fxy / NF,
+              fz = r / (NF * NF);
+    if ((fx == NF - 1 && cx != gc.n[0] - 1) || (fy == NF - 1 && cy != gc.n[1] - 1) ||
+        (fz == NF - 1 && cz != gc.n[2] - 1))
+      continue;
+    T acc = T(0);
+#pragma unroll
+    for (int az = 0; az < N1; ++az) acc += pw[fz][az] * t2[c][fxy + NF * NF * az];
+    const int i = 2 * K * cx + fx, j = 2 * K * cy + fy, k = 2 * K * cz + fz;
+    const T v = bnd_node(gf, i, j, k) ? T(0) : acc;
+    const long long fn = c * gf.N + node_id(gf, i, j, k);
+    xf[fn] = v;
+    if (xadd) xadd[fn] += v;
+  }
 }
 
 // rc = P_H^T (rf - sub) in two steps.  Per coarse cell (one CTA): the 7^3 fine values it
@@ -1021,7 +1093,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_qk3_restrict_cells(Geom gc, Geom
   const long long cell = blockIdx.x;
   const int cx = (int)(cell % gc.n[0]), cy = (int)((cell / gc.n[0]) % gc.n[1]),
             cz = (int)(cell / ((long long)gc.n[0] * gc.n[1]));
-  if (tid < NF * N1) pw[tid / N1][tid % N1] = (T)cPW[tid / N1][tid % N1];
+  if (tid < NF * N1) pw[tid / N1][tid % N1] = Tab<T>::pw(tid / N1, tid % N1);
   for (int e = tid; e < NF * NF * NF; e += RS_THREADS) {
     const int fx = e % NF, fy = (e / NF) % NF, fz = e / (NF * NF);
     const bool own = (fx < NF - 1 || cx == gc.n[0] - 1) && (fy < NF - 1 || cy == gc.n[1] - 1) &&
@@ -1160,10 +1232,13 @@ void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* ou
 
 void qk3_prolong(const LevelDev& coarse, const LevelDev& fine, int prec, const void* xc, void* xf, cudaStream_t s,
                  void* xadd) {
-  const unsigned b = (unsigned)((3 * fine.g.N + 255) / 256);
+  const unsigned nc = (unsigned)coarse.g.ncells;
   if (prec == PREC_F64)
-    qk3::k_qk3_prolong<double><<<b, 256, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf, (double*)xadd);
-  else qk3::k_qk3_prolong<float><<<b, 256, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf, (float*)xadd);
+    qk3::k_qk3_prolong_cells<double><<<nc, 128, 0, s>>>(coarse.g, fine.g, (const double*)xc, (double*)xf,
+                                                        (double*)xadd);
+  else
+    qk3::k_qk3_prolong_cells<float><<<nc, 128, 0, s>>>(coarse.g, fine.g, (const float*)xc, (float*)xf,
+                                                       (float*)xadd);
   count_launch(1);
 }
 
