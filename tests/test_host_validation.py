@@ -66,6 +66,16 @@ def test_create_rejects_invalid_arguments(lib, args, kw, words):
     assert words in lib.als_last_error(None).decode()
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_order_three_refuses_tensor_coefficients(lib, d):
+    """Order 3 is built for scalar viscosity in 2D and 3D: tensor coefficients are refused
+    before any device work (the arrays are never read)."""
+    mu = [np.zeros(1)] * 2
+    with pytest.raises(A.ALSError) as e:
+        A.Context(d, 4, 2, mu, 1.0, mu_eff=mu, order=3)
+    assert e.value.status == A.ALS_EINVAL and "scalar viscosity" in str(e.value), str(e.value)
+
+
 @pytest.mark.parametrize("gamma", [-1.0, float("nan"), float("inf")])
 def test_create_rejects_invalid_gamma(lib, gamma):
     with pytest.raises(A.ALSError) as e:
