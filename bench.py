@@ -547,6 +547,34 @@ def ours(args, dist):
     # FGMRES count (at the workload's DR 1e8 it does not converge, with either pairing):
     # solve time and iterations, FP32 V-cycles/s and the finest-level interior-star
     # kernel's live time, FP32 against bfloat16 storage
+    # order 3: the same mixed step with the F-cycle, the cycle of the paper's 3D runs (Table
+    # linear): iterations, solve time, FP32 F-cycles/s
+    fcycle = None
+    if not args.quick and order == 3:
+        ctxc = Context(pb.d, pb.n, pb.levels, mu_d, pb.gamma, stream=stream, mode=A.ALS_MODE_MIXED,
+                       rtol=RTOL, maxit=200, sweeps=spec["sweeps"], schur=schur, order=order, cycle=A.ALS_CYCLE_F)
+        uc, pc = torch.zeros_like(u_d), torch.zeros_like(p_d)
+        ctxc.solve(f_d, ubc_d, None, uc, pc)
+        torch.cuda.synchronize()
+        e0.record()
+        info_c = ctxc.solve(f_d, ubc_d, None, uc, pc)[2]
+        e1.record()
+        torch.cuda.synchronize()
+        t_fc = e0.elapsed_time(e1) / 1e3
+        for _ in range(3):
+            ctxc.vcycle(b32, x32, A.ALS_PREC_FP32)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            ctxc.vcycle(b32, x32, A.ALS_PREC_FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        fcycle = {"iterations": info_c.iterations, "converged": bool(info_c.converged), "solve_ms": t_fc * 1e3,
+                  "fcycles_per_s": 10 / (e0.elapsed_time(e1) / 1e3),
+                  "rel_diff_vs_vcycle": {"u": float(torch.linalg.norm(uc - u_d) / torch.linalg.norm(u_d)),
+                                         "p": float(torch.linalg.norm(pc - p_d) / torch.linalg.norm(p_d))}}
+        ctxc.close()
+
     bf16_storage = None
     if not tensor and not args.quick and order == 2:
         specm = dict(spec, dr=1e4)
@@ -686,6 +714,7 @@ def ours(args, dist):
         "mixed_vs_fp64_speedup": t64 / t_step,
         "mixed_vs_fp64_rel_err": {"u": err_u, "p": err_p},
         "setup_fp64": setup_fp64,
+        "fcycle": fcycle,
         "gamma_1e4": gamma_large,
         "bf16_storage": bf16_storage,
         "e2e": {"value": dist.world * dofs / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": h2d,

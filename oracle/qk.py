@@ -354,16 +354,26 @@ def two_level_error(fine: LevelK, coarse: LevelK, smoother="star", transfer="rob
 
 
 class HierarchyK:
-    """Levels 0 (coarsest) .. L-1 of order k with the gamma-robust cycle of Sec. 4: s GMRES
-    steps right-preconditioned by the star PSC operator (smoother "gmres"; "jacobi" is the
-    point-Jacobi negative control), robust (or standard) prolongation, its transpose as
-    restriction, exact coarse solve; the interface the oracle's Stokes solver uses
+    """Levels 0 (coarsest) .. L-1 of order k with the gamma-robust cycle of Sec. 4: s steps of
+    GMRES right-preconditioned by the star PSC operator (smoother "gmres"), or of damped
+    Richardson on it ("richardson", damping tau, default 2^-d), or point Jacobi ("jacobi",
+    the negative control); robust (or standard) prolongation, its transpose as restriction,
+    exact coarse solve; cycle "V" or "F" (the paper's 3D runs use an F-cycle, Table linear;
+    the F-cycle is the recursion of oracle/mg.py: the coarse correction is an F-cycle from
+    zero, then a V-cycle from its result).  The interface the oracle's Stokes solver uses
     (levels, cycle)."""
 
-    def __init__(self, d, n, k, mus, gamma, steps=5, smoother="gmres", transfer="robust", W="Mp"):
+    def __init__(self, d, n, k, mus, gamma, steps=5, smoother="gmres", transfer="robust", W="Mp", cycle="V",
+                 tau=None):
         import scipy.linalg as sla
+        if cycle not in ("V", "F"):
+            raise ValueError(cycle)
+        if smoother not in ("gmres", "richardson", "jacobi"):
+            raise ValueError(smoother)
         L = len(mus)
         self.d, self.k, self.L, self.steps, self.smoother = d, k, L, steps, smoother
+        self.cycle_type = cycle
+        self.tau = tau if tau is not None else (2.0 ** -d if smoother == "richardson" else 1.0)
         self.levels = []
         for lvl in range(L):
             f = 2 ** (L - 1 - lvl)
@@ -392,16 +402,35 @@ class HierarchyK:
         x[self.coarse_free] = sla.cho_solve(self._chol, b[self.coarse_free])
         return x
 
-    def vcycle(self, b, lvl=None):
-        from .mg import smooth_gmres
+    def smooth(self, lvl, x, b):
+        from .mg import smooth_gmres, smooth_richardson
+        A = self.levels[lvl].A
+        if self.smoother == "richardson":
+            return smooth_richardson(A, self.Dinv(lvl), x, b, self.steps, self.tau)
+        return smooth_gmres(A, self.Dinv(lvl), x, b, self.steps)
+
+    def vcycle(self, b, lvl=None, x0=None):
         lvl = self.L - 1 if lvl is None else lvl
         if lvl == 0:
             return self.coarse_solve(b)
         A = self.levels[lvl].A
-        x = smooth_gmres(A, self.Dinv(lvl), np.zeros_like(b), b, self.steps)
+        x = self.smooth(lvl, np.zeros_like(b) if x0 is None else x0.copy(), b)
         ec = self.vcycle(self.P[lvl].T @ (b - A @ x), lvl - 1)
         x = x + self.P[lvl] @ ec
-        return smooth_gmres(A, self.Dinv(lvl), x, b, self.steps)
+        return self.smooth(lvl, x, b)
+
+    def fcycle(self, b, lvl=None):
+        lvl = self.L - 1 if lvl is None else lvl
+        if lvl == 0:
+            return self.coarse_solve(b)
+        A = self.levels[lvl].A
+        x = self.smooth(lvl, np.zeros_like(b), b)
+        bc = self.P[lvl].T @ (b - A @ x)
+        ec = self.fcycle(bc, lvl - 1)
+        if lvl - 1 > 0:
+            ec = self.vcycle(bc, lvl - 1, x0=ec)
+        x = x + self.P[lvl] @ ec
+        return self.smooth(lvl, x, b)
 
     def cycle(self, b):
-        return self.vcycle(b)
+        return self.fcycle(b) if self.cycle_type == "F" else self.vcycle(b)

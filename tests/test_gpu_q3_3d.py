@@ -166,6 +166,23 @@ def test_q3_3d_vcycle_fp64(n, levels):
     assert rel(host(x), H.vcycle(b)) <= 1e-12
 
 
+@pytest.mark.parametrize("smoother,cycle", [(A.ALS_SMOOTH_GMRES, A.ALS_CYCLE_F),
+                                           (A.ALS_SMOOTH_RICHARDSON, A.ALS_CYCLE_V),
+                                           (A.ALS_SMOOTH_RICHARDSON, A.ALS_CYCLE_F)])
+def test_q3_3d_cycle_variants_fp64(smoother, cycle):
+    """The F-cycle (the paper's cycle for Table linear) and Richardson smoothing (damping
+    2^-d) at order 3, against the order-k oracle's cycles."""
+    pb = _problem(8, 3, 1.0, 1e2)
+    ctx = _ctx(pb, sweeps=2, smoother=smoother, cycle=cycle)
+    H = HierarchyK(3, pb.n, 3, pb.mu, pb.gamma, steps=2,
+                   smoother="gmres" if smoother == A.ALS_SMOOTH_GMRES else "richardson",
+                   cycle="F" if cycle == A.ALS_CYCLE_F else "V")
+    b = _free(H.levels[-1], 12)
+    x = torch.zeros_like(dev(b))
+    ctx.vcycle(dev(b), x)
+    assert rel(host(x), H.cycle(b)) <= 1e-12
+
+
 @pytest.mark.parametrize("schur,W,gamma,dr", [(A.ALS_SCHUR_P1, "Mp", 1e2, 1e4), (A.ALS_SCHUR_P2, "Mp_mu", 1e3, 1e6)])
 def test_q3_3d_fgmres_counts_equal_the_oracle(schur, W, gamma, dr):
     pb = _problem(8, 3, gamma, dr)

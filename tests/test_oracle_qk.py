@@ -32,6 +32,28 @@ def test_k2_equals_the_q2_oracle(d, n, W):
         assert abs(x - y).max() <= 1e-12 * abs(y).max()
 
 
+@pytest.mark.parametrize("d,n,smoother,cycle", [(2, 8, "gmres", "F"), (2, 8, "richardson", "V"),
+                                                (2, 8, "richardson", "F"), (3, 4, "richardson", "F")])
+def test_k2_cycles_equal_the_q2_oracle(d, n, smoother, cycle):
+    """At k = 2 the order-k hierarchy's cycles (V and F, GMRES and Richardson smoothing) are
+    the k = 2 oracle's (itself pinned by its error-propagation formula), and the F-cycle and
+    the V-cycle really differ."""
+    from oracle.mg import Hierarchy
+    from oracle.qk import HierarchyK
+    rng = np.random.default_rng(2)
+    L = 3 if d == 2 else 2
+    sizes = [n // 2 ** (L - 1 - l) for l in range(L)]
+    mus = [np.exp(rng.standard_normal((m ** d, 3 ** d))) for m in sizes]
+    a = HierarchyK(d, n, 2, mus, 5.0, steps=2, smoother=smoother, cycle=cycle)
+    b = Hierarchy(d, n, mus, 5.0, steps=2, smoother=smoother, cycle=cycle)
+    r = rng.standard_normal(a.levels[-1].mesh.nu)
+    r[~a.levels[-1].free] = 0.0
+    x, y = a.cycle(r), b.cycle(r)
+    assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y)
+    if cycle == "F" and L > 2:
+        assert np.linalg.norm(a.vcycle(r) - x) > 1e-6 * np.linalg.norm(x)
+
+
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_gauss_exact_and_lagrange_nodal(k):
     g, w = np.polynomial.legendre.leggauss(k + 1)
