@@ -9,7 +9,9 @@
  * unit box (0,1)^d with n[k] cells per direction, homogeneous structure on
  * every multigrid level (level 0 = coarsest, level L-1 = finest, n_l = n / 2^(L-1-l)).
  *
- * Data layout (all arrays dense, C order, no padding):
+ * Data layout (all arrays dense, C order, no padding; for options.order = 3 the
+ * counts change as its documentation states: N = prod(3 n_k + 1), 4^d points and
+ * C(d + 2, d) pressure coefficients per cell):
  *   velocity vector : d blocks of N nodal values, N = prod(2 n_k + 1), node
  *                     index x-fastest; Dirichlet (boundary) entries are kept
  *                     and carry identity rows.
@@ -177,9 +179,10 @@ void als_default_options(als_options* opt);
  * levels' points): the FP32 cycle does not converge there; the P2 pairing has no such
  * limit.
  * stream: a cudaStream_t (NULL = legacy default stream).
- * Size limits (ALS_EINVAL): d (2n+1)^d velocity values, d 3^d n^d per-cell
- * outputs and d 3^d (n+1)^d vertex-star patch outputs (products over the axes)
- * must each stay below 2^31 (the kernels index them with 32 bits). */
+ * Size limits (ALS_EINVAL): d (k n+1)^d velocity values, d (k+1)^d n^d per-cell
+ * outputs and d (2k-1)^d (n+1)^d vertex-star patch outputs (k = options.order;
+ * products over the axes) must each stay below 2^31 (the kernels index them with
+ * 32 bits). */
 als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
                       void* stream, als_ctx** out);
 

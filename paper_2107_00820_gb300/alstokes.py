@@ -184,6 +184,12 @@ def default_options(**kw):
     return o
 
 
+def pressure_per_cell(dim, order):
+    """Pressure unknowns per cell, dim P_(order-1)^disc = C(order - 1 + dim, dim)."""
+    import math
+    return math.comb(order - 1 + dim, dim)
+
+
 class Context:
     """An als_ctx: setup once (als_create), then apply / V-cycle / solve."""
 
@@ -225,8 +231,7 @@ class Context:
         return self.dim * int(np.prod([self.order * v + 1 for v in nl]))
 
     def npres(self):
-        per_cell = (6 if self.dim == 2 else 10) if self.order == 3 else self.dim + 1
-        return per_cell * int(np.prod(self.n))
+        return pressure_per_cell(self.dim, self.order) * int(np.prod(self.n))
 
     # calls -----------------------------------------------------------------
     def _call(self, name, *args):
@@ -419,8 +424,9 @@ class Batch:
             self._keep += [keep, qp, mu]
             gammas[i] = float(ins["gamma"])
             opts[i] = default_options(**ins.get("options", {}))
-            nu = dim * int(np.prod([2 * v + 1 for v in n]))
-            self.shapes.append((nu, (dim + 1) * int(np.prod(n))))
+            order = int(opts[i].order)
+            nu = dim * int(np.prod([order * v + 1 for v in n]))
+            self.shapes.append((nu, pressure_per_cell(dim, order) * int(np.prod(n))))
             self._meta.append((dim, n, levels))
         out = c_void_p()
         st = lib.als_batch_create(k, meshes, coeffs, gammas, opts, c_void_p(stream) if stream else None, byref(out))

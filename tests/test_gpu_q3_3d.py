@@ -238,3 +238,29 @@ def test_q3_3d_loaded_inverses_give_the_same_fp32_smoother():
     z2 = torch.zeros_like(r)
     ctx.star_smooth(1, r, z2, A.ALS_PREC_FP32)
     assert rel(host(z2), star_patches_k(lv).apply(host(r).astype(np.float64))) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [A.ALS_MODE_FP64, A.ALS_MODE_MIXED])
+def test_q3_batch_of_orders_and_dimensions(mode):
+    """A batch mixing order-3 instances in 2D and 3D with an order-2 one: the merged form
+    refuses order 3 (its kernels are order 2), the batch runs the instances' own cycle
+    graphs side by side, and every instance is bitwise its single-instance solve."""
+    from paper_2107_00820_gb300 import Batch
+    opts = {"mode": mode, "schur": A.ALS_SCHUR_P2, "rtol": 1e-8, "order": 3}
+    pbs = [_problem(4, 2, 1e2, 1e4, seed=41), _problem(8, 3, 1e3, 1e4, seed=42),
+           P.sinker_problem_k(16, 3, 3, 4, 0.1, 200.0, 1e4, 10.0, 1e2, 43, d=2)]
+    ins = [{"dim": pb.d, "n": pb.n, "levels": pb.levels, "coeffs": pb.mu, "gamma": pb.gamma, "options": opts}
+           for pb in pbs]
+    pb2 = P.sinker_problem(2, 16, 3, 4, 0.1, 200.0, 1e4, 10.0, 1e2, 44)
+    opts2 = dict(opts, order=2)
+    ins.append({"dim": 2, "n": pb2.n, "levels": pb2.levels, "coeffs": pb2.mu, "gamma": pb2.gamma, "options": opts2})
+    batch = Batch(ins)
+    assert batch.mode == A.ALS_BATCH_BRANCHES
+    ub, pb_, infos = batch.solve([pb.f for pb in pbs] + [pb2.f], [pb.u_bc for pb in pbs] + [pb2.u_bc])
+    for i, (pb, o) in enumerate(zip(pbs + [pb2], [opts] * 3 + [opts2])):
+        ctx = Context(pb.d, pb.n, pb.levels, pb.mu, pb.gamma, **o)
+        u, p, info = ctx.solve(pb.f, pb.u_bc)
+        assert infos[i].converged == 1 and infos[i].iterations == info.iterations
+        assert np.array_equal(ub[i], u) and np.array_equal(pb_[i], p)
+        ctx.close()
+    batch.close()
