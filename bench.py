@@ -576,7 +576,7 @@ def ours(args, dist):
         ctxc.close()
 
     bf16_storage = None
-    if not tensor and not args.quick and order == 2:
+    if not tensor and not args.quick and (order == 2 or pb.d == 3):   # not built for order 3 in 2D
         specm = dict(spec, dr=1e4)
         pbm = make_problem(specm)
         mum = [dev(m) for m in pbm.mu]
@@ -584,7 +584,7 @@ def ours(args, dist):
         res = {}
         for name, store in (("fp32", A.ALS_STORE_FP32), ("bf16", A.ALS_STORE_BF16)):
             cm = Context(pbm.d, pbm.n, pbm.levels, mum, pbm.gamma, stream=stream, mode=A.ALS_MODE_MIXED, rtol=RTOL,
-                         maxit=300, sweeps=spec["sweeps"], schur=A.ALS_SCHUR_P2, store=store)
+                         maxit=300, sweeps=spec["sweeps"], schur=A.ALS_SCHUR_P2, store=store, order=order)
             um, pm = torch.zeros_like(u_d), torch.zeros_like(p_d)
             cm.solve(fm, ubm, None, um, pm, check=False)
             torch.cuda.synchronize()

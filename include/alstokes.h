@@ -148,7 +148,9 @@ typedef struct {
                      at DR 1e4 (2D and 3D) and, in 2D, up to DR 1e8 at gamma 1e3 (+3), but
                      the 3D 32^3 solve at DR 1e8, gamma 1e4 did not converge; with P1 it
                      costs a few iterations at DR 1e4 and does not converge from DR 1e6.
-                     Order 2 only. */
+                     Order 2, and order 3 in 3D (its wrapped FP32 rows rounded the same way;
+                     the interior solves of the FP32 transfers read them too); refused for
+                     order 3 in 2D (ALS_EINVAL). */
 } als_options;
 
 typedef struct {

@@ -884,8 +884,8 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     return fail(c, ALS_EINVAL, "unknown setup arithmetic");
   if (c->opt.store != ALS_STORE_FP32 && c->opt.store != ALS_STORE_BF16)
     return fail(c, ALS_EINVAL, "unknown star storage");
-  if (c->opt.store == ALS_STORE_BF16 && c->opt.order != 2)
-    return fail(c, ALS_EINVAL, "bfloat16 star storage is built for order 2");
+  if (c->opt.store == ALS_STORE_BF16 && c->opt.order != 2 && !(c->opt.order == 3 && c->dim == 3))
+    return fail(c, ALS_EINVAL, "bfloat16 star storage is built for order 2 and for order 3 in 3D");
   if (c->opt.order != 2 && c->opt.order != 3) return fail(c, ALS_EINVAL, "order must be 2 or 3");
   if (c->opt.order == 3 && coeff->kind != ALS_COEFF_SCALAR)
     return fail(c, ALS_EINVAL, "order 3 is built for scalar viscosity");
@@ -961,9 +961,10 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
     if (l > 0) {
       ALS_TRY(dalloc(c, &Lv.inv64, (size_t)Lv.g.nverts * Lv.pstride));
       ALS_TRY(alloc_star_storage(c, Lv));
-      if (c->opt.store == ALS_STORE_BF16) {   // the block-packed stars again, in bfloat16
+      if (c->opt.store == ALS_STORE_BF16) {   // the FP32 stars again, in bfloat16
         uint16_t* p16 = nullptr;
-        ALS_TRY(dalloc(c, &p16, (size_t)(Lv.split ? Lv.nint : Lv.g.nverts) * block_stride_bf16(Lv.np)));
+        const size_t per = c->k == 3 ? qk3_star32_floats() : (size_t)block_stride_bf16(Lv.np);
+        ALS_TRY(dalloc(c, &p16, (size_t)(Lv.split ? Lv.nint : Lv.g.nverts) * per));
         Lv.inv16 = p16;
       }
     }

@@ -20,6 +20,7 @@
 // by block Gauss-Jordan elimination (16 pivots per pass, the pivot block and the panels in
 // shared memory).  Deterministic: per-cell and per-star outputs are staged and summed per
 // node in a fixed order.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <type_traits>
@@ -877,7 +878,43 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply(Geom g, const T
 // loads in flight while the current pair is used); r is held twice over so that
 // r_((i + t) mod NS) needs no wrap.  interior / mode as k_qk3_star_apply.
 constexpr int WV = WLD / 4;   // float4 per row (94)
-__global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const float* __restrict__ inv,
+// The rows' storage: FP32, or bfloat16 (ALS_STORE_BF16: the same rows rounded to nearest
+// from FP64, 752-byte rows), widened to FP32 on the way into shared memory; every product
+// and sum in FP32 either way.  A pair of rows is 188 16-byte words in FP32 (thread tid
+// loads words tid and tid + 128) and 94 in bfloat16 (8 entries a word, threads 0..93).
+template <typename TS>
+struct RowPair;
+template <>
+struct RowPair<float> {
+  float4 a, b;
+  __device__ __forceinline__ void load(const float* base, int tid) {
+    const float4* W = reinterpret_cast<const float4*>(base);
+    a = __ldg(W + tid);
+    b = tid + STAR_THREADS < 2 * WV ? __ldg(W + tid + STAR_THREADS) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ __forceinline__ void store(float* w, int tid) const {
+    reinterpret_cast<float4*>(w)[tid] = a;
+    if (tid + STAR_THREADS < 2 * WV) reinterpret_cast<float4*>(w)[tid + STAR_THREADS] = b;
+  }
+};
+template <>
+struct RowPair<__nv_bfloat16> {
+  uint4 a;
+  __device__ __forceinline__ void load(const __nv_bfloat16* base, int tid) {
+    a = tid < WV ? __ldg(reinterpret_cast<const uint4*>(base) + tid) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  __device__ __forceinline__ void store(float* w, int tid) const {
+    if (tid >= WV) return;
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&a);
+    const float2 p0 = __bfloat1622float2(h[0]), p1 = __bfloat1622float2(h[1]);
+    const float2 p2 = __bfloat1622float2(h[2]), p3 = __bfloat1622float2(h[3]);
+    reinterpret_cast<float4*>(w)[2 * tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
+    reinterpret_cast<float4*>(w)[2 * tid + 1] = make_float4(p2.x, p2.y, p3.x, p3.y);
+  }
+};
+
+template <typename TS>
+__global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const TS* __restrict__ inv,
                                                                    int interior, int mode,
                                                                    const float* __restrict__ r,
                                                                    float* __restrict__ out) {
@@ -899,12 +936,9 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const
     vz = (int)(item / ((long long)g.nv[0] * g.nv[1]));
   }
   const long long v = (long long)vx + (long long)g.nv[0] * ((long long)vy + (long long)g.nv[1] * vz);
-  const float4* W = reinterpret_cast<const float4*>(inv + v * WSTRIDE);
-  // a pair of rows is 2 * WV = 188 float4: thread tid takes float4 tid and tid + 128
-  constexpr int PAIR = 2 * WV;
-  float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
-  f0 = __ldg(W + tid);
-  if (tid + STAR_THREADS < PAIR) f1 = __ldg(W + tid + STAR_THREADS);
+  const TS* W = inv + v * WSTRIDE;
+  RowPair<TS> rp;
+  rp.load(W, tid);
   for (int e = tid; e < NS; e += STAR_THREADS) {
     long long nd;
     const float val = star_node(g, vx, vy, vz, e, nd) ? r[(e / SN) * g.N + nd] : 0.f;
@@ -914,17 +948,11 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const
   float acc[STAR_ROWS];
 #pragma unroll
   for (int k = 0; k < STAR_ROWS; ++k) acc[k] = 0.f;
-  float* w0 = &wsh[0][0][0];
-  reinterpret_cast<float4*>(w0)[tid] = f0;
-  if (tid + STAR_THREADS < PAIR) reinterpret_cast<float4*>(w0)[tid + STAR_THREADS] = f1;
+  rp.store(&wsh[0][0][0], tid);
   __syncthreads();
   for (int pr = 0; pr < WT / 2; ++pr) {
     const int cur = pr & 1;
-    if (pr + 1 < WT / 2) {   // the next pair's loads, in flight during this pair's products
-      const float4* Wn = W + (long long)(pr + 1) * PAIR;
-      f0 = __ldg(Wn + tid);
-      if (tid + STAR_THREADS < PAIR) f1 = __ldg(Wn + tid + STAR_THREADS);
-    }
+    if (pr + 1 < WT / 2) rp.load(W + (long long)(pr + 1) * 2 * WLD, tid);   // in flight during this pair
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int t = 2 * pr + h;
@@ -941,11 +969,7 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const
         }
       }
     }
-    if (pr + 1 < WT / 2) {
-      float* wn = &wsh[cur ^ 1][0][0];
-      reinterpret_cast<float4*>(wn)[tid] = f0;
-      if (tid + STAR_THREADS < PAIR) reinterpret_cast<float4*>(wn)[tid + STAR_THREADS] = f1;
-    }
+    if (pr + 1 < WT / 2) rp.store(&wsh[cur ^ 1][0][0], tid);
     __syncthreads();
   }
 #pragma unroll
@@ -962,6 +986,22 @@ __global__ void __launch_bounds__(STAR_THREADS) k_qk3_star_apply_w(Geom g, const
       }
     }
   }
+}
+
+// the wrapped rows in bfloat16, rounded to nearest from the FP64 packed diagonals
+__global__ void k_qk3_wrap16(long long nverts, int pstride, const double* __restrict__ inv64,
+                             __nv_bfloat16* __restrict__ inv16) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nverts * WSTRIDE) return;
+  const long long v = e / WSTRIDE;
+  const int r = (int)(e % WSTRIDE), t = r / WLD, i = r % WLD;
+  double val = 0.0;
+  if (i < NS) {
+    const int j = i + t;
+    const double* S = inv64 + v * pstride;
+    val = j < NS ? S[diag_start(NS, t) + i] : S[diag_start(NS, NS - t) + (j - NS)];
+  }
+  inv16[e] = __double2bfloat16(val);
 }
 
 // the wrapped FP32 rows from the FP64 packed diagonals (loading caller-supplied inverses)
@@ -1181,6 +1221,11 @@ void qk3_derive32(const LevelDev& L, cudaStream_t s) {
   const long long tot = L.g.nverts * qk3::WSTRIDE;
   qk3::k_qk3_wrap32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
   count_launch(1);
+  if (L.inv16) {
+    qk3::k_qk3_wrap16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g.nverts, L.pstride, L.inv64,
+                                                                   (__nv_bfloat16*)L.inv16);
+    count_launch(1);
+  }
 }
 
 void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64) {
@@ -1200,6 +1245,12 @@ void qk3_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_
     qk3::k_qk3_star_setup<double><<<(unsigned)ctas, qk3::SETUP_THREADS, qk3::SETUP_SMEM, s>>>(
         L.g, gamma, L.mu64, L.winv64, L.qk_ws, L.inv64, L.inv32, L.pstride, st);
   count_launch(1);
+  if (L.inv16) {   // ALS_STORE_BF16: the rows again in bfloat16, from the FP64 inverses
+    const long long tot = L.g.nverts * qk3::WSTRIDE;
+    qk3::k_qk3_wrap16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g.nverts, L.pstride, L.inv64,
+                                                                   (__nv_bfloat16*)L.inv16);
+    count_launch(1);
+  }
 }
 
 void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
@@ -1211,7 +1262,12 @@ void qk3_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void*
                                                                    (double*)scratch);
     qk3::k_qk3_star_gather<double><<<b3, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
   } else {
-    qk3::k_qk3_star_apply_w<<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r, (float*)scratch);
+    if (L.inv16)
+      qk3::k_qk3_star_apply_w<__nv_bfloat16><<<nv, qk3::STAR_THREADS, 0, s>>>(
+          L.g, (const __nv_bfloat16*)L.inv16, 0, 0, (const float*)r, (float*)scratch);
+    else
+      qk3::k_qk3_star_apply_w<float><<<nv, qk3::STAR_THREADS, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r,
+                                                                      (float*)scratch);
     qk3::k_qk3_star_gather<float><<<b3, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
   }
   count_launch(2);
@@ -1225,8 +1281,12 @@ void qk3_interior_solve(const LevelDev& fine, int prec, const void* in, void* ou
     qk3::k_qk3_star_apply<double><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
         fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
   else
-    qk3::k_qk3_star_apply_w<<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(fine.g, fine.inv32, 1, subtract ? 2 : 1,
-                                                                       (const float*)in, (float*)out);
+    if (fine.inv16)
+      qk3::k_qk3_star_apply_w<__nv_bfloat16><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
+          fine.g, (const __nv_bfloat16*)fine.inv16, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
+    else
+      qk3::k_qk3_star_apply_w<float><<<(unsigned)nc, qk3::STAR_THREADS, 0, s>>>(
+          fine.g, fine.inv32, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
   count_launch(1);
 }
 

@@ -264,3 +264,53 @@ def test_q3_batch_of_orders_and_dimensions(mode):
         assert np.array_equal(ub[i], u) and np.array_equal(pb_[i], p)
         ctx.close()
     batch.close()
+
+
+def _to_bfloat16(x):
+    """Round to the nearest bfloat16 (8 significant bits), ties to even, from float64."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def test_q3_3d_smoother_with_bfloat16_rows():
+    """ALS_STORE_BF16 at order 3 in 3D: the FP32 smoother streams the wrapped rows rounded
+    to bfloat16 from the FP64 inverses; against the star products of the context's own FP64
+    inverses rounded the same way (host, FP64 sums), entry by entry within FP32 rounding of
+    the sums, and visibly different from the FP32-stored smoother (the rounding is real)."""
+    pb = _problem(4, 2, 1e2, 1e3)
+    ctx = _ctx(pb, store=A.ALS_STORE_BF16)
+    ref32 = _ctx(pb)
+    lv = LevelK(3, pb.n, 3, pb.mu[1], pb.gamma)
+    m = lv.mesh
+    r = _free(lv, 14).astype(np.float32).astype(np.float64)
+    z = torch.zeros(m.nu, dtype=torch.float32, device="cuda")
+    ctx.star_smooth(1, dev(r, torch.float32), z, A.ALS_PREC_FP32)
+    z32 = torch.zeros_like(z)
+    ref32.star_smooth(1, dev(r, torch.float32), z32, A.ALS_PREC_FP32)
+    verts = all_vertices_k(m)
+    offs = np.array([[o % 5, (o // 5) % 5, o // 25] for o in range(125)]) - 2
+    ref, scale = np.zeros(m.nu), np.zeros(m.nu)
+    for vid, v in enumerate(verts):
+        g = 3 * v + offs
+        free = np.all(g > 0, axis=1) & np.all(g < np.array(m.nn) - 1, axis=1)
+        nodes = (g[:, 0] + m.nn[0] * (g[:, 1] + m.nn[1] * g[:, 2]))
+        dofs = np.concatenate([a * m.N + nodes for a in range(3)])
+        keep = np.flatnonzero(np.tile(free, 3))
+        F = _to_bfloat16(ctx.patch_inverse(1, vid))[np.ix_(keep, keep)]
+        rv = r[dofs[keep]]
+        np.add.at(ref, dofs[keep], F @ rv)
+        np.add.at(scale, dofs[keep], np.abs(F) @ np.abs(rv))
+    got = host(z)
+    assert np.all(np.abs(got - ref) <= 400 * 2.0 ** -24 * scale + 1e-30)
+    assert rel(host(z32), ref) > 1e-4          # the FP32-stored smoother differs by the rounding
+
+
+def test_q3_3d_mixed_solve_with_bfloat16_rows():
+    """The mixed solve on bfloat16 rows at mild contrast: converges (P2 pairing), a few
+    iterations more than on FP32 rows at most."""
+    pb = _problem(8, 3, 1e2, 1e4)
+    kw = dict(schur=A.ALS_SCHUR_P2, rtol=1e-8, mode=A.ALS_MODE_MIXED)
+    _, _, i32 = _ctx(pb, **kw).solve(pb.f, pb.u_bc)
+    _, _, i16 = _ctx(pb, store=A.ALS_STORE_BF16, **kw).solve(pb.f, pb.u_bc)
+    assert i32.converged and i16.converged
+    assert i16.iterations <= i32.iterations + 4, (i16.iterations, i32.iterations)
