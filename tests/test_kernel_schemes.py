@@ -1,0 +1,142 @@
+"""Host checks of the index schemes of the 3D order-3 star kernels (csrc/qk3.cu), restated
+in NumPy: the enumeration of an upper triangle by paired rows, the symmetric block
+Gauss-Jordan elimination on the upper triangle with the sign invariant
+M_ji = s_i s_j M_ij, the product over wrapped rows W_t[i] = A(i, (i + t) mod N) (odd N),
+and the paired-diagonal product of the FP64 kernel.  Each restates the kernel's loop
+structure (not its arithmetic order) and compares with the plain dense result; a wrong
+index, sign or bound fails it.  CPU only; these emulate kernels, they are not the oracle."""
+import numpy as np
+import pytest
+
+
+def tri_entry(N, e):
+    half = (N - 1) // 2
+    p, off = divmod(e, N + 1)
+    if p < half:
+        if off < N - p:
+            return p, p + off
+        i = N - 1 - p
+        return i, i + off - (N - p)
+    return half, half + off
+
+
+def diag_start(n, t):
+    return t * n - (t * (t - 1)) // 2
+
+
+@pytest.mark.parametrize("N", [27, 375, 5])
+def test_triangle_enumeration_covers_each_entry_once(N):
+    seen = [tri_entry(N, e) for e in range(N * (N + 1) // 2)]
+    assert len(set(seen)) == len(seen) == N * (N + 1) // 2
+    assert all(0 <= i <= j < N for i, j in seen)
+    # consecutive e walk along a row (coalesced rows of the workspace)
+    steps = sum(1 for a, b in zip(seen, seen[1:]) if a[0] == b[0] and b[1] == a[1] + 1)
+    assert steps >= len(seen) - 2 * N
+
+
+def symmetric_block_gauss_jordan(A, BB):
+    """The kernel's passes on the upper triangle only: X_x = M(min(x, K), max(x, K)),
+    Y = Dk X, M_ij -= sigma_j X_i . Y_j (sigma_j = -1 for j < k0), M_iK = -Y_i (i < k0),
+    M_Kj = Y_j (j beyond K), M_KK = Dk."""
+    N = A.shape[0]
+    M = np.triu(A).astype(np.float64)
+    for k0 in range(0, N, BB):
+        b = min(BB, N - k0)
+        K = np.arange(k0, k0 + b)
+        Dk = np.linalg.inv(np.array([[M[min(m, l), max(m, l)] for l in K] for m in K]))
+        X = np.zeros((N, b))
+        for x in range(N):
+            if k0 <= x < k0 + b:
+                continue
+            for li, k in enumerate(K):
+                X[x, li] = M[x, k] if x < k else M[k, x]
+        Y = Dk @ X.T
+        new = M.copy()
+        for e in range(N * (N + 1) // 2):
+            i, j = tri_entry(N, e)
+            ik, jk = k0 <= i < k0 + b, k0 <= j < k0 + b
+            if ik and jk:
+                new[i, j] = Dk[i - k0, j - k0]
+            elif jk:
+                new[i, j] = -Y[j - k0, i]
+            elif ik:
+                new[i, j] = Y[i - k0, j]
+            else:
+                sigma = -1.0 if j < k0 else 1.0
+                new[i, j] = M[i, j] - sigma * X[i] @ Y[:, j]
+        M = new
+    return M
+
+
+@pytest.mark.parametrize("N,BB", [(37, 16), (27, 16), (75, 16), (33, 8)])
+def test_symmetric_block_gauss_jordan_inverts(N, BB):
+    rng = np.random.default_rng(N)
+    B = rng.standard_normal((N, N))
+    A = B @ B.T + N * np.eye(N)
+    M = symmetric_block_gauss_jordan(A, BB)
+    Ainv = np.linalg.inv(A)
+    assert np.abs(np.triu(M) - np.triu(Ainv)).max() <= 1e-13 * np.abs(Ainv).max()
+
+
+def test_symmetric_block_gauss_jordan_with_identity_rows():
+    """Absent and Dirichlet star nodes enter as identity rows and columns: their entries of
+    the inverse stay exactly those of the identity."""
+    rng = np.random.default_rng(3)
+    N, free = 37, np.ones(37, bool)
+    free[[0, 5, 6, 20, 36]] = False
+    B = rng.standard_normal((N, N))
+    A = B @ B.T + N * np.eye(N)
+    A[~free] = 0.0
+    A[:, ~free] = 0.0
+    A[~free, ~free] = 1.0
+    M = symmetric_block_gauss_jordan(A, 16)
+    U = np.triu(M)
+    idx = np.flatnonzero(~free)
+    assert np.all(U[np.ix_(idx, idx)] == np.triu(np.eye(len(idx))))
+    mixed = np.not_equal.outer(free, free)      # one index free, the other not
+    assert np.all(U[np.triu(mixed)] == 0.0)
+    Ainv = np.linalg.inv(A)
+    assert np.abs(U - np.triu(Ainv)).max() <= 1e-13 * np.abs(Ainv).max()
+
+
+@pytest.mark.parametrize("N", [375, 7])
+def test_wrapped_row_product(N):
+    WT, WLD = (N + 1) // 2, (N + 4) // 4 * 4
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((N, N))
+    A = A + A.T
+    W = np.zeros((WT, WLD))
+    for t in range(WT):
+        for i in range(N):
+            W[t, i] = A[i, (i + t) % N]
+    assert WT * WLD >= N * (N + 1) // 2
+    r = rng.standard_normal(N)
+    r2 = np.concatenate([r, r])
+    y = np.zeros(N)
+    for t in range(WT):
+        for i in range(N):
+            y[i] += W[t, i] * r2[i + t]
+            if t > 0:
+                m = i - t + N if i - t < 0 else i - t
+                y[i] += W[t, m] * r2[m]
+    assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
+
+
+@pytest.mark.parametrize("N", [375, 9])
+def test_paired_diagonal_product(N):
+    """The FP64 star product over packed diagonals, steps t and N - t in one iteration."""
+    rng = np.random.default_rng(N)
+    A = rng.standard_normal((N, N))
+    A = A + A.T
+    S = np.concatenate([np.diag(A, t) for t in range(N)])
+    r = rng.standard_normal(N)
+    y = np.array([S[i] * r[i] for i in range(N)])
+    for t in range(1, N // 2 + 1):
+        u = N - t
+        for i in range(N):
+            a, b = i < u, i < t
+            p1 = diag_start(N, t) + i if a else diag_start(N, u) + (i - u)
+            p2 = diag_start(N, u) + i if b else diag_start(N, t) + (i - t)
+            assert 0 <= p1 < len(S) and 0 <= p2 < len(S)
+            y[i] += S[p1] * r[i + t if a else i - u] + S[p2] * r[i + u if b else i - t]
+    assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
