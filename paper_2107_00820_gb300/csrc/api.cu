@@ -804,10 +804,10 @@ constexpr long long kSplitVertices = 32768;
 static als_status alloc_star_storage(als_ctx* c, LevelDev& Lv) {
   const Geom& g = Lv.g;
   const int d = c->dim;
-  if (c->k == 3) {   // order 3: an FP32 copy of every star (2D: packed by diagonals, 3D: wrapped rows)
+  if (c->k == 3) {   // order 3: an FP32 copy of every star, in wrapped rows
     Lv.split = 0;
     Lv.nbnd = 0;
-    return dalloc(c, &Lv.inv32, (size_t)g.nverts * (d == 3 ? qk3_star32_floats() : (size_t)Lv.pstride));
+    return dalloc(c, &Lv.inv32, (size_t)g.nverts * qk_star32_floats(d));
   }
   Lv.nint = 1;
   for (int k = 0; k < d; ++k) Lv.nint *= g.nv[k] - 2;

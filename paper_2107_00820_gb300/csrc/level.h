@@ -141,6 +141,10 @@ void qk_mass_setup(const LevelDev& L, double gamma, int w_mu, int variant, doubl
                    DevStatus* st, cudaStream_t s);
 // df64: 3D levels eliminate in double-float (2D order 3 is FP64 throughout)
 void qk_patch_setup(const LevelDev& L, double gamma, DevStatus* st, cudaStream_t s, int df64);
+// FP32 entries per star of an order-3 level (inv32 holds the stars in wrapped rows), and
+// inv32 formed from inv64
+size_t qk_star32_floats(int dim);
+void qk_derive32(const LevelDev& L, cudaStream_t s);
 void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* scratch, const void* den,
                      cudaStream_t s);
 void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out, int subtract, cudaStream_t s);

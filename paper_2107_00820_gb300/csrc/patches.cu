@@ -935,9 +935,8 @@ __global__ void __launch_bounds__(256) k_derive32_bnd(Geom g, int pstride, const
 }
 
 void patch_derive32(const LevelDev& L, cudaStream_t s) {
-  if (L.k == 3) {   // 2D: the same packed-by-diagonals layout in both precisions; 3D: wrapped rows
-    if (L.g.dim == 3) qk3_derive32(L, s);
-    else vec_cast(L.g.nverts * L.pstride, L.inv64, PREC_F64, L.inv32, PREC_F32, s);
+  if (L.k == 3) {   // the FP32 wrapped rows of the order-3 stars
+    qk_derive32(L, s);
     return;
   }
   const long long nv32 = L.split ? L.nint : L.g.nverts;

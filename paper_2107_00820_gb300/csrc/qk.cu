@@ -32,6 +32,14 @@ constexpr int NE = 2 * NB;     // velocity dofs per cell
 constexpr int NPR = 6;         // pressure monomials per cell
 constexpr int S1 = 2 * K - 1;  // star nodes per axis
 constexpr int NS = 2 * S1 * S1;   // star dofs (50)
+// FP32 star storage in wrapped rows W_t[i] = A(i, (i + t) mod NS), t = 0..NS/2 (NS is even:
+// row NS/2 holds each pair {i, i + NS/2} twice, and the product reads it once per row), rows
+// padded to 52 entries (16-byte rows): 1,352 floats a star against 1,276 for the packed
+// diagonals; the product then needs no per-entry choice of diagonal
+constexpr int kWT = NS / 2 + 1;   // 26
+constexpr int kWLD = 52;
+constexpr int kWStride = kWT * kWLD;
+static_assert(NS % 2 == 0 && kWLD % 4 == 0 && kWLD >= NS, "wrapped-row layout");
 
 // 1D tables at the Gauss points: L[q][a] = l_a(g_q), D[q][a] = l_a'(g_q), W[q]; the 2D
 // pressure monomials at the points PSI[q][p]; the prolongation weights PW[f][a] = l_a(xi_f)
@@ -498,14 +506,14 @@ __global__ void __launch_bounds__(256) k_qk_star_setup(Geom g, double gamma, con
     }
     __syncthreads();
   }
-  // upper triangle by diagonals (entry (i, i+t)), symmetrised
+  // FP64: upper triangle by diagonals (entry (i, i+t)); FP32: the wrapped rows; both symmetrised
   for (int t = 0; t < NS; ++t) {
     const int base = diag_start(NS, t);
-    for (int i = tid; i + t < NS; i += nt) {
-      const double val = 0.5 * (M[i][i + t] + M[i + t][i]);
-      inv64[v * pstride + base + i] = val;
-      inv32[v * pstride + base + i] = (float)val;
-    }
+    for (int i = tid; i + t < NS; i += nt) inv64[v * pstride + base + i] = 0.5 * (M[i][i + t] + M[i + t][i]);
+  }
+  for (int e = tid; e < kWStride; e += nt) {
+    const int t = e / kWLD, i = e % kWLD, j = i + t < NS ? i + t : i + t - NS;
+    inv32[v * kWStride + e] = i < NS ? (float)(0.5 * (M[i][j] + M[j][i])) : 0.f;
   }
 }
 
@@ -575,6 +583,87 @@ __global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, 
       }
     }
   }
+}
+
+// The FP32 product from the wrapped rows: one warp per star (8 a block), the star's rows
+// staged in shared memory by 16-byte loads from all lanes at once, r held twice over so
+// that no index wraps; y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t]
+// r_(i-t) (indices mod NS).  interior / mode as k_qk_star_apply.
+__global__ void __launch_bounds__(256) k_qk_star_apply_w(Geom g, const float* __restrict__ inv, int interior,
+                                                         int mode, const float* __restrict__ r,
+                                                         float* __restrict__ out) {
+  constexpr int R = (NS + 31) / 32, WPB = 8, NV = kWStride / 4;
+  __shared__ float rs2[WPB][2 * NS];
+  __shared__ __align__(16) float ws[WPB][kWStride];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long count = interior ? (long long)(g.n[0] / 2) * (g.n[1] / 2) : (long long)(g.n[0] + 1) * (g.n[1] + 1);
+  const long long item = (long long)blockIdx.x * WPB + w;
+  if (item >= count) return;   // uniform over the warp; no block barrier below
+  int vx, vy;
+  if (interior) { vx = 2 * (int)(item % (g.n[0] / 2)) + 1; vy = 2 * (int)(item / (g.n[0] / 2)) + 1; }
+  else { vx = (int)(item % (g.n[0] + 1)); vy = (int)(item / (g.n[0] + 1)); }
+  const long long v = (long long)vx + (long long)(g.n[0] + 1) * vy;
+  const float4* src = reinterpret_cast<const float4*>(inv + v * kWStride);
+  float4* dst = reinterpret_cast<float4*>(&ws[w][0]);
+#pragma unroll 4
+  for (int e = lane; e < NV; e += 32) dst[e] = __ldg(src + e);
+  for (int e = lane; e < NS; e += 32) {
+    long long nd;
+    const float val = star_node(g, vx, vy, e, nd) ? r[(e / (S1 * S1)) * g.N + nd] : 0.f;
+    rs2[w][e] = val;
+    rs2[w][e + NS] = val;
+  }
+  __syncwarp();
+  float acc[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = 0.f;
+  const float* W = &ws[w][0];
+  const float* rr = &rs2[w][0];
+#pragma unroll 2
+  for (int t = 0; t < kWT; ++t) {
+    const float* wr = W + t * kWLD;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < NS) {
+        acc[k] += wr[i] * rr[i + t];
+        if (t > 0 && t < NS / 2) {
+          const int m = i - t < 0 ? i - t + NS : i - t;   // row m = i - t (mod NS) holds A(m, i)
+          acc[k] += wr[m] * rr[m];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = lane + 32 * k;
+    if (i >= NS) continue;
+    if (!interior) {
+      out[v * NS + i] = acc[k];
+    } else {
+      long long nd;
+      if (star_node(g, vx, vy, i, nd)) {
+        float* o = out + (i / (S1 * S1)) * g.N + nd;
+        *o = mode == 2 ? *o - acc[k] : acc[k];
+      }
+    }
+  }
+}
+
+// the wrapped FP32 rows from the FP64 packed diagonals (loading caller-supplied inverses)
+__global__ void k_qk_wrap32(long long nverts, int pstride, const double* __restrict__ inv64,
+                            float* __restrict__ inv32) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nverts * kWStride) return;
+  const long long v = e / kWStride;
+  const int rem = (int)(e % kWStride), t = rem / kWLD, i = rem % kWLD;
+  float val = 0.f;
+  if (i < NS) {
+    const int j = i + t;
+    const double* S = inv64 + v * pstride;
+    val = (float)(j < NS ? S[diag_start(NS, t) + i] : S[diag_start(NS, NS - t) + (j - NS)]);
+  }
+  inv32[e] = val;
 }
 
 // z(node) = sum over the stars containing the node (vertices v with |i - 3v| <= 2 per
@@ -714,6 +803,15 @@ void qk_apply_epi(const LevelDev& L, int prec, double gamma, const void* x, void
   else apply_epi_t<float>(L, gamma, x, y, e, s, e0, e1);
 }
 
+size_t qk_star32_floats(int dim) { return dim == 3 ? qk3_star32_floats() : (size_t)qk::kWStride; }
+
+void qk_derive32(const LevelDev& L, cudaStream_t s) {
+  if (L.g.dim == 3) return qk3_derive32(L, s);
+  const long long tot = L.g.nverts * qk::kWStride;
+  qk::k_qk_wrap32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.g.nverts, L.pstride, L.inv64, L.inv32);
+  count_launch(1);
+}
+
 void qk_load_vector(const LevelDev& L, const double* f_qp, double* F, cudaStream_t s) {
   if (L.g.dim == 3) return qk3_load_vector(L, f_qp, F, s);
   const long long tot = L.g.ncells * qk::NE;
@@ -748,8 +846,8 @@ void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* 
         L.g, L.inv64, L.pstride, 0, 0, (const double*)r, (double*)scratch);
     qk::k_qk_star_gather<double><<<b2, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
   } else {
-    qk::k_qk_star_apply<float><<<(unsigned)((L.g.nverts + W32 - 1) / W32), 32 * W32, 0, s>>>(
-        L.g, L.inv32, L.pstride, 0, 0, (const float*)r, (float*)scratch);
+    qk::k_qk_star_apply_w<<<(unsigned)((L.g.nverts + 7) / 8), 256, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r,
+                                                                        (float*)scratch);
     qk::k_qk_star_gather<float><<<b2, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
   }
   count_launch(2);
@@ -765,8 +863,8 @@ void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out
     qk::k_qk_star_apply<double><<<(unsigned)((nc + W64 - 1) / W64), 32 * W64, 0, s>>>(
         fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
   else
-    qk::k_qk_star_apply<float><<<(unsigned)((nc + W32 - 1) / W32), 32 * W32, 0, s>>>(
-        fine.g, fine.inv32, fine.pstride, 1, subtract ? 2 : 1, (const float*)in, (float*)out);
+    qk::k_qk_star_apply_w<<<(unsigned)((nc + 7) / 8), 256, 0, s>>>(fine.g, fine.inv32, 1, subtract ? 2 : 1,
+                                                                 (const float*)in, (float*)out);
   count_launch(1);
 }
 

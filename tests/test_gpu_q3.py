@@ -173,3 +173,26 @@ def test_q3_fgmres_counts_equal_the_oracle(schur, W, gamma, dr):
     um, pm, im = _ctx(pb, schur=schur, rtol=1e-8, mode=A.ALS_MODE_MIXED).solve(pb.f, pb.u_bc)
     assert im.converged and im.iterations <= its + 2, (im.iterations, its)
     assert _true_residual(s, pb, um, pm) <= 1.5e-8
+
+
+def test_q3_loaded_inverses_give_the_same_fp32_smoother():
+    """Caller-supplied FP64 inverses (packed by diagonals) are rounded into the FP32 wrapped
+    rows by the setup's own rule: reloading the context's inverses leaves the FP32
+    smoother's output bit for bit unchanged."""
+    pb = _problem(8, 2, 1e2, 1e3)
+    ctx = _ctx(pb)
+    lv = LevelK(2, pb.n, 3, pb.mu[1], pb.gamma)
+    np_ = 50
+    stride = (np_ * (np_ + 1) // 2 + 3) // 4 * 4
+    starts = [t * np_ - t * (t - 1) // 2 for t in range(np_)]
+
+    def pack(full):
+        return np.concatenate([np.diag(full, t) for t in range(np_)] + [np.zeros(stride - starts[-1] - 1)])
+
+    r = dev(_free(lv, 13), torch.float32)
+    z0 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z0, A.ALS_PREC_FP32)
+    ctx.load_patch_inverses(1, np.concatenate([pack(ctx.patch_inverse(1, v)) for v in range(9 ** 2)]))
+    z1 = torch.zeros_like(r)
+    ctx.star_smooth(1, r, z1, A.ALS_PREC_FP32)
+    assert torch.equal(z0, z1)

@@ -1,7 +1,7 @@
-"""Host checks of the index schemes of the 3D order-3 star kernels (csrc/qk3.cu), restated
+"""Host checks of the index schemes of the order-3 star kernels (csrc/qk3.cu, csrc/qk.cu), restated
 in NumPy: the enumeration of an upper triangle by paired rows, the symmetric block
 Gauss-Jordan elimination on the upper triangle with the sign invariant
-M_ji = s_i s_j M_ij, the product over wrapped rows W_t[i] = A(i, (i + t) mod N) (odd N),
+M_ji = s_i s_j M_ij, the product over wrapped rows W_t[i] = A(i, (i + t) mod N) (odd N in 3D, even in 2D),
 and the paired-diagonal product of the FP64 kernel.  Each restates the kernel's loop
 structure (not its arithmetic order) and compares with the plain dense result; a wrong
 index, sign or bound fails it.  CPU only; these emulate kernels, they are not the oracle."""
@@ -117,6 +117,30 @@ def test_wrapped_row_product(N):
         for i in range(N):
             y[i] += W[t, i] * r2[i + t]
             if t > 0:
+                m = i - t + N if i - t < 0 else i - t
+                y[i] += W[t, m] * r2[m]
+    assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
+
+
+@pytest.mark.parametrize("N", [50, 8])
+def test_wrapped_row_product_even_order(N):
+    """Even N (the 2D order-3 stars, N = 50): rows t = 0..N/2, the row N/2 read once per
+    row (it holds each pair {i, i + N/2} twice), the transposed term for 0 < t < N/2."""
+    WT, WLD = N // 2 + 1, (N + 3) // 4 * 4
+    rng = np.random.default_rng(N)
+    A = rng.standard_normal((N, N))
+    A = A + A.T
+    W = np.zeros((WT, WLD))
+    for t in range(WT):
+        for i in range(N):
+            W[t, i] = A[i, (i + t) % N]
+    r = rng.standard_normal(N)
+    r2 = np.concatenate([r, r])
+    y = np.zeros(N)
+    for t in range(WT):
+        for i in range(N):
+            y[i] += W[t, i] * r2[i + t]
+            if 0 < t < N // 2:
                 m = i - t + N if i - t < 0 else i - t
                 y[i] += W[t, m] * r2[m]
     assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
