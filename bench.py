@@ -721,7 +721,7 @@ def ours(args, dist):
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm",
                      "kernel": ("k_patch_tma<%d> (FP32 interior-star smoother, finest level)" % pb.d) if order == 2
-                     else "k_qk%s_star_apply<float> + k_qk%s_star_gather (FP32 order-3 star smoother, finest level)"
+                     else "k_qk%s_star_apply_w + k_qk%s_star_gather<float> (FP32 order-3 star smoother, finest level)"
                      % (("3", "3") if pb.d == 3 else ("", "")),
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,

@@ -585,69 +585,131 @@ __global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, 
   }
 }
 
-// The FP32 product from the wrapped rows: one warp per star (8 a block), the star's rows
-// staged in shared memory by 16-byte loads from all lanes at once, r held twice over so
-// that no index wraps; y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t]
-// r_(i-t) (indices mod NS).  interior / mode as k_qk_star_apply.
-__global__ void __launch_bounds__(256) k_qk_star_apply_w(Geom g, const float* __restrict__ inv, int interior,
-                                                         int mode, const float* __restrict__ r,
-                                                         float* __restrict__ out) {
-  constexpr int R = (NS + 31) / 32, WPB = 8, NV = kWStride / 4;
+// The FP32 product from the wrapped rows, a star per warp (8 warps a block), the star's rows
+// staged in shared memory, r held twice over so that no index wraps;
+// y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t] r_(i-t) (indices mod NS).
+// interior / mode as k_qk_star_apply.  Persistent: the host sizes the grid to
+// kStarWBlocksPerSM blocks an SM and each warp walks the stars item, item + warps, ...;
+// while it multiplies one star out of shared memory, the next star's rows (16-byte loads,
+// at most eleven a lane) and r values are already on their way into registers, so every
+// star but a warp's first has its memory latency hidden behind the previous star's
+// products.  (With one star a warp and no prefetch, each star paid its dependent round
+// trips in full: 7.7 long-scoreboard stalls per issued instruction, DRAM 35 % busy.)
+// Outputs never overlap inputs within a launch (the scratch rows, or interior nodes of
+// distinct coarse cells), so reading the next star's r early is safe.
+constexpr int kStarWBlocksPerSM = 3;   // 3 x 256 threads at <= 85 registers, 3 x 46.5 KB shared
+
+__global__ void __launch_bounds__(256, kStarWBlocksPerSM) k_qk_star_apply_w(Geom g, const float* __restrict__ inv,
+                                                                            int interior, int mode,
+                                                                            const float* __restrict__ r,
+                                                                            float* __restrict__ out) {
+  constexpr int R = (NS + 31) / 32, WPB = 8, NV = kWStride / 4, PF = (NV + 31) / 32;
   __shared__ float rs2[WPB][2 * NS];
   __shared__ __align__(16) float ws[WPB][kWStride];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long count = interior ? (long long)(g.n[0] / 2) * (g.n[1] / 2) : (long long)(g.n[0] + 1) * (g.n[1] + 1);
-  const long long item = (long long)blockIdx.x * WPB + w;
+  const long long nwarps = (long long)gridDim.x * WPB;
+  long long item = (long long)blockIdx.x * WPB + w;
   if (item >= count) return;   // uniform over the warp; no block barrier below
-  int vx, vy;
-  if (interior) { vx = 2 * (int)(item % (g.n[0] / 2)) + 1; vy = 2 * (int)(item / (g.n[0] / 2)) + 1; }
-  else { vx = (int)(item % (g.n[0] + 1)); vy = (int)(item / (g.n[0] + 1)); }
-  const long long v = (long long)vx + (long long)(g.n[0] + 1) * vy;
-  const float4* src = reinterpret_cast<const float4*>(inv + v * kWStride);
-  float4* dst = reinterpret_cast<float4*>(&ws[w][0]);
-#pragma unroll 4
-  for (int e = lane; e < NV; e += 32) dst[e] = __ldg(src + e);
-  for (int e = lane; e < NS; e += 32) {
-    long long nd;
-    const float val = star_node(g, vx, vy, e, nd) ? r[(e / (S1 * S1)) * g.N + nd] : 0.f;
-    rs2[w][e] = val;
-    rs2[w][e + NS] = val;
-  }
-  __syncwarp();
-  float acc[R];
+  const auto vertex = [&](long long it, int& vx, int& vy) {
+    if (interior) { vx = 2 * (int)(it % (g.n[0] / 2)) + 1; vy = 2 * (int)(it / (g.n[0] / 2)) + 1; }
+    else { vx = (int)(it % (g.n[0] + 1)); vy = (int)(it / (g.n[0] + 1)); }
+  };
+  // a star's rows and r values into registers (consumed by the next pass's staging)
+  float4 pw[PF];
+  float pr[R];
+  const auto fetch = [&](long long it) {
+    int fx, fy;
+    vertex(it, fx, fy);
+    const float4* src = reinterpret_cast<const float4*>(inv + ((long long)fx + (long long)(g.n[0] + 1) * fy) * kWStride);
 #pragma unroll
-  for (int k = 0; k < R; ++k) acc[k] = 0.f;
-  const float* W = &ws[w][0];
-  const float* rr = &rs2[w][0];
-#pragma unroll 2
-  for (int t = 0; t < kWT; ++t) {
-    const float* wr = W + t * kWLD;
+    for (int q = 0; q < PF; ++q) {
+      const int e = lane + 32 * q;
+      if (e < NV) pw[q] = __ldg(src + e);
+    }
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const int i = lane + 32 * k;
-      if (i < NS) {
-        acc[k] += wr[i] * rr[i + t];
-        if (t > 0 && t < NS / 2) {
-          const int m = i - t < 0 ? i - t + NS : i - t;   // row m = i - t (mod NS) holds A(m, i)
-          acc[k] += wr[m] * rr[m];
+      const int e = lane + 32 * k;
+      long long nd;
+      pr[k] = (e < NS && star_node(g, fx, fy, e, nd)) ? r[(e / (S1 * S1)) * g.N + nd] : 0.f;
+    }
+  };
+  fetch(item);
+  for (;;) {
+    int vx, vy;
+    vertex(item, vx, vy);
+    const long long v = (long long)vx + (long long)(g.n[0] + 1) * vy;
+    __syncwarp();   // every lane has finished reading the previous star from ws / rs2
+    float4* dst = reinterpret_cast<float4*>(&ws[w][0]);
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = lane + 32 * q;
+      if (e < NV) dst[e] = pw[q];
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int e = lane + 32 * k;
+      if (e < NS) {
+        rs2[w][e] = pr[k];
+        rs2[w][e + NS] = pr[k];
+      }
+    }
+    __syncwarp();
+    const long long next = item + nwarps;
+    if (next < count) fetch(next);   // in flight during this star's products
+    float acc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = 0.f;
+    const float* W = &ws[w][0];
+    const float* rr = &rs2[w][0];
+#pragma unroll 2
+    for (int t = 0; t < kWT; ++t) {
+      const float* wr = W + t * kWLD;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        if (i < NS) {
+          acc[k] += wr[i] * rr[i + t];
+          if (t > 0 && t < NS / 2) {
+            const int m = i - t < 0 ? i - t + NS : i - t;   // row m = i - t (mod NS) holds A(m, i)
+            acc[k] += wr[m] * rr[m];
+          }
         }
       }
     }
-  }
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int i = lane + 32 * k;
-    if (i >= NS) continue;
-    if (!interior) {
-      out[v * NS + i] = acc[k];
-    } else {
-      long long nd;
-      if (star_node(g, vx, vy, i, nd)) {
-        float* o = out + (i / (S1 * S1)) * g.N + nd;
-        *o = mode == 2 ? *o - acc[k] : acc[k];
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i >= NS) continue;
+      if (!interior) {
+        out[v * NS + i] = acc[k];
+      } else {
+        long long nd;
+        if (star_node(g, vx, vy, i, nd)) {
+          float* o = out + (i / (S1 * S1)) * g.N + nd;
+          *o = mode == 2 ? *o - acc[k] : acc[k];
+        }
       }
     }
+    if (next >= count) break;
+    item = next;
   }
+}
+
+// blocks of a k_qk_star_apply_w launch over `count` stars: one star a warp up to
+// kStarWBlocksPerSM resident blocks an SM, beyond that the warps loop
+static unsigned star_w_blocks(long long count) {
+  static const int cap = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    return kStarWBlocksPerSM * sms;
+  }();
+  const long long need = (count + 7) / 8;
+  return (unsigned)(need < 1 ? 1 : need < cap ? need : cap);
 }
 
 // the wrapped FP32 rows from the FP64 packed diagonals (loading caller-supplied inverses)
@@ -846,8 +908,8 @@ void qk_patch_smooth(const LevelDev& L, int prec, const void* r, void* z, void* 
         L.g, L.inv64, L.pstride, 0, 0, (const double*)r, (double*)scratch);
     qk::k_qk_star_gather<double><<<b2, 256, 0, s>>>(L.g, (const double*)scratch, (double*)z, (const double*)den);
   } else {
-    qk::k_qk_star_apply_w<<<(unsigned)((L.g.nverts + 7) / 8), 256, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r,
-                                                                        (float*)scratch);
+    qk::k_qk_star_apply_w<<<qk::star_w_blocks(L.g.nverts), 256, 0, s>>>(L.g, L.inv32, 0, 0, (const float*)r,
+                                                                      (float*)scratch);
     qk::k_qk_star_gather<float><<<b2, 256, 0, s>>>(L.g, (const float*)scratch, (float*)z, (const float*)den);
   }
   count_launch(2);
@@ -863,8 +925,8 @@ void qk_interior_solve(const LevelDev& fine, int prec, const void* in, void* out
     qk::k_qk_star_apply<double><<<(unsigned)((nc + W64 - 1) / W64), 32 * W64, 0, s>>>(
         fine.g, fine.inv64, fine.pstride, 1, subtract ? 2 : 1, (const double*)in, (double*)out);
   else
-    qk::k_qk_star_apply_w<<<(unsigned)((nc + 7) / 8), 256, 0, s>>>(fine.g, fine.inv32, 1, subtract ? 2 : 1,
-                                                                 (const float*)in, (float*)out);
+    qk::k_qk_star_apply_w<<<qk::star_w_blocks(nc), 256, 0, s>>>(fine.g, fine.inv32, 1, subtract ? 2 : 1,
+                                                              (const float*)in, (float*)out);
   count_launch(1);
 }
 

@@ -196,3 +196,29 @@ def test_q3_loaded_inverses_give_the_same_fp32_smoother():
     z1 = torch.zeros_like(r)
     ctx.star_smooth(1, r, z1, A.ALS_PREC_FP32)
     assert torch.equal(z0, z1)
+
+
+def test_q3_fp32_star_kernel_with_warps_walking_several_stars():
+    """The FP32 star kernel is persistent (three blocks an SM; each warp walks several stars,
+    the next star's rows prefetched while it multiplies the current one).  On 2D 96^2
+    (9,409 stars, more than the 3,648 warps of a 152-SM grid; 2,304 interior stars for the
+    transfers) the FP32 smoother and the FP32 robust transfers, whose local solves write and
+    subtract through the same kernel, match the FP64 path (its own star kernel) within the
+    FP32 smoother bar: a star skipped, repeated or read from another warp's rows fails it."""
+    pb = _problem(96, 5, 1.0, 1e2)
+    ctx = _ctx(pb)
+    L = pb.levels - 1
+    rng = np.random.default_rng(23)
+    out = {}
+    r = rng.standard_normal(ctx.nu(L))
+    xc = rng.standard_normal(ctx.nu(L - 1))
+    for prec, dt in ((A.ALS_PREC_FP64, torch.float64), (A.ALS_PREC_FP32, torch.float32)):
+        z = torch.zeros(ctx.nu(L), dtype=dt, device="cuda")
+        ctx.star_smooth(L, dev(r, dt), z, prec)
+        xf = torch.zeros(ctx.nu(L), dtype=dt, device="cuda")
+        ctx.prolong(L, dev(xc, dt), xf, prec)
+        rc = torch.zeros(ctx.nu(L - 1), dtype=dt, device="cuda")
+        ctx.restrict(L, dev(r, dt), rc, prec)
+        out[prec] = [host(z), host(xf), host(rc)]
+    for a, b in zip(out[A.ALS_PREC_FP32], out[A.ALS_PREC_FP64]):
+        assert rel(a, b) <= 1e-4

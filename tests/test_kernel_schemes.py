@@ -164,3 +164,37 @@ def test_paired_diagonal_product(N):
             assert 0 <= p1 < len(S) and 0 <= p2 < len(S)
             y[i] += S[p1] * r[i + t if a else i - u] + S[p2] * r[i + u if b else i - t]
     assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
+
+
+@pytest.mark.parametrize("count", [1, 7, 81, 3648, 3649, 16641])
+@pytest.mark.parametrize("sms", [152, 1])
+def test_persistent_star_walk_with_prefetch(count, sms):
+    """The 2D order-3 FP32 star kernel's walk: min(ceil(count / 8), 3 sms) blocks of 8 warps,
+    warp item = block * 8 + w, then item + warps ...; the warp fetches its first star before
+    the loop and, in each pass, the next star (if any) before it multiplies the current one.
+    Every star is staged and multiplied exactly once, always from the fetch made one pass
+    earlier; the 16-byte words of a star (1,352 floats) split over 32 lanes in 11 slots
+    cover each word once."""
+    WPB, NV = 8, 26 * 52 // 4
+    blocks = max(1, min((count + 7) // 8, 3 * sms))
+    nwarps = blocks * WPB
+    done = []
+    for b in range(blocks):
+        for w in range(WPB):
+            item = b * WPB + w
+            if item >= count:
+                continue
+            held = item                    # fetch(item) before the loop
+            while True:
+                staged = held              # the registers go to shared memory
+                nxt = item + nwarps
+                if nxt < count:
+                    held = nxt             # fetch(next), in flight during the products
+                assert staged == item
+                done.append(item)
+                if nxt >= count:
+                    break
+                item = nxt
+    assert sorted(done) == list(range(count))
+    words = [lane + 32 * q for q in range((NV + 31) // 32) for lane in range(32) if lane + 32 * q < NV]
+    assert sorted(words) == list(range(NV))
