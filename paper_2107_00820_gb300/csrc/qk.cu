@@ -587,7 +587,8 @@ __global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, 
 
 // The FP32 product from the wrapped rows, a star per warp (8 warps a block), the star's rows
 // staged in shared memory, r held twice over so that no index wraps;
-// y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t] r_(i-t) (indices mod NS).
+// y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t] r_(i-t) (indices mod NS),
+// rows i and i + NS/2 on one lane (see below).
 // interior / mode as k_qk_star_apply.  Persistent: the host sizes the grid to
 // kStarWBlocksPerSM blocks an SM and each warp walks the stars item, item + warps, ...;
 // while it multiplies one star out of shared memory, the next star's rows (16-byte loads,
@@ -603,7 +604,8 @@ __global__ void __launch_bounds__(256, kStarWBlocksPerSM) k_qk_star_apply_w(Geom
                                                                             int interior, int mode,
                                                                             const float* __restrict__ r,
                                                                             float* __restrict__ out) {
-  constexpr int R = (NS + 31) / 32, WPB = 8, NV = kWStride / 4, PF = (NV + 31) / 32;
+  constexpr int R = (NS + 31) / 32, WPB = 8, NV = kWStride / 4, PF = (NV + 31) / 32, H = NS / 2;
+  static_assert(H <= 32 && kWT == H + 1, "two rows a lane");
   __shared__ float rs2[WPB][2 * NS];
   __shared__ __align__(16) float ws[WPB][kWStride];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -657,30 +659,32 @@ __global__ void __launch_bounds__(256, kStarWBlocksPerSM) k_qk_star_apply_w(Geom
     __syncwarp();
     const long long next = item + nwarps;
     if (next < count) fetch(next);   // in flight during this star's products
-    float acc[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) acc[k] = 0.f;
+    // lane j < H owns rows j and j + H; row j takes step t while row j + H takes step
+    // H - t, which reads the same two r values (r_(j+t) and r_(j-t mod NS)): six shared
+    // reads per four FMAs instead of eight
+    float acc[2] = {0.f, 0.f};
     const float* W = &ws[w][0];
     const float* rr = &rs2[w][0];
+    if (lane < H) {
+      const int j = lane;
 #pragma unroll 2
-    for (int t = 0; t < kWT; ++t) {
-      const float* wr = W + t * kWLD;
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const int i = lane + 32 * k;
-        if (i < NS) {
-          acc[k] += wr[i] * rr[i + t];
-          if (t > 0 && t < NS / 2) {
-            const int m = i - t < 0 ? i - t + NS : i - t;   // row m = i - t (mod NS) holds A(m, i)
-            acc[k] += wr[m] * rr[m];
-          }
+      for (int t = 0; t <= H; ++t) {
+        const float* wt = W + t * kWLD;         // W_t
+        const float* wu = W + (H - t) * kWLD;   // W_(H-t)
+        const float a = rr[j + t], b = rr[j - t + NS];
+        acc[0] += wt[j] * a;
+        if (t > 0 && t < H) {
+          const int m = j - t < 0 ? j - t + NS : j - t;   // row m = j - t (mod NS) holds A(m, j)
+          acc[0] += wt[m] * b;
+          acc[1] += wu[j + t] * a;                        // A(j + t, j + H) r_(j+t)
         }
+        acc[1] += wu[j + H] * b;                          // A(j + H, j - t) r_(j-t)
       }
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int i = lane + 32 * k;
-      if (i >= NS) continue;
+    for (int k = 0; k < 2; ++k) {
+      if (lane >= H) break;
+      const int i = lane + H * k;
       if (!interior) {
         out[v * NS + i] = acc[k];
       } else {

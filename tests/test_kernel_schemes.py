@@ -198,3 +198,35 @@ def test_persistent_star_walk_with_prefetch(count, sms):
     assert sorted(done) == list(range(count))
     words = [lane + 32 * q for q in range((NV + 31) // 32) for lane in range(32) if lane + 32 * q < NV]
     assert sorted(words) == list(range(NV))
+
+
+@pytest.mark.parametrize("N", [50, 8])
+def test_wrapped_row_product_paired_rows(N):
+    """The 2D order-3 FP32 kernel's pairing: lane j < N/2 owns rows j and j + N/2 and walks
+    t = 0..N/2, taking row j at step t and row j + N/2 at step N/2 - t, which need the same
+    two r values (r_(j+t) and r_(j-t mod N)); each row gets every forward term once and the
+    transposed terms for 0 < step < N/2, so the product equals A r."""
+    H, WLD = N // 2, (N + 3) // 4 * 4
+    rng = np.random.default_rng(N + 1)
+    A = rng.standard_normal((N, N))
+    A = A + A.T
+    W = np.zeros((H + 1, WLD))
+    for t in range(H + 1):
+        for i in range(N):
+            W[t, i] = A[i, (i + t) % N]
+    r = rng.standard_normal(N)
+    r2 = np.concatenate([r, r])
+    y = np.zeros(N)
+    for j in range(H):
+        acc0 = acc1 = 0.0
+        for t in range(H + 1):
+            a, b = r2[j + t], r2[j - t + N]
+            assert 0 <= j + t < N and 0 <= j - t + N < 2 * N
+            acc0 += W[t, j] * a
+            if 0 < t < H:
+                m = j - t + N if j - t < 0 else j - t
+                acc0 += W[t, m] * b
+                acc1 += W[H - t, j + t] * a
+            acc1 += W[H - t, j + H] * b
+        y[j], y[j + H] = acc0, acc1
+    assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
