@@ -312,11 +312,15 @@ als_status als_profile_read_kernel(als_ctx* ctx, int kind, double* total_ms, lon
  *     `level` (1 <= level < levels, vertex index x-fastest), the FP64 inverse of its
  *     patch matrix in the layout of als_star_smooth_static's `inv` (upper triangle by
  *     diagonals, padded to a multiple of 4 entries; identity rows at absent and
- *     boundary nodes); the FP32 copies of the cycle are rounded from it.
+ *     boundary nodes): np = d (2k - 1)^d dofs a patch at order k (18 / 81 at k = 2,
+ *     50 / 375 at k = 3), (n_l + 1)^d blocks of round_up(np (np + 1) / 2, 4) doubles;
+ *     the FP32 copies of the cycle are rounded from it.
  *   als_load_coarse_inverse: `inv` (host or device) is the nfree x nfree row-major
- *     inverse of the coarsest A_gamma on its free dofs, nfree = d prod(2 n_0 - 1),
+ *     inverse of the coarsest A_gamma on its free dofs, nfree = d prod(k n_0 - 1),
  *     free dofs ordered component-major, then interior nodes x-fastest.
- * Both copy synchronously; als_update_coefficients overwrites them again. */
+ * Both copy synchronously and read exactly those sizes from the caller's buffer (the
+ * Python binding checks the length and dtype first); als_update_coefficients
+ * overwrites them again. */
 als_status als_load_patch_inverses(als_ctx* ctx, int level, const double* packed);
 als_status als_load_coarse_inverse(als_ctx* ctx, const double* inv);
 

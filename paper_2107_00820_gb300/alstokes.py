@@ -168,6 +168,18 @@ def _check_dtype(a, prec):
         raise TypeError(f"expected {want} data for prec={prec}, got {name}")
 
 
+def _check_f64_len(a, need, what):
+    """An FP64 array (NumPy or torch, host or device) of at least `need` entries."""
+    if a is None:
+        raise ValueError(f"{what}: an array is required")
+    name = str(a.dtype)
+    if not name.endswith("float64"):
+        raise TypeError(f"{what}: expected float64 data, got {name}")
+    size = int(a.numel()) if hasattr(a, "numel") else int(a.size)
+    if size < need:
+        raise ValueError(f"{what}: {size} entries, the context needs {need}")
+
+
 def _cuda_tensor(a):
     if not (hasattr(a, "is_cuda") and a.is_cuda):
         raise TypeError("this entry point takes CUDA tensors (device pointers)")
@@ -271,7 +283,7 @@ class Context:
         self._call("als_apply_stokes", _ptr(u), _ptr(p), _ptr(yu), _ptr(yp))
 
     def patch_inverse(self, level, vertex):
-        np_ = self.dim * (2 * self.order - 1) ** self.dim
+        np_ = self.patch_dofs()
         out = np.zeros((np_, np_))
         self._call("als_patch_inverse", level, int(vertex), _ptr(out))
         return out
@@ -317,13 +329,32 @@ class Context:
     def set_patch_kernel(self, level, variant):
         self._call("als_set_patch_kernel", c_int(level), c_int(variant))
 
+    def patch_dofs(self):
+        """Dofs of an interior vertex star: d (2k - 1)^d."""
+        return self.dim * (2 * self.order - 1) ** self.dim
+
+    def coarse_free_dofs(self):
+        """Free velocity dofs of the coarsest level: d prod(k n_0 - 1)."""
+        return self.dim * int(np.prod([self.order * v - 1 for v in self.level_n(0)]))
+
     def load_patch_inverses(self, level, packed):
         """Replace the patch inverses of `level` by FP64 ones packed by diagonals
-        (nverts x stride, host or device); the FP32 copies are rounded from them."""
+        (nverts x stride, host or device); the FP32 copies are rounded from them.
+        The array's dtype and length are checked here, so that the library's copy
+        never reads past the caller's buffer."""
+        if not 1 <= int(level) < self.levels:
+            raise ValueError(f"level must be in [1, {self.levels})")
+        np_ = self.patch_dofs()
+        stride = (np_ * (np_ + 1) // 2 + 3) // 4 * 4
+        nverts = int(np.prod([v + 1 for v in self.level_n(level)]))
+        _check_f64_len(packed, nverts * stride, "packed patch inverses")
         self._call("als_load_patch_inverses", c_int(level), _ptr(packed))
 
     def load_coarse_inverse(self, inv):
-        """Replace the coarse inverse (nfree x nfree FP64, host or device)."""
+        """Replace the coarse inverse (nfree x nfree FP64, host or device); dtype and
+        length checked as for load_patch_inverses."""
+        nf = self.coarse_free_dofs()
+        _check_f64_len(inv, nf * nf, "coarse inverse")
         self._call("als_load_coarse_inverse", _ptr(inv))
 
     def set_wait_limit(self, polls):
@@ -427,7 +458,7 @@ class Batch:
             order = int(opts[i].order)
             nu = dim * int(np.prod([order * v + 1 for v in n]))
             self.shapes.append((nu, pressure_per_cell(dim, order) * int(np.prod(n))))
-            self._meta.append((dim, n, levels))
+            self._meta.append((dim, n, levels, opts[i]))
         out = c_void_p()
         st = lib.als_batch_create(k, meshes, coeffs, gammas, opts, c_void_p(stream) if stream else None, byref(out))
         if st != ALS_OK:
@@ -494,8 +525,8 @@ class Batch:
         self._check(self._lib.als_batch_context(self._b, c_int(i), byref(ptr)))
         ctx = Context.__new__(_BorrowedContext)
         ctx._ctx, ctx._lib = ptr, self._lib
-        dim, n, levels = self._meta[i]
-        ctx.dim, ctx.n, ctx.levels = dim, n, levels
+        dim, n, levels, options = self._meta[i]
+        ctx.dim, ctx.n, ctx.levels, ctx.options = dim, n, levels, options
         return ctx
 
     def close(self):

@@ -191,3 +191,31 @@ def test_static_smoother_binding_checks(lib):
         A.als_star_smooth_static(2, [4, 4], A.ALS_PREC_FP64, np.zeros(8), np.zeros(8), np.zeros(8))
     with pytest.raises(TypeError):
         A.als_star_smooth_static(2, [4, 4], A.ALS_PREC_FP64, torch.zeros(8), torch.zeros(8), torch.zeros(8))
+
+
+@pytest.mark.parametrize("dim,order,n,levels", [(2, 2, (8, 8), 2), (3, 2, (4, 4, 4), 2), (2, 3, (8, 8), 2),
+                                                (3, 3, (4, 4, 4), 2)])
+def test_injection_binding_checks_length_and_dtype(dim, order, n, levels):
+    """Factor injection copies exactly nverts x stride (patches) and nfree^2 (coarse)
+    doubles from the caller's buffer, so the binding refuses a short array, FP32 data, or
+    a level without patches before any call crosses the ABI (the context here has no
+    library handle: reaching the ABI would raise AttributeError instead)."""
+    ctx = A.Context.__new__(A.Context)
+    ctx.dim, ctx.n, ctx.levels = dim, n, levels
+    ctx.options = A.default_options(order=order)
+    np_ = dim * (2 * order - 1) ** dim
+    assert ctx.patch_dofs() == {(2, 2): 18, (3, 2): 81, (2, 3): 50, (3, 3): 375}[(dim, order)]
+    stride = (np_ * (np_ + 1) // 2 + 3) // 4 * 4
+    need = int(np.prod([v + 1 for v in n])) * stride
+    with pytest.raises(ValueError):
+        ctx.load_patch_inverses(1, np.zeros(need - 1))
+    with pytest.raises(TypeError):
+        ctx.load_patch_inverses(1, np.zeros(need, np.float32))
+    with pytest.raises(ValueError):
+        ctx.load_patch_inverses(0, np.zeros(need))
+    nf = dim * int(np.prod([order * v // 2 - 1 for v in n]))
+    assert ctx.coarse_free_dofs() == nf
+    with pytest.raises(ValueError):
+        ctx.load_coarse_inverse(np.zeros(nf * nf - 1))
+    with pytest.raises(TypeError):
+        ctx.load_coarse_inverse(np.zeros(nf * nf, np.float32))
