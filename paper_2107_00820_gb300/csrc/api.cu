@@ -1118,6 +1118,7 @@ als_status als_vcycle(als_ctx* c, int prec, const void* b, void* x) {
 als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void* z) {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no smoother");
+  if (!r || !z) return fail(c, ALS_EINVAL, "null vector");
   MGWork& w = work_for(c, prec);
   begin(c);
   patch_smooth(c->lev[level], prec, r, z, w.scratch[level], c->stream);
@@ -1127,6 +1128,7 @@ als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void*
 als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf) {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "prolongation needs level >= 1");
+  if (!xc || !xf) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   prolong_level(c, work_for(c, prec), level, xc, xf, nullptr);
   return finish(c, "prolong");
@@ -1135,6 +1137,7 @@ als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf
 als_status als_restrict(als_ctx* c, int level, int prec, const void* rf, void* rc) {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "restriction needs level >= 1");
+  if (!rf || !rc) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   restrict_level(c, work_for(c, prec), level, rf, rc);
   return finish(c, "restrict");
@@ -1142,6 +1145,7 @@ als_status als_restrict(als_ctx* c, int level, int prec, const void* rf, void* r
 
 als_status als_coarse_solve(als_ctx* c, int prec, const void* b, void* x) {
   ALS_TRY(check_level(c, 0, prec));
+  if (!b || !x) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   coarse_apply(c->lev[0], c->coarse, prec, b, x, c->stream);
   return finish(c, "coarse_solve");
@@ -1160,6 +1164,7 @@ als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* ou
   if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no patches");
   const LevelDev& Lv = c->lev[level];
   if (vertex < 0 || vertex >= Lv.g.nverts) return fail(c, ALS_EINVAL, "vertex out of range");
+  if (!out) return fail(c, ALS_EINVAL, "null output");
   std::vector<double> packed(Lv.pstride), full((size_t)Lv.np * Lv.np);
   if (cudaMemcpyAsync(packed.data(), Lv.inv64 + vertex * Lv.pstride, sizeof(double) * Lv.pstride,
                       cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||

@@ -190,6 +190,32 @@ def test_solve_history():
     assert h[-1] <= 1e-8 * h[0] < h[-2]
 
 
+def test_null_vectors_refused_through_the_abi():
+    """Every per-level entry point refuses a NULL vector with ALS_EINVAL before it queues
+    any work, and the context stays usable: an apply after the refusals matches the
+    oracle."""
+    pb = sinker(2, 8, 2, 1e2, dr=1e3, seed=65)
+    ctx = context(pb)
+    lib, c = ctx._lib, ctx._ctx
+    v = torch.zeros(ctx.nu(), dtype=torch.float64, device="cuda")
+    p = A.c_void_p(v.data_ptr())
+    calls = [("als_apply_agamma", (c, 1, 0, None, p)), ("als_vcycle", (c, 0, p, None)),
+             ("als_star_smooth", (c, 1, 0, None, p)), ("als_star_smooth", (c, 1, 0, p, None)),
+             ("als_prolong", (c, 1, 0, None, p)), ("als_prolong", (c, 1, 0, p, None)),
+             ("als_restrict", (c, 1, 0, None, p)), ("als_restrict", (c, 1, 0, p, None)),
+             ("als_coarse_solve", (c, 0, None, p)), ("als_coarse_solve", (c, 0, p, None)),
+             ("als_apply_stokes", (c, p, None, p, p)), ("als_patch_inverse", (c, 1, 0, None)),
+             ("als_load_patch_inverses", (c, 1, None)), ("als_load_coarse_inverse", (c, None))]
+    for name, args in calls:
+        assert getattr(lib, name)(*args) == A.ALS_EINVAL, name
+        assert lib.als_last_error(c)
+    H = oracle(pb)
+    x = random_free(H.levels[-1], 66)
+    y = torch.zeros_like(v)
+    ctx.apply_agamma(dev(x), y)
+    assert rel(host(y), H.levels[-1].A @ x) <= 1e-12
+
+
 _SPLIT_SCRIPT = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
