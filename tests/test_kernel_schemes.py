@@ -1,4 +1,5 @@
-"""Host checks of the index schemes of the order-3 star kernels (csrc/qk3.cu, csrc/qk.cu), restated
+"""Host checks of the index schemes of the order-3 star kernels (csrc/qk3.cu, csrc/qk.cu) and of
+the shared-memory layouts of the order-2 3D cell kernel (csrc/apply_lines.cuh), restated
 in NumPy: the enumeration of an upper triangle by paired rows, the symmetric block
 Gauss-Jordan elimination on the upper triangle with the sign invariant
 M_ji = s_i s_j M_ij, the product over wrapped rows W_t[i] = A(i, (i + t) mod N) (odd N in 3D, even in 2D),
@@ -230,3 +231,49 @@ def test_wrapped_row_product_paired_rows(N):
             acc1 += W[H - t, j + H] * b
         y[j], y[j + H] = acc0, acc1
     assert np.abs(y - A @ r).max() <= 1e-12 * np.abs(A).sum(1).max()
+
+
+def _ofs_xy(m, c, x, y, z):
+    return m * 81 + c * 9 + x + 27 * y + 3 * z
+
+
+def _ofs_yz(m, c, x, y, z):
+    return m * 81 + c * 9 + 3 * x + y + 27 * z
+
+
+def _ofs_pt(m, c, x, y, z):
+    return m * 81 + c * 27 + 3 * x + 9 * y + z
+
+
+def test_line_kernel_stage_layouts_are_bank_conflict_free():
+    """The 3D line-per-lane cell kernel: lane (c, b1, b2) = (lane / 9, lane % 3, lane / 3 % 3)
+    of 27 in its line stages, lane = Gauss point (p % 3, p / 3 % 3, p / 9) in its point stage.
+    Every shared-memory access of every stage (one instruction = one fixed array m and one
+    fixed line position) puts the 27 lanes on 27 distinct 4-byte banks, as the layouts'
+    comment states, and so do the staged outputs (lane * 3 + a).  The block write-out
+    (thread (row, cell) = (tid / 8, tid % 8) of 216 reading its cell's three values of a
+    row, cells 243 floats apart) is at most 2-way conflicted: 32 threads on 20 banks; a
+    244-float stride would make it conflict-free."""
+    lanes = [(ln // 9, (ln % 9) % 3, (ln % 9) // 3) for ln in range(27)]
+    pts = [(p % 3, (p // 3) % 3, p // 9) for p in range(27)]
+    accesses = []
+    for m in range(3):
+        for q in range(3):
+            accesses += [
+                [_ofs_xy(m, c, q, b1, b2) for c, b1, b2 in lanes],   # X write, X^T read
+                [_ofs_xy(m, c, b1, q, b2) for c, b1, b2 in lanes],   # Y read, Y^T write
+                [_ofs_yz(m, c, b1, q, b2) for c, b1, b2 in lanes],   # Y write, Y^T read
+                [_ofs_yz(m, c, b1, b2, q) for c, b1, b2 in lanes],   # Z read, Z^T write
+                [_ofs_pt(m, c, b1, b2, q) for c, b1, b2 in lanes],   # Z write, Z^T read
+                [_ofs_pt(m, q, *p) for p in pts],                     # gradient read, flux write
+            ]
+    for a in range(3):
+        accesses.append([ln * 3 + a for ln in range(27)])           # staged x-line outputs
+    for addrs in accesses:
+        assert len(set(addrs)) == 27 and len({x % 32 for x in addrs}) == 27
+    for stride, worst in ((243, 2), (244, 1)):                       # block write-out, 216 threads
+        for warp in range(27 * 8 // 32 + 1):
+            tids = [t for t in range(32 * warp, 32 * warp + 32) if t < 27 * 8]
+            for a in range(3):
+                banks = [((t & 7) * stride + (t >> 3) * 3 + a) % 32 for t in tids]
+                assert max(banks.count(b) for b in set(banks)) == worst
