@@ -255,3 +255,28 @@ def test_solve_in_bench_configuration(full):
     du = np.linalg.norm(um - uf) / np.linalg.norm(uf)
     dp = np.linalg.norm(pm - pf) / np.linalg.norm(pf)
     assert du <= 1e-7 and dp <= 1e-7, (du, dp)
+
+
+@pytest.mark.parametrize("workload", ["sinker3d_32", "sinker3d_32_g1e4"])
+def test_double_float_setup_equals_fp64_setup(workload):
+    """Mixed mode inverts the patches and the coarse operator in double-float arithmetic by
+    default; ALS_SETUP_FP64 inverts them in FP64.  On the bench workload (gamma 10, P1) and at
+    gamma 1e4 (P2), both solved to rtol 1e-12: the same FGMRES iteration counts (to 1e-8 and
+    to 1e-12) and solutions within 1e-9 of each other (measured on a GB300: 8e-13 / 8e-14 at
+    gamma 10, 1.1e-11 / 3.9e-13 at gamma 1e4, u / p)."""
+    spec = bench.WORKLOADS[workload]
+    pb = bench.make_problem(spec)
+    mu = [torch.as_tensor(m, device="cuda") for m in pb.mu]
+    schur = A.ALS_SCHUR_P2 if spec.get("schur") == "P2" else A.ALS_SCHUR_P1
+    res = []
+    for setup in (A.ALS_SETUP_AUTO, A.ALS_SETUP_FP64):
+        ctx = Context(pb.d, pb.n, pb.levels, mu, pb.gamma, mode=A.ALS_MODE_MIXED, sweeps=spec["sweeps"],
+                      schur=schur, setup=setup, rtol=1e-12, maxit=300)
+        u, p, info = ctx.solve(pb.f, pb.u_bc)
+        h = ctx.solve_history()
+        res.append((np.array(u), np.array(p), int(np.flatnonzero(h <= 1e-8 * h[0])[0]), info.iterations))
+        ctx.close()
+    (u0, p0, a0, b0), (u1, p1, a1, b1) = res
+    assert (a0, b0) == (a1, b1)
+    assert np.linalg.norm(u0 - u1) <= 1e-9 * np.linalg.norm(u1)
+    assert np.linalg.norm(p0 - p1) <= 1e-9 * np.linalg.norm(p1)
