@@ -277,3 +277,80 @@ def test_line_kernel_stage_layouts_are_bank_conflict_free():
             for a in range(3):
                 banks = [((t & 7) * stride + (t >> 3) * 3 + a) % 32 for t in tids]
                 assert max(banks.count(b) for b in set(banks)) == worst
+
+
+def _patch_out_index(nv, vx, vy, vz, i):
+    """The row layout of the 3D star-patch outputs (csrc/common.cuh, patch_out_index)."""
+    c, o = divmod(i, 27)
+    ox, oy, oz = o % 3, (o // 3) % 3, o // 9
+    row = ((c * 3 + oz) * 3 + oy) * (nv[1] * nv[2]) + vz * nv[1] + vy
+    return row * (3 * nv[0]) + 3 * vx + ox
+
+
+@pytest.mark.parametrize("n", [(4, 3, 5), (2, 2, 2)])
+def test_fused_patch_gather_in_the_cell_kernel(n):
+    """The 3D cell kernel's x-line input formed from the star-patch outputs (apply_lines.cuh,
+    patch_line): lane (c, b1, b2) of cell (cx, cy, cz) sums, for the nodes 2cx + a of its
+    x-line, the outputs of the <= 8 stars containing each node, read from the row layout as
+    columns 3cx + 1 (a = 0), 3cx + 2 and 3cx + 3 (a = 1), 3cx + 4 (a = 2) of the rows of
+    its <= 4 (y, z) taps; 0 at Dirichlet nodes.  That equals the direct sum over stars, and
+    the owner rule (the cell with the node's lower corner, the last cell for the upper
+    boundary) stores every node of the mesh exactly once."""
+    nv = [v + 1 for v in n]
+    nn = [2 * v + 1 for v in n]
+    rng = np.random.default_rng(sum(n))
+    star = rng.standard_normal((nv[0] * nv[1] * nv[2], 81))      # star outputs, patch dof order
+    out = np.zeros(81 * nv[1] * nv[2] * 3 * nv[0] + 8)
+    for vz in range(nv[2]):
+        for vy in range(nv[1]):
+            for vx in range(nv[0]):
+                v = vx + nv[0] * (vy + nv[1] * vz)
+                for i in range(81):
+                    out[_patch_out_index(nv, vx, vy, vz, i)] = star[v, i]
+    # direct sums: node (ni, nj, nk) of component c collects star v at offset o when
+    # ni = 2 vx + ox - 1 (per axis); 0 on the boundary
+    direct = np.zeros((3, nn[2], nn[1], nn[0]))
+    for vz in range(nv[2]):
+        for vy in range(nv[1]):
+            for vx in range(nv[0]):
+                v = vx + nv[0] * (vy + nv[1] * vz)
+                for i in range(81):
+                    c, o = divmod(i, 27)
+                    ni, nj, nk = 2 * vx + o % 3 - 1, 2 * vy + (o // 3) % 3 - 1, 2 * vz + o // 9 - 1
+                    if 0 < ni < nn[0] - 1 and 0 < nj < nn[1] - 1 and 0 < nk < nn[2] - 1:
+                        direct[c, nk, nj, ni] += star[v, i]
+    stored = np.zeros_like(direct)
+    count = np.zeros(direct.shape, dtype=int)
+    ncol = 3 * nv[0]
+
+    def taps(m):
+        return [(m >> 1, 2), ((m >> 1) + 1, 0)] if m & 1 else [(m >> 1, 1)]
+
+    for cz in range(n[2]):
+        for cy in range(n[1]):
+            for cx in range(n[0]):
+                for c in range(3):
+                    for b2 in range(3):
+                        for b1 in range(3):
+                            nj, nk = 2 * cy + b1, 2 * cz + b2
+                            u = np.zeros(3)
+                            if 0 < nj < nn[1] - 1 and 0 < nk < nn[2] - 1:
+                                acc = np.zeros(3)
+                                for vz_, oz in taps(nk):
+                                    for vy_, oy in taps(nj):
+                                        row = ((c * 3 + oz) * 3 + oy) * (nv[1] * nv[2]) + vz_ * nv[1] + vy_
+                                        rp = row * ncol + 3 * cx
+                                        acc += [out[rp + 1], out[rp + 2] + out[rp + 3], out[rp + 4]]
+                                for a in range(3):
+                                    ni = 2 * cx + a
+                                    u[a] = 0.0 if ni in (0, nn[0] - 1) else acc[a]
+                            for a in range(3):
+                                ni = 2 * cx + a
+                                assert u[a] == pytest.approx(direct[c, nk, nj, ni], abs=1e-12)
+                            if (b1 < 2 or cy == n[1] - 1) and (b2 < 2 or cz == n[2] - 1):
+                                for a in range(3):
+                                    if a < 2 or cx == n[0] - 1:
+                                        stored[c, nk, nj, 2 * cx + a] = u[a]
+                                        count[c, nk, nj, 2 * cx + a] += 1
+    assert np.all(count == 1)
+    assert np.allclose(stored, direct, atol=1e-12)
