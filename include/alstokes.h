@@ -61,7 +61,7 @@ typedef struct als_ctx als_ctx;
 typedef enum {
   ALS_OK = 0,
   ALS_EINVAL = 1,      /* invalid argument (sizes, levels, options, NULL) */
-  ALS_ENOMEM = 2,      /* device allocation failed */
+  ALS_ENOMEM = 2,      /* device or host allocation failed (no C++ exception crosses this ABI) */
   ALS_ECUDA = 3,       /* a CUDA runtime call failed */
   ALS_ENOTSPD = 4,     /* non-positive pivot in the symmetric sweep of a patch or the coarse operator */
   ALS_ENOTCONV = 5,    /* FGMRES did not reach rtol within maxit iterations */

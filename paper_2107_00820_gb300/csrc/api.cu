@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -659,6 +660,20 @@ void matvec(als_ctx* c, const double* x, double* y) {
   op_apply(F, PREC_F64, OP_VISC | OP_AL | OP_BT | OP_B, c->gamma, x, y, x + c->nu, y + c->nu, c->stream);
 }
 
+// No C++ exception crosses the C ABI: every entry point that returns a status is a
+// function-try-block whose handler maps the exception in flight (host containers and
+// strings can throw std::bad_alloc) to a status.  A failure there leaves whatever the
+// call had changed, like any other mid-call failure.
+als_status caught_exception() noexcept {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return ALS_ENOMEM;
+  } catch (...) {
+    return ALS_EINVAL;
+  }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -688,7 +703,7 @@ static thread_local std::string t_create_err;
 
 const char* als_last_error(const als_ctx* ctx) { return ctx ? ctx->err.c_str() : t_create_err.c_str(); }
 
-als_status als_destroy(als_ctx* ctx) {
+als_status als_destroy(als_ctx* ctx) try {
   if (!ctx) return ALS_EINVAL;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   free_graphs(ctx);
@@ -703,6 +718,8 @@ als_status als_destroy(als_ctx* ctx) {
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 // Setup (Secs. 4-5) with the coefficients of every level: copies them, builds
@@ -990,7 +1007,7 @@ static als_status create_impl(als_ctx* c, const als_mesh* mesh, const als_coeff*
 }
 
 als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma, const als_options* opt,
-                      void* stream, als_ctx** out) {
+                      void* stream, als_ctx** out) try {
   t_create_err.clear();
   if (!out) {
     t_create_err = "null output pointer";
@@ -1008,9 +1025,11 @@ als_status als_create(const als_mesh* mesh, const als_coeff* coeff, double gamma
   }
   *out = c;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_update_coefficients(als_ctx* c, const als_coeff* coeff) {
+als_status als_update_coefficients(als_ctx* c, const als_coeff* coeff) try {
   if (!c || !coeff || !coeff->qp) return c ? fail(c, ALS_EINVAL, "null coefficients") : ALS_EINVAL;
   if ((coeff->kind == ALS_COEFF_TENSOR) != (c->lev[0].tensor != 0))
     return fail(c, ALS_EINVAL, "coefficient kind differs from the one the context was created with");
@@ -1018,9 +1037,11 @@ als_status als_update_coefficients(als_ctx* c, const als_coeff* coeff) {
   cudaEventRecord(c->order_ev, c->user_stream);
   cudaStreamWaitEvent(c->stream, c->order_ev, 0);
   return run_setup(c, coeff);
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_profile(als_ctx* c, int on) {
+als_status als_profile(als_ctx* c, int on) try {
   if (!c) return ALS_EINVAL;
   Prof& p = c->prof;
   if ((on != 0) == p.on) return ALS_OK;
@@ -1039,6 +1060,8 @@ als_status als_profile(als_ctx* c, int on) {
   p.acc_ms[0] = p.acc_ms[1] = 0.0;
   p.acc_n[0] = p.acc_n[1] = 0;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 // moves the recorded pairs into the per-kind accumulators
@@ -1058,7 +1081,7 @@ static als_status prof_drain(als_ctx* c) {
   return ALS_OK;
 }
 
-als_status als_profile_read_kernel(als_ctx* c, int kind, double* total_ms, long long* launches) {
+als_status als_profile_read_kernel(als_ctx* c, int kind, double* total_ms, long long* launches) try {
   if (!c || !total_ms || !launches) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
   if (kind < 0 || kind > 1) return fail(c, ALS_EINVAL, "kind must be 0 (patch kernel) or 1 (operator apply)");
   ALS_TRY(prof_drain(c));
@@ -1067,10 +1090,14 @@ als_status als_profile_read_kernel(als_ctx* c, int kind, double* total_ms, long 
   c->prof.acc_ms[kind] = 0.0;
   c->prof.acc_n[kind] = 0;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) {
+als_status als_profile_read(als_ctx* c, double* total_ms, long long* launches) try {
   return als_profile_read_kernel(c, 0, total_ms, launches);
+} catch (...) {
+  return caught_exception();
 }
 
 long long als_kernel_launches(void) { return launch_count(); }
@@ -1094,15 +1121,17 @@ static als_status finish(als_ctx* c, const char* what) {
   return check_status(c, what);
 }
 
-als_status als_apply_agamma(als_ctx* c, int level, int prec, const void* x, void* y) {
+als_status als_apply_agamma(als_ctx* c, int level, int prec, const void* x, void* y) try {
   ALS_TRY(check_level(c, level, prec));
   if (!x || !y) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   op_apply(c->lev[level], prec, OP_VISC | OP_AL, c->gamma, x, y, nullptr, nullptr, c->stream);
   return finish(c, "apply_agamma");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_vcycle(als_ctx* c, int prec, const void* b, void* x) {
+als_status als_vcycle(als_ctx* c, int prec, const void* b, void* x) try {
   ALS_TRY(check_level(c, c ? c->L - 1 : 0, prec));
   if (!b || !x) return fail(c, ALS_EINVAL, "null vector");
   MGWork& w = work_for(c, prec);
@@ -1113,9 +1142,11 @@ als_status als_vcycle(als_ctx* c, int prec, const void* b, void* x) {
   ALS_TRY(run_vcycle(c, w));
   cudaMemcpyAsync(x, w.x[l], bytes, cudaMemcpyDeviceToDevice, c->stream);
   return finish(c, "vcycle");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void* z) {
+als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void* z) try {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no smoother");
   if (!r || !z) return fail(c, ALS_EINVAL, "null vector");
@@ -1123,43 +1154,53 @@ als_status als_star_smooth(als_ctx* c, int level, int prec, const void* r, void*
   begin(c);
   patch_smooth(c->lev[level], prec, r, z, w.scratch[level], c->stream);
   return finish(c, "star_smooth");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf) {
+als_status als_prolong(als_ctx* c, int level, int prec, const void* xc, void* xf) try {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "prolongation needs level >= 1");
   if (!xc || !xf) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   prolong_level(c, work_for(c, prec), level, xc, xf, nullptr);
   return finish(c, "prolong");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_restrict(als_ctx* c, int level, int prec, const void* rf, void* rc) {
+als_status als_restrict(als_ctx* c, int level, int prec, const void* rf, void* rc) try {
   ALS_TRY(check_level(c, level, prec));
   if (level < 1) return fail(c, ALS_EINVAL, "restriction needs level >= 1");
   if (!rf || !rc) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   restrict_level(c, work_for(c, prec), level, rf, rc);
   return finish(c, "restrict");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_coarse_solve(als_ctx* c, int prec, const void* b, void* x) {
+als_status als_coarse_solve(als_ctx* c, int prec, const void* b, void* x) try {
   ALS_TRY(check_level(c, 0, prec));
   if (!b || !x) return fail(c, ALS_EINVAL, "null vector");
   begin(c);
   coarse_apply(c->lev[0], c->coarse, prec, b, x, c->stream);
   return finish(c, "coarse_solve");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_apply_stokes(als_ctx* c, const double* u, const double* p, double* yu, double* yp) {
+als_status als_apply_stokes(als_ctx* c, const double* u, const double* p, double* yu, double* yp) try {
   if (!c || !u || !p || !yu || !yp) return c ? fail(c, ALS_EINVAL, "null vector") : ALS_EINVAL;
   const LevelDev& F = c->lev[c->L - 1];
   begin(c);
   op_apply(F, PREC_F64, OP_VISC | OP_AL | OP_BT | OP_B, c->gamma, u, yu, p, yp, c->stream);
   return finish(c, "apply_stokes");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* out) {
+als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* out) try {
   ALS_TRY(check_level(c, level, PREC_F64));
   if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no patches");
   const LevelDev& Lv = c->lev[level];
@@ -1180,9 +1221,11 @@ als_status als_patch_inverse(als_ctx* c, int level, long long vertex, double* ou
   if (cudaMemcpy(out, full.data(), sizeof(double) * full.size(), cudaMemcpyDefault) != cudaSuccess)
     return cuda_check(c, "patch_inverse copy");
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_load_patch_inverses(als_ctx* c, int level, const double* packed) {
+als_status als_load_patch_inverses(als_ctx* c, int level, const double* packed) try {
   ALS_TRY(check_level(c, level, PREC_F64));
   if (level < 1) return fail(c, ALS_EINVAL, "the coarsest level has no patches");
   if (!packed) return fail(c, ALS_EINVAL, "null inverses");
@@ -1193,31 +1236,39 @@ als_status als_load_patch_inverses(als_ctx* c, int level, const double* packed) 
     return cuda_check(c, "load patch inverses");
   patch_derive32(Lv, c->stream);
   return finish(c, "load patch inverses");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_load_coarse_inverse(als_ctx* c, const double* inv) {
+als_status als_load_coarse_inverse(als_ctx* c, const double* inv) try {
   if (!c || !inv) return c ? fail(c, ALS_EINVAL, "null inverse") : ALS_EINVAL;
   const size_t n = (size_t)c->coarse.nfree;
   begin(c);
   if (cudaMemcpyAsync(c->coarse.inv, inv, sizeof(double) * n * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
     return cuda_check(c, "load coarse inverse");
   return finish(c, "load coarse inverse");
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_set_wait_limit(als_ctx* c, int polls) {
+als_status als_set_wait_limit(als_ctx* c, int polls) try {
   if (!c) return ALS_EINVAL;
   cudaStreamSynchronize(c->stream);
   free_graphs(c);   // the captured cycles embed the limit as a kernel argument
   for (LevelDev& Lv : c->lev) Lv.wait_polls = polls < 0 ? kWaitPolls : polls;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_solve_history(const als_ctx* c, double* out, int cap, int* count) {
+als_status als_solve_history(const als_ctx* c, double* out, int cap, int* count) try {
   if (!c || !count || (cap > 0 && !out)) return ALS_EINVAL;
   const std::vector<double>& h = c->run.hist;
   *count = (int)h.size();
   for (int i = 0; i < cap && i < (int)h.size(); ++i) out[i] = h[i];
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 // ---- the outer solve in stages, so that a batch can interleave the FGMRES
@@ -1407,7 +1458,7 @@ static als_status solve_finish(als_ctx* c, als_solve_info* info) {
 }
 
 als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const double* r2, double* u, double* p,
-                     als_solve_info* info) {
+                     als_solve_info* info) try {
   if (!c) return ALS_EINVAL;
   ALS_TRY(solve_start(c, f_qp, u_bc, r2, u, p));
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "solve rhs");
@@ -1418,6 +1469,8 @@ als_status als_solve(als_ctx* c, const double* f_qp, const double* u_bc, const d
     ALS_TRY(solve_iter_done(c));
   }
   return solve_finish(c, info);
+} catch (...) {
+  return caught_exception();
 }
 
 
@@ -1526,7 +1579,7 @@ void als_newton_default_params(als_newton_params* prm) {
 }
 
 als_status als_newton_solve(als_ctx* c, const als_newton_params* prm, const double* f_qp, const double* u_bc,
-                            double* u, double* p, als_newton_info* info) {
+                            double* u, double* p, als_newton_info* info) try {
   if (!c) return ALS_EINVAL;
   if (!prm || !f_qp || !u || !p) return fail(c, ALS_EINVAL, "parameters, f_qp, u and p are required");
   if (!c->lev[0].tensor || c->opt.schur != ALS_SCHUR_P2)
@@ -1596,9 +1649,11 @@ als_status als_newton_solve(als_ctx* c, const als_newton_params* prm, const doub
   }
   if (!converged) return fail(c, ALS_ENOTCONV, "Newton did not reach rtol within maxit steps");
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, int cap, int* count) {
+als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, int cap, int* count) try {
   if (!c || !count || (cap > 0 && (!res || !linear_its))) return ALS_EINVAL;
   const als_ctx::NewtonBuf& W = c->nw;
   *count = (int)W.hist.size();
@@ -1607,6 +1662,8 @@ als_status als_newton_history(const als_ctx* c, double* res, int* linear_its, in
     linear_its[i] = i == 0 ? 0 : W.lin[i - 1];
   }
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 }  // extern "C"
@@ -2064,7 +2121,7 @@ static als_status batch_fail(als_batch* b, als_status code, const std::string& m
 extern "C" {
 
 als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* coeffs, const double* gammas,
-                            const als_options* opts, void* stream, als_batch** out) {
+                            const als_options* opts, void* stream, als_batch** out) try {
   if (!out) return ALS_EINVAL;
   *out = nullptr;
   if (count < 1 || !meshes || !coeffs || !gammas) {
@@ -2089,9 +2146,11 @@ als_status als_batch_create(int count, const als_mesh* meshes, const als_coeff* 
   b->mode = all ? ALS_BATCH_MERGED : ALS_BATCH_BRANCHES;
   *out = b;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_destroy(als_batch* b) {
+als_status als_batch_destroy(als_batch* b) try {
   if (!b) return ALS_EINVAL;
   for (als_ctx* c : b->ctx) cudaStreamSynchronize(c->stream);
   if (b->mstream) cudaStreamSynchronize(b->mstream);
@@ -2112,17 +2171,21 @@ als_status als_batch_destroy(als_batch* b) {
   for (als_ctx* c : b->ctx) als_destroy(c);
   delete b;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_context(als_batch* b, int i, als_ctx** ctx) {
+als_status als_batch_context(als_batch* b, int i, als_ctx** ctx) try {
   if (!b || !ctx) return ALS_EINVAL;
   if (i < 0 || i >= (int)b->ctx.size()) return batch_fail(b, ALS_EINVAL, "instance index out of range");
   *ctx = b->ctx[i];
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 als_status als_batch_solve(als_batch* b, const double* const* f_qp, const double* const* u_bc,
-                           const double* const* r2, double* const* u, double* const* p, als_solve_info* infos) {
+                           const double* const* r2, double* const* u, double* const* p, als_solve_info* infos) try {
   if (!b || !f_qp || !u || !p) return ALS_EINVAL;
   const int n = (int)b->ctx.size();
   std::vector<als_status> st(n, ALS_OK);
@@ -2231,9 +2294,11 @@ als_status als_batch_solve(als_batch* b, const double* const* f_qp, const double
     }
   }
   return first;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void* const* xv) {
+als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void* const* xv) try {
   if (!b || !bv || !xv) return ALS_EINVAL;
   if (prec != PREC_F64 && prec != PREC_F32) return batch_fail(b, ALS_EINVAL, "prec must be FP64 or FP32");
   const int n = (int)b->ctx.size();
@@ -2328,11 +2393,13 @@ als_status als_batch_vcycle(als_batch* b, int prec, const void* const* bv, void*
     if (st != ALS_OK) return batch_fail(b, st, b->ctx[i]->err);
   }
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 const char* als_batch_last_error(const als_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
-als_status als_batch_set_mode(als_batch* b, int mode) {
+als_status als_batch_set_mode(als_batch* b, int mode) try {
   if (!b) return ALS_EINVAL;
   if (mode != ALS_BATCH_MERGED && mode != ALS_BATCH_BRANCHES) return batch_fail(b, ALS_EINVAL, "unknown batch mode");
   if (mode == ALS_BATCH_MERGED)
@@ -2343,9 +2410,11 @@ als_status als_batch_set_mode(als_batch* b, int mode) {
     }
   b->mode = mode;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_set_grouping(als_batch* b, int grouping) {
+als_status als_batch_set_grouping(als_batch* b, int grouping) try {
   if (!b) return ALS_EINVAL;
   if (grouping < -1 || grouping >= kGroupings) return batch_fail(b, ALS_EINVAL, "grouping must be -1 .. 4");
   for (als_ctx* c : b->ctx) cudaStreamSynchronize(c->stream);
@@ -2364,15 +2433,19 @@ als_status als_batch_set_grouping(als_batch* b, int grouping) {
   for (float& t : b->plan_ms) t = -1.f;
   b->forced_grouping = grouping;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_get_mode(const als_batch* b, int* mode) {
+als_status als_batch_get_mode(const als_batch* b, int* mode) try {
   if (!b || !mode) return ALS_EINVAL;
   *mode = b->mode;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_batch_merged_plan(const als_batch* b, int* grouping, int* groups, float* ms, long long* kernels) {
+als_status als_batch_merged_plan(const als_batch* b, int* grouping, int* groups, float* ms, long long* kernels) try {
   if (!b || !grouping || !groups) return ALS_EINVAL;
   if (!b->plan.exec) return ALS_EINVAL;
   *grouping = b->plan.grouping;
@@ -2381,10 +2454,12 @@ als_status als_batch_merged_plan(const als_batch* b, int* grouping, int* groups,
     for (int k = 0; k < kGroupings; ++k) ms[k] = b->plan_ms[k];
   if (kernels) *kernels = b->plan.kernels;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 als_status als_batch_merged_tune(const als_batch* b, int group, int level, int* products_variant,
-                                 int* interior_variant, float* ms, int* instances) {
+                                 int* interior_variant, float* ms, int* instances) try {
   if (!b || !products_variant || !interior_variant) return ALS_EINVAL;
   if (!b->plan.exec || group < 0 || group >= (int)b->plan.g.size()) return ALS_EINVAL;
   const MergedCycle& M = b->plan.g[group];
@@ -2400,9 +2475,11 @@ als_status als_batch_merged_tune(const als_batch* b, int group, int level, int* 
     for (size_t i = 0; i < M.inst.size(); ++i)
       instances[i] = (int)(std::find(b->ctx.begin(), b->ctx.end(), M.inst[i]) - b->ctx.begin());
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_set_patch_kernel(als_ctx* c, int level, int variant) {
+als_status als_set_patch_kernel(als_ctx* c, int level, int variant) try {
   if (!c) return ALS_EINVAL;
   if (level < 1 || level >= c->L) return fail(c, ALS_EINVAL, "level must be in [1, levels)");
   if (variant < -1 || variant > 2) return fail(c, ALS_EINVAL, "variant must be -1, 0, 1 or 2");
@@ -2410,9 +2487,11 @@ als_status als_set_patch_kernel(als_ctx* c, int level, int variant) {
   free_graphs(c);   // the captured cycles embed the variant
   c->lev[level].patch_kernel = variant;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
-als_status als_autotune_info(als_ctx* c, int level, int* variant, float* ms) {
+als_status als_autotune_info(als_ctx* c, int level, int* variant, float* ms) try {
   if (!c || !variant) return c ? fail(c, ALS_EINVAL, "null output") : ALS_EINVAL;
   if (level < 1 || level >= c->L) return fail(c, ALS_EINVAL, "level must be in [1, levels)");
   const LevelDev& Lv = c->lev[level];
@@ -2420,6 +2499,8 @@ als_status als_autotune_info(als_ctx* c, int level, int* variant, float* ms) {
   if (ms)
     for (int k = 0; k < 3; ++k) ms[k] = Lv.patch_kernel >= 0 ? Lv.tune_ms[k] : 0.f;
   return ALS_OK;
+} catch (...) {
+  return caught_exception();
 }
 
 }  // extern "C"
