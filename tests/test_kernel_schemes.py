@@ -354,3 +354,66 @@ def test_fused_patch_gather_in_the_cell_kernel(n):
                                         count[c, nk, nj, 2 * cx + a] += 1
     assert np.all(count == 1)
     assert np.allclose(stored, direct, atol=1e-12)
+
+
+def _launch_batch_tables(blocks, kmax=64):
+    """csrc/batch.cuh, launch_batch: consecutive groups of at most kmax items with blocks,
+    each a table of start offsets (items with no blocks left out)."""
+    tables, i = [], 0
+    while i < len(blocks):
+        start, items, total = [], [], 0
+        while i < len(blocks) and len(items) < kmax:
+            if blocks[i]:
+                start.append(total)
+                items.append(i)
+                total += blocks[i]
+            i += 1
+        start.append(total)
+        if items:
+            tables.append((start, items))
+    return tables
+
+
+def _batch_slot(start, count, b):
+    lo, hi = 0, count - 1
+    while lo < hi:
+        mid = (lo + hi + 1) >> 1
+        if start[mid] <= b:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_merged_launch_work_list(seed):
+    """Merged batch launches (csrc/batch.cuh): every block of every launch finds, by the
+    binary search over the start offsets, the one item whose range holds it, and each item
+    with blocks gets exactly its blocks, once, with local indices 0 .. blocks - 1; items
+    with none get no launch slot.  Persistent shares: at least one block and at most
+    min(work, cap) per item with work, none without, in proportion to the work."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 150))
+    blocks = [int(b) for b in rng.integers(0, 9, n) * (rng.random(n) < 0.8)]
+    seen = {}
+    for start, items in _launch_batch_tables(blocks):
+        assert len(items) <= 64
+        for b in range(start[-1]):
+            s = _batch_slot(start, len(items), b)
+            assert start[s] <= b < start[s + 1]
+            seen.setdefault(items[s], []).append(b - start[s])
+    for i, nb in enumerate(blocks):
+        assert sorted(seen.get(i, [])) == list(range(nb))
+    work = [int(w) for w in rng.integers(0, 5000, n)]
+    cap, capacity = int(rng.integers(1, 64)), int(rng.integers(100, 3000))
+    W = sum(work)
+    shares = []
+    for w in work:
+        b = 0 if w <= 0 else min(max(-(-capacity * w // W), 1), w, cap)
+        shares.append(b)
+        if w:
+            assert 1 <= b <= min(w, cap)
+        else:
+            assert b == 0
+    if W:
+        assert sum(shares) <= capacity + n
