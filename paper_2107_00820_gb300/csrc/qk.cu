@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(32 * star_warps<T>()) k_qk_star_apply(Geom g, 
   }
 }
 
-// The FP32 product from the wrapped rows, a star per warp (8 warps a block), the star's rows
-// staged in shared memory, r held twice over so that no index wraps;
+// The FP32 product from the wrapped rows, one star at a time per warp (8 warps a block), the
+// star's rows staged in shared memory, r held twice over so that no index wraps;
 // y_i = sum_(t <= NS/2) W_t[i] r_(i+t) + sum_(0 < t < NS/2) W_t[i-t] r_(i-t) (indices mod NS),
 // rows i and i + NS/2 on one lane (see below).
 // interior / mode as k_qk_star_apply.  Persistent: the host sizes the grid to
